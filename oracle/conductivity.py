@@ -1,0 +1,173 @@
+"""Thermal conductivity of the oracle: BTE-RTA for crystals and QHGK.
+
+Plain FP64 NumPy.  TEST INFRASTRUCTURE ONLY: the library never imports this
+module.
+
+BTE-RTA (paper Eq. RTA, Eq. heat_capacity):
+  kappa_ab = 1/(N_k V) sum_mu c_mu v_mu,a v_mu,b tau_mu,  tau = 1/(2 gamma),
+  c_mu = hbar omega dn/dT = kB x^2 e^x / (e^x - 1)^2,  x = hbar omega / kB T
+  (classical limit c = kB, section "Classical limit").
+  Reading for degenerate modes (paper silent): inside each degenerate set D
+  at one q, v_a v_b is replaced by the basis-invariant trace
+  sum_{s,s' in D} Re(V^a_{ss'} conj(V^b_{ss'})), which equals v_a v_b
+  outside degeneracies.
+
+QHGK (paper Eq. conductivity_amorphous, twod_heat_capacity,
+generalized_velocity, lorentzian_amorphous):
+  kappa_ab = 1/V sum_{mu mu'} c_{mu mu'} Re(v^a_{mu mu'} conj(v^b_{mu mu'})) tau_{mu mu'}
+  c_{mu mu'} = (hbar omega omega' / T) (n' - n) / (omega - omega')   [reading:
+      the printed order of n - n' gives -c_mu in the limit omega' -> omega;
+      the limit c_mu is used for |d nu| < degen_tol]
+  tau_{mu mu'} = (gamma + gamma') / ((omega - omega')^2 + (gamma + gamma')^2)
+  v^a_{mu mu'} = i (E^T A_a E)_{mu mu'} / (2 sqrt(omega omega'))   [reading of
+      the garbled print: A_a(i, j) = sum_L (x_i - x_j - L)_a D(i, jL), the
+      real antisymmetric position-weighted dynamical matrix with true image
+      distances; i A_a is Hermitian]
+Units: kappa in W/(m K); V in A^3; v in A/ps; tau in ps; c in J/K.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+from kald_inputs.lattice import mesh_qpoints
+from .anharmonic import bose
+from .phonons import degenerate_sets, velocity_matrices
+from .units import EV_A2_AMU, HBAR_EVPS, KB_EVK, KB_JK, TWO_PI
+
+#: (J/K) (A/ps)^2 ps / A^3  ->  W / (m K)
+KAPPA_SI = 1e4 * 1e-12 / 1e-30
+
+
+def heat_capacity(omega, T, classical=False):
+    """c_mu in J/K for omega in rad/ps (0 where omega <= 0)."""
+    omega = np.asarray(omega, dtype=float)
+    out = np.zeros_like(omega)
+    good = omega > 0
+    if classical:
+        out[good] = KB_JK
+        return out
+    x = HBAR_EVPS * omega[good] / (KB_EVK * T)
+    ex = np.exp(-x)
+    out[good] = KB_JK * x * x * ex / (1.0 - ex) ** 2
+    return out
+
+
+def kappa_rta(sys, mesh, nu, eig, gamma, T, omega_min_thz=0.01, degen_tol_thz=1e-5,
+              classical=False):
+    """3x3 kappa (W/(m K)) from Eq. RTA with the degenerate trace form."""
+    qs = mesh_qpoints(sys.lattice, mesh)
+    nq = qs.shape[0]
+    kappa = np.zeros((3, 3))
+    for k in range(nq):
+        V = velocity_matrices(sys, qs[k], eig[k], nu[k])
+        omega = TWO_PI * nu[k]
+        valid = nu[k] > omega_min_thz
+        c = heat_capacity(np.where(valid, omega, 0.0), T, classical)
+        for D in degenerate_sets(nu[k], degen_tol_thz):
+            D = [s for s in D if valid[s] and gamma[k, s] > 0]
+            if not D:
+                continue
+            sub = V[:, D][:, :, D]                                   # [3, d, d]
+            vv = np.real(np.einsum("ast,bst->ab", sub, sub.conj()))  # trace form
+            # c and tau are equal inside a set (gamma already averaged)
+            ct = np.mean(c[D] / (2.0 * gamma[k, D]))
+            kappa += ct * vv
+    return kappa * KAPPA_SI / (nq * sys.volume)
+
+
+def position_weighted_dynmat(sys):
+    """A_a [3, nb, nb] (eV/(A amu)): A_a(i,j) = sum_L (x_i - x_j - L)_a
+    Phi2(i, jL) / sqrt(m_i m_j), with L the image each block is seen through."""
+    nb = 3 * sys.n_atoms
+    m = sys.masses
+    i = sys.fc2_idx[:, 0]
+    j = sys.fc2_idx[:, 1]
+    L = sys.fc2_idx[:, 2:5].astype(float) @ sys.lattice
+    d = sys.positions[i] - sys.positions[j] - L                        # [B, 3]
+    blk = sys.fc2 / np.sqrt(m[i] * m[j])[:, None, None]
+    A = np.zeros((3, nb, nb))
+    for b in range(blk.shape[0]):
+        for a in range(3):
+            A[a, 3 * i[b]:3 * i[b] + 3, 3 * j[b]:3 * j[b] + 3] += d[b, a] * blk[b]
+    return A
+
+
+def generalized_velocity(sys, nu, eig, omega_min_thz=0.01):
+    """W_a [3, nb, nb] (A/ps), the imaginary part of v^a_{mu mu'}:
+    v^a = i W_a with W_a = (E^T A_a E) / (2 sqrt(omega omega'))
+    (Eq. generalized_velocity, reading above).  Masked modes give zero rows."""
+    E = eig[0].real.T                                   # columns = modes
+    omega = TWO_PI * nu[0]
+    valid = nu[0] > omega_min_thz
+    w = np.where(valid, omega, 1.0)
+    A = position_weighted_dynmat(sys)
+    W = np.einsum("dm,ade,en->amn", E, A, E) * EV_A2_AMU
+    W = W / (2.0 * np.sqrt(np.outer(w, w)))[None]
+    W[:, ~valid, :] = 0.0
+    W[:, :, ~valid] = 0.0
+    return W
+
+
+def generalized_heat_capacity(omega, T, degen_tol_omega, classical=False):
+    """c_{mu mu'} [nb, nb] (J/K) for valid omega (rad/ps) (reading above)."""
+    n = bose(omega, T, classical)
+    c = heat_capacity(omega, T, classical)
+    w1, w2 = omega[:, None], omega[None, :]
+    dw = w1 - w2
+    close = np.abs(dw) < degen_tol_omega
+    safe = np.where(close, 1.0, dw)
+    hbar_J = HBAR_EVPS * 1.602176634e-19 * 1e-12       # J s
+    # (hbar omega omega' / T) (n' - n)/(omega - omega'); omega in rad/ps -> 1e12
+    cc = hbar_J * (w1 * 1e12) * (w2 * 1e12) / T * (n[None, :] - n[:, None]) / (safe * 1e12)
+    cmid = 0.5 * (c[:, None] + c[None, :])
+    return np.where(close, cmid, cc)
+
+
+def lorentzian_tau(omega, gamma):
+    """tau_{mu mu'} [nb, nb] in ps (Eq. lorentzian_amorphous)."""
+    gs = gamma[:, None] + gamma[None, :]
+    dw = omega[:, None] - omega[None, :]
+    den = dw * dw + gs * gs
+    return np.where(den > 0, gs / np.where(den > 0, den, 1.0), 0.0)
+
+
+def kappa_qhgk(sys, nu, eig, gamma, T, omega_min_thz=0.01, degen_tol_thz=1e-5,
+               classical=False, W=None):
+    """3x3 kappa (W/(m K)) of a Gamma-only system (Eq. conductivity_amorphous)."""
+    omega = TWO_PI * nu[0]
+    valid = (nu[0] > omega_min_thz) & (gamma > 0)
+    if W is None:
+        W = generalized_velocity(sys, nu, eig, omega_min_thz)
+    cc = generalized_heat_capacity(np.where(valid, omega, 1.0), T, TWO_PI * degen_tol_thz, classical)
+    tau = lorentzian_tau(omega, np.where(valid, gamma, 0.0))
+    pair = valid[:, None] & valid[None, :]
+    wgt = np.where(pair, cc * tau, 0.0)
+    kappa = np.einsum("mn,amn,bmn->ab", wgt, W, W)
+    return kappa * KAPPA_SI / sys.volume
+
+
+def kappa_qhgk_mesh(sys, mesh, nu, eig, gamma, T, omega_min_thz=0.01, degen_tol_thz=1e-5,
+                    classical=False, degenerate_pairs_only=False):
+    """q-resolved QHGK on a mesh (same-q interband pairs), with velocities in
+    the atom-position phase gauge; equals kappa_qhgk of the folded supercell.
+    degenerate_pairs_only keeps the pairs with |d nu| < degen_tol (the part
+    that reduces to BTE-RTA)."""
+    qs = mesh_qpoints(sys.lattice, mesh)
+    nq = qs.shape[0]
+    kappa = np.zeros((3, 3))
+    for k in range(nq):
+        valid = (nu[k] > omega_min_thz) & (gamma[k] > 0)
+        # eigenvectors in the atom-phase gauge: eta~ = P eta, P = diag(exp(i q.x))
+        ph = np.exp(1j * (np.repeat(sys.positions, 3, axis=0) @ qs[k]))
+        eig_t = eig[k] * ph[None, :]
+        V = velocity_matrices(sys, qs[k], eig_t, nu[k], atom_phase=True)
+        omega = TWO_PI * nu[k]
+        cc = generalized_heat_capacity(np.where(valid, omega, 1.0), T, TWO_PI * degen_tol_thz, classical)
+        tau = lorentzian_tau(omega, np.where(valid, gamma[k], 0.0))
+        pair = valid[:, None] & valid[None, :]
+        if degenerate_pairs_only:
+            pair &= np.abs(nu[k][:, None] - nu[k][None, :]) < degen_tol_thz
+        wgt = np.where(pair, cc * tau, 0.0)
+        kappa += np.real(np.einsum("mn,amn,bmn->ab", wgt, V, V.conj()))
+    return kappa * KAPPA_SI / (nq * sys.volume)
