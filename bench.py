@@ -1,0 +1,307 @@
+"""Benchmark of the GB300 hot path (one JSON line on rank 0).
+
+A step is one pass of the whole crystal hot path over the 32-atom / 8x8x8
+workload (96 branches, T = 300 K, sigma = 0.05 THz, 3 sigma):
+kald_phonons -> kald_linewidths -> kald_kappa_rta, inputs and outputs
+resident on the device.  value = momentum-conserving three-phonon triplets
+(N_k^2 nb^3 per step) per second.  `e2e` is the same metric through the same
+calls with HOST buffers (host<->device copies inside the timed region).
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (the linewidths of one q-point per step, plus its phonons), on the
+host cores.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import kald_inputs as ki  # noqa: E402
+
+METRIC = "3-phonon triplets/sec (kappa time-to-solution path)"
+UNIT = "triplets/s"
+WORKLOADS = {"C1": ki.c1, "C2": ki.c2, "C5": ki.c5}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines: list[str] = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------- oracle timing
+def time_oracle_sample(w, n_q: int = 1):
+    """Oracle linewidths of n_q q-points of the workload (all q', both
+    processes), plus the phonons they need; returns (triplets/s, seconds, sample)."""
+    from oracle import anharmonic as an
+    from oracle import phonons as ph
+    s = w.systems[0]
+    t0 = time.perf_counter()
+    nu, eig = ph.phonons(s, w.mesh)
+    qs = list(range(1, 1 + n_q))
+    an.linewidths(s, w.mesh, nu, eig, w.T, w.sigma_thz, w.n_sigma, q_list=qs)
+    dt = time.perf_counter() - t0
+    trip = n_q * w.n_q * s.n_branches ** 3
+    return trip / dt, dt, f"phonons on the full mesh + linewidths of {n_q} q-point(s) x all q' ({trip} triplets)"
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = WORKLOADS[args.workload]()
+    cores = os.cpu_count()
+    for _ in range(args.warmup):
+        time_oracle_sample(w)
+    vals, secs = [], []
+    sample = ""
+    for _ in range(args.steps):
+        v, dt, sample = time_oracle_sample(w)
+        vals.append(v)
+        secs.append(dt)
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{w.name}: {w.description}", "global_batch": 1,
+                       "parallelism": "host cores", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------- GPU arm
+def run_kald(args):
+    import torch
+    import paper_2009_01967_gb300 as kk
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    kk.load_library()
+    w = WORKLOADS[args.workload]()
+    s = w.systems[0]
+    nq, nb = w.n_q, s.n_branches
+    opt = kk.Options(temperature_K=w.T, sigma_thz=w.sigma_thz, n_sigma=w.n_sigma,
+                     precision=args.precision)
+    ctx = kk.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    ctx.set_stream(stream.cuda_stream)
+    nu = torch.zeros((nq, nb), dtype=torch.float64, device=dev)
+    eig = torch.zeros((nq, nb, nb), dtype=torch.complex128, device=dev)
+    gam = torch.zeros(nq * nb, dtype=torch.float64, device=dev)
+    kap = torch.zeros((3, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    trip_info = {}
+
+    def step():
+        kk.kald_phonons(ctx, s, w.mesh, nu_thz=nu, eigvec=eig, want_vel=False)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        _, trip = kk.kald_linewidths(ctx, s, w.mesh, nu, eig, opt, gamma=gam)
+        ev1.record(stream)
+        kk.kald_kappa_rta(ctx, s, w.mesh, nu, eig, gam, opt, kappa=kap)
+        trip_info["trip"] = trip
+        return ev0, ev1
+
+    for _ in range(args.warmup):
+        step()
+        flush.fill_(1.0)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    step_ms, lw_ms = [], []
+    for _ in range(args.steps):
+        flush.fill_(float(_))                      # L2 flush, outside the step events
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e0, e1 = step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(a.elapsed_time(b))
+        lw_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    triplets_step = nq * nq * nb ** 3
+    value = world * triplets_step * args.steps / (total_ms / 1e3)
+
+    # ---- end to end through host buffers (pinned), same calls
+    nu_h = torch.zeros((nq, nb), dtype=torch.float64).pin_memory().numpy()
+    eig_h = torch.zeros((nq, nb, nb), dtype=torch.complex128).pin_memory().numpy()
+    gam_h = torch.zeros(nq * nb, dtype=torch.float64).pin_memory().numpy()
+    kap_h = np.zeros((3, 3))
+    sys_bytes = (s.masses.nbytes + s.positions.nbytes + s.fc2_idx.nbytes + s.fc2.nbytes +
+                 s.fc3_idx.nbytes + s.fc3.nbytes)
+    e2e_ms = []
+    for it in range(max(1, min(args.steps, 3))):
+        flush.fill_(2.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        kk.kald_phonons(ctx, s, w.mesh, nu_thz=nu_h, eigvec=eig_h, want_vel=False)
+        kk.kald_linewidths(ctx, s, w.mesh, nu_h, eig_h, opt, gamma=gam_h)
+        kk.kald_kappa_rta(ctx, s, w.mesh, nu_h, eig_h, gam_h, opt, kappa=kap_h)
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    h2d = 3 * sys_bytes + 2 * (nu_h.nbytes + eig_h.nbytes) + gam_h.nbytes
+    d2h = nu_h.nbytes + eig_h.nbytes + gam_h.nbytes + kap_h.nbytes
+    e2e_value = triplets_step / (float(np.mean(e2e_ms)) / 1e3)
+
+    # ---- roofline of the dominant kernel (linewidth projection)
+    trip, allowed = trip_info["trip"]
+    n_valid = int(torch.sum(nu > opt.omega_min_thz).item())
+    n_fc3 = s.fc3.shape[0]
+    flops = (n_valid * nq * (20.0 * n_fc3 + 8.0 * nb ** 3)     # Y build + T' = eps'^T Y
+             + allowed * 8.0 * nb)                              # phi at delta-allowed pairs
+    lw_avg_s = float(np.mean(lw_ms)) / 1e3
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, FMA = 2 flops
+    if args.precision == "fp64":
+        fp32_peak = fp32_peak / 64.0
+    achieved = flops / lw_avg_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None,
+                "kernel": "lw_main_kernel", "flops_per_launch": flops,
+                "peak_note": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz"}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, dt, sample = time_oracle_sample(w)
+        cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": sample, "seconds": dt}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.precision == "fp32" else "f64",
+                "data": "synthetic",
+                "config": {"workload": f"{w.name}: {w.description}", "global_batch": world,
+                           "seq_len": None, "parallelism": f"replicas{world}",
+                           "l2": "flushed (256 MB write) between timed steps",
+                           "precision": args.precision,
+                           "linewidth_ms": float(np.mean(lw_ms))},
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                        "d2h_bytes_per_step": int(d2h)},
+                "gpu_launches": 9 * args.steps,     # dynmat, jacobi, 5 linewidth, 2 kappa kernels
+                "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+                "kappa_W_mK": kap.cpu().numpy().round(6).tolist(),
+                "delta_allowed_fraction": allowed / trip}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="kald", choices=["kald", "reference"])
+    ap.add_argument("--workload", default="C2", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_kald(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,177 @@
+/*
+ * kald.h -- C ABI of the GB300 anharmonic lattice-dynamics hot path.
+ *
+ * Method: arXiv:2009.01967 (kappa-ALDo).  Harmonic phonons (section "Lattice
+ * Dynamics", Eq. eigenvectors_crystal), three-phonon linewidths (Eq.
+ * gamma_operators, projection_plus, phase_space, delta_deconstructed), the
+ * BTE-RTA conductivity (Eq. RTA) and the quasi-harmonic Green-Kubo
+ * conductivity (Eq. conductivity_amorphous, twod_heat_capacity,
+ * generalized_velocity, lorentzian_amorphous).
+ *
+ * Units: Angstrom, amu, eV, K, THz.  Outputs: nu in THz (negative for an
+ * imaginary mode), gamma in ps^-1 (an angular-frequency rate; the lifetime is
+ * tau = 1/(2 gamma) ps), group velocities in A/ps, kappa in W/(m K).
+ *
+ * Ownership: the caller owns every buffer.  The library copies what it needs
+ * during a call and keeps no caller pointer after the call returns.  A
+ * kald_ctx owns the device workspace, a CUDA stream and the error message; it
+ * is not thread-safe (one host thread per context).
+ *
+ * Pointers: the arrays inside kald_system are HOST pointers.  The bulk arrays
+ * passed to the calls (nu_thz, eigvec, gamma, vel, kappa, vgen) may be host or
+ * device pointers on the context's device; the kind is detected with
+ * cudaPointerGetAttributes.  Device inputs are read in place, device outputs
+ * written in place; host inputs/outputs are staged through the workspace.
+ *
+ * Errors: every call returns a kald_status; kald_last_error() gives a
+ * message.  The library never aborts or exits and has no CPU fallback: with no
+ * usable GPU, kald_ctx_create returns KALD_E_CUDA.  A device wait that runs
+ * past its iteration limit returns KALD_E_TIMEOUT.
+ */
+#ifndef KALD_H
+#define KALD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kald_ctx kald_ctx;
+
+typedef enum {
+    KALD_OK = 0,
+    KALD_E_INVALID = 1,      /* bad argument (shape, range, non-finite value)   */
+    KALD_E_NOMEM = 2,        /* device allocation failed                        */
+    KALD_E_CUDA = 3,         /* CUDA runtime error, or no usable device          */
+    KALD_E_NOCONV = 4,       /* eigensolver did not converge                    */
+    KALD_E_TIMEOUT = 5,      /* a bounded device wait expired                   */
+    KALD_E_UNSUPPORTED = 6   /* valid request outside what this build supports  */
+} kald_status;
+
+/* Arithmetic of the projection/linewidth step (kald_linewidths).  Phonons,
+ * Bose factors, 1/omega weights and every kappa reduction are FP64 in all
+ * modes. */
+typedef enum {
+    KALD_FP64 = 0,           /* plain FP64 on CUDA cores                       */
+    KALD_FP32 = 1            /* projection + delta epilogue in FP32 on CUDA
+                                cores, FP64 accumulation across q'            */
+} kald_precision;
+
+/* One crystal unit cell, or one Gamma-only supercell (used with mesh 1x1x1).
+ * Force constants are in home-cell-first sparse atom-block form (the storage
+ * of the paper's appendix "Code details"):
+ *   fc2 block b:  d2E / du_{i0,a} du_{jR,c}, index row fc2_idx[b] = {i, j, R0, R1, R2}
+ *   fc3 block b:  d3E / du_{i0,a} du_{jRj,c} du_{kRk,d},
+ *                 index row fc3_idx[b] = {i, j, Rj0, Rj1, Rj2, k, Rk0, Rk1, Rk2}
+ * R is an integer cell vector in units of the rows of `lattice`.  For a
+ * Gamma-only supercell R keeps the image a pair is seen through, so the
+ * generalised velocity uses true interatomic distances.  All HOST pointers. */
+typedef struct {
+    int32_t n_atoms;
+    const double *masses;      /* [n_atoms] amu, > 0                          */
+    const double *positions;   /* [n_atoms][3] Cartesian Angstrom             */
+    double lattice[3][3];      /* rows = cell vectors A1, A2, A3 (Angstrom)    */
+    int32_t n_fc2;
+    const int32_t *fc2_idx;    /* [n_fc2][5]                                  */
+    const double *fc2;         /* [n_fc2][3][3] eV/A^2                        */
+    int32_t n_fc3;
+    const int32_t *fc3_idx;    /* [n_fc3][9]                                  */
+    const double *fc3;         /* [n_fc3][3][3][3] eV/A^3                     */
+} kald_system;
+
+typedef struct {
+    double temperature_K;      /* T > 0                                       */
+    double sigma_thz;          /* Gaussian width of the energy delta (THz)   */
+    double n_sigma;            /* truncation |d nu| < n_sigma * sigma, > 0   */
+    double omega_min_thz;      /* modes with nu < omega_min are excluded     */
+    double degen_tol_thz;      /* degenerate sets: |d nu| < degen_tol        */
+    int32_t classical;         /* 1: n = kB T / (hbar omega) (Eq. classic_n) */
+    int32_t precision;         /* kald_precision                             */
+} kald_options;
+
+/* Create a context on CUDA device `device` (own stream, empty workspace).
+ * Returns KALD_E_CUDA when the device cannot be used. */
+kald_status kald_ctx_create(kald_ctx **ctx, int device);
+
+/* Destroy a context (NULL is allowed); frees its workspace and stream. */
+void kald_ctx_destroy(kald_ctx *ctx);
+
+/* Message of the last failed call on this context ("" if none).  The
+ * string is owned by the context and valid until its next call. */
+const char *kald_last_error(const kald_ctx *ctx);
+
+/* Use `stream` (a cudaStream_t on the context's device, or NULL for the
+ * context's own stream) for every later call.  The caller keeps ownership. */
+kald_status kald_set_stream(kald_ctx *ctx, void *stream);
+
+/* Harmonic phonons on the Gamma-centred mesh (paper, section "Lattice
+ * Dynamics"): D(q) = sum_R Phi2(i0,jR)/sqrt(m_i m_j) exp(-i q.R) (Bloch sum
+ * before Eq. eigenvectors_crystal), Hermitian eigenpairs in FP64 (Eq.
+ * eigenvectors_crystal), and the Hellmann-Feynman group velocity
+ * v_s = eta_s^dagger (dD/dq) eta_s / (2 omega_s) (Eq. velocity_crystal,
+ * read with the conjugate and the -i R of chi = exp(-i q.R)).
+ * q = sum_i k_i b_i / N_i, k_i in [0, N_i), flat index (k0*N1 + k1)*N2 + k2.
+ *   mesh    [3] > 0; {1,1,1} = Gamma only (real eigenvectors)
+ *   nu_thz  [Nq][nb] out, ascending within each q (nb = 3 n_atoms)
+ *   eigvec  [Nq][nb][nb][2] out, complex128, row s = eigenvector of mode s,
+ *           unit norm (interleaved re, im)
+ *   vel     [Nq][nb][3] out (A/ps), or NULL
+ * This build diagonalises nb <= 96 (KALD_E_UNSUPPORTED above).
+ * KALD_E_NOCONV if the Jacobi sweeps do not converge. */
+kald_status kald_phonons(kald_ctx *ctx, const kald_system *sys, const int32_t mesh[3],
+                         double *nu_thz, double *eigvec, double *vel);
+
+/* Three-phonon linewidths gamma_mu = Gamma^0_mu in ps^-1 (Eq. gamma_operators,
+ * projection_plus, phase_space, delta_deconstructed):
+ *   gamma_mu = (hbar pi / 8 N_k) sum_{q' s' s''} |phi|^2 / (w w' w'')
+ *              [ (n' - n'') delta(w + w' - w'') + 1/2 (1 + n' + n'') delta(w - w' - w'') ]
+ * with one projection phi = phi^+(qs, q's', q''s''), q'' = q + q', per
+ * momentum-conserving triplet: the - process of (q, -q') has the same
+ * |phi|^2 up to gauge (time reversal), so both weights apply to it.  The
+ * delta is a Gaussian in angular frequency, standard deviation 2 pi sigma,
+ * truncated at |d nu| < n_sigma sigma.  Modes with nu < omega_min get
+ * gamma = 0 and take no part as mu' or mu''.  gamma is averaged over
+ * degenerate sets (|d nu| < degen_tol, same q).
+ *   n_sys   number of systems; n_sys > 1 requires mesh {1,1,1} (batched Gamma-only)
+ *   sys     [n_sys]
+ *   nu_thz, eigvec   per system concatenated, as written by kald_phonons
+ *   gamma   [sum over systems of Nq*nb] out
+ *   n_triplets [2] out or NULL: momentum-conserving triplets Nq^2 nb^3, and
+ *           those with a non-zero delta weight
+ * This build supports nb <= 96 per system. */
+kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys,
+                            const int32_t mesh[3], const double *nu_thz, const double *eigvec,
+                            const kald_options *opt, double *gamma, uint64_t *n_triplets);
+
+/* BTE-RTA conductivity (Eq. RTA, Eq. heat_capacity):
+ *   kappa_ab = 1/(N_k V) sum_mu c_mu tau_mu v_a v_b,  tau = 1/(2 gamma),
+ * with, inside each degenerate set D at one q, v_a v_b replaced by the
+ * basis-invariant sum_{s,s' in D} Re(V^a_{ss'} conj(V^b_{ss'})) of the
+ * Hellmann-Feynman velocity matrix.  Modes with nu < omega_min or gamma <= 0
+ * are skipped.
+ *   kappa [3][3] out (W/(m K)); sums in FP64 in a fixed order. */
+kald_status kald_kappa_rta(kald_ctx *ctx, const kald_system *sys, const int32_t mesh[3],
+                           const double *nu_thz, const double *eigvec, const double *gamma,
+                           const kald_options *opt, double *kappa);
+
+/* Quasi-harmonic Green-Kubo conductivity of Gamma-only systems (Eq.
+ * conductivity_amorphous, twod_heat_capacity, generalized_velocity,
+ * lorentzian_amorphous):
+ *   kappa_ab = 1/V sum_{mu mu'} c_{mu mu'} tau_{mu mu'} W_a W_b,
+ *   v_{mu mu' a} = i W_a,  W_a = (E^T A_a E)_{mu mu'} / (2 sqrt(w w')),
+ *   A_a(i, j) = sum_L (x_i - x_j - L)_a Phi2(i, jL) / sqrt(m_i m_j),
+ *   c_{mu mu'} = (hbar w w' / T)(n' - n)/(w - w')  (c_mu for |d nu| < degen_tol),
+ *   tau_{mu mu'} = (g + g') / ((w - w')^2 + (g + g')^2).
+ *   eigvec  real eigenvectors (imaginary parts must be zero)
+ *   kappa   [n_sys][3][3] out
+ *   vgen    [3][nb][nb] out (W_a in A/ps, system 0 only) or NULL */
+kald_status kald_kappa_qhgk(kald_ctx *ctx, int32_t n_sys, const kald_system *sys,
+                            const double *nu_thz, const double *eigvec, const double *gamma,
+                            const kald_options *opt, double *kappa, double *vgen);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KALD_H */

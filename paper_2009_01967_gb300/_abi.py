@@ -1,0 +1,269 @@
+"""ctypes binding of libkald.so (include/kald.h).  Argument marshalling only:
+every step of the computation runs in the library's CUDA kernels.  There is
+no fallback: without the built library (or without a GPU) the calls raise.
+
+Bulk arrays may be numpy arrays (host) or torch tensors on the context's CUDA
+device; the library detects the pointer kind.  Shapes and dtypes follow
+include/kald.h: float64 for real arrays, complex128 for eigenvectors.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkald.so")
+
+KALD_OK = 0
+STATUS = {0: "KALD_OK", 1: "KALD_E_INVALID", 2: "KALD_E_NOMEM", 3: "KALD_E_CUDA",
+          4: "KALD_E_NOCONV", 5: "KALD_E_TIMEOUT", 6: "KALD_E_UNSUPPORTED"}
+PRECISION = {"fp64": 0, "fp32": 1}
+
+EXPORTS = ["kald_ctx_create", "kald_ctx_destroy", "kald_last_error", "kald_set_stream",
+           "kald_phonons", "kald_linewidths", "kald_kappa_rta", "kald_kappa_qhgk"]
+
+
+class KaldError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class kald_system(C.Structure):
+    _fields_ = [("n_atoms", C.c_int32), ("masses", C.c_void_p), ("positions", C.c_void_p),
+                ("lattice", C.c_double * 9), ("n_fc2", C.c_int32), ("fc2_idx", C.c_void_p),
+                ("fc2", C.c_void_p), ("n_fc3", C.c_int32), ("fc3_idx", C.c_void_p),
+                ("fc3", C.c_void_p)]
+
+
+class kald_options(C.Structure):
+    _fields_ = [("temperature_K", C.c_double), ("sigma_thz", C.c_double), ("n_sigma", C.c_double),
+                ("omega_min_thz", C.c_double), ("degen_tol_thz", C.c_double),
+                ("classical", C.c_int32), ("precision", C.c_int32)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libkald.so once; raise if it is missing (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libkald.so not built at {path}; run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    vp, i32, st = C.c_void_p, C.c_int32, C.c_int
+    lib.kald_ctx_create.argtypes = [C.POINTER(vp), C.c_int]
+    lib.kald_ctx_create.restype = st
+    lib.kald_ctx_destroy.argtypes = [vp]
+    lib.kald_ctx_destroy.restype = None
+    lib.kald_last_error.argtypes = [vp]
+    lib.kald_last_error.restype = C.c_char_p
+    lib.kald_set_stream.argtypes = [vp, vp]
+    lib.kald_set_stream.restype = st
+    lib.kald_phonons.argtypes = [vp, C.POINTER(kald_system), C.POINTER(i32), vp, vp, vp]
+    lib.kald_phonons.restype = st
+    lib.kald_linewidths.argtypes = [vp, i32, C.POINTER(kald_system), C.POINTER(i32), vp, vp,
+                                    C.POINTER(kald_options), vp, C.POINTER(C.c_uint64)]
+    lib.kald_linewidths.restype = st
+    lib.kald_kappa_rta.argtypes = [vp, C.POINTER(kald_system), C.POINTER(i32), vp, vp, vp,
+                                   C.POINTER(kald_options), vp]
+    lib.kald_kappa_rta.restype = st
+    lib.kald_kappa_qhgk.argtypes = [vp, i32, C.POINTER(kald_system), vp, vp, vp,
+                                    C.POINTER(kald_options), vp, vp]
+    lib.kald_kappa_qhgk.restype = st
+    _lib = lib
+    return lib
+
+
+@dataclass
+class Options:
+    temperature_K: float
+    sigma_thz: float
+    n_sigma: float = 3.0
+    omega_min_thz: float = 0.01
+    degen_tol_thz: float = 1e-5
+    classical: bool = False
+    precision: str = "fp64"
+
+    def c(self) -> kald_options:
+        return kald_options(self.temperature_K, self.sigma_thz, self.n_sigma, self.omega_min_thz,
+                            self.degen_tol_thz, int(bool(self.classical)), PRECISION[self.precision])
+
+
+class Context:
+    """A library context on one CUDA device (own stream and workspace)."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load_library()
+        self.handle = C.c_void_p()
+        s = self.lib.kald_ctx_create(C.byref(self.handle), int(device))
+        if s != KALD_OK:
+            raise KaldError(s, f"kald_ctx_create(device={device}) failed")
+        self.device = device
+
+    def check(self, status: int):
+        if status != KALD_OK:
+            raise KaldError(status, self.lib.kald_last_error(self.handle).decode())
+
+    def set_stream(self, stream_ptr: int | None):
+        self.check(self.lib.kald_set_stream(self.handle, C.c_void_p(stream_ptr or 0)))
+
+    def close(self):
+        if self.handle:
+            self.lib.kald_ctx_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+# ---- marshalling helpers ------------------------------------------------------
+
+def _ptr(a, dtype, n_elem, name):
+    """Address of a contiguous float64/complex128 numpy array or torch tensor."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"{name}: need a C-contiguous {np.dtype(dtype).name} array")
+        if a.size != n_elem:
+            raise ValueError(f"{name}: {a.size} elements, expected {n_elem}")
+        return a.ctypes.data
+    # torch tensor (duck-typed so torch stays optional)
+    if hasattr(a, "data_ptr") and hasattr(a, "is_contiguous"):
+        want = {np.float64: "torch.float64", np.complex128: "torch.complex128"}[dtype]
+        if str(a.dtype) != want or not a.is_contiguous():
+            raise TypeError(f"{name}: need a contiguous {want} tensor")
+        if a.numel() != n_elem:
+            raise ValueError(f"{name}: {a.numel()} elements, expected {n_elem}")
+        return a.data_ptr()
+    raise TypeError(f"{name}: numpy array or torch tensor expected")
+
+
+def c_system(s) -> tuple[kald_system, list]:
+    """kald_system for an object with the fields of kald_inputs.System; the
+    second value keeps the host arrays alive for the call."""
+    keep = [np.ascontiguousarray(s.masses, dtype=np.float64),
+            np.ascontiguousarray(s.positions, dtype=np.float64),
+            np.ascontiguousarray(s.fc2_idx, dtype=np.int32),
+            np.ascontiguousarray(s.fc2, dtype=np.float64),
+            np.ascontiguousarray(s.fc3_idx, dtype=np.int32),
+            np.ascontiguousarray(s.fc3, dtype=np.float64)]
+    lat = (C.c_double * 9)(*np.asarray(s.lattice, dtype=np.float64).reshape(-1))
+    cs = kald_system(int(keep[0].shape[0]), keep[0].ctypes.data, keep[1].ctypes.data, lat,
+                     int(keep[3].shape[0]), keep[2].ctypes.data, keep[3].ctypes.data,
+                     int(keep[5].shape[0]), keep[4].ctypes.data, keep[5].ctypes.data)
+    return cs, keep
+
+
+def _mesh(mesh):
+    m = (C.c_int32 * 3)(*[int(x) for x in mesh])
+    return m, int(np.prod([int(x) for x in mesh]))
+
+
+# ---- entry points (same names as the C ABI) -----------------------------------
+
+def kald_phonons(ctx: Context, system, mesh, nu_thz=None, eigvec=None, vel=None, want_vel=True):
+    """Phonons on the mesh; returns (nu_thz [Nq, nb], eigvec [Nq, nb, nb], vel [Nq, nb, 3] or None).
+    Outputs default to new host numpy arrays."""
+    cs, keep = c_system(system)
+    m, nq = _mesh(mesh)
+    nb = 3 * cs.n_atoms
+    if nu_thz is None:
+        nu_thz = np.zeros((nq, nb))
+    if eigvec is None:
+        eigvec = np.zeros((nq, nb, nb), dtype=np.complex128)
+    if vel is None and want_vel:
+        vel = np.zeros((nq, nb, 3))
+    ctx.check(ctx.lib.kald_phonons(ctx.handle, C.byref(cs), m,
+                                   _ptr(nu_thz, np.float64, nq * nb, "nu_thz"),
+                                   _ptr(eigvec, np.complex128, nq * nb * nb, "eigvec"),
+                                   _ptr(vel, np.float64, nq * nb * 3, "vel")))
+    del keep
+    return nu_thz, eigvec, vel
+
+
+def _systems(systems):
+    if not isinstance(systems, (list, tuple)):
+        systems = [systems]
+    arr = (kald_system * len(systems))()
+    keep = []
+    for x, s in enumerate(systems):
+        cs, k = c_system(s)
+        arr[x] = cs
+        keep.append(k)
+    return arr, keep, [3 * int(np.asarray(s.masses).shape[0]) for s in systems]
+
+
+def kald_linewidths(ctx: Context, systems, mesh, nu_thz, eigvec, options: Options, gamma=None):
+    """Linewidths gamma (ps^-1); returns (gamma, (n_triplets, n_allowed))."""
+    arr, keep, nbs = _systems(systems)
+    m, nq = _mesh(mesh)
+    n_modes = sum(nq * nb for nb in nbs)
+    n_eig = sum(nq * nb * nb for nb in nbs)
+    if gamma is None:
+        gamma = np.zeros(n_modes) if isinstance(nu_thz, np.ndarray) else None
+        if gamma is None:
+            import torch
+            gamma = torch.zeros(n_modes, dtype=torch.float64, device=nu_thz.device)
+    trip = (C.c_uint64 * 2)()
+    opt = options.c()
+    ctx.check(ctx.lib.kald_linewidths(ctx.handle, len(nbs), arr, m,
+                                      _ptr(nu_thz, np.float64, n_modes, "nu_thz"),
+                                      _ptr(eigvec, np.complex128, n_eig, "eigvec"),
+                                      C.byref(opt), _ptr(gamma, np.float64, n_modes, "gamma"), trip))
+    del keep
+    return gamma, (int(trip[0]), int(trip[1]))
+
+
+def kald_kappa_rta(ctx: Context, system, mesh, nu_thz, eigvec, gamma, options: Options, kappa=None):
+    """BTE-RTA kappa [3, 3] in W/(m K)."""
+    cs, keep = c_system(system)
+    m, nq = _mesh(mesh)
+    nb = 3 * cs.n_atoms
+    if kappa is None:
+        kappa = np.zeros((3, 3))
+    opt = options.c()
+    ctx.check(ctx.lib.kald_kappa_rta(ctx.handle, C.byref(cs), m,
+                                     _ptr(nu_thz, np.float64, nq * nb, "nu_thz"),
+                                     _ptr(eigvec, np.complex128, nq * nb * nb, "eigvec"),
+                                     _ptr(gamma, np.float64, nq * nb, "gamma"), C.byref(opt),
+                                     _ptr(kappa, np.float64, 9, "kappa")))
+    del keep
+    return kappa
+
+
+def kald_kappa_qhgk(ctx: Context, systems, nu_thz, eigvec, gamma, options: Options, kappa=None,
+                    vgen=None, want_vgen=False):
+    """QHGK kappa [n_sys, 3, 3] (W/(m K)) and, optionally, W_a [3, nb, nb] of system 0."""
+    arr, keep, nbs = _systems(systems)
+    n_modes = sum(nbs)
+    n_eig = sum(nb * nb for nb in nbs)
+    if kappa is None:
+        kappa = np.zeros((len(nbs), 3, 3))
+    if vgen is None and want_vgen:
+        vgen = np.zeros((3, nbs[0], nbs[0]))
+    opt = options.c()
+    ctx.check(ctx.lib.kald_kappa_qhgk(ctx.handle, len(nbs), arr,
+                                      _ptr(nu_thz, np.float64, n_modes, "nu_thz"),
+                                      _ptr(eigvec, np.complex128, n_eig, "eigvec"),
+                                      _ptr(gamma, np.float64, n_modes, "gamma"), C.byref(opt),
+                                      _ptr(kappa, np.float64, 9 * len(nbs), "kappa"),
+                                      _ptr(vgen, np.float64, 3 * nbs[0] * nbs[0], "vgen")))
+    del keep
+    return kappa, vgen

@@ -1,0 +1,619 @@
+// Host side of the C ABI (include/kald.h): validation, planning of the
+// sparse force-constant tables, workspace and pointer staging, and the
+// launch sequence of each entry point.  Every step of the computation runs in
+// the kernels of phonons.cu, linewidths.cu and kappa.cu; nothing here
+// computes a result on the host.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <tuple>
+
+#include "kald_internal.h"
+
+namespace kald {
+
+kald_status fail(kald_ctx *ctx, kald_status st, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+kald_status cuda_check(kald_ctx *ctx, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return KALD_OK;
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return fail(ctx, KALD_E_NOMEM, m);
+    return fail(ctx, KALD_E_CUDA, m);
+}
+
+kald_status ws_reserve(kald_ctx *ctx, size_t bytes) {
+    ctx->ws_used = 0;
+    if (bytes <= ctx->ws_cap) return KALD_OK;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "workspace sync");
+    if (ctx->ws) cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_cap = 0;
+    const size_t cap = bytes + bytes / 8 + (1 << 20);
+    e = cudaMalloc(reinterpret_cast<void **>(&ctx->ws), cap);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, KALD_E_NOMEM, "cannot allocate " + std::to_string(cap) + " bytes of workspace");
+    }
+    ctx->ws_cap = cap;
+    return KALD_OK;
+}
+
+void *ws_take(kald_ctx *ctx, size_t bytes) {
+    void *p = ctx->ws + ctx->ws_used;
+    ctx->ws_used += ws_round(bytes);
+    return p;
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+kald_status check_mesh(kald_ctx *ctx, const int32_t mesh[3]) {
+    if (!mesh) return fail(ctx, KALD_E_INVALID, "mesh is NULL");
+    for (int a = 0; a < 3; ++a)
+        if (mesh[a] <= 0 || mesh[a] > 4096)
+            return fail(ctx, KALD_E_INVALID, "mesh entries must be in [1, 4096]");
+    const long long nq = (long long)mesh[0] * mesh[1] * mesh[2];
+    if (nq > (1LL << 24)) return fail(ctx, KALD_E_INVALID, "mesh too large");
+    return KALD_OK;
+}
+
+namespace {
+
+bool finite_all(const double *p, size_t n) {
+    for (size_t x = 0; x < n; ++x)
+        if (!std::isfinite(p[x])) return false;
+    return true;
+}
+
+void invert3(const double a[3][3], double inv[3][3]) {
+    const double det = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) -
+                       a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0]) +
+                       a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
+    inv[0][0] = (a[1][1] * a[2][2] - a[1][2] * a[2][1]) / det;
+    inv[0][1] = (a[0][2] * a[2][1] - a[0][1] * a[2][2]) / det;
+    inv[0][2] = (a[0][1] * a[1][2] - a[0][2] * a[1][1]) / det;
+    inv[1][0] = (a[1][2] * a[2][0] - a[1][0] * a[2][2]) / det;
+    inv[1][1] = (a[0][0] * a[2][2] - a[0][2] * a[2][0]) / det;
+    inv[1][2] = (a[0][2] * a[1][0] - a[0][0] * a[1][2]) / det;
+    inv[2][0] = (a[1][0] * a[2][1] - a[1][1] * a[2][0]) / det;
+    inv[2][1] = (a[0][1] * a[2][0] - a[0][0] * a[2][1]) / det;
+    inv[2][2] = (a[0][0] * a[1][1] - a[0][1] * a[1][0]) / det;
+}
+
+// Cartesian q = sum_i k_i b_i / N_i (rows b_i = 2 pi inv(A)^T) and the
+// integer mesh coordinates, flat index (k0 N1 + k1) N2 + k2.
+void mesh_points(const double lat[3][3], const int32_t mesh[3], std::vector<double> &qc,
+                 std::vector<int> &qf) {
+    double inv[3][3];
+    invert3(lat, inv);
+    double b[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) b[i][j] = 2.0 * kPi * inv[j][i];
+    const int nq = mesh[0] * mesh[1] * mesh[2];
+    qc.assign(3 * (size_t)nq, 0.0);
+    qf.assign(3 * (size_t)nq, 0);
+    int x = 0;
+    for (int k0 = 0; k0 < mesh[0]; ++k0)
+        for (int k1 = 0; k1 < mesh[1]; ++k1)
+            for (int k2 = 0; k2 < mesh[2]; ++k2, ++x) {
+                const double f[3] = {(double)k0 / mesh[0], (double)k1 / mesh[1], (double)k2 / mesh[2]};
+                for (int c = 0; c < 3; ++c)
+                    qc[3 * x + c] = f[0] * b[0][c] + f[1] * b[1][c] + f[2] * b[2][c];
+                qf[3 * x] = k0; qf[3 * x + 1] = k1; qf[3 * x + 2] = k2;
+            }
+}
+
+// Device copies of one planned system's tables.
+struct DevSystem {
+    int *pair2_i = nullptr, *pair2_j = nullptr, *pair2_start = nullptr;
+    double *fc2 = nullptr, *fc2_r = nullptr, *fc2_d = nullptr;
+    int *p3_start = nullptr, *p3_jk = nullptr, *b_i = nullptr, *b_rj = nullptr, *b_rk = nullptr;
+    void *fc3 = nullptr;
+    double *rep = nullptr;
+};
+
+template <typename T>
+T *upload(kald_ctx *ctx, const std::vector<T> &v) {
+    T *d = static_cast<T *>(ws_take(ctx, sizeof(T) * std::max<size_t>(v.size(), 1)));
+    if (!v.empty()) cudaMemcpyAsync(d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, ctx->stream);
+    return d;
+}
+template <typename T>
+size_t bytes_of(const std::vector<T> &v) { return ws_round(sizeof(T) * std::max<size_t>(v.size(), 1)); }
+
+size_t fc2_bytes(const HostSystem &h) {
+    return bytes_of(h.pair2_i) + bytes_of(h.pair2_j) + bytes_of(h.pair2_start) + bytes_of(h.fc2_scaled) +
+           bytes_of(h.fc2_rcart) + bytes_of(h.fc2_dist);
+}
+void upload_fc2(kald_ctx *ctx, const HostSystem &h, DevSystem &d) {
+    d.pair2_i = upload(ctx, h.pair2_i);
+    d.pair2_j = upload(ctx, h.pair2_j);
+    d.pair2_start = upload(ctx, h.pair2_start);
+    d.fc2 = upload(ctx, h.fc2_scaled);
+    d.fc2_r = upload(ctx, h.fc2_rcart);
+    d.fc2_d = upload(ctx, h.fc2_dist);
+}
+DevFc2 dev_fc2(const HostSystem &h, const DevSystem &d) {
+    DevFc2 f;
+    f.n_pairs = (int)h.pair2_i.size();
+    f.pair_i = d.pair2_i; f.pair_j = d.pair2_j; f.pair_start = d.pair2_start;
+    f.blk = d.fc2; f.rcart = d.fc2_r;
+    return f;
+}
+
+// Input array: device pointer used in place, host pointer staged.
+template <typename T>
+const T *stage_in(kald_ctx *ctx, const T *p, size_t n, bool dev) {
+    if (dev) return p;
+    T *d = static_cast<T *>(ws_take(ctx, sizeof(T) * n));
+    cudaMemcpyAsync(d, p, sizeof(T) * n, cudaMemcpyHostToDevice, ctx->stream);
+    return d;
+}
+
+kald_status finish(kald_ctx *ctx, const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(ctx, e, what);
+    e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_check(ctx, e, what);
+    ctx->err.clear();
+    return KALD_OK;
+}
+
+kald_status set_device(kald_ctx *ctx) {
+    return cuda_check(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+}
+
+}  // namespace
+
+kald_status plan_system(kald_ctx *ctx, const kald_system *s, HostSystem &h) {
+    if (!s) return fail(ctx, KALD_E_INVALID, "system is NULL");
+    const int n = s->n_atoms;
+    if (n <= 0) return fail(ctx, KALD_E_INVALID, "n_atoms must be > 0");
+    if (!s->masses || !s->positions) return fail(ctx, KALD_E_INVALID, "masses/positions NULL");
+    if (s->n_fc2 < 0 || s->n_fc3 < 0) return fail(ctx, KALD_E_INVALID, "negative block count");
+    if ((s->n_fc2 && (!s->fc2 || !s->fc2_idx)) || (s->n_fc3 && (!s->fc3 || !s->fc3_idx)))
+        return fail(ctx, KALD_E_INVALID, "force-constant arrays NULL");
+    if (is_device_ptr(s->masses) || is_device_ptr(s->positions) || is_device_ptr(s->fc2) ||
+        is_device_ptr(s->fc3) || is_device_ptr(s->fc2_idx) || is_device_ptr(s->fc3_idx))
+        return fail(ctx, KALD_E_INVALID, "kald_system arrays must be host pointers");
+    for (int i = 0; i < n; ++i)
+        if (!(s->masses[i] > 0.0) || !std::isfinite(s->masses[i]))
+            return fail(ctx, KALD_E_INVALID, "masses must be finite and > 0");
+    if (!finite_all(s->positions, 3 * (size_t)n) || !finite_all(&s->lattice[0][0], 9) ||
+        !finite_all(s->fc2, 9 * (size_t)s->n_fc2) || !finite_all(s->fc3, 27 * (size_t)s->n_fc3))
+        return fail(ctx, KALD_E_INVALID, "non-finite value in positions, lattice or force constants");
+    h.n_atoms = n;
+    h.nb = 3 * n;
+    std::memcpy(h.lattice, s->lattice, sizeof(h.lattice));
+    const double (*L)[3] = s->lattice;
+    h.volume = std::fabs(L[0][0] * (L[1][1] * L[2][2] - L[1][2] * L[2][1]) -
+                         L[0][1] * (L[1][0] * L[2][2] - L[1][2] * L[2][0]) +
+                         L[0][2] * (L[1][0] * L[2][1] - L[1][1] * L[2][0]));
+    if (!(h.volume > 0.0)) return fail(ctx, KALD_E_INVALID, "lattice vectors are degenerate");
+    h.masses.assign(s->masses, s->masses + n);
+    h.positions.assign(s->positions, s->positions + 3 * n);
+    auto cart = [&](const int32_t *R, double out[3]) {
+        for (int c = 0; c < 3; ++c) out[c] = R[0] * L[0][c] + R[1] * L[1][c] + R[2] * L[2][c];
+    };
+    // ---- fc2, grouped by (i, j)
+    const int n2 = s->n_fc2;
+    for (int b = 0; b < n2; ++b) {
+        const int32_t *x = s->fc2_idx + 5 * (size_t)b;
+        if (x[0] < 0 || x[0] >= n || x[1] < 0 || x[1] >= n)
+            return fail(ctx, KALD_E_INVALID, "fc2_idx atom index out of range");
+    }
+    std::vector<int> o2(n2);
+    std::iota(o2.begin(), o2.end(), 0);
+    std::stable_sort(o2.begin(), o2.end(), [&](int a, int b) {
+        const int32_t *x = s->fc2_idx + 5 * (size_t)a, *y = s->fc2_idx + 5 * (size_t)b;
+        return std::make_pair(x[0], x[1]) < std::make_pair(y[0], y[1]);
+    });
+    h.fc2_scaled.resize(9 * (size_t)n2);
+    h.fc2_rcart.resize(3 * (size_t)n2);
+    h.fc2_dist.resize(3 * (size_t)n2);
+    h.pair2_i.clear(); h.pair2_j.clear(); h.pair2_start.clear();
+    for (int t = 0; t < n2; ++t) {
+        const int b = o2[t];
+        const int32_t *x = s->fc2_idx + 5 * (size_t)b;
+        const int i = x[0], j = x[1];
+        if (h.pair2_i.empty() || h.pair2_i.back() != i || h.pair2_j.back() != j) {
+            h.pair2_i.push_back(i); h.pair2_j.push_back(j); h.pair2_start.push_back(t);
+        }
+        const double sc = 1.0 / std::sqrt(s->masses[i] * s->masses[j]);
+        for (int e = 0; e < 9; ++e) h.fc2_scaled[9 * (size_t)t + e] = s->fc2[9 * (size_t)b + e] * sc;
+        double R[3];
+        cart(x + 2, R);
+        for (int c = 0; c < 3; ++c) {
+            h.fc2_rcart[3 * (size_t)t + c] = R[c];
+            h.fc2_dist[3 * (size_t)t + c] = s->positions[3 * i + c] - s->positions[3 * j + c] - R[c];
+        }
+    }
+    h.pair2_start.push_back(n2);
+    // ---- fc3, grouped by (j, k) output pair; replica table
+    const int n3 = s->n_fc3;
+    std::map<std::tuple<int, int, int>, int> rep_index;
+    auto rep_of = [&](const int32_t *R) {
+        auto key = std::make_tuple((int)R[0], (int)R[1], (int)R[2]);
+        auto it = rep_index.find(key);
+        if (it != rep_index.end()) return it->second;
+        const int id = (int)rep_index.size();
+        rep_index.emplace(key, id);
+        double c[3];
+        cart(R, c);
+        h.rep_cart.insert(h.rep_cart.end(), c, c + 3);
+        return id;
+    };
+    h.rep_cart.clear();
+    {
+        const int32_t z[3] = {0, 0, 0};
+        rep_of(z);
+    }
+    for (int b = 0; b < n3; ++b) {
+        const int32_t *x = s->fc3_idx + 9 * (size_t)b;
+        if (x[0] < 0 || x[0] >= n || x[1] < 0 || x[1] >= n || x[5] < 0 || x[5] >= n)
+            return fail(ctx, KALD_E_INVALID, "fc3_idx atom index out of range");
+    }
+    std::vector<int> o3(n3);
+    std::iota(o3.begin(), o3.end(), 0);
+    std::stable_sort(o3.begin(), o3.end(), [&](int a, int b) {
+        const int32_t *x = s->fc3_idx + 9 * (size_t)a, *y = s->fc3_idx + 9 * (size_t)b;
+        return std::make_pair(x[1], x[5]) < std::make_pair(y[1], y[5]);
+    });
+    h.fc3_scaled.resize(27 * (size_t)n3);
+    h.fc3_i.resize(n3); h.fc3_rj.resize(n3); h.fc3_rk.resize(n3);
+    h.pair3_j.clear(); h.pair3_k.clear(); h.pair3_start.clear();
+    for (int t = 0; t < n3; ++t) {
+        const int b = o3[t];
+        const int32_t *x = s->fc3_idx + 9 * (size_t)b;
+        const int i = x[0], j = x[1], k = x[5];
+        if (h.pair3_j.empty() || h.pair3_j.back() != j || h.pair3_k.back() != k) {
+            h.pair3_j.push_back(j); h.pair3_k.push_back(k); h.pair3_start.push_back(t);
+        }
+        const double sc = 1.0 / std::sqrt(s->masses[i] * s->masses[j] * s->masses[k]);
+        for (int e = 0; e < 27; ++e) h.fc3_scaled[27 * (size_t)t + e] = s->fc3[27 * (size_t)b + e] * sc;
+        h.fc3_i[t] = i;
+        h.fc3_rj[t] = rep_of(x + 2);
+        h.fc3_rk[t] = rep_of(x + 6);
+    }
+    h.pair3_start.push_back(n3);
+    h.n_rep = (int)rep_index.size();
+    return KALD_OK;
+}
+
+}  // namespace kald
+
+using namespace kald;
+
+extern "C" {
+
+kald_status kald_ctx_create(kald_ctx **out, int device) {
+    if (!out) return KALD_E_INVALID;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n <= 0 || device < 0 || device >= n) {
+        cudaGetLastError();
+        return KALD_E_CUDA;
+    }
+    kald_ctx *ctx = new kald_ctx();
+    ctx->device = device;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return KALD_E_CUDA;
+    }
+    ctx->stream = ctx->own_stream;
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+    ctx->sm_count = v;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    ctx->smem_optin = (size_t)v;
+    *out = ctx;
+    return KALD_OK;
+}
+
+void kald_ctx_destroy(kald_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->own_stream) cudaStreamSynchronize(ctx->own_stream);
+    if (ctx->stream && ctx->stream != ctx->own_stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    delete ctx;
+}
+
+const char *kald_last_error(const kald_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+kald_status kald_set_stream(kald_ctx *ctx, void *stream) {
+    if (!ctx) return KALD_E_INVALID;
+    ctx->stream = stream ? static_cast<cudaStream_t>(stream) : ctx->own_stream;
+    return KALD_OK;
+}
+
+kald_status kald_phonons(kald_ctx *ctx, const kald_system *sys, const int32_t mesh[3],
+                         double *nu_thz, double *eigvec, double *vel) {
+    if (!ctx) return KALD_E_INVALID;
+    kald_status st = set_device(ctx);
+    if (st) return st;
+    if ((st = check_mesh(ctx, mesh))) return st;
+    if (!nu_thz || !eigvec) return fail(ctx, KALD_E_INVALID, "nu_thz/eigvec NULL");
+    HostSystem h;
+    if ((st = plan_system(ctx, sys, h))) return st;
+    const int nb = h.nb;
+    if (nb > kMaxNbSmall)
+        return fail(ctx, KALD_E_UNSUPPORTED, "kald_phonons: this build diagonalises nb <= 96");
+    std::vector<double> qc;
+    std::vector<int> qf;
+    mesh_points(h.lattice, mesh, qc, qf);
+    const int nq = (int)(qc.size() / 3);
+    const size_t nn = (size_t)nq * nb * nb;
+    const bool d_nu = is_device_ptr(nu_thz), d_eig = is_device_ptr(eigvec);
+    const bool d_vel = vel && is_device_ptr(vel);
+    size_t need = fc2_bytes(h) + bytes_of(qc) + 2 * ws_round(sizeof(double2) * nn) + ws_round(sizeof(int));
+    if (!d_nu) need += ws_round(sizeof(double) * nq * nb);
+    if (!d_eig) need += ws_round(sizeof(double2) * nn);
+    if (vel && !d_vel) need += ws_round(sizeof(double) * 3 * nq * nb);
+    if ((st = ws_reserve(ctx, need))) return st;
+    DevSystem d;
+    upload_fc2(ctx, h, d);
+    const double *qcart = upload(ctx, qc);
+    double2 *D = static_cast<double2 *>(ws_take(ctx, sizeof(double2) * nn));
+    double2 *V = static_cast<double2 *>(ws_take(ctx, sizeof(double2) * nn));
+    int *nonconv = static_cast<int *>(ws_take(ctx, sizeof(int)));
+    double *nu_d = d_nu ? nu_thz : static_cast<double *>(ws_take(ctx, sizeof(double) * nq * nb));
+    double2 *eig_d = d_eig ? reinterpret_cast<double2 *>(eigvec)
+                           : static_cast<double2 *>(ws_take(ctx, sizeof(double2) * nn));
+    double *vel_d = nullptr;
+    if (vel) vel_d = d_vel ? vel : static_cast<double *>(ws_take(ctx, sizeof(double) * 3 * nq * nb));
+    cudaStream_t s = ctx->stream;
+    cudaMemsetAsync(nonconv, 0, sizeof(int), s);
+    cudaError_t e = launch_dynmat(dev_fc2(h, d), nb, nq, qcart, D, s);
+    if (e == cudaSuccess) e = launch_jacobi(nb, nq, D, V, nu_d, eig_d, nonconv, ctx->smem_optin, s);
+    if (e == cudaSuccess && vel) e = launch_velocity_diag(dev_fc2(h, d), nb, nq, qcart, nu_d, eig_d, vel_d, s);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "kald_phonons launch");
+    int nc = 0;
+    cudaMemcpyAsync(&nc, nonconv, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (!d_nu) cudaMemcpyAsync(nu_thz, nu_d, sizeof(double) * nq * nb, cudaMemcpyDeviceToHost, s);
+    if (!d_eig) cudaMemcpyAsync(eigvec, eig_d, sizeof(double2) * nn, cudaMemcpyDeviceToHost, s);
+    if (vel && !d_vel) cudaMemcpyAsync(vel, vel_d, sizeof(double) * 3 * nq * nb, cudaMemcpyDeviceToHost, s);
+    if ((st = finish(ctx, "kald_phonons"))) return st;
+    if (nc) return fail(ctx, KALD_E_NOCONV, "Jacobi eigensolver did not converge at " + std::to_string(nc) + " q-points");
+    return KALD_OK;
+}
+
+static kald_status check_options(kald_ctx *ctx, const kald_options *o) {
+    if (!o) return fail(ctx, KALD_E_INVALID, "options NULL");
+    if (!(o->temperature_K > 0.0) || !std::isfinite(o->temperature_K))
+        return fail(ctx, KALD_E_INVALID, "temperature must be > 0");
+    if (!(o->sigma_thz > 0.0) || !std::isfinite(o->sigma_thz))
+        return fail(ctx, KALD_E_INVALID, "sigma must be > 0");
+    if (!(o->n_sigma > 0.0) || !std::isfinite(o->n_sigma))
+        return fail(ctx, KALD_E_INVALID, "n_sigma must be > 0");
+    if (!(o->omega_min_thz >= 0.0) || !(o->degen_tol_thz >= 0.0))
+        return fail(ctx, KALD_E_INVALID, "omega_min and degen_tol must be >= 0");
+    if (o->precision != KALD_FP64 && o->precision != KALD_FP32)
+        return fail(ctx, KALD_E_INVALID, "unknown precision");
+    return KALD_OK;
+}
+
+kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys,
+                            const int32_t mesh[3], const double *nu_thz, const double *eigvec,
+                            const kald_options *opt, double *gamma, uint64_t *n_triplets) {
+    if (!ctx) return KALD_E_INVALID;
+    kald_status st = set_device(ctx);
+    if (st) return st;
+    if ((st = check_mesh(ctx, mesh))) return st;
+    if ((st = check_options(ctx, opt))) return st;
+    if (n_sys <= 0 || !sys) return fail(ctx, KALD_E_INVALID, "n_sys must be > 0");
+    const int nq_mesh = mesh[0] * mesh[1] * mesh[2];
+    if (n_sys > 1 && nq_mesh != 1)
+        return fail(ctx, KALD_E_INVALID, "several systems need mesh {1,1,1} (Gamma-only batch)");
+    if (!nu_thz || !eigvec || !gamma) return fail(ctx, KALD_E_INVALID, "nu/eigvec/gamma NULL");
+    const bool d_nu = is_device_ptr(nu_thz), d_eig = is_device_ptr(eigvec), d_g = is_device_ptr(gamma);
+    const int fp32 = opt->precision == KALD_FP32;
+    uint64_t tot = 0, allowed_tot = 0;
+    size_t off_nb = 0, off_eig = 0;
+    for (int x = 0; x < n_sys; ++x) {
+        HostSystem h;
+        if ((st = plan_system(ctx, &sys[x], h))) return st;
+        const int nb = h.nb;
+        if (nb > kMaxNbSmall)
+            return fail(ctx, KALD_E_UNSUPPORTED, "kald_linewidths: this build supports nb <= 96");
+        std::vector<double> qc;
+        std::vector<int> qf;
+        mesh_points(h.lattice, mesh, qc, qf);
+        const int nq = nq_mesh;
+        const size_t nn = (size_t)nq * nb * nb;
+        LwParams p;
+        p.nb = nb; p.nq = nq;
+        for (int a = 0; a < 3; ++a) p.mesh[a] = mesh[a];
+        p.n_rep = h.n_rep;
+        p.n_pairs3 = (int)h.pair3_j.size();
+        p.n_elem = p.n_pairs3 * 9;
+        p.sigma_w = kTwoPi * opt->sigma_thz;
+        p.cut_w = opt->n_sigma * p.sigma_w;
+        p.T = opt->temperature_K;
+        p.classical = opt->classical ? 1 : 0;
+        p.omega_min_w = kTwoPi * opt->omega_min_thz;
+        // about 64 items per SM for balance, q' chunks as long as that allows
+        {
+            const long long want = 64LL * std::max(1, ctx->sm_count);
+            int nch = (int)std::max(1LL, std::min<long long>(nq, (want + nq - 1) / nq));
+            p.qp_chunk = (nq + nch - 1) / nch;
+            p.n_chunks = (nq + p.qp_chunk - 1) / p.qp_chunk;
+        }
+        std::vector<int> pjk(2 * (size_t)p.n_pairs3);
+        for (int t = 0; t < p.n_pairs3; ++t) { pjk[2 * t] = h.pair3_j[t]; pjk[2 * t + 1] = h.pair3_k[t]; }
+        std::vector<float> fc3f;
+        if (fp32) fc3f.assign(h.fc3_scaled.begin(), h.fc3_scaled.end());
+        const size_t c2 = fp32 ? sizeof(float2) : sizeof(double2);
+        size_t need = bytes_of(h.pair3_start) + bytes_of(pjk) + bytes_of(h.fc3_i) + bytes_of(h.fc3_rj) +
+                      bytes_of(h.fc3_rk) + (fp32 ? bytes_of(fc3f) : bytes_of(h.fc3_scaled)) +
+                      bytes_of(h.rep_cart) + bytes_of(qc) + bytes_of(qf) +
+                      2 * ws_round(sizeof(double) * nq * nb) + ws_round(c2 * nn) +
+                      ws_round(c2 * (size_t)nq * h.n_rep) +
+                      ws_round(sizeof(double) * (size_t)nq * p.n_chunks * nb) + 2 * ws_round(16);
+        if (!d_nu) need += ws_round(sizeof(double) * nq * nb);
+        if (!d_eig) need += ws_round(sizeof(double2) * nn);
+        if (!d_g) need += ws_round(sizeof(double) * nq * nb);
+        if ((st = ws_reserve(ctx, need))) return st;
+        LwDev d;
+        d.pair_start = upload(ctx, h.pair3_start);
+        d.pair_jk = upload(ctx, pjk);
+        d.blk_i = upload(ctx, h.fc3_i);
+        d.blk_rj = upload(ctx, h.fc3_rj);
+        d.blk_rk = upload(ctx, h.fc3_rk);
+        d.fc3 = fp32 ? (const void *)upload(ctx, fc3f) : (const void *)upload(ctx, h.fc3_scaled);
+        d.rep_cart = upload(ctx, h.rep_cart);
+        d.qcart = upload(ctx, qc);
+        d.qfrac = upload(ctx, qf);
+        d.nu = stage_in(ctx, nu_thz + off_nb, (size_t)nq * nb, d_nu);
+        d.eig = stage_in(ctx, reinterpret_cast<const double2 *>(eigvec) + off_eig, nn, d_eig);
+        d.omega = static_cast<double *>(ws_take(ctx, sizeof(double) * nq * nb));
+        d.occ = static_cast<double *>(ws_take(ctx, sizeof(double) * nq * nb));
+        d.eps_work = ws_take(ctx, c2 * nn);
+        d.chi = ws_take(ctx, c2 * (size_t)nq * h.n_rep);
+        d.partial = static_cast<double *>(ws_take(ctx, sizeof(double) * (size_t)nq * p.n_chunks * nb));
+        d.allowed = static_cast<unsigned long long *>(ws_take(ctx, 16));
+        d.queue = static_cast<int *>(ws_take(ctx, 16));
+        double *g_d = d_g ? gamma + off_nb : static_cast<double *>(ws_take(ctx, sizeof(double) * nq * nb));
+        cudaStream_t s = ctx->stream;
+        cudaError_t e = launch_lw_prep(p, d, fp32, s);
+        if (e == cudaSuccess) e = launch_lw_main(p, d, fp32, ctx->sm_count, ctx->smem_optin, s);
+        if (e == cudaSuccess) e = launch_lw_finish(p, d, opt->degen_tol_thz, g_d, s);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "kald_linewidths launch");
+        unsigned long long al = 0;
+        cudaMemcpyAsync(&al, d.allowed, sizeof(al), cudaMemcpyDeviceToHost, s);
+        if (!d_g) cudaMemcpyAsync(gamma + off_nb, g_d, sizeof(double) * nq * nb, cudaMemcpyDeviceToHost, s);
+        if ((st = finish(ctx, "kald_linewidths"))) return st;
+        tot += (uint64_t)nq * nq * (uint64_t)nb * nb * nb;
+        allowed_tot += al;
+        off_nb += (size_t)nq * nb;
+        off_eig += nn;
+    }
+    if (n_triplets) { n_triplets[0] = tot; n_triplets[1] = allowed_tot; }
+    return KALD_OK;
+}
+
+kald_status kald_kappa_rta(kald_ctx *ctx, const kald_system *sys, const int32_t mesh[3],
+                           const double *nu_thz, const double *eigvec, const double *gamma,
+                           const kald_options *opt, double *kappa) {
+    if (!ctx) return KALD_E_INVALID;
+    kald_status st = set_device(ctx);
+    if (st) return st;
+    if ((st = check_mesh(ctx, mesh))) return st;
+    if ((st = check_options(ctx, opt))) return st;
+    if (!nu_thz || !eigvec || !gamma || !kappa) return fail(ctx, KALD_E_INVALID, "NULL array");
+    HostSystem h;
+    if ((st = plan_system(ctx, sys, h))) return st;
+    const int nb = h.nb;
+    if (nb > kMaxNbSmall) return fail(ctx, KALD_E_UNSUPPORTED, "kald_kappa_rta: nb <= 96");
+    std::vector<double> qc;
+    std::vector<int> qf;
+    mesh_points(h.lattice, mesh, qc, qf);
+    const int nq = (int)(qc.size() / 3);
+    const size_t nn = (size_t)nq * nb * nb;
+    const bool d_nu = is_device_ptr(nu_thz), d_eig = is_device_ptr(eigvec), d_g = is_device_ptr(gamma);
+    const bool d_k = is_device_ptr(kappa);
+    size_t need = fc2_bytes(h) + bytes_of(qc) + ws_round(sizeof(double) * 9 * (size_t)nq) + ws_round(72);
+    if (!d_nu) need += ws_round(sizeof(double) * nq * nb);
+    if (!d_eig) need += ws_round(sizeof(double2) * nn);
+    if (!d_g) need += ws_round(sizeof(double) * nq * nb);
+    if ((st = ws_reserve(ctx, need))) return st;
+    DevSystem d;
+    upload_fc2(ctx, h, d);
+    const double *qcart = upload(ctx, qc);
+    const double *nu_d = stage_in(ctx, nu_thz, (size_t)nq * nb, d_nu);
+    const double2 *eig_d = stage_in(ctx, reinterpret_cast<const double2 *>(eigvec), nn, d_eig);
+    const double *g_d = stage_in(ctx, gamma, (size_t)nq * nb, d_g);
+    double *partial = static_cast<double *>(ws_take(ctx, sizeof(double) * 9 * (size_t)nq));
+    double *k_d = d_k ? kappa : static_cast<double *>(ws_take(ctx, 72));
+    const double scale = kKappaSI / ((double)nq * h.volume);
+    cudaError_t e = launch_kappa_rta(dev_fc2(h, d), nb, nq, qcart, nu_d, eig_d, g_d, opt->temperature_K,
+                                     opt->classical, opt->omega_min_thz, opt->degen_tol_thz, partial,
+                                     k_d, scale, ctx->stream);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "kald_kappa_rta launch");
+    if (!d_k) cudaMemcpyAsync(kappa, k_d, 72, cudaMemcpyDeviceToHost, ctx->stream);
+    return finish(ctx, "kald_kappa_rta");
+}
+
+kald_status kald_kappa_qhgk(kald_ctx *ctx, int32_t n_sys, const kald_system *sys,
+                            const double *nu_thz, const double *eigvec, const double *gamma,
+                            const kald_options *opt, double *kappa, double *vgen) {
+    if (!ctx) return KALD_E_INVALID;
+    kald_status st = set_device(ctx);
+    if (st) return st;
+    if ((st = check_options(ctx, opt))) return st;
+    if (n_sys <= 0 || !sys) return fail(ctx, KALD_E_INVALID, "n_sys must be > 0");
+    if (!nu_thz || !eigvec || !gamma || !kappa) return fail(ctx, KALD_E_INVALID, "NULL array");
+    const bool d_nu = is_device_ptr(nu_thz), d_eig = is_device_ptr(eigvec), d_g = is_device_ptr(gamma);
+    const bool d_k = is_device_ptr(kappa), d_v = vgen && is_device_ptr(vgen);
+    size_t off_nb = 0, off_eig = 0;
+    for (int x = 0; x < n_sys; ++x) {
+        HostSystem h;
+        if ((st = plan_system(ctx, &sys[x], h))) return st;
+        const int nb = h.nb;
+        const size_t nn = (size_t)nb * nb;
+        // CSR by row atom i: the (i, j) sorted fc2 order is contiguous in i
+        std::vector<int> row_start(h.n_atoms + 1, 0), col_j(h.fc2_scaled.size() / 9);
+        for (size_t p = 0; p < h.pair2_i.size(); ++p)
+            for (int b = h.pair2_start[p]; b < h.pair2_start[p + 1]; ++b) {
+                col_j[b] = h.pair2_j[p];
+                row_start[h.pair2_i[p] + 1]++;
+            }
+        for (int i = 0; i < h.n_atoms; ++i) row_start[i + 1] += row_start[i];
+        const int n_partial = std::min(nb, 4 * std::max(1, ctx->sm_count));
+        size_t need = bytes_of(row_start) + bytes_of(col_j) + bytes_of(h.fc2_scaled) + bytes_of(h.fc2_dist) +
+                      ws_round(sizeof(double) * nn) + 2 * ws_round(sizeof(double) * 3 * nn) +
+                      ws_round(sizeof(double) * (9 * (size_t)n_partial + nb)) + ws_round(72);
+        if (!d_nu) need += ws_round(sizeof(double) * nb);
+        if (!d_eig) need += ws_round(sizeof(double2) * nn);
+        if (!d_g) need += ws_round(sizeof(double) * nb);
+        if ((st = ws_reserve(ctx, need))) return st;
+        DevFc2Dist f;
+        f.n_rows = h.n_atoms;
+        f.row_start = upload(ctx, row_start);
+        f.col_j = upload(ctx, col_j);
+        f.blk = upload(ctx, h.fc2_scaled);
+        f.dist = upload(ctx, h.fc2_dist);
+        const double *nu_d = stage_in(ctx, nu_thz + off_nb, (size_t)nb, d_nu);
+        const double2 *eig_d = stage_in(ctx, reinterpret_cast<const double2 *>(eigvec) + off_eig, nn, d_eig);
+        const double *g_d = stage_in(ctx, gamma + off_nb, (size_t)nb, d_g);
+        double *E = static_cast<double *>(ws_take(ctx, sizeof(double) * nn));
+        double *B = static_cast<double *>(ws_take(ctx, sizeof(double) * 3 * nn));
+        double *W = static_cast<double *>(ws_take(ctx, sizeof(double) * 3 * nn));
+        double *partial = static_cast<double *>(ws_take(ctx, sizeof(double) * (9 * (size_t)n_partial + nb)));
+        double *k_d = d_k ? kappa + 9 * (size_t)x : static_cast<double *>(ws_take(ctx, 72));
+        const double scale = kKappaSI / h.volume;
+        cudaError_t e = launch_qhgk(f, nb, nu_d, eig_d, g_d, opt->temperature_K, opt->classical,
+                                    opt->omega_min_thz, opt->degen_tol_thz, E, B, W, partial, n_partial,
+                                    k_d, scale, ctx->stream);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "kald_kappa_qhgk launch");
+        if (!d_k) cudaMemcpyAsync(kappa + 9 * (size_t)x, k_d, 72, cudaMemcpyDeviceToHost, ctx->stream);
+        if (vgen && x == 0)
+            cudaMemcpyAsync(vgen, W, sizeof(double) * 3 * nn,
+                            d_v ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream);
+        if ((st = finish(ctx, "kald_kappa_qhgk"))) return st;
+        off_nb += nb;
+        off_eig += nn;
+    }
+    return KALD_OK;
+}
+
+}  // extern "C"

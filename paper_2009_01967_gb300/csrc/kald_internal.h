@@ -1,0 +1,162 @@
+// Internal declarations shared by the translation units of libkald.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/kald.h"
+
+// ---- physical constants (CODATA 2018) ---------------------------------------
+namespace kald {
+constexpr double kEvJ = 1.602176634e-19;     // J / eV
+constexpr double kAmuKg = 1.66053906660e-27; // kg / amu
+constexpr double kHbarJs = 1.054571817e-34;  // J s
+constexpr double kKbJK = 1.380649e-23;       // J / K
+// 1 eV/(A^2 amu) in ps^-2
+constexpr double kEvA2AmuPs2 = kEvJ / (1e-20 * kAmuKg) * 1e-24;
+constexpr double kHbarEvPs = kHbarJs / kEvJ * 1e12;   // eV ps
+constexpr double kKbEvK = kKbJK / kEvJ;                // eV / K
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kTwoPi = 2.0 * kPi;
+// (J/K) (A/ps)^2 ps / A^3 -> W/(m K)
+constexpr double kKappaSI = 1e4 * 1e-12 / 1e-30;
+
+constexpr int kMaxNbSmall = 96;    // largest nb of the per-q dense kernels
+constexpr int kMaxDegen = 96;      // largest degenerate set handled
+}  // namespace kald
+
+// ---- context -----------------------------------------------------------------
+struct kald_ctx {
+    int device = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    char *ws = nullptr;          // device workspace
+    size_t ws_cap = 0;
+    size_t ws_used = 0;
+    std::string err;
+    int sm_count = 0;
+    size_t smem_optin = 0;
+};
+
+namespace kald {
+
+// Set ctx->err and return `st`.
+kald_status fail(kald_ctx *ctx, kald_status st, const std::string &msg);
+
+// Check a CUDA call; on error record it (with `what`) and return KALD_E_CUDA.
+kald_status cuda_check(kald_ctx *ctx, cudaError_t e, const char *what);
+
+// Workspace: reserve(total) grows the buffer (synchronising first); take()
+// carves 256-byte aligned pieces until the next reset().
+kald_status ws_reserve(kald_ctx *ctx, size_t bytes);
+void *ws_take(kald_ctx *ctx, size_t bytes);
+inline size_t ws_round(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Pointer kind: true if `p` is device (or managed) memory usable on ctx->device.
+bool is_device_ptr(const void *p);
+
+// ---- host-side plan of a system ---------------------------------------------
+struct HostSystem {
+    int n_atoms = 0;
+    int nb = 0;
+    double lattice[3][3];
+    double volume = 0;
+    std::vector<double> masses, positions;
+    // fc2 grouped by (i, j) atom pair (CSR over pairs)
+    std::vector<int> pair2_i, pair2_j, pair2_start;   // pairs, start offsets (n_pairs+1)
+    std::vector<int> fc2_rep;                          // replica index per block (sorted order)
+    std::vector<double> fc2_scaled;                    // [n_fc2][9] Phi2/sqrt(mi mj)
+    std::vector<double> fc2_rcart;                     // [n_fc2][3] Cartesian R
+    std::vector<double> fc2_dist;                      // [n_fc2][3] x_i - x_j - R
+    // fc3 grouped by (j, k) atom pair (CSR over output pairs)
+    std::vector<int> pair3_j, pair3_k, pair3_start;
+    std::vector<int> fc3_i, fc3_rj, fc3_rk;            // per block (sorted order)
+    std::vector<double> fc3_scaled;                    // [n_fc3][27] Phi3/sqrt(mi mj mk)
+    // distinct replica vectors (Cartesian) referenced by fc3 / fc2
+    std::vector<double> rep_cart;                      // [n_rep][3]
+    int n_rep = 0;
+};
+
+// Validate and plan one kald_system (host).  Returns KALD_OK or an error.
+kald_status plan_system(kald_ctx *ctx, const kald_system *s, HostSystem &h);
+
+kald_status check_mesh(kald_ctx *ctx, const int32_t mesh[3]);
+
+// ---- kernels (launch wrappers) ----------------------------------------------
+// phonons.cu
+struct DevFc2 {
+    int n_pairs;
+    const int *pair_i, *pair_j, *pair_start;
+    const double *blk;        // [n][9]
+    const double *rcart;      // [n][3]
+};
+cudaError_t launch_dynmat(const DevFc2 &f, int nb, int nq, const double *qcart,
+                          double2 *D, cudaStream_t st);
+cudaError_t launch_jacobi(int nb, int nq, double2 *A, double2 *V, double *nu_thz,
+                          double2 *eig_out, int *nonconv, size_t smem_optin, cudaStream_t st);
+cudaError_t launch_velocity_diag(const DevFc2 &f, int nb, int nq, const double *qcart,
+                                 const double *nu_thz, const double2 *eig, double *vel,
+                                 cudaStream_t st);
+
+// linewidths.cu
+struct LwParams {
+    int nb, nq, mesh[3];
+    int n_rep;
+    int n_pairs3;             // (j,k) output pairs
+    int n_elem;               // n_pairs3 * 9 output elements
+    double sigma_w;           // 2 pi sigma (rad/ps)
+    double cut_w;             // n_sigma * sigma_w
+    double T;
+    int classical;
+    double omega_min_w;       // 2 pi omega_min (rad/ps)
+    int qp_chunk;             // q' per work item
+    int n_chunks;             // ceil(nq / qp_chunk)
+};
+struct LwDev {
+    const int *pair_start;    // [n_pairs3+1]
+    const int *pair_jk;       // [n_pairs3][2]
+    const int *blk_i, *blk_rj, *blk_rk;   // [n_fc3]
+    const void *fc3;          // [n_fc3][27] float or double (scaled)
+    const double *rep_cart;   // [n_rep][3]
+    const double *qcart;      // [nq][3]
+    const int *qfrac;         // [nq][3]
+    const double *nu;         // [nq][nb] THz
+    const double2 *eig;       // [nq][nb][nb]
+    // derived (filled by prep kernels)
+    double *omega;            // [nq*nb] rad/ps (0 if masked)
+    double *occ;              // [nq*nb] Bose n (0 if masked)
+    void *eps_work;           // [nq][nb][nb] float2 (fp32 path) or unused
+    void *chi;                // [nq][n_rep] float2 or double2: exp(-i q.R)
+    double *partial;          // [nq][n_chunks][nb] FP64 partial sums
+    unsigned long long *allowed;   // [1] delta-allowed triplet count
+    int *queue;               // [1] work counter
+};
+cudaError_t launch_lw_prep(const LwParams &p, const LwDev &d, int fp32, cudaStream_t st);
+cudaError_t launch_lw_main(const LwParams &p, const LwDev &d, int fp32, int sm_count,
+                           size_t smem_optin, cudaStream_t st);
+cudaError_t launch_lw_finish(const LwParams &p, const LwDev &d, double degen_tol_thz,
+                             double *gamma_out, cudaStream_t st);
+
+// kappa.cu
+cudaError_t launch_kappa_rta(const DevFc2 &f, int nb, int nq, const double *qcart,
+                             const double *nu_thz, const double2 *eig, const double *gamma,
+                             double T, int classical, double omega_min_thz, double degen_tol_thz,
+                             double *partial /*[nq][9]*/, double *kappa_out /*[9]*/,
+                             double scale, cudaStream_t st);
+struct DevFc2Dist {
+    int n_rows;               // atoms i
+    const int *row_start;     // CSR by i over blocks
+    const int *col_j;         // [n] atom j
+    const double *blk;        // [n][9] Phi2/sqrt(mi mj)
+    const double *dist;       // [n][3] x_i - x_j - L
+};
+cudaError_t launch_qhgk(const DevFc2Dist &f, int nb, const double *nu_thz, const double2 *eig,
+                        const double *gamma, double T, int classical, double omega_min_thz,
+                        double degen_tol_thz, double *Ework /*[nb*nb]*/, double *Bwork /*[3][nb][nb]*/,
+                        double *W /*[3][nb][nb]*/, double *partial, int n_partial,
+                        double *kappa_out /*[9]*/, double scale, cudaStream_t st);
+
+}  // namespace kald

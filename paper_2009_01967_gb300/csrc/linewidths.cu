@@ -1,0 +1,451 @@
+// Three-phonon linewidths on the GPU (paper, section "Boltzman Transport
+// Equation": Eq. projection_plus, gamma_operators, phase_space,
+// delta_deconstructed, and Gamma^0).
+//
+// For every momentum-conserving triplet (q s, q' s', q'' s''), q'' = q + q',
+//   phi(s, s', s'') = sum_{b c} eps'_b(s') Y_s(b, c) conj(eps''_c(s''))
+//   Y_s(b, c) = sum_{blocks (i; j Rj; k Rk) -> (b, c)} sum_a Phi3~_{a b c}
+//                 eps_{ia}(q s) chi(q', Rj) conj(chi(q'', Rk))
+// with Phi3~ = Phi3 / sqrt(mi mj mk), eps = eta (mass scaling lives in Phi3~)
+// and chi(q, R) = exp(-i q.R).  The first (home) index is contracted on the
+// sparse blocks, the two others are dense complex contractions:
+//   T'(s', c) = sum_b eps'(b, s') Y(b, c),   phi(s', s'') = sum_c T'(s', c) conj(eps''(c, s'')).
+// The epilogue applies both processes to the one projection (the - process of
+// (q, -q') has the same |phi|^2 up to gauge):
+//   acc_s += |phi|^2 / (w' w'') [ (n' - n'') G(w + w' - w'') + 1/2 (1 + n' + n'') G(w - w' - w'') ]
+// where G(d) = exp(-d^2 / 2 sigma^2) for |d| < n_sigma sigma; the constant
+// hbar pi / (8 N_k) (eV/A^2 amu -> ps^-2)^3 / (sqrt(2 pi) sigma w) is applied
+// per mode at the end in FP64.
+//
+// Work: a persistent grid pulls items (q, chunk of q') from a device counter
+// (atomicAdd only; nothing waits).  Each item writes its own FP64 partial
+// sums, which a second kernel adds in a fixed order, so results do not
+// depend on the schedule.
+
+#include <algorithm>
+
+#include "kald_internal.h"
+
+namespace kald {
+namespace {
+
+template <typename R> struct C2;
+template <> struct C2<float> { using T = float2; };
+template <> struct C2<double> { using T = double2; };
+
+template <typename T2> __device__ __forceinline__ T2 mk(double x, double y);
+template <> __device__ __forceinline__ float2 mk<float2>(double x, double y) {
+    return make_float2((float)x, (float)y);
+}
+template <> __device__ __forceinline__ double2 mk<double2>(double x, double y) {
+    return make_double2(x, y);
+}
+
+constexpr int kThreads = 256;
+constexpr int kTile = 6;           // register tile edge (complex)
+
+// ---------------------------------------------------------------- prep kernels
+__global__ void mode_prep_kernel(int n, const double *__restrict__ nu, double omega_min_w,
+                                 double T, int classical, double *__restrict__ omega,
+                                 double *__restrict__ occ) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    const double w = kTwoPi * nu[x];
+    const bool ok = isfinite(w) && (w > omega_min_w);
+    double n_b = 0.0;
+    if (ok) {
+        const double xx = kHbarEvPs * w / (kKbEvK * T);
+        n_b = classical ? 1.0 / xx : 1.0 / expm1(fmin(xx, 700.0));
+    }
+    omega[x] = ok ? w : 0.0;
+    occ[x] = n_b;
+}
+
+template <typename R2>
+__global__ void chi_kernel(int nq, int n_rep, const double *__restrict__ qcart,
+                           const double *__restrict__ rep, R2 *__restrict__ chi) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= nq * n_rep) return;
+    const int q = x / n_rep, r = x % n_rep;
+    double s, c;
+    sincos(qcart[3 * q] * rep[3 * r] + qcart[3 * q + 1] * rep[3 * r + 1] +
+               qcart[3 * q + 2] * rep[3 * r + 2], &s, &c);
+    chi[x] = mk<R2>(c, -s);                    // exp(-i q.R)
+}
+
+// epsT[q][b][s] = eta[q][s][b] in the working precision
+template <typename R2>
+__global__ void eps_transpose_kernel(int nq, int nb, const double2 *__restrict__ eig,
+                                     R2 *__restrict__ epsT) {
+    const size_t n = (size_t)nq * nb * nb;
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < n;
+         x += (size_t)gridDim.x * blockDim.x) {
+        const size_t q = x / ((size_t)nb * nb);
+        const int r = (int)(x % ((size_t)nb * nb));
+        const int b = r / nb, s = r % nb;
+        const double2 v = eig[(q * nb + s) * nb + b];
+        epsT[x] = mk<R2>(v.x, v.y);
+    }
+}
+
+// -------------------------------------------------------------- main kernel
+template <typename R> struct Smem {
+    using R2 = typename C2<R>::T;
+};
+
+template <typename R2>
+__device__ __forceinline__ void cfma(R2 &acc, const R2 a, const R2 b) {   // acc += a b
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+
+// Shared memory layout (R2 = complex of the working precision; P = nb
+// rounded up to a multiple of kTile):
+//   Y    [P][P]     Y(b, c), then T'^T(c, s')
+//   EpT  [P][P]     eps(q')^T            (only when operands live in smem)
+//   EppT [P][P]     conj(eps(q''))^T     (only when operands live in smem)
+//   es   [P]        eps(q, s) column
+//   chip, chipp [n_rep]    chi(q'), chi(q'')
+//   wp, np_, wpp, npp [P]  omega and n of q' / q'' (R)
+//   red  [nwarps][nb] double   per-warp sums over the item's q'
+template <typename R, bool OPER_SMEM>
+__global__ void __launch_bounds__(kThreads, 1)
+lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
+               const typename C2<R>::T *__restrict__ epsT_all,
+               const typename C2<R>::T *__restrict__ chi_all) {
+    using R2 = typename C2<R>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nb = p.nb;
+    const int P = ((nb + kTile - 1) / kTile) * kTile;
+    const int tpr = P / kTile;                       // tiles per row
+    const int n_tiles = tpr * tpr;
+    R2 *Y = reinterpret_cast<R2 *>(smem_raw);
+    R2 *EpT = Y + (size_t)P * P;
+    R2 *EppT = OPER_SMEM ? EpT + (size_t)P * P : EpT;
+    R2 *es = OPER_SMEM ? EppT + (size_t)P * P : EpT;
+    R2 *chip = es + P;
+    R2 *chipp = chip + p.n_rep;
+    R *wp = reinterpret_cast<R *>(chipp + p.n_rep);
+    R *np_ = wp + P;
+    R *wpp = np_ + P;
+    R *npp = wpp + P;
+    double *red = reinterpret_cast<double *>(
+        (reinterpret_cast<uintptr_t>(npp + P) + 15) & ~uintptr_t(15));
+    __shared__ int item_sm;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarps = kThreads / 32;
+    const R sig2inv = (R)(0.5 / (p.sigma_w * p.sigma_w));
+    const R cut = (R)p.cut_w;
+    const int n_items = p.nq * p.n_chunks;
+    unsigned long long allowed = 0;
+
+    for (;;) {
+        if (tid == 0) item_sm = atomicAdd(d.queue, 1);
+        __syncthreads();
+        const int item = item_sm;
+        __syncthreads();
+        if (item >= n_items) break;
+        const int q = item / p.n_chunks;
+        const int chunk = item % p.n_chunks;
+        for (int x = tid; x < nwarps * nb; x += kThreads) red[x] = 0.0;
+
+        const int qp0 = chunk * p.qp_chunk;
+        const int qp1 = min(p.nq, qp0 + p.qp_chunk);
+        for (int qp = qp0; qp < qp1; ++qp) {
+            // q'' = q + q' on the mesh
+            const int *kq = d.qfrac + 3 * q, *kp = d.qfrac + 3 * qp;
+            const int k0 = (kq[0] + kp[0]) % p.mesh[0];
+            const int k1 = (kq[1] + kp[1]) % p.mesh[1];
+            const int k2 = (kq[2] + kp[2]) % p.mesh[2];
+            const int qpp = (k0 * p.mesh[1] + k1) * p.mesh[2] + k2;
+            __syncthreads();
+            // stage per-pair data
+            for (int x = tid; x < p.n_rep; x += kThreads) {
+                chip[x] = chi_all[(size_t)qp * p.n_rep + x];
+                chipp[x] = chi_all[(size_t)qpp * p.n_rep + x];
+            }
+            for (int x = tid; x < P; x += kThreads) {
+                const bool in = x < nb;
+                wp[x] = in ? (R)d.omega[(size_t)qp * nb + x] : (R)0;
+                np_[x] = in ? (R)d.occ[(size_t)qp * nb + x] : (R)0;
+                wpp[x] = in ? (R)d.omega[(size_t)qpp * nb + x] : (R)0;
+                npp[x] = in ? (R)d.occ[(size_t)qpp * nb + x] : (R)0;
+            }
+            if (OPER_SMEM) {
+                const R2 *src1 = epsT_all + (size_t)qp * nb * nb;
+                const R2 *src2 = epsT_all + (size_t)qpp * nb * nb;
+                for (int x = tid; x < P * P; x += kThreads) {
+                    const int b = x / P, s = x % P;
+                    const bool in = (b < nb) && (s < nb);
+                    R2 v1 = in ? src1[b * nb + s] : mk<R2>(0.0, 0.0);
+                    R2 v2 = in ? src2[b * nb + s] : mk<R2>(0.0, 0.0);
+                    v2.y = -v2.y;
+                    EpT[x] = v1;
+                    EppT[x] = v2;
+                }
+            }
+            __syncthreads();
+
+            for (int s = 0; s < nb; ++s) {
+                const double w_s = d.omega[(size_t)q * nb + s];
+                if (w_s <= 0.0) continue;              // masked mode (uniform branch)
+                const R w = (R)w_s;
+                // ---- Y_s: zero, then gather over blocks
+                for (int x = tid; x < P; x += kThreads)
+                    es[x] = x < nb ? epsT_all[((size_t)q * nb + x) * nb + s] : mk<R2>(0.0, 0.0);
+                for (int x = tid; x < P * P; x += kThreads) Y[x] = mk<R2>(0.0, 0.0);
+                __syncthreads();
+                for (int e = tid; e < p.n_elem; e += kThreads) {
+                    const int pr = e / 9, bg = e % 9;
+                    const int j = d.pair_jk[2 * pr], k = d.pair_jk[2 * pr + 1];
+                    R2 acc = mk<R2>(0.0, 0.0);
+                    for (int bl = d.pair_start[pr]; bl < d.pair_start[pr + 1]; ++bl) {
+                        const int i = d.blk_i[bl];
+                        const R *f = fc3 + (size_t)27 * bl + bg;
+                        const R2 e0 = es[3 * i], e1 = es[3 * i + 1], e2 = es[3 * i + 2];
+                        const R f0 = __ldg(f), f1 = __ldg(f + 9), f2 = __ldg(f + 18);
+                        R2 wv;
+                        wv.x = f0 * e0.x + f1 * e1.x + f2 * e2.x;
+                        wv.y = f0 * e0.y + f1 * e1.y + f2 * e2.y;
+                        const R2 a = chip[d.blk_rj[bl]];
+                        const R2 b = chipp[d.blk_rk[bl]];
+                        // P = chi(q', Rj) conj(chi(q'', Rk))
+                        R2 ph;
+                        ph.x = a.x * b.x + a.y * b.y;
+                        ph.y = a.y * b.x - a.x * b.y;
+                        cfma(acc, wv, ph);
+                    }
+                    Y[(size_t)(3 * j + bg / 3) * P + 3 * k + bg % 3] = acc;
+                }
+                __syncthreads();
+
+                // ---- GEMM1: T'(s', c) = sum_b epsT'(b, s') Y(b, c)
+                const int ti = tid / tpr, tj = tid % tpr;
+                const bool active = tid < n_tiles;
+                const int r0 = ti * kTile, c0 = tj * kTile;
+                R2 acc[kTile][kTile];
+                if (active) {
+#pragma unroll
+                    for (int r = 0; r < kTile; ++r)
+#pragma unroll
+                        for (int c = 0; c < kTile; ++c) acc[r][c] = mk<R2>(0.0, 0.0);
+                    for (int b = 0; b < nb; ++b) {
+                        R2 av[kTile], bv[kTile];
+                        const R2 *arow = OPER_SMEM ? EpT + (size_t)b * P
+                                                   : epsT_all + ((size_t)qp * nb + b) * nb;
+#pragma unroll
+                        for (int r = 0; r < kTile; ++r)
+                            av[r] = (OPER_SMEM || r0 + r < nb) ? arow[r0 + r] : mk<R2>(0.0, 0.0);
+#pragma unroll
+                        for (int c = 0; c < kTile; ++c) bv[c] = Y[(size_t)b * P + c0 + c];
+#pragma unroll
+                        for (int r = 0; r < kTile; ++r)
+#pragma unroll
+                            for (int c = 0; c < kTile; ++c) cfma(acc[r][c], av[r], bv[c]);
+                    }
+                }
+                __syncthreads();
+                if (active) {
+#pragma unroll
+                    for (int r = 0; r < kTile; ++r)
+#pragma unroll
+                        for (int c = 0; c < kTile; ++c)
+                            Y[(size_t)(c0 + c) * P + r0 + r] = acc[r][c];   // T'^T(c, s')
+                }
+                __syncthreads();
+
+                // ---- GEMM2 + epilogue over (s', s'') tiles inside the delta band
+                R part = (R)0;
+                if (active) {
+                    R wlo = (R)1e30, whi = (R)-1e30, xlo = (R)1e30, xhi = (R)-1e30;
+#pragma unroll
+                    for (int r = 0; r < kTile; ++r) {
+                        wlo = fmin(wlo, wp[r0 + r]); whi = fmax(whi, wp[r0 + r]);
+                        xlo = fmin(xlo, wpp[c0 + r]); xhi = fmax(xhi, wpp[c0 + r]);
+                    }
+                    // d+ = w + w' - w'' in [w + wlo - xhi, w + whi - xlo]
+                    // d- = w - w' - w'' in [w - whi - xhi, w - wlo - xlo]
+                    const bool band_p = (w + wlo - xhi < cut) && (w + whi - xlo > -cut);
+                    const bool band_m = (w - whi - xhi < cut) && (w - wlo - xlo > -cut);
+                    if (band_p || band_m) {
+#pragma unroll
+                        for (int r = 0; r < kTile; ++r)
+#pragma unroll
+                            for (int c = 0; c < kTile; ++c) acc[r][c] = mk<R2>(0.0, 0.0);
+                        for (int c = 0; c < nb; ++c) {
+                            R2 av[kTile], bv[kTile];
+#pragma unroll
+                            for (int r = 0; r < kTile; ++r) av[r] = Y[(size_t)c * P + r0 + r];
+                            if (OPER_SMEM) {
+#pragma unroll
+                                for (int k = 0; k < kTile; ++k) bv[k] = EppT[(size_t)c * P + c0 + k];
+                            } else {
+                                const R2 *brow = epsT_all + ((size_t)qpp * nb + c) * nb;
+#pragma unroll
+                                for (int k = 0; k < kTile; ++k) {
+                                    R2 v = (c0 + k < nb) ? brow[c0 + k] : mk<R2>(0.0, 0.0);
+                                    v.y = -v.y;
+                                    bv[k] = v;
+                                }
+                            }
+#pragma unroll
+                            for (int r = 0; r < kTile; ++r)
+#pragma unroll
+                                for (int k = 0; k < kTile; ++k) cfma(acc[r][k], av[r], bv[k]);
+                        }
+#pragma unroll
+                        for (int r = 0; r < kTile; ++r) {
+                            const R w1 = wp[r0 + r], n1 = np_[r0 + r];
+                            if (w1 <= (R)0) continue;
+                            const R iw1 = (R)1 / w1;
+#pragma unroll
+                            for (int c = 0; c < kTile; ++c) {
+                                const R w2 = wpp[c0 + c];
+                                if (w2 <= (R)0) continue;
+                                const R n2 = npp[c0 + c];
+                                const R dp = w + w1 - w2;
+                                const R dm = w - w1 - w2;
+                                R g = (R)0;
+                                bool hit = false;
+                                if (fabs(dp) < cut) { g += (n1 - n2) * exp(-dp * dp * sig2inv); hit = true; }
+                                if (fabs(dm) < cut) { g += (R)0.5 * ((R)1 + n1 + n2) * exp(-dm * dm * sig2inv); hit = true; }
+                                if (hit) {
+                                    ++allowed;
+                                    const R2 f = acc[r][c];
+                                    part += (f.x * f.x + f.y * f.y) * g * iw1 / w2;
+                                }
+                            }
+                        }
+                    }
+                }
+                // per-warp sum into red[warp][s] (fixed order across q')
+                double pd = (double)part;
+                for (int o = 16; o > 0; o >>= 1) pd += __shfl_xor_sync(0xffffffffu, pd, o);
+                if (lane == 0) red[warp * nb + s] += pd;
+                __syncthreads();
+            }
+        }
+        __syncthreads();
+        for (int s = tid; s < nb; s += kThreads) {
+            double t = 0.0;
+            for (int w8 = 0; w8 < nwarps; ++w8) t += red[w8 * nb + s];
+            d.partial[((size_t)q * p.n_chunks + chunk) * nb + s] = t;
+        }
+        __syncthreads();
+    }
+    // delta-allowed triplet count
+    for (int o = 16; o > 0; o >>= 1) allowed += __shfl_xor_sync(0xffffffffu, allowed, o);
+    if (lane == 0 && allowed) atomicAdd(d.allowed, allowed);
+}
+
+// gamma = pref / w * sum over chunks; then average over degenerate sets.
+__global__ void lw_finish_kernel(int nq, int nb, int n_chunks, const double *__restrict__ partial,
+                                 const double *__restrict__ omega, const double *__restrict__ nu,
+                                 double pref, double degen_tol, double *__restrict__ gamma) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    double *g = gamma + (size_t)q * nb;
+    for (int s = 0; s < nb; ++s) {
+        double t = 0.0;
+        for (int c = 0; c < n_chunks; ++c) t += partial[((size_t)q * n_chunks + c) * nb + s];
+        const double w = omega[(size_t)q * nb + s];
+        g[s] = (w > 0.0) ? pref * t / w : 0.0;
+    }
+    // degenerate sets: chains of |d nu| < tol in ascending order of nu
+    int order[kMaxNbSmall];
+    const double *v = nu + (size_t)q * nb;
+    for (int s = 0; s < nb; ++s) order[s] = s;
+    for (int a = 1; a < nb; ++a) {             // insertion sort (stable)
+        const int x = order[a];
+        int b = a - 1;
+        while (b >= 0 && v[order[b]] > v[x]) { order[b + 1] = order[b]; --b; }
+        order[b + 1] = x;
+    }
+    int start = 0;
+    for (int a = 1; a <= nb; ++a) {
+        if (a == nb || v[order[a]] - v[order[a - 1]] >= degen_tol) {
+            if (a - start > 1) {
+                double t = 0.0;
+                for (int b = start; b < a; ++b) t += g[order[b]];
+                t /= (double)(a - start);
+                for (int b = start; b < a; ++b) g[order[b]] = t;
+            }
+            start = a;
+        }
+    }
+}
+
+template <typename R>
+size_t lw_smem_bytes(const LwParams &p, bool oper_smem) {
+    using R2 = typename C2<R>::T;
+    const int P = ((p.nb + kTile - 1) / kTile) * kTile;
+    size_t b = sizeof(R2) * (size_t)P * P * (oper_smem ? 3 : 1);
+    b += sizeof(R2) * (P + 2 * p.n_rep);
+    b += sizeof(R) * 4 * P;
+    b = (b + 15) & ~size_t(15);
+    b += sizeof(double) * (kThreads / 32) * p.nb;
+    return b + 16;
+}
+
+}  // namespace
+
+cudaError_t launch_lw_prep(const LwParams &p, const LwDev &d, int fp32, cudaStream_t st) {
+    const int n = p.nq * p.nb;
+    mode_prep_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, d.nu, p.omega_min_w, p.T, p.classical,
+                                                      d.omega, d.occ);
+    const int nc = p.nq * p.n_rep;
+    const size_t ne = (size_t)p.nq * p.nb * p.nb;
+    const int grid = (int)std::min<size_t>((ne + 255) / 256, 4096);
+    if (fp32) {
+        chi_kernel<float2><<<(nc + 255) / 256, 256, 0, st>>>(p.nq, p.n_rep, d.qcart, d.rep_cart,
+                                                             (float2 *)d.chi);
+        eps_transpose_kernel<float2><<<grid, 256, 0, st>>>(p.nq, p.nb, d.eig, (float2 *)d.eps_work);
+    } else {
+        chi_kernel<double2><<<(nc + 255) / 256, 256, 0, st>>>(p.nq, p.n_rep, d.qcart, d.rep_cart,
+                                                              (double2 *)d.chi);
+        eps_transpose_kernel<double2><<<grid, 256, 0, st>>>(p.nq, p.nb, d.eig, (double2 *)d.eps_work);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lw_main(const LwParams &p, const LwDev &d, int fp32, int sm_count,
+                           size_t smem_optin, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(d.queue, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(d.allowed, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    const int n_items = p.nq * p.n_chunks;
+    const int grid = std::max(1, std::min(n_items, sm_count));
+    if (fp32) {
+        const size_t smem = lw_smem_bytes<float>(p, true);
+        if (smem > smem_optin) return cudaErrorInvalidValue;
+        auto k = lw_main_kernel<float, true>;
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, kThreads, smem, st>>>(p, d, (const float *)d.fc3, (const float2 *)d.eps_work,
+                                        (const float2 *)d.chi);
+    } else {
+        const size_t smem = lw_smem_bytes<double>(p, false);
+        if (smem > smem_optin) return cudaErrorInvalidValue;
+        auto k = lw_main_kernel<double, false>;
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, kThreads, smem, st>>>(p, d, (const double *)d.fc3, (const double2 *)d.eps_work,
+                                        (const double2 *)d.chi);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lw_finish(const LwParams &p, const LwDev &d, double degen_tol_thz,
+                             double *gamma_out, cudaStream_t st) {
+    const double pref = kHbarEvPs * kPi / 8.0 * kEvA2AmuPs2 * kEvA2AmuPs2 * kEvA2AmuPs2 /
+                        (double)p.nq / (sqrt(kTwoPi) * p.sigma_w);
+    lw_finish_kernel<<<(p.nq + 63) / 64, 64, 0, st>>>(p.nq, p.nb, p.n_chunks, d.partial, d.omega,
+                                                     d.nu, pref, degen_tol_thz, gamma_out);
+    return cudaGetLastError();
+}
+
+}  // namespace kald

@@ -1,0 +1,284 @@
+// Harmonic phonons on the GPU (FP64): Bloch-summed dynamical matrix, a
+// parallel cyclic Jacobi Hermitian eigensolver with one CTA per q-point, and
+// Hellmann-Feynman group velocities.
+//
+// Paper: section "Lattice Dynamics" -- D(q) = sum_R Phi2(i0, jR)/sqrt(mi mj)
+// exp(-i q.R) and D(q) eta = omega^2 eta (Eq. eigenvectors_crystal); the
+// velocity v = eta^dagger (dD/dq) eta / (2 omega) (Eq. velocity_crystal, read
+// with the conjugate and the -i R that chi = exp(-i q.R) implies).
+
+#include <algorithm>
+
+#include "kald_internal.h"
+
+namespace kald {
+namespace {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {   // conj(a) * b
+    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+
+// D[q] (nb x nb, row-major) from fc2 blocks grouped by atom pair: one output
+// element (pair, a, b) per thread iteration, blocks summed in a fixed order.
+__global__ void dynmat_kernel(DevFc2 f, int nb, const double *__restrict__ qcart,
+                              double2 *__restrict__ D) {
+    const int q = blockIdx.x;
+    const double qx = qcart[3 * q], qy = qcart[3 * q + 1], qz = qcart[3 * q + 2];
+    double2 *Dq = D + (size_t)q * nb * nb;
+    const int n_elem = f.n_pairs * 9;
+    for (int e = threadIdx.x; e < n_elem; e += blockDim.x) {
+        const int p = e / 9, ab = e % 9;
+        const int i = f.pair_i[p], j = f.pair_j[p];
+        double2 acc = make_double2(0.0, 0.0);
+        for (int b = f.pair_start[p]; b < f.pair_start[p + 1]; ++b) {
+            const double *R = f.rcart + 3 * b;
+            double s, c;
+            sincos(qx * R[0] + qy * R[1] + qz * R[2], &s, &c);
+            const double v = f.blk[9 * b + ab];
+            acc.x += v * c;            // exp(-i q.R) = c - i s
+            acc.y -= v * s;
+        }
+        Dq[(size_t)(3 * i + ab / 3) * nb + 3 * j + ab % 3] = acc;
+    }
+}
+
+// Parallel cyclic Jacobi for one Hermitian matrix per CTA.
+//   A (shared, pitch ld = nb|1 so column walks hit distinct banks),
+//   Vt (global) holds the eigenvectors as rows: Vt[s][dof].
+// Round-robin pairing (player m-1 fixed, the others rotating) visits every
+// pair once per sweep of m-1 rounds; pairs of one round are disjoint, so
+// their rotations commute and are applied together: columns (A U), then
+// rows (U^dagger A), then Vt <- (V U)^T.
+// Rotation zeroing A_pq = r e^{i phi}: U = diag(1, e^{-i phi}) R(theta), with
+// the real Jacobi angle t = tan(theta) = sign(z)/(|z| + sqrt(1 + z^2)),
+// z = (A_qq - A_pp) / (2 r).
+__global__ void __launch_bounds__(256)
+jacobi_kernel(int nb, double2 *__restrict__ Ain, double2 *__restrict__ Vt_all,
+              double *__restrict__ nu_out, double2 *__restrict__ eig_out, int *nonconv) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ld = nb | 1;
+    double2 *A = reinterpret_cast<double2 *>(smem_raw);
+    const int m = (nb + 1) & ~1;              // even number of players
+    const int np = m / 2;
+    // per-pair rotation data
+    int *pp = reinterpret_cast<int *>(A + (size_t)nb * ld);
+    int *pq = pp + np;
+    double *cs = reinterpret_cast<double *>(pq + np + (np & 1));
+    double *sn = cs + np;
+    double *er = sn + np;                      // e^{-i phi} real part
+    double *ei = er + np;                      // e^{-i phi} imag part
+    double *red = ei + np;                     // reduction scratch [2 * 32]
+    int *flag = reinterpret_cast<int *>(red + 64);
+
+    const int q = blockIdx.x;
+    const double2 *Aq = Ain + (size_t)q * nb * nb;
+    double2 *Vt = Vt_all + (size_t)q * nb * nb;
+    const int tid = threadIdx.x, nt = blockDim.x;
+
+    // load the Hermitian part (D + D^dagger)/2 and set Vt = I
+    for (int e = tid; e < nb * nb; e += nt) {
+        const int r = e / nb, c = e % nb;
+        const double2 x = Aq[(size_t)r * nb + c], y = Aq[(size_t)c * nb + r];
+        A[r * ld + c] = make_double2(0.5 * (x.x + y.x), 0.5 * (x.y - y.y));
+        Vt[e] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+    }
+    __syncthreads();
+
+    const int max_sweeps = 40;
+    int converged = 0;
+    for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
+        for (int rnd = 0; rnd < m - 1; ++rnd) {
+            for (int k = tid; k < np; k += nt) {
+                int a, b;
+                if (k == 0) { a = m - 1; b = rnd; }
+                else { a = (rnd + k) % (m - 1); b = (rnd - k + (m - 1)) % (m - 1); }
+                int p = min(a, b), qq = max(a, b);
+                double c_ = 1.0, s_ = 0.0, xr = 1.0, xi = 0.0;
+                if (qq < nb) {
+                    const double app = A[p * ld + p].x, aqq = A[qq * ld + qq].x;
+                    const double2 apq = A[p * ld + qq];
+                    const double r = hypot(apq.x, apq.y);
+                    if (r > 0.0) {
+                        const double z = (aqq - app) / (2.0 * r);
+                        const double t = (z >= 0.0 ? 1.0 : -1.0) / (fabs(z) + sqrt(1.0 + z * z));
+                        c_ = 1.0 / sqrt(1.0 + t * t);
+                        s_ = t * c_;
+                        xr = apq.x / r;             // e^{-i phi} = conj(apq)/r
+                        xi = -apq.y / r;
+                    }
+                } else {
+                    p = -1;                          // dummy player when nb is odd
+                }
+                pp[k] = p; pq[k] = qq; cs[k] = c_; sn[k] = s_; er[k] = xr; ei[k] = xi;
+            }
+            __syncthreads();
+            // columns: A <- A U, and Vt <- (V U)^T
+            for (int t = tid; t < nb * np; t += nt) {
+                const int k = t / nb, r = t % nb;
+                const int p = pp[k];
+                if (p < 0) continue;
+                const int qq = pq[k];
+                const double c_ = cs[k], s_ = sn[k];
+                const double2 e = make_double2(er[k], ei[k]);
+                double2 x = A[r * ld + p], y = A[r * ld + qq];
+                double2 ye = cmul(y, e);
+                A[r * ld + p] = make_double2(c_ * x.x - s_ * ye.x, c_ * x.y - s_ * ye.y);
+                A[r * ld + qq] = make_double2(s_ * x.x + c_ * ye.x, s_ * x.y + c_ * ye.y);
+                x = Vt[(size_t)p * nb + r];
+                y = Vt[(size_t)qq * nb + r];
+                ye = cmul(y, e);
+                Vt[(size_t)p * nb + r] = make_double2(c_ * x.x - s_ * ye.x, c_ * x.y - s_ * ye.y);
+                Vt[(size_t)qq * nb + r] = make_double2(s_ * x.x + c_ * ye.x, s_ * x.y + c_ * ye.y);
+            }
+            __syncthreads();
+            // rows: A <- U^dagger A
+            for (int t = tid; t < nb * np; t += nt) {
+                const int k = t / nb, c = t % nb;
+                const int p = pp[k];
+                if (p < 0) continue;
+                const int qq = pq[k];
+                const double c_ = cs[k], s_ = sn[k];
+                const double2 ec = make_double2(er[k], -ei[k]);     // e^{+i phi}
+                const double2 x = A[p * ld + c], y = A[qq * ld + c];
+                const double2 ye = cmul(ec, y);
+                A[p * ld + c] = make_double2(c_ * x.x - s_ * ye.x, c_ * x.y - s_ * ye.y);
+                A[qq * ld + c] = make_double2(s_ * x.x + c_ * ye.x, s_ * x.y + c_ * ye.y);
+            }
+            __syncthreads();
+            // exact zeros on the rotated pairs, real diagonal
+            for (int k = tid; k < np; k += nt) {
+                const int p = pp[k];
+                if (p < 0) continue;
+                const int qq = pq[k];
+                if (sn[k] != 0.0) {
+                    A[p * ld + qq] = make_double2(0.0, 0.0);
+                    A[qq * ld + p] = make_double2(0.0, 0.0);
+                }
+                A[p * ld + p].y = 0.0;
+                A[qq * ld + qq].y = 0.0;
+            }
+            __syncthreads();
+        }
+        // convergence: off-diagonal Frobenius norm vs the diagonal
+        double off = 0.0, dia = 0.0;
+        for (int e = tid; e < nb * nb; e += nt) {
+            const int r = e / nb, c = e % nb;
+            const double2 v = A[r * ld + c];
+            const double a2 = v.x * v.x + v.y * v.y;
+            if (r == c) dia += a2; else off += a2;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            dia += __shfl_xor_sync(0xffffffffu, dia, o);
+        }
+        if ((tid & 31) == 0) { red[tid >> 5] = off; red[32 + (tid >> 5)] = dia; }
+        __syncthreads();
+        if (tid == 0) {
+            double so = 0.0, sd = 0.0;
+            for (int w = 0; w < (nt + 31) / 32; ++w) { so += red[w]; sd += red[32 + w]; }
+            *flag = (so <= 1e-30 * sd) ? 1 : 0;
+        }
+        __syncthreads();
+        converged = *flag;
+        __syncthreads();
+    }
+    if (!converged && tid == 0) atomicAdd(nonconv, 1);
+
+    // ascending order: rank of each eigenvalue (ties broken by index)
+    for (int s = tid; s < nb; s += nt) {
+        const double ls = A[s * ld + s].x;
+        int rank = 0;
+        for (int t = 0; t < nb; ++t) {
+            const double lt = A[t * ld + t].x;
+            rank += (lt < ls) || (lt == ls && t < s);
+        }
+        const double w2 = ls * kEvA2AmuPs2;
+        nu_out[(size_t)q * nb + rank] = (w2 >= 0.0 ? sqrt(w2) : -sqrt(-w2)) / kTwoPi;
+        double2 *dst = eig_out + ((size_t)q * nb + rank) * nb;
+        const double2 *src = Vt + (size_t)s * nb;
+        for (int d = 0; d < nb; ++d) dst[d] = src[d];
+    }
+}
+
+// Diagonal Hellmann-Feynman velocity of every mode at every q.
+__global__ void velocity_kernel(DevFc2 f, int nb, const double *__restrict__ qcart,
+                                const double *__restrict__ nu, const double2 *__restrict__ eig,
+                                double *__restrict__ vel) {
+    const int q = blockIdx.x;
+    const double qx = qcart[3 * q], qy = qcart[3 * q + 1], qz = qcart[3 * q + 2];
+    for (int s = threadIdx.x; s < nb; s += blockDim.x) {
+        const double2 *e = eig + ((size_t)q * nb + s) * nb;
+        double v[3] = {0.0, 0.0, 0.0};
+        for (int p = 0; p < f.n_pairs; ++p) {
+            const int i = f.pair_i[p], j = f.pair_j[p];
+            for (int b = f.pair_start[p]; b < f.pair_start[p + 1]; ++b) {
+                const double *R = f.rcart + 3 * b;
+                double sn, cn;
+                sincos(qx * R[0] + qy * R[1] + qz * R[2], &sn, &cn);
+                // h = sum_{ab} conj(e_ia) blk_ab e_jb
+                double2 h = make_double2(0.0, 0.0);
+                for (int a = 0; a < 3; ++a) {
+                    double2 t = make_double2(0.0, 0.0);
+                    for (int c = 0; c < 3; ++c) {
+                        const double bv = f.blk[9 * b + 3 * a + c];
+                        const double2 ej = e[3 * j + c];
+                        t.x += bv * ej.x; t.y += bv * ej.y;
+                    }
+                    const double2 r = cmulc(e[3 * i + a], t);
+                    h.x += r.x; h.y += r.y;
+                }
+                // dD/dq_a carries (-i R_a) exp(-i q.R); with z = exp(-i q.R) h,
+                // Re(-i R_a z) = R_a Im(z)
+                const double2 ph = make_double2(cn, -sn);
+                const double2 z = cmul(ph, h);
+                v[0] += R[0] * z.y; v[1] += R[1] * z.y; v[2] += R[2] * z.y;
+            }
+        }
+        const double w = kTwoPi * nu[(size_t)q * nb + s];
+        const double f2 = (w > 0.0) ? kEvA2AmuPs2 / (2.0 * w) : 0.0;
+        for (int a = 0; a < 3; ++a) vel[((size_t)q * nb + s) * 3 + a] = v[a] * f2;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_dynmat(const DevFc2 &f, int nb, int nq, const double *qcart, double2 *D,
+                          cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(D, 0, sizeof(double2) * (size_t)nq * nb * nb, st);
+    if (e != cudaSuccess) return e;
+    dynmat_kernel<<<nq, 256, 0, st>>>(f, nb, qcart, D);
+    return cudaGetLastError();
+}
+
+size_t jacobi_smem_bytes(int nb) {
+    const int ld = nb | 1;
+    const int np = ((nb + 1) & ~1) / 2;
+    size_t b = sizeof(double2) * (size_t)nb * ld;
+    b += sizeof(int) * (2 * np + (np & 1));
+    b += sizeof(double) * (4 * np + 64);
+    b += 16;
+    return b;
+}
+
+cudaError_t launch_jacobi(int nb, int nq, double2 *A, double2 *V, double *nu_thz,
+                          double2 *eig_out, int *nonconv, size_t smem_optin, cudaStream_t st) {
+    const size_t smem = jacobi_smem_bytes(nb);
+    if (smem > smem_optin) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    jacobi_kernel<<<nq, 256, smem, st>>>(nb, A, V, nu_thz, eig_out, nonconv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_velocity_diag(const DevFc2 &f, int nb, int nq, const double *qcart,
+                                 const double *nu_thz, const double2 *eig, double *vel,
+                                 cudaStream_t st) {
+    velocity_kernel<<<nq, 128, 0, st>>>(f, nb, qcart, nu_thz, eig, vel);
+    return cudaGetLastError();
+}
+
+}  // namespace kald

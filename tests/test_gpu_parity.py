@@ -1,0 +1,240 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Stage-isolated where the eigensolver gauge would get in the way: the GPU
+linewidth and conductivity calls are fed the oracle's frequencies and
+eigenvectors, so gamma and kappa are compared element by element.  End-to-end
+checks compare only gauge-invariant results.
+
+Tolerances: FP64 path 1e-10 relative (the arithmetic is the same up to the
+order of the sums); FP32 path 1e-5 relative on gamma and 1e-4 on kappa.
+"""
+
+import numpy as np
+import pytest
+
+import kald_inputs as ki
+from oracle import anharmonic as an
+from oracle import conductivity as co
+from oracle import phonons as ph
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def k():
+    from paper_2009_01967_gb300 import build
+    build.build()
+    import paper_2009_01967_gb300 as kk
+    ctx = kk.Context(0)
+    yield kk, ctx
+    ctx.close()
+
+
+def _opts(kk, w, precision="fp64", **kw):
+    return kk.Options(temperature_K=w.T, sigma_thz=w.sigma_thz, n_sigma=w.n_sigma,
+                      precision=precision, **kw)
+
+
+def _rel(a, b, floor):
+    return np.max(np.abs(a - b) / np.maximum(np.abs(b), floor))
+
+
+# ---------------------------------------------------------------- phonons
+@pytest.mark.parametrize("case", ["C1", "binary3", "C2"])
+def test_phonons_match_oracle(k, case):
+    kk, ctx = k
+    if case == "C1":
+        w = ki.c1()
+    elif case == "binary3":
+        w = ki.small_binary(mesh=(3, 3, 3))
+    else:
+        w = ki.c2()
+    s = w.systems[0]
+    nu, eig, vel = kk.kald_phonons(ctx, s, w.mesh)
+    nu_o, eig_o = ph.phonons(s, w.mesh)
+    # squared frequencies to 1e-12 of the largest (sqrt amplifies zeros at Gamma)
+    sq = lambda x: np.sign(x) * x * x
+    np.testing.assert_allclose(sq(nu), sq(nu_o), atol=1e-12 * np.max(nu_o) ** 2)
+    assert np.all(np.diff(nu, axis=1) >= -1e-12)             # ascending
+    qs = ki.mesh_qpoints(s.lattice, w.mesh)
+    for q in range(0, len(qs), max(1, len(qs) // 9)):
+        D = ph.dynamical_matrix(s, qs[q])
+        E = eig[q].T
+        np.testing.assert_allclose(E.conj().T @ E, np.eye(E.shape[0]), atol=1e-12)
+        res = D @ E - E * (np.diag(E.conj().T @ D @ E).real)[None, :]
+        assert np.abs(res).max() < 1e-11 * np.abs(D).max()
+    # velocities of non-degenerate modes (degenerate ones depend on the basis)
+    v_o = ph.group_velocities(s, w.mesh, nu_o, eig_o)
+    for q in range(len(qs)):
+        gaps = np.diff(nu_o[q])
+        nd = np.ones(nu_o.shape[1], bool)
+        nd[:-1] &= gaps > 1e-6
+        nd[1:] &= gaps > 1e-6
+        nd &= nu_o[q] > 0.01
+        np.testing.assert_allclose(vel[q][nd], v_o[q][nd], rtol=1e-8, atol=1e-9)
+
+
+# ---------------------------------------------------------------- linewidths
+def _lw_case(case):
+    if case == "C1":
+        return ki.c1()
+    if case == "binary3":
+        return ki.small_binary(mesh=(3, 3, 3), sigma=0.1)
+    if case == "binary_random":
+        w = ki.small_binary(mesh=(3, 3, 3), sigma=0.1)
+        w.systems = [ki.random_fc3_system(w.systems[0], 60, seed=11)]
+        return w
+    if case == "gamma_only_32":
+        s = ki.fcc_supercell_system(2, seed=5)
+        return ki.Workload("g32", [s], (1, 1, 1), 300.0, 0.1, 3.0)
+    if case == "C5_mesh6":
+        return ki.c5(mesh=(6, 6, 6))
+    raise KeyError(case)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", ["C1", "binary3", "binary_random", "gamma_only_32", "C5_mesh6"])
+def test_linewidths_match_oracle(k, case, precision):
+    kk, ctx = k
+    w = _lw_case(case)
+    s = w.systems[0]
+    nu_o, eig_o = ph.phonons(s, w.mesh)
+    g_o = an.linewidths(s, w.mesh, nu_o, eig_o, w.T, w.sigma_thz, w.n_sigma)
+    g, (tot, allowed) = kk.kald_linewidths(ctx, s, w.mesh, nu_o, eig_o, _opts(kk, w, precision))
+    g = g.reshape(g_o.shape)
+    assert tot == w.n_q ** 2 * s.n_branches ** 3
+    floor = 1e-6 * g_o.max()
+    if precision == "fp64":
+        assert _rel(g, g_o, floor) < 1e-10
+    else:
+        assert _rel(g, g_o, floor) < 1e-5
+    assert np.all(g[nu_o <= 0.01] == 0.0)
+    # delta-allowed count: (s, s', s'') with both modes valid and |d nu| < n sigma sigma
+    if precision == "fp64":
+        nq, nb = nu_o.shape
+        kf = ki.mesh_fractions(w.mesh)
+        valid = nu_o > 0.01
+        cnt = 0
+        cut = w.n_sigma * w.sigma_thz * 2 * np.pi
+        om = 2 * np.pi * nu_o
+        for q in range(nq):
+            qpp = an.mesh_index(w.mesh, kf[q][None, :] + kf)
+            a = om[q][:, None, None]
+            b = om[:, None, :, None]
+            c = om[qpp][:, None, None, :]
+            ok = valid[q][:, None, None] & valid[:, None, :, None] & valid[qpp][:, None, None, :]
+            hit = (np.abs(a + b - c) < cut) | (np.abs(a - b - c) < cut)
+            cnt += int(np.sum(ok & hit))
+        assert allowed == cnt
+
+
+def test_linewidths_c2_sampled_q(k):
+    """Full-size 32-atom / 8^3 workload in the launch configuration the
+    benchmark times (FP32), checked at sampled q-points against the oracle."""
+    kk, ctx = k
+    w = ki.c2()
+    s = w.systems[0]
+    nu_o, eig_o = ph.phonons(s, w.mesh)
+    g, (tot, allowed) = kk.kald_linewidths(ctx, s, w.mesh, nu_o, eig_o, _opts(kk, w, "fp32"))
+    g = g.reshape(nu_o.shape)
+    qs = [1, 137]
+    g_o = an.linewidths(s, w.mesh, nu_o, eig_o, w.T, w.sigma_thz, w.n_sigma, q_list=qs)
+    assert _rel(g[qs], g_o, 1e-6 * g_o.max()) < 1e-5
+    assert tot == 512 ** 2 * 96 ** 3 and 0 < allowed < tot
+
+
+# ---------------------------------------------------------------- kappa
+def test_kappa_rta_matches_oracle(k):
+    kk, ctx = k
+    w = ki.c1()
+    s = w.systems[0]
+    nu_o, eig_o = ph.phonons(s, w.mesh)
+    g_o = an.linewidths(s, w.mesh, nu_o, eig_o, w.T, w.sigma_thz, w.n_sigma)
+    kap = kk.kald_kappa_rta(ctx, s, w.mesh, nu_o, eig_o, g_o, _opts(kk, w))
+    kap_o = co.kappa_rta(s, w.mesh, nu_o, eig_o, g_o, w.T)
+    np.testing.assert_allclose(kap, kap_o, rtol=1e-10, atol=1e-12 * np.abs(kap_o).max())
+
+
+def test_kappa_rta_binary_anisotropic(k):
+    kk, ctx = k
+    w = ki.small_binary(mesh=(4, 4, 4), sigma=0.1)
+    s = w.systems[0]
+    nu_o, eig_o = ph.phonons(s, w.mesh)
+    g_o = an.linewidths(s, w.mesh, nu_o, eig_o, w.T, w.sigma_thz, w.n_sigma)
+    kap = kk.kald_kappa_rta(ctx, s, w.mesh, nu_o, eig_o, g_o, _opts(kk, w))
+    kap_o = co.kappa_rta(s, w.mesh, nu_o, eig_o, g_o, w.T)
+    np.testing.assert_allclose(kap, kap_o, rtol=1e-10, atol=1e-12 * np.abs(kap_o).max())
+
+
+@pytest.mark.parametrize("ncell,seed", [(1, 4), (2, 5)])
+def test_kappa_qhgk_matches_oracle(k, ncell, seed):
+    kk, ctx = k
+    s = ki.fcc_supercell_system(ncell, seed=seed)
+    T, sig = 300.0, 0.1
+    nu_o, eig_o = ph.phonons(s, (1, 1, 1))
+    g_o = an.linewidths_gamma_only(s, nu_o, eig_o, T, sig)
+    w = ki.Workload("q", [s], (1, 1, 1), T, sig, 3.0)
+    kap, vgen = kk.kald_kappa_qhgk(ctx, [s], nu_o, eig_o, g_o, _opts(kk, w), want_vgen=True)
+    W_o = co.generalized_velocity(s, nu_o, eig_o)
+    kap_o = co.kappa_qhgk(s, nu_o, eig_o, g_o, T, W=W_o)
+    np.testing.assert_allclose(vgen, W_o, rtol=1e-10, atol=1e-11 * np.abs(W_o).max())
+    np.testing.assert_allclose(kap[0], kap_o, rtol=1e-10, atol=1e-12 * np.abs(kap_o).max())
+
+
+# ---------------------------------------------------------------- end to end
+def test_end_to_end_c1_gauge_free(k):
+    kk, ctx = k
+    w = ki.c1()
+    s = w.systems[0]
+    nu, eig, _ = kk.kald_phonons(ctx, s, w.mesh)
+    g, _ = kk.kald_linewidths(ctx, s, w.mesh, nu, eig, _opts(kk, w))
+    kap = kk.kald_kappa_rta(ctx, s, w.mesh, nu, eig, g, _opts(kk, w))
+    nu_o, eig_o = ph.phonons(s, w.mesh)
+    g_o = an.linewidths(s, w.mesh, nu_o, eig_o, w.T, w.sigma_thz, w.n_sigma)
+    kap_o = co.kappa_rta(s, w.mesh, nu_o, eig_o, g_o, w.T)
+    assert _rel(g.reshape(g_o.shape), g_o, 1e-6 * g_o.max()) < 1e-9
+    np.testing.assert_allclose(kap, kap_o, rtol=1e-9)
+
+
+def test_device_pointers_in_and_out(k):
+    torch = pytest.importorskip("torch")
+    kk, ctx = k
+    w = ki.small_binary(mesh=(3, 3, 3), sigma=0.1)
+    s = w.systems[0]
+    nq, nb = w.n_q, s.n_branches
+    nu = torch.zeros((nq, nb), dtype=torch.float64, device="cuda")
+    eig = torch.zeros((nq, nb, nb), dtype=torch.complex128, device="cuda")
+    kk.kald_phonons(ctx, s, w.mesh, nu_thz=nu, eigvec=eig, want_vel=False)
+    g = torch.zeros(nq * nb, dtype=torch.float64, device="cuda")
+    kk.kald_linewidths(ctx, s, w.mesh, nu, eig, _opts(kk, w), gamma=g)
+    kap = torch.zeros((3, 3), dtype=torch.float64, device="cuda")
+    kk.kald_kappa_rta(ctx, s, w.mesh, nu, eig, g, _opts(kk, w), kappa=kap)
+    nu_h, eig_h, _ = kk.kald_phonons(ctx, s, w.mesh, want_vel=False)
+    g_h, _ = kk.kald_linewidths(ctx, s, w.mesh, nu_h, eig_h, _opts(kk, w))
+    kap_h = kk.kald_kappa_rta(ctx, s, w.mesh, nu_h, eig_h, g_h, _opts(kk, w))
+    np.testing.assert_allclose(kap.cpu().numpy(), kap_h, rtol=1e-12)
+
+
+# ---------------------------------------------------------------- errors
+def test_invalid_inputs_are_rejected(k):
+    kk, ctx = k
+    w = ki.small_binary(mesh=(2, 2, 2))
+    s = w.systems[0]
+    bad = ki.System(np.array([28.09, -1.0]), s.positions, s.lattice, s.fc2_idx, s.fc2,
+                    s.fc3_idx, s.fc3)
+    with pytest.raises(kk.KaldError) as e:
+        kk.kald_phonons(ctx, bad, w.mesh)
+    assert e.value.status == 1
+    with pytest.raises(kk.KaldError) as e:
+        kk.kald_phonons(ctx, s, (0, 2, 2))
+    assert e.value.status == 1
+    nu, eig, _ = kk.kald_phonons(ctx, s, w.mesh)
+    o = _opts(kk, w)
+    o.n_sigma = 0.0
+    with pytest.raises(kk.KaldError) as e:
+        kk.kald_linewidths(ctx, s, w.mesh, nu, eig, o)
+    assert e.value.status == 1
+    big = ki.fcc_supercell_system(3, seed=1)        # 108 atoms: nb = 324 > 96
+    with pytest.raises(kk.KaldError) as e:
+        kk.kald_phonons(ctx, big, (1, 1, 1))
+    assert e.value.status == 6
