@@ -9,7 +9,8 @@ from .lattice import (fcc_primitive, fcc_conventional, l11_binary, reciprocal,
                       mesh_fractions, mesh_qpoints)
 from .lj import lj_system, lj_radial, pair_tensors, LJ_EPSILON, LJ_SIGMA, LJ_CUTOFF
 from .configs import (Workload, WORKLOADS, c1, c2, c3, c4, c5, small_fcc_prim,
-                      small_binary, random_fc3_system, supercell_of, A_FCC)
+                      small_binary, random_fc3_system, supercell_of, A_FCC,
+                      fcc_supercell_system)
 from .rng import SplitMix64, shuffled_labels
 
 __all__ = [
@@ -17,5 +18,5 @@ __all__ = [
     "mesh_fractions", "mesh_qpoints", "lj_system", "lj_radial", "pair_tensors",
     "LJ_EPSILON", "LJ_SIGMA", "LJ_CUTOFF", "Workload", "WORKLOADS", "c1", "c2",
     "c3", "c4", "c5", "small_fcc_prim", "small_binary", "random_fc3_system",
-    "supercell_of", "A_FCC", "SplitMix64", "shuffled_labels",
+    "supercell_of", "A_FCC", "fcc_supercell_system", "SplitMix64", "shuffled_labels",
 ]

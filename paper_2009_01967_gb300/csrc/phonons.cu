@@ -66,7 +66,8 @@ jacobi_kernel(int nb, double2 *__restrict__ Ain, double2 *__restrict__ Vt_all,
     // per-pair rotation data
     int *pp = reinterpret_cast<int *>(A + (size_t)nb * ld);
     int *pq = pp + np;
-    double *cs = reinterpret_cast<double *>(pq + np + (np & 1));
+    // 2 np ints = 8 np bytes keep the doubles that follow 8-byte aligned
+    double *cs = reinterpret_cast<double *>(pp + 2 * np);
     double *sn = cs + np;
     double *er = sn + np;                      // e^{-i phi} real part
     double *ei = er + np;                      // e^{-i phi} imag part
@@ -257,7 +258,7 @@ size_t jacobi_smem_bytes(int nb) {
     const int ld = nb | 1;
     const int np = ((nb + 1) & ~1) / 2;
     size_t b = sizeof(double2) * (size_t)nb * ld;
-    b += sizeof(int) * (2 * np + (np & 1));
+    b += sizeof(int) * (2 * np);
     b += sizeof(double) * (4 * np + 64);
     b += 16;
     return b;
