@@ -165,6 +165,8 @@ def run_kald(args):
     dev = torch.device("cuda", local)
     kk.load_library()
     w = WORKLOADS[args.workload]()
+    if args.mesh:
+        w.mesh = tuple(int(x) for x in args.mesh.split(","))
     s = w.systems[0]
     nq, nb = w.n_q, s.n_branches
     opt = kk.Options(temperature_K=w.T, sigma_thz=w.sigma_thz, n_sigma=w.n_sigma,
@@ -230,7 +232,7 @@ def run_kald(args):
     sys_bytes = (s.masses.nbytes + s.positions.nbytes + s.fc2_idx.nbytes + s.fc2.nbytes +
                  s.fc3_idx.nbytes + s.fc3.nbytes)
     e2e_ms = []
-    for it in range(max(1, min(args.steps, 3))):
+    for it in range(0 if args.no_e2e else max(1, min(args.steps, 3))):
         flush.fill_(2.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -240,7 +242,7 @@ def run_kald(args):
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     h2d = 3 * sys_bytes + 2 * (nu_h.nbytes + eig_h.nbytes) + gam_h.nbytes
     d2h = nu_h.nbytes + eig_h.nbytes + gam_h.nbytes + kap_h.nbytes
-    e2e_value = triplets_step / (float(np.mean(e2e_ms)) / 1e3)
+    e2e_value = triplets_step / (float(np.mean(e2e_ms)) / 1e3) if e2e_ms else None
 
     # ---- roofline of the dominant kernel (linewidth projection)
     trip, allowed = trip_info["trip"]
@@ -297,6 +299,8 @@ def main():
     ap.add_argument("--workload", default="C2", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling runs)")
+    ap.add_argument("--mesh", default=None, help="override the q-mesh, e.g. 4,4,4 (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -86,10 +86,13 @@ def position_weighted_dynmat(sys):
     L = sys.fc2_idx[:, 2:5].astype(float) @ sys.lattice
     d = sys.positions[i] - sys.positions[j] - L                        # [B, 3]
     blk = sys.fc2 / np.sqrt(m[i] * m[j])[:, None, None]
-    A = np.zeros((3, nb, nb))
-    for b in range(blk.shape[0]):
-        for a in range(3):
-            A[a, 3 * i[b]:3 * i[b] + 3, 3 * j[b]:3 * j[b] + 3] += d[b, a] * blk[b]
+    rows = (3 * i[:, None, None] + np.arange(3)[None, :, None]) * nb
+    cols = 3 * j[:, None, None] + np.arange(3)[None, None, :]
+    flat = (rows + cols).reshape(-1)
+    A = np.zeros((3, nb * nb))
+    for a in range(3):
+        np.add.at(A[a], flat, (d[:, a, None, None] * blk).reshape(-1))
+    A = A.reshape(3, nb, nb)
     return A
 
 
@@ -102,7 +105,7 @@ def generalized_velocity(sys, nu, eig, omega_min_thz=0.01):
     valid = nu[0] > omega_min_thz
     w = np.where(valid, omega, 1.0)
     A = position_weighted_dynmat(sys)
-    W = np.einsum("dm,ade,en->amn", E, A, E) * EV_A2_AMU
+    W = np.stack([E.T @ A[a] @ E for a in range(3)]) * EV_A2_AMU
     W = W / (2.0 * np.sqrt(np.outer(w, w)))[None]
     W[:, ~valid, :] = 0.0
     W[:, :, ~valid] = 0.0

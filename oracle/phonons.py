@@ -47,15 +47,19 @@ def dynamical_matrix(sys, q_cart, with_derivative=False, atom_phase=False):
     if atom_phase:
         R = R + sys.positions[j] - sys.positions[i]
     ph = np.exp(-1j * (R @ q_cart))                              # [B]
-    D = np.zeros((nb, nb), dtype=complex)
-    dD = np.zeros((3, nb, nb), dtype=complex) if with_derivative else None
-    for b in range(blocks.shape[0]):
-        sl_i = slice(3 * i[b], 3 * i[b] + 3)
-        sl_j = slice(3 * j[b], 3 * j[b] + 3)
-        D[sl_i, sl_j] += blocks[b] * ph[b]
-        if with_derivative:
-            for a in range(3):
-                dD[a, sl_i, sl_j] += (-1j * R[b, a]) * blocks[b] * ph[b]
+    # scatter-add every block into its (i, j) 3x3 position
+    rows = (3 * i[:, None, None] + np.arange(3)[None, :, None]) * nb
+    cols = 3 * j[:, None, None] + np.arange(3)[None, None, :]
+    flat = (rows + cols).reshape(-1)
+    D = np.zeros(nb * nb, dtype=complex)
+    np.add.at(D, flat, (blocks * ph[:, None, None]).reshape(-1))
+    D = D.reshape(nb, nb)
+    dD = None
+    if with_derivative:
+        dD = np.zeros((3, nb * nb), dtype=complex)
+        for a in range(3):
+            np.add.at(dD[a], flat, ((-1j * R[:, a] * ph)[:, None, None] * blocks).reshape(-1))
+        dD = dD.reshape(3, nb, nb)
     D = 0.5 * (D + D.conj().T)
     if with_derivative:
         dD = 0.5 * (dD + np.conj(np.transpose(dD, (0, 2, 1))))
@@ -95,7 +99,7 @@ def velocity_matrices(sys, q_cart, eig_q, nu_q, atom_phase=False):
     good = omega > 0
     w = np.where(good, omega, 1.0)
     E = eig_q.T                                        # columns = modes
-    V = np.einsum("sd,ade,et->ast", E.conj().T, dD, E)  # eta^dagger dD eta
+    V = np.stack([E.conj().T @ dD[a] @ E for a in range(3)])   # eta^dagger dD eta
     V = V * EV_A2_AMU / (2.0 * np.sqrt(np.outer(w, w)))[None]
     V[:, ~good, :] = 0.0
     V[:, :, ~good] = 0.0

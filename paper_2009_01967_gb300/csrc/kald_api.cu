@@ -444,8 +444,6 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
         p.nb = nb; p.nq = nq;
         for (int a = 0; a < 3; ++a) p.mesh[a] = mesh[a];
         p.n_rep = h.n_rep;
-        p.n_pairs3 = (int)h.pair3_j.size();
-        p.n_elem = p.n_pairs3 * 9;
         p.sigma_w = kTwoPi * opt->sigma_thz;
         p.cut_w = opt->n_sigma * p.sigma_w;
         p.T = opt->temperature_K;
@@ -458,13 +456,24 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
             p.qp_chunk = (nq + nch - 1) / nch;
             p.n_chunks = (nq + p.qp_chunk - 1) / p.qp_chunk;
         }
-        std::vector<int> pjk(2 * (size_t)p.n_pairs3);
-        for (int t = 0; t < p.n_pairs3; ++t) { pjk[2 * t] = h.pair3_j[t]; pjk[2 * t + 1] = h.pair3_k[t]; }
+        YSchedule ys;
+        plan_ybuild(h, ys);
+        p.n_rounds = ys.n_rounds;
+        const size_t n3 = h.fc3_i.size();
+        std::vector<int4> binfo(std::max<size_t>(n3, 1), make_int4(0, 0, 0, 0));
+        for (size_t b = 0; b < n3; ++b) binfo[b] = make_int4(h.fc3_i[b], h.fc3_rj[b], h.fc3_rk[b], 0);
         std::vector<float> fc3f;
-        if (fp32) fc3f.assign(h.fc3_scaled.begin(), h.fc3_scaled.end());
+        std::vector<double> fc3d;
+        if (fp32) fc3f.assign(28 * std::max<size_t>(n3, 1), 0.0f);
+        else fc3d.assign(28 * std::max<size_t>(n3, 1), 0.0);
+        for (size_t b = 0; b < n3; ++b)
+            for (int e = 0; e < 27; ++e) {
+                if (fp32) fc3f[28 * b + e] = (float)h.fc3_scaled[27 * b + e];
+                else fc3d[28 * b + e] = h.fc3_scaled[27 * b + e];
+            }
         const size_t c2 = fp32 ? sizeof(float2) : sizeof(double2);
-        size_t need = bytes_of(h.pair3_start) + bytes_of(pjk) + bytes_of(h.fc3_i) + bytes_of(h.fc3_rj) +
-                      bytes_of(h.fc3_rk) + (fp32 ? bytes_of(fc3f) : bytes_of(h.fc3_scaled)) +
+        size_t need = bytes_of(ys.group_jk) + bytes_of(ys.segs) + bytes_of(ys.sched) + bytes_of(binfo) +
+                      (fp32 ? bytes_of(fc3f) : bytes_of(fc3d)) +
                       bytes_of(h.rep_cart) + bytes_of(qc) + bytes_of(qf) +
                       2 * ws_round(sizeof(double) * nq * nb) + ws_round(c2 * nn) +
                       ws_round(c2 * (size_t)nq * h.n_rep) +
@@ -474,12 +483,11 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
         if (!d_g) need += ws_round(sizeof(double) * nq * nb);
         if ((st = ws_reserve(ctx, need))) return st;
         LwDev d;
-        d.pair_start = upload(ctx, h.pair3_start);
-        d.pair_jk = upload(ctx, pjk);
-        d.blk_i = upload(ctx, h.fc3_i);
-        d.blk_rj = upload(ctx, h.fc3_rj);
-        d.blk_rk = upload(ctx, h.fc3_rk);
-        d.fc3 = fp32 ? (const void *)upload(ctx, fc3f) : (const void *)upload(ctx, h.fc3_scaled);
+        d.group_jk = upload(ctx, ys.group_jk);
+        d.segs = upload(ctx, ys.segs);
+        d.sched = upload(ctx, ys.sched);
+        d.blkinfo = upload(ctx, binfo);
+        d.fc3 = fp32 ? (const void *)upload(ctx, fc3f) : (const void *)upload(ctx, fc3d);
         d.rep_cart = upload(ctx, h.rep_cart);
         d.qcart = upload(ctx, qc);
         d.qfrac = upload(ctx, qf);

@@ -105,8 +105,7 @@ cudaError_t launch_velocity_diag(const DevFc2 &f, int nb, int nq, const double *
 struct LwParams {
     int nb, nq, mesh[3];
     int n_rep;
-    int n_pairs3;             // (j,k) output pairs
-    int n_elem;               // n_pairs3 * 9 output elements
+    int n_rounds;             // rounds of the Y-build lane schedule
     double sigma_w;           // 2 pi sigma (rad/ps)
     double cut_w;             // n_sigma * sigma_w
     double T;
@@ -115,11 +114,19 @@ struct LwParams {
     int qp_chunk;             // q' per work item
     int n_chunks;             // ceil(nq / qp_chunk)
 };
+// Y-build lane schedule (built on the host by plan_ybuild): in round r lane t
+// runs segments sched[r*256+t] .. sched[r*256+t+1]-1.  A segment is
+// (group, first block, end block, red): the blocks of one (j, k) atom pair,
+// or a slice of them; red > 1 marks a slice whose partial sums are added
+// across `red` aligned lanes with shuffles (a "heavy" round: every lane has
+// exactly one segment, all with the same red); group < 0 is an empty slot.
+constexpr int kLwThreads = 256;
 struct LwDev {
-    const int *pair_start;    // [n_pairs3+1]
-    const int *pair_jk;       // [n_pairs3][2]
-    const int *blk_i, *blk_rj, *blk_rk;   // [n_fc3]
-    const void *fc3;          // [n_fc3][27] float or double (scaled)
+    const int *group_jk;      // [n_groups][2] atoms (j, k)
+    const int4 *segs;         // [n_seg] (group, b0, b1, red)
+    const int *sched;         // [n_rounds * 256 + 1]
+    const int4 *blkinfo;      // [n_fc3] (i, rep(Rj), rep(Rk), 0), schedule order
+    const void *fc3;          // [n_fc3][28] float or double, Phi3 / sqrt(mi mj mk), padded
     const double *rep_cart;   // [n_rep][3]
     const double *qcart;      // [nq][3]
     const int *qfrac;         // [nq][3]
@@ -128,12 +135,21 @@ struct LwDev {
     // derived (filled by prep kernels)
     double *omega;            // [nq*nb] rad/ps (0 if masked)
     double *occ;              // [nq*nb] Bose n (0 if masked)
-    void *eps_work;           // [nq][nb][nb] float2 (fp32 path) or unused
-    void *chi;                // [nq][n_rep] float2 or double2: exp(-i q.R)
+    void *eps_work;           // [nq][nb][nb] eps^T in the working precision
+    void *chi;                // [nq][n_rep] exp(-i q.R) in the working precision
     double *partial;          // [nq][n_chunks][nb] FP64 partial sums
     unsigned long long *allowed;   // [1] delta-allowed triplet count
     int *queue;               // [1] work counter
 };
+struct YSchedule {
+    std::vector<int> group_jk;     // [n_groups][2]
+    std::vector<int4> segs;
+    std::vector<int> sched;
+    std::vector<int> blk_order;    // schedule position -> block index of HostSystem fc3 order
+    int n_rounds = 0;
+};
+// Build the lane schedule of the Y-build for one planned system.
+void plan_ybuild(const HostSystem &h, YSchedule &ys);
 cudaError_t launch_lw_prep(const LwParams &p, const LwDev &d, int fp32, cudaStream_t st);
 cudaError_t launch_lw_main(const LwParams &p, const LwDev &d, int fp32, int sm_count,
                            size_t smem_optin, cudaStream_t st);

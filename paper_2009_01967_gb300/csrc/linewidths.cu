@@ -89,16 +89,37 @@ __global__ void eps_transpose_kernel(int nq, int nb, const double2 *__restrict__
 }
 
 // -------------------------------------------------------------- main kernel
-template <typename R> struct Smem {
-    using R2 = typename C2<R>::T;
-};
-
 template <typename R2>
 __device__ __forceinline__ void cfma(R2 &acc, const R2 a, const R2 b) {   // acc += a b
     acc.x = fma(a.x, b.x, acc.x);
     acc.x = fma(-a.y, b.y, acc.x);
     acc.y = fma(a.x, b.y, acc.y);
     acc.y = fma(a.y, b.x, acc.y);
+}
+template <typename R2>
+__device__ __forceinline__ R2 cmul(const R2 a, const R2 b) {
+    R2 r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+
+// Load the 28 (27 + pad) scaled Phi3 values of one block.
+__device__ __forceinline__ void load_blk(const float *f, float v[28]) {
+    const float4 *f4 = reinterpret_cast<const float4 *>(f);
+#pragma unroll
+    for (int x = 0; x < 7; ++x) {
+        const float4 t = __ldg(f4 + x);
+        v[4 * x] = t.x; v[4 * x + 1] = t.y; v[4 * x + 2] = t.z; v[4 * x + 3] = t.w;
+    }
+}
+__device__ __forceinline__ void load_blk(const double *f, double v[28]) {
+    const double2 *f2 = reinterpret_cast<const double2 *>(f);
+#pragma unroll
+    for (int x = 0; x < 14; ++x) {
+        const double2 t = __ldg(f2 + x);
+        v[2 * x] = t.x; v[2 * x + 1] = t.y;
+    }
 }
 
 // Shared memory layout (R2 = complex of the working precision; P = nb
@@ -110,6 +131,7 @@ __device__ __forceinline__ void cfma(R2 &acc, const R2 a, const R2 b) {   // acc
 //   chip, chipp [n_rep]    chi(q'), chi(q'')
 //   wp, np_, wpp, npp [P]  omega and n of q' / q'' (R)
 //   red  [nwarps][nb] double   per-warp sums over the item's q'
+//   tiles [256] int  active (s', s'') tiles of the delta band
 template <typename R, bool OPER_SMEM>
 __global__ void __launch_bounds__(kThreads, 1)
 lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
@@ -120,7 +142,7 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
     const int nb = p.nb;
     const int P = ((nb + kTile - 1) / kTile) * kTile;
     const int tpr = P / kTile;                       // tiles per row
-    const int n_tiles = tpr * tpr;
+    const int n_tiles = tpr * tpr;                   // <= 256 for nb <= 96
     R2 *Y = reinterpret_cast<R2 *>(smem_raw);
     R2 *EpT = Y + (size_t)P * P;
     R2 *EppT = OPER_SMEM ? EpT + (size_t)P * P : EpT;
@@ -133,7 +155,8 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
     R *npp = wpp + P;
     double *red = reinterpret_cast<double *>(
         (reinterpret_cast<uintptr_t>(npp + P) + 15) & ~uintptr_t(15));
-    __shared__ int item_sm;
+    int *tiles = reinterpret_cast<int *>(red + (kThreads / 32) * nb);
+    __shared__ int item_sm, n_act_sm, warp_cnt[kThreads / 32];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarps = kThreads / 32;
@@ -193,39 +216,59 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
                 const double w_s = d.omega[(size_t)q * nb + s];
                 if (w_s <= 0.0) continue;              // masked mode (uniform branch)
                 const R w = (R)w_s;
-                // ---- Y_s: zero, then gather over blocks
+                // ---- Y_s: zero, then the scheduled gather over fc3 blocks
                 for (int x = tid; x < P; x += kThreads)
                     es[x] = x < nb ? epsT_all[((size_t)q * nb + x) * nb + s] : mk<R2>(0.0, 0.0);
                 for (int x = tid; x < P * P; x += kThreads) Y[x] = mk<R2>(0.0, 0.0);
                 __syncthreads();
-                for (int e = tid; e < p.n_elem; e += kThreads) {
-                    const int pr = e / 9, bg = e % 9;
-                    const int j = d.pair_jk[2 * pr], k = d.pair_jk[2 * pr + 1];
-                    R2 acc = mk<R2>(0.0, 0.0);
-                    for (int bl = d.pair_start[pr]; bl < d.pair_start[pr + 1]; ++bl) {
-                        const int i = d.blk_i[bl];
-                        const R *f = fc3 + (size_t)27 * bl + bg;
-                        const R2 e0 = es[3 * i], e1 = es[3 * i + 1], e2 = es[3 * i + 2];
-                        const R f0 = __ldg(f), f1 = __ldg(f + 9), f2 = __ldg(f + 18);
-                        R2 wv;
-                        wv.x = f0 * e0.x + f1 * e1.x + f2 * e2.x;
-                        wv.y = f0 * e0.y + f1 * e1.y + f2 * e2.y;
-                        const R2 a = chip[d.blk_rj[bl]];
-                        const R2 b = chipp[d.blk_rk[bl]];
-                        // P = chi(q', Rj) conj(chi(q'', Rk))
-                        R2 ph;
-                        ph.x = a.x * b.x + a.y * b.y;
-                        ph.y = a.y * b.x - a.x * b.y;
-                        cfma(acc, wv, ph);
+                for (int r = 0; r < p.n_rounds; ++r) {
+                    const int g0 = d.sched[r * kThreads + tid], g1 = d.sched[r * kThreads + tid + 1];
+                    for (int sg = g0; sg < g1; ++sg) {
+                        const int4 seg = d.segs[sg];
+                        R2 acc[9];
+#pragma unroll
+                        for (int x = 0; x < 9; ++x) acc[x] = mk<R2>(0.0, 0.0);
+                        for (int bl = seg.y; bl < seg.z; ++bl) {
+                            const int4 bi = __ldg(d.blkinfo + bl);
+                            R v[28];
+                            load_blk(fc3 + (size_t)28 * bl, v);
+                            const R2 a = chip[bi.y], b = chipp[bi.z];
+                            // P = chi(q', Rj) conj(chi(q'', Rk))
+                            R2 ph;
+                            ph.x = a.x * b.x + a.y * b.y;
+                            ph.y = a.y * b.x - a.x * b.y;
+                            const R2 e0 = cmul(es[3 * bi.x], ph);
+                            const R2 e1 = cmul(es[3 * bi.x + 1], ph);
+                            const R2 e2 = cmul(es[3 * bi.x + 2], ph);
+#pragma unroll
+                            for (int x = 0; x < 9; ++x) {
+                                acc[x].x = fma(v[x], e0.x, fma(v[9 + x], e1.x, fma(v[18 + x], e2.x, acc[x].x)));
+                                acc[x].y = fma(v[x], e0.y, fma(v[9 + x], e1.y, fma(v[18 + x], e2.y, acc[x].y)));
+                            }
+                        }
+                        const int rr = seg.w;
+                        if (rr > 1) {                  // heavy slice: add the R lanes' partials
+                            for (int o = rr >> 1; o > 0; o >>= 1)
+#pragma unroll
+                                for (int x = 0; x < 9; ++x) {
+                                    acc[x].x += __shfl_xor_sync(0xffffffffu, acc[x].x, o);
+                                    acc[x].y += __shfl_xor_sync(0xffffffffu, acc[x].y, o);
+                                }
+                        }
+                        if (seg.x >= 0 && (rr <= 1 || (lane & (rr - 1)) == 0)) {
+                            const int j = d.group_jk[2 * seg.x], k = d.group_jk[2 * seg.x + 1];
+#pragma unroll
+                            for (int x = 0; x < 9; ++x)
+                                Y[(size_t)(3 * j + x / 3) * P + 3 * k + x % 3] = acc[x];
+                        }
                     }
-                    Y[(size_t)(3 * j + bg / 3) * P + 3 * k + bg % 3] = acc;
                 }
                 __syncthreads();
 
-                // ---- GEMM1: T'(s', c) = sum_b epsT'(b, s') Y(b, c)
+                // ---- GEMM1: T'(s', c) = sum_b epsT'(b, s') Y(b, c), dense
                 const int ti = tid / tpr, tj = tid % tpr;
                 const bool active = tid < n_tiles;
-                const int r0 = ti * kTile, c0 = tj * kTile;
+                int r0 = ti * kTile, c0 = tj * kTile;
                 R2 acc[kTile][kTile];
                 if (active) {
 #pragma unroll
@@ -247,18 +290,8 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
                             for (int c = 0; c < kTile; ++c) cfma(acc[r][c], av[r], bv[c]);
                     }
                 }
-                __syncthreads();
-                if (active) {
-#pragma unroll
-                    for (int r = 0; r < kTile; ++r)
-#pragma unroll
-                        for (int c = 0; c < kTile; ++c)
-                            Y[(size_t)(c0 + c) * P + r0 + r] = acc[r][c];   // T'^T(c, s')
-                }
-                __syncthreads();
-
-                // ---- GEMM2 + epilogue over (s', s'') tiles inside the delta band
-                R part = (R)0;
+                // ---- delta band: list the (s', s'') tiles that can hold an allowed pair
+                bool band = false;
                 if (active) {
                     R wlo = (R)1e30, whi = (R)-1e30, xlo = (R)1e30, xhi = (R)-1e30;
 #pragma unroll
@@ -268,34 +301,87 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
                     }
                     // d+ = w + w' - w'' in [w + wlo - xhi, w + whi - xlo]
                     // d- = w - w' - w'' in [w - whi - xhi, w - wlo - xlo]
-                    const bool band_p = (w + wlo - xhi < cut) && (w + whi - xlo > -cut);
-                    const bool band_m = (w - whi - xhi < cut) && (w - wlo - xlo > -cut);
-                    if (band_p || band_m) {
+                    band = ((w + wlo - xhi < cut) && (w + whi - xlo > -cut)) ||
+                           ((w - whi - xhi < cut) && (w - wlo - xlo > -cut));
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, band);
+                if (lane == 0) warp_cnt[warp] = __popc(bal);
+                __syncthreads();
+                if (active) {
+#pragma unroll
+                    for (int r = 0; r < kTile; ++r)
+#pragma unroll
+                        for (int c = 0; c < kTile; ++c)
+                            Y[(size_t)(c0 + c) * P + r0 + r] = acc[r][c];   // T'^T(c, s')
+                }
+                if (band) {
+                    int off = 0;
+                    for (int w8 = 0; w8 < warp; ++w8) off += warp_cnt[w8];
+                    off += __popc(bal & ((1u << lane) - 1u));
+                    tiles[off] = tid;
+                }
+                if (tid == 0) {
+                    int t = 0;
+                    for (int w8 = 0; w8 < nwarps; ++w8) t += warp_cnt[w8];
+                    n_act_sm = t;
+                }
+                __syncthreads();
+
+                // ---- GEMM2 + epilogue on the band tiles, K split over S lanes
+                const int n_act = n_act_sm;
+                int S = 1;
+                while (S < 8 && n_act * S * 2 <= kThreads) S <<= 1;
+                const int per_pass = kThreads / S;
+                const int ks = tid & (S - 1);
+                const int kc = (nb + S - 1) / S;
+                const int kb0 = ks * kc, kb1 = min(nb, kb0 + kc);
+                R part = (R)0;
+                for (int base = 0; base < n_act; base += per_pass) {
+                    // every lane runs every pass (the shuffles below need the
+                    // whole warp); lanes past the list do no work
+                    const int ti2 = base + tid / S;
+                    const bool valid = ti2 < n_act;
+                    const int tt = valid ? tiles[ti2] : 0;
+                    r0 = (tt / tpr) * kTile;
+                    c0 = (tt % tpr) * kTile;
+#pragma unroll
+                    for (int r = 0; r < kTile; ++r)
+#pragma unroll
+                        for (int c = 0; c < kTile; ++c) acc[r][c] = mk<R2>(0.0, 0.0);
+                    const int ke = valid ? kb1 : kb0;
+                    for (int c = kb0; c < ke; ++c) {
+                        R2 av[kTile], bv[kTile];
+#pragma unroll
+                        for (int r = 0; r < kTile; ++r) av[r] = Y[(size_t)c * P + r0 + r];
+                        if (OPER_SMEM) {
+#pragma unroll
+                            for (int k = 0; k < kTile; ++k) bv[k] = EppT[(size_t)c * P + c0 + k];
+                        } else {
+                            const R2 *brow = epsT_all + ((size_t)qpp * nb + c) * nb;
+#pragma unroll
+                            for (int k = 0; k < kTile; ++k) {
+                                R2 v = (c0 + k < nb) ? brow[c0 + k] : mk<R2>(0.0, 0.0);
+                                v.y = -v.y;
+                                bv[k] = v;
+                            }
+                        }
 #pragma unroll
                         for (int r = 0; r < kTile; ++r)
 #pragma unroll
-                            for (int c = 0; c < kTile; ++c) acc[r][c] = mk<R2>(0.0, 0.0);
-                        for (int c = 0; c < nb; ++c) {
-                            R2 av[kTile], bv[kTile];
+                            for (int k = 0; k < kTile; ++k) cfma(acc[r][k], av[r], bv[k]);
+                    }
+                    // add the S partial tiles (aligned lanes, fixed order)
+                    for (int o = S >> 1; o > 0; o >>= 1) {
+                        const unsigned m = 0xffffffffu;
 #pragma unroll
-                            for (int r = 0; r < kTile; ++r) av[r] = Y[(size_t)c * P + r0 + r];
-                            if (OPER_SMEM) {
+                        for (int r = 0; r < kTile; ++r)
 #pragma unroll
-                                for (int k = 0; k < kTile; ++k) bv[k] = EppT[(size_t)c * P + c0 + k];
-                            } else {
-                                const R2 *brow = epsT_all + ((size_t)qpp * nb + c) * nb;
-#pragma unroll
-                                for (int k = 0; k < kTile; ++k) {
-                                    R2 v = (c0 + k < nb) ? brow[c0 + k] : mk<R2>(0.0, 0.0);
-                                    v.y = -v.y;
-                                    bv[k] = v;
-                                }
+                            for (int c = 0; c < kTile; ++c) {
+                                acc[r][c].x += __shfl_xor_sync(m, acc[r][c].x, o);
+                                acc[r][c].y += __shfl_xor_sync(m, acc[r][c].y, o);
                             }
-#pragma unroll
-                            for (int r = 0; r < kTile; ++r)
-#pragma unroll
-                                for (int k = 0; k < kTile; ++k) cfma(acc[r][k], av[r], bv[k]);
-                        }
+                    }
+                    if (valid && ks == 0) {
 #pragma unroll
                         for (int r = 0; r < kTile; ++r) {
                             const R w1 = wp[r0 + r], n1 = np_[r0 + r];
@@ -387,6 +473,7 @@ size_t lw_smem_bytes(const LwParams &p, bool oper_smem) {
     b += sizeof(R) * 4 * P;
     b = (b + 15) & ~size_t(15);
     b += sizeof(double) * (kThreads / 32) * p.nb;
+    b += sizeof(int) * kThreads;
     return b + 16;
 }
 
