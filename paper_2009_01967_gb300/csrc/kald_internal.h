@@ -115,16 +115,16 @@ struct LwParams {
     int n_chunks;             // ceil(nq / qp_chunk)
 };
 // Y-build lane schedule (built on the host by plan_ybuild): in round r lane t
-// runs segments sched[r*256+t] .. sched[r*256+t+1]-1.  A segment is
+// runs segments sched[r*kLwThreads+t] .. sched[r*kLwThreads+t+1]-1.  A segment is
 // (group, first block, end block, red): the blocks of one (j, k) atom pair,
 // or a slice of them; red > 1 marks a slice whose partial sums are added
 // across `red` aligned lanes with shuffles (a "heavy" round: every lane has
 // exactly one segment, all with the same red); group < 0 is an empty slot.
-constexpr int kLwThreads = 256;
+constexpr int kLwThreads = 512;
 struct LwDev {
     const int *group_jk;      // [n_groups][2] atoms (j, k)
     const int4 *segs;         // [n_seg] (group, b0, b1, red)
-    const int *sched;         // [n_rounds * 256 + 1]
+    const int *sched;         // [n_rounds * kLwThreads + 1]
     const int4 *blkinfo;      // [n_fc3] (i, rep(Rj), rep(Rk), 0), schedule order
     const void *fc3;          // [n_fc3][28] float or double, Phi3 / sqrt(mi mj mk), padded
     const double *rep_cart;   // [n_rep][3]

@@ -41,8 +41,9 @@ template <> __device__ __forceinline__ double2 mk<double2>(double x, double y) {
     return make_double2(x, y);
 }
 
-constexpr int kThreads = 256;
-constexpr int kTile = 6;           // register tile edge (complex)
+constexpr int kThreads = kLwThreads;   // 512: 16 warps per SM
+constexpr int kTR = 6;                 // register tile: kTR rows (s') ...
+constexpr int kTC = 3;                 // ... by kTC columns (complex)
 
 // ---------------------------------------------------------------- prep kernels
 __global__ void mode_prep_kernel(int n, const double *__restrict__ nu, double omega_min_w,
@@ -123,15 +124,17 @@ __device__ __forceinline__ void load_blk(const double *f, double v[28]) {
 }
 
 // Shared memory layout (R2 = complex of the working precision; P = nb
-// rounded up to a multiple of kTile):
-//   Y    [P][P]     Y(b, c), then T'^T(c, s')
+// rounded up to a multiple of kTR, Q = P + 1):
+//   Y    [P][Q]     Y(b, c) at b*P + c, then T'^T(c, s') at c*Q + s' (odd
+//                   pitch: the transposed store walks distinct banks)
 //   EpT  [P][P]     eps(q')^T            (only when operands live in smem)
 //   EppT [P][P]     conj(eps(q''))^T     (only when operands live in smem)
 //   es   [P]        eps(q, s) column
 //   chip, chipp [n_rep]    chi(q'), chi(q'')
 //   wp, np_, wpp, npp [P]  omega and n of q' / q'' (R)
-//   red  [nwarps][nb] double   per-warp sums over the item's q'
-//   tiles [256] int  active (s', s'') tiles of the delta band
+//   red  [nb] double       per-mode sums over the item's q' (fixed order)
+//   wsum [nwarps] double   per-warp sums of the current mode
+//   tiles [kThreads] short active (s', s'') tiles of the delta band
 template <typename R, bool OPER_SMEM>
 __global__ void __launch_bounds__(kThreads, 1)
 lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
@@ -139,12 +142,14 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
                const typename C2<R>::T *__restrict__ chi_all) {
     using R2 = typename C2<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int nwarps = kThreads / 32;
     const int nb = p.nb;
-    const int P = ((nb + kTile - 1) / kTile) * kTile;
-    const int tpr = P / kTile;                       // tiles per row
-    const int n_tiles = tpr * tpr;                   // <= 256 for nb <= 96
+    const int P = ((nb + kTR - 1) / kTR) * kTR;
+    const int Q = P + 1;
+    const int tcols = P / kTC;                       // column tiles
+    const int n_tiles = (P / kTR) * tcols;           // <= 512 for nb <= 96
     R2 *Y = reinterpret_cast<R2 *>(smem_raw);
-    R2 *EpT = Y + (size_t)P * P;
+    R2 *EpT = Y + (size_t)P * Q;
     R2 *EppT = OPER_SMEM ? EpT + (size_t)P * P : EpT;
     R2 *es = OPER_SMEM ? EppT + (size_t)P * P : EpT;
     R2 *chip = es + P;
@@ -155,11 +160,11 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
     R *npp = wpp + P;
     double *red = reinterpret_cast<double *>(
         (reinterpret_cast<uintptr_t>(npp + P) + 15) & ~uintptr_t(15));
-    int *tiles = reinterpret_cast<int *>(red + (kThreads / 32) * nb);
-    __shared__ int item_sm, n_act_sm, warp_cnt[kThreads / 32];
+    double *wsum = red + nb;
+    short *tiles = reinterpret_cast<short *>(wsum + nwarps);
+    __shared__ int item_sm, n_act_sm, warp_cnt[nwarps];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nwarps = kThreads / 32;
     const R sig2inv = (R)(0.5 / (p.sigma_w * p.sigma_w));
     const R cut = (R)p.cut_w;
     const int n_items = p.nq * p.n_chunks;
@@ -173,7 +178,7 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
         if (item >= n_items) break;
         const int q = item / p.n_chunks;
         const int chunk = item % p.n_chunks;
-        for (int x = tid; x < nwarps * nb; x += kThreads) red[x] = 0.0;
+        for (int x = tid; x < nb; x += kThreads) red[x] = 0.0;
 
         const int qp0 = chunk * p.qp_chunk;
         const int qp1 = min(p.nq, qp0 + p.qp_chunk);
@@ -225,9 +230,9 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
                     const int g0 = d.sched[r * kThreads + tid], g1 = d.sched[r * kThreads + tid + 1];
                     for (int sg = g0; sg < g1; ++sg) {
                         const int4 seg = d.segs[sg];
-                        R2 acc[9];
+                        R2 acc9[9];
 #pragma unroll
-                        for (int x = 0; x < 9; ++x) acc[x] = mk<R2>(0.0, 0.0);
+                        for (int x = 0; x < 9; ++x) acc9[x] = mk<R2>(0.0, 0.0);
                         for (int bl = seg.y; bl < seg.z; ++bl) {
                             const int4 bi = __ldg(d.blkinfo + bl);
                             R v[28];
@@ -242,8 +247,8 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
                             const R2 e2 = cmul(es[3 * bi.x + 2], ph);
 #pragma unroll
                             for (int x = 0; x < 9; ++x) {
-                                acc[x].x = fma(v[x], e0.x, fma(v[9 + x], e1.x, fma(v[18 + x], e2.x, acc[x].x)));
-                                acc[x].y = fma(v[x], e0.y, fma(v[9 + x], e1.y, fma(v[18 + x], e2.y, acc[x].y)));
+                                acc9[x].x = fma(v[x], e0.x, fma(v[9 + x], e1.x, fma(v[18 + x], e2.x, acc9[x].x)));
+                                acc9[x].y = fma(v[x], e0.y, fma(v[9 + x], e1.y, fma(v[18 + x], e2.y, acc9[x].y)));
                             }
                         }
                         const int rr = seg.w;
@@ -251,43 +256,44 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
                             for (int o = rr >> 1; o > 0; o >>= 1)
 #pragma unroll
                                 for (int x = 0; x < 9; ++x) {
-                                    acc[x].x += __shfl_xor_sync(0xffffffffu, acc[x].x, o);
-                                    acc[x].y += __shfl_xor_sync(0xffffffffu, acc[x].y, o);
+                                    acc9[x].x += __shfl_xor_sync(0xffffffffu, acc9[x].x, o);
+                                    acc9[x].y += __shfl_xor_sync(0xffffffffu, acc9[x].y, o);
                                 }
                         }
                         if (seg.x >= 0 && (rr <= 1 || (lane & (rr - 1)) == 0)) {
                             const int j = d.group_jk[2 * seg.x], k = d.group_jk[2 * seg.x + 1];
 #pragma unroll
                             for (int x = 0; x < 9; ++x)
-                                Y[(size_t)(3 * j + x / 3) * P + 3 * k + x % 3] = acc[x];
+                                Y[(size_t)(3 * j + x / 3) * P + 3 * k + x % 3] = acc9[x];
                         }
                     }
                 }
                 __syncthreads();
 
-                // ---- GEMM1: T'(s', c) = sum_b epsT'(b, s') Y(b, c), dense
-                const int ti = tid / tpr, tj = tid % tpr;
+                // ---- GEMM1: T'(s', c) = sum_b epsT'(b, s') Y(b, c), dense.
+                // A warp holds one row tile (broadcast A) over 32 column tiles.
+                const int ti = tid / tcols, tj = tid % tcols;
                 const bool active = tid < n_tiles;
-                int r0 = ti * kTile, c0 = tj * kTile;
-                R2 acc[kTile][kTile];
+                int r0 = ti * kTR, c0 = tj * kTC;
+                R2 acc[kTR][kTC];
                 if (active) {
 #pragma unroll
-                    for (int r = 0; r < kTile; ++r)
+                    for (int r = 0; r < kTR; ++r)
 #pragma unroll
-                        for (int c = 0; c < kTile; ++c) acc[r][c] = mk<R2>(0.0, 0.0);
+                        for (int c = 0; c < kTC; ++c) acc[r][c] = mk<R2>(0.0, 0.0);
                     for (int b = 0; b < nb; ++b) {
-                        R2 av[kTile], bv[kTile];
+                        R2 av[kTR], bv[kTC];
                         const R2 *arow = OPER_SMEM ? EpT + (size_t)b * P
                                                    : epsT_all + ((size_t)qp * nb + b) * nb;
 #pragma unroll
-                        for (int r = 0; r < kTile; ++r)
+                        for (int r = 0; r < kTR; ++r)
                             av[r] = (OPER_SMEM || r0 + r < nb) ? arow[r0 + r] : mk<R2>(0.0, 0.0);
 #pragma unroll
-                        for (int c = 0; c < kTile; ++c) bv[c] = Y[(size_t)b * P + c0 + c];
+                        for (int c = 0; c < kTC; ++c) bv[c] = Y[(size_t)b * P + c0 + c];
 #pragma unroll
-                        for (int r = 0; r < kTile; ++r)
+                        for (int r = 0; r < kTR; ++r)
 #pragma unroll
-                            for (int c = 0; c < kTile; ++c) cfma(acc[r][c], av[r], bv[c]);
+                            for (int c = 0; c < kTC; ++c) cfma(acc[r][c], av[r], bv[c]);
                     }
                 }
                 // ---- delta band: list the (s', s'') tiles that can hold an allowed pair
@@ -295,10 +301,9 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
                 if (active) {
                     R wlo = (R)1e30, whi = (R)-1e30, xlo = (R)1e30, xhi = (R)-1e30;
 #pragma unroll
-                    for (int r = 0; r < kTile; ++r) {
-                        wlo = fmin(wlo, wp[r0 + r]); whi = fmax(whi, wp[r0 + r]);
-                        xlo = fmin(xlo, wpp[c0 + r]); xhi = fmax(xhi, wpp[c0 + r]);
-                    }
+                    for (int r = 0; r < kTR; ++r) { wlo = fmin(wlo, wp[r0 + r]); whi = fmax(whi, wp[r0 + r]); }
+#pragma unroll
+                    for (int c = 0; c < kTC; ++c) { xlo = fmin(xlo, wpp[c0 + c]); xhi = fmax(xhi, wpp[c0 + c]); }
                     // d+ = w + w' - w'' in [w + wlo - xhi, w + whi - xlo]
                     // d- = w - w' - w'' in [w - whi - xhi, w - wlo - xlo]
                     band = ((w + wlo - xhi < cut) && (w + whi - xlo > -cut)) ||
@@ -309,16 +314,16 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
                 __syncthreads();
                 if (active) {
 #pragma unroll
-                    for (int r = 0; r < kTile; ++r)
+                    for (int r = 0; r < kTR; ++r)
 #pragma unroll
-                        for (int c = 0; c < kTile; ++c)
-                            Y[(size_t)(c0 + c) * P + r0 + r] = acc[r][c];   // T'^T(c, s')
+                        for (int c = 0; c < kTC; ++c)
+                            Y[(size_t)(c0 + c) * Q + r0 + r] = acc[r][c];   // T'^T(c, s')
                 }
                 if (band) {
                     int off = 0;
                     for (int w8 = 0; w8 < warp; ++w8) off += warp_cnt[w8];
                     off += __popc(bal & ((1u << lane) - 1u));
-                    tiles[off] = tid;
+                    tiles[off] = (short)tid;
                 }
                 if (tid == 0) {
                     int t = 0;
@@ -341,54 +346,53 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
                     // whole warp); lanes past the list do no work
                     const int ti2 = base + tid / S;
                     const bool valid = ti2 < n_act;
-                    const int tt = valid ? tiles[ti2] : 0;
-                    r0 = (tt / tpr) * kTile;
-                    c0 = (tt % tpr) * kTile;
+                    const int tt = valid ? (int)tiles[ti2] : 0;
+                    r0 = (tt / tcols) * kTR;
+                    c0 = (tt % tcols) * kTC;
 #pragma unroll
-                    for (int r = 0; r < kTile; ++r)
+                    for (int r = 0; r < kTR; ++r)
 #pragma unroll
-                        for (int c = 0; c < kTile; ++c) acc[r][c] = mk<R2>(0.0, 0.0);
+                        for (int c = 0; c < kTC; ++c) acc[r][c] = mk<R2>(0.0, 0.0);
                     const int ke = valid ? kb1 : kb0;
                     for (int c = kb0; c < ke; ++c) {
-                        R2 av[kTile], bv[kTile];
+                        R2 av[kTR], bv[kTC];
 #pragma unroll
-                        for (int r = 0; r < kTile; ++r) av[r] = Y[(size_t)c * P + r0 + r];
+                        for (int r = 0; r < kTR; ++r) av[r] = Y[(size_t)c * Q + r0 + r];
                         if (OPER_SMEM) {
 #pragma unroll
-                            for (int k = 0; k < kTile; ++k) bv[k] = EppT[(size_t)c * P + c0 + k];
+                            for (int k = 0; k < kTC; ++k) bv[k] = EppT[(size_t)c * P + c0 + k];
                         } else {
                             const R2 *brow = epsT_all + ((size_t)qpp * nb + c) * nb;
 #pragma unroll
-                            for (int k = 0; k < kTile; ++k) {
+                            for (int k = 0; k < kTC; ++k) {
                                 R2 v = (c0 + k < nb) ? brow[c0 + k] : mk<R2>(0.0, 0.0);
                                 v.y = -v.y;
                                 bv[k] = v;
                             }
                         }
 #pragma unroll
-                        for (int r = 0; r < kTile; ++r)
+                        for (int r = 0; r < kTR; ++r)
 #pragma unroll
-                            for (int k = 0; k < kTile; ++k) cfma(acc[r][k], av[r], bv[k]);
+                            for (int k = 0; k < kTC; ++k) cfma(acc[r][k], av[r], bv[k]);
                     }
                     // add the S partial tiles (aligned lanes, fixed order)
                     for (int o = S >> 1; o > 0; o >>= 1) {
-                        const unsigned m = 0xffffffffu;
 #pragma unroll
-                        for (int r = 0; r < kTile; ++r)
+                        for (int r = 0; r < kTR; ++r)
 #pragma unroll
-                            for (int c = 0; c < kTile; ++c) {
-                                acc[r][c].x += __shfl_xor_sync(m, acc[r][c].x, o);
-                                acc[r][c].y += __shfl_xor_sync(m, acc[r][c].y, o);
+                            for (int c = 0; c < kTC; ++c) {
+                                acc[r][c].x += __shfl_xor_sync(0xffffffffu, acc[r][c].x, o);
+                                acc[r][c].y += __shfl_xor_sync(0xffffffffu, acc[r][c].y, o);
                             }
                     }
                     if (valid && ks == 0) {
 #pragma unroll
-                        for (int r = 0; r < kTile; ++r) {
+                        for (int r = 0; r < kTR; ++r) {
                             const R w1 = wp[r0 + r], n1 = np_[r0 + r];
                             if (w1 <= (R)0) continue;
                             const R iw1 = (R)1 / w1;
 #pragma unroll
-                            for (int c = 0; c < kTile; ++c) {
+                            for (int c = 0; c < kTC; ++c) {
                                 const R w2 = wpp[c0 + c];
                                 if (w2 <= (R)0) continue;
                                 const R n2 = npp[c0 + c];
@@ -407,19 +411,21 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
                         }
                     }
                 }
-                // per-warp sum into red[warp][s] (fixed order across q')
+                // block sum of this mode, added to red[s] in a fixed order
                 double pd = (double)part;
                 for (int o = 16; o > 0; o >>= 1) pd += __shfl_xor_sync(0xffffffffu, pd, o);
-                if (lane == 0) red[warp * nb + s] += pd;
+                if (lane == 0) wsum[warp] = pd;
                 __syncthreads();
+                if (tid == 0) {
+                    double t = 0.0;
+                    for (int w8 = 0; w8 < nwarps; ++w8) t += wsum[w8];
+                    red[s] += t;
+                }
             }
         }
         __syncthreads();
-        for (int s = tid; s < nb; s += kThreads) {
-            double t = 0.0;
-            for (int w8 = 0; w8 < nwarps; ++w8) t += red[w8 * nb + s];
-            d.partial[((size_t)q * p.n_chunks + chunk) * nb + s] = t;
-        }
+        for (int s = tid; s < nb; s += kThreads)
+            d.partial[((size_t)q * p.n_chunks + chunk) * nb + s] = red[s];
         __syncthreads();
     }
     // delta-allowed triplet count
@@ -467,13 +473,14 @@ __global__ void lw_finish_kernel(int nq, int nb, int n_chunks, const double *__r
 template <typename R>
 size_t lw_smem_bytes(const LwParams &p, bool oper_smem) {
     using R2 = typename C2<R>::T;
-    const int P = ((p.nb + kTile - 1) / kTile) * kTile;
-    size_t b = sizeof(R2) * (size_t)P * P * (oper_smem ? 3 : 1);
+    const int P = ((p.nb + kTR - 1) / kTR) * kTR;
+    size_t b = sizeof(R2) * (size_t)P * (P + 1);
+    if (oper_smem) b += 2 * sizeof(R2) * (size_t)P * P;
     b += sizeof(R2) * (P + 2 * p.n_rep);
     b += sizeof(R) * 4 * P;
     b = (b + 15) & ~size_t(15);
-    b += sizeof(double) * (kThreads / 32) * p.nb;
-    b += sizeof(int) * kThreads;
+    b += sizeof(double) * (p.nb + kThreads / 32);
+    b += sizeof(short) * kThreads;
     return b + 16;
 }
 
