@@ -170,6 +170,31 @@ kald_status kald_kappa_qhgk(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
                             const double *nu_thz, const double *eigvec, const double *gamma,
                             const kald_options *opt, double *kappa, double *vgen);
 
+/* kald_kappa_rta for callers that cannot allocate device memory.  The paper
+ * has no counterpart: this is an interface addition, not part of the method.
+ * Some callers cannot call cudaMalloc -- an application whose device memory
+ * is all owned by another runtime's pool, or a latency-critical loop where a
+ * device allocation (which may synchronise the device) is not allowed.  This
+ * call returns the same kappa as kald_kappa_rta but keeps its scratch (the
+ * force-constant tables, the q-points and the per-q partial sums) in one
+ * static device array of 4 MiB, present on every GPU that loads the library
+ * until the process exits; it calls no cudaMalloc or cudaFree.
+ *   ctx     may be NULL; if given, its device is made current, its stream is
+ *           used when `stream` is NULL, and failures are described by
+ *           kald_last_error(ctx)
+ *   stream  cudaStream_t to run on, or NULL (then ctx's stream, or the
+ *           default stream without ctx); the call synchronises it
+ *   nu_thz, eigvec, gamma, kappa   DEVICE pointers (as for kald_kappa_rta)
+ * The first call on a device looks up the array's device address and caches
+ * it; make that first call before any stream capture.  Calls share the one
+ * array, so calls that overlap on the GPU race.  A system and mesh whose
+ * scratch exceeds 4 MiB (roughly 48 KB per 1000 q-points plus 96 bytes per
+ * fc2 block) is rejected with KALD_E_INVALID. */
+kald_status kald_kappa_rta_noalloc(kald_ctx *ctx, void *stream, const kald_system *sys,
+                                   const int32_t mesh[3], const double *nu_thz,
+                                   const double *eigvec, const double *gamma,
+                                   const kald_options *opt, double *kappa);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,7 +24,8 @@ STATUS = {0: "KALD_OK", 1: "KALD_E_INVALID", 2: "KALD_E_NOMEM", 3: "KALD_E_CUDA"
 PRECISION = {"fp64": 0, "fp32": 1}
 
 EXPORTS = ["kald_ctx_create", "kald_ctx_destroy", "kald_last_error", "kald_set_stream",
-           "kald_phonons", "kald_linewidths", "kald_kappa_rta", "kald_kappa_qhgk"]
+           "kald_phonons", "kald_linewidths", "kald_kappa_rta", "kald_kappa_qhgk",
+           "kald_kappa_rta_noalloc"]
 
 
 class KaldError(RuntimeError):
@@ -77,6 +78,9 @@ def load_library(path: str = LIB_PATH):
     lib.kald_kappa_qhgk.argtypes = [vp, i32, C.POINTER(kald_system), vp, vp, vp,
                                     C.POINTER(kald_options), vp, vp]
     lib.kald_kappa_qhgk.restype = st
+    lib.kald_kappa_rta_noalloc.argtypes = [vp, vp, C.POINTER(kald_system), C.POINTER(i32), vp, vp, vp,
+                                           C.POINTER(kald_options), vp]
+    lib.kald_kappa_rta_noalloc.restype = st
     _lib = lib
     return lib
 
@@ -267,3 +271,24 @@ def kald_kappa_qhgk(ctx: Context, systems, nu_thz, eigvec, gamma, options: Optio
                                       _ptr(vgen, np.float64, 3 * nbs[0] * nbs[0], "vgen")))
     del keep
     return kappa, vgen
+
+
+def kald_kappa_rta_noalloc(ctx: Context | None, system, mesh, nu_thz, eigvec, gamma, options: Options,
+                           kappa, stream_ptr: int | None = None):
+    """kald_kappa_rta without any device allocation (static scratch inside the
+    library); every array argument must be a CUDA tensor on the device."""
+    lib = ctx.lib if ctx is not None else load_library()
+    cs, keep = c_system(system)
+    m, nq = _mesh(mesh)
+    nb = 3 * cs.n_atoms
+    opt = options.c()
+    status = lib.kald_kappa_rta_noalloc(ctx.handle if ctx is not None else None, stream_ptr, C.byref(cs), m,
+                                        _ptr(nu_thz, np.float64, nq * nb, "nu_thz"),
+                                        _ptr(eigvec, np.complex128, nq * nb * nb, "eigvec"),
+                                        _ptr(gamma, np.float64, nq * nb, "gamma"), C.byref(opt),
+                                        _ptr(kappa, np.float64, 9, "kappa"))
+    del keep
+    if status != KALD_OK:
+        msg = lib.kald_last_error(ctx.handle).decode() if ctx is not None else ""
+        raise KaldError(status, msg or "kald_kappa_rta_noalloc failed")
+    return kappa
