@@ -117,8 +117,10 @@ kald_status kald_set_stream(kald_ctx *ctx, void *stream);
  *   eigvec  [Nq][nb][nb][2] out, complex128, row s = eigenvector of mode s,
  *           unit norm (interleaved re, im)
  *   vel     [Nq][nb][3] out (A/ps), or NULL
- * This build diagonalises nb <= 96 (KALD_E_UNSUPPORTED above).
- * KALD_E_NOCONV if the Jacobi sweeps do not converge. */
+ * nb <= 96: one parallel Jacobi eigensolver per q (KALD_E_NOCONV if the
+ * sweeps do not converge).  nb > 96 is supported at Gamma only (mesh
+ * {1,1,1}; KALD_E_UNSUPPORTED otherwise): Householder tridiagonalisation,
+ * bisection, inverse iteration, back-transformation, all FP64. */
 kald_status kald_phonons(kald_ctx *ctx, const kald_system *sys, const int32_t mesh[3],
                          double *nu_thz, double *eigvec, double *vel);
 
@@ -139,7 +141,8 @@ kald_status kald_phonons(kald_ctx *ctx, const kald_system *sys, const int32_t me
  *   gamma   [sum over systems of Nq*nb] out
  *   n_triplets [2] out or NULL: momentum-conserving triplets Nq^2 nb^3, and
  *           those with a non-zero delta weight
- * This build supports nb <= 96 per system. */
+ * nb <= 96: persistent (q, q') kernel; nb > 96 (mesh {1,1,1} only): mode by
+ * mode, phi_mu = E Y_mu E^T with Y_mu = sum_a E[mu][a] Phi3(a, ., .). */
 kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys,
                             const int32_t mesh[3], const double *nu_thz, const double *eigvec,
                             const kald_options *opt, double *gamma, uint64_t *n_triplets);

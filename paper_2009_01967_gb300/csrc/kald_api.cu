@@ -356,8 +356,9 @@ kald_status kald_phonons(kald_ctx *ctx, const kald_system *sys, const int32_t me
     HostSystem h;
     if ((st = plan_system(ctx, sys, h))) return st;
     const int nb = h.nb;
-    if (nb > kMaxNbSmall)
-        return fail(ctx, KALD_E_UNSUPPORTED, "kald_phonons: this build diagonalises nb <= 96");
+    const bool large = nb > kMaxNbSmall;
+    if (large && (mesh[0] != 1 || mesh[1] != 1 || mesh[2] != 1))
+        return fail(ctx, KALD_E_UNSUPPORTED, "kald_phonons: nb > 96 is diagonalised at Gamma only (mesh {1,1,1})");
     std::vector<double> qc;
     std::vector<int> qf;
     mesh_points(h.lattice, mesh, qc, qf);
@@ -366,6 +367,7 @@ kald_status kald_phonons(kald_ctx *ctx, const kald_system *sys, const int32_t me
     const bool d_nu = is_device_ptr(nu_thz), d_eig = is_device_ptr(eigvec);
     const bool d_vel = vel && is_device_ptr(vel);
     size_t need = fc2_bytes(h) + bytes_of(qc) + 2 * ws_round(sizeof(double2) * nn) + ws_round(sizeof(int));
+    if (large) need += eigh_large_scratch_bytes(nb);
     if (!d_nu) need += ws_round(sizeof(double) * nq * nb);
     if (!d_eig) need += ws_round(sizeof(double2) * nn);
     if (vel && !d_vel) need += ws_round(sizeof(double) * 3 * nq * nb);
@@ -382,9 +384,13 @@ kald_status kald_phonons(kald_ctx *ctx, const kald_system *sys, const int32_t me
     double *vel_d = nullptr;
     if (vel) vel_d = d_vel ? vel : static_cast<double *>(ws_take(ctx, sizeof(double) * 3 * nq * nb));
     cudaStream_t s = ctx->stream;
+    double *big = large ? static_cast<double *>(ws_take(ctx, eigh_large_scratch_bytes(nb))) : nullptr;
     cudaMemsetAsync(nonconv, 0, sizeof(int), s);
     cudaError_t e = launch_dynmat(dev_fc2(h, d), nb, nq, qcart, D, s);
-    if (e == cudaSuccess) e = launch_jacobi(nb, nq, D, V, nu_d, eig_d, nonconv, ctx->smem_optin, s);
+    if (e == cudaSuccess) {
+        if (large) e = launch_eigh_large(nb, D, big, nu_d, eig_d, s);
+        else e = launch_jacobi(nb, nq, D, V, nu_d, eig_d, nonconv, ctx->smem_optin, s);
+    }
     if (e == cudaSuccess && vel) e = launch_velocity_diag(dev_fc2(h, d), nb, nq, qcart, nu_d, eig_d, vel_d, s);
     if (e != cudaSuccess) return cuda_check(ctx, e, "kald_phonons launch");
     int nc = 0;
@@ -433,8 +439,71 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
         HostSystem h;
         if ((st = plan_system(ctx, &sys[x], h))) return st;
         const int nb = h.nb;
-        if (nb > kMaxNbSmall)
-            return fail(ctx, KALD_E_UNSUPPORTED, "kald_linewidths: this build supports nb <= 96");
+        if (nb > kMaxNbSmall && nq_mesh != 1)
+            return fail(ctx, KALD_E_UNSUPPORTED, "kald_linewidths: nb > 96 needs mesh {1,1,1}");
+        if (nb > kMaxNbSmall) {
+            // ---- Gamma-only path, mode by mode
+            const size_t nn = (size_t)nb * nb;
+            GammaPlan gp;
+            gp.n_groups = (int)h.pair3_j.size();
+            gp.n_part = std::max(1, 2 * ctx->sm_count);
+            std::vector<double> nu_h(nb);
+            if (d_nu) cudaMemcpy(nu_h.data(), nu_thz + off_nb, sizeof(double) * nb, cudaMemcpyDeviceToHost);
+            else std::copy(nu_thz + off_nb, nu_thz + off_nb + nb, nu_h.begin());
+            gp.omega_h.resize(nb);
+            for (int m = 0; m < nb; ++m) {
+                const double w = kTwoPi * nu_h[m];
+                gp.omega_h[m] = (std::isfinite(w) && w > kTwoPi * opt->omega_min_thz) ? w : 0.0;
+            }
+            std::vector<int> gjk(2 * (size_t)gp.n_groups);
+            for (int g = 0; g < gp.n_groups; ++g) { gjk[2 * g] = h.pair3_j[g]; gjk[2 * g + 1] = h.pair3_k[g]; }
+            const size_t rs = fp32 ? sizeof(float) : sizeof(double);
+            size_t need = bytes_of(gjk) + bytes_of(h.pair3_start) + bytes_of(h.fc3_i) + bytes_of(h.fc3_scaled) +
+                          4 * ws_round(rs * nn) + 2 * ws_round(sizeof(double) * nb) +
+                          ws_round(sizeof(double) * nb * (size_t)gp.n_part) + ws_round(sizeof(int) * nb) +
+                          ws_round(16);
+            if (!d_nu) need += ws_round(sizeof(double) * nb);
+            if (!d_eig) need += ws_round(sizeof(double2) * nn);
+            if (!d_g) need += ws_round(sizeof(double) * nb);
+            if ((st = ws_reserve(ctx, need))) return st;
+            GammaDev gd;
+            gd.group_jk = upload(ctx, gjk);
+            gd.group_start = upload(ctx, h.pair3_start);
+            gd.blk_i = upload(ctx, h.fc3_i);
+            gd.fc3 = upload(ctx, h.fc3_scaled);
+            gd.nu = stage_in(ctx, nu_thz + off_nb, (size_t)nb, d_nu);
+            gd.eig = stage_in(ctx, reinterpret_cast<const double2 *>(eigvec) + off_eig, nn, d_eig);
+            gd.omega = static_cast<double *>(ws_take(ctx, sizeof(double) * nb));
+            gd.occ = static_cast<double *>(ws_take(ctx, sizeof(double) * nb));
+            gd.E = ws_take(ctx, rs * nn);
+            gd.Y = ws_take(ctx, rs * nn);
+            gd.T = ws_take(ctx, rs * nn);
+            gd.PHI = ws_take(ctx, rs * nn);
+            gd.partial = static_cast<double *>(ws_take(ctx, sizeof(double) * nb * (size_t)gp.n_part));
+            gd.order = static_cast<int *>(ws_take(ctx, sizeof(int) * nb));
+            gd.allowed = static_cast<unsigned long long *>(ws_take(ctx, 16));
+            double *g_d = d_g ? gamma + off_nb : static_cast<double *>(ws_take(ctx, sizeof(double) * nb));
+            LwParams p;
+            p.nb = nb; p.nq = 1;
+            p.mesh[0] = p.mesh[1] = p.mesh[2] = 1;
+            p.n_rep = 0; p.n_rounds = 0; p.qp_chunk = 1; p.n_chunks = 1;
+            p.sigma_w = kTwoPi * opt->sigma_thz;
+            p.cut_w = opt->n_sigma * p.sigma_w;
+            p.T = opt->temperature_K;
+            p.classical = opt->classical ? 1 : 0;
+            p.omega_min_w = kTwoPi * opt->omega_min_thz;
+            cudaError_t e = launch_gamma_only(gp, gd, p, fp32, opt->degen_tol_thz, g_d, ctx->stream);
+            if (e != cudaSuccess) return cuda_check(ctx, e, "kald_linewidths (Gamma-only) launch");
+            unsigned long long al = 0;
+            cudaMemcpyAsync(&al, gd.allowed, sizeof(al), cudaMemcpyDeviceToHost, ctx->stream);
+            if (!d_g) cudaMemcpyAsync(gamma + off_nb, g_d, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->stream);
+            if ((st = finish(ctx, "kald_linewidths"))) return st;
+            tot += (uint64_t)nb * nb * nb;
+            allowed_tot += al;
+            off_nb += nb;
+            off_eig += nn;
+            continue;
+        }
         std::vector<double> qc;
         std::vector<int> qf;
         mesh_points(h.lattice, mesh, qc, qf);

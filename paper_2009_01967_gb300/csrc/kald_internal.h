@@ -97,6 +97,10 @@ cudaError_t launch_dynmat(const DevFc2 &f, int nb, int nq, const double *qcart,
                           double2 *D, cudaStream_t st);
 cudaError_t launch_jacobi(int nb, int nq, double2 *A, double2 *V, double *nu_thz,
                           double2 *eig_out, int *nonconv, size_t smem_optin, cudaStream_t st);
+// eigh_large.cu: one real symmetric matrix of any size (the Gamma-only D)
+size_t eigh_large_scratch_bytes(int n);
+cudaError_t launch_eigh_large(int n, const double2 *D, double *scratch, double *nu_out,
+                              double2 *eig_out, cudaStream_t st);
 cudaError_t launch_velocity_diag(const DevFc2 &f, int nb, int nq, const double *qcart,
                                  const double *nu_thz, const double2 *eig, double *vel,
                                  cudaStream_t st);
@@ -155,6 +159,29 @@ cudaError_t launch_lw_main(const LwParams &p, const LwDev &d, int fp32, int sm_c
                            size_t smem_optin, cudaStream_t st);
 cudaError_t launch_lw_finish(const LwParams &p, const LwDev &d, double degen_tol_thz,
                              double *gamma_out, cudaStream_t st);
+
+cudaError_t launch_mode_prep(int n, const double *nu, double omega_min_w, double T, int classical,
+                             double *omega, double *occ, cudaStream_t st);
+
+// gamma_only.cu: Gamma-only linewidths of a system with nb > kMaxNbSmall
+struct GammaPlan {
+    int n_groups = 0;
+    int n_part = 0;                  // epilogue CTAs (partial sums) per mode
+    std::vector<double> omega_h;     // [nb] rad/ps, 0 for a masked mode
+};
+struct GammaDev {
+    const int *group_jk, *group_start, *blk_i;   // (j, k) groups of fc3 blocks
+    const double *fc3;               // [n_fc3][27] Phi3 / sqrt(mi mj mk)
+    const double2 *eig;              // [nb][nb] (real parts used)
+    const double *nu;                // [nb] THz
+    double *omega, *occ;             // [nb]
+    void *E, *Y, *T, *PHI;           // [nb][nb] in the working precision
+    double *partial;                 // [nb][n_part]
+    int *order;                      // [nb]
+    unsigned long long *allowed;
+};
+cudaError_t launch_gamma_only(const GammaPlan &gp, const GammaDev &d, const LwParams &p, int fp32,
+                              double degen_tol_thz, double *gamma_out, cudaStream_t st);
 
 // kappa.cu
 cudaError_t launch_kappa_rta(const DevFc2 &f, int nb, int nq, const double *qcart,

@@ -486,6 +486,12 @@ size_t lw_smem_bytes(const LwParams &p, bool oper_smem) {
 
 }  // namespace
 
+cudaError_t launch_mode_prep(int n, const double *nu, double omega_min_w, double T, int classical,
+                             double *omega, double *occ, cudaStream_t st) {
+    mode_prep_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, nu, omega_min_w, T, classical, omega, occ);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_lw_prep(const LwParams &p, const LwDev &d, int fp32, cudaStream_t st) {
     const int n = p.nq * p.nb;
     mode_prep_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, d.nu, p.omega_min_w, p.T, p.classical,

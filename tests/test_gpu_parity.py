@@ -243,5 +243,52 @@ def test_invalid_inputs_are_rejected(k):
     assert e.value.status == 1
     big = ki.fcc_supercell_system(3, seed=1)        # 108 atoms: nb = 324 > 96
     with pytest.raises(kk.KaldError) as e:
-        kk.kald_phonons(ctx, big, (1, 1, 1))
+        kk.kald_phonons(ctx, big, (2, 1, 1))         # large cells only at Gamma
     assert e.value.status == 6
+
+
+# ---------------------------------------------------------------- large Gamma-only cells
+@pytest.fixture(scope="module")
+def big324():
+    """108-atom (324-mode) disordered supercell, the smallest of the batched
+    Gamma-only workload (heavy fraction 0.3, seed 1000)."""
+    s = ki.fcc_supercell_system(3, seed=1000, heavy_fraction=0.3)
+    nu_o, eig_o = ph.phonons(s, (1, 1, 1))
+    g_o = an.linewidths_gamma_only(s, nu_o, eig_o, 300.0, 0.05)
+    return s, nu_o, eig_o, g_o
+
+
+def test_large_gamma_phonons_match_oracle(k, big324):
+    kk, ctx = k
+    s, nu_o, eig_o, _ = big324
+    nu, eig, _ = kk.kald_phonons(ctx, s, (1, 1, 1), want_vel=False)
+    sq = lambda x: np.sign(x) * x * x
+    np.testing.assert_allclose(sq(nu), sq(nu_o), atol=1e-11 * np.max(nu_o) ** 2)
+    assert np.abs(eig.imag).max() == 0.0
+    E = eig[0].real.T
+    np.testing.assert_allclose(E.T @ E, np.eye(E.shape[0]), atol=1e-11)
+    D = ph.dynamical_matrix(s, np.zeros(3)).real
+    res = D @ E - E * np.diag(E.T @ D @ E)[None, :]
+    assert np.abs(res).max() < 1e-11 * np.abs(D).max()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_large_gamma_linewidths_match_oracle(k, big324, precision, tol):
+    kk, ctx = k
+    s, nu_o, eig_o, g_o = big324
+    w = ki.Workload("g324", [s], (1, 1, 1), 300.0, 0.05, 3.0)
+    g, (tot, allowed) = kk.kald_linewidths(ctx, s, (1, 1, 1), nu_o, eig_o, _opts(kk, w, precision))
+    assert tot == 324 ** 3 and 0 < allowed < tot
+    assert _rel(g, g_o, 1e-6 * g_o.max()) < tol
+
+
+def test_large_gamma_end_to_end_qhgk(k, big324):
+    kk, ctx = k
+    s, nu_o, eig_o, g_o = big324
+    w = ki.Workload("g324", [s], (1, 1, 1), 300.0, 0.05, 3.0)
+    nu, eig, _ = kk.kald_phonons(ctx, s, (1, 1, 1), want_vel=False)
+    g, _ = kk.kald_linewidths(ctx, s, (1, 1, 1), nu, eig, _opts(kk, w))
+    kap, _ = kk.kald_kappa_qhgk(ctx, [s], nu, eig, g, _opts(kk, w))
+    kap_o = co.kappa_qhgk(s, nu_o, eig_o, g_o, 300.0)
+    assert _rel(g, g_o, 1e-6 * g_o.max()) < 1e-8        # gauge-free after degenerate averaging
+    np.testing.assert_allclose(kap[0], kap_o, rtol=1e-8, atol=1e-10 * np.abs(kap_o).max())
