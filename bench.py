@@ -33,7 +33,7 @@ import kald_inputs as ki  # noqa: E402
 
 METRIC = "3-phonon triplets/sec (kappa time-to-solution path)"
 UNIT = "triplets/s"
-WORKLOADS = {"C1": ki.c1, "C2": ki.c2, "C5": ki.c5}
+WORKLOADS = {"C1": ki.c1, "C2": ki.c2, "C3": ki.c3, "C4": ki.c4, "C5": ki.c5}
 
 
 def _peaks():
@@ -110,19 +110,29 @@ def dist_env():
 
 
 # ------------------------------------------------------------- oracle timing
-def time_oracle_sample(w, n_q: int = 1):
-    """Oracle linewidths of n_q q-points of the workload (all q', both
-    processes), plus the phonons they need; returns (triplets/s, seconds, sample)."""
+def time_oracle_sample(w, n_q: int = 1, n_modes: int = 4):
+    """Oracle on a bounded sample of the workload: for a crystal, phonons on
+    the full mesh + linewidths of n_q q-points (all q', both processes); for a
+    Gamma-only system, its phonons + the linewidths of n_modes modes.
+    Returns (triplets/s, seconds, description)."""
     from oracle import anharmonic as an
     from oracle import phonons as ph
     s = w.systems[0]
     t0 = time.perf_counter()
     nu, eig = ph.phonons(s, w.mesh)
-    qs = list(range(1, 1 + n_q))
-    an.linewidths(s, w.mesh, nu, eig, w.T, w.sigma_thz, w.n_sigma, q_list=qs)
+    if w.n_q == 1:
+        nb = s.n_branches
+        modes = list(range(nb // 2, nb // 2 + n_modes))
+        an.linewidths_gamma_only(s, nu, eig, w.T, w.sigma_thz, w.n_sigma, modes=modes)
+        trip = n_modes * nb * nb
+        what = f"phonons of system 0 + linewidths of {n_modes} modes ({trip} triplets)"
+    else:
+        qs = list(range(1, 1 + n_q))
+        an.linewidths(s, w.mesh, nu, eig, w.T, w.sigma_thz, w.n_sigma, q_list=qs)
+        trip = n_q * w.n_q * s.n_branches ** 3
+        what = f"phonons on the full mesh + linewidths of {n_q} q-point(s) x all q' ({trip} triplets)"
     dt = time.perf_counter() - t0
-    trip = n_q * w.n_q * s.n_branches ** 3
-    return trip / dt, dt, f"phonons on the full mesh + linewidths of {n_q} q-point(s) x all q' ({trip} triplets)"
+    return trip / dt, dt, what
 
 
 def run_reference(args):
@@ -167,28 +177,46 @@ def run_kald(args):
     w = WORKLOADS[args.workload]()
     if args.mesh:
         w.mesh = tuple(int(x) for x in args.mesh.split(","))
+    gamma_only = w.n_q == 1
     s = w.systems[0]
-    nq, nb = w.n_q, s.n_branches
+    nq = w.n_q
+    nbs = [x.n_branches for x in w.systems]
+    nb = nbs[0]
     opt = kk.Options(temperature_K=w.T, sigma_thz=w.sigma_thz, n_sigma=w.n_sigma,
                      precision=args.precision)
     ctx = kk.Context(local)
     stream = torch.cuda.current_stream(dev)
     ctx.set_stream(stream.cuda_stream)
-    nu = torch.zeros((nq, nb), dtype=torch.float64, device=dev)
-    eig = torch.zeros((nq, nb, nb), dtype=torch.complex128, device=dev)
-    gam = torch.zeros(nq * nb, dtype=torch.float64, device=dev)
-    kap = torch.zeros((3, 3), dtype=torch.float64, device=dev)
+    n_modes = sum(nq * b for b in nbs)
+    n_eig = sum(nq * b * b for b in nbs)
+    nu = torch.zeros(n_modes, dtype=torch.float64, device=dev)
+    eig = torch.zeros(n_eig, dtype=torch.complex128, device=dev)
+    gam = torch.zeros(n_modes, dtype=torch.float64, device=dev)
+    kap = torch.zeros((len(nbs), 3, 3), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     trip_info = {}
+    offs_m = np.cumsum([0] + [nq * b for b in nbs])
+    offs_e = np.cumsum([0] + [nq * b * b for b in nbs])
+
+    def phon(nu_t, eig_t):
+        for x, sx in enumerate(w.systems):
+            kk.kald_phonons(ctx, sx, w.mesh, nu_thz=nu_t[offs_m[x]:offs_m[x + 1]],
+                            eigvec=eig_t[offs_e[x]:offs_e[x + 1]], want_vel=False)
+
+    def kappa(nu_t, eig_t, gam_t, kap_t):
+        if gamma_only:
+            kk.kald_kappa_qhgk(ctx, w.systems, nu_t, eig_t, gam_t, opt, kappa=kap_t)
+        else:
+            kk.kald_kappa_rta(ctx, s, w.mesh, nu_t, eig_t, gam_t, opt, kappa=kap_t[0])
 
     def step():
-        kk.kald_phonons(ctx, s, w.mesh, nu_thz=nu, eigvec=eig, want_vel=False)
+        phon(nu, eig)
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        _, trip = kk.kald_linewidths(ctx, s, w.mesh, nu, eig, opt, gamma=gam)
+        _, trip = kk.kald_linewidths(ctx, w.systems, w.mesh, nu, eig, opt, gamma=gam)
         ev1.record(stream)
-        kk.kald_kappa_rta(ctx, s, w.mesh, nu, eig, gam, opt, kappa=kap)
+        kappa(nu, eig, gam, kap)
         trip_info["trip"] = trip
         return ev0, ev1
 
@@ -221,24 +249,24 @@ def run_kald(args):
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    triplets_step = nq * nq * nb ** 3
+    triplets_step = sum(nq * nq * b ** 3 for b in nbs)
     value = world * triplets_step * args.steps / (total_ms / 1e3)
 
     # ---- end to end through host buffers (pinned), same calls
-    nu_h = torch.zeros((nq, nb), dtype=torch.float64).pin_memory().numpy()
-    eig_h = torch.zeros((nq, nb, nb), dtype=torch.complex128).pin_memory().numpy()
-    gam_h = torch.zeros(nq * nb, dtype=torch.float64).pin_memory().numpy()
-    kap_h = np.zeros((3, 3))
-    sys_bytes = (s.masses.nbytes + s.positions.nbytes + s.fc2_idx.nbytes + s.fc2.nbytes +
-                 s.fc3_idx.nbytes + s.fc3.nbytes)
+    nu_h = torch.zeros(n_modes, dtype=torch.float64).pin_memory().numpy()
+    eig_h = torch.zeros(n_eig, dtype=torch.complex128).pin_memory().numpy()
+    gam_h = torch.zeros(n_modes, dtype=torch.float64).pin_memory().numpy()
+    kap_h = np.zeros((len(nbs), 3, 3))
+    sys_bytes = sum(x.masses.nbytes + x.positions.nbytes + x.fc2_idx.nbytes + x.fc2.nbytes +
+                    x.fc3_idx.nbytes + x.fc3.nbytes for x in w.systems)
     e2e_ms = []
     for it in range(0 if args.no_e2e else max(1, min(args.steps, 3))):
         flush.fill_(2.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        kk.kald_phonons(ctx, s, w.mesh, nu_thz=nu_h, eigvec=eig_h, want_vel=False)
-        kk.kald_linewidths(ctx, s, w.mesh, nu_h, eig_h, opt, gamma=gam_h)
-        kk.kald_kappa_rta(ctx, s, w.mesh, nu_h, eig_h, gam_h, opt, kappa=kap_h)
+        phon(nu_h, eig_h)
+        kk.kald_linewidths(ctx, w.systems, w.mesh, nu_h, eig_h, opt, gamma=gam_h)
+        kappa(nu_h, eig_h, gam_h, kap_h)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     h2d = 3 * sys_bytes + 2 * (nu_h.nbytes + eig_h.nbytes) + gam_h.nbytes
     d2h = nu_h.nbytes + eig_h.nbytes + gam_h.nbytes + kap_h.nbytes
@@ -246,21 +274,29 @@ def run_kald(args):
 
     # ---- roofline of the dominant kernel (linewidth projection)
     trip, allowed = trip_info["trip"]
-    n_valid = int(torch.sum(nu > opt.omega_min_thz).item())
-    n_fc3 = s.fc3.shape[0]
-    flops = (n_valid * nq * (20.0 * n_fc3 + 8.0 * nb ** 3)     # Y build + T' = eps'^T Y
-             + allowed * 8.0 * nb)                              # phi at delta-allowed pairs
-    lw_avg_s = float(np.mean(lw_ms)) / 1e3
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, FMA = 2 flops
-    if args.precision == "fp64":
-        fp32_peak = fp32_peak / 64.0
+    lw_avg_s = float(np.mean(lw_ms)) / 1e3
+    if gamma_only:
+        # per valid mode: two dense nb^3 contractions (E Y, then (E Y) E^T), 2 flop per FMA
+        nu_c = nu.cpu().numpy()
+        flops = sum(4.0 * b ** 3 * int(np.sum(nu_c[offs_m[x]:offs_m[x + 1]] > opt.omega_min_thz))
+                    for x, b in enumerate(nbs))
+        kernel = "g_gemm_nt_kernel"
+    else:
+        n_valid = int(torch.sum(nu > opt.omega_min_thz).item())
+        n_fc3 = s.fc3.shape[0]
+        flops = (n_valid * nq * (20.0 * n_fc3 + 8.0 * nb ** 3)     # Y build + T' = eps'^T Y
+                 + allowed * 8.0 * nb)                              # phi at delta-allowed pairs
+        kernel = "lw_main_kernel"
+    peak = fp32_peak if args.precision == "fp32" else fp32_peak / 64.0
     achieved = flops / lw_avg_s / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": None,
-                "kernel": "lw_main_kernel", "flops_per_launch": flops,
-                "peak_note": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz"}
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": kernel, "flops_per_launch": flops,
+                "peak_note": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz" +
+                             ("" if args.precision == "fp32" else " / 64 (FP64)")}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, sample = time_oracle_sample(w)
@@ -281,7 +317,7 @@ def run_kald(args):
                         "d2h_bytes_per_step": int(d2h)},
                 "gpu_launches": 9 * args.steps,     # dynmat, jacobi, 5 linewidth, 2 kappa kernels
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
-                "kappa_W_mK": kap.cpu().numpy().round(6).tolist(),
+                "kappa_W_mK": kap.cpu().numpy().round(6).tolist()[:2],
                 "delta_allowed_fraction": allowed / trip}
         print(json.dumps(line), flush=True)
     ctx.close()
