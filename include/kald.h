@@ -54,8 +54,13 @@ typedef enum {
  * modes. */
 typedef enum {
     KALD_FP64 = 0,           /* plain FP64 on CUDA cores                       */
-    KALD_FP32 = 1            /* projection + delta epilogue in FP32 on CUDA
+    KALD_FP32 = 1,           /* projection + delta epilogue in FP32 on CUDA
                                 cores, FP64 accumulation across q'            */
+    KALD_BF16_SPLIT = 2      /* Gamma-only systems with nb > 96: the two
+                                projection contractions on tcgen05 tensor
+                                cores with BF16 hi+lo operands (three MMAs per
+                                product) and FP32 accumulation; weights and
+                                sums in FP64.  KALD_E_UNSUPPORTED otherwise.  */
 } kald_precision;
 
 /* One crystal unit cell, or one Gamma-only supercell (used with mesh 1x1x1).

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libkald.so")
 KALD_OK = 0
 STATUS = {0: "KALD_OK", 1: "KALD_E_INVALID", 2: "KALD_E_NOMEM", 3: "KALD_E_CUDA",
           4: "KALD_E_NOCONV", 5: "KALD_E_TIMEOUT", 6: "KALD_E_UNSUPPORTED"}
-PRECISION = {"fp64": 0, "fp32": 1}
+PRECISION = {"fp64": 0, "fp32": 1, "bf16split": 2}
 
 EXPORTS = ["kald_ctx_create", "kald_ctx_destroy", "kald_last_error", "kald_set_stream",
            "kald_phonons", "kald_linewidths", "kald_kappa_rta", "kald_kappa_qhgk",

@@ -197,22 +197,48 @@ cudaError_t run_plain(const GammaPlan &gp, const GammaDev &d, const LwParams &p,
     return cudaGetLastError();
 }
 
+// gamma[mu] = pref / w_mu * sum of the mode's band-tile partials (CSR, fixed order).
+__global__ void g_gamma_csr_kernel(int nb, const int *__restrict__ tile_start, const double *__restrict__ partial,
+                                   const double *__restrict__ omega, double pref, double *__restrict__ gamma) {
+    const int mu = blockIdx.x * blockDim.x + threadIdx.x;
+    if (mu >= nb) return;
+    double t = 0.0;
+    for (int k = tile_start[mu]; k < tile_start[mu + 1]; ++k) t += partial[k];
+    const double w = omega[mu];
+    gamma[mu] = (w > 0.0) ? pref * t / w : 0.0;
+}
+
 }  // namespace
 
-cudaError_t launch_gamma_only(const GammaPlan &gp, const GammaDev &d, const LwParams &p, int fp32,
+cudaError_t launch_gamma_only(const GammaPlan &gp, const GammaDev &d, const LwParams &p, int mode,
                               double degen_tol_thz, double *gamma_out, cudaStream_t st) {
     const int nb = p.nb;
     cudaError_t e = launch_mode_prep(nb, d.nu, p.omega_min_w, p.T, p.classical, d.omega, d.occ, st);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(d.allowed, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(d.partial, 0, sizeof(double) * (size_t)nb * gp.n_part, st);
-    if (e != cudaSuccess) return e;
-    e = fp32 ? run_plain<float>(gp, d, p, st) : run_plain<double>(gp, d, p, st);
-    if (e != cudaSuccess) return e;
     const double pref = kHbarEvPs * kPi / 8.0 * kEvA2AmuPs2 * kEvA2AmuPs2 * kEvA2AmuPs2 /
                         (sqrt(kTwoPi) * p.sigma_w);
-    g_gamma_kernel<<<(nb + 127) / 128, 128, 0, st>>>(nb, gp.n_part, d.partial, d.omega, pref, gamma_out);
+    if (mode == 2) {
+        const size_t nt = gp.tiles.size();
+        e = cudaMemsetAsync(d.partial_tc, 0, sizeof(double) * std::max<size_t>(nt, 1), st);
+        if (e != cudaSuccess) return e;
+        e = launch_gamma_only_tc(gp, d, p, d.tc_scratch, gp.tiles, gp.tile_start, d.tiles_dev, gp.symmetric,
+                                 d.partial_tc, d.err, st);
+        if (e != cudaSuccess) return e;
+        // tile_start is uploaded right after the tiles (same allocation)
+        const int *ts = reinterpret_cast<const int *>(d.tiles_dev + std::max<size_t>(nt, 1));
+        e = cudaMemcpyAsync(const_cast<int *>(ts), gp.tile_start.data(), sizeof(int) * (nb + 1),
+                            cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
+        g_gamma_csr_kernel<<<(nb + 127) / 128, 128, 0, st>>>(nb, ts, d.partial_tc, d.omega, pref, gamma_out);
+    } else {
+        e = cudaMemsetAsync(d.partial, 0, sizeof(double) * (size_t)nb * gp.n_part, st);
+        if (e != cudaSuccess) return e;
+        e = mode == 1 ? run_plain<float>(gp, d, p, st) : run_plain<double>(gp, d, p, st);
+        if (e != cudaSuccess) return e;
+        g_gamma_kernel<<<(nb + 127) / 128, 128, 0, st>>>(nb, gp.n_part, d.partial, d.omega, pref, gamma_out);
+    }
     g_rank_kernel<<<(nb + 127) / 128, 128, 0, st>>>(nb, d.nu, d.order);
     g_degen_kernel<<<1, 32, 0, st>>>(nb, d.nu, d.order, degen_tol_thz, gamma_out);
     return cudaGetLastError();

@@ -10,7 +10,9 @@
 #include <cstring>
 #include <map>
 #include <numeric>
+#include <array>
 #include <tuple>
+#include <unordered_map>
 
 #include "kald_internal.h"
 
@@ -403,6 +405,71 @@ kald_status kald_phonons(kald_ctx *ctx, const kald_system *sys, const int32_t me
     return KALD_OK;
 }
 
+namespace kald {
+namespace {
+// True when every fc3 block (i; j Rj; k Rk) has the partner (i; k Rk; j Rj)
+// with the last two Cartesian indices exchanged (then Y_mu and phi are
+// symmetric and the tensor-core path computes only the upper triangle).
+bool fc3_symmetric_last_two(const kald_system *s) {
+    struct H {
+        size_t operator()(const std::array<int, 9> &a) const {
+            size_t h = 1469598103934665603ull;
+            for (int v : a) h = (h ^ (size_t)(uint32_t)v) * 1099511628211ull;
+            return h;
+        }
+    };
+    std::unordered_map<std::array<int, 9>, int, H> idx;
+    idx.reserve((size_t)s->n_fc3 * 2);
+    for (int b = 0; b < s->n_fc3; ++b) {
+        std::array<int, 9> k;
+        for (int x = 0; x < 9; ++x) k[x] = s->fc3_idx[9 * (size_t)b + x];
+        idx.emplace(k, b);
+    }
+    for (int b = 0; b < s->n_fc3; ++b) {
+        const int32_t *x = s->fc3_idx + 9 * (size_t)b;
+        const std::array<int, 9> k = {x[0], x[5], x[6], x[7], x[8], x[1], x[2], x[3], x[4]};
+        auto it = idx.find(k);
+        if (it == idx.end()) return false;
+        const double *f = s->fc3 + 27 * (size_t)b, *g = s->fc3 + 27 * (size_t)it->second;
+        for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < 3; ++c)
+                for (int d = 0; d < 3; ++d) {
+                    const double u = f[9 * a + 3 * c + d], v = g[9 * a + 3 * d + c];
+                    if (std::fabs(u - v) > 1e-12 * (std::fabs(u) + std::fabs(v)) + 1e-300) return false;
+                }
+    }
+    return true;
+}
+// (tm, tn) tiles of T E^T that the delta window can reach, per mode.
+void band_tiles(const std::vector<double> &w, int tile, double cut, int symmetric, std::vector<int2> &tiles,
+                std::vector<int> &start) {
+    const int nb = (int)w.size(), nt = (nb + tile - 1) / tile;
+    std::vector<double> lo(nt, 1e300), hi(nt, -1e300);
+    for (int m = 0; m < nb; ++m)
+        if (w[m] > 0.0) { lo[m / tile] = std::min(lo[m / tile], w[m]); hi[m / tile] = std::max(hi[m / tile], w[m]); }
+    auto band = [&](double x, int a, int b) {
+        return ((x + lo[a] - hi[b] < cut) && (x + hi[a] - lo[b] > -cut)) ||
+               ((x - hi[a] - hi[b] < cut) && (x - lo[a] - lo[b] > -cut));
+    };
+    tiles.clear();
+    start.assign(nb + 1, 0);
+    for (int mu = 0; mu < nb; ++mu) {
+        start[mu] = (int)tiles.size();
+        if (!(w[mu] > 0.0)) continue;
+        for (int a = 0; a < nt; ++a) {
+            if (!(hi[a] >= lo[a])) continue;
+            for (int b = symmetric ? a : 0; b < nt; ++b) {
+                if (!(hi[b] >= lo[b])) continue;
+                if (band(w[mu], a, b) || (symmetric && b != a && band(w[mu], b, a)))
+                    tiles.push_back(make_int2(a, b));
+            }
+        }
+    }
+    start[nb] = (int)tiles.size();
+}
+}  // namespace
+}  // namespace kald
+
 static kald_status check_options(kald_ctx *ctx, const kald_options *o) {
     if (!o) return fail(ctx, KALD_E_INVALID, "options NULL");
     if (!(o->temperature_K > 0.0) || !std::isfinite(o->temperature_K))
@@ -413,7 +480,7 @@ static kald_status check_options(kald_ctx *ctx, const kald_options *o) {
         return fail(ctx, KALD_E_INVALID, "n_sigma must be > 0");
     if (!(o->omega_min_thz >= 0.0) || !(o->degen_tol_thz >= 0.0))
         return fail(ctx, KALD_E_INVALID, "omega_min and degen_tol must be >= 0");
-    if (o->precision != KALD_FP64 && o->precision != KALD_FP32)
+    if (o->precision != KALD_FP64 && o->precision != KALD_FP32 && o->precision != KALD_BF16_SPLIT)
         return fail(ctx, KALD_E_INVALID, "unknown precision");
     return KALD_OK;
 }
@@ -457,11 +524,22 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
             }
             std::vector<int> gjk(2 * (size_t)gp.n_groups);
             for (int g = 0; g < gp.n_groups; ++g) { gjk[2 * g] = h.pair3_j[g]; gjk[2 * g + 1] = h.pair3_k[g]; }
+            const int mode = opt->precision;     // 0 FP64, 1 FP32, 2 BF16 split (tensor cores)
             const size_t rs = fp32 ? sizeof(float) : sizeof(double);
+            if (mode == KALD_BF16_SPLIT) {
+                gp.symmetric = fc3_symmetric_last_two(&sys[x]) ? 1 : 0;
+                band_tiles(gp.omega_h, tc_tile(), opt->n_sigma * kTwoPi * opt->sigma_thz, gp.symmetric,
+                           gp.tiles, gp.tile_start);
+            }
+            const size_t n_tiles = std::max<size_t>(gp.tiles.size(), 1);
             size_t need = bytes_of(gjk) + bytes_of(h.pair3_start) + bytes_of(h.fc3_i) + bytes_of(h.fc3_scaled) +
-                          4 * ws_round(rs * nn) + 2 * ws_round(sizeof(double) * nb) +
-                          ws_round(sizeof(double) * nb * (size_t)gp.n_part) + ws_round(sizeof(int) * nb) +
+                          2 * ws_round(sizeof(double) * nb) + ws_round(sizeof(int) * nb) + ws_round(16) +
                           ws_round(16);
+            if (mode == KALD_BF16_SPLIT)
+                need += tc_gamma_scratch_bytes(nb) + ws_round(sizeof(int2) * n_tiles + sizeof(int) * (nb + 1)) +
+                        ws_round(sizeof(double) * n_tiles);
+            else
+                need += 4 * ws_round(rs * nn) + ws_round(sizeof(double) * nb * (size_t)gp.n_part);
             if (!d_nu) need += ws_round(sizeof(double) * nb);
             if (!d_eig) need += ws_round(sizeof(double2) * nn);
             if (!d_g) need += ws_round(sizeof(double) * nb);
@@ -475,13 +553,23 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
             gd.eig = stage_in(ctx, reinterpret_cast<const double2 *>(eigvec) + off_eig, nn, d_eig);
             gd.omega = static_cast<double *>(ws_take(ctx, sizeof(double) * nb));
             gd.occ = static_cast<double *>(ws_take(ctx, sizeof(double) * nb));
-            gd.E = ws_take(ctx, rs * nn);
-            gd.Y = ws_take(ctx, rs * nn);
-            gd.T = ws_take(ctx, rs * nn);
-            gd.PHI = ws_take(ctx, rs * nn);
-            gd.partial = static_cast<double *>(ws_take(ctx, sizeof(double) * nb * (size_t)gp.n_part));
+            gd.E = gd.Y = gd.T = gd.PHI = nullptr;
+            gd.partial = nullptr;
+            gd.tc_scratch = nullptr; gd.tiles_dev = nullptr; gd.partial_tc = nullptr;
+            if (mode == KALD_BF16_SPLIT) {
+                gd.tc_scratch = ws_take(ctx, tc_gamma_scratch_bytes(nb));
+                gd.tiles_dev = static_cast<int2 *>(ws_take(ctx, sizeof(int2) * n_tiles + sizeof(int) * (nb + 1)));
+                gd.partial_tc = static_cast<double *>(ws_take(ctx, sizeof(double) * n_tiles));
+            } else {
+                gd.E = ws_take(ctx, rs * nn);
+                gd.Y = ws_take(ctx, rs * nn);
+                gd.T = ws_take(ctx, rs * nn);
+                gd.PHI = ws_take(ctx, rs * nn);
+                gd.partial = static_cast<double *>(ws_take(ctx, sizeof(double) * nb * (size_t)gp.n_part));
+            }
             gd.order = static_cast<int *>(ws_take(ctx, sizeof(int) * nb));
             gd.allowed = static_cast<unsigned long long *>(ws_take(ctx, 16));
+            gd.err = static_cast<int *>(ws_take(ctx, 16));
             double *g_d = d_g ? gamma + off_nb : static_cast<double *>(ws_take(ctx, sizeof(double) * nb));
             LwParams p;
             p.nb = nb; p.nq = 1;
@@ -492,18 +580,24 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
             p.T = opt->temperature_K;
             p.classical = opt->classical ? 1 : 0;
             p.omega_min_w = kTwoPi * opt->omega_min_thz;
-            cudaError_t e = launch_gamma_only(gp, gd, p, fp32, opt->degen_tol_thz, g_d, ctx->stream);
+            cudaMemsetAsync(gd.err, 0, sizeof(int), ctx->stream);
+            cudaError_t e = launch_gamma_only(gp, gd, p, mode, opt->degen_tol_thz, g_d, ctx->stream);
             if (e != cudaSuccess) return cuda_check(ctx, e, "kald_linewidths (Gamma-only) launch");
             unsigned long long al = 0;
+            int errf = 0;
             cudaMemcpyAsync(&al, gd.allowed, sizeof(al), cudaMemcpyDeviceToHost, ctx->stream);
+            cudaMemcpyAsync(&errf, gd.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
             if (!d_g) cudaMemcpyAsync(gamma + off_nb, g_d, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->stream);
             if ((st = finish(ctx, "kald_linewidths"))) return st;
+            if (errf) return fail(ctx, KALD_E_TIMEOUT, "kald_linewidths: a tensor-core pipeline wait expired");
             tot += (uint64_t)nb * nb * nb;
             allowed_tot += al;
             off_nb += nb;
             off_eig += nn;
             continue;
         }
+        if (opt->precision == KALD_BF16_SPLIT)
+            return fail(ctx, KALD_E_UNSUPPORTED, "KALD_BF16_SPLIT applies to Gamma-only systems with nb > 96");
         std::vector<double> qc;
         std::vector<int> qf;
         mesh_points(h.lattice, mesh, qc, qf);

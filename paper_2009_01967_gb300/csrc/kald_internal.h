@@ -168,6 +168,10 @@ struct GammaPlan {
     int n_groups = 0;
     int n_part = 0;                  // epilogue CTAs (partial sums) per mode
     std::vector<double> omega_h;     // [nb] rad/ps, 0 for a masked mode
+    // tensor-core path: delta-band tiles (tm, tn) of each mode, CSR by mode
+    std::vector<int2> tiles;
+    std::vector<int> tile_start;     // [nb + 1]
+    int symmetric = 0;               // Phi3 symmetric in its last two indices
 };
 struct GammaDev {
     const int *group_jk, *group_start, *blk_i;   // (j, k) groups of fc3 blocks
@@ -179,9 +183,21 @@ struct GammaDev {
     double *partial;                 // [nb][n_part]
     int *order;                      // [nb]
     unsigned long long *allowed;
+    // tensor-core path
+    void *tc_scratch;                // tc_gamma_scratch_bytes(nb)
+    int2 *tiles_dev;                 // [tiles]
+    double *partial_tc;              // [tiles]
+    int *err;                        // bounded-wait failures
 };
-cudaError_t launch_gamma_only(const GammaPlan &gp, const GammaDev &d, const LwParams &p, int fp32,
+// mode: 0 FP64 CUDA cores, 1 FP32 CUDA cores, 2 BF16-split tensor cores
+cudaError_t launch_gamma_only(const GammaPlan &gp, const GammaDev &d, const LwParams &p, int mode,
                               double degen_tol_thz, double *gamma_out, cudaStream_t st);
+size_t tc_gamma_scratch_bytes(int nb);
+int tc_tile(void);
+cudaError_t launch_gamma_only_tc(const GammaPlan &gp, const GammaDev &d, const LwParams &p, void *scratch,
+                                 const std::vector<int2> &tiles, const std::vector<int> &tile_start,
+                                 int2 *tiles_dev, int symmetric, double *partial_tc, int *err,
+                                 cudaStream_t st);
 
 // kappa.cu
 cudaError_t launch_kappa_rta(const DevFc2 &f, int nb, int nq, const double *qcart,

@@ -1,0 +1,431 @@
+// Tensor-core (tcgen05) path of the Gamma-only linewidths: the per-mode
+// contractions T = E Y_mu^T-form and phi = T E^T (paper Eq. projection_plus at
+// q = 0) on 5th-generation tensor cores with a BF16 hi+lo split.
+//
+// Every operand x is carried as two BF16 planes, hi = bf16(x), lo = bf16(x - hi),
+// and a product is formed from three MMAs, A_hi B_hi + A_hi B_lo + A_lo B_hi,
+// accumulated in FP32 in tensor memory; the dropped lo*lo term and the
+// rounding of lo leave about 16 significant bits per product.
+//
+// Kernel shape (one 128 x 128 output tile per CTA, 128 threads):
+//   warp 0 lane 0   TMA producer: 4 tiled loads per K block of 64 (A hi/lo,
+//                   B hi/lo; 128-byte swizzle), 3-stage ring of mbarriers
+//   warp 1          allocates 128 TMEM columns; lane 0 issues the MMAs
+//                   (M = 128, N = 128, K = 16, kind::f16, BF16 in, FP32 out)
+//                   and commits each stage back to the producer
+//   warps 0-3       epilogue: tcgen05.ld of their 32 accumulator lanes
+// Every mbarrier wait is bounded; on expiry the CTA records the failure in a
+// device flag, lets its copies and MMAs drain (bounded again), frees its TMEM
+// and returns, and the host reports KALD_E_TIMEOUT.
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "kald_internal.h"
+
+namespace kald {
+namespace {
+
+constexpr int kBM = 128, kBN = 128, kBK = 64;      // tile; 64 BF16 = one 128-byte swizzle row
+constexpr int kStages = 3;
+constexpr int kTileBytes = kBM * kBK * 2;          // 16 KB per operand plane per stage
+constexpr int kStageBytes = 4 * kTileBytes;        // A hi, A lo, B hi, B lo
+constexpr uint32_t kWaitLimit = 1u << 22;          // polls of a bounded wait
+
+enum : int { EPI_SPLIT = 0, EPI_GAMMA = 1 };
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: true when the phase completed, false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (uint32_t it = 0; it < kWaitLimit; ++it)
+        if (mbar_try(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+// K-major operand tile, 128-byte swizzle: start address, LBO (unused here,
+// 16 B), SBO = 1024 B between 8-row groups, descriptor version 1, layout 2.
+__device__ __forceinline__ uint64_t smem_desc(const void *p) {
+    const uint64_t a = smem_u32(p);
+    return ((a >> 4) & 0x3FFFull) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+           (2ull << 61);
+}
+// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both
+// K-major, N = 128, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
+                            ((uint32_t)(kBM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(tmem_d), "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int x = 0; x < 32; ++x) v[x] = __uint_as_float(r[x]);
+}
+
+struct EpiGamma {
+    const double *omega;      // [nb] rad/ps (0 = masked)
+    const double *occ;        // [nb]
+    double w;                 // omega of the mode
+    double sig2inv, cut;
+    double *partial;          // [n_tiles] per-tile sums of this mode
+    unsigned long long *allowed;
+    const int2 *tiles;        // (tm, tn) of the band tiles of this mode
+    int symmetric;            // phi symmetric: upper-triangle tiles, symmetrised weights
+};
+struct EpiSplit {
+    __nv_bfloat16 *hi, *lo;   // [rows][ld] output planes
+    int ld;
+};
+
+// C[m][n] = sum_k A[m][k] B[n][k]; A, B as BF16 hi/lo planes behind four
+// tensor maps (box 64 x 128, 128-byte swizzle).  Grid: one CTA per tile.
+template <int EPI>
+__global__ void __launch_bounds__(128, 1)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
+               int M, int N, int K, EpiSplit es, EpiGamma eg, int *err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte alignment for the swizzled tiles
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
+    __shared__ uint32_t tmem_base_sm;
+    __shared__ int fail_sm;
+    __shared__ double wn_sm[kBN], nn_sm[kBN];
+    __shared__ double red[4];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int tm, tn;
+    if (EPI == EPI_GAMMA) {
+        const int2 t = eg.tiles[blockIdx.x];
+        tm = t.x; tn = t.y;
+    } else {
+        tm = blockIdx.y; tn = blockIdx.x;
+    }
+    const int nkb = (K + kBK - 1) / kBK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        mbar_init(&done, 1);
+        fail_sm = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(&tmem_base_sm)), "r"(128) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_sm;
+
+    int issued = 0;      // stages handed to TMA by the producer (drain bookkeeping)
+    if (warp == 0 && lane == 0) {
+        // ---- producer
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb % kStages;
+            if (kb >= kStages && !mbar_wait(&empty[s], ((kb / kStages) - 1) & 1)) { fail_sm = 1; break; }
+            unsigned char *st = base + (size_t)s * kStageBytes;
+            mbar_expect_tx(&full[s], kStageBytes);
+            tma_load_2d(st, &mAh, &full[s], kb * kBK, tm * kBM);
+            tma_load_2d(st + kTileBytes, &mAl, &full[s], kb * kBK, tm * kBM);
+            tma_load_2d(st + 2 * kTileBytes, &mBh, &full[s], kb * kBK, tn * kBN);
+            tma_load_2d(st + 3 * kTileBytes, &mBl, &full[s], kb * kBK, tn * kBN);
+            ++issued;
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int s = kb % kStages;
+            if (!mbar_wait(&full[s], (kb / kStages) & 1) || *(volatile int *)&fail_sm) { fail_sm = 1; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            unsigned char *st = base + (size_t)s * kStageBytes;
+            const uint64_t ah = smem_desc(st), al = smem_desc(st + kTileBytes);
+            const uint64_t bh = smem_desc(st + 2 * kTileBytes), bl = smem_desc(st + 3 * kTileBytes);
+#pragma unroll
+            for (int k = 0; k < kBK / 16; ++k) {
+                const uint64_t dk = (uint64_t)((k * 32) >> 4);     // 16 BF16 = 32 B along K
+                mma_bf16(tmem, ah + dk, bh + dk, (kb > 0 || k > 0) ? 1u : 0u);
+                mma_bf16(tmem, ah + dk, bl + dk, 1u);
+                mma_bf16(tmem, al + dk, bh + dk, 1u);
+            }
+            mma_commit(&empty[s]);               // stage free once these MMAs finish
+        }
+        mma_commit(&done);                       // accumulator complete
+    }
+    __syncwarp();
+    // ---- epilogue: wait for the accumulator (bounded)
+    bool ok = mbar_wait(&done, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!ok || *(volatile int *)&fail_sm) {
+        ok = false;
+        if (threadIdx.x == 0) atomicOr(err, 1);
+    }
+    const int row = warp * 32 + lane;            // accumulator lane = tile row
+    const int m = tm * kBM + row;
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    if (EPI == EPI_SPLIT) {
+#pragma unroll 1
+        for (int c0 = 0; c0 < kBN; c0 += 32) {
+            float v[32];
+            tmem_ld32(taddr + c0, v);
+            if (ok && m < M) {
+                __nv_bfloat16 *ph = es.hi + (size_t)m * es.ld + tn * kBN + c0;
+                __nv_bfloat16 *pl = es.lo + (size_t)m * es.ld + tn * kBN + c0;
+#pragma unroll
+                for (int x = 0; x < 32; ++x) {
+                    if (tn * kBN + c0 + x >= N) break;
+                    const __nv_bfloat16 h = __float2bfloat16_rn(v[x]);
+                    ph[x] = h;
+                    pl[x] = __float2bfloat16_rn(v[x] - __bfloat162float(h));
+                }
+            }
+        }
+    } else {
+        for (int x = threadIdx.x; x < kBN; x += blockDim.x) {
+            const int n = tn * kBN + x;
+            wn_sm[x] = n < N ? eg.omega[n] : 0.0;
+            nn_sm[x] = n < N ? eg.occ[n] : 0.0;
+        }
+        __syncthreads();
+        const double w = eg.w;
+        const double w1 = m < M ? eg.omega[m] : 0.0, n1 = m < M ? eg.occ[m] : 0.0;
+        const bool upper = eg.symmetric && (tn > tm);
+        double acc = 0.0;
+        unsigned long long cnt = 0;
+#pragma unroll 1
+        for (int c0 = 0; c0 < kBN; c0 += 32) {
+            float v[32];
+            tmem_ld32(taddr + c0, v);
+            if (!(w1 > 0.0)) continue;
+#pragma unroll 4
+            for (int x = 0; x < 32; ++x) {
+                const double w2 = wn_sm[c0 + x];
+                if (!(w2 > 0.0)) continue;
+                const double n2 = nn_sm[c0 + x];
+                double g = 0.0;
+                const double dp = w + w1 - w2, dm = w - w1 - w2;
+                const bool hm = fabs(dm) < eg.cut;
+                bool a = hm, b = false;
+                if (fabs(dp) < eg.cut) { g += (n1 - n2) * exp(-dp * dp * eg.sig2inv); a = true; }
+                if (hm) g += 0.5 * (1.0 + n1 + n2) * exp(-dm * dm * eg.sig2inv);
+                if (upper) {                     // the mirrored element (mu'', mu') of the lower triangle
+                    const double dp2 = w + w2 - w1;
+                    b = hm;
+                    if (fabs(dp2) < eg.cut) { g += (n2 - n1) * exp(-dp2 * dp2 * eg.sig2inv); b = true; }
+                    if (hm) g += 0.5 * (1.0 + n1 + n2) * exp(-dm * dm * eg.sig2inv);
+                }
+                if (a || b) {
+                    const double f = (double)v[x];
+                    acc += f * f * g / (w1 * w2);
+                    cnt += (unsigned long long)a + (unsigned long long)b;
+                }
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        }
+        if (lane == 0) red[warp] = acc;
+        if (lane == 0 && cnt && ok) atomicAdd(eg.allowed, cnt);
+        __syncthreads();
+        if (threadIdx.x == 0) eg.partial[blockIdx.x] = ok ? red[0] + red[1] + red[2] + red[3] : 0.0;
+    }
+    // ---- teardown: let in-flight TMA/MMA work finish before freeing TMEM
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (*(volatile int *)&fail_sm && threadIdx.x == 0) {
+        // drain: the latest load of each stage completes its transaction (bounded)
+        for (int s = 0; s < kStages; ++s) {
+            int last = -1;
+            for (int kb = s; kb < issued; kb += kStages) last = kb;
+            if (last >= 0) mbar_wait(&full[s], (last / kStages) & 1);
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
+    }
+}
+
+// hi/lo BF16 planes of a row-major matrix (rows x cols) into padded planes
+// (rows_pad x ld); the padding stays zero from the caller's memset.
+template <typename SRC>
+__global__ void split_kernel(int rows, int cols, const SRC *__restrict__ src, size_t src_stride, int ld,
+                             __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
+    const size_t n = (size_t)rows * cols;
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < n;
+         x += (size_t)gridDim.x * blockDim.x) {
+        const size_t r = x / cols, c = x % cols;
+        float v;
+        if constexpr (sizeof(SRC) == 16) v = (float)reinterpret_cast<const double2 *>(src)[r * src_stride + c].x;
+        else v = (float)src[r * src_stride + c];
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        hi[r * ld + c] = h;
+        lo[r * ld + c] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+}
+
+// YT[c][b] of one mode straight into BF16 hi/lo planes (FP64 sums).
+__global__ void ybuild_bf16_kernel(int n_groups, const int *__restrict__ group_jk,
+                                   const int *__restrict__ group_start, const int *__restrict__ blk_i,
+                                   const double *__restrict__ fc3, const double2 *__restrict__ eig_mu,
+                                   int ld, __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_groups * 9) return;
+    const int g = e / 9, bg = e % 9;
+    const int j = group_jk[2 * g], k = group_jk[2 * g + 1];
+    double acc = 0.0;
+    for (int bl = group_start[g]; bl < group_start[g + 1]; ++bl) {
+        const int i = blk_i[bl];
+        const double *f = fc3 + (size_t)27 * bl + bg;
+        acc += f[0] * eig_mu[3 * i].x + f[9] * eig_mu[3 * i + 1].x + f[18] * eig_mu[3 * i + 2].x;
+    }
+    const float v = (float)acc;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const size_t off = (size_t)(3 * k + bg % 3) * ld + 3 * j + bg / 3;
+    hi[off] = h;
+    lo[off] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// Tensor map of a BF16 plane [rows][ld] (ld a multiple of 64), box 64 x 128.
+bool make_map(CUtensorMap *map, const __nv_bfloat16 *ptr, int rows, int ld) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(ptr), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+constexpr size_t kSmemBytes = kStages * kStageBytes + 1024;
+
+}  // namespace
+
+int tc_tile(void) { return kBM; }
+
+size_t tc_gamma_scratch_bytes(int nb) {
+    const int ld = (nb + kBK - 1) / kBK * kBK;
+    const int rows = (nb + kBM - 1) / kBM * kBM;
+    return 6 * ws_round(sizeof(__nv_bfloat16) * (size_t)rows * ld) + ws_round(sizeof(int) * 4);
+}
+
+// The tensor-core pipeline for one Gamma-only system (Y build, T = E Y^T-form,
+// phi tiles of the delta band with the weight epilogue), mode by mode.
+cudaError_t launch_gamma_only_tc(const GammaPlan &gp, const GammaDev &d, const LwParams &p, void *scratch,
+                                 const std::vector<int2> &tiles, const std::vector<int> &tile_start,
+                                 int2 *tiles_dev, int symmetric, double *partial_tc, int *err,
+                                 cudaStream_t st) {
+    const int nb = p.nb;
+    const int ld = (nb + kBK - 1) / kBK * kBK;
+    const int rows = (nb + kBM - 1) / kBM * kBM;
+    const size_t plane = ws_round(sizeof(__nv_bfloat16) * (size_t)rows * ld);
+    char *b = static_cast<char *>(scratch);
+    auto P = [&](int i) { return reinterpret_cast<__nv_bfloat16 *>(b + i * plane); };
+    __nv_bfloat16 *Eh = P(0), *El = P(1), *Yh = P(2), *Yl = P(3), *Th = P(4), *Tl = P(5);
+    cudaError_t e = cudaMemsetAsync(b, 0, 6 * plane, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    split_kernel<double2><<<4096, 256, 0, st>>>(nb, nb, reinterpret_cast<const double2 *>(d.eig),
+                                                (size_t)nb, ld, Eh, El);
+    CUtensorMap mEh, mEl, mYh, mYl, mTh, mTl;
+    if (!make_map(&mEh, Eh, rows, ld) || !make_map(&mEl, El, rows, ld) || !make_map(&mYh, Yh, rows, ld) ||
+        !make_map(&mYl, Yl, rows, ld) || !make_map(&mTh, Th, rows, ld) || !make_map(&mTl, Tl, rows, ld))
+        return cudaErrorInvalidValue;
+    auto k1 = tc_gemm_kernel<EPI_SPLIT>;
+    auto k2 = tc_gemm_kernel<EPI_GAMMA>;
+    e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(tiles_dev, tiles.data(), sizeof(int2) * std::max<size_t>(tiles.size(), 1),
+                        cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    const int nt = rows / kBM;
+    const double sig2inv = 0.5 / (p.sigma_w * p.sigma_w);
+    for (int mu = 0; mu < nb; ++mu) {
+        const int t0 = tile_start[mu], t1 = tile_start[mu + 1];
+        if (!(gp.omega_h[mu] > 0.0) || t1 == t0) continue;
+        // Y_mu^T planes: the previous mode's entries live on the same (sparse)
+        // pattern and are all overwritten
+        ybuild_bf16_kernel<<<(gp.n_groups * 9 + 255) / 256, 256, 0, st>>>(
+            gp.n_groups, d.group_jk, d.group_start, d.blk_i, d.fc3, d.eig + (size_t)mu * nb, ld, Yh, Yl);
+        EpiSplit es{Th, Tl, ld};
+        EpiGamma eg{};
+        k1<<<dim3(nt, nt), 128, kSmemBytes, st>>>(mEh, mEl, mYh, mYl, nb, nb, ld, es, eg, err);
+        EpiGamma eg2{d.omega, d.occ, gp.omega_h[mu], sig2inv, p.cut_w, partial_tc + t0, d.allowed,
+                     tiles_dev + t0, symmetric};
+        EpiSplit es0{nullptr, nullptr, 0};
+        k2<<<t1 - t0, 128, kSmemBytes, st>>>(mTh, mTl, mEh, mEl, nb, nb, ld, es0, eg2, err);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace kald

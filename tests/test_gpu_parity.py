@@ -292,3 +292,23 @@ def test_large_gamma_end_to_end_qhgk(k, big324):
     kap_o = co.kappa_qhgk(s, nu_o, eig_o, g_o, 300.0)
     assert _rel(g, g_o, 1e-6 * g_o.max()) < 1e-8        # gauge-free after degenerate averaging
     np.testing.assert_allclose(kap[0], kap_o, rtol=1e-8, atol=1e-10 * np.abs(kap_o).max())
+
+
+@pytest.mark.parametrize("kind", ["lj", "random_fc3"])
+def test_large_gamma_bf16split_tensor_cores(k, big324, kind):
+    """tcgen05 BF16 hi+lo path (three MMAs per product, FP32 accumulation in
+    tensor memory).  The LJ system has a permutation-symmetric Phi3, so only
+    the upper triangle of phi is computed; the random extra blocks break that
+    symmetry and the full delta band is computed."""
+    kk, ctx = k
+    s, nu_o, eig_o, g_o = big324
+    if kind == "random_fc3":
+        s = ki.random_fc3_system(s, 400, seed=21, scale=0.02)
+        g_o = an.linewidths_gamma_only(s, nu_o, eig_o, 300.0, 0.05)
+    w = ki.Workload("g324", [s], (1, 1, 1), 300.0, 0.05, 3.0)
+    g, (tot, allowed) = kk.kald_linewidths(ctx, s, (1, 1, 1), nu_o, eig_o, _opts(kk, w, "bf16split"))
+    g64, (_, allowed64) = kk.kald_linewidths(ctx, s, (1, 1, 1), nu_o, eig_o, _opts(kk, w, "fp64"))
+    assert allowed == allowed64
+    err = _rel(g, g_o, 1e-6 * g_o.max())
+    print(f"bf16 split gamma max rel err {err:.3e}")
+    assert err < 1e-4
