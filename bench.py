@@ -279,24 +279,51 @@ def run_kald(args):
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, FMA = 2 flops
     lw_avg_s = float(np.mean(lw_ms)) / 1e3
     if gamma_only:
-        # per valid mode: two dense nb^3 contractions (E Y, then (E Y) E^T), 2 flop per FMA
         nu_c = nu.cpu().numpy()
-        flops = sum(4.0 * b ** 3 * int(np.sum(nu_c[offs_m[x]:offs_m[x + 1]] > opt.omega_min_thz))
-                    for x, b in enumerate(nbs))
-        kernel = "g_gemm_nt_kernel"
-    else:
-        n_valid = int(torch.sum(nu > opt.omega_min_thz).item())
-        n_fc3 = s.fc3.shape[0]
-        flops = (n_valid * nq * (20.0 * n_fc3 + 8.0 * nb ** 3)     # Y build + T' = eps'^T Y
-                 + allowed * 8.0 * nb)                              # phi at delta-allowed pairs
-        kernel = "lw_main_kernel"
-    peak = fp32_peak if args.precision == "fp32" else fp32_peak / 64.0
+        if args.precision == "bf16split":
+            # executed tensor work: 3 BF16 MMAs per product; GEMM1 over all
+            # 128 x 128 tiles, GEMM2 over the delta-band tiles (upper triangle)
+            flops = 0.0
+            cut = w.n_sigma * 2 * np.pi * w.sigma_thz
+            for x, b in enumerate(nbs):
+                om = 2 * np.pi * nu_c[offs_m[x]:offs_m[x + 1]]
+                om = np.where(nu_c[offs_m[x]:offs_m[x + 1]] > opt.omega_min_thz, om, 0.0)
+                nt = -(-b // 128)
+                ld = -(-b // 64) * 64
+                lo = np.full(nt, np.inf); hi = np.full(nt, -np.inf)
+                for m in range(b):
+                    if om[m] > 0:
+                        lo[m // 128] = min(lo[m // 128], om[m]); hi[m // 128] = max(hi[m // 128], om[m])
+                def band(ww, a, c):
+                    return ((ww + lo[a] - hi[c] < cut) and (ww + hi[a] - lo[c] > -cut)) or \
+                           ((ww - hi[a] - hi[c] < cut) and (ww - lo[a] - lo[c] > -cut))
+                n_tiles = 0
+                for ww in om[om > 0]:
+                    for a in range(nt):
+                        for c in range(a, nt):
+                            if hi[a] >= lo[a] and hi[c] >= lo[c] and (band(ww, a, c) or (c != a and band(ww, c, a))):
+                                n_tiles += 1
+                n_valid = int(np.sum(om > 0))
+                flops += 3 * 2.0 * 128 * 128 * ld * (n_valid * nt * nt + n_tiles)
+            kernel = "tc_gemm_kernel"
+        else:
+            # per valid mode: two dense nb^3 contractions (E Y, then (E Y) E^T), 2 flop per FMA
+            flops = sum(4.0 * b ** 3 * int(np.sum(nu_c[offs_m[x]:offs_m[x + 1]] > opt.omega_min_thz))
+                        for x, b in enumerate(nbs))
+            kernel = "g_gemm_nt_kernel"
     achieved = flops / lw_avg_s / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": kernel, "flops_per_launch": flops,
-                "peak_note": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz" +
-                             ("" if args.precision == "fp32" else " / 64 (FP64)")}
+    if args.precision == "bf16split":
+        peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None, "kernel": kernel, "flops_per_launch": flops,
+                    "peak_note": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16, power-capped loop), of measured"}
+    else:
+        peak = fp32_peak if args.precision == "fp32" else fp32_peak / 64.0
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "kernel": kernel, "flops_per_launch": flops,
+                    "peak_note": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz" +
+                                 ("" if args.precision == "fp32" else " / 64 (FP64)")}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, sample = time_oracle_sample(w)
@@ -306,7 +333,7 @@ def run_kald(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32" if args.precision == "fp32" else "f64",
+                "dtype": {"fp32": "f32", "fp64": "f64", "bf16split": "bf16x3"}[args.precision],
                 "data": "synthetic",
                 "config": {"workload": f"{w.name}: {w.description}", "global_batch": world,
                            "seq_len": None, "parallelism": f"replicas{world}",
@@ -333,11 +360,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="kald", choices=["kald", "reference"])
     ap.add_argument("--workload", default="C2", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default=None, choices=["fp32", "fp64", "bf16split"],
+                    help="default: fp32 for crystals, bf16split (tensor cores) for Gamma-only workloads")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling runs)")
     ap.add_argument("--mesh", default=None, help="override the q-mesh, e.g. 4,4,4 (profiling runs)")
     args = ap.parse_args()
+    if args.precision is None:
+        args.precision = "bf16split" if WORKLOADS[args.workload]().n_q == 1 else "fp32"
     if args.impl == "reference":
         return run_reference(args)
     return run_kald(args)
