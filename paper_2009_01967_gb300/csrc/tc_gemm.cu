@@ -136,7 +136,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ 
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
     __shared__ uint32_t tmem_base_sm;
     __shared__ int fail_sm;
-    __shared__ double wn_sm[kBN], nn_sm[kBN];
+    __shared__ float wn_sm[kBN], nn_sm[kBN];
     __shared__ double red[4];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -211,68 +211,72 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ 
     const int m = tm * kBM + row;
     const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
     if (EPI == EPI_SPLIT) {
+        // whole tile, 16-byte stores: rows and columns past M, N hold exact
+        // zeros (their A rows / B rows are zero padding) and the planes are
+        // allocated to the padded size
+        uint4 *ph = reinterpret_cast<uint4 *>(es.hi + (size_t)m * es.ld + tn * kBN);
+        uint4 *pl = reinterpret_cast<uint4 *>(es.lo + (size_t)m * es.ld + tn * kBN);
 #pragma unroll 1
         for (int c0 = 0; c0 < kBN; c0 += 32) {
             float v[32];
             tmem_ld32(taddr + c0, v);
-            if (ok && m < M) {
-                __nv_bfloat16 *ph = es.hi + (size_t)m * es.ld + tn * kBN + c0;
-                __nv_bfloat16 *pl = es.lo + (size_t)m * es.ld + tn * kBN + c0;
+            if (!ok) continue;
 #pragma unroll
-                for (int x = 0; x < 32; ++x) {
-                    if (tn * kBN + c0 + x >= N) break;
-                    const __nv_bfloat16 h = __float2bfloat16_rn(v[x]);
-                    ph[x] = h;
-                    pl[x] = __float2bfloat16_rn(v[x] - __bfloat162float(h));
+            for (int q = 0; q < 4; ++q) {
+                uint32_t hw[4], lw[4];
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    const float a = v[8 * q + 2 * x], b = v[8 * q + 2 * x + 1];
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+                    const __nv_bfloat162 l = __floats2bfloat162_rn(a - __low2float(h), b - __high2float(h));
+                    hw[x] = *reinterpret_cast<const uint32_t *>(&h);
+                    lw[x] = *reinterpret_cast<const uint32_t *>(&l);
                 }
+                ph[(c0 >> 3) + q] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                pl[(c0 >> 3) + q] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
             }
         }
     } else {
+        // delta weights in FP32 (window test first; the FP64 unit is slow)
         for (int x = threadIdx.x; x < kBN; x += blockDim.x) {
             const int n = tn * kBN + x;
-            wn_sm[x] = n < N ? eg.omega[n] : 0.0;
-            nn_sm[x] = n < N ? eg.occ[n] : 0.0;
+            wn_sm[x] = n < N ? (float)eg.omega[n] : 0.0f;
+            nn_sm[x] = n < N ? (float)eg.occ[n] : 0.0f;
         }
         __syncthreads();
-        const double w = eg.w;
-        const double w1 = m < M ? eg.omega[m] : 0.0, n1 = m < M ? eg.occ[m] : 0.0;
+        const float w = (float)eg.w, cut = (float)eg.cut, s2i = (float)eg.sig2inv;
+        const float w1 = m < M ? (float)eg.omega[m] : 0.0f, n1 = m < M ? (float)eg.occ[m] : 0.0f;
         const bool upper = eg.symmetric && (tn > tm);
-        double acc = 0.0;
+        float acc = 0.0f;
         unsigned long long cnt = 0;
 #pragma unroll 1
         for (int c0 = 0; c0 < kBN; c0 += 32) {
             float v[32];
             tmem_ld32(taddr + c0, v);
-            if (!(w1 > 0.0)) continue;
+            if (!(w1 > 0.0f)) continue;
 #pragma unroll 4
             for (int x = 0; x < 32; ++x) {
-                const double w2 = wn_sm[c0 + x];
-                if (!(w2 > 0.0)) continue;
-                const double n2 = nn_sm[c0 + x];
-                double g = 0.0;
-                const double dp = w + w1 - w2, dm = w - w1 - w2;
-                const bool hm = fabs(dm) < eg.cut;
-                bool a = hm, b = false;
-                if (fabs(dp) < eg.cut) { g += (n1 - n2) * exp(-dp * dp * eg.sig2inv); a = true; }
-                if (hm) g += 0.5 * (1.0 + n1 + n2) * exp(-dm * dm * eg.sig2inv);
-                if (upper) {                     // the mirrored element (mu'', mu') of the lower triangle
-                    const double dp2 = w + w2 - w1;
-                    b = hm;
-                    if (fabs(dp2) < eg.cut) { g += (n2 - n1) * exp(-dp2 * dp2 * eg.sig2inv); b = true; }
-                    if (hm) g += 0.5 * (1.0 + n1 + n2) * exp(-dm * dm * eg.sig2inv);
-                }
-                if (a || b) {
-                    const double f = (double)v[x];
-                    acc += f * f * g / (w1 * w2);
-                    cnt += (unsigned long long)a + (unsigned long long)b;
-                }
+                const float w2 = wn_sm[c0 + x];
+                const float dp = w + w1 - w2, dm = w - w1 - w2, dp2 = w + w2 - w1;
+                const bool hp = fabsf(dp) < cut, hm = fabsf(dm) < cut;
+                const bool hp2 = upper && fabsf(dp2) < cut;
+                if (!(w2 > 0.0f) || !(hp || hm || hp2)) continue;
+                const float n2 = nn_sm[c0 + x];
+                float g = 0.0f;
+                if (hp) g += (n1 - n2) * expf(-dp * dp * s2i);
+                if (hm) g += (upper ? 1.0f : 0.5f) * (1.0f + n1 + n2) * expf(-dm * dm * s2i);
+                if (hp2) g += (n2 - n1) * expf(-dp2 * dp2 * s2i);
+                const float f = v[x];
+                acc += f * f * g / (w1 * w2);
+                cnt += (unsigned long long)(hp || hm) + (unsigned long long)(upper && (hp2 || hm));
             }
         }
+        double accd = (double)acc;
         for (int o = 16; o > 0; o >>= 1) {
-            acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            accd += __shfl_xor_sync(0xffffffffu, accd, o);
             cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
         }
-        if (lane == 0) red[warp] = acc;
+        if (lane == 0) red[warp] = accd;
         if (lane == 0 && cnt && ok) atomicAdd(eg.allowed, cnt);
         __syncthreads();
         if (threadIdx.x == 0) eg.partial[blockIdx.x] = ok ? red[0] + red[1] + red[2] + red[3] : 0.0;
