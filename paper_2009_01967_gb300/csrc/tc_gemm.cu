@@ -25,6 +25,7 @@
 #include <cmath>
 
 #include "kald_internal.h"
+#include "tc_common.cuh"
 
 namespace kald {
 namespace {
@@ -33,79 +34,11 @@ constexpr int kBM = 128, kBN = 128, kBK = 64;      // tile; 64 BF16 = one 128-by
 constexpr int kStages = 3;
 constexpr int kTileBytes = kBM * kBK * 2;          // 16 KB per operand plane per stage
 constexpr int kStageBytes = 4 * kTileBytes;        // A hi, A lo, B hi, B lo
-constexpr uint32_t kWaitLimit = 1u << 22;          // polls of a bounded wait
 
 enum : int { EPI_SPLIT = 0, EPI_GAMMA = 1 };
+constexpr uint32_t kIdesc = tc::idesc_bf16(kBN);
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait: true when the phase completed, false when the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (uint32_t it = 0; it < kWaitLimit; ++it)
-        if (mbar_try(bar, parity)) return true;
-    return false;
-}
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
-        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
-        : "memory");
-}
-// K-major operand tile, 128-byte swizzle: start address, LBO (unused here,
-// 16 B), SBO = 1024 B between 8-row groups, descriptor version 1, layout 2.
-__device__ __forceinline__ uint64_t smem_desc(const void *p) {
-    const uint64_t a = smem_u32(p);
-    return ((a >> 4) & 0x3FFFull) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
-           (2ull << 61);
-}
-// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both
-// K-major, N = 128, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
-                            ((uint32_t)(kBM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-        ::"r"(tmem_d), "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
-        : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int x = 0; x < 32; ++x) v[x] = __uint_as_float(r[x]);
-}
+using namespace tc;
 
 struct EpiGamma {
     const double *omega;      // [nb] rad/ps (0 = masked)
@@ -191,9 +124,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ 
 #pragma unroll
             for (int k = 0; k < kBK / 16; ++k) {
                 const uint64_t dk = (uint64_t)((k * 32) >> 4);     // 16 BF16 = 32 B along K
-                mma_bf16(tmem, ah + dk, bh + dk, (kb > 0 || k > 0) ? 1u : 0u);
-                mma_bf16(tmem, ah + dk, bl + dk, 1u);
-                mma_bf16(tmem, al + dk, bh + dk, 1u);
+                mma_bf16(tmem, ah + dk, bh + dk, kIdesc, (kb > 0 || k > 0) ? 1u : 0u);
+                mma_bf16(tmem, ah + dk, bl + dk, kIdesc, 1u);
+                mma_bf16(tmem, al + dk, bh + dk, kIdesc, 1u);
             }
             mma_commit(&empty[s]);               // stage free once these MMAs finish
         }
