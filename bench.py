@@ -311,6 +311,20 @@ def run_kald(args):
             flops = sum(4.0 * b ** 3 * int(np.sum(nu_c[offs_m[x]:offs_m[x + 1]] > opt.omega_min_thz))
                         for x, b in enumerate(nbs))
             kernel = "g_gemm_nt_kernel"
+    else:
+        if args.precision == "bf16split":
+            # executed tensor work: per pair, GEMM1 and GEMM2 over ceil(nb^2 / 128)
+            # row tiles of N = K = 2H (H = nb rounded up to 32), 3 MMAs per product
+            H = -(-nb // 32) * 32
+            mt = -(-(nb * nb) // 128)
+            flops = nq * nq * 2.0 * mt * 3 * 2.0 * 128 * (2 * H) * (2 * H)
+            kernel = "tcx_gemm_kernel"
+        else:
+            n_valid = int(torch.sum(nu > opt.omega_min_thz).item())
+            n_fc3 = s.fc3.shape[0]
+            flops = (n_valid * nq * (20.0 * n_fc3 + 8.0 * nb ** 3)     # Y build + T' = eps'^T Y
+                     + allowed * 8.0 * nb)                              # phi at delta-allowed pairs
+            kernel = "lw_main_kernel"
     achieved = flops / lw_avg_s / 1e12
     if args.precision == "bf16split":
         peak = float(peaks.get("bf16_tflops_sustained", 1700.0))

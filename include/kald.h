@@ -56,11 +56,13 @@ typedef enum {
     KALD_FP64 = 0,           /* plain FP64 on CUDA cores                       */
     KALD_FP32 = 1,           /* projection + delta epilogue in FP32 on CUDA
                                 cores, FP64 accumulation across q'            */
-    KALD_BF16_SPLIT = 2      /* Gamma-only systems with nb > 96: the two
-                                projection contractions on tcgen05 tensor
-                                cores with BF16 hi+lo operands (three MMAs per
-                                product) and FP32 accumulation; weights and
-                                sums in FP64.  KALD_E_UNSUPPORTED otherwise.  */
+    KALD_BF16_SPLIT = 2      /* the two dense projection contractions on
+                                tcgen05 tensor cores with BF16 hi+lo operands
+                                (three MMAs per product) and FP32
+                                accumulation; the Bloch-phase gather (crystals)
+                                and the delta epilogue in FP32, sums over q'
+                                and modes in FP64.  Crystals (nb <= 96) and
+                                Gamma-only systems of any size.               */
 } kald_precision;
 
 /* One crystal unit cell, or one Gamma-only supercell (used with mesh 1x1x1).

@@ -596,8 +596,10 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
             off_eig += nn;
             continue;
         }
-        if (opt->precision == KALD_BF16_SPLIT)
-            return fail(ctx, KALD_E_UNSUPPORTED, "KALD_BF16_SPLIT applies to Gamma-only systems with nb > 96");
+        // BF16 split: the two dense contractions on tensor cores, with the
+        // FP32 tables of the CUDA-core path for the Y-build
+        const int tcx = opt->precision == KALD_BF16_SPLIT;
+        const int f32w = fp32 || tcx;
         std::vector<double> qc;
         std::vector<int> qf;
         mesh_points(h.lattice, mesh, qc, qf);
@@ -618,6 +620,19 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
             int nch = (int)std::max(1LL, std::min<long long>(nq, (want + nq - 1) / nq));
             p.qp_chunk = (nq + nch - 1) / nch;
             p.n_chunks = (nq + p.qp_chunk - 1) / p.qp_chunk;
+            if (tcx) { p.qp_chunk = nq; p.n_chunks = 1; }
+        }
+        const int tcx_b = tcx ? tcx_batch(nb, nq, ctx->sm_count) : 0;
+        // tensor-core path: the fc3 blocks in (j, k) group order, the groups
+        // split over the gather CTAs
+        std::vector<int2> tc_gjk;
+        std::vector<int> tc_part_start, tc_glist;
+        if (tcx) {
+            const int n_groups = (int)h.pair3_j.size();
+            tc_gjk.resize(std::max(1, n_groups));
+            for (int g = 0; g < n_groups; ++g) tc_gjk[g] = make_int2(h.pair3_j[g], h.pair3_k[g]);
+            plan_tcx_parts(h, tcx_parts(n_groups), tc_part_start, tc_glist);
+            if (tc_glist.empty()) tc_glist.push_back(0);
         }
         YSchedule ys;
         plan_ybuild(h, ys);
@@ -627,16 +642,16 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
         for (size_t b = 0; b < n3; ++b) binfo[b] = make_int4(h.fc3_i[b], h.fc3_rj[b], h.fc3_rk[b], 0);
         std::vector<float> fc3f;
         std::vector<double> fc3d;
-        if (fp32) fc3f.assign(28 * std::max<size_t>(n3, 1), 0.0f);
+        if (f32w) fc3f.assign(28 * std::max<size_t>(n3, 1), 0.0f);
         else fc3d.assign(28 * std::max<size_t>(n3, 1), 0.0);
         for (size_t b = 0; b < n3; ++b)
             for (int e = 0; e < 27; ++e) {
-                if (fp32) fc3f[28 * b + e] = (float)h.fc3_scaled[27 * b + e];
+                if (f32w) fc3f[28 * b + e] = (float)h.fc3_scaled[27 * b + e];
                 else fc3d[28 * b + e] = h.fc3_scaled[27 * b + e];
             }
-        const size_t c2 = fp32 ? sizeof(float2) : sizeof(double2);
+        const size_t c2 = f32w ? sizeof(float2) : sizeof(double2);
         size_t need = bytes_of(ys.group_jk) + bytes_of(ys.segs) + bytes_of(ys.sched) + bytes_of(binfo) +
-                      (fp32 ? bytes_of(fc3f) : bytes_of(fc3d)) +
+                      (f32w ? bytes_of(fc3f) : bytes_of(fc3d)) +
                       bytes_of(h.rep_cart) + bytes_of(qc) + bytes_of(qf) +
                       2 * ws_round(sizeof(double) * nq * nb) + ws_round(c2 * nn) +
                       ws_round(c2 * (size_t)nq * h.n_rep) +
@@ -644,13 +659,16 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
         if (!d_nu) need += ws_round(sizeof(double) * nq * nb);
         if (!d_eig) need += ws_round(sizeof(double2) * nn);
         if (!d_g) need += ws_round(sizeof(double) * nq * nb);
+        if (tcx)
+            need += ws_round(tcx_scratch_bytes(nb, nq, tcx_b)) + ws_round(16) + bytes_of(tc_gjk) +
+                    bytes_of(tc_part_start) + bytes_of(tc_glist) + bytes_of(h.pair3_start);
         if ((st = ws_reserve(ctx, need))) return st;
         LwDev d;
         d.group_jk = upload(ctx, ys.group_jk);
         d.segs = upload(ctx, ys.segs);
         d.sched = upload(ctx, ys.sched);
         d.blkinfo = upload(ctx, binfo);
-        d.fc3 = fp32 ? (const void *)upload(ctx, fc3f) : (const void *)upload(ctx, fc3d);
+        d.fc3 = f32w ? (const void *)upload(ctx, fc3f) : (const void *)upload(ctx, fc3d);
         d.rep_cart = upload(ctx, h.rep_cart);
         d.qcart = upload(ctx, qc);
         d.qfrac = upload(ctx, qf);
@@ -664,15 +682,33 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
         d.allowed = static_cast<unsigned long long *>(ws_take(ctx, 16));
         d.queue = static_cast<int *>(ws_take(ctx, 16));
         double *g_d = d_g ? gamma + off_nb : static_cast<double *>(ws_take(ctx, sizeof(double) * nq * nb));
+        void *tc_scr = tcx ? ws_take(ctx, tcx_scratch_bytes(nb, nq, tcx_b)) : nullptr;
+        int *tc_err = tcx ? static_cast<int *>(ws_take(ctx, 16)) : nullptr;
+        TcxGroups tg;
+        if (tcx) {
+            tg.n_groups = (int)h.pair3_j.size();
+            tg.n_parts = (int)tc_part_start.size() - 1;
+            tg.part_start = upload(ctx, tc_part_start);
+            tg.glist = upload(ctx, tc_glist);
+            tg.gstart = upload(ctx, h.pair3_start);
+            tg.gjk = upload(ctx, tc_gjk);
+            tg.blkinfo = d.blkinfo;               // group order (HostSystem order)
+            tg.fc3 = static_cast<const float *>(d.fc3);
+        }
         cudaStream_t s = ctx->stream;
-        cudaError_t e = launch_lw_prep(p, d, fp32, s);
-        if (e == cudaSuccess) e = launch_lw_main(p, d, fp32, ctx->sm_count, ctx->smem_optin, s);
+        cudaError_t e = launch_lw_prep(p, d, f32w, s);
+        if (e == cudaSuccess)
+            e = tcx ? launch_lw_tensor(p, d, tg, tc_scr, tcx_b, ctx->sm_count, tc_err, s)
+                    : launch_lw_main(p, d, fp32, ctx->sm_count, ctx->smem_optin, s);
         if (e == cudaSuccess) e = launch_lw_finish(p, d, opt->degen_tol_thz, g_d, s);
         if (e != cudaSuccess) return cuda_check(ctx, e, "kald_linewidths launch");
         unsigned long long al = 0;
+        int errf = 0;
         cudaMemcpyAsync(&al, d.allowed, sizeof(al), cudaMemcpyDeviceToHost, s);
+        if (tcx) cudaMemcpyAsync(&errf, tc_err, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (!d_g) cudaMemcpyAsync(gamma + off_nb, g_d, sizeof(double) * nq * nb, cudaMemcpyDeviceToHost, s);
         if ((st = finish(ctx, "kald_linewidths"))) return st;
+        if (errf) return fail(ctx, KALD_E_TIMEOUT, "kald_linewidths: a tensor-core pipeline wait expired");
         tot += (uint64_t)nq * nq * (uint64_t)nb * nb * nb;
         allowed_tot += al;
         off_nb += (size_t)nq * nb;

@@ -199,6 +199,26 @@ cudaError_t launch_gamma_only_tc(const GammaPlan &gp, const GammaDev &d, const L
                                  int2 *tiles_dev, int symmetric, double *partial_tc, int *err,
                                  cudaStream_t st);
 
+// tc_crystal.cu: crystal linewidth sums on tensor cores (BF16 split, nb <= 96).
+// The gather runs over the fc3 blocks grouped by (j, k) atom pair (the order
+// of HostSystem), the groups split over CTAs by plan_tcx_parts.
+struct TcxGroups {
+    int n_groups = 0, n_parts = 0;
+    const int *part_start = nullptr;  // [n_parts + 1] into glist
+    const int *glist = nullptr;       // group ids, part by part
+    const int *gstart = nullptr;      // [n_groups + 1] blocks of each group (CSR)
+    const int2 *gjk = nullptr;        // [n_groups] atoms (j, k)
+    const int4 *blkinfo = nullptr;    // [n_fc3] (i, rep(Rj), rep(Rk), 0), group order
+    const float *fc3 = nullptr;       // [n_fc3][28] Phi3 / sqrt(mi mj mk), FP32, padded
+};
+int tcx_half(int nb);
+int tcx_batch(int nb, int nq, int sm_count);
+int tcx_parts(int n_groups);
+void plan_tcx_parts(const HostSystem &h, int n_parts, std::vector<int> &part_start, std::vector<int> &glist);
+size_t tcx_scratch_bytes(int nb, int nq, int batch);
+cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups &g, void *scratch, int batch,
+                             int sms, int *err, cudaStream_t st);
+
 // kappa.cu
 cudaError_t launch_kappa_rta(const DevFc2 &f, int nb, int nq, const double *qcart,
                              const double *nu_thz, const double2 *eig, const double *gamma,

@@ -1,0 +1,682 @@
+// Tensor-core (tcgen05) path of the crystal linewidths (paper Eq.
+// projection_plus, gamma_operators, phase_space), for batches of
+// momentum-conserving pairs (q, q'), q'' = q + q' on the mesh.
+//
+// The two dense complex contractions of every (pair, mode s),
+//   T'(s', c)       = sum_b eps'(b, s') Y_s(b, c)
+//   phi(s, s', s'') = sum_c T'(s', c) conj(eps''(c, s'')),
+// run as real GEMMs on BF16 pieces with FP32 accumulation in tensor memory:
+// the data operand (Y, T') as hi + lo, the eigenvector operand as hi + lo
+// (three MMAs per product) or, for nb <= 64, hi + mid + lo (five MMAs).  With H = nb rounded up to 32, K' = 2H
+// (k' < H: real part of index b or c, k' >= H: imaginary part) and the
+// row count M = nb^2 padded to a multiple of 128:
+//   A1[pair][k'][m],  m = c nb + s:  (Re Y_s(b, c) | Im Y_s(b, c))   (gather, CUDA cores)
+//   B1[q'][n'][k']    n' = s': (Re eps' | -Im eps'),  n' = H + s': (Im eps' | Re eps')
+//   GEMM1 row m = (c, s), column n' = Re / Im T'(s', c), stored as
+//   T1[pair][k''][m2], k'' = (part, c), m2 = s nb + s':  (Re T'(s', c) | Im T'(s', c))
+//   B2[q''][n''][k''] n'' = s'': (Re eps'' | Im eps''),  n'' = H + s'': (-Im eps'' | Re eps'')
+//   GEMM2 row m2 = (s, s'), column n'' = Re / Im phi(s, s', s''); the epilogue adds
+//     |phi|^2 / (w' w'') [ (n' - n'') G(w + w' - w'') + 1/2 (1 + n' + n'') G(w - w' - w'') ]
+//   with the same FP32 window test and Gaussian as the CUDA-core kernel.
+// A1 and T1 are stored MN-major (rows contiguous), so the gather (one thread
+// per mode s) and the GEMM1 epilogue (32 consecutive s' per thread) write
+// whole runs; the B operands are K-major.  GEMM2's epilogue writes one FP32
+// sum per row (s, s'); a reduction kernel adds them per mode in a fixed
+// order (FP32 within a pair, FP64 across pairs).
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <queue>
+
+#include "kald_internal.h"
+#include "tc_common.cuh"
+
+namespace kald {
+namespace {
+using namespace tc;
+
+constexpr int kBM = 128, kBK = 64, kStages = 2;
+enum : int { EPI_T = 0, EPI_PHI = 1 };
+
+// BN = N = K' = 2H (64, 128 or 192; crystals have nb <= 96); PB = BF16
+// pieces of the eigenvector operand B (3 where the resident copy fits in
+// shared memory, else 2).
+template <int BN, int PB> struct Cfg {
+    static constexpr int kNkb = BN / kBK;                  // K blocks
+    static constexpr int kABytes = kBM * kBK * 2;          // one A plane per stage (two 64-row atoms)
+    static constexpr int kBBlk = BN * kBK * 2;             // one B plane of one K block
+    static constexpr int kBBytes = kNkb * PB * kBBlk;      // resident B, all pieces
+    static constexpr int kStageBytes = 2 * kABytes;
+    static constexpr int kSmem = kBBytes + kStages * kStageBytes + 1024;
+    static constexpr int kTmemCols = 2 * BN <= 128 ? 128 : 2 * BN <= 256 ? 256 : 512;   // two accumulators
+};
+
+struct XParams {
+    int nb, H, Kp;            // branches, half width (nb rounded up to 32), K' = 2H
+    int Mp;                   // rows nb^2 padded to a multiple of 128
+    int nq, mesh0, mesh1, mesh2;
+    long long pair0;          // first pair of the batch: pair = q * nq + q'
+    int n_pairs;
+    const int *qfrac;         // [nq][3] integer mesh coordinates
+    __nv_bfloat16 *t1h, *t1l; // GEMM1 output [pairs][Kp][Mp]
+    const float *omega;       // [nq][nb] rad/ps (0 = masked)
+    const float *occ;         // [nq][nb]
+    float sig2inv, cut;
+    float *rowval;            // GEMM2 output [pairs][Mp]: sum over s'' of row (s, s')
+    unsigned long long *allowed;
+};
+
+__device__ __forceinline__ void pair_of(const XParams &x, int a, int &q, int &qp, int &qpp) {
+    const long long pi = x.pair0 + a;
+    q = (int)(pi / x.nq);
+    qp = (int)(pi - (long long)q * x.nq);
+    const int *kq = x.qfrac + 3 * q, *kp = x.qfrac + 3 * qp;
+    const int k0 = (kq[0] + kp[0]) % x.mesh0;
+    const int k1 = (kq[1] + kp[1]) % x.mesh1;
+    const int k2 = (kq[2] + kp[2]) % x.mesh2;
+    qpp = (k0 * x.mesh1 + k1) * x.mesh2 + k2;
+}
+
+// MN-major operand tile, 128-byte swizzle: atoms of 64 rows (128 B) x 8 K
+// values; LBO = 8 KB between the two 64-row halves of the 128-row tile,
+// SBO = 1 KB between groups of 8 K values.
+__device__ __forceinline__ uint64_t smem_desc_mn(const void *p) {
+    const uint64_t a = smem_u32(p);
+    return ((a >> 4) & 0x3FFFull) | ((uint64_t)(8192 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           (1ull << 46) | (2ull << 61);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo_half, __nv_bfloat16 hi_half) {
+    return (uint32_t)__bfloat16_as_ushort(lo_half) | ((uint32_t)__bfloat16_as_ushort(hi_half) << 16);
+}
+
+// D[m][n] = sum_k A[pair][k][m] B[z][n][k] over the 128-row tiles
+// [blockIdx.x * tpc, ...) of one pair (blockIdx.y); A MN-major, B K-major;
+// z = q' for GEMM1, q'' for GEMM2.  Warp-specialised and persistent over the
+// CTA's tiles: warp 0 issues TMA (B once, resident; A through a two-stage
+// ring), warp 1 issues the MMAs into one of two TMEM accumulators (at
+// column 0 and at half the allocation), warps 4..11 run the epilogue of the previous tile meanwhile (warp w reads TMEM
+// lanes 32 (w % 4) ..; warps 4..7 take one half of the columns, 8..11 the
+// other).  Every wait is bounded; a failed wait sets *err and the CTA winds
+// down without touching memory it does not own.
+constexpr int kWsThreads = 384;
+constexpr int kEpiWarps = 8;
+
+template <int EPI, int BN, int PB>
+__global__ void __launch_bounds__(kWsThreads, 1)
+tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+                const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBm,
+                const __grid_constant__ CUtensorMap mBl, XParams x, int tpc, int *err) {
+    using C = Cfg<BN, PB>;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char *sB = base;                      // [kb][piece][BN rows x 128 B]
+    unsigned char *sA = base + C::kBBytes;         // [stage][hi, lo][two 64-row atoms]
+    __shared__ __align__(8) uint64_t bfull, afull[kStages], aempty[kStages], tfull[2], tempty[2], drain;
+    __shared__ uint32_t tmem_base_sm;
+    __shared__ int fail_sm;
+    __shared__ float w2_sm[128], n2_sm[128], iw2_sm[128];
+    __shared__ float rowsum[2][2][kBM];          // [tile parity][column half][row]
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int a = blockIdx.y;
+    const int mt = x.Mp / kBM;
+    const int t0 = blockIdx.x * tpc, t1 = min(mt, t0 + tpc);
+    const int n_tiles = max(0, t1 - t0);
+    const int nb = x.nb, H = x.H;
+    constexpr int nkb = C::kNkb;
+    constexpr uint32_t idesc = idesc_bf16(BN) | (1u << 15);     // A MN-major
+    int q, qp, qpp;
+    pair_of(x, a, q, qp, qpp);
+    const int bz = (EPI == EPI_T) ? qp : qpp;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bfull, 1);
+        for (int s = 0; s < kStages; ++s) { mbar_init(&afull[s], 1); mbar_init(&aempty[s], 1); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], kEpiWarps); }
+        mbar_init(&drain, 1);
+        fail_sm = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (EPI == EPI_PHI) {
+        // columns of q'': masked modes and padding get a frequency no window reaches
+        for (int t = threadIdx.x; t < 128; t += blockDim.x) {
+            const float w2 = t < nb ? x.omega[(size_t)qpp * nb + t] : 0.0f;
+            const bool v = w2 > 0.0f;
+            w2_sm[t] = v ? w2 : 1e30f;
+            n2_sm[t] = v ? x.occ[(size_t)qpp * nb + t] : 0.0f;
+            iw2_sm[t] = v ? 1.0f / w2 : 0.0f;
+        }
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(&tmem_base_sm)), "r"(C::kTmemCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_sm;
+
+    int issued = 0;                                // A stages handed to TMA (drain bookkeeping)
+    if (warp == 0) {
+        if (lane == 0) {
+            mbar_expect_tx(&bfull, C::kBBytes);
+            for (int kb = 0; kb < nkb; ++kb) {
+                tma_load_3d(sB + (PB * kb) * C::kBBlk, &mBh, &bfull, kb * kBK, 0, bz);
+                if (PB == 3) tma_load_3d(sB + (PB * kb + 1) * C::kBBlk, &mBm, &bfull, kb * kBK, 0, bz);
+                tma_load_3d(sB + (PB * kb + PB - 1) * C::kBBlk, &mBl, &bfull, kb * kBK, 0, bz);
+            }
+            int it = 0;
+            for (int tile = t0; tile < t1; ++tile) {
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = it % kStages;
+                    if (it >= kStages && !mbar_wait(&aempty[s], ((it / kStages) - 1) & 1)) fail_sm = 1;
+                    if (*(volatile int *)&fail_sm) break;
+                    unsigned char *st = sA + (size_t)s * C::kStageBytes;
+                    mbar_expect_tx(&afull[s], C::kStageBytes);
+                    tma_load_3d(st, &mAh, &afull[s], tile * kBM, kb * kBK, a);
+                    tma_load_3d(st + C::kABytes / 2, &mAh, &afull[s], tile * kBM + 64, kb * kBK, a);
+                    tma_load_3d(st + C::kABytes, &mAl, &afull[s], tile * kBM, kb * kBK, a);
+                    tma_load_3d(st + C::kABytes + C::kABytes / 2, &mAl, &afull[s], tile * kBM + 64, kb * kBK, a);
+                    ++issued;
+                }
+                if (*(volatile int *)&fail_sm) break;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            if (!mbar_wait(&bfull, 0)) fail_sm = 1;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            int it = 0;
+            for (int i = 0; i < n_tiles && !*(volatile int *)&fail_sm; ++i) {
+                const int buf = i & 1;
+                if (i >= 2 && !mbar_wait(&tempty[buf], ((i >> 1) - 1) & 1)) { fail_sm = 1; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + (uint32_t)(buf * (C::kTmemCols / 2));
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = it % kStages;
+                    if (!mbar_wait(&afull[s], (it / kStages) & 1) || *(volatile int *)&fail_sm) {
+                        fail_sm = 1;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    unsigned char *st = sA + (size_t)s * C::kStageBytes;
+                    const uint64_t ah = smem_desc_mn(st), al = smem_desc_mn(st + C::kABytes);
+                    const uint64_t bh = smem_desc(sB + (PB * kb) * C::kBBlk);
+                    const uint64_t bm = smem_desc(sB + (PB * kb + 1) * C::kBBlk);
+                    const uint64_t bl = smem_desc(sB + (PB * kb + PB - 1) * C::kBBlk);
+#pragma unroll
+                    for (int k = 0; k < kBK / 16; ++k) {
+                        const uint64_t da = (uint64_t)((k * 2048) >> 4), db = (uint64_t)((k * 32) >> 4);
+                        // a b = (ah + al)(bh [+ bm] + bl) without the smallest terms
+                        mma_bf16(d, ah + da, bh + db, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                        mma_bf16(d, ah + da, bl + db, idesc, 1u);
+                        mma_bf16(d, al + da, bh + db, idesc, 1u);
+                        if (PB == 3) {
+                            mma_bf16(d, ah + da, bm + db, idesc, 1u);
+                            mma_bf16(d, al + da, bm + db, idesc, 1u);
+                        }
+                    }
+                    mma_commit(&aempty[s]);
+                }
+                if (*(volatile int *)&fail_sm) break;
+                mma_commit(&tfull[buf]);
+            }
+            mma_commit(&drain);                    // every MMA of this thread done
+        }
+    } else if (warp >= 4) {
+        const int ew = warp - 4, qd = warp & 3, hf = ew >> 2;
+        const int row = qd * 32 + lane;
+        float cut = x.cut, s2i = x.sig2inv;
+        unsigned long long cnt = 0;
+        for (int i = 0; i < n_tiles; ++i) {
+            const int tile = t0 + i, buf = i & 1;
+            bool ok = !*(volatile int *)&fail_sm && mbar_wait(&tfull[buf], (i >> 1) & 1);
+            ok = __all_sync(0xffffffffu, ok);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (!ok) fail_sm = 1;
+            const uint32_t taddr = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(buf * (C::kTmemCols / 2));
+            const int r = tile * kBM + row;            // (c, s) for GEMM1, (s, s') for GEMM2
+            const bool rv = r < nb * nb;
+            const int r_hi = r / nb, r_lo = r - r_hi * nb;
+            if (EPI == EPI_T) {
+                const int c = r_hi, s = r_lo;
+                const bool vec = (nb % 8) == 0;
+                for (int ci = hf; ok && ci < BN / 32; ci += 2) {
+                    const int c0 = ci * 32;
+                    float v[32];
+                    tmem_ld32(taddr + c0, v);
+                    if (!rv) continue;
+                    const int part = c0 >= H ? 1 : 0;   // H is a multiple of 32
+                    const int sp0 = c0 - part * H;
+                    if (sp0 >= nb) continue;
+                    const size_t off = ((size_t)a * x.Kp + part * H + c) * x.Mp + (size_t)s * nb + sp0;
+                    if (vec && sp0 + 32 <= nb) {
+                        uint4 *ph = reinterpret_cast<uint4 *>(x.t1h + off);
+                        uint4 *pl = reinterpret_cast<uint4 *>(x.t1l + off);
+#pragma unroll
+                        for (int g = 0; g < 4; ++g) {
+                            uint32_t hw[4], lw[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const float f0 = v[8 * g + 2 * e], f1 = v[8 * g + 2 * e + 1];
+                                const __nv_bfloat16 h0 = __float2bfloat16_rn(f0), h1 = __float2bfloat16_rn(f1);
+                                hw[e] = pack_bf16x2(h0, h1);
+                                lw[e] = pack_bf16x2(__float2bfloat16_rn(f0 - __bfloat162float(h0)),
+                                                    __float2bfloat16_rn(f1 - __bfloat162float(h1)));
+                            }
+                            ph[g] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                            pl[g] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 32; ++e) {
+                            if (sp0 + e >= nb) continue;
+                            const __nv_bfloat16 h = __float2bfloat16_rn(v[e]);
+                            x.t1h[off + e] = h;
+                            x.t1l[off + e] = __float2bfloat16_rn(v[e] - __bfloat162float(h));
+                        }
+                    }
+                }
+            } else {
+                const int s = r_hi, sp = r_lo;
+                const float w = rv ? x.omega[(size_t)q * nb + s] : 0.0f;
+                const float w1 = rv ? x.omega[(size_t)qp * nb + sp] : 0.0f;
+                const float n1 = rv ? x.occ[(size_t)qp * nb + sp] : 0.0f;
+                const bool live = rv && w > 0.0f && w1 > 0.0f;
+                const float wp = w + w1, wm = w - w1;
+                float acc = 0.0f;
+                for (int ci = hf; ok && ci < H / 16; ci += 2) {
+                    const int c0 = ci * 16;
+                    float re[16], im[16];
+                    tmem_ld16(taddr + c0, re);
+                    tmem_ld16(taddr + H + c0, im);
+                    if (!live) continue;
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const float w2 = w2_sm[c0 + k], n2 = n2_sm[c0 + k];
+                        const float dp = wp - w2, dm = wm - w2;
+                        const bool hp = fabsf(dp) < cut, hm = fabsf(dm) < cut;
+                        const float gp = hp ? (n1 - n2) * __expf(-dp * dp * s2i) : 0.0f;
+                        const float gm = hm ? 0.5f * (1.0f + n1 + n2) * __expf(-dm * dm * s2i) : 0.0f;
+                        const float p2 = fmaf(re[k], re[k], im[k] * im[k]);
+                        acc = fmaf(p2 * (gp + gm), iw2_sm[c0 + k], acc);
+                        cnt += (hp || hm) ? 1ull : 0ull;
+                    }
+                }
+                rowsum[buf][hf][row] = live ? acc / w1 : 0.0f;
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[buf]);
+            if (EPI == EPI_PHI) {
+                // both column halves of the row, in a fixed order (the buffer of
+                // this tile parity is rewritten two tiles later, after the next
+                // named barrier)
+                named_sync(1, kEpiWarps * 32);
+                if (hf == 0 && ok && rv) x.rowval[(size_t)a * x.Mp + r] = rowsum[buf][0][row] + rowsum[buf][1][row];
+            }
+        }
+        if (EPI == EPI_PHI) {
+            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+            if (lane == 0 && cnt) atomicAdd(x.allowed, cnt);
+        }
+    }
+    __syncthreads();
+    if (*(volatile int *)&fail_sm) {
+        if (threadIdx.x == 0) {
+            atomicOr(err, 1);
+            // let the copies already issued land before the CTA exits (bounded)
+            mbar_wait(&bfull, 0);
+            for (int st = 0; st < kStages; ++st) {
+                int last = -1;
+                for (int k = st; k < issued; k += kStages) last = k;
+                if (last >= 0) mbar_wait(&afull[st], (last / kStages) & 1);
+            }
+        }
+    }
+    if (warp == 1) {
+        if (lane == 0) mbar_wait(&drain, 0);
+        __syncwarp();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::kTmemCols)
+                     : "memory");
+    }
+}
+
+// Phase-summed contraction over the home index (gather), CTA = (group part,
+// pair in batch), thread = mode s of q:
+//   Y_s(3j + beta, 3k + gamma) = sum over the blocks (i; j Rj; k Rk) of the
+//     atom pair (j, k) of sum_alpha Phi3~[alpha beta gamma] eps_{3i+alpha}(q s)
+//     chi(q', Rj) conj(chi(q'', Rk)),
+// in FP32; every block is read once per warp (same address in all lanes)
+// and serves 32 modes.  Y is written to A1 as BF16 hi/lo: for a fixed
+// (b, c) the lanes of a warp cover consecutive rows m = c nb + s.
+__global__ void __launch_bounds__(128)
+ycx_gather_kernel(XParams x, TcxGroups g, const float2 *__restrict__ epsT_all,
+                  const float2 *__restrict__ chi_all, int n_rep, __nv_bfloat16 *__restrict__ a1h,
+                  __nv_bfloat16 *__restrict__ a1l) {
+    extern __shared__ float2 chi_sm[];             // chi(q', R), chi(q'', R)
+    const int part = blockIdx.x, a = blockIdx.y;
+    int q, qp, qpp;
+    pair_of(x, a, q, qp, qpp);
+    for (int t = threadIdx.x; t < n_rep; t += blockDim.x) {
+        chi_sm[t] = chi_all[(size_t)qp * n_rep + t];
+        chi_sm[n_rep + t] = chi_all[(size_t)qpp * n_rep + t];
+    }
+    __syncthreads();
+    const int nb = x.nb, s = threadIdx.x;
+    if (s >= nb) return;
+    const float2 *eps = epsT_all + (size_t)q * nb * nb;      // eps(q)(row, s) at row * nb + s
+    const size_t pbase = (size_t)a * x.Kp * x.Mp;
+    for (int gi = g.part_start[part]; gi < g.part_start[part + 1]; ++gi) {
+        const int gr = g.glist[gi];
+        const int2 jk = g.gjk[gr];
+        float2 acc[9];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) acc[t] = make_float2(0.f, 0.f);
+        for (int bl = g.gstart[gr]; bl < g.gstart[gr + 1]; ++bl) {
+            const int4 bi = __ldg(g.blkinfo + bl);
+            const float4 *f4 = reinterpret_cast<const float4 *>(g.fc3 + (size_t)28 * bl);
+            float v[28];
+#pragma unroll
+            for (int t = 0; t < 7; ++t) {
+                const float4 u = __ldg(f4 + t);
+                v[4 * t] = u.x; v[4 * t + 1] = u.y; v[4 * t + 2] = u.z; v[4 * t + 3] = u.w;
+            }
+            const float2 c1 = chi_sm[bi.y], c2 = chi_sm[n_rep + bi.z];
+            const float2 ph = make_float2(c1.x * c2.x + c1.y * c2.y, c1.y * c2.x - c1.x * c2.y);
+            float2 e[3];
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                const float2 u = __ldg(eps + (size_t)(3 * bi.x + t) * nb + s);
+                e[t] = make_float2(u.x * ph.x - u.y * ph.y, u.x * ph.y + u.y * ph.x);
+            }
+            // complex += real * complex as packed FP32x2 FMAs
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                acc[t] = __ffma2_rn(make_float2(v[18 + t], v[18 + t]), e[2], acc[t]);
+                acc[t] = __ffma2_rn(make_float2(v[9 + t], v[9 + t]), e[1], acc[t]);
+                acc[t] = __ffma2_rn(make_float2(v[t], v[t]), e[0], acc[t]);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const int b = 3 * jk.x + t / 3, c = 3 * jk.y + t % 3;
+            const size_t o_re = pbase + (size_t)b * x.Mp + (size_t)c * nb + s;
+            const size_t o_im = o_re + (size_t)x.H * x.Mp;
+            const __nv_bfloat16 hr = __float2bfloat16_rn(acc[t].x), hm = __float2bfloat16_rn(acc[t].y);
+            a1h[o_re] = hr;
+            a1l[o_re] = __float2bfloat16_rn(acc[t].x - __bfloat162float(hr));
+            a1h[o_im] = hm;
+            a1l[o_im] = __float2bfloat16_rn(acc[t].y - __bfloat162float(hm));
+        }
+    }
+}
+
+// B1 (which = 0) and B2 (which = 1) of every q, [nq][2H][2H] K-major, as
+// BF16 pieces: hi + lo, or hi + mid + lo when mid is given.
+__global__ void embed_kernel(int nq, int nb, int H, const double2 *__restrict__ eig, int which,
+                             __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ mid,
+                             __nv_bfloat16 *__restrict__ lo) {
+    const int Kp = 2 * H, BN = 2 * H;
+    const size_t n = (size_t)nq * BN * Kp;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const int q = (int)(t / ((size_t)BN * Kp));
+        const int rem = (int)(t % ((size_t)BN * Kp));
+        const int rw = rem / Kp, k = rem % Kp;
+        const bool im_row = rw >= H, im_col = k >= H;
+        const int sm = rw - (im_row ? H : 0), b = k - (im_col ? H : 0);
+        float v = 0.0f;
+        if (sm < nb && b < nb) {
+            const double2 e = eig[((size_t)q * nb + sm) * nb + b];      // eps(q)(b, sm)
+            if (which == 0) v = (float)(im_row ? (im_col ? e.x : e.y) : (im_col ? -e.y : e.x));
+            else v = (float)(im_row ? (im_col ? e.x : -e.y) : (im_col ? e.y : e.x));
+        }
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        const float r = v - __bfloat162float(h);
+        hi[t] = h;
+        if (mid) {
+            const __nv_bfloat16 m = __float2bfloat16_rn(r);
+            mid[t] = m;
+            lo[t] = __float2bfloat16_rn(r - __bfloat162float(m));
+        } else {
+            lo[t] = __float2bfloat16_rn(r);
+        }
+    }
+}
+
+__global__ void f32_tables_kernel(int n, const double *__restrict__ omega, const double *__restrict__ occ,
+                                  float *__restrict__ wf, float *__restrict__ nf) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) { wf[t] = (float)omega[t]; nf[t] = (float)occ[t]; }
+}
+
+// gacc[q][s] += sum over the batch's pairs of q (in order) of
+// sum_s' rowval[pair][s nb + s']; one warp per mode s, FP32 within a pair
+// (lane-strided sums and a fixed shuffle tree), FP64 across pairs.
+__global__ void rows_reduce_kernel(XParams x, double *__restrict__ gacc) {
+    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    const int nb = x.nb;
+    if (s >= nb) return;
+    double sum = 0.0;
+    int qcur = -1;
+    for (int a = 0; a < x.n_pairs; ++a) {
+        const int q = (int)((x.pair0 + a) / x.nq);
+        if (q != qcur) {
+            if (qcur >= 0 && lane == 0) gacc[(size_t)qcur * nb + s] += sum;
+            sum = 0.0;
+            qcur = q;
+        }
+        const float *rv = x.rowval + (size_t)a * x.Mp + (size_t)s * nb;
+        float v = 0.0f;
+        for (int sp = lane; sp < nb; sp += 32) v += rv[sp];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        sum += (double)v;
+    }
+    if (qcur >= 0 && lane == 0) gacc[(size_t)qcur * nb + s] += sum;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+// 3-D map of BF16 planes [items][rows][inner]: box 64 x box_rows x 1,
+// 128-byte swizzle (64 BF16 = one swizzle row).
+bool make_map3(CUtensorMap *map, const __nv_bfloat16 *ptr, int inner, int rows, int items, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)rows, (cuuint64_t)items};
+    const cuuint64_t strides[2] = {(cuuint64_t)inner * 2, (cuuint64_t)inner * 2 * rows};
+    const cuuint32_t box[3] = {64u, (cuuint32_t)box_rows, 1u};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(ptr), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN, int PB>
+cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, XParams x,
+                        const CUtensorMap *maps, int batch, int tpc, __nv_bfloat16 *a1h, __nv_bfloat16 *a1l,
+                        double *gacc, int *err, cudaStream_t st) {
+    auto k1 = tcx_gemm_kernel<EPI_T, BN, PB>;
+    auto k2 = tcx_gemm_kernel<EPI_PHI, BN, PB>;
+    constexpr int smem = Cfg<BN, PB>::kSmem;
+    cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const int nb = p.nb;
+    const int gthreads = (nb + 31) / 32 * 32;
+    const size_t gsmem = sizeof(float2) * 2 * (size_t)std::max(1, p.n_rep);
+    const int mt = x.Mp / kBM;
+    const int gx = (mt + tpc - 1) / tpc;
+    const long long total = (long long)p.nq * p.nq;
+    for (long long p0 = 0; p0 < total; p0 += batch) {
+        x.pair0 = p0;
+        x.n_pairs = (int)std::min<long long>(batch, total - p0);
+        ycx_gather_kernel<<<dim3(g.n_parts, x.n_pairs), gthreads, gsmem, st>>>(
+            x, g, static_cast<const float2 *>(d.eps_work), static_cast<const float2 *>(d.chi), p.n_rep, a1h, a1l);
+        k1<<<dim3(gx, x.n_pairs), kWsThreads, smem, st>>>(maps[0], maps[1], maps[2], maps[3], maps[4], x, tpc,
+                                                            err);
+        k2<<<dim3(gx, x.n_pairs), kWsThreads, smem, st>>>(maps[5], maps[6], maps[7], maps[8], maps[9], x, tpc,
+                                                            err);
+        rows_reduce_kernel<<<(nb + 3) / 4, 128, 0, st>>>(x, gacc);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int tcx_half(int nb) { return (nb + 31) / 32 * 32; }
+
+int tcx_batch(int nb, int nq, int sm_count) {
+    // pairs per launch: about four GEMM tiles per SM; KALD_TCX_BATCH
+    // overrides (tuning)
+    const long long total = (long long)nq * nq;
+    const int mt = (nb * nb + kBM - 1) / kBM;
+    long long b = std::max(1, 4 * std::max(1, sm_count) / mt);
+    if (const char *env = std::getenv("KALD_TCX_BATCH")) {
+        const long long v = std::atoll(env);
+        if (v > 0) b = v;
+    }
+    return (int)std::max(1LL, std::min(b, total));
+}
+
+int tcx_parts(int n_groups) { return std::max(1, std::min(n_groups, 128)); }
+
+// Longest-processing-time partition of the (j, k) groups over n_parts CTAs
+// (weight = blocks + a constant for the 36 stores of a group).
+void plan_tcx_parts(const HostSystem &h, int n_parts, std::vector<int> &part_start, std::vector<int> &glist) {
+    const int n_groups = (int)h.pair3_j.size();
+    std::vector<int> order(n_groups);
+    for (int gr = 0; gr < n_groups; ++gr) order[gr] = gr;
+    auto weight = [&](int gr) { return h.pair3_start[gr + 1] - h.pair3_start[gr] + 4; };
+    std::stable_sort(order.begin(), order.end(), [&](int u, int v) { return weight(u) > weight(v); });
+    typedef std::pair<long long, int> Load;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int x = 0; x < n_parts; ++x) heap.push(Load(0, x));
+    std::vector<std::vector<int>> parts(n_parts);
+    for (int gr : order) {
+        Load l = heap.top();
+        heap.pop();
+        parts[l.second].push_back(gr);
+        l.first += weight(gr);
+        heap.push(l);
+    }
+    part_start.assign(1, 0);
+    glist.clear();
+    for (int x = 0; x < n_parts; ++x) {
+        glist.insert(glist.end(), parts[x].begin(), parts[x].end());
+        part_start.push_back((int)glist.size());
+    }
+}
+
+size_t tcx_scratch_bytes(int nb, int nq, int batch) {
+    const int H = tcx_half(nb), Kp = 2 * H, BN = 2 * H;
+    const size_t Mp = (size_t)(nb * nb + kBM - 1) / kBM * kBM;
+    const size_t eb = ws_round(sizeof(__nv_bfloat16) * (size_t)nq * BN * Kp);
+    const size_t ab = ws_round(sizeof(__nv_bfloat16) * (size_t)batch * Kp * Mp);
+    return 6 * eb + 4 * ab + 2 * ws_round(sizeof(float) * (size_t)nq * nb) +
+           ws_round(sizeof(float) * (size_t)batch * Mp) + ws_round(sizeof(double) * (size_t)nq * nb);
+}
+
+// Crystal linewidth sums on tensor cores (nb <= 96).  Needs the FP32 prep
+// of launch_lw_prep (eps^T, chi, omega, occ) in d and the group tables g;
+// writes the per-(q, s) sums into d.partial ([nq][1][nb], n_chunks = 1) for
+// launch_lw_finish, the delta-allowed count into d.allowed and bounded-wait
+// failures into err.
+cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups &g, void *scratch, int batch,
+                             int sms, int *err, cudaStream_t st) {
+    const int nb = p.nb, nq = p.nq;
+    if (nb < 1 || nb > 96 || batch < 1 || g.n_parts < 1 || sms < 1) return cudaErrorInvalidValue;
+    const int H = tcx_half(nb), Kp = 2 * H, BN = 2 * H;
+    const int Mp = (nb * nb + kBM - 1) / kBM * kBM;
+    char *b = static_cast<char *>(scratch);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { char *r = b + off; off += ws_round(bytes); return r; };
+    const size_t eb = sizeof(__nv_bfloat16) * (size_t)nq * BN * Kp;
+    auto *b1h = reinterpret_cast<__nv_bfloat16 *>(take(eb));
+    auto *b1m = reinterpret_cast<__nv_bfloat16 *>(take(eb));
+    auto *b1l = reinterpret_cast<__nv_bfloat16 *>(take(eb));
+    auto *b2h = reinterpret_cast<__nv_bfloat16 *>(take(eb));
+    auto *b2m = reinterpret_cast<__nv_bfloat16 *>(take(eb));
+    auto *b2l = reinterpret_cast<__nv_bfloat16 *>(take(eb));
+    const bool three = BN <= 128;          // three pieces of B fit in shared memory
+    const size_t ab = sizeof(__nv_bfloat16) * (size_t)batch * Kp * Mp;
+    auto *a1h = reinterpret_cast<__nv_bfloat16 *>(take(ab));
+    auto *a1l = reinterpret_cast<__nv_bfloat16 *>(take(ab));
+    auto *t1h = reinterpret_cast<__nv_bfloat16 *>(take(ab));
+    auto *t1l = reinterpret_cast<__nv_bfloat16 *>(take(ab));
+    auto *wf = reinterpret_cast<float *>(take(sizeof(float) * (size_t)nq * nb));
+    auto *nf = reinterpret_cast<float *>(take(sizeof(float) * (size_t)nq * nb));
+    auto *rowval = reinterpret_cast<float *>(take(sizeof(float) * (size_t)batch * Mp));
+    auto *gacc = reinterpret_cast<double *>(take(sizeof(double) * (size_t)nq * nb));
+
+    // entries of A1 / T1 that no group or column covers stay zero: clear once
+    cudaError_t e = cudaMemsetAsync(a1h, 0, 4 * ws_round(ab), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(gacc, 0, sizeof(double) * (size_t)nq * nb, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.allowed, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    const int eg = (int)std::min<size_t>(((size_t)nq * BN * Kp + 255) / 256, 4096);
+    embed_kernel<<<eg, 256, 0, st>>>(nq, nb, H, d.eig, 0, b1h, three ? b1m : nullptr, b1l);
+    embed_kernel<<<eg, 256, 0, st>>>(nq, nb, H, d.eig, 1, b2h, three ? b2m : nullptr, b2l);
+    f32_tables_kernel<<<(nq * nb + 255) / 256, 256, 0, st>>>(nq * nb, d.omega, d.occ, wf, nf);
+
+    CUtensorMap maps[10];
+    if (!make_map3(&maps[0], a1h, Mp, Kp, batch, kBK) || !make_map3(&maps[1], a1l, Mp, Kp, batch, kBK) ||
+        !make_map3(&maps[2], b1h, Kp, BN, nq, BN) || !make_map3(&maps[3], b1m, Kp, BN, nq, BN) ||
+        !make_map3(&maps[4], b1l, Kp, BN, nq, BN) ||
+        !make_map3(&maps[5], t1h, Mp, Kp, batch, kBK) || !make_map3(&maps[6], t1l, Mp, Kp, batch, kBK) ||
+        !make_map3(&maps[7], b2h, Kp, BN, nq, BN) || !make_map3(&maps[8], b2m, Kp, BN, nq, BN) ||
+        !make_map3(&maps[9], b2l, Kp, BN, nq, BN))
+        return cudaErrorInvalidValue;
+
+    XParams x;
+    x.nb = nb; x.H = H; x.Kp = Kp; x.Mp = Mp;
+    x.nq = nq; x.mesh0 = p.mesh[0]; x.mesh1 = p.mesh[1]; x.mesh2 = p.mesh[2];
+    x.pair0 = 0; x.n_pairs = 0;
+    x.qfrac = d.qfrac;
+    x.t1h = t1h; x.t1l = t1l;
+    x.omega = wf; x.occ = nf;
+    x.sig2inv = (float)(0.5 / (p.sigma_w * p.sigma_w));
+    x.cut = (float)p.cut_w;
+    x.rowval = rowval;
+    x.allowed = d.allowed;
+    // tiles per GEMM CTA: at most one wave of CTAs per batch (each CTA loads
+    // its B operand once); KALD_TCX_TPC overrides (tuning)
+    const int mt = Mp / kBM;
+    int tpc = (int)std::max<long long>(1, ((long long)mt * batch + sms - 1) / sms);
+    if (const char *env = std::getenv("KALD_TCX_TPC")) {
+        const int v = std::atoi(env);
+        if (v > 0) tpc = v;
+    }
+    tpc = std::min(tpc, mt);
+    switch (BN) {
+        case 64: e = run_batches<64, 3>(p, d, g, x, maps, batch, tpc, a1h, a1l, gacc, err, st); break;
+        case 128: e = run_batches<128, 3>(p, d, g, x, maps, batch, tpc, a1h, a1l, gacc, err, st); break;
+        default: e = run_batches<192, 2>(p, d, g, x, maps, batch, tpc, a1h, a1l, gacc, err, st); break;
+    }
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(d.partial, gacc, sizeof(double) * (size_t)nq * nb, cudaMemcpyDeviceToDevice, st);
+}
+
+}  // namespace kald

@@ -144,6 +144,48 @@ def test_linewidths_c2_sampled_q(k):
     assert tot == 512 ** 2 * 96 ** 3 and 0 < allowed < tot
 
 
+@pytest.mark.parametrize("case", ["binary3", "binary_random", "C5_mesh6", "fcc32_mesh2"])
+def test_crystal_bf16split_tensor_cores(k, case):
+    """Crystal linewidths with the two dense contractions on tcgen05 (BF16
+    hi+lo, three MMAs per product, FP32 accumulation).  The delta windows are
+    decided in FP32 as in the FP32 CUDA-core path, so the allowed counts
+    agree exactly; gamma within 1e-5 of the FP64 oracle (split precision)."""
+    kk, ctx = k
+    if case == "fcc32_mesh2":
+        w = ki.Workload("fcc32", [ki.fcc_supercell_system(2, seed=2)], (2, 2, 2), 300.0, 0.1, 3.0)
+    else:
+        w = _lw_case(case)
+    s = w.systems[0]
+    nu_o, eig_o = ph.phonons(s, w.mesh)
+    g_o = an.linewidths(s, w.mesh, nu_o, eig_o, w.T, w.sigma_thz, w.n_sigma)
+    g, (tot, allowed) = kk.kald_linewidths(ctx, s, w.mesh, nu_o, eig_o, _opts(kk, w, "bf16split"))
+    _, (_, allowed32) = kk.kald_linewidths(ctx, s, w.mesh, nu_o, eig_o, _opts(kk, w, "fp32"))
+    g = g.reshape(g_o.shape)
+    assert tot == w.n_q ** 2 * s.n_branches ** 3
+    assert allowed == allowed32
+    assert np.all(g[nu_o <= 0.01] == 0.0)
+    err = _rel(g, g_o, 1e-6 * g_o.max())
+    print(f"{case}: bf16 split gamma max rel err {err:.3e}")
+    assert err < 1e-5
+
+
+def test_crystal_bf16split_c2_sampled_q(k):
+    """The 32-atom / 8^3 workload on tensor cores in the benchmark's launch
+    configuration, checked at sampled q-points against the oracle."""
+    kk, ctx = k
+    w = ki.c2()
+    s = w.systems[0]
+    nu_o, eig_o = ph.phonons(s, w.mesh)
+    g, (tot, allowed) = kk.kald_linewidths(ctx, s, w.mesh, nu_o, eig_o, _opts(kk, w, "bf16split"))
+    g = g.reshape(nu_o.shape)
+    qs = [1, 137]
+    g_o = an.linewidths(s, w.mesh, nu_o, eig_o, w.T, w.sigma_thz, w.n_sigma, q_list=qs)
+    err = _rel(g[qs], g_o, 1e-6 * g_o.max())
+    print(f"C2 bf16 split gamma max rel err {err:.3e}")
+    assert err < 1e-5
+    assert tot == 512 ** 2 * 96 ** 3 and 0 < allowed < tot
+
+
 # ---------------------------------------------------------------- kappa
 def test_kappa_rta_matches_oracle(k):
     kk, ctx = k
