@@ -20,9 +20,10 @@
 //   with the same FP32 window test and Gaussian as the CUDA-core kernel.
 // A1 and T1 are stored MN-major (rows contiguous), so the gather (one thread
 // per mode s) and the GEMM1 epilogue (32 consecutive s' per thread) write
-// whole runs; the B operands are K-major.  GEMM2's epilogue writes one FP32
-// sum per row (s, s'); a reduction kernel adds them per mode in a fixed
-// order (FP32 within a pair, FP64 across pairs).
+// whole runs; the B operands are K-major.  GEMM2's epilogue sums each mode's
+// rows (s, s') of a tile in a fixed order (FP32) into one of two slots per
+// (pair, mode); a mode spans at most two tiles (nb <= 96).  Once every pair
+// of q is done, a reduction adds the slots over q' in order in FP64.
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -66,7 +67,9 @@ struct XParams {
     const float *omega;       // [nq][nb] rad/ps (0 = masked)
     const float *occ;         // [nq][nb]
     float sig2inv, cut;
-    float *rowval;            // GEMM2 output [pairs][Mp]: sum over s'' of row (s, s')
+    int n_slices;             // q-slices of slots (a batch spans fewer q values)
+    float *slots;             // GEMM2 output [n_slices][nq (q')][nb][2]: per-mode sums over the
+                              // mode's rows in its first tile (0) and in the next tile (1)
     unsigned long long *allowed;
 };
 
@@ -316,11 +319,30 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[buf]);
             if (EPI == EPI_PHI) {
-                // both column halves of the row, in a fixed order (the buffer of
-                // this tile parity is rewritten two tiles later, after the next
-                // named barrier)
+                // per-mode sums over the tile's rows: mode segment j goes to warp
+                // 4 + (j % 4), lanes take rows 32 apart, then a fixed shuffle tree.
+                // (The buffer of this tile parity is rewritten two tiles later,
+                // after the next named barrier.)
                 named_sync(1, kEpiWarps * 32);
-                if (hf == 0 && ok && rv) x.rowval[(size_t)a * x.Mp + r] = rowsum[buf][0][row] + rowsum[buf][1][row];
+                if (hf == 0 && ok) {
+                    const int rt = tile * kBM, re = min(nb * nb, rt + kBM);
+                    if (rt < re) {
+                        const int s_lo = rt / nb, s_hi = (re - 1) / nb;
+                        float *sl = x.slots + ((size_t)(q % x.n_slices) * x.nq + qp) * nb * 2;
+                        for (int sm = s_lo + qd; sm <= s_hi; sm += 4) {
+                            const int b0 = max(rt, sm * nb), b1 = min(re, (sm + 1) * nb);
+                            float v = 0.0f;
+                            for (int rr = b0 + lane; rr < b1; rr += 32)
+                                v += rowsum[buf][0][rr - rt] + rowsum[buf][1][rr - rt];
+                            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                            if (lane == 0) {
+                                const bool first = b0 == sm * nb;
+                                sl[2 * sm + (first ? 0 : 1)] = v;
+                                if (first && b1 == (sm + 1) * nb) sl[2 * sm + 1] = 0.0f;   // no continuation
+                            }
+                        }
+                    }
+                }
             }
         }
         if (EPI == EPI_PHI) {
@@ -351,36 +373,42 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
 }
 
 // Phase-summed contraction over the home index (gather), CTA = (group part,
-// pair in batch), thread = mode s of q:
+// P consecutive pairs of the batch with the same q), thread = mode s of q:
 //   Y_s(3j + beta, 3k + gamma) = sum over the blocks (i; j Rj; k Rk) of the
 //     atom pair (j, k) of sum_alpha Phi3~[alpha beta gamma] eps_{3i+alpha}(q s)
 //     chi(q', Rj) conj(chi(q'', Rk)),
-// in FP32; every block is read once per warp (same address in all lanes)
-// and serves 32 modes.  Y is written to A1 as BF16 hi/lo: for a fixed
-// (b, c) the lanes of a warp cover consecutive rows m = c nb + s.
+// in FP32; a block (the same address in all lanes) and eps(q) are read once
+// for the P pairs, which differ only in the phase.  Y is written to A1 as
+// BF16 hi/lo: for a fixed (b, c) the lanes of a warp cover consecutive rows
+// m = c nb + s.
+template <int P>
 __global__ void __launch_bounds__(128)
 ycx_gather_kernel(XParams x, TcxGroups g, const float2 *__restrict__ epsT_all,
                   const float2 *__restrict__ chi_all, int n_rep, __nv_bfloat16 *__restrict__ a1h,
                   __nv_bfloat16 *__restrict__ a1l) {
-    extern __shared__ float2 chi_sm[];             // chi(q', R), chi(q'', R)
-    const int part = blockIdx.x, a = blockIdx.y;
-    int q, qp, qpp;
-    pair_of(x, a, q, qp, qpp);
-    for (int t = threadIdx.x; t < n_rep; t += blockDim.x) {
-        chi_sm[t] = chi_all[(size_t)qp * n_rep + t];
-        chi_sm[n_rep + t] = chi_all[(size_t)qpp * n_rep + t];
+    extern __shared__ float2 chi_sm[];             // [P][chi(q', R), chi(q'', R)]
+    const int part = blockIdx.x, a0 = blockIdx.y * P;
+    int q = 0;
+    for (int p = 0; p < P; ++p) {
+        int qp, qpp;
+        pair_of(x, a0 + p, q, qp, qpp);
+        for (int t = threadIdx.x; t < n_rep; t += blockDim.x) {
+            chi_sm[(2 * p) * n_rep + t] = chi_all[(size_t)qp * n_rep + t];
+            chi_sm[(2 * p + 1) * n_rep + t] = chi_all[(size_t)qpp * n_rep + t];
+        }
     }
     __syncthreads();
     const int nb = x.nb, s = threadIdx.x;
     if (s >= nb) return;
     const float2 *eps = epsT_all + (size_t)q * nb * nb;      // eps(q)(row, s) at row * nb + s
-    const size_t pbase = (size_t)a * x.Kp * x.Mp;
     for (int gi = g.part_start[part]; gi < g.part_start[part + 1]; ++gi) {
         const int gr = g.glist[gi];
         const int2 jk = g.gjk[gr];
-        float2 acc[9];
+        float2 acc[P][9];
 #pragma unroll
-        for (int t = 0; t < 9; ++t) acc[t] = make_float2(0.f, 0.f);
+        for (int p = 0; p < P; ++p)
+#pragma unroll
+            for (int t = 0; t < 9; ++t) acc[p][t] = make_float2(0.f, 0.f);
         for (int bl = g.gstart[gr]; bl < g.gstart[gr + 1]; ++bl) {
             const int4 bi = __ldg(g.blkinfo + bl);
             const float4 *f4 = reinterpret_cast<const float4 *>(g.fc3 + (size_t)28 * bl);
@@ -390,32 +418,40 @@ ycx_gather_kernel(XParams x, TcxGroups g, const float2 *__restrict__ epsT_all,
                 const float4 u = __ldg(f4 + t);
                 v[4 * t] = u.x; v[4 * t + 1] = u.y; v[4 * t + 2] = u.z; v[4 * t + 3] = u.w;
             }
-            const float2 c1 = chi_sm[bi.y], c2 = chi_sm[n_rep + bi.z];
-            const float2 ph = make_float2(c1.x * c2.x + c1.y * c2.y, c1.y * c2.x - c1.x * c2.y);
-            float2 e[3];
+            float2 u[3];
 #pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                const float2 u = __ldg(eps + (size_t)(3 * bi.x + t) * nb + s);
-                e[t] = make_float2(u.x * ph.x - u.y * ph.y, u.x * ph.y + u.y * ph.x);
-            }
-            // complex += real * complex as packed FP32x2 FMAs
+            for (int t = 0; t < 3; ++t) u[t] = __ldg(eps + (size_t)(3 * bi.x + t) * nb + s);
 #pragma unroll
-            for (int t = 0; t < 9; ++t) {
-                acc[t] = __ffma2_rn(make_float2(v[18 + t], v[18 + t]), e[2], acc[t]);
-                acc[t] = __ffma2_rn(make_float2(v[9 + t], v[9 + t]), e[1], acc[t]);
-                acc[t] = __ffma2_rn(make_float2(v[t], v[t]), e[0], acc[t]);
+            for (int p = 0; p < P; ++p) {
+                const float2 c1 = chi_sm[(2 * p) * n_rep + bi.y], c2 = chi_sm[(2 * p + 1) * n_rep + bi.z];
+                const float2 ph = make_float2(c1.x * c2.x + c1.y * c2.y, c1.y * c2.x - c1.x * c2.y);
+                float2 e[3];
+#pragma unroll
+                for (int t = 0; t < 3; ++t)
+                    e[t] = make_float2(u[t].x * ph.x - u[t].y * ph.y, u[t].x * ph.y + u[t].y * ph.x);
+                // complex += real * complex as packed FP32x2 FMAs
+#pragma unroll
+                for (int t = 0; t < 9; ++t) {
+                    acc[p][t] = __ffma2_rn(make_float2(v[18 + t], v[18 + t]), e[2], acc[p][t]);
+                    acc[p][t] = __ffma2_rn(make_float2(v[9 + t], v[9 + t]), e[1], acc[p][t]);
+                    acc[p][t] = __ffma2_rn(make_float2(v[t], v[t]), e[0], acc[p][t]);
+                }
             }
         }
 #pragma unroll
-        for (int t = 0; t < 9; ++t) {
-            const int b = 3 * jk.x + t / 3, c = 3 * jk.y + t % 3;
-            const size_t o_re = pbase + (size_t)b * x.Mp + (size_t)c * nb + s;
-            const size_t o_im = o_re + (size_t)x.H * x.Mp;
-            const __nv_bfloat16 hr = __float2bfloat16_rn(acc[t].x), hm = __float2bfloat16_rn(acc[t].y);
-            a1h[o_re] = hr;
-            a1l[o_re] = __float2bfloat16_rn(acc[t].x - __bfloat162float(hr));
-            a1h[o_im] = hm;
-            a1l[o_im] = __float2bfloat16_rn(acc[t].y - __bfloat162float(hm));
+        for (int p = 0; p < P; ++p) {
+            const size_t pbase = (size_t)(a0 + p) * x.Kp * x.Mp;
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                const int b = 3 * jk.x + t / 3, c = 3 * jk.y + t % 3;
+                const size_t o_re = pbase + (size_t)b * x.Mp + (size_t)c * nb + s;
+                const size_t o_im = o_re + (size_t)x.H * x.Mp;
+                const __nv_bfloat16 hr = __float2bfloat16_rn(acc[p][t].x), hm = __float2bfloat16_rn(acc[p][t].y);
+                a1h[o_re] = hr;
+                a1l[o_re] = __float2bfloat16_rn(acc[p][t].x - __bfloat162float(hr));
+                a1h[o_im] = hm;
+                a1l[o_im] = __float2bfloat16_rn(acc[p][t].y - __bfloat162float(hm));
+            }
         }
     }
 }
@@ -459,29 +495,21 @@ __global__ void f32_tables_kernel(int n, const double *__restrict__ omega, const
     if (t < n) { wf[t] = (float)omega[t]; nf[t] = (float)occ[t]; }
 }
 
-// gacc[q][s] += sum over the batch's pairs of q (in order) of
-// sum_s' rowval[pair][s nb + s']; one warp per mode s, FP32 within a pair
-// (lane-strided sums and a fixed shuffle tree), FP64 across pairs.
-__global__ void rows_reduce_kernel(XParams x, double *__restrict__ gacc) {
-    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+// gacc[q][s] = sum over q' in order of both slots of (q, q', s), FP64, for
+// the completed q in [q0, q1).
+__global__ void slots_reduce_kernel(XParams x, int q0, int q1, double *__restrict__ gacc) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int nb = x.nb;
-    if (s >= nb) return;
+    if (t >= (q1 - q0) * nb) return;
+    const int q = q0 + t / nb, s = t - (t / nb) * nb;
+    const float2 *sl = reinterpret_cast<const float2 *>(x.slots) + (size_t)(q % x.n_slices) * x.nq * nb + s;
     double sum = 0.0;
-    int qcur = -1;
-    for (int a = 0; a < x.n_pairs; ++a) {
-        const int q = (int)((x.pair0 + a) / x.nq);
-        if (q != qcur) {
-            if (qcur >= 0 && lane == 0) gacc[(size_t)qcur * nb + s] += sum;
-            sum = 0.0;
-            qcur = q;
-        }
-        const float *rv = x.rowval + (size_t)a * x.Mp + (size_t)s * nb;
-        float v = 0.0f;
-        for (int sp = lane; sp < nb; sp += 32) v += rv[sp];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        sum += (double)v;
+#pragma unroll 4
+    for (int qp = 0; qp < x.nq; ++qp) {
+        const float2 v = sl[(size_t)qp * nb];
+        sum += (double)v.x + (double)v.y;
     }
-    if (qcur >= 0 && lane == 0) gacc[(size_t)qcur * nb + s] += sum;
+    gacc[(size_t)q * nb + s] = sum;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -529,16 +557,38 @@ cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, X
     const int mt = x.Mp / kBM;
     const int gx = (mt + tpc - 1) / tpc;
     const long long total = (long long)p.nq * p.nq;
+    // pairs per gather CTA: a divisor of nq and of the batch, so that the
+    // CTA's pairs share q (every batch starts at a multiple of the batch)
+    int gp = 1;
+    for (int c = 4; c > 1; c /= 2)
+        if (p.nq % c == 0 && batch % c == 0) { gp = c; break; }
+    if (const char *env = std::getenv("KALD_TCX_GP")) {
+        const int v = std::atoi(env);
+        if (v == 1 || ((v == 2 || v == 4) && p.nq % v == 0 && batch % v == 0)) gp = v;
+    }
     for (long long p0 = 0; p0 < total; p0 += batch) {
         x.pair0 = p0;
         x.n_pairs = (int)std::min<long long>(batch, total - p0);
-        ycx_gather_kernel<<<dim3(g.n_parts, x.n_pairs), gthreads, gsmem, st>>>(
-            x, g, static_cast<const float2 *>(d.eps_work), static_cast<const float2 *>(d.chi), p.n_rep, a1h, a1l);
+        const float2 *ew = static_cast<const float2 *>(d.eps_work), *cw = static_cast<const float2 *>(d.chi);
+        if (gp == 4)
+            ycx_gather_kernel<4><<<dim3(g.n_parts, x.n_pairs / 4), gthreads, 4 * gsmem, st>>>(x, g, ew, cw, p.n_rep,
+                                                                                               a1h, a1l);
+        else if (gp == 2)
+            ycx_gather_kernel<2><<<dim3(g.n_parts, x.n_pairs / 2), gthreads, 2 * gsmem, st>>>(x, g, ew, cw, p.n_rep,
+                                                                                               a1h, a1l);
+        else
+            ycx_gather_kernel<1><<<dim3(g.n_parts, x.n_pairs), gthreads, gsmem, st>>>(x, g, ew, cw, p.n_rep, a1h,
+                                                                                      a1l);
         k1<<<dim3(gx, x.n_pairs), kWsThreads, smem, st>>>(maps[0], maps[1], maps[2], maps[3], maps[4], x, tpc,
                                                             err);
         k2<<<dim3(gx, x.n_pairs), kWsThreads, smem, st>>>(maps[5], maps[6], maps[7], maps[8], maps[9], x, tpc,
                                                             err);
-        rows_reduce_kernel<<<(nb + 3) / 4, 128, 0, st>>>(x, gacc);
+        // q values completed by this batch
+        const int qa = (int)(p0 / p.nq), qb = (int)((p0 + x.n_pairs) / p.nq);
+        if (qb > qa) {
+            const int n = (qb - qa) * nb;
+            slots_reduce_kernel<<<(n + 127) / 128, 128, 0, st>>>(x, qa, qb, gacc);
+        }
     }
     return cudaGetLastError();
 }
@@ -547,12 +597,17 @@ cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, X
 
 int tcx_half(int nb) { return (nb + 31) / 32 * 32; }
 
+// q-slices of the slot buffer: a batch touches at most ceil(batch / nq) + 1
+// values of q, and a slice is reused only after its q was reduced.
+static int tcx_slices(int nq, int batch) { return (batch + nq - 1) / nq + 1; }
+
 int tcx_batch(int nb, int nq, int sm_count) {
-    // pairs per launch: about four GEMM tiles per SM; KALD_TCX_BATCH
-    // overrides (tuning)
+    // pairs per launch: about eight GEMM tiles per SM, a multiple of 4 (the
+    // gather takes up to 4 pairs per CTA); KALD_TCX_BATCH overrides (tuning)
     const long long total = (long long)nq * nq;
     const int mt = (nb * nb + kBM - 1) / kBM;
-    long long b = std::max(1, 4 * std::max(1, sm_count) / mt);
+    long long b = std::max(1, 8 * std::max(1, sm_count) / mt);
+    if (b >= 4) b = b / 4 * 4;
     if (const char *env = std::getenv("KALD_TCX_BATCH")) {
         const long long v = std::atoll(env);
         if (v > 0) b = v;
@@ -595,7 +650,8 @@ size_t tcx_scratch_bytes(int nb, int nq, int batch) {
     const size_t eb = ws_round(sizeof(__nv_bfloat16) * (size_t)nq * BN * Kp);
     const size_t ab = ws_round(sizeof(__nv_bfloat16) * (size_t)batch * Kp * Mp);
     return 6 * eb + 4 * ab + 2 * ws_round(sizeof(float) * (size_t)nq * nb) +
-           ws_round(sizeof(float) * (size_t)batch * Mp) + ws_round(sizeof(double) * (size_t)nq * nb);
+           ws_round(sizeof(float) * 2 * (size_t)tcx_slices(nq, batch) * nq * nb) +
+           ws_round(sizeof(double) * (size_t)nq * nb);
 }
 
 // Crystal linewidth sums on tensor cores (nb <= 96).  Needs the FP32 prep
@@ -627,7 +683,8 @@ cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups 
     auto *t1l = reinterpret_cast<__nv_bfloat16 *>(take(ab));
     auto *wf = reinterpret_cast<float *>(take(sizeof(float) * (size_t)nq * nb));
     auto *nf = reinterpret_cast<float *>(take(sizeof(float) * (size_t)nq * nb));
-    auto *rowval = reinterpret_cast<float *>(take(sizeof(float) * (size_t)batch * Mp));
+    const int n_slices = tcx_slices(nq, batch);
+    auto *slots = reinterpret_cast<float *>(take(sizeof(float) * 2 * (size_t)n_slices * nq * nb));
     auto *gacc = reinterpret_cast<double *>(take(sizeof(double) * (size_t)nq * nb));
 
     // entries of A1 / T1 that no group or column covers stay zero: clear once
@@ -659,7 +716,8 @@ cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups 
     x.omega = wf; x.occ = nf;
     x.sig2inv = (float)(0.5 / (p.sigma_w * p.sigma_w));
     x.cut = (float)p.cut_w;
-    x.rowval = rowval;
+    x.n_slices = n_slices;
+    x.slots = slots;
     x.allowed = d.allowed;
     // tiles per GEMM CTA: at most one wave of CTAs per batch (each CTA loads
     // its B operand once); KALD_TCX_TPC overrides (tuning)
