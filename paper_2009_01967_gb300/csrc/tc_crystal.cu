@@ -541,10 +541,24 @@ bool make_map3(CUtensorMap *map, const __nv_bfloat16 *ptr, int inner, int rows, 
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Pairs of one lane (stream) of the batched pipeline: its A1 / T1 planes
+// and tensor maps.
+struct Lane {
+    cudaStream_t st;
+    cudaEvent_t done[2];           // after GEMM2 of the lane's batches, alternately
+    XParams x;
+    CUtensorMap maps[10];          // A1 hi/lo, B1 h/m/l, T1 hi/lo, B2 h/m/l
+    __nv_bfloat16 *a1h, *a1l;
+};
+
+// Batches alternate between two lanes, so that one batch's gather (CUDA
+// cores) can run beside the other's GEMMs (tensor cores); a q is reduced on
+// the lane whose batch completes it, after the other lane's latest batch.
+// Batch i starts only after batch i - 3 (the other lane) has finished, which
+// bounds the q values in flight (see tcx_slices).
 template <int BN, int PB>
-cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, XParams x,
-                        const CUtensorMap *maps, int batch, int tpc, __nv_bfloat16 *a1h, __nv_bfloat16 *a1l,
-                        double *gacc, int *err, cudaStream_t st) {
+cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, Lane *lanes, int batch, int tpc,
+                        double *gacc, int *err) {
     auto k1 = tcx_gemm_kernel<EPI_T, BN, PB>;
     auto k2 = tcx_gemm_kernel<EPI_PHI, BN, PB>;
     constexpr int smem = Cfg<BN, PB>::kSmem;
@@ -554,7 +568,7 @@ cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, X
     const int nb = p.nb;
     const int gthreads = (nb + 31) / 32 * 32;
     const size_t gsmem = sizeof(float2) * 2 * (size_t)std::max(1, p.n_rep);
-    const int mt = x.Mp / kBM;
+    const int mt = lanes[0].x.Mp / kBM;
     const int gx = (mt + tpc - 1) / tpc;
     const long long total = (long long)p.nq * p.nq;
     // pairs per gather CTA: a divisor of nq and of the batch, so that the
@@ -566,28 +580,42 @@ cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, X
         const int v = std::atoi(env);
         if (v == 1 || ((v == 2 || v == 4) && p.nq % v == 0 && batch % v == 0)) gp = v;
     }
-    for (long long p0 = 0; p0 < total; p0 += batch) {
+    const float2 *ew = static_cast<const float2 *>(d.eps_work), *cw = static_cast<const float2 *>(d.chi);
+    long long i = 0;
+    for (long long p0 = 0; p0 < total; p0 += batch, ++i) {
+        Lane &L = lanes[i & 1];
+        const Lane &O = lanes[(i & 1) ^ 1];
+        if (i >= 3) {
+            e = cudaStreamWaitEvent(L.st, O.done[((i - 3) >> 1) & 1], 0);
+            if (e != cudaSuccess) return e;
+        }
+        XParams x = L.x;
         x.pair0 = p0;
         x.n_pairs = (int)std::min<long long>(batch, total - p0);
-        const float2 *ew = static_cast<const float2 *>(d.eps_work), *cw = static_cast<const float2 *>(d.chi);
         if (gp == 4)
-            ycx_gather_kernel<4><<<dim3(g.n_parts, x.n_pairs / 4), gthreads, 4 * gsmem, st>>>(x, g, ew, cw, p.n_rep,
-                                                                                               a1h, a1l);
+            ycx_gather_kernel<4><<<dim3(g.n_parts, x.n_pairs / 4), gthreads, 4 * gsmem, L.st>>>(
+                x, g, ew, cw, p.n_rep, L.a1h, L.a1l);
         else if (gp == 2)
-            ycx_gather_kernel<2><<<dim3(g.n_parts, x.n_pairs / 2), gthreads, 2 * gsmem, st>>>(x, g, ew, cw, p.n_rep,
-                                                                                               a1h, a1l);
+            ycx_gather_kernel<2><<<dim3(g.n_parts, x.n_pairs / 2), gthreads, 2 * gsmem, L.st>>>(
+                x, g, ew, cw, p.n_rep, L.a1h, L.a1l);
         else
-            ycx_gather_kernel<1><<<dim3(g.n_parts, x.n_pairs), gthreads, gsmem, st>>>(x, g, ew, cw, p.n_rep, a1h,
-                                                                                      a1l);
-        k1<<<dim3(gx, x.n_pairs), kWsThreads, smem, st>>>(maps[0], maps[1], maps[2], maps[3], maps[4], x, tpc,
-                                                            err);
-        k2<<<dim3(gx, x.n_pairs), kWsThreads, smem, st>>>(maps[5], maps[6], maps[7], maps[8], maps[9], x, tpc,
-                                                            err);
+            ycx_gather_kernel<1><<<dim3(g.n_parts, x.n_pairs), gthreads, gsmem, L.st>>>(x, g, ew, cw, p.n_rep,
+                                                                                        L.a1h, L.a1l);
+        k1<<<dim3(gx, x.n_pairs), kWsThreads, smem, L.st>>>(L.maps[0], L.maps[1], L.maps[2], L.maps[3], L.maps[4],
+                                                              x, tpc, err);
+        k2<<<dim3(gx, x.n_pairs), kWsThreads, smem, L.st>>>(L.maps[5], L.maps[6], L.maps[7], L.maps[8], L.maps[9],
+                                                              x, tpc, err);
+        e = cudaEventRecord(L.done[(i >> 1) & 1], L.st);
+        if (e != cudaSuccess) return e;
         // q values completed by this batch
         const int qa = (int)(p0 / p.nq), qb = (int)((p0 + x.n_pairs) / p.nq);
         if (qb > qa) {
+            if (i > 0) {
+                e = cudaStreamWaitEvent(L.st, O.done[((i - 1) >> 1) & 1], 0);
+                if (e != cudaSuccess) return e;
+            }
             const int n = (qb - qa) * nb;
-            slots_reduce_kernel<<<(n + 127) / 128, 128, 0, st>>>(x, qa, qb, gacc);
+            slots_reduce_kernel<<<(n + 127) / 128, 128, 0, L.st>>>(x, qa, qb, gacc);
         }
     }
     return cudaGetLastError();
@@ -597,16 +625,18 @@ cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, X
 
 int tcx_half(int nb) { return (nb + 31) / 32 * 32; }
 
-// q-slices of the slot buffer: a batch touches at most ceil(batch / nq) + 1
-// values of q, and a slice is reused only after its q was reduced.
-static int tcx_slices(int nq, int batch) { return (batch + nq - 1) / nq + 1; }
+// q-slices of the slot buffer: the batches that may run at once (k+1..k+3
+// while the q completed by batch k waits for its reduction) touch at most
+// ceil(4 batch / nq) + 1 values of q; a slice is reused only after its q was
+// reduced.
+static int tcx_slices(int nq, int batch) { return (4 * batch + nq - 1) / nq + 2; }
 
 int tcx_batch(int nb, int nq, int sm_count) {
-    // pairs per launch: about eight GEMM tiles per SM, a multiple of 4 (the
+    // pairs per launch: about sixteen GEMM tiles per SM, a multiple of 4 (the
     // gather takes up to 4 pairs per CTA); KALD_TCX_BATCH overrides (tuning)
     const long long total = (long long)nq * nq;
     const int mt = (nb * nb + kBM - 1) / kBM;
-    long long b = std::max(1, 8 * std::max(1, sm_count) / mt);
+    long long b = std::max(1, 16 * std::max(1, sm_count) / mt);
     if (b >= 4) b = b / 4 * 4;
     if (const char *env = std::getenv("KALD_TCX_BATCH")) {
         const long long v = std::atoll(env);
@@ -649,7 +679,7 @@ size_t tcx_scratch_bytes(int nb, int nq, int batch) {
     const size_t Mp = (size_t)(nb * nb + kBM - 1) / kBM * kBM;
     const size_t eb = ws_round(sizeof(__nv_bfloat16) * (size_t)nq * BN * Kp);
     const size_t ab = ws_round(sizeof(__nv_bfloat16) * (size_t)batch * Kp * Mp);
-    return 6 * eb + 4 * ab + 2 * ws_round(sizeof(float) * (size_t)nq * nb) +
+    return 6 * eb + 8 * ab + 2 * ws_round(sizeof(float) * (size_t)nq * nb) +
            ws_round(sizeof(float) * 2 * (size_t)tcx_slices(nq, batch) * nq * nb) +
            ws_round(sizeof(double) * (size_t)nq * nb);
 }
@@ -677,10 +707,9 @@ cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups 
     auto *b2l = reinterpret_cast<__nv_bfloat16 *>(take(eb));
     const bool three = BN <= 128;          // three pieces of B fit in shared memory
     const size_t ab = sizeof(__nv_bfloat16) * (size_t)batch * Kp * Mp;
-    auto *a1h = reinterpret_cast<__nv_bfloat16 *>(take(ab));
-    auto *a1l = reinterpret_cast<__nv_bfloat16 *>(take(ab));
-    auto *t1h = reinterpret_cast<__nv_bfloat16 *>(take(ab));
-    auto *t1l = reinterpret_cast<__nv_bfloat16 *>(take(ab));
+    __nv_bfloat16 *pl[2][4];                       // per lane: A1 hi, A1 lo, T1 hi, T1 lo
+    for (int l = 0; l < 2; ++l)
+        for (int k = 0; k < 4; ++k) pl[l][k] = reinterpret_cast<__nv_bfloat16 *>(take(ab));
     auto *wf = reinterpret_cast<float *>(take(sizeof(float) * (size_t)nq * nb));
     auto *nf = reinterpret_cast<float *>(take(sizeof(float) * (size_t)nq * nb));
     const int n_slices = tcx_slices(nq, batch);
@@ -688,7 +717,7 @@ cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups 
     auto *gacc = reinterpret_cast<double *>(take(sizeof(double) * (size_t)nq * nb));
 
     // entries of A1 / T1 that no group or column covers stay zero: clear once
-    cudaError_t e = cudaMemsetAsync(a1h, 0, 4 * ws_round(ab), st);
+    cudaError_t e = cudaMemsetAsync(pl[0][0], 0, 8 * ws_round(ab), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(gacc, 0, sizeof(double) * (size_t)nq * nb, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.allowed, 0, sizeof(unsigned long long), st);
@@ -698,27 +727,32 @@ cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups 
     embed_kernel<<<eg, 256, 0, st>>>(nq, nb, H, d.eig, 1, b2h, three ? b2m : nullptr, b2l);
     f32_tables_kernel<<<(nq * nb + 255) / 256, 256, 0, st>>>(nq * nb, d.omega, d.occ, wf, nf);
 
-    CUtensorMap maps[10];
-    if (!make_map3(&maps[0], a1h, Mp, Kp, batch, kBK) || !make_map3(&maps[1], a1l, Mp, Kp, batch, kBK) ||
-        !make_map3(&maps[2], b1h, Kp, BN, nq, BN) || !make_map3(&maps[3], b1m, Kp, BN, nq, BN) ||
-        !make_map3(&maps[4], b1l, Kp, BN, nq, BN) ||
-        !make_map3(&maps[5], t1h, Mp, Kp, batch, kBK) || !make_map3(&maps[6], t1l, Mp, Kp, batch, kBK) ||
-        !make_map3(&maps[7], b2h, Kp, BN, nq, BN) || !make_map3(&maps[8], b2m, Kp, BN, nq, BN) ||
-        !make_map3(&maps[9], b2l, Kp, BN, nq, BN))
-        return cudaErrorInvalidValue;
-
     XParams x;
     x.nb = nb; x.H = H; x.Kp = Kp; x.Mp = Mp;
     x.nq = nq; x.mesh0 = p.mesh[0]; x.mesh1 = p.mesh[1]; x.mesh2 = p.mesh[2];
     x.pair0 = 0; x.n_pairs = 0;
     x.qfrac = d.qfrac;
-    x.t1h = t1h; x.t1l = t1l;
+    x.t1h = nullptr; x.t1l = nullptr;
     x.omega = wf; x.occ = nf;
     x.sig2inv = (float)(0.5 / (p.sigma_w * p.sigma_w));
     x.cut = (float)p.cut_w;
     x.n_slices = n_slices;
     x.slots = slots;
     x.allowed = d.allowed;
+    Lane lanes[2];
+    for (int l = 0; l < 2; ++l) {
+        Lane &L = lanes[l];
+        L.x = x;
+        L.a1h = pl[l][0]; L.a1l = pl[l][1];
+        L.x.t1h = pl[l][2]; L.x.t1l = pl[l][3];
+        if (!make_map3(&L.maps[0], pl[l][0], Mp, Kp, batch, kBK) ||
+            !make_map3(&L.maps[1], pl[l][1], Mp, Kp, batch, kBK) || !make_map3(&L.maps[2], b1h, Kp, BN, nq, BN) ||
+            !make_map3(&L.maps[3], b1m, Kp, BN, nq, BN) || !make_map3(&L.maps[4], b1l, Kp, BN, nq, BN) ||
+            !make_map3(&L.maps[5], pl[l][2], Mp, Kp, batch, kBK) ||
+            !make_map3(&L.maps[6], pl[l][3], Mp, Kp, batch, kBK) || !make_map3(&L.maps[7], b2h, Kp, BN, nq, BN) ||
+            !make_map3(&L.maps[8], b2m, Kp, BN, nq, BN) || !make_map3(&L.maps[9], b2l, Kp, BN, nq, BN))
+            return cudaErrorInvalidValue;
+    }
     // tiles per GEMM CTA: at most one wave of CTAs per batch (each CTA loads
     // its B operand once); KALD_TCX_TPC overrides (tuning)
     const int mt = Mp / kBM;
@@ -728,11 +762,30 @@ cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups 
         if (v > 0) tpc = v;
     }
     tpc = std::min(tpc, mt);
-    switch (BN) {
-        case 64: e = run_batches<64, 3>(p, d, g, x, maps, batch, tpc, a1h, a1l, gacc, err, st); break;
-        case 128: e = run_batches<128, 3>(p, d, g, x, maps, batch, tpc, a1h, a1l, gacc, err, st); break;
-        default: e = run_batches<192, 2>(p, d, g, x, maps, batch, tpc, a1h, a1l, gacc, err, st); break;
+    // second lane: its own stream, forked from and joined back into st
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    e = cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking);
+    for (int k = 0; k < 5 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[4], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, ev[4], 0);
+    if (e == cudaSuccess) {
+        lanes[0].st = st; lanes[0].done[0] = ev[0]; lanes[0].done[1] = ev[1];
+        lanes[1].st = aux; lanes[1].done[0] = ev[2]; lanes[1].done[1] = ev[3];
+        switch (BN) {
+            case 64: e = run_batches<64, 3>(p, d, g, lanes, batch, tpc, gacc, err); break;
+            case 128: e = run_batches<128, 3>(p, d, g, lanes, batch, tpc, gacc, err); break;
+            default: e = run_batches<192, 2>(p, d, g, lanes, batch, tpc, gacc, err); break;
+        }
     }
+    // join (also after an error, so that nothing is left running on aux)
+    if (aux && ev[4]) {
+        cudaEventRecord(ev[4], aux);
+        cudaStreamWaitEvent(st, ev[4], 0);
+    }
+    if (aux) cudaStreamDestroy(aux);
+    for (int k = 0; k < 5; ++k)
+        if (ev[k]) cudaEventDestroy(ev[k]);
     if (e != cudaSuccess) return e;
     return cudaMemcpyAsync(d.partial, gacc, sizeof(double) * (size_t)nq * nb, cudaMemcpyDeviceToDevice, st);
 }
