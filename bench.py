@@ -229,6 +229,7 @@ def run_kald(args):
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
     sampler.start()
+    launches0 = kk.kald_kernel_launches()
     step_ms, lw_ms = [], []
     for _ in range(args.steps):
         flush.fill_(float(_))                      # L2 flush, outside the step events
@@ -241,6 +242,7 @@ def run_kald(args):
         step_ms.append(a.elapsed_time(b))
         lw_ms.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
+    launches = kk.kald_kernel_launches() - launches0
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
@@ -314,10 +316,12 @@ def run_kald(args):
     else:
         if args.precision == "bf16split":
             # executed tensor work: per pair, GEMM1 and GEMM2 over ceil(nb^2 / 128)
-            # row tiles of N = K = 2H (H = nb rounded up to 32), 3 MMAs per product
+            # row tiles of N = K = 2H (H = nb rounded up to 32); 3 MMAs per
+            # product (5 when H <= 64: three-piece eigenvector operand)
             H = -(-nb // 32) * 32
             mt = -(-(nb * nb) // 128)
-            flops = nq * nq * 2.0 * mt * 3 * 2.0 * 128 * (2 * H) * (2 * H)
+            n_mma = 5 if H <= 64 else 3
+            flops = nq * nq * 2.0 * mt * n_mma * 2.0 * 128 * (2 * H) * (2 * H)
             kernel = "tcx_gemm_kernel"
         else:
             n_valid = int(torch.sum(nu > opt.omega_min_thz).item())
@@ -326,16 +330,20 @@ def run_kald(args):
                      + allowed * 8.0 * nb)                              # phi at delta-allowed pairs
             kernel = "lw_main_kernel"
     achieved = flops / lw_avg_s / 1e12
+    timed = ("one kald_linewidths call, CUDA events on its stream: every kernel of the stage "
+             "(gather / Y-build, operand splits, GEMMs, reductions), so frac is a lower bound for the "
+             "GEMM kernel itself; per-kernel shares are in profiles/")
     if args.precision == "bf16split":
         peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": None, "kernel": kernel, "flops_per_launch": flops,
+                    "timed_region": timed,
                     "peak_note": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16, power-capped loop), of measured"}
     else:
         peak = fp32_peak if args.precision == "fp32" else fp32_peak / 64.0
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": None,
-                    "kernel": kernel, "flops_per_launch": flops,
+                    "kernel": kernel, "flops_per_launch": flops, "timed_region": timed,
                     "peak_note": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz" +
                                  ("" if args.precision == "fp32" else " / 64 (FP64)")}
     cpu = None
@@ -356,7 +364,7 @@ def run_kald(args):
                            "linewidth_ms": float(np.mean(lw_ms))},
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},
-                "gpu_launches": 9 * args.steps,     # dynmat, jacobi, 5 linewidth, 2 kappa kernels
+                "gpu_launches": int(launches),      # library kernels in the timed steps (its own counter)
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
                 "kappa_W_mK": kap.cpu().numpy().round(6).tolist()[:2],
                 "delta_allowed_fraction": allowed / trip}
@@ -375,13 +383,13 @@ def main():
     ap.add_argument("--impl", default="kald", choices=["kald", "reference"])
     ap.add_argument("--workload", default="C2", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default=None, choices=["fp32", "fp64", "bf16split"],
-                    help="default: fp32 for crystals, bf16split (tensor cores) for Gamma-only workloads")
+                    help="default: fp64 for C1 (the plain-method configuration), bf16split (tensor cores) otherwise")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling runs)")
     ap.add_argument("--mesh", default=None, help="override the q-mesh, e.g. 4,4,4 (profiling runs)")
     args = ap.parse_args()
     if args.precision is None:
-        args.precision = "bf16split" if WORKLOADS[args.workload]().n_q == 1 else "fp32"
+        args.precision = "fp64" if args.workload == "C1" else "bf16split"
     if args.impl == "reference":
         return run_reference(args)
     return run_kald(args)

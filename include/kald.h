@@ -112,6 +112,11 @@ const char *kald_last_error(const kald_ctx *ctx);
  * context's own stream) for every later call.  The caller keeps ownership. */
 kald_status kald_set_stream(kald_ctx *ctx, void *stream);
 
+/* Number of CUDA kernels this library has launched in the process so far,
+ * over all contexts (a diagnostic counter, read without synchronising; it
+ * has no counterpart in the paper).  Never fails. */
+uint64_t kald_kernel_launches(void);
+
 /* Harmonic phonons on the Gamma-centred mesh (paper, section "Lattice
  * Dynamics"): D(q) = sum_R Phi2(i0,jR)/sqrt(m_i m_j) exp(-i q.R) (Bloch sum
  * before Eq. eigenvectors_crystal), Hermitian eigenpairs in FP64 (Eq.

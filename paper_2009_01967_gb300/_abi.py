@@ -25,7 +25,7 @@ PRECISION = {"fp64": 0, "fp32": 1, "bf16split": 2}
 
 EXPORTS = ["kald_ctx_create", "kald_ctx_destroy", "kald_last_error", "kald_set_stream",
            "kald_phonons", "kald_linewidths", "kald_kappa_rta", "kald_kappa_qhgk",
-           "kald_kappa_rta_noalloc"]
+           "kald_kappa_rta_noalloc", "kald_kernel_launches"]
 
 
 class KaldError(RuntimeError):
@@ -81,8 +81,15 @@ def load_library(path: str = LIB_PATH):
     lib.kald_kappa_rta_noalloc.argtypes = [vp, vp, C.POINTER(kald_system), C.POINTER(i32), vp, vp, vp,
                                            C.POINTER(kald_options), vp]
     lib.kald_kappa_rta_noalloc.restype = st
+    lib.kald_kernel_launches.argtypes = []
+    lib.kald_kernel_launches.restype = C.c_uint64
     _lib = lib
     return lib
+
+
+def kald_kernel_launches() -> int:
+    """Kernel launches the library has made in this process (diagnostic)."""
+    return int(load_library().kald_kernel_launches())
 
 
 @dataclass

@@ -316,16 +316,16 @@ cudaError_t launch_eigh_large(int n, const double2 *D, double *scratch, double *
     double *vbuf = vec, *p = vec + n, *w = vec + 2 * n, *dd = vec + 3 * n, *ee = vec + 4 * n,
            *lam = vec + 5 * n;
     const unsigned g = (unsigned)std::min<size_t>((nn + 255) / 256, 16384);
-    he_real_kernel<<<g, 256, 0, st>>>(n, D, A);
+    he_real_kernel<<<counted(g), 256, 0, st>>>(n, D, A);
     for (int k = 0; k + 2 < n; ++k) {
-        hh_column_kernel<<<1, 1024, 0, st>>>(n, k, A, vbuf, dd, ee);
+        hh_column_kernel<<<counted(1), 1024, 0, st>>>(n, k, A, vbuf, dd, ee);
         const int m = n - k - 1;
-        hh_symv_kernel<<<(m * 32 + 255) / 256, 256, 0, st>>>(n, k, A, vbuf, p);
-        hh_w_kernel<<<1, 1024, 0, st>>>(n, k, vbuf, p, w);
+        hh_symv_kernel<<<counted((m * 32 + 255) / 256), 256, 0, st>>>(n, k, A, vbuf, p);
+        hh_w_kernel<<<counted(1), 1024, 0, st>>>(n, k, vbuf, p, w);
         const size_t mm = (size_t)m * m;
-        hh_rank2_kernel<<<(unsigned)std::min<size_t>((mm + 255) / 256, 8192), 256, 0, st>>>(n, k, A, vbuf, w);
+        hh_rank2_kernel<<<counted((unsigned)std::min<size_t>((mm + 255) / 256, 8192)), 256, 0, st>>>(n, k, A, vbuf, w);
     }
-    hh_tail_kernel<<<1, 32, 0, st>>>(n, A, dd, ee);
+    hh_tail_kernel<<<counted(1), 32, 0, st>>>(n, A, dd, ee);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // Gershgorin interval and the tridiagonal norm (host, O(n))
@@ -344,8 +344,8 @@ cudaError_t launch_eigh_large(int n, const double2 *D, double *scratch, double *
     }
     const double pad = 1e-12 * std::max(tn, 1e-300);
     const double pivmin = 1e-300 + 1e-30 * tn * tn;
-    bisect_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, dd, ee, lo - pad, hi + pad, pivmin, lam);
-    invit_kernel<<<(n + 127) / 128, 128, 0, st>>>(n, dd, ee, lam, tn, scr, Zt);
+    bisect_kernel<<<counted((n + 127) / 128), 128, 0, st>>>(n, dd, ee, lo - pad, hi + pad, pivmin, lam);
+    invit_kernel<<<counted((n + 127) / 128), 128, 0, st>>>(n, dd, ee, lam, tn, scr, Zt);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // near-degenerate sets of the (ascending) eigenvalues
@@ -372,13 +372,13 @@ cudaError_t launch_eigh_large(int n, const double2 *D, double *scratch, double *
         e = cudaMemcpyAsync(dsets, csr.data(), sizeof(int) * csr.size(), cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return e;
         for (int x = 0; x < n_sets; ++x)
-            mgs_kernel<<<1, 256, 0, st>>>(n, dsets + 2 * x, Zt);
+            mgs_kernel<<<counted(1), 256, 0, st>>>(n, dsets + 2 * x, Zt);
         e = cudaStreamSynchronize(st);                // csr must outlive the copy
         if (e != cudaSuccess) return e;
     }
     for (int k = n - 3; k >= 0; --k)
-        backtransform_kernel<<<(n * 32 + 255) / 256, 256, 0, st>>>(n, k, A, Zt);
-    he_output_kernel<<<g, 256, 0, st>>>(n, lam, Zt, nu_out, eig_out);
+        backtransform_kernel<<<counted((n * 32 + 255) / 256), 256, 0, st>>>(n, k, A, Zt);
+    he_output_kernel<<<counted(g), 256, 0, st>>>(n, lam, Zt, nu_out, eig_out);
     return cudaGetLastError();
 }
 

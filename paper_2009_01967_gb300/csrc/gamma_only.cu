@@ -181,17 +181,17 @@ cudaError_t run_plain(const GammaPlan &gp, const GammaDev &d, const LwParams &p,
     R *YT = static_cast<R *>(d.Y);
     R *T = static_cast<R *>(d.T);
     R *PHI = static_cast<R *>(d.PHI);
-    g_real_kernel<R><<<(unsigned)std::min<size_t>((nn + 255) / 256, 8192), 256, 0, st>>>(nn, d.eig, E);
+    g_real_kernel<R><<<counted((unsigned)std::min<size_t>((nn + 255) / 256, 8192)), 256, 0, st>>>(nn, d.eig, E);
     const double sig2inv = 0.5 / (p.sigma_w * p.sigma_w);
     const dim3 ggrid((nb + 63) / 64, (nb + 63) / 64);
     for (int mu = 0; mu < nb; ++mu) {
         if (!(gp.omega_h[mu] > 0.0)) continue;
         cudaMemsetAsync(YT, 0, sizeof(R) * nn, st);
-        g_ybuild_kernel<R><<<(gp.n_groups * 9 + 255) / 256, 256, 0, st>>>(
+        g_ybuild_kernel<R><<<counted((gp.n_groups * 9 + 255) / 256), 256, 0, st>>>(
             nb, gp.n_groups, d.group_jk, d.group_start, d.blk_i, d.fc3, E + (size_t)mu * nb, YT);
-        g_gemm_nt_kernel<R><<<ggrid, 256, 0, st>>>(nb, nb, nb, E, YT, T);
-        g_gemm_nt_kernel<R><<<ggrid, 256, 0, st>>>(nb, nb, nb, T, E, PHI);
-        g_epilogue_kernel<R><<<gp.n_part, 256, 0, st>>>(nb, PHI, gp.omega_h[mu], d.omega, d.occ, sig2inv,
+        g_gemm_nt_kernel<R><<<counted(ggrid), 256, 0, st>>>(nb, nb, nb, E, YT, T);
+        g_gemm_nt_kernel<R><<<counted(ggrid), 256, 0, st>>>(nb, nb, nb, T, E, PHI);
+        g_epilogue_kernel<R><<<counted(gp.n_part), 256, 0, st>>>(nb, PHI, gp.omega_h[mu], d.omega, d.occ, sig2inv,
                                                         p.cut_w, d.partial + (size_t)mu * gp.n_part, d.allowed);
     }
     return cudaGetLastError();
@@ -231,16 +231,16 @@ cudaError_t launch_gamma_only(const GammaPlan &gp, const GammaDev &d, const LwPa
         e = cudaMemcpyAsync(const_cast<int *>(ts), gp.tile_start.data(), sizeof(int) * (nb + 1),
                             cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return e;
-        g_gamma_csr_kernel<<<(nb + 127) / 128, 128, 0, st>>>(nb, ts, d.partial_tc, d.omega, pref, gamma_out);
+        g_gamma_csr_kernel<<<counted((nb + 127) / 128), 128, 0, st>>>(nb, ts, d.partial_tc, d.omega, pref, gamma_out);
     } else {
         e = cudaMemsetAsync(d.partial, 0, sizeof(double) * (size_t)nb * gp.n_part, st);
         if (e != cudaSuccess) return e;
         e = mode == 1 ? run_plain<float>(gp, d, p, st) : run_plain<double>(gp, d, p, st);
         if (e != cudaSuccess) return e;
-        g_gamma_kernel<<<(nb + 127) / 128, 128, 0, st>>>(nb, gp.n_part, d.partial, d.omega, pref, gamma_out);
+        g_gamma_kernel<<<counted((nb + 127) / 128), 128, 0, st>>>(nb, gp.n_part, d.partial, d.omega, pref, gamma_out);
     }
-    g_rank_kernel<<<(nb + 127) / 128, 128, 0, st>>>(nb, d.nu, d.order);
-    g_degen_kernel<<<1, 32, 0, st>>>(nb, d.nu, d.order, degen_tol_thz, gamma_out);
+    g_rank_kernel<<<counted((nb + 127) / 128), 128, 0, st>>>(nb, d.nu, d.order);
+    g_degen_kernel<<<counted(1), 32, 0, st>>>(nb, d.nu, d.order, degen_tol_thz, gamma_out);
     return cudaGetLastError();
 }
 

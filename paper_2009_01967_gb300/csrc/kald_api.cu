@@ -298,11 +298,15 @@ kald_status plan_system(kald_ctx *ctx, const kald_system *s, HostSystem &h) {
     return KALD_OK;
 }
 
+std::atomic<unsigned long long> g_launches{0};
+
 }  // namespace kald
 
 using namespace kald;
 
 extern "C" {
+
+uint64_t kald_kernel_launches(void) { return (uint64_t)g_launches.load(std::memory_order_relaxed); }
 
 kald_status kald_ctx_create(kald_ctx **out, int device) {
     if (!out) return KALD_E_INVALID;

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include <string>
 #include <vector>
 
@@ -42,6 +44,14 @@ struct kald_ctx {
 };
 
 namespace kald {
+
+// Kernel launches made by the library in this process (a diagnostic read
+// through kald_kernel_launches): every launch passes its grid through counted().
+extern std::atomic<unsigned long long> g_launches;
+inline dim3 counted(dim3 grid) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return grid;
+}
 
 // Set ctx->err and return `st`.
 kald_status fail(kald_ctx *ctx, kald_status st, const std::string &msg);

@@ -354,9 +354,9 @@ cudaError_t launch_kappa_rta(const DevFc2 &f, int nb, int nq, const double *qcar
                              const double *nu_thz, const double2 *eig, const double *gamma,
                              double T, int classical, double omega_min_thz, double degen_tol_thz,
                              double *partial, double *kappa_out, double scale, cudaStream_t st) {
-    kappa_rta_kernel<<<nq, kRtaThreads, 0, st>>>(f, nb, qcart, nu_thz, eig, gamma, T, classical,
+    kappa_rta_kernel<<<counted(nq), kRtaThreads, 0, st>>>(f, nb, qcart, nu_thz, eig, gamma, T, classical,
                                                 omega_min_thz, degen_tol_thz, partial);
-    sum_partials_kernel<<<1, 32, 0, st>>>(nq, partial, scale, kappa_out);
+    sum_partials_kernel<<<counted(1), 32, 0, st>>>(nq, partial, scale, kappa_out);
     return cudaGetLastError();
 }
 
@@ -366,18 +366,18 @@ cudaError_t launch_qhgk(const DevFc2Dist &f, int nb, const double *nu_thz, const
                         double *partial, int n_partial, double *kappa_out, double scale,
                         cudaStream_t st) {
     const size_t nn = (size_t)nb * nb;
-    real_part_kernel<<<(unsigned)std::min<size_t>((nn + 255) / 256, 8192), 256, 0, st>>>(nn, eig, Ework);
+    real_part_kernel<<<counted((unsigned)std::min<size_t>((nn + 255) / 256, 8192)), 256, 0, st>>>(nn, eig, Ework);
     const size_t ns = (size_t)f.n_rows * 3 * nb;
-    sparse_ae_kernel<<<(unsigned)std::min<size_t>((ns + 255) / 256, 16384), 256, 0, st>>>(f, nb, Ework, Bwork);
+    sparse_ae_kernel<<<counted((unsigned)std::min<size_t>((ns + 255) / 256, 16384)), 256, 0, st>>>(f, nb, Ework, Bwork);
     double *omega = partial + (size_t)n_partial * 9;     // scratch after the partials
-    qhgk_modes_kernel<<<(nb + 255) / 256, 256, 0, st>>>(nb, nu_thz, omega_min_thz, omega);
+    qhgk_modes_kernel<<<counted((nb + 255) / 256), 256, 0, st>>>(nb, nu_thz, omega_min_thz, omega);
     dim3 grid((nb + 63) / 64, (nb + 63) / 64, 3);
-    dgemm_w_kernel<<<grid, 256, 0, st>>>(nb, Ework, Bwork, omega, W);
+    dgemm_w_kernel<<<counted(grid), 256, 0, st>>>(nb, Ework, Bwork, omega, W);
     const int rows = (nb + n_partial - 1) / n_partial;
     const int nblk = (nb + rows - 1) / rows;
-    qhgk_pairsum_kernel<<<nblk, 256, 0, st>>>(nb, W, omega, gamma, T, classical,
+    qhgk_pairsum_kernel<<<counted(nblk), 256, 0, st>>>(nb, W, omega, gamma, T, classical,
                                               kTwoPi * degen_tol_thz, rows, partial);
-    sum_partials_kernel<<<1, 32, 0, st>>>(nblk, partial, scale, kappa_out);
+    sum_partials_kernel<<<counted(1), 32, 0, st>>>(nblk, partial, scale, kappa_out);
     return cudaGetLastError();
 }
 

@@ -488,25 +488,25 @@ size_t lw_smem_bytes(const LwParams &p, bool oper_smem) {
 
 cudaError_t launch_mode_prep(int n, const double *nu, double omega_min_w, double T, int classical,
                              double *omega, double *occ, cudaStream_t st) {
-    mode_prep_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, nu, omega_min_w, T, classical, omega, occ);
+    mode_prep_kernel<<<counted((n + 255) / 256), 256, 0, st>>>(n, nu, omega_min_w, T, classical, omega, occ);
     return cudaGetLastError();
 }
 
 cudaError_t launch_lw_prep(const LwParams &p, const LwDev &d, int fp32, cudaStream_t st) {
     const int n = p.nq * p.nb;
-    mode_prep_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, d.nu, p.omega_min_w, p.T, p.classical,
+    mode_prep_kernel<<<counted((n + 255) / 256), 256, 0, st>>>(n, d.nu, p.omega_min_w, p.T, p.classical,
                                                       d.omega, d.occ);
     const int nc = p.nq * p.n_rep;
     const size_t ne = (size_t)p.nq * p.nb * p.nb;
     const int grid = (int)std::min<size_t>((ne + 255) / 256, 4096);
     if (fp32) {
-        chi_kernel<float2><<<(nc + 255) / 256, 256, 0, st>>>(p.nq, p.n_rep, d.qcart, d.rep_cart,
+        chi_kernel<float2><<<counted((nc + 255) / 256), 256, 0, st>>>(p.nq, p.n_rep, d.qcart, d.rep_cart,
                                                              (float2 *)d.chi);
-        eps_transpose_kernel<float2><<<grid, 256, 0, st>>>(p.nq, p.nb, d.eig, (float2 *)d.eps_work);
+        eps_transpose_kernel<float2><<<counted(grid), 256, 0, st>>>(p.nq, p.nb, d.eig, (float2 *)d.eps_work);
     } else {
-        chi_kernel<double2><<<(nc + 255) / 256, 256, 0, st>>>(p.nq, p.n_rep, d.qcart, d.rep_cart,
+        chi_kernel<double2><<<counted((nc + 255) / 256), 256, 0, st>>>(p.nq, p.n_rep, d.qcart, d.rep_cart,
                                                               (double2 *)d.chi);
-        eps_transpose_kernel<double2><<<grid, 256, 0, st>>>(p.nq, p.nb, d.eig, (double2 *)d.eps_work);
+        eps_transpose_kernel<double2><<<counted(grid), 256, 0, st>>>(p.nq, p.nb, d.eig, (double2 *)d.eps_work);
     }
     return cudaGetLastError();
 }
@@ -525,7 +525,7 @@ cudaError_t launch_lw_main(const LwParams &p, const LwDev &d, int fp32, int sm_c
         auto k = lw_main_kernel<float, true>;
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k<<<grid, kThreads, smem, st>>>(p, d, (const float *)d.fc3, (const float2 *)d.eps_work,
+        k<<<counted(grid), kThreads, smem, st>>>(p, d, (const float *)d.fc3, (const float2 *)d.eps_work,
                                         (const float2 *)d.chi);
     } else {
         const size_t smem = lw_smem_bytes<double>(p, false);
@@ -533,7 +533,7 @@ cudaError_t launch_lw_main(const LwParams &p, const LwDev &d, int fp32, int sm_c
         auto k = lw_main_kernel<double, false>;
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k<<<grid, kThreads, smem, st>>>(p, d, (const double *)d.fc3, (const double2 *)d.eps_work,
+        k<<<counted(grid), kThreads, smem, st>>>(p, d, (const double *)d.fc3, (const double2 *)d.eps_work,
                                         (const double2 *)d.chi);
     }
     return cudaGetLastError();
@@ -543,7 +543,7 @@ cudaError_t launch_lw_finish(const LwParams &p, const LwDev &d, double degen_tol
                              double *gamma_out, cudaStream_t st) {
     const double pref = kHbarEvPs * kPi / 8.0 * kEvA2AmuPs2 * kEvA2AmuPs2 * kEvA2AmuPs2 /
                         (double)p.nq / (sqrt(kTwoPi) * p.sigma_w);
-    lw_finish_kernel<<<(p.nq + 63) / 64, 64, 0, st>>>(p.nq, p.nb, p.n_chunks, d.partial, d.omega,
+    lw_finish_kernel<<<counted((p.nq + 63) / 64), 64, 0, st>>>(p.nq, p.nb, p.n_chunks, d.partial, d.omega,
                                                      d.nu, pref, degen_tol_thz, gamma_out);
     return cudaGetLastError();
 }

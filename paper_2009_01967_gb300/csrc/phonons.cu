@@ -250,7 +250,7 @@ cudaError_t launch_dynmat(const DevFc2 &f, int nb, int nq, const double *qcart, 
                           cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(D, 0, sizeof(double2) * (size_t)nq * nb * nb, st);
     if (e != cudaSuccess) return e;
-    dynmat_kernel<<<nq, 256, 0, st>>>(f, nb, qcart, D);
+    dynmat_kernel<<<counted(nq), 256, 0, st>>>(f, nb, qcart, D);
     return cudaGetLastError();
 }
 
@@ -271,14 +271,14 @@ cudaError_t launch_jacobi(int nb, int nq, double2 *A, double2 *V, double *nu_thz
     cudaError_t e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    jacobi_kernel<<<nq, 256, smem, st>>>(nb, A, V, nu_thz, eig_out, nonconv);
+    jacobi_kernel<<<counted(nq), 256, smem, st>>>(nb, A, V, nu_thz, eig_out, nonconv);
     return cudaGetLastError();
 }
 
 cudaError_t launch_velocity_diag(const DevFc2 &f, int nb, int nq, const double *qcart,
                                  const double *nu_thz, const double2 *eig, double *vel,
                                  cudaStream_t st) {
-    velocity_kernel<<<nq, 128, 0, st>>>(f, nb, qcart, nu_thz, eig, vel);
+    velocity_kernel<<<counted(nq), 128, 0, st>>>(f, nb, qcart, nu_thz, eig, vel);
     return cudaGetLastError();
 }
 

@@ -593,17 +593,17 @@ cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, L
         x.pair0 = p0;
         x.n_pairs = (int)std::min<long long>(batch, total - p0);
         if (gp == 4)
-            ycx_gather_kernel<4><<<dim3(g.n_parts, x.n_pairs / 4), gthreads, 4 * gsmem, L.st>>>(
+            ycx_gather_kernel<4><<<counted(dim3(g.n_parts, x.n_pairs / 4)), gthreads, 4 * gsmem, L.st>>>(
                 x, g, ew, cw, p.n_rep, L.a1h, L.a1l);
         else if (gp == 2)
-            ycx_gather_kernel<2><<<dim3(g.n_parts, x.n_pairs / 2), gthreads, 2 * gsmem, L.st>>>(
+            ycx_gather_kernel<2><<<counted(dim3(g.n_parts, x.n_pairs / 2)), gthreads, 2 * gsmem, L.st>>>(
                 x, g, ew, cw, p.n_rep, L.a1h, L.a1l);
         else
-            ycx_gather_kernel<1><<<dim3(g.n_parts, x.n_pairs), gthreads, gsmem, L.st>>>(x, g, ew, cw, p.n_rep,
+            ycx_gather_kernel<1><<<counted(dim3(g.n_parts, x.n_pairs)), gthreads, gsmem, L.st>>>(x, g, ew, cw, p.n_rep,
                                                                                         L.a1h, L.a1l);
-        k1<<<dim3(gx, x.n_pairs), kWsThreads, smem, L.st>>>(L.maps[0], L.maps[1], L.maps[2], L.maps[3], L.maps[4],
+        k1<<<counted(dim3(gx, x.n_pairs)), kWsThreads, smem, L.st>>>(L.maps[0], L.maps[1], L.maps[2], L.maps[3], L.maps[4],
                                                               x, tpc, err);
-        k2<<<dim3(gx, x.n_pairs), kWsThreads, smem, L.st>>>(L.maps[5], L.maps[6], L.maps[7], L.maps[8], L.maps[9],
+        k2<<<counted(dim3(gx, x.n_pairs)), kWsThreads, smem, L.st>>>(L.maps[5], L.maps[6], L.maps[7], L.maps[8], L.maps[9],
                                                               x, tpc, err);
         e = cudaEventRecord(L.done[(i >> 1) & 1], L.st);
         if (e != cudaSuccess) return e;
@@ -615,7 +615,7 @@ cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, L
                 if (e != cudaSuccess) return e;
             }
             const int n = (qb - qa) * nb;
-            slots_reduce_kernel<<<(n + 127) / 128, 128, 0, L.st>>>(x, qa, qb, gacc);
+            slots_reduce_kernel<<<counted((n + 127) / 128), 128, 0, L.st>>>(x, qa, qb, gacc);
         }
     }
     return cudaGetLastError();
@@ -723,9 +723,9 @@ cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups 
     if (e == cudaSuccess) e = cudaMemsetAsync(d.allowed, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     const int eg = (int)std::min<size_t>(((size_t)nq * BN * Kp + 255) / 256, 4096);
-    embed_kernel<<<eg, 256, 0, st>>>(nq, nb, H, d.eig, 0, b1h, three ? b1m : nullptr, b1l);
-    embed_kernel<<<eg, 256, 0, st>>>(nq, nb, H, d.eig, 1, b2h, three ? b2m : nullptr, b2l);
-    f32_tables_kernel<<<(nq * nb + 255) / 256, 256, 0, st>>>(nq * nb, d.omega, d.occ, wf, nf);
+    embed_kernel<<<counted(eg), 256, 0, st>>>(nq, nb, H, d.eig, 0, b1h, three ? b1m : nullptr, b1l);
+    embed_kernel<<<counted(eg), 256, 0, st>>>(nq, nb, H, d.eig, 1, b2h, three ? b2m : nullptr, b2l);
+    f32_tables_kernel<<<counted((nq * nb + 255) / 256), 256, 0, st>>>(nq * nb, d.omega, d.occ, wf, nf);
 
     XParams x;
     x.nb = nb; x.H = H; x.Kp = Kp; x.Mp = Mp;

@@ -331,7 +331,7 @@ cudaError_t launch_gamma_only_tc(const GammaPlan &gp, const GammaDev &d, const L
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(err, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    split_kernel<double2><<<4096, 256, 0, st>>>(nb, nb, reinterpret_cast<const double2 *>(d.eig),
+    split_kernel<double2><<<counted(4096), 256, 0, st>>>(nb, nb, reinterpret_cast<const double2 *>(d.eig),
                                                 (size_t)nb, ld, Eh, El);
     CUtensorMap mEh, mEl, mYh, mYl, mTh, mTl;
     if (!make_map(&mEh, Eh, rows, ld) || !make_map(&mEl, El, rows, ld) || !make_map(&mYh, Yh, rows, ld) ||
@@ -352,15 +352,15 @@ cudaError_t launch_gamma_only_tc(const GammaPlan &gp, const GammaDev &d, const L
         if (!(gp.omega_h[mu] > 0.0) || t1 == t0) continue;
         // Y_mu^T planes: the previous mode's entries live on the same (sparse)
         // pattern and are all overwritten
-        ybuild_bf16_kernel<<<(gp.n_groups * 9 + 255) / 256, 256, 0, st>>>(
+        ybuild_bf16_kernel<<<counted((gp.n_groups * 9 + 255) / 256), 256, 0, st>>>(
             gp.n_groups, d.group_jk, d.group_start, d.blk_i, d.fc3, d.eig + (size_t)mu * nb, ld, Yh, Yl);
         EpiSplit es{Th, Tl, ld};
         EpiGamma eg{};
-        k1<<<dim3(nt, nt), 128, kSmemBytes, st>>>(mEh, mEl, mYh, mYl, nb, nb, ld, es, eg, err);
+        k1<<<counted(dim3(nt, nt)), 128, kSmemBytes, st>>>(mEh, mEl, mYh, mYl, nb, nb, ld, es, eg, err);
         EpiGamma eg2{d.omega, d.occ, gp.omega_h[mu], sig2inv, p.cut_w, partial_tc + t0, d.allowed,
                      tiles_dev + t0, symmetric};
         EpiSplit es0{nullptr, nullptr, 0};
-        k2<<<t1 - t0, 128, kSmemBytes, st>>>(mTh, mTl, mEh, mEl, nb, nb, ld, es0, eg2, err);
+        k2<<<counted(t1 - t0), 128, kSmemBytes, st>>>(mTh, mTl, mEh, mEl, nb, nb, ld, es0, eg2, err);
     }
     return cudaGetLastError();
 }

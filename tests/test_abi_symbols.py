@@ -52,3 +52,16 @@ def test_context_without_gpu_reports_cuda_error(lib):
     lib.kald_ctx_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]
     assert lib.kald_ctx_create(ctypes.byref(h), 0) == 3
     assert not h.value
+
+
+def test_launch_counter_starts_at_zero_without_gpu(lib):
+    """The diagnostic launch counter is readable without a device and counts
+    nothing when no call ran."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    lib.kald_kernel_launches.restype = ctypes.c_uint64
+    assert lib.kald_kernel_launches() == 0
