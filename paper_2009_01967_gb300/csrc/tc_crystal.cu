@@ -632,12 +632,14 @@ int tcx_half(int nb) { return (nb + 31) / 32 * 32; }
 static int tcx_slices(int nq, int batch) { return (4 * batch + nq - 1) / nq + 2; }
 
 int tcx_batch(int nb, int nq, int sm_count) {
-    // pairs per launch: about sixteen GEMM tiles per SM, a multiple of 4 (the
-    // gather takes up to 4 pairs per CTA); KALD_TCX_BATCH overrides (tuning)
+    // pairs per launch, a multiple of 4 (the gather takes up to 4 pairs per
+    // CTA): with two or more row tiles per pair, half an SM count of pairs,
+    // so that two CTAs per pair (half the tiles each) fill one wave; with a
+    // single tile, sixteen pairs per SM.  KALD_TCX_BATCH overrides (tuning).
     const long long total = (long long)nq * nq;
     const int mt = (nb * nb + kBM - 1) / kBM;
-    long long b = std::max(1, 16 * std::max(1, sm_count) / mt);
-    if (b >= 4) b = b / 4 * 4;
+    const int sms = std::max(1, sm_count);
+    long long b = mt >= 2 ? std::max(4, sms / 2 / 4 * 4) : 16LL * sms;
     if (const char *env = std::getenv("KALD_TCX_BATCH")) {
         const long long v = std::atoll(env);
         if (v > 0) b = v;
