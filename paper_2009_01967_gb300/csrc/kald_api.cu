@@ -259,9 +259,11 @@ kald_status plan_system(kald_ctx *ctx, const kald_system *s, HostSystem &h) {
         double c[3];
         cart(R, c);
         h.rep_cart.insert(h.rep_cart.end(), c, c + 3);
+        h.rep_int.insert(h.rep_int.end(), {(int)R[0], (int)R[1], (int)R[2]});
         return id;
     };
     h.rep_cart.clear();
+    h.rep_int.clear();
     {
         const int32_t z[3] = {0, 0, 0};
         rep_of(z);
@@ -600,14 +602,27 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
             off_eig += nn;
             continue;
         }
-        // BF16 split: the two dense contractions on tensor cores, with the
-        // FP32 tables of the CUDA-core path for the Y-build
-        const int tcx = opt->precision == KALD_BF16_SPLIT;
-        const int f32w = fp32 || tcx;
         std::vector<double> qc;
         std::vector<int> qf;
         mesh_points(h.lattice, mesh, qc, qf);
         const int nq = nq_mesh;
+        // One- and two-atom cells: the register kernel of small_nb.cu in every
+        // precision (FP32 arithmetic unless FP64 is asked for), with the Bloch
+        // phases from a table of L-th roots of unity (L = lcm of the mesh).
+        const size_t n3 = h.fc3_i.size();
+        int sn_L = 1, sn_m0 = 0;
+        for (int a = 0; a < 3; ++a) sn_L = std::lcm(sn_L, (int)mesh[a]);
+        for (size_t b = 0; b < n3; ++b) {
+            int l1 = 0;
+            for (int c = 0; c < 3; ++c)
+                l1 += std::abs(h.rep_int[3 * h.fc3_rj[b] + c]) + std::abs(h.rep_int[3 * h.fc3_rk[b] + c]);
+            sn_m0 = std::max(sn_m0, (sn_L - 1) * l1);
+        }
+        const int small = sn_supported(nb) && sn_m0 < 8192;
+        // BF16 split: the two dense contractions on tensor cores, with the
+        // FP32 tables of the CUDA-core path for the phase sum
+        const int tcx = opt->precision == KALD_BF16_SPLIT && !small;
+        const int f32w = opt->precision != KALD_FP64;
         const size_t nn = (size_t)nq * nb * nb;
         LwParams p;
         p.nb = nb; p.nq = nq;
@@ -625,6 +640,28 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
             p.qp_chunk = (nq + nch - 1) / nch;
             p.n_chunks = (nq + p.qp_chunk - 1) / p.qp_chunk;
             if (tcx) { p.qp_chunk = nq; p.n_chunks = 1; }
+            if (small) {
+                p.qp_chunk = sn_chunk(nb);
+                p.n_chunks = (nq + p.qp_chunk - 1) / p.qp_chunk;
+            }
+        }
+        std::vector<int> sn_kk;
+        std::vector<int4> sn_bj, sn_bk;
+        std::vector<int2> sn_gjk;
+        if (small) {
+            sn_kk.resize(3 * (size_t)nq);
+            for (int q = 0; q < nq; ++q)
+                for (int c = 0; c < 3; ++c) sn_kk[3 * (size_t)q + c] = qf[3 * (size_t)q + c] * (sn_L / mesh[c]);
+            sn_bj.resize(std::max<size_t>(n3, 1), make_int4(0, 0, 0, 0));
+            sn_bk.resize(std::max<size_t>(n3, 1), make_int4(0, 0, 0, 0));
+            for (size_t b = 0; b < n3; ++b) {
+                const int *rj = &h.rep_int[3 * h.fc3_rj[b]], *rk = &h.rep_int[3 * h.fc3_rk[b]];
+                sn_bj[b] = make_int4(h.fc3_i[b], rj[0], rj[1], rj[2]);
+                sn_bk[b] = make_int4(rk[0], rk[1], rk[2], 0);
+            }
+            const int ng = (int)h.pair3_j.size();
+            sn_gjk.resize(std::max(1, ng));
+            for (int g = 0; g < ng; ++g) sn_gjk[g] = make_int2(h.pair3_j[g], h.pair3_k[g]);
         }
         const int tcx_b = tcx ? tcx_batch(nb, nq, ctx->sm_count) : 0;
         // tensor-core path: the fc3 blocks in (j, k) group order, the groups
@@ -641,7 +678,6 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
         YSchedule ys;
         plan_ybuild(h, ys);
         p.n_rounds = ys.n_rounds;
-        const size_t n3 = h.fc3_i.size();
         std::vector<int4> binfo(std::max<size_t>(n3, 1), make_int4(0, 0, 0, 0));
         for (size_t b = 0; b < n3; ++b) binfo[b] = make_int4(h.fc3_i[b], h.fc3_rj[b], h.fc3_rk[b], 0);
         std::vector<float> fc3f;
@@ -666,6 +702,9 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
         if (tcx)
             need += ws_round(tcx_scratch_bytes(nb, nq, tcx_b)) + ws_round(16) + bytes_of(tc_gjk) +
                     bytes_of(tc_part_start) + bytes_of(tc_glist) + bytes_of(h.pair3_start);
+        if (small)
+            need += bytes_of(sn_kk) + bytes_of(sn_bj) + bytes_of(sn_bk) + bytes_of(sn_gjk) +
+                    bytes_of(h.pair3_start) + ws_round(c2 * (2 * (size_t)sn_m0 + 1));
         if ((st = ws_reserve(ctx, need))) return st;
         LwDev d;
         d.group_jk = upload(ctx, ys.group_jk);
@@ -699,11 +738,23 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
             tg.blkinfo = d.blkinfo;               // group order (HostSystem order)
             tg.fc3 = static_cast<const float *>(d.fc3);
         }
+        SnTables sn;
+        if (small) {
+            sn.L = sn_L; sn.m0 = sn_m0;
+            sn.n_groups = (int)h.pair3_j.size();
+            sn.kk = upload(ctx, sn_kk);
+            sn.gstart = upload(ctx, h.pair3_start);
+            sn.gjk = upload(ctx, sn_gjk);
+            sn.bj = upload(ctx, sn_bj);
+            sn.bk = upload(ctx, sn_bk);
+            sn.roots = ws_take(ctx, c2 * (2 * (size_t)sn_m0 + 1));
+        }
         cudaStream_t s = ctx->stream;
         cudaError_t e = launch_lw_prep(p, d, f32w, s);
         if (e == cudaSuccess)
-            e = tcx ? launch_lw_tensor(p, d, tg, tc_scr, tcx_b, ctx->sm_count, tc_err, s)
-                    : launch_lw_main(p, d, fp32, ctx->sm_count, ctx->smem_optin, s);
+            e = small ? launch_lw_small(p, d, sn, f32w, s)
+                : tcx ? launch_lw_tensor(p, d, tg, tc_scr, tcx_b, ctx->sm_count, tc_err, s)
+                      : launch_lw_main(p, d, fp32, ctx->sm_count, ctx->smem_optin, s);
         if (e == cudaSuccess) e = launch_lw_finish(p, d, opt->degen_tol_thz, g_d, s);
         if (e != cudaSuccess) return cuda_check(ctx, e, "kald_linewidths launch");
         unsigned long long al = 0;

@@ -87,6 +87,7 @@ struct HostSystem {
     std::vector<double> fc3_scaled;                    // [n_fc3][27] Phi3/sqrt(mi mj mk)
     // distinct replica vectors (Cartesian) referenced by fc3 / fc2
     std::vector<double> rep_cart;                      // [n_rep][3]
+    std::vector<int> rep_int;                          // [n_rep][3] integer cell vectors
     int n_rep = 0;
 };
 
@@ -208,6 +209,24 @@ cudaError_t launch_gamma_only_tc(const GammaPlan &gp, const GammaDev &d, const L
                                  const std::vector<int2> &tiles, const std::vector<int> &tile_start,
                                  int2 *tiles_dev, int symmetric, double *partial_tc, int *err,
                                  cudaStream_t st);
+
+// small_nb.cu: crystal linewidths of one- and two-atom cells (nb = 3 or 6),
+// one thread per (pair, mode), the projection in registers.  The Bloch phase
+// of a block is a root of unity of order L = lcm(mesh), taken from a table:
+// q.R = 2 pi sum_d k_d n_d / N_d for q = sum_d (k_d / N_d) b_d, R = sum_d n_d a_d.
+struct SnTables {
+    int L, m0;                        // root order, index offset of the table
+    int n_groups;
+    const int *kk;                    // [nq][3] k_d L / N_d
+    const int *gstart;                // [n_groups + 1] blocks of each (j, k) group
+    const int2 *gjk;                  // [n_groups] atoms (j, k)
+    const int4 *bj;                   // [n_fc3] (i, Rj in cells), group order
+    const int4 *bk;                   // [n_fc3] (Rk in cells, 0)
+    void *roots;                      // [2 m0 + 1] exp(-2 pi i (t - m0) / L), working precision
+};
+bool sn_supported(int nb);
+int sn_chunk(int nb);
+cudaError_t launch_lw_small(const LwParams &p, const LwDev &d, const SnTables &t, int fp32, cudaStream_t st);
 
 // tc_crystal.cu: crystal linewidth sums on tensor cores (BF16 split, nb <= 96).
 // The gather runs over the fc3 blocks grouped by (j, k) atom pair (the order

@@ -90,11 +90,15 @@ def _lw_case(case):
         return ki.Workload("g32", [s], (1, 1, 1), 300.0, 0.1, 3.0)
     if case == "C5_mesh6":
         return ki.c5(mesh=(6, 6, 6))
+    if case == "binary_mesh234":
+        # uneven mesh: the phase roots have order lcm(2, 3, 4) = 12
+        return ki.small_binary(mesh=(2, 3, 4), sigma=0.1)
     raise KeyError(case)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("case", ["C1", "binary3", "binary_random", "gamma_only_32", "C5_mesh6"])
+@pytest.mark.parametrize("case", ["C1", "binary3", "binary_random", "gamma_only_32", "C5_mesh6",
+                                  "binary_mesh234"])
 def test_linewidths_match_oracle(k, case, precision):
     kk, ctx = k
     w = _lw_case(case)
@@ -144,15 +148,20 @@ def test_linewidths_c2_sampled_q(k):
     assert tot == 512 ** 2 * 96 ** 3 and 0 < allowed < tot
 
 
-@pytest.mark.parametrize("case", ["binary3", "binary_random", "C5_mesh6", "fcc32_mesh2"])
+@pytest.mark.parametrize("case", ["binary3", "binary_random", "C5_mesh6", "fcc4_mesh3", "fcc32_mesh2"])
 def test_crystal_bf16split_tensor_cores(k, case):
-    """Crystal linewidths with the two dense contractions on tcgen05 (BF16
-    hi+lo, three MMAs per product, FP32 accumulation).  The delta windows are
-    decided in FP32 as in the FP32 CUDA-core path, so the allowed counts
-    agree exactly; gamma within 1e-5 of the FP64 oracle (split precision)."""
+    """Crystal linewidths in the BF16-split mode: the two dense contractions on
+    tcgen05 (BF16 pieces, FP32 accumulation) for cells of three or more atoms,
+    the FP32 register kernel for one- and two-atom cells.  The delta windows
+    are decided in FP32 as in the FP32 CUDA-core path, so the allowed counts
+    agree exactly; gamma within 1e-5 of the FP64 oracle."""
     kk, ctx = k
     if case == "fcc32_mesh2":
         w = ki.Workload("fcc32", [ki.fcc_supercell_system(2, seed=2)], (2, 2, 2), 300.0, 0.1, 3.0)
+    elif case == "fcc4_mesh3":
+        # 4-atom cell (12 branches): tensor tiles with N = K = 64 and the
+        # three-piece eigenvector operand
+        w = ki.Workload("fcc4", [ki.fcc_supercell_system(1, seed=7)], (3, 3, 3), 300.0, 0.1, 3.0)
     else:
         w = _lw_case(case)
     s = w.systems[0]
