@@ -731,6 +731,12 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
         if (tcx) {
             tg.n_groups = (int)h.pair3_j.size();
             tg.n_parts = (int)tc_part_start.size() - 1;
+            for (int x = 0; x < tg.n_parts; ++x) {
+                int nbk = 0;
+                for (int gi = tc_part_start[x]; gi < tc_part_start[x + 1]; ++gi)
+                    nbk += h.pair3_start[tc_glist[gi] + 1] - h.pair3_start[tc_glist[gi]];
+                tg.max_part_blocks = std::max(tg.max_part_blocks, nbk);
+            }
             tg.part_start = upload(ctx, tc_part_start);
             tg.glist = upload(ctx, tc_glist);
             tg.gstart = upload(ctx, h.pair3_start);

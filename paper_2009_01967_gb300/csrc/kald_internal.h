@@ -233,6 +233,7 @@ cudaError_t launch_lw_small(const LwParams &p, const LwDev &d, const SnTables &t
 // of HostSystem), the groups split over CTAs by plan_tcx_parts.
 struct TcxGroups {
     int n_groups = 0, n_parts = 0;
+    int max_part_blocks = 0;          // most fc3 blocks in one part (shared-memory staging)
     const int *part_start = nullptr;  // [n_parts + 1] into glist
     const int *glist = nullptr;       // group ids, part by part
     const int *gstart = nullptr;      // [n_groups + 1] blocks of each group (CSR)

@@ -386,7 +386,12 @@ __global__ void __launch_bounds__(128)
 ycx_gather_kernel(XParams x, TcxGroups g, const float2 *__restrict__ epsT_all,
                   const float2 *__restrict__ chi_all, int n_rep, __nv_bfloat16 *__restrict__ a1h,
                   __nv_bfloat16 *__restrict__ a1l) {
-    extern __shared__ float2 chi_sm[];             // [P][chi(q', R), chi(q'', R)]
+    // shared memory: the part's blocks (7 float4 of Phi3 + one int4 each, in
+    // processing order), then chi(q', R), chi(q'', R) of the P pairs
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4 *f_sm = reinterpret_cast<float4 *>(smem_raw);
+    int4 *b_sm = reinterpret_cast<int4 *>(f_sm + 7 * (size_t)g.max_part_blocks);
+    float2 *chi_sm = reinterpret_cast<float2 *>(b_sm + g.max_part_blocks);
     const int part = blockIdx.x, a0 = blockIdx.y * P;
     int q = 0;
     for (int p = 0; p < P; ++p) {
@@ -397,25 +402,38 @@ ycx_gather_kernel(XParams x, TcxGroups g, const float2 *__restrict__ epsT_all,
             chi_sm[(2 * p + 1) * n_rep + t] = chi_all[(size_t)qpp * n_rep + t];
         }
     }
+    {
+        int off = 0;
+        for (int gi = g.part_start[part]; gi < g.part_start[part + 1]; ++gi) {
+            const int gr = g.glist[gi];
+            const int b0 = g.gstart[gr], n = g.gstart[gr + 1] - b0;
+            const float4 *src = reinterpret_cast<const float4 *>(g.fc3) + 7 * (size_t)b0;
+            for (int t = threadIdx.x; t < 7 * n; t += blockDim.x) f_sm[7 * (size_t)off + t] = __ldg(src + t);
+            for (int t = threadIdx.x; t < n; t += blockDim.x) b_sm[off + t] = __ldg(g.blkinfo + b0 + t);
+            off += n;
+        }
+    }
     __syncthreads();
     const int nb = x.nb, s = threadIdx.x;
     if (s >= nb) return;
     const float2 *eps = epsT_all + (size_t)q * nb * nb;      // eps(q)(row, s) at row * nb + s
+    int lb = 0;                                    // block index in shared memory
     for (int gi = g.part_start[part]; gi < g.part_start[part + 1]; ++gi) {
         const int gr = g.glist[gi];
         const int2 jk = g.gjk[gr];
+        const int lb_end = lb + g.gstart[gr + 1] - g.gstart[gr];
         float2 acc[P][9];
 #pragma unroll
         for (int p = 0; p < P; ++p)
 #pragma unroll
             for (int t = 0; t < 9; ++t) acc[p][t] = make_float2(0.f, 0.f);
-        for (int bl = g.gstart[gr]; bl < g.gstart[gr + 1]; ++bl) {
-            const int4 bi = __ldg(g.blkinfo + bl);
-            const float4 *f4 = reinterpret_cast<const float4 *>(g.fc3 + (size_t)28 * bl);
+        for (; lb < lb_end; ++lb) {
+            const int4 bi = b_sm[lb];
+            const float4 *f4 = f_sm + 7 * (size_t)lb;
             float v[28];
 #pragma unroll
             for (int t = 0; t < 7; ++t) {
-                const float4 u = __ldg(f4 + t);
+                const float4 u = f4[t];
                 v[4 * t] = u.x; v[4 * t + 1] = u.y; v[4 * t + 2] = u.z; v[4 * t + 3] = u.w;
             }
             float2 u[3];
@@ -567,14 +585,24 @@ cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, L
     if (e != cudaSuccess) return e;
     const int nb = p.nb;
     const int gthreads = (nb + 31) / 32 * 32;
-    const size_t gsmem = sizeof(float2) * 2 * (size_t)std::max(1, p.n_rep);
+    const size_t gsmem = sizeof(float2) * 2 * (size_t)std::max(1, p.n_rep);   // per pair
+    const size_t gblk = (7 * sizeof(float4) + sizeof(int4)) * (size_t)std::max(1, g.max_part_blocks);
+    e = cudaFuncSetAttribute(ycx_gather_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(gblk + gsmem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ycx_gather_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(gblk + 2 * gsmem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ycx_gather_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(gblk + 4 * gsmem));
+    if (e != cudaSuccess) return e;
     const int mt = lanes[0].x.Mp / kBM;
     const int gx = (mt + tpc - 1) / tpc;
     const long long total = (long long)p.nq * p.nq;
-    // pairs per gather CTA: a divisor of nq and of the batch, so that the
-    // CTA's pairs share q (every batch starts at a multiple of the batch)
+    // pairs per gather CTA: 2 when that divides nq and the batch, so that the
+    // CTA's pairs share q (every batch starts at a multiple of the batch);
+    // 2 keeps the registers at ~80 per thread (4 needs ~130)
     int gp = 1;
-    for (int c = 4; c > 1; c /= 2)
+    for (int c = 2; c > 1; c /= 2)
         if (p.nq % c == 0 && batch % c == 0) { gp = c; break; }
     if (const char *env = std::getenv("KALD_TCX_GP")) {
         const int v = std::atoi(env);
@@ -593,13 +621,13 @@ cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, L
         x.pair0 = p0;
         x.n_pairs = (int)std::min<long long>(batch, total - p0);
         if (gp == 4)
-            ycx_gather_kernel<4><<<counted(dim3(g.n_parts, x.n_pairs / 4)), gthreads, 4 * gsmem, L.st>>>(
+            ycx_gather_kernel<4><<<counted(dim3(g.n_parts, x.n_pairs / 4)), gthreads, gblk + 4 * gsmem, L.st>>>(
                 x, g, ew, cw, p.n_rep, L.a1h, L.a1l);
         else if (gp == 2)
-            ycx_gather_kernel<2><<<counted(dim3(g.n_parts, x.n_pairs / 2)), gthreads, 2 * gsmem, L.st>>>(
+            ycx_gather_kernel<2><<<counted(dim3(g.n_parts, x.n_pairs / 2)), gthreads, gblk + 2 * gsmem, L.st>>>(
                 x, g, ew, cw, p.n_rep, L.a1h, L.a1l);
         else
-            ycx_gather_kernel<1><<<counted(dim3(g.n_parts, x.n_pairs)), gthreads, gsmem, L.st>>>(x, g, ew, cw, p.n_rep,
+            ycx_gather_kernel<1><<<counted(dim3(g.n_parts, x.n_pairs)), gthreads, gblk + gsmem, L.st>>>(x, g, ew, cw, p.n_rep,
                                                                                         L.a1h, L.a1l);
         k1<<<counted(dim3(gx, x.n_pairs)), kWsThreads, smem, L.st>>>(L.maps[0], L.maps[1], L.maps[2], L.maps[3], L.maps[4],
                                                               x, tpc, err);
