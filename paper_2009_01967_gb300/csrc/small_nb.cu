@@ -31,19 +31,53 @@ __device__ __forceinline__ R2 cmul(R2 a, R2 b) {
     r.y = a.x * b.y + a.y * b.x;
     return r;
 }
-template <typename R2>
-__device__ __forceinline__ void cfma(R2 &acc, R2 a, R2 b) {      // acc += a b
+// FP64: scalar FMAs; FP32: packed FP32x2 FMAs (two lanes of the complex
+// value per instruction).
+__device__ __forceinline__ void cfma(double2 &acc, double2 a, double2 b) {      // acc += a b
     acc.x = fma(a.x, b.x, acc.x);
     acc.x = fma(-a.y, b.y, acc.x);
     acc.y = fma(a.x, b.y, acc.y);
     acc.y = fma(a.y, b.x, acc.y);
 }
-template <typename R2>
-__device__ __forceinline__ void cfma_conj(R2 &acc, R2 a, R2 b) { // acc += a conj(b)
+__device__ __forceinline__ void cfma(float2 &acc, float2 a, float2 b) {
+    acc = __ffma2_rn(make_float2(a.x, a.x), b, acc);
+    acc = __ffma2_rn(make_float2(-a.y, a.y), make_float2(b.y, b.x), acc);
+}
+__device__ __forceinline__ void cfma_conj(double2 &acc, double2 a, double2 b) { // acc += a conj(b)
     acc.x = fma(a.x, b.x, acc.x);
     acc.x = fma(a.y, b.y, acc.x);
     acc.y = fma(a.y, b.x, acc.y);
     acc.y = fma(-a.x, b.y, acc.y);
+}
+__device__ __forceinline__ void cfma_conj(float2 &acc, float2 a, float2 b) {
+    acc = __ffma2_rn(make_float2(b.x, b.x), a, acc);
+    acc = __ffma2_rn(make_float2(b.y, -b.y), make_float2(a.y, a.x), acc);
+}
+// acc += v * e (v real)
+__device__ __forceinline__ void rfma(double2 &acc, double v, double2 e) {
+    acc.x = fma(v, e.x, acc.x);
+    acc.y = fma(v, e.y, acc.y);
+}
+__device__ __forceinline__ void rfma(float2 &acc, float v, float2 e) {
+    acc = __ffma2_rn(make_float2(v, v), e, acc);
+}
+
+// The 28 (27 + pad) values of one Phi3 block, as 16-byte loads.
+__device__ __forceinline__ void load_block(const float *f, float v[28]) {
+    const float4 *f4 = reinterpret_cast<const float4 *>(f);
+#pragma unroll
+    for (int x = 0; x < 7; ++x) {
+        const float4 u = __ldg(f4 + x);
+        v[4 * x] = u.x; v[4 * x + 1] = u.y; v[4 * x + 2] = u.z; v[4 * x + 3] = u.w;
+    }
+}
+__device__ __forceinline__ void load_block(const double *f, double v[28]) {
+    const double2 *f2 = reinterpret_cast<const double2 *>(f);
+#pragma unroll
+    for (int x = 0; x < 14; ++x) {
+        const double2 u = __ldg(f2 + x);
+        v[2 * x] = u.x; v[2 * x + 1] = u.y;
+    }
 }
 
 // roots[t] = exp(-2 pi i (t - m0) / L), argument reduced to [0, L) first.
@@ -109,12 +143,13 @@ sn_kernel(LwParams p, LwDev d, SnTables t, const R *__restrict__ fc3, const type
                 R2 e[3];
 #pragma unroll
                 for (int x = 0; x < 3; ++x) e[x] = cmul(eq[(3 * bj.x + x) * NB + s], ph);
-                const R *f = fc3 + (size_t)28 * bl;
+                R v[28];
+                load_block(fc3 + (size_t)28 * bl, v);
 #pragma unroll
                 for (int x = 0; x < 9; ++x) {
-                    const R v0 = __ldg(f + x), v1 = __ldg(f + 9 + x), v2 = __ldg(f + 18 + x);
-                    acc[x].x = fma(v0, e[0].x, fma(v1, e[1].x, fma(v2, e[2].x, acc[x].x)));
-                    acc[x].y = fma(v0, e[0].y, fma(v1, e[1].y, fma(v2, e[2].y, acc[x].y)));
+                    rfma(acc[x], v[18 + x], e[2]);
+                    rfma(acc[x], v[9 + x], e[1]);
+                    rfma(acc[x], v[x], e[0]);
                 }
             }
             // add the group's 3x3 block at atoms (j, k) with constant register indices
