@@ -388,7 +388,7 @@ ycx_gather_kernel(XParams x, TcxGroups g, const float2 *__restrict__ epsT_all,
                   __nv_bfloat16 *__restrict__ a1l) {
     // shared memory: the part's blocks (7 float4 of Phi3 + one int4 each, in
     // processing order), then chi(q', R), chi(q'', R) of the P pairs
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     float4 *f_sm = reinterpret_cast<float4 *>(smem_raw);
     int4 *b_sm = reinterpret_cast<int4 *>(f_sm + 7 * (size_t)g.max_part_blocks);
     float2 *chi_sm = reinterpret_cast<float2 *>(b_sm + g.max_part_blocks);
