@@ -109,6 +109,21 @@ def dist_env():
     return rank, world, local
 
 
+def job_throughput(local_ms: float, world: int, units_per_step: float, steps: int, device=None):
+    """Whole-job rate of N replicas (weak scaling, no data-path collective):
+    the slowest rank's time (max over ranks) for `steps` steps, and
+    world * units_per_step * steps / that time.  The max is one all-reduce on
+    `device` (a CUDA device under NCCL, the CPU under gloo)."""
+    total_ms = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, world * units_per_step * steps / (total_ms / 1e3)
+
+
 # ------------------------------------------------------------- oracle timing
 def time_oracle_sample(w, n_q: int = 1, n_modes: int = 4):
     """Oracle on a bounded sample of the workload: for a crystal, phonons on
@@ -246,13 +261,8 @@ def run_kald(args):
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
     triplets_step = sum(nq * nq * b ** 3 for b in nbs)
-    value = world * triplets_step * args.steps / (total_ms / 1e3)
+    total_ms, value = job_throughput(float(sum(step_ms)), world, triplets_step, args.steps, device=dev)
 
     # ---- end to end through host buffers (pinned), same calls
     nu_h = torch.zeros(n_modes, dtype=torch.float64).pin_memory().numpy()
