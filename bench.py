@@ -301,7 +301,7 @@ def run_kald(args):
                 om = 2 * np.pi * nu_c[offs_m[x]:offs_m[x + 1]]
                 om = np.where(nu_c[offs_m[x]:offs_m[x + 1]] > opt.omega_min_thz, om, 0.0)
                 nt = -(-b // 128)
-                ld = -(-b // 64) * 64
+                ld = -(-b // 128) * 128
                 lo = np.full(nt, np.inf); hi = np.full(nt, -np.inf)
                 for m in range(b):
                     if om[m] > 0:

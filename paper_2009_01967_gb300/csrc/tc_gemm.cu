@@ -10,7 +10,8 @@
 // Kernel shape (one 128 x 128 output tile per CTA, 128 threads):
 //   warp 0 lane 0   TMA producer: 4 tiled loads per K block of 64 (A hi/lo,
 //                   B hi/lo; 128-byte swizzle), 3-stage ring of mbarriers
-//   warp 1          allocates 128 TMEM columns; lane 0 issues the MMAs
+//   warp 1          allocates 512 TMEM columns (four accumulators, K blocks
+//                   round-robin); lane 0 issues the MMAs
 //                   (M = 128, N = 128, K = 16, kind::f16, BF16 in, FP32 out)
 //                   and commits each stage back to the producer
 //   warps 0-3       epilogue: tcgen05.ld of their 32 accumulator lanes
@@ -32,6 +33,12 @@ namespace {
 
 constexpr int kBM = 128, kBN = 128, kBK = 64;      // tile; 64 BF16 = one 128-byte swizzle row
 constexpr int kStages = 3;
+// The K loop is spread round-robin over kAcc accumulators (all 512 TMEM
+// columns) that the epilogue adds in FP32: a long chain of tensor-core
+// accumulations (2592 / 16 x 3 for the 864-atom cell) drifts towards zero by
+// about 1e-5 relative; four chains of a quarter of the length keep gamma
+// within 1e-5 of the FP64 oracle.
+constexpr int kAcc = 4;
 constexpr int kTileBytes = kBM * kBK * 2;          // 16 KB per operand plane per stage
 constexpr int kStageBytes = 4 * kTileBytes;        // A hi, A lo, B hi, B lo
 
@@ -54,6 +61,17 @@ struct EpiSplit {
     __nv_bfloat16 *hi, *lo;   // [rows][ld] output planes
     int ld;
 };
+
+// Columns [c, c + 32) of the nacc accumulators, added in a fixed order.
+__device__ __forceinline__ void tmem_ld_sum(uint32_t taddr, int nacc, float v[32]) {
+    tmem_ld32(taddr, v);
+    for (int a = 1; a < nacc; ++a) {
+        float u[32];
+        tmem_ld32(taddr + (uint32_t)(a * kBN), u);
+#pragma unroll
+        for (int x = 0; x < 32; ++x) v[x] += u[x];
+    }
+}
 
 // C[m][n] = sum_k A[m][k] B[n][k]; A, B as BF16 hi/lo planes behind four
 // tensor maps (box 64 x 128, 128-byte swizzle).  Grid: one CTA per tile.
@@ -81,6 +99,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ 
         tm = blockIdx.y; tn = blockIdx.x;
     }
     const int nkb = (K + kBK - 1) / kBK;
+    const int nacc = min(kAcc, nkb);             // accumulators that received MMAs
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
@@ -90,7 +109,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ 
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"(smem_u32(&tmem_base_sm)), "r"(128) : "memory");
+                     ::"r"(smem_u32(&tmem_base_sm)), "r"(kAcc * kBN) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -124,9 +143,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ 
 #pragma unroll
             for (int k = 0; k < kBK / 16; ++k) {
                 const uint64_t dk = (uint64_t)((k * 32) >> 4);     // 16 BF16 = 32 B along K
-                mma_bf16(tmem, ah + dk, bh + dk, kIdesc, (kb > 0 || k > 0) ? 1u : 0u);
-                mma_bf16(tmem, ah + dk, bl + dk, kIdesc, 1u);
-                mma_bf16(tmem, al + dk, bh + dk, kIdesc, 1u);
+                const uint32_t dacc = tmem + (uint32_t)((kb % kAcc) * kBN);
+                mma_bf16(dacc, ah + dk, bh + dk, kIdesc, (kb >= kAcc || k > 0) ? 1u : 0u);
+                mma_bf16(dacc, ah + dk, bl + dk, kIdesc, 1u);
+                mma_bf16(dacc, al + dk, bh + dk, kIdesc, 1u);
             }
             mma_commit(&empty[s]);               // stage free once these MMAs finish
         }
@@ -152,7 +172,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ 
 #pragma unroll 1
         for (int c0 = 0; c0 < kBN; c0 += 32) {
             float v[32];
-            tmem_ld32(taddr + c0, v);
+            tmem_ld_sum(taddr + c0, nacc, v);
             if (!ok) continue;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -185,7 +205,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ 
 #pragma unroll 1
         for (int c0 = 0; c0 < kBN; c0 += 32) {
             float v[32];
-            tmem_ld32(taddr + c0, v);
+            tmem_ld_sum(taddr + c0, nacc, v);
             if (!(w1 > 0.0f)) continue;
 #pragma unroll 4
             for (int x = 0; x < 32; ++x) {
@@ -228,7 +248,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ 
     __syncthreads();
     if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kAcc * kBN)
+                     : "memory");
     }
 }
 
@@ -309,7 +330,7 @@ constexpr size_t kSmemBytes = kStages * kStageBytes + 1024;
 int tc_tile(void) { return kBM; }
 
 size_t tc_gamma_scratch_bytes(int nb) {
-    const int ld = (nb + kBK - 1) / kBK * kBK;
+    const int ld = (nb + kBN - 1) / kBN * kBN;     // whole 128-column tiles per row
     const int rows = (nb + kBM - 1) / kBM * kBM;
     return 6 * ws_round(sizeof(__nv_bfloat16) * (size_t)rows * ld) + ws_round(sizeof(int) * 4);
 }
@@ -321,7 +342,7 @@ cudaError_t launch_gamma_only_tc(const GammaPlan &gp, const GammaDev &d, const L
                                  int2 *tiles_dev, int symmetric, double *partial_tc, int *err,
                                  cudaStream_t st) {
     const int nb = p.nb;
-    const int ld = (nb + kBK - 1) / kBK * kBK;
+    const int ld = (nb + kBN - 1) / kBN * kBN;     // whole 128-column tiles per row
     const int rows = (nb + kBM - 1) / kBM * kBM;
     const size_t plane = ws_round(sizeof(__nv_bfloat16) * (size_t)rows * ld);
     char *b = static_cast<char *>(scratch);

@@ -348,7 +348,7 @@ def test_large_gamma_end_to_end_qhgk(k, big324):
 @pytest.mark.parametrize("kind", ["lj", "random_fc3"])
 def test_large_gamma_bf16split_tensor_cores(k, big324, kind):
     """tcgen05 BF16 hi+lo path (three MMAs per product, FP32 accumulation in
-    tensor memory).  The LJ system has a permutation-symmetric Phi3, so only
+    tensor memory), gamma within 1e-5 of the FP64 oracle.  The LJ system has a permutation-symmetric Phi3, so only
     the upper triangle of phi is computed; the random extra blocks break that
     symmetry and the full delta band is computed."""
     kk, ctx = k
@@ -362,4 +362,50 @@ def test_large_gamma_bf16split_tensor_cores(k, big324, kind):
     assert allowed == allowed64
     err = _rel(g, g_o, 1e-6 * g_o.max())
     print(f"bf16 split gamma max rel err {err:.3e}")
-    assert err < 1e-4
+    assert err < 1e-5
+
+
+def test_c3_bf16split_sampled_modes(k):
+    """The 864-atom Gamma-only workload (2592 modes) on tensor cores, at full
+    size in the benchmark's launch configuration, checked at sampled modes that
+    are not degenerate (so the oracle's unaveraged gamma applies)."""
+    kk, ctx = k
+    w = ki.c3()
+    s = w.systems[0]
+    nu_o, eig_o = ph.phonons(s, w.mesh)
+    g, (tot, allowed) = kk.kald_linewidths(ctx, s, w.mesh, nu_o, eig_o, _opts(kk, w, "bf16split"))
+    g = g.reshape(nu_o.shape)[0]
+    nu0 = nu_o[0]
+    modes = []
+    for m in (5, 700, 1300, 1900, 2500):
+        gap = min(abs(nu0[m] - nu0[m - 1]), abs(nu0[m + 1] - nu0[m]))
+        if gap > 1e-4:
+            modes.append(m)
+    assert len(modes) >= 3
+    g_o = an.linewidths_gamma_only(s, nu_o, eig_o, w.T, w.sigma_thz, w.n_sigma, modes=modes, average=False)
+    g64, _ = kk.kald_linewidths(ctx, s, w.mesh, nu_o, eig_o, _opts(kk, w, "fp64"))
+    g64 = g64.reshape(nu_o.shape)[0]
+    for m, go in zip(modes, g_o):
+        print(f"mode {m}: nu {nu0[m]:.5f} THz, oracle {go:.9e}, bf16 {g[m]:.9e}, fp64 {g64[m]:.9e}")
+    err = np.max(np.abs(g[modes] - g_o) / np.abs(g_o))
+    print(f"C3 bf16 split gamma max rel err {err:.3e} at modes {modes}")
+    assert err < 1e-5
+    assert tot == 2592 ** 3 and 0 < allowed < tot
+
+
+def test_c5_full_mesh_sampled_q(k):
+    """The 2-atom / 24^3 workload (13824 q-points) in the benchmark's launch
+    configuration (the FP32 register kernel behind the BF16-split request),
+    checked at sampled q-points against the oracle."""
+    kk, ctx = k
+    w = ki.c5()
+    s = w.systems[0]
+    nu_o, eig_o = ph.phonons(s, w.mesh)
+    g, (tot, allowed) = kk.kald_linewidths(ctx, s, w.mesh, nu_o, eig_o, _opts(kk, w, "bf16split"))
+    g = g.reshape(nu_o.shape)
+    qs = [1, 5000]
+    g_o = an.linewidths(s, w.mesh, nu_o, eig_o, w.T, w.sigma_thz, w.n_sigma, q_list=qs)
+    err = _rel(g[qs], g_o, 1e-6 * g_o.max())
+    print(f"C5 gamma max rel err {err:.3e}")
+    assert err < 1e-5
+    assert tot == 13824 ** 2 * 6 ** 3 and 0 < allowed < tot
