@@ -407,7 +407,9 @@ kald_status kald_phonons(kald_ctx *ctx, const kald_system *sys, const int32_t me
     if (!d_eig) cudaMemcpyAsync(eigvec, eig_d, sizeof(double2) * nn, cudaMemcpyDeviceToHost, s);
     if (vel && !d_vel) cudaMemcpyAsync(vel, vel_d, sizeof(double) * 3 * nq * nb, cudaMemcpyDeviceToHost, s);
     if ((st = finish(ctx, "kald_phonons"))) return st;
-    if (nc) return fail(ctx, KALD_E_NOCONV, "Jacobi eigensolver did not converge at " + std::to_string(nc) + " q-points");
+    if (nc)
+        return fail(ctx, KALD_E_NOCONV,
+                    "Jacobi eigensolver did not converge at " + std::to_string(nc) + " q-points");
     return KALD_OK;
 }
 

@@ -401,7 +401,10 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
                                 R g = (R)0;
                                 bool hit = false;
                                 if (fabs(dp) < cut) { g += (n1 - n2) * exp(-dp * dp * sig2inv); hit = true; }
-                                if (fabs(dm) < cut) { g += (R)0.5 * ((R)1 + n1 + n2) * exp(-dm * dm * sig2inv); hit = true; }
+                                if (fabs(dm) < cut) {
+                                    g += (R)0.5 * ((R)1 + n1 + n2) * exp(-dm * dm * sig2inv);
+                                    hit = true;
+                                }
                                 if (hit) {
                                     ++allowed;
                                     const R2 f = acc[r][c];

@@ -7,9 +7,10 @@
 //   phi(s, s', s'') = sum_c T'(s', c) conj(eps''(c, s'')),
 // run as real GEMMs on BF16 pieces with FP32 accumulation in tensor memory:
 // the data operand (Y, T') as hi + lo, the eigenvector operand as hi + lo
-// (three MMAs per product) or, for nb <= 64, hi + mid + lo (five MMAs).  With H = nb rounded up to 32, K' = 2H
-// (k' < H: real part of index b or c, k' >= H: imaginary part) and the
-// row count M = nb^2 padded to a multiple of 128:
+// (three MMAs per product) or, for nb <= 64, hi + mid + lo (five MMAs).
+// With H = nb rounded up to 32, K' = 2H (k' < H: real part of index b or c,
+// k' >= H: imaginary part) and the row count M = nb^2 padded to a multiple
+// of 128:
 //   A1[pair][k'][m],  m = c nb + s:  (Re Y_s(b, c) | Im Y_s(b, c))   (gather, CUDA cores)
 //   B1[q'][n'][k']    n' = s': (Re eps' | -Im eps'),  n' = H + s': (Im eps' | Re eps')
 //   GEMM1 row m = (c, s), column n' = Re / Im T'(s', c), stored as
@@ -102,9 +103,9 @@ __device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo_half, __nv_bflo
 // z = q' for GEMM1, q'' for GEMM2.  Warp-specialised and persistent over the
 // CTA's tiles: warp 0 issues TMA (B once, resident; A through a two-stage
 // ring), warp 1 issues the MMAs into one of two TMEM accumulators (at
-// column 0 and at half the allocation), warps 4..11 run the epilogue of the previous tile meanwhile (warp w reads TMEM
-// lanes 32 (w % 4) ..; warps 4..7 take one half of the columns, 8..11 the
-// other).  Every wait is bounded; a failed wait sets *err and the CTA winds
+// column 0 and at half the allocation), warps 4..11 run the epilogue of
+// the previous tile meanwhile (warp w reads TMEM lanes 32 (w % 4) ..; warps
+// 4..7 take one half of the columns, 8..11 the other).  Every wait is bounded; a failed wait sets *err and the CTA winds
 // down without touching memory it does not own.
 constexpr int kWsThreads = 384;
 constexpr int kEpiWarps = 8;
@@ -627,12 +628,12 @@ cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, L
             ycx_gather_kernel<2><<<counted(dim3(g.n_parts, x.n_pairs / 2)), gthreads, gblk + 2 * gsmem, L.st>>>(
                 x, g, ew, cw, p.n_rep, L.a1h, L.a1l);
         else
-            ycx_gather_kernel<1><<<counted(dim3(g.n_parts, x.n_pairs)), gthreads, gblk + gsmem, L.st>>>(x, g, ew, cw, p.n_rep,
-                                                                                        L.a1h, L.a1l);
-        k1<<<counted(dim3(gx, x.n_pairs)), kWsThreads, smem, L.st>>>(L.maps[0], L.maps[1], L.maps[2], L.maps[3], L.maps[4],
-                                                              x, tpc, err);
-        k2<<<counted(dim3(gx, x.n_pairs)), kWsThreads, smem, L.st>>>(L.maps[5], L.maps[6], L.maps[7], L.maps[8], L.maps[9],
-                                                              x, tpc, err);
+            ycx_gather_kernel<1><<<counted(dim3(g.n_parts, x.n_pairs)), gthreads, gblk + gsmem, L.st>>>(
+                x, g, ew, cw, p.n_rep, L.a1h, L.a1l);
+        k1<<<counted(dim3(gx, x.n_pairs)), kWsThreads, smem, L.st>>>(L.maps[0], L.maps[1], L.maps[2], L.maps[3],
+                                                                    L.maps[4], x, tpc, err);
+        k2<<<counted(dim3(gx, x.n_pairs)), kWsThreads, smem, L.st>>>(L.maps[5], L.maps[6], L.maps[7], L.maps[8],
+                                                                    L.maps[9], x, tpc, err);
         e = cudaEventRecord(L.done[(i >> 1) & 1], L.st);
         if (e != cudaSuccess) return e;
         // q values completed by this batch

@@ -409,3 +409,27 @@ def test_c5_full_mesh_sampled_q(k):
     print(f"C5 gamma max rel err {err:.3e}")
     assert err < 1e-5
     assert tot == 13824 ** 2 * 6 ** 3 and 0 < allowed < tot
+
+
+@pytest.mark.parametrize("cell", ["binary", "fcc4"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16split"])
+def test_no_third_order_blocks_gives_zero_gamma(k, cell, precision):
+    """Degenerate input: without Phi3 blocks every projection vanishes, so
+    gamma is exactly zero in every path (register kernel for the 2-atom cell,
+    tensor cores or CUDA cores for the 4-atom cell), while the delta-allowed
+    count, which depends on the frequencies only, is unchanged."""
+    kk, ctx = k
+    if cell == "binary":
+        w = ki.small_binary(mesh=(3, 3, 3), sigma=0.1)
+        base = w.systems[0]
+    else:
+        base = ki.fcc_supercell_system(1, seed=7)
+        w = ki.Workload("fcc4", [base], (3, 3, 3), 300.0, 0.1, 3.0)
+    empty = ki.System(base.masses.copy(), base.positions.copy(), base.lattice.copy(),
+                      base.fc2_idx.copy(), base.fc2.copy(), np.zeros((0, 9), dtype=np.int32),
+                      np.zeros((0, 3, 3, 3)), name=base.name + "_no_fc3")
+    nu_o, eig_o = ph.phonons(base, w.mesh)
+    g0, (tot0, al0) = kk.kald_linewidths(ctx, empty, w.mesh, nu_o, eig_o, _opts(kk, w, precision))
+    _, (tot1, al1) = kk.kald_linewidths(ctx, base, w.mesh, nu_o, eig_o, _opts(kk, w, precision))
+    assert np.all(g0 == 0.0)
+    assert tot0 == tot1 and al0 == al1 > 0
