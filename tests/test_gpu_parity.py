@@ -433,3 +433,30 @@ def test_no_third_order_blocks_gives_zero_gamma(k, cell, precision):
     _, (tot1, al1) = kk.kald_linewidths(ctx, base, w.mesh, nu_o, eig_o, _opts(kk, w, precision))
     assert np.all(g0 == 0.0)
     assert tot0 == tot1 and al0 == al1 > 0
+
+
+@pytest.mark.parametrize("case", ["C2_mesh4", "C5_mesh8"])
+def test_kappa_split_path_against_fp64_gpu_path(k, case):
+    """kappa time-to-solution path: the BF16-split linewidths give kappa_RTA
+    within 1e-4 (relative to the largest component) of the plain FP64 GPU
+    path on the same GB300; both timings are printed."""
+    import time
+    kk, ctx = k
+    if case == "C2_mesh4":
+        w = ki.c2()
+        w.mesh = (4, 4, 4)
+    else:
+        w = ki.c5(mesh=(8, 8, 8))
+    s = w.systems[0]
+    nu, eig = kk.kald_phonons(ctx, s, w.mesh)[:2]
+    kap = {}
+    for prec in ("fp64", "bf16split"):
+        t0 = time.perf_counter()
+        g, _ = kk.kald_linewidths(ctx, s, w.mesh, nu, eig, _opts(kk, w, prec))
+        kap[prec] = kk.kald_kappa_rta(ctx, s, w.mesh, nu, eig, g, _opts(kk, w, prec))
+        print(f"{case} {prec}: linewidths + kappa {time.perf_counter() - t0:.3f} s, "
+              f"kappa_xx {kap[prec][0][0]:.6e}")
+    a, b = np.asarray(kap["bf16split"]), np.asarray(kap["fp64"])
+    err = np.max(np.abs(a - b)) / np.max(np.abs(b))
+    print(f"{case}: kappa split vs fp64 rel err {err:.3e}")
+    assert err < 1e-4
