@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <numeric>
 #include <array>
@@ -183,6 +184,22 @@ kald_status set_device(kald_ctx *ctx) {
 
 }  // namespace
 
+// Stable order of n items by an integer key in [0, n_keys): a counting sort
+// when the key range is modest, else a stable comparison sort.
+static std::vector<int> stable_key_order(int n, long long n_keys, const std::function<long long(int)> &key) {
+    std::vector<int> o(n);
+    if (n_keys <= (1LL << 22)) {
+        std::vector<int> cnt((size_t)n_keys + 1, 0);
+        for (int t = 0; t < n; ++t) ++cnt[(size_t)key(t) + 1];
+        for (long long k = 0; k < n_keys; ++k) cnt[(size_t)k + 1] += cnt[(size_t)k];
+        for (int t = 0; t < n; ++t) o[cnt[(size_t)key(t)]++] = t;
+    } else {
+        std::iota(o.begin(), o.end(), 0);
+        std::stable_sort(o.begin(), o.end(), [&](int a, int b) { return key(a) < key(b); });
+    }
+    return o;
+}
+
 kald_status plan_system(kald_ctx *ctx, const kald_system *s, HostSystem &h) {
     if (!s) return fail(ctx, KALD_E_INVALID, "system is NULL");
     const int n = s->n_atoms;
@@ -220,11 +237,9 @@ kald_status plan_system(kald_ctx *ctx, const kald_system *s, HostSystem &h) {
         if (x[0] < 0 || x[0] >= n || x[1] < 0 || x[1] >= n)
             return fail(ctx, KALD_E_INVALID, "fc2_idx atom index out of range");
     }
-    std::vector<int> o2(n2);
-    std::iota(o2.begin(), o2.end(), 0);
-    std::stable_sort(o2.begin(), o2.end(), [&](int a, int b) {
-        const int32_t *x = s->fc2_idx + 5 * (size_t)a, *y = s->fc2_idx + 5 * (size_t)b;
-        return std::make_pair(x[0], x[1]) < std::make_pair(y[0], y[1]);
+    const std::vector<int> o2 = stable_key_order(n2, (long long)n * n, [&](int b) {
+        const int32_t *x = s->fc2_idx + 5 * (size_t)b;
+        return (long long)x[0] * n + x[1];
     });
     h.fc2_scaled.resize(9 * (size_t)n2);
     h.fc2_rcart.resize(3 * (size_t)n2);
@@ -249,13 +264,30 @@ kald_status plan_system(kald_ctx *ctx, const kald_system *s, HostSystem &h) {
     h.pair2_start.push_back(n2);
     // ---- fc3, grouped by (j, k) output pair; replica table
     const int n3 = s->n_fc3;
+    // replica index of an integer cell vector, in first-seen order: a dense
+    // table over the vectors' bounding cube when it is small, else a map
+    long long bmax = 0;
+    for (int b = 0; b < n3; ++b)
+        for (int d = 0; d < 3; ++d)
+            bmax = std::max<long long>(bmax, std::max(std::llabs((long long)s->fc3_idx[9 * (size_t)b + 2 + d]),
+                                                      std::llabs((long long)s->fc3_idx[9 * (size_t)b + 6 + d])));
+    const long long span = 2 * bmax + 1;
+    const bool dense = span * span * span <= (1LL << 22);
+    std::vector<int> rep_slot(dense ? (size_t)(span * span * span) : 0, -1);
     std::map<std::tuple<int, int, int>, int> rep_index;
+    int n_rep = 0;
     auto rep_of = [&](const int32_t *R) {
-        auto key = std::make_tuple((int)R[0], (int)R[1], (int)R[2]);
-        auto it = rep_index.find(key);
-        if (it != rep_index.end()) return it->second;
-        const int id = (int)rep_index.size();
-        rep_index.emplace(key, id);
+        int *slot = nullptr;
+        if (dense) {
+            slot = &rep_slot[(size_t)(((R[0] + bmax) * span + (R[1] + bmax)) * span + (R[2] + bmax))];
+            if (*slot >= 0) return *slot;
+        } else {
+            auto it = rep_index.find(std::make_tuple((int)R[0], (int)R[1], (int)R[2]));
+            if (it != rep_index.end()) return it->second;
+        }
+        const int id = n_rep++;
+        if (dense) *slot = id;
+        else rep_index.emplace(std::make_tuple((int)R[0], (int)R[1], (int)R[2]), id);
         double c[3];
         cart(R, c);
         h.rep_cart.insert(h.rep_cart.end(), c, c + 3);
@@ -273,11 +305,9 @@ kald_status plan_system(kald_ctx *ctx, const kald_system *s, HostSystem &h) {
         if (x[0] < 0 || x[0] >= n || x[1] < 0 || x[1] >= n || x[5] < 0 || x[5] >= n)
             return fail(ctx, KALD_E_INVALID, "fc3_idx atom index out of range");
     }
-    std::vector<int> o3(n3);
-    std::iota(o3.begin(), o3.end(), 0);
-    std::stable_sort(o3.begin(), o3.end(), [&](int a, int b) {
-        const int32_t *x = s->fc3_idx + 9 * (size_t)a, *y = s->fc3_idx + 9 * (size_t)b;
-        return std::make_pair(x[1], x[5]) < std::make_pair(y[1], y[5]);
+    const std::vector<int> o3 = stable_key_order(n3, (long long)n * n, [&](int b) {
+        const int32_t *x = s->fc3_idx + 9 * (size_t)b;
+        return (long long)x[1] * n + x[5];
     });
     h.fc3_scaled.resize(27 * (size_t)n3);
     h.fc3_i.resize(n3); h.fc3_rj.resize(n3); h.fc3_rk.resize(n3);
@@ -296,7 +326,88 @@ kald_status plan_system(kald_ctx *ctx, const kald_system *s, HostSystem &h) {
         h.fc3_rk[t] = rep_of(x + 6);
     }
     h.pair3_start.push_back(n3);
-    h.n_rep = (int)rep_index.size();
+    h.n_rep = n_rep;
+    return KALD_OK;
+}
+
+// 128-bit content hash (two multiply-xor lanes over 64-bit words).
+struct Hash2 {
+    uint64_t a = 0x243F6A8885A308D3ull, b = 0x13198A2E03707344ull;
+    void word(uint64_t w) {
+        a = (a ^ w) * 0x9E3779B97F4A7C15ull;
+        a ^= a >> 29;
+        b = (b ^ (w + 0x632BE59BD9B4E019ull)) * 0xC2B2AE3D27D4EB4Full;
+        b ^= b >> 31;
+    }
+    void bytes(const void *p, size_t n) {
+        const unsigned char *c = static_cast<const unsigned char *>(p);
+        size_t i = 0;
+        // four independent chains over 32-byte strides, folded in at the end
+        uint64_t l[4] = {0x452821E638D01377ull, 0xBE5466CF34E90C6Cull, 0xC0AC29B7C97C50DDull,
+                         0x3F84D5B5B5470917ull};
+        for (; i + 32 <= n; i += 32) {
+            for (int k = 0; k < 4; ++k) {
+                uint64_t w;
+                std::memcpy(&w, c + i + 8 * k, 8);
+                l[k] = (l[k] ^ w) * 0x9E3779B97F4A7C15ull;
+                l[k] ^= l[k] >> 29;
+            }
+        }
+        for (int k = 0; k < 4; ++k) word(l[k]);
+        for (; i + 8 <= n; i += 8) {
+            uint64_t w;
+            std::memcpy(&w, c + i, 8);
+            word(w);
+        }
+        uint64_t t = 0;
+        for (size_t k = 0; i < n; ++i, ++k) t |= (uint64_t)c[i] << (8 * k);
+        word(t ^ ((uint64_t)n << 56));
+    }
+};
+
+kald_status plan_system_cached(kald_ctx *ctx, const kald_system *s, std::shared_ptr<const HostSystem> &out) {
+    if (!s) return fail(ctx, KALD_E_INVALID, "system is NULL");
+    if (s->n_atoms <= 0 || s->n_fc2 < 0 || s->n_fc3 < 0 || !s->masses || !s->positions ||
+        (s->n_fc2 && (!s->fc2 || !s->fc2_idx)) || (s->n_fc3 && (!s->fc3 || !s->fc3_idx)) ||
+        is_device_ptr(s->masses) || is_device_ptr(s->positions) || is_device_ptr(s->fc2) ||
+        is_device_ptr(s->fc3) || is_device_ptr(s->fc2_idx) || is_device_ptr(s->fc3_idx)) {
+        HostSystem h;                              // reports the error
+        return plan_system(ctx, s, h);
+    }
+    Hash2 hs;
+    hs.word((uint64_t)s->n_atoms);
+    hs.word((uint64_t)s->n_fc2);
+    hs.word((uint64_t)s->n_fc3);
+    hs.bytes(&s->lattice[0][0], sizeof(double) * 9);
+    hs.bytes(s->masses, sizeof(double) * (size_t)s->n_atoms);
+    hs.bytes(s->positions, sizeof(double) * 3 * (size_t)s->n_atoms);
+    if (s->n_fc2) {
+        hs.bytes(s->fc2_idx, sizeof(int32_t) * 5 * (size_t)s->n_fc2);
+        hs.bytes(s->fc2, sizeof(double) * 9 * (size_t)s->n_fc2);
+    }
+    if (s->n_fc3) {
+        hs.bytes(s->fc3_idx, sizeof(int32_t) * 9 * (size_t)s->n_fc3);
+        hs.bytes(s->fc3, sizeof(double) * 27 * (size_t)s->n_fc3);
+    }
+    for (size_t x = 0; x < ctx->plans.size(); ++x)
+        if (ctx->plans[x].k0 == hs.a && ctx->plans[x].k1 == hs.b) {
+            out = ctx->plans[x].h;
+            return KALD_OK;
+        }
+    auto h = std::make_shared<HostSystem>();
+    kald_status st = plan_system(ctx, s, *h);
+    if (st) return st;
+    const size_t bytes = sizeof(double) * (h->fc3_scaled.size() + h->fc2_scaled.size() + 6 * h->fc2_rcart.size()) +
+                         sizeof(int) * 4 * h->fc3_i.size();
+    // keep at most 32 plans and 1 GB of them, dropping the oldest
+    size_t total = bytes;
+    for (const auto &p : ctx->plans) total += p.bytes;
+    while (!ctx->plans.empty() && (ctx->plans.size() >= 32 || total > (size_t(1) << 30))) {
+        total -= ctx->plans.front().bytes;
+        ctx->plans.erase(ctx->plans.begin());
+    }
+    ctx->plans.push_back({hs.a, hs.b, h, bytes});
+    out = h;
     return KALD_OK;
 }
 
@@ -361,8 +472,9 @@ kald_status kald_phonons(kald_ctx *ctx, const kald_system *sys, const int32_t me
     if (st) return st;
     if ((st = check_mesh(ctx, mesh))) return st;
     if (!nu_thz || !eigvec) return fail(ctx, KALD_E_INVALID, "nu_thz/eigvec NULL");
-    HostSystem h;
-    if ((st = plan_system(ctx, sys, h))) return st;
+    std::shared_ptr<const HostSystem> hp;
+    if ((st = plan_system_cached(ctx, sys, hp))) return st;
+    const HostSystem &h = *hp;
     const int nb = h.nb;
     const bool large = nb > kMaxNbSmall;
     if (large && (mesh[0] != 1 || mesh[1] != 1 || mesh[2] != 1))
@@ -511,8 +623,9 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
     uint64_t tot = 0, allowed_tot = 0;
     size_t off_nb = 0, off_eig = 0;
     for (int x = 0; x < n_sys; ++x) {
-        HostSystem h;
-        if ((st = plan_system(ctx, &sys[x], h))) return st;
+        std::shared_ptr<const HostSystem> hp;
+        if ((st = plan_system_cached(ctx, &sys[x], hp))) return st;
+        const HostSystem &h = *hp;
         const int nb = h.nb;
         if (nb > kMaxNbSmall && nq_mesh != 1)
             return fail(ctx, KALD_E_UNSUPPORTED, "kald_linewidths: nb > 96 needs mesh {1,1,1}");
@@ -535,7 +648,8 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
             const int mode = opt->precision;     // 0 FP64, 1 FP32, 2 BF16 split (tensor cores)
             const size_t rs = fp32 ? sizeof(float) : sizeof(double);
             if (mode == KALD_BF16_SPLIT) {
-                gp.symmetric = fc3_symmetric_last_two(&sys[x]) ? 1 : 0;
+                if (h.fc3_symmetric < 0) h.fc3_symmetric = fc3_symmetric_last_two(&sys[x]) ? 1 : 0;
+                gp.symmetric = h.fc3_symmetric;
                 band_tiles(gp.omega_h, tc_tile(), opt->n_sigma * kTwoPi * opt->sigma_thz, gp.symmetric,
                            gp.tiles, gp.tile_start);
             }
@@ -790,8 +904,9 @@ kald_status kald_kappa_rta(kald_ctx *ctx, const kald_system *sys, const int32_t 
     if ((st = check_mesh(ctx, mesh))) return st;
     if ((st = check_options(ctx, opt))) return st;
     if (!nu_thz || !eigvec || !gamma || !kappa) return fail(ctx, KALD_E_INVALID, "NULL array");
-    HostSystem h;
-    if ((st = plan_system(ctx, sys, h))) return st;
+    std::shared_ptr<const HostSystem> hp;
+    if ((st = plan_system_cached(ctx, sys, hp))) return st;
+    const HostSystem &h = *hp;
     const int nb = h.nb;
     if (nb > kMaxNbSmall) return fail(ctx, KALD_E_UNSUPPORTED, "kald_kappa_rta: nb <= 96");
     std::vector<double> qc;
@@ -836,8 +951,9 @@ kald_status kald_kappa_qhgk(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
     const bool d_k = is_device_ptr(kappa), d_v = vgen && is_device_ptr(vgen);
     size_t off_nb = 0, off_eig = 0;
     for (int x = 0; x < n_sys; ++x) {
-        HostSystem h;
-        if ((st = plan_system(ctx, &sys[x], h))) return st;
+        std::shared_ptr<const HostSystem> hp;
+        if ((st = plan_system_cached(ctx, &sys[x], hp))) return st;
+        const HostSystem &h = *hp;
         const int nb = h.nb;
         const size_t nn = (size_t)nb * nb;
         // CSR by row atom i: the (i, j) sorted fc2 order is contiguous in i

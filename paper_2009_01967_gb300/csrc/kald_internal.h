@@ -6,6 +6,7 @@
 
 #include <atomic>
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -31,6 +32,9 @@ constexpr int kMaxDegen = 96;      // largest degenerate set handled
 }  // namespace kald
 
 // ---- context -----------------------------------------------------------------
+namespace kald {
+struct HostSystem;
+}
 struct kald_ctx {
     int device = 0;
     cudaStream_t own_stream = nullptr;
@@ -41,6 +45,14 @@ struct kald_ctx {
     std::string err;
     int sm_count = 0;
     size_t smem_optin = 0;
+    // host plans of recently seen systems, keyed by a 128-bit hash of their
+    // whole content (oldest first)
+    struct Plan {
+        uint64_t k0, k1;
+        std::shared_ptr<const kald::HostSystem> h;
+        size_t bytes;
+    };
+    std::vector<Plan> plans;
 };
 
 namespace kald {
@@ -89,10 +101,14 @@ struct HostSystem {
     std::vector<double> rep_cart;                      // [n_rep][3]
     std::vector<int> rep_int;                          // [n_rep][3] integer cell vectors
     int n_rep = 0;
+    mutable int fc3_symmetric = -1;                    // Phi3 symmetric in its last two indices (lazy)
 };
 
 // Validate and plan one kald_system (host).  Returns KALD_OK or an error.
 kald_status plan_system(kald_ctx *ctx, const kald_system *s, HostSystem &h);
+// The same through the context's plan cache: a system whose content (sizes,
+// geometry, masses, force constants) hashes to a cached plan reuses it.
+kald_status plan_system_cached(kald_ctx *ctx, const kald_system *s, std::shared_ptr<const HostSystem> &h);
 
 kald_status check_mesh(kald_ctx *ctx, const int32_t mesh[3]);
 
