@@ -1,19 +1,32 @@
 // FP64 eigensolver for one real symmetric matrix too large for the per-q
 // Jacobi kernel (the dynamical matrix of a Gamma-only supercell, nb > 96;
-// paper Eq. eigenvectors: D eta = omega^2 eta).
+// the eigenproblem of Section 2: D eta = omega^2 eta).
 //
-//   1. Householder tridiagonalisation: for k = 0 .. n-3 the reflector
-//      H = I - 2 v v^T (|v| = 1) maps column k below the diagonal onto alpha e1;
-//      the trailing block becomes A - v w^T - w v^T with p = A v,
-//      w = 2 (p - (v.p) v).  v is kept in column k below the diagonal.
-//   2. Bisection with Sturm counts (number of negative pivots of T - x I)
-//      gives eigenvalue i to full precision, one thread per eigenvalue.
+//   1. Householder tridiagonalisation.  Reflector k (k = 0 .. n-3) is
+//      H_k = I - 2 v v^T (|v| = 1) mapping row k right of the diagonal onto
+//      alpha e1; with p = A v, K = v.p and w = 2 (p - K v) the trailing block
+//      becomes A - v w^T - w v^T.  One launch per reflector: every CTA rebuilds
+//      the updated row k+1 from the stored row, v_k and w_k (O(n) work, repeated
+//      per CTA, so no grid-wide barrier is needed), forms v_{k+1}, and then, for
+//      its share of the rows below, applies the rank-2 update of reflector k
+//      and takes the dot product with v_{k+1} (the matrix-vector product of the
+//      next reflector) in the same pass.  v_k is kept in row k right of the
+//      diagonal (contiguous, read by the back-transformation).
+//   2. Gershgorin interval and |T| on the device, then multisection with
+//      Sturm counts (number of negative pivots of T - x I), one warp per
+//      eigenvalue, to an interval of max(eps |T|, 2 eps |lambda|).
 //   3. Inverse iteration: (T - lambda_i I) x = b solved by tridiagonal LU with
-//      partial pivoting (a zero pivot is replaced by eps |T|), three solves.
+//      partial pivoting (a zero pivot is replaced by eps |T|), three solves;
+//      vectors stored component-major X[j][i] so neighbouring threads touch
+//      neighbouring addresses.
 //   4. Vectors of eigenvalues closer than 1e-9 |T| (near-degenerate sets) are
-//      orthonormalised by modified Gram-Schmidt inside each set.
-//   5. Back-transformation z <- H_0 H_1 ... H_{n-3} z.
-// Output: ascending eigenvalues and row-major eigenvectors Zt[s][d].
+//      orthonormalised by modified Gram-Schmidt inside each set; the sets are
+//      found on the device (one CTA per possible set start).
+//   5. Back-transformation z <- H_0 H_1 ... H_{n-3} z: each CTA holds a few
+//      vectors in shared memory and applies all reflectors to them, then
+//      writes eigenvalues (as frequencies) and row-major eigenvectors [s][d].
+// No host synchronisation inside: every stage reads its scalars from device
+// memory.
 
 #include <algorithm>
 #include <cmath>
@@ -23,9 +36,24 @@
 namespace kald {
 namespace {
 
+constexpr double kEps = 2.220446049250313e-16;
+constexpr int kTriThreads = 512;
+
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// Sum over the CTA; every warp reduces the per-warp partials with the same
+// shuffle tree, so all threads (and all CTAs given the same data) obtain the
+// same value.
+__device__ __forceinline__ double block_sum(double v, double *red) {
+    v = warp_sum(v);
+    __syncthreads();                                   // earlier readers of red[] done
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    return warp_sum(lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0);
 }
 
 // A = Re(D) (row-major), symmetrised.
@@ -38,261 +66,372 @@ __global__ void he_real_kernel(int n, const double2 *__restrict__ D, double *__r
     }
 }
 
-// Step 1a: reflector of column k (one CTA of 1024 threads).  Writes v into
-// A[k+1..n-1][k] and vbuf (zero at indices <= k), d[k], e[k].
-__global__ void __launch_bounds__(1024)
-hh_column_kernel(int n, int k, double *__restrict__ A, double *__restrict__ vbuf,
-                 double *__restrict__ dd, double *__restrict__ ee) {
+// Step 1, launch for reflector index k (k = -1 .. n-3): applies reflector k
+// (when k >= 0; v_k and p_k come from vin/pin), forms reflector r = k + 1 and
+// its product p_r = A^(r) v_r (written to vout/pout).  Shared memory: v_k, w_k
+// and the rebuilt row r (overwritten by v_r), n doubles each.  CTA 0 writes
+// d[r], e[r], v_r and stores v_k into row k of A.  For r = n-2 (the last
+// launch) only the 2 x 2 tail of T is left: d[n-2], e[n-2], d[n-1].
+__global__ void __launch_bounds__(kTriThreads)
+tri_step_kernel(int n, int k, double *__restrict__ A, const double *__restrict__ vin,
+                const double *__restrict__ pin, double *__restrict__ vout, double *__restrict__ pout,
+                double *__restrict__ dd, double *__restrict__ ee) {
+    extern __shared__ double sm[];
+    double *sv = sm, *sw = sm + n, *sa = sm + 2 * n;
     __shared__ double red[32];
-    __shared__ double s_alpha, s_scale;
-    const int tid = threadIdx.x;
-    double ss = 0.0;
-    for (int i = k + 1 + tid; i < n; i += blockDim.x) {
-        const double x = A[(size_t)i * n + k];
-        ss += x * x;
-    }
-    ss = warp_sum(ss);
-    if ((tid & 31) == 0) red[tid >> 5] = ss;
-    __syncthreads();
-    if (tid == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        const double x0 = A[(size_t)(k + 1) * n + k];
-        const double nrm = sqrt(t);
-        const double alpha = (x0 > 0.0) ? -nrm : nrm;     // alpha = -sign(x0) |x|
-        // v = x - alpha e1, |v|^2 = t - 2 alpha x0 + alpha^2 = 2 (t - alpha x0)
-        const double vv = 2.0 * (t - alpha * x0);
-        s_alpha = alpha;
-        s_scale = (vv > 0.0) ? 1.0 / sqrt(vv) : 0.0;
-        dd[k] = A[(size_t)k * n + k];
-        ee[k] = (vv > 0.0) ? alpha : x0;
-    }
-    __syncthreads();
-    const double alpha = s_alpha, sc = s_scale;
-    for (int i = tid; i < n; i += blockDim.x) {
-        double v = 0.0;
-        if (i > k) {
-            const double x = A[(size_t)i * n + k];
-            v = ((i == k + 1) ? x - alpha : x) * sc;
-            A[(size_t)i * n + k] = v;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const bool prev = k >= 0;
+    const int r = k + 1;
+    if (prev) {
+        double part = 0.0;
+        for (int j = k + 1 + tid; j < n; j += nt) {
+            const double v = vin[j], p = pin[j];
+            sv[j] = v;
+            sw[j] = p;
+            part += v * p;
         }
-        vbuf[i] = v;
+        const double K = block_sum(part, red);
+        for (int j = k + 1 + tid; j < n; j += nt) sw[j] = 2.0 * (sw[j] - K * sv[j]);
+        __syncthreads();
+    }
+    // row r of A^(r), columns r .. n-1
+    const double vr = prev ? sv[r] : 0.0, wr = prev ? sw[r] : 0.0;
+    for (int j = r + tid; j < n; j += nt) {
+        double a = A[(size_t)r * n + j];
+        if (prev) a = fma(-wr, sv[j], fma(-vr, sw[j], a));
+        sa[j] = a;
+    }
+    __syncthreads();
+    if (r >= n - 2) {                                  // tail: no reflector r
+        if (blockIdx.x == 0 && tid == 0) {
+            dd[n - 2] = sa[n - 2];
+            ee[n - 2] = sa[n - 1];
+            double a = A[(size_t)(n - 1) * n + n - 1];
+            if (prev) a -= 2.0 * sv[n - 1] * sw[n - 1];
+            dd[n - 1] = a;
+        }
+        if (blockIdx.x == 0 && prev)
+            for (int j = k + 1 + tid; j < n; j += nt) A[(size_t)k * n + j] = sv[j];
+        return;
+    }
+    const double x0 = sa[r + 1];                       // read before anyone rescales sa
+    double part = 0.0;
+    for (int j = r + 1 + tid; j < n; j += nt) part += sa[j] * sa[j];
+    const double t = block_sum(part, red);
+    const double nrm = sqrt(t);
+    const double alpha = (x0 > 0.0) ? -nrm : nrm;      // alpha = -sign(x0) |x|
+    // v = x - alpha e1, |v|^2 = t - 2 alpha x0 + alpha^2 = 2 (t - alpha x0)
+    const double vv = 2.0 * (t - alpha * x0);
+    const double sc = (vv > 0.0) ? 1.0 / sqrt(vv) : 0.0;
+    for (int j = r + 1 + tid; j < n; j += nt) sa[j] = ((j == r + 1) ? sa[j] - alpha : sa[j]) * sc;
+    __syncthreads();
+    if (blockIdx.x == 0) {
+        if (tid == 0) {
+            dd[r] = sa[r];
+            ee[r] = (vv > 0.0) ? alpha : x0;
+        }
+        for (int j = tid; j < n; j += nt) vout[j] = (j > r) ? sa[j] : 0.0;
+        if (prev)
+            for (int j = k + 1 + tid; j < n; j += nt) A[(size_t)k * n + j] = sv[j];
+    }
+    // rows i > r: rank-2 update of reflector k on columns > r, then p_r[i]
+    const int lane = tid & 31;
+    const int warps = nt >> 5;
+    for (int i = r + 1 + (int)blockIdx.x * warps + (tid >> 5); i < n; i += (int)gridDim.x * warps) {
+        double *row = A + (size_t)i * n;
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        int j = r + 1 + lane;
+        if (prev) {
+            const double vi = sv[i], wi = sw[i];
+            for (; j + 96 < n; j += 128) {
+                double a[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) a[u] = row[j + 32 * u];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int c = j + 32 * u;
+                    a[u] = fma(-wi, sv[c], fma(-vi, sw[c], a[u]));
+                    row[c] = a[u];
+                    acc[u] = fma(a[u], sa[c], acc[u]);
+                }
+            }
+            for (; j < n; j += 32) {
+                const double a = fma(-wi, sv[j], fma(-vi, sw[j], row[j]));
+                row[j] = a;
+                acc[0] = fma(a, sa[j], acc[0]);
+            }
+        } else {
+            for (; j + 96 < n; j += 128) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[u] = fma(row[j + 32 * u], sa[j + 32 * u], acc[u]);
+            }
+            for (; j < n; j += 32) acc[0] = fma(row[j], sa[j], acc[0]);
+        }
+        const double tot = warp_sum((acc[0] + acc[1]) + (acc[2] + acc[3]));
+        if (lane == 0) pout[i] = tot;
     }
 }
 
-// Step 1b: p = A v over the trailing block (one warp per row).
-__global__ void hh_symv_kernel(int n, int k, const double *__restrict__ A, const double *__restrict__ v,
-                               double *__restrict__ p) {
-    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    const int i = k + 1 + row;
-    if (i >= n) return;
-    const double *a = A + (size_t)i * n;
-    double s = 0.0;
-    for (int j = k + 1 + lane; j < n; j += 32) s += a[j] * v[j];
-    s = warp_sum(s);
-    if (lane == 0) p[i] = s;
-}
-
-// Step 1c: w = 2 (p - (v.p) v) (one CTA).
+// Step 2a: Gershgorin interval of T (padded by 1e-12 |T|), |T| = max_i
+// (|d_i| + |e_{i-1}| + |e_i|) and the pivot floor of the Sturm counts:
+// g = {lo, hi, |T|, pivmin}; also e2_i = e_i^2.  One CTA.
 __global__ void __launch_bounds__(1024)
-hh_w_kernel(int n, int k, const double *__restrict__ v, const double *__restrict__ p, double *__restrict__ w) {
-    __shared__ double red[32];
-    __shared__ double s_K;
-    const int tid = threadIdx.x;
-    double s = 0.0;
-    for (int i = k + 1 + tid; i < n; i += blockDim.x) s += v[i] * p[i];
-    s = warp_sum(s);
-    if ((tid & 31) == 0) red[tid >> 5] = s;
-    __syncthreads();
-    if (tid == 0) {
-        double t = 0.0;
-        for (int x = 0; x < (int)(blockDim.x >> 5); ++x) t += red[x];
-        s_K = t;
+gersh_kernel(int n, const double *__restrict__ d, const double *__restrict__ e, double *__restrict__ g,
+             double *__restrict__ e2) {
+    __shared__ double s_lo[32], s_hi[32], s_tn[32];
+    double lo = 1e300, hi = -1e300, tn = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        if (i < n - 1) e2[i] = e[i] * e[i];
+        const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
+        lo = fmin(lo, d[i] - r);
+        hi = fmax(hi, d[i] + r);
+        tn = fmax(tn, fabs(d[i]) + r);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s_lo[threadIdx.x >> 5] = lo;
+        s_hi[threadIdx.x >> 5] = hi;
+        s_tn[threadIdx.x >> 5] = tn;
     }
     __syncthreads();
-    const double K = s_K;
-    for (int i = k + 1 + tid; i < n; i += blockDim.x) w[i] = 2.0 * (p[i] - K * v[i]);
-}
-
-// Step 1d: A <- A - v w^T - w v^T on the trailing block.
-__global__ void hh_rank2_kernel(int n, int k, double *__restrict__ A, const double *__restrict__ v,
-                                const double *__restrict__ w) {
-    const int m = n - k - 1;
-    const size_t tot = (size_t)m * m;
-    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < tot;
-         x += (size_t)gridDim.x * blockDim.x) {
-        const int i = k + 1 + (int)(x / m), j = k + 1 + (int)(x % m);
-        A[(size_t)i * n + j] -= v[i] * w[j] + w[i] * v[j];
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            lo = fmin(lo, s_lo[w]);
+            hi = fmax(hi, s_hi[w]);
+            tn = fmax(tn, s_tn[w]);
+        }
+        const double pad = 1e-12 * fmax(tn, 1e-300);
+        g[0] = lo - pad;
+        g[1] = hi + pad;
+        g[2] = tn;
+        g[3] = 1e-300 + 1e-30 * tn * tn;
     }
 }
 
-__global__ void hh_tail_kernel(int n, const double *__restrict__ A, double *__restrict__ dd,
-                               double *__restrict__ ee) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    if (n >= 2) {
-        dd[n - 2] = A[(size_t)(n - 2) * n + n - 2];
-        ee[n - 2] = A[(size_t)(n - 1) * n + n - 2];
-    }
-    dd[n - 1] = A[(size_t)(n - 1) * n + n - 1];
-}
-
-// Step 2: eigenvalue i by bisection on the Sturm count.
-__device__ int sturm_count(int n, const double *d, const double *e, double x, double pivmin) {
+// Step 2b: eigenvalue i (ascending) from the Sturm count, the number of
+// negative pivots q_j of the LDL^T factorisation of T - x I.  The pivots are
+// carried as ratios q_j = a_j / a_{j-1} of the leading principal minors,
+// a_j = (d_j - x) a_{j-1} - e_{j-1}^2 a_{j-2} (a_{-1} = 1, a_{-2} = 0), which is
+// the pivot recurrence q_j = d_j - x - e_{j-1}^2 / q_{j-1} without a division
+// in the dependency chain.  A zero minor (a pivot exactly 0) is replaced by
+// -pivmin a_{j-1}; the pair (a_j, a_{j-1}) is rescaled by 2^-400 or 2^400
+// (exact) whenever a_j leaves [2^-400, 2^400].  Sign, zero and exponent tests
+// work on the bit patterns.
+__device__ int sturm_count(int n, const double *__restrict__ d, const double *__restrict__ e2, double x,
+                           double pivmin) {
     int cnt = 0;
-    double q = d[0] - x;
-    if (fabs(q) < pivmin) q = -pivmin;
-    cnt += q < 0.0;
-    for (int j = 1; j < n; ++j) {
-        q = d[j] - x - e[j - 1] * e[j - 1] / q;
-        if (fabs(q) < pivmin) q = -pivmin;
-        cnt += q < 0.0;
+    double am = 1.0, amm = 0.0;                        // a_{j-1}, a_{j-2}
+    for (int j = 0; j < n; ++j) {
+        const double t = (j > 0) ? e2[j - 1] * amm : 0.0;
+        double a = fma(d[j] - x, am, -t);
+        if ((__double_as_longlong(a) << 1) == 0) a = -pivmin * am;
+        cnt += (__double_as_longlong(a) ^ __double_as_longlong(am)) < 0;   // q_j < 0
+        const int ex = (__double2hiint(a) >> 20) & 0x7ff;
+        if (ex > 1023 + 400) {
+            a *= 0x1p-400;
+            am *= 0x1p-400;
+        } else if (ex < 1023 - 400) {
+            a *= 0x1p+400;
+            am *= 0x1p+400;
+        }
+        amm = am;
+        am = a;
     }
     return cnt;
 }
 
-__global__ void bisect_kernel(int n, const double *__restrict__ d, const double *__restrict__ e,
-                              double lo0, double hi0, double pivmin, double *__restrict__ lam) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double lo = lo0, hi = hi0;
-    for (int it = 0; it < 200; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (mid <= lo || mid >= hi) break;            // interval at machine resolution
-        if (sturm_count(n, d, e, mid, pivmin) > i) hi = mid; else lo = mid;
+// Multisection, one warp per eigenvalue: each round the 32 lanes take the
+// Sturm count at the 32 interior points that split the bracket [lo, hi] into
+// 33 equal parts, and the bracket shrinks to the part where the count first
+// exceeds i (lambda_i < x there).  About 11 rounds reach an interval of
+// max(eps |T|, 2 eps |lambda|).
+__global__ void __launch_bounds__(128)
+bisect_kernel(int n, const double *__restrict__ d, const double *__restrict__ e2,
+              const double *__restrict__ g, double *__restrict__ lam) {
+    const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;                                // whole warps
+    double lo = g[0], hi = g[1];
+    const double atol = kEps * g[2], pivmin = g[3];
+    for (int it = 0; it < 64; ++it) {
+        if (hi - lo <= fmax(atol, 2.0 * kEps * fmax(fabs(lo), fabs(hi)))) break;
+        const double x = lo + (hi - lo) * ((double)(lane + 1) / 33.0);
+        const unsigned above = __ballot_sync(0xffffffffu, sturm_count(n, d, e2, x, pivmin) > i);
+        const int f = above ? __ffs(above) - 1 : 32;   // first point above lambda_i
+        const double xf = __shfl_sync(0xffffffffu, x, min(f, 31));
+        const double xp = __shfl_sync(0xffffffffu, x, max(f - 1, 0));
+        const double nlo = (f == 0) ? lo : xp;
+        const double nhi = (f == 32) ? hi : xf;
+        if (nlo <= lo && nhi >= hi) break;            // bracket at machine resolution
+        lo = nlo;
+        hi = nhi;
     }
-    lam[i] = 0.5 * (lo + hi);
+    if (lane == 0) lam[i] = 0.5 * (lo + hi);
 }
 
-// Step 3: inverse iteration, one thread per eigenvalue; scratch interleaved
-// [j][thread] so that neighbouring threads touch neighbouring addresses.
+// Step 3: inverse iteration, one thread per eigenvalue t.  LU factors of
+// T - lambda_t I stored [j][t]: reciprocal pivots rdg, first and second
+// superdiagonals u1, u2 of U, multipliers ml and row-exchange flags piv.
+// The running row of the elimination and the running components of the
+// solves stay in registers; x is stored component-major X[j][t].
 __global__ void invit_kernel(int n, const double *__restrict__ d, const double *__restrict__ e,
-                             const double *__restrict__ lam, double tnorm, double *__restrict__ scr,
-                             double *__restrict__ Zt) {
+                             const double *__restrict__ lam, const double *__restrict__ g,
+                             double *__restrict__ rdg, double *__restrict__ u1, double *__restrict__ u2,
+                             double *__restrict__ ml, unsigned char *__restrict__ piv,
+                             double *__restrict__ X) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
-    const size_t S = (size_t)n;                       // stride between j entries
-    double *dg = scr;                                 // [n][n] diag of U
-    double *u1 = scr + S * S;                         // first super
-    double *u2 = scr + 2 * S * S;                     // second super
-    double *ml = scr + 3 * S * S;                     // multipliers
-    double *x = Zt + (size_t)t * n;
+    const size_t S = (size_t)n;
     const double sigma = lam[t];
-    const double tiny = 2.2e-16 * tnorm;
-    // factorise T - sigma I with partial pivoting; ipiv packed in the sign of ml? keep a flag array
-    unsigned long long *piv = reinterpret_cast<unsigned long long *>(scr + 4 * S * S);   // [n][n] flags
-    for (int j = 0; j < n; ++j) {
-        dg[(size_t)j * S + t] = d[j] - sigma;
-        u1[(size_t)j * S + t] = (j < n - 1) ? e[j] : 0.0;
-        u2[(size_t)j * S + t] = 0.0;
-    }
+    const double tiny = kEps * g[2];
+    // factorise P (T - sigma I) = L U, row j of U = (dj, u1j, u2j) at columns j, j+1, j+2
+    double cd = d[0] - sigma, cu = (n > 1) ? e[0] : 0.0;
     for (int j = 0; j < n - 1; ++j) {
-        const size_t a = (size_t)j * S + t, b = (size_t)(j + 1) * S + t;
-        const double dj = dg[a], lj = e[j];
-        if (fabs(dj) >= fabs(lj)) {
-            const double f = (dj != 0.0) ? lj / dj : 0.0;
-            ml[a] = f;
-            dg[b] -= f * u1[a];
-            piv[a] = 0;
-        } else {
-            const double f = dj / lj;
-            ml[a] = f;
-            dg[a] = lj;
-            const double tmp = dg[b];
-            dg[b] = u1[a] - f * tmp;
-            u1[a] = tmp;
-            if (j < n - 2) {
-                u2[a] = u1[b];
-                u1[b] = -f * u1[b];
-            }
-            piv[a] = 1;
+        const double lj = e[j];
+        const double nd = d[j + 1] - sigma;
+        const double nu = (j + 1 < n - 1) ? e[j + 1] : 0.0;
+        double dj, u1j, u2j, f, ncd, ncu;
+        unsigned char pv;
+        if (fabs(cd) >= fabs(lj)) {                    // keep row j
+            f = (cd != 0.0) ? lj / cd : 0.0;
+            dj = cd; u1j = cu; u2j = 0.0; pv = 0;
+            ncd = nd - f * cu; ncu = nu;
+        } else {                                       // exchange rows j and j+1
+            f = cd / lj;
+            dj = lj; u1j = nd; u2j = nu; pv = 1;
+            ncd = cu - f * nd; ncu = -f * nu;
         }
-        if (fabs(dg[a]) < tiny) dg[a] = tiny;
+        if (fabs(dj) < tiny) dj = tiny;
+        const size_t a = (size_t)j * S + t;
+        rdg[a] = 1.0 / dj;
+        u1[a] = u1j;
+        u2[a] = u2j;
+        ml[a] = f;
+        piv[a] = pv;
+        cd = ncd;
+        cu = ncu;
     }
-    if (fabs(dg[(size_t)(n - 1) * S + t]) < tiny) dg[(size_t)(n - 1) * S + t] = tiny;
+    if (fabs(cd) < tiny) cd = tiny;
+    rdg[(size_t)(n - 1) * S + t] = 1.0 / cd;
     // start vector: deterministic, not aligned with any special direction
-    for (int j = 0; j < n; ++j) x[j] = 1.0 + 0.5 * sin(0.7 * (double)(j + 1) * (double)(t + 3));
+    double scale = 1.0;
     for (int it = 0; it < 3; ++it) {
-        for (int j = 0; j < n - 1; ++j) {                 // apply L^-1 P
+        // x <- L^-1 P x (the previous iterate rescaled to unit norm on load)
+        double cx = (it == 0) ? 1.0 + 0.5 * sin(0.7 * (double)(t + 3)) : X[t] * scale;
+        for (int j = 0; j < n - 1; ++j) {
             const size_t a = (size_t)j * S + t;
+            const double nx = (it == 0) ? 1.0 + 0.5 * sin(0.7 * (double)(j + 2) * (double)(t + 3))
+                                        : X[a + S] * scale;
+            const double m = ml[a];
             if (piv[a]) {
-                const double tmp = x[j];
-                x[j] = x[j + 1];
-                x[j + 1] = tmp - ml[a] * x[j];
+                X[a] = nx;
+                cx = cx - m * nx;
             } else {
-                x[j + 1] -= ml[a] * x[j];
+                X[a] = cx;
+                cx = nx - m * cx;
             }
         }
-        for (int j = n - 1; j >= 0; --j) {                // U back substitution
+        X[(size_t)(n - 1) * S + t] = cx;
+        // x <- U^-1 x
+        double x1 = 0.0, x2 = 0.0, nrm = 0.0;
+        for (int j = n - 1; j >= 0; --j) {
             const size_t a = (size_t)j * S + t;
-            double s = x[j];
-            if (j + 1 < n) s -= u1[a] * x[j + 1];
-            if (j + 2 < n) s -= u2[a] * x[j + 2];
-            x[j] = s / dg[a];
+            const double x = (X[a] - u1[a] * x1 - u2[a] * x2) * rdg[a];
+            X[a] = x;
+            nrm += x * x;
+            x2 = x1;
+            x1 = x;
         }
-        double nrm = 0.0;
-        for (int j = 0; j < n; ++j) nrm += x[j] * x[j];
-        nrm = 1.0 / sqrt(nrm);
-        for (int j = 0; j < n; ++j) x[j] *= nrm;
+        scale = 1.0 / sqrt(nrm);
     }
+    for (int j = 0; j < n; ++j) X[(size_t)j * S + t] *= scale;
 }
 
-// Step 4: modified Gram-Schmidt inside each near-degenerate set (one CTA per set).
+// Step 4: modified Gram-Schmidt inside the near-degenerate set that starts at
+// eigenvalue blockIdx.x (the CTA returns when no set of two or more starts there).
 __global__ void __launch_bounds__(256)
-mgs_kernel(int n, const int *__restrict__ set_start, double *__restrict__ Zt) {
+mgs_kernel(int n, const double *__restrict__ lam, const double *__restrict__ g, double *__restrict__ X) {
     __shared__ double red[8];
     __shared__ double s_dot;
-    const int s0 = set_start[blockIdx.x], s1 = set_start[blockIdx.x + 1];
+    const int s0 = blockIdx.x;
+    const double thr = 1e-9 * g[2];
+    const bool starts = (s0 == 0 || lam[s0] - lam[s0 - 1] > thr) && (s0 + 1 < n && lam[s0 + 1] - lam[s0] <= thr);
+    if (!starts) return;
+    int s1 = s0 + 1;
+    while (s1 < n && lam[s1] - lam[s1 - 1] <= thr) ++s1;
+    const size_t S = (size_t)n;
     for (int a = s0; a < s1; ++a) {
-        double *za = Zt + (size_t)a * n;
         for (int b = s0; b < a; ++b) {
-            const double *zb = Zt + (size_t)b * n;
             double s = 0.0;
-            for (int j = threadIdx.x; j < n; j += blockDim.x) s += za[j] * zb[j];
+            for (int j = threadIdx.x; j < n; j += blockDim.x) s += X[j * S + a] * X[j * S + b];
             s = warp_sum(s);
             if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
             __syncthreads();
             if (threadIdx.x == 0) { double t = 0; for (int w = 0; w < 8; ++w) t += red[w]; s_dot = t; }
             __syncthreads();
             const double dt = s_dot;
-            for (int j = threadIdx.x; j < n; j += blockDim.x) za[j] -= dt * zb[j];
+            for (int j = threadIdx.x; j < n; j += blockDim.x) X[j * S + a] -= dt * X[j * S + b];
             __syncthreads();
         }
         double s = 0.0;
-        for (int j = threadIdx.x; j < n; j += blockDim.x) s += za[j] * za[j];
+        for (int j = threadIdx.x; j < n; j += blockDim.x) s += X[j * S + a] * X[j * S + a];
         s = warp_sum(s);
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
         __syncthreads();
         if (threadIdx.x == 0) { double t = 0; for (int w = 0; w < 8; ++w) t += red[w]; s_dot = 1.0 / sqrt(t); }
         __syncthreads();
         const double sc = s_dot;
-        for (int j = threadIdx.x; j < n; j += blockDim.x) za[j] *= sc;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) X[j * S + a] *= sc;
         __syncthreads();
     }
 }
 
-// Step 5: z_s <- H_k z_s = z_s - 2 v (v . z_s), one warp per vector s.
-__global__ void backtransform_kernel(int n, int k, const double *__restrict__ A, double *__restrict__ Zt) {
-    const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (s >= n) return;
-    double *z = Zt + (size_t)s * n;
-    double dot = 0.0;
-    for (int j = k + 1 + lane; j < n; j += 32) dot += A[(size_t)j * n + k] * z[j];
-    dot = warp_sum(dot);
-    for (int j = k + 1 + lane; j < n; j += 32) z[j] -= 2.0 * dot * A[(size_t)j * n + k];
-}
-
-__global__ void he_output_kernel(int n, const double *__restrict__ lam, const double *__restrict__ Zt,
-                                 double *__restrict__ nu, double2 *__restrict__ eig) {
-    const size_t nn = (size_t)n * n;
-    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < nn;
-         x += (size_t)gridDim.x * blockDim.x) {
-        eig[x] = make_double2(Zt[x], 0.0);
-        if (x < (size_t)n) {
-            const double w2 = lam[x] * kEvA2AmuPs2;
-            nu[x] = (w2 >= 0.0 ? sqrt(w2) : -sqrt(-w2)) / kTwoPi;
+// Step 5: z_s <- H_0 ... H_{n-3} z_s for the vpb vectors s0 .. s0+vpb-1 of this
+// CTA (one warp per vector, vectors in shared memory), then the outputs:
+// eigenvector s as row s of eig (imaginary part 0) and its frequency.
+__global__ void backtransform_kernel(int n, int vpb, const double *__restrict__ A,
+                                     const double *__restrict__ X, const double *__restrict__ lam,
+                                     double *__restrict__ nu, double2 *__restrict__ eig) {
+    extern __shared__ double zs[];
+    const int s0 = blockIdx.x * vpb;
+    const int nv = min(vpb, n - s0);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int x = tid; x < nv * n; x += nt) {
+        const int j = x / nv, sl = x % nv;
+        zs[(size_t)sl * n + j] = X[(size_t)j * n + s0 + sl];
+    }
+    __syncthreads();
+    const int w = tid >> 5, lane = tid & 31;
+    if (w < nv) {
+        double *z = zs + (size_t)w * n;
+        for (int k = n - 3; k >= 0; --k) {
+            const double *v = A + (size_t)k * n;
+            double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+            int j = k + 1 + lane;
+            for (; j + 96 < n; j += 128) {
+                d0 = fma(v[j], z[j], d0);
+                d1 = fma(v[j + 32], z[j + 32], d1);
+                d2 = fma(v[j + 64], z[j + 64], d2);
+                d3 = fma(v[j + 96], z[j + 96], d3);
+            }
+            for (; j < n; j += 32) d0 = fma(v[j], z[j], d0);
+            const double f = 2.0 * warp_sum((d0 + d1) + (d2 + d3));
+            for (j = k + 1 + lane; j < n; j += 32) z[j] = fma(-f, v[j], z[j]);
+            __syncwarp();                              // next reflector reads other lanes' z[j]
         }
+    }
+    __syncthreads();
+    for (int x = tid; x < nv * n; x += nt) {
+        const int sl = x / n, j = x % n;
+        eig[(size_t)(s0 + sl) * n + j] = make_double2(zs[(size_t)sl * n + j], 0.0);
+    }
+    if (tid < nv) {
+        const double w2 = lam[s0 + tid] * kEvA2AmuPs2;
+        nu[s0 + tid] = (w2 >= 0.0 ? sqrt(w2) : -sqrt(-w2)) / kTwoPi;
     }
 }
 
@@ -300,85 +439,60 @@ __global__ void he_output_kernel(int n, const double *__restrict__ lam, const do
 
 size_t eigh_large_scratch_bytes(int n) {
     const size_t nn = (size_t)n * n;
-    // A, Zt, 5 interleaved LU arrays, vectors
-    return ws_round(sizeof(double) * nn) * 7 + ws_round(sizeof(double) * 6 * (size_t)n) +
-           ws_round(sizeof(int) * (n + 1));
+    // A, X, rdg, u1, u2, ml; piv; v0, v1, p0, p1, d, e, e^2, lambda and g
+    return ws_round(sizeof(double) * nn) * 6 + ws_round(nn) + ws_round(sizeof(double) * (8 * (size_t)n + 4));
+}
+
+bool eigh_large_supported(int n, size_t smem_optin) {
+    return n >= 3 && sizeof(double) * 3 * (size_t)n + 1024 <= smem_optin &&
+           sizeof(double) * (size_t)n <= smem_optin;
 }
 
 cudaError_t launch_eigh_large(int n, const double2 *D, double *scratch, double *nu_out,
-                              double2 *eig_out, cudaStream_t st) {
+                              double2 *eig_out, int sms, size_t smem_optin, cudaStream_t st) {
+    if (!eigh_large_supported(n, smem_optin)) return cudaErrorInvalidValue;
     const size_t nn = (size_t)n * n;
     char *base = reinterpret_cast<char *>(scratch);
+    const size_t mat = ws_round(sizeof(double) * nn);
     double *A = reinterpret_cast<double *>(base);
-    double *Zt = reinterpret_cast<double *>(base + ws_round(sizeof(double) * nn));
-    double *scr = reinterpret_cast<double *>(base + 2 * ws_round(sizeof(double) * nn));
-    double *vec = reinterpret_cast<double *>(base + 7 * ws_round(sizeof(double) * nn));
-    double *vbuf = vec, *p = vec + n, *w = vec + 2 * n, *dd = vec + 3 * n, *ee = vec + 4 * n,
-           *lam = vec + 5 * n;
-    const unsigned g = (unsigned)std::min<size_t>((nn + 255) / 256, 16384);
-    he_real_kernel<<<counted(g), 256, 0, st>>>(n, D, A);
-    for (int k = 0; k + 2 < n; ++k) {
-        hh_column_kernel<<<counted(1), 1024, 0, st>>>(n, k, A, vbuf, dd, ee);
-        const int m = n - k - 1;
-        hh_symv_kernel<<<counted((m * 32 + 255) / 256), 256, 0, st>>>(n, k, A, vbuf, p);
-        hh_w_kernel<<<counted(1), 1024, 0, st>>>(n, k, vbuf, p, w);
-        const size_t mm = (size_t)m * m;
-        hh_rank2_kernel<<<counted((unsigned)std::min<size_t>((mm + 255) / 256, 8192)), 256, 0, st>>>(n, k, A, vbuf, w);
-    }
-    hh_tail_kernel<<<counted(1), 32, 0, st>>>(n, A, dd, ee);
-    cudaError_t e = cudaGetLastError();
+    double *X = reinterpret_cast<double *>(base + mat);
+    double *rdg = reinterpret_cast<double *>(base + 2 * mat);
+    double *u1 = reinterpret_cast<double *>(base + 3 * mat);
+    double *u2 = reinterpret_cast<double *>(base + 4 * mat);
+    double *ml = reinterpret_cast<double *>(base + 5 * mat);
+    unsigned char *piv = reinterpret_cast<unsigned char *>(base + 6 * mat);
+    double *vec = reinterpret_cast<double *>(base + 6 * mat + ws_round(nn));
+    double *vb[2] = {vec, vec + n}, *pb[2] = {vec + 2 * n, vec + 3 * n};
+    double *dd = vec + 4 * n, *ee = vec + 5 * n, *lam = vec + 6 * n, *e2 = vec + 7 * n, *g = vec + 8 * n;
+
+    const unsigned gr = (unsigned)std::min<size_t>((nn + 255) / 256, 16384);
+    he_real_kernel<<<counted(gr), 256, 0, st>>>(n, D, A);
+    const size_t tri_smem = sizeof(double) * 3 * (size_t)n;
+    cudaError_t e = cudaFuncSetAttribute(tri_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tri_smem);
     if (e != cudaSuccess) return e;
-    // Gershgorin interval and the tridiagonal norm (host, O(n))
-    std::vector<double> hd(n), he(std::max(1, n - 1));
-    e = cudaMemcpyAsync(hd.data(), dd, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && n > 1)
-        e = cudaMemcpyAsync(he.data(), ee, sizeof(double) * (n - 1), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return e;
-    double lo = 1e300, hi = -1e300, tn = 0.0;
-    for (int i = 0; i < n; ++i) {
-        const double r = (i > 0 ? std::fabs(he[i - 1]) : 0.0) + (i < n - 1 ? std::fabs(he[i]) : 0.0);
-        lo = std::min(lo, hd[i] - r);
-        hi = std::max(hi, hd[i] + r);
-        tn = std::max(tn, std::fabs(hd[i]) + r);
+    const int warps = kTriThreads / 32;
+    for (int k = -1; k <= n - 3; ++k) {
+        const int rows = n - k - 2;                   // rows below the new reflector's row
+        const int grid = std::max(1, std::min((rows + warps - 1) / warps, std::max(sms, 1)));
+        const int cur = (k + 2) & 1, nxt = (k + 1) & 1;   // v_k in vb[k & 1]
+        tri_step_kernel<<<counted(grid), kTriThreads, tri_smem, st>>>(n, k, A, vb[cur], pb[cur], vb[nxt],
+                                                                      pb[nxt], dd, ee);
     }
-    const double pad = 1e-12 * std::max(tn, 1e-300);
-    const double pivmin = 1e-300 + 1e-30 * tn * tn;
-    bisect_kernel<<<counted((n + 127) / 128), 128, 0, st>>>(n, dd, ee, lo - pad, hi + pad, pivmin, lam);
-    invit_kernel<<<counted((n + 127) / 128), 128, 0, st>>>(n, dd, ee, lam, tn, scr, Zt);
-    e = cudaGetLastError();
+    gersh_kernel<<<counted(1), 1024, 0, st>>>(n, dd, ee, g, e2);
+    const unsigned g32 = (unsigned)((n + 31) / 32);
+    bisect_kernel<<<counted((unsigned)((n + 3) / 4)), 128, 0, st>>>(n, dd, e2, g, lam);
+    invit_kernel<<<counted(g32), 32, 0, st>>>(n, dd, ee, lam, g, rdg, u1, u2, ml, piv, X);
+    mgs_kernel<<<counted(n), 256, 0, st>>>(n, lam, g, X);
+    // vectors per CTA: about one CTA per SM, within the shared memory limit
+    int vpb = std::max(1, (n + std::max(sms, 1) - 1) / std::max(sms, 1));
+    vpb = std::min(vpb, 32);
+    vpb = std::min<int>(vpb, (int)(smem_optin / (sizeof(double) * (size_t)n)));
+    const size_t bt_smem = sizeof(double) * (size_t)vpb * n;
+    e = cudaFuncSetAttribute(backtransform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt_smem);
     if (e != cudaSuccess) return e;
-    // near-degenerate sets of the (ascending) eigenvalues
-    std::vector<double> hl(n);
-    e = cudaMemcpyAsync(hl.data(), lam, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return e;
-    std::vector<int> sets;
-    int start = 0;
-    for (int i = 1; i <= n; ++i) {
-        if (i == n || hl[i] - hl[i - 1] > 1e-9 * tn) {
-            if (i - start > 1) { sets.push_back(start); sets.push_back(i); }
-            start = i;
-        }
-    }
-    if (!sets.empty()) {
-        // CSR of the sets: starts followed by the end of the last one; sets are
-        // disjoint, so pairs (start, end) are stored and one CTA reads its pair
-        int *dsets = reinterpret_cast<int *>(vec + 6 * n);
-        std::vector<int> csr;
-        for (size_t x = 0; x < sets.size(); x += 2) { csr.push_back(sets[x]); csr.push_back(sets[x + 1]); }
-        const int n_sets = (int)csr.size() / 2;
-        // repack into start[i] = csr[2i], end[i] = csr[2i+1] as set_start[2i], set_start[2i+1]
-        e = cudaMemcpyAsync(dsets, csr.data(), sizeof(int) * csr.size(), cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) return e;
-        for (int x = 0; x < n_sets; ++x)
-            mgs_kernel<<<counted(1), 256, 0, st>>>(n, dsets + 2 * x, Zt);
-        e = cudaStreamSynchronize(st);                // csr must outlive the copy
-        if (e != cudaSuccess) return e;
-    }
-    for (int k = n - 3; k >= 0; --k)
-        backtransform_kernel<<<counted((n * 32 + 255) / 256), 256, 0, st>>>(n, k, A, Zt);
-    he_output_kernel<<<counted(g), 256, 0, st>>>(n, lam, Zt, nu_out, eig_out);
+    backtransform_kernel<<<counted((unsigned)((n + vpb - 1) / vpb)), 32 * vpb, bt_smem, st>>>(n, vpb, A, X, lam,
+                                                                                            nu_out, eig_out);
     return cudaGetLastError();
 }
 

@@ -479,6 +479,8 @@ kald_status kald_phonons(kald_ctx *ctx, const kald_system *sys, const int32_t me
     const bool large = nb > kMaxNbSmall;
     if (large && (mesh[0] != 1 || mesh[1] != 1 || mesh[2] != 1))
         return fail(ctx, KALD_E_UNSUPPORTED, "kald_phonons: nb > 96 is diagonalised at Gamma only (mesh {1,1,1})");
+    if (large && !eigh_large_supported(nb, ctx->smem_optin))
+        return fail(ctx, KALD_E_UNSUPPORTED, "kald_phonons: cell too large for the Gamma-only eigensolver");
     std::vector<double> qc;
     std::vector<int> qf;
     mesh_points(h.lattice, mesh, qc, qf);
@@ -508,7 +510,7 @@ kald_status kald_phonons(kald_ctx *ctx, const kald_system *sys, const int32_t me
     cudaMemsetAsync(nonconv, 0, sizeof(int), s);
     cudaError_t e = launch_dynmat(dev_fc2(h, d), nb, nq, qcart, D, s);
     if (e == cudaSuccess) {
-        if (large) e = launch_eigh_large(nb, D, big, nu_d, eig_d, s);
+        if (large) e = launch_eigh_large(nb, D, big, nu_d, eig_d, ctx->sm_count, ctx->smem_optin, s);
         else e = launch_jacobi(nb, nq, D, V, nu_d, eig_d, nonconv, ctx->smem_optin, s);
     }
     if (e == cudaSuccess && vel) e = launch_velocity_diag(dev_fc2(h, d), nb, nq, qcart, nu_d, eig_d, vel_d, s);

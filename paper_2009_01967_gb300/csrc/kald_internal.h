@@ -124,10 +124,13 @@ cudaError_t launch_dynmat(const DevFc2 &f, int nb, int nq, const double *qcart,
                           double2 *D, cudaStream_t st);
 cudaError_t launch_jacobi(int nb, int nq, double2 *A, double2 *V, double *nu_thz,
                           double2 *eig_out, int *nonconv, size_t smem_optin, cudaStream_t st);
-// eigh_large.cu: one real symmetric matrix of any size (the Gamma-only D)
+// eigh_large.cu: one real symmetric matrix (the Gamma-only D), n up to about
+// 9600 (three length-n FP64 vectors per CTA in shared memory)
 size_t eigh_large_scratch_bytes(int n);
+// n >= 3 and three length-n FP64 vectors fit in one CTA's shared memory
+bool eigh_large_supported(int n, size_t smem_optin);
 cudaError_t launch_eigh_large(int n, const double2 *D, double *scratch, double *nu_out,
-                              double2 *eig_out, cudaStream_t st);
+                              double2 *eig_out, int sms, size_t smem_optin, cudaStream_t st);
 cudaError_t launch_velocity_diag(const DevFc2 &f, int nb, int nq, const double *qcart,
                                  const double *nu_thz, const double2 *eig, double *vel,
                                  cudaStream_t st);

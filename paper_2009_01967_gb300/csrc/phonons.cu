@@ -23,25 +23,27 @@ __device__ __forceinline__ double2 cmulc(double2 a, double2 b) {   // conj(a) * 
 
 // D[q] (nb x nb, row-major) from fc2 blocks grouped by atom pair: one output
 // element (pair, a, b) per thread iteration, blocks summed in a fixed order.
-__global__ void dynmat_kernel(DevFc2 f, int nb, const double *__restrict__ qcart,
+// Grid: x strides over the elements of one q, y over the q-points.
+__global__ void dynmat_kernel(DevFc2 f, int nb, int nq, const double *__restrict__ qcart,
                               double2 *__restrict__ D) {
-    const int q = blockIdx.x;
-    const double qx = qcart[3 * q], qy = qcart[3 * q + 1], qz = qcart[3 * q + 2];
-    double2 *Dq = D + (size_t)q * nb * nb;
     const int n_elem = f.n_pairs * 9;
-    for (int e = threadIdx.x; e < n_elem; e += blockDim.x) {
-        const int p = e / 9, ab = e % 9;
-        const int i = f.pair_i[p], j = f.pair_j[p];
-        double2 acc = make_double2(0.0, 0.0);
-        for (int b = f.pair_start[p]; b < f.pair_start[p + 1]; ++b) {
-            const double *R = f.rcart + 3 * b;
-            double s, c;
-            sincos(qx * R[0] + qy * R[1] + qz * R[2], &s, &c);
-            const double v = f.blk[9 * b + ab];
-            acc.x += v * c;            // exp(-i q.R) = c - i s
-            acc.y -= v * s;
+    for (int q = blockIdx.y; q < nq; q += gridDim.y) {
+        const double qx = qcart[3 * q], qy = qcart[3 * q + 1], qz = qcart[3 * q + 2];
+        double2 *Dq = D + (size_t)q * nb * nb;
+        for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_elem; e += gridDim.x * blockDim.x) {
+            const int p = e / 9, ab = e % 9;
+            const int i = f.pair_i[p], j = f.pair_j[p];
+            double2 acc = make_double2(0.0, 0.0);
+            for (int b = f.pair_start[p]; b < f.pair_start[p + 1]; ++b) {
+                const double *R = f.rcart + 3 * b;
+                double s, c;
+                sincos(qx * R[0] + qy * R[1] + qz * R[2], &s, &c);
+                const double v = f.blk[9 * b + ab];
+                acc.x += v * c;            // exp(-i q.R) = c - i s
+                acc.y -= v * s;
+            }
+            Dq[(size_t)(3 * i + ab / 3) * nb + 3 * j + ab % 3] = acc;
         }
-        Dq[(size_t)(3 * i + ab / 3) * nb + 3 * j + ab % 3] = acc;
     }
 }
 
@@ -250,7 +252,11 @@ cudaError_t launch_dynmat(const DevFc2 &f, int nb, int nq, const double *qcart, 
                           cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(D, 0, sizeof(double2) * (size_t)nq * nb * nb, st);
     if (e != cudaSuccess) return e;
-    dynmat_kernel<<<counted(nq), 256, 0, st>>>(f, nb, qcart, D);
+    // enough CTAs along x to fill the GPU when there are few q-points
+    const int n_elem = f.n_pairs * 9;
+    const int gx = std::max(1, std::min((n_elem + 255) / 256, std::max(1, 1216 / std::max(nq, 1))));
+    const dim3 grid((unsigned)gx, (unsigned)std::min(nq, 65535));
+    dynmat_kernel<<<counted(grid), 256, 0, st>>>(f, nb, nq, qcart, D);
     return cudaGetLastError();
 }
 
