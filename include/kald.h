@@ -62,7 +62,7 @@ typedef enum {
                                 accumulation; the Bloch-phase gather (crystals)
                                 and the delta epilogue in FP32, sums over q'
                                 and modes in FP64.  Crystals (nb <= 96) and
-                                Gamma-only systems of any size.               */
+                                Gamma-only systems.                           */
 } kald_precision;
 
 /* One crystal unit cell, or one Gamma-only supercell (used with mesh 1x1x1).
@@ -131,8 +131,10 @@ uint64_t kald_kernel_launches(void);
  *   vel     [Nq][nb][3] out (A/ps), or NULL
  * nb <= 96: one parallel Jacobi eigensolver per q (KALD_E_NOCONV if the
  * sweeps do not converge).  nb > 96 is supported at Gamma only (mesh
- * {1,1,1}; KALD_E_UNSUPPORTED otherwise): Householder tridiagonalisation,
- * bisection, inverse iteration, back-transformation, all FP64. */
+ * {1,1,1}; KALD_E_UNSUPPORTED otherwise) and up to the size whose three
+ * length-nb FP64 vectors fit one CTA's shared memory (nb of about 9600 on
+ * GB300; KALD_E_UNSUPPORTED beyond): Householder tridiagonalisation, Sturm
+ * multisection, inverse iteration, back-transformation, all FP64. */
 kald_status kald_phonons(kald_ctx *ctx, const kald_system *sys, const int32_t mesh[3],
                          double *nu_thz, double *eigvec, double *vel);
 
