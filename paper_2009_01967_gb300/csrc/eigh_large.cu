@@ -134,10 +134,14 @@ tri_step_kernel(int n, int k, double *__restrict__ A, const double *__restrict__
         if (prev)
             for (int j = k + 1 + tid; j < n; j += nt) A[(size_t)k * n + j] = sv[j];
     }
-    // rows i > r: rank-2 update of reflector k on columns > r, then p_r[i]
+    // rows i > r: rank-2 update of reflector k on columns > r, then p_r[i];
+    // row r + 1 + t goes to CTA t mod grid (rows dealt over the CTAs first, so
+    // every SM gets a share when there are fewer rows than warps in the grid)
     const int lane = tid & 31;
     const int warps = nt >> 5;
-    for (int i = r + 1 + (int)blockIdx.x * warps + (tid >> 5); i < n; i += (int)gridDim.x * warps) {
+    const int rows = n - r - 1;
+    for (int t = (int)blockIdx.x + (int)gridDim.x * (tid >> 5); t < rows; t += (int)gridDim.x * warps) {
+        const int i = r + 1 + t;
         double *row = A + (size_t)i * n;
         double acc[4] = {0.0, 0.0, 0.0, 0.0};
         int j = r + 1 + lane;
@@ -471,10 +475,9 @@ cudaError_t launch_eigh_large(int n, const double2 *D, double *scratch, double *
     cudaError_t e = cudaFuncSetAttribute(tri_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)tri_smem);
     if (e != cudaSuccess) return e;
-    const int warps = kTriThreads / 32;
     for (int k = -1; k <= n - 3; ++k) {
         const int rows = n - k - 2;                   // rows below the new reflector's row
-        const int grid = std::max(1, std::min((rows + warps - 1) / warps, std::max(sms, 1)));
+        const int grid = std::max(1, std::min(rows, std::max(sms, 1)));   // one CTA per SM
         const int cur = (k + 2) & 1, nxt = (k + 1) & 1;   // v_k in vb[k & 1]
         tri_step_kernel<<<counted(grid), kTriThreads, tri_smem, st>>>(n, k, A, vb[cur], pb[cur], vb[nxt],
                                                                       pb[nxt], dd, ee);
