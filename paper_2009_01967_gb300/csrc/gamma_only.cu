@@ -224,7 +224,7 @@ cudaError_t launch_gamma_only(const GammaPlan &gp, const GammaDev &d, const LwPa
         e = cudaMemsetAsync(d.partial_tc, 0, sizeof(double) * std::max<size_t>(nt, 1), st);
         if (e != cudaSuccess) return e;
         e = launch_gamma_only_tc(gp, d, p, d.tc_scratch, gp.tiles, gp.tile_start, d.tiles_dev, gp.symmetric,
-                                 d.partial_tc, d.err, st);
+                                 d.partial_tc, d.err, gp.sms, st);
         if (e != cudaSuccess) return e;
         // tile_start is uploaded right after the tiles (same allocation)
         const int *ts = reinterpret_cast<const int *>(d.tiles_dev + std::max<size_t>(nt, 1));

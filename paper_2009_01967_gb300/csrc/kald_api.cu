@@ -637,6 +637,7 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
             GammaPlan gp;
             gp.n_groups = (int)h.pair3_j.size();
             gp.n_part = std::max(1, 2 * ctx->sm_count);
+            gp.sms = std::max(1, ctx->sm_count);
             std::vector<double> nu_h(nb);
             if (d_nu) cudaMemcpy(nu_h.data(), nu_thz + off_nb, sizeof(double) * nb, cudaMemcpyDeviceToHost);
             else std::copy(nu_thz + off_nb, nu_thz + off_nb + nb, nu_h.begin());
@@ -660,7 +661,7 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
                           2 * ws_round(sizeof(double) * nb) + ws_round(sizeof(int) * nb) + ws_round(16) +
                           ws_round(16);
             if (mode == KALD_BF16_SPLIT)
-                need += tc_gamma_scratch_bytes(nb) + ws_round(sizeof(int2) * n_tiles + sizeof(int) * (nb + 1)) +
+                need += tc_gamma_scratch_bytes(nb, ctx->sm_count) + ws_round(sizeof(int2) * n_tiles + sizeof(int) * (nb + 1)) +
                         ws_round(sizeof(double) * n_tiles);
             else
                 need += 4 * ws_round(rs * nn) + ws_round(sizeof(double) * nb * (size_t)gp.n_part);
@@ -681,7 +682,7 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
             gd.partial = nullptr;
             gd.tc_scratch = nullptr; gd.tiles_dev = nullptr; gd.partial_tc = nullptr;
             if (mode == KALD_BF16_SPLIT) {
-                gd.tc_scratch = ws_take(ctx, tc_gamma_scratch_bytes(nb));
+                gd.tc_scratch = ws_take(ctx, tc_gamma_scratch_bytes(nb, ctx->sm_count));
                 gd.tiles_dev = static_cast<int2 *>(ws_take(ctx, sizeof(int2) * n_tiles + sizeof(int) * (nb + 1)));
                 gd.partial_tc = static_cast<double *>(ws_take(ctx, sizeof(double) * n_tiles));
             } else {

@@ -202,6 +202,7 @@ struct GammaPlan {
     std::vector<int2> tiles;
     std::vector<int> tile_start;     // [nb + 1]
     int symmetric = 0;               // Phi3 symmetric in its last two indices
+    int sms = 1;                     // SMs of the device (modes per tensor-core launch)
 };
 struct GammaDev {
     const int *group_jk, *group_start, *blk_i;   // (j, k) groups of fc3 blocks
@@ -214,7 +215,7 @@ struct GammaDev {
     int *order;                      // [nb]
     unsigned long long *allowed;
     // tensor-core path
-    void *tc_scratch;                // tc_gamma_scratch_bytes(nb)
+    void *tc_scratch;                // tc_gamma_scratch_bytes(nb, sms)
     int2 *tiles_dev;                 // [tiles]
     double *partial_tc;              // [tiles]
     int *err;                        // bounded-wait failures
@@ -222,11 +223,13 @@ struct GammaDev {
 // mode: 0 FP64 CUDA cores, 1 FP32 CUDA cores, 2 BF16-split tensor cores
 cudaError_t launch_gamma_only(const GammaPlan &gp, const GammaDev &d, const LwParams &p, int mode,
                               double degen_tol_thz, double *gamma_out, cudaStream_t st);
-size_t tc_gamma_scratch_bytes(int nb);
+// modes per launch of the tensor-core Gamma-only path and its scratch bytes
+int tc_gamma_batch(int nb, int sms);
+size_t tc_gamma_scratch_bytes(int nb, int sms);
 int tc_tile(void);
 cudaError_t launch_gamma_only_tc(const GammaPlan &gp, const GammaDev &d, const LwParams &p, void *scratch,
                                  const std::vector<int2> &tiles, const std::vector<int> &tile_start,
-                                 int2 *tiles_dev, int symmetric, double *partial_tc, int *err,
+                                 int2 *tiles_dev, int symmetric, double *partial_tc, int *err, int sms,
                                  cudaStream_t st);
 
 // small_nb.cu: crystal linewidths of one- and two-atom cells (nb = 3 or 6),

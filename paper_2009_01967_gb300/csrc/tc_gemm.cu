@@ -7,6 +7,11 @@
 // accumulated in FP32 in tensor memory; the dropped lo*lo term and the
 // rounding of lo leave about 16 significant bits per product.
 //
+// Several modes go through each launch (a batch of MB modes, so that small
+// systems still fill the GPU): the Y and T planes of the batch are stacked
+// (plane b at rows b * rows .. ), GEMM1 takes the mode from blockIdx.z and
+// GEMM2 from its tile record.
+//
 // Kernel shape (one 128 x 128 output tile per CTA, 128 threads):
 //   warp 0 lane 0   TMA producer: 4 tiled loads per K block of 64 (A hi/lo,
 //                   B hi/lo; 128-byte swizzle), 3-stage ring of mbarriers
@@ -50,16 +55,18 @@ using namespace tc;
 struct EpiGamma {
     const double *omega;      // [nb] rad/ps (0 = masked)
     const double *occ;        // [nb]
-    double w;                 // omega of the mode
+    int mu0;                  // first mode of the batch
+    int a_rows;               // rows of one T plane (stacked per mode of the batch)
     double sig2inv, cut;
-    double *partial;          // [n_tiles] per-tile sums of this mode
+    double *partial;          // [n_tiles] per-tile sums of this batch
     unsigned long long *allowed;
-    const int2 *tiles;        // (tm, tn) of the band tiles of this mode
+    const int2 *tiles;        // (tm | b << 16, tn): band tile (tm, tn) of mode mu0 + b
     int symmetric;            // phi symmetric: upper-triangle tiles, symmetrised weights
 };
 struct EpiSplit {
-    __nv_bfloat16 *hi, *lo;   // [rows][ld] output planes
+    __nv_bfloat16 *hi, *lo;   // [batch][rows][ld] output planes
     int ld;
+    int b_rows;               // rows of one Y / T plane (stacked per mode of the batch)
 };
 
 // Columns [c, c + 32) of the nacc accumulators, added in a fixed order.
@@ -91,13 +98,17 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ 
     __shared__ double red[4];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int tm, tn;
+    int tm, tn, bz;                              // tile and mode of the batch
     if (EPI == EPI_GAMMA) {
         const int2 t = eg.tiles[blockIdx.x];
-        tm = t.x; tn = t.y;
+        tm = t.x & 0xffff; bz = t.x >> 16; tn = t.y;
     } else {
-        tm = blockIdx.y; tn = blockIdx.x;
+        tm = blockIdx.y; tn = blockIdx.x; bz = blockIdx.z;
     }
+    // row coordinates of the A and B tiles: T (GEMM2's A) and Y (GEMM1's B)
+    // are stacked per mode of the batch
+    const int a_row = tm * kBM + (EPI == EPI_GAMMA ? bz * eg.a_rows : 0);
+    const int b_row = tn * kBN + (EPI == EPI_SPLIT ? bz * es.b_rows : 0);
     const int nkb = (K + kBK - 1) / kBK;
     const int nacc = min(kAcc, nkb);             // accumulators that received MMAs
 
@@ -125,10 +136,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ 
             if (kb >= kStages && !mbar_wait(&empty[s], ((kb / kStages) - 1) & 1)) { fail_sm = 1; break; }
             unsigned char *st = base + (size_t)s * kStageBytes;
             mbar_expect_tx(&full[s], kStageBytes);
-            tma_load_2d(st, &mAh, &full[s], kb * kBK, tm * kBM);
-            tma_load_2d(st + kTileBytes, &mAl, &full[s], kb * kBK, tm * kBM);
-            tma_load_2d(st + 2 * kTileBytes, &mBh, &full[s], kb * kBK, tn * kBN);
-            tma_load_2d(st + 3 * kTileBytes, &mBl, &full[s], kb * kBK, tn * kBN);
+            tma_load_2d(st, &mAh, &full[s], kb * kBK, a_row);
+            tma_load_2d(st + kTileBytes, &mAl, &full[s], kb * kBK, a_row);
+            tma_load_2d(st + 2 * kTileBytes, &mBh, &full[s], kb * kBK, b_row);
+            tma_load_2d(st + 3 * kTileBytes, &mBl, &full[s], kb * kBK, b_row);
             ++issued;
         }
     } else if (warp == 1 && lane == 0) {
@@ -167,8 +178,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ 
         // whole tile, 16-byte stores: rows and columns past M, N hold exact
         // zeros (their A rows / B rows are zero padding) and the planes are
         // allocated to the padded size
-        uint4 *ph = reinterpret_cast<uint4 *>(es.hi + (size_t)m * es.ld + tn * kBN);
-        uint4 *pl = reinterpret_cast<uint4 *>(es.lo + (size_t)m * es.ld + tn * kBN);
+        const size_t orow = (size_t)bz * es.b_rows + m;
+        uint4 *ph = reinterpret_cast<uint4 *>(es.hi + orow * es.ld + tn * kBN);
+        uint4 *pl = reinterpret_cast<uint4 *>(es.lo + orow * es.ld + tn * kBN);
 #pragma unroll 1
         for (int c0 = 0; c0 < kBN; c0 += 32) {
             float v[32];
@@ -197,7 +209,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ 
             nn_sm[x] = n < N ? (float)eg.occ[n] : 0.0f;
         }
         __syncthreads();
-        const float w = (float)eg.w, cut = (float)eg.cut, s2i = (float)eg.sig2inv;
+        const float w = (float)eg.omega[eg.mu0 + bz], cut = (float)eg.cut, s2i = (float)eg.sig2inv;
         const float w1 = m < M ? (float)eg.omega[m] : 0.0f, n1 = m < M ? (float)eg.occ[m] : 0.0f;
         const bool upper = eg.symmetric && (tn > tm);
         float acc = 0.0f;
@@ -271,13 +283,18 @@ __global__ void split_kernel(int rows, int cols, const SRC *__restrict__ src, si
     }
 }
 
-// YT[c][b] of one mode straight into BF16 hi/lo planes (FP64 sums).
+// YT[c][b] of mode mu0 + blockIdx.y straight into its BF16 hi/lo planes
+// (plane stride plane_elems; FP64 sums).
 __global__ void ybuild_bf16_kernel(int n_groups, const int *__restrict__ group_jk,
                                    const int *__restrict__ group_start, const int *__restrict__ blk_i,
-                                   const double *__restrict__ fc3, const double2 *__restrict__ eig_mu,
-                                   int ld, __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
+                                   const double *__restrict__ fc3, const double2 *__restrict__ eig, int nb,
+                                   int mu0, int ld, size_t plane_elems, __nv_bfloat16 *__restrict__ hi,
+                                   __nv_bfloat16 *__restrict__ lo) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_groups * 9) return;
+    const double2 *eig_mu = eig + (size_t)(mu0 + blockIdx.y) * nb;
+    hi += blockIdx.y * plane_elems;
+    lo += blockIdx.y * plane_elems;
     const int g = e / 9, bg = e % 9;
     const int j = group_jk[2 * g], k = group_jk[2 * g + 1];
     double acc = 0.0;
@@ -329,58 +346,82 @@ constexpr size_t kSmemBytes = kStages * kStageBytes + 1024;
 
 int tc_tile(void) { return kBM; }
 
-size_t tc_gamma_scratch_bytes(int nb) {
+// Modes per launch: enough GEMM1 tiles for about two CTAs per SM, at most 32.
+int tc_gamma_batch(int nb, int sms) {
+    const int nt = (nb + kBM - 1) / kBM;
+    const int want = (2 * std::max(sms, 1) + nt * nt - 1) / (nt * nt);
+    return std::max(1, std::min({want, 32, nb}));
+}
+
+size_t tc_gamma_scratch_bytes(int nb, int sms) {
     const int ld = (nb + kBN - 1) / kBN * kBN;     // whole 128-column tiles per row
     const int rows = (nb + kBM - 1) / kBM * kBM;
-    return 6 * ws_round(sizeof(__nv_bfloat16) * (size_t)rows * ld) + ws_round(sizeof(int) * 4);
+    const size_t plane = ws_round(sizeof(__nv_bfloat16) * (size_t)rows * ld);
+    // E hi/lo, then Y hi, Y lo, T hi, T lo of every mode of a batch
+    return (2 + 4 * (size_t)tc_gamma_batch(nb, sms)) * plane + ws_round(sizeof(int) * 4);
 }
 
 // The tensor-core pipeline for one Gamma-only system (Y build, T = E Y^T-form,
-// phi tiles of the delta band with the weight epilogue), mode by mode.
+// phi tiles of the delta band with the weight epilogue), MB modes per launch.
 cudaError_t launch_gamma_only_tc(const GammaPlan &gp, const GammaDev &d, const LwParams &p, void *scratch,
                                  const std::vector<int2> &tiles, const std::vector<int> &tile_start,
-                                 int2 *tiles_dev, int symmetric, double *partial_tc, int *err,
+                                 int2 *tiles_dev, int symmetric, double *partial_tc, int *err, int sms,
                                  cudaStream_t st) {
     const int nb = p.nb;
     const int ld = (nb + kBN - 1) / kBN * kBN;     // whole 128-column tiles per row
     const int rows = (nb + kBM - 1) / kBM * kBM;
+    const int mb = tc_gamma_batch(nb, sms);
     const size_t plane = ws_round(sizeof(__nv_bfloat16) * (size_t)rows * ld);
+    const size_t stack = (size_t)mb * plane;        // one operand plane for every mode of a batch
     char *b = static_cast<char *>(scratch);
-    auto P = [&](int i) { return reinterpret_cast<__nv_bfloat16 *>(b + i * plane); };
-    __nv_bfloat16 *Eh = P(0), *El = P(1), *Yh = P(2), *Yl = P(3), *Th = P(4), *Tl = P(5);
-    cudaError_t e = cudaMemsetAsync(b, 0, 6 * plane, st);
+    __nv_bfloat16 *Eh = reinterpret_cast<__nv_bfloat16 *>(b);
+    __nv_bfloat16 *El = reinterpret_cast<__nv_bfloat16 *>(b + plane);
+    auto S = [&](int i) { return reinterpret_cast<__nv_bfloat16 *>(b + 2 * plane + i * stack); };
+    __nv_bfloat16 *Yh = S(0), *Yl = S(1), *Th = S(2), *Tl = S(3);
+    cudaError_t e = cudaMemsetAsync(b, 0, 2 * plane + 4 * stack, st);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(err, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     split_kernel<double2><<<counted(4096), 256, 0, st>>>(nb, nb, reinterpret_cast<const double2 *>(d.eig),
                                                 (size_t)nb, ld, Eh, El);
+    // the planes of one stack are contiguous: plane_elems = plane / 2 elements apart
+    const size_t plane_elems = plane / sizeof(__nv_bfloat16);
+    const int stack_rows = (int)((size_t)mb * plane_elems / ld);
     CUtensorMap mEh, mEl, mYh, mYl, mTh, mTl;
-    if (!make_map(&mEh, Eh, rows, ld) || !make_map(&mEl, El, rows, ld) || !make_map(&mYh, Yh, rows, ld) ||
-        !make_map(&mYl, Yl, rows, ld) || !make_map(&mTh, Th, rows, ld) || !make_map(&mTl, Tl, rows, ld))
+    if (plane_elems % ld != 0 || !make_map(&mEh, Eh, rows, ld) || !make_map(&mEl, El, rows, ld) ||
+        !make_map(&mYh, Yh, stack_rows, ld) || !make_map(&mYl, Yl, stack_rows, ld) ||
+        !make_map(&mTh, Th, stack_rows, ld) || !make_map(&mTl, Tl, stack_rows, ld))
         return cudaErrorInvalidValue;
+    const int prow = (int)(plane_elems / ld);      // rows from one plane to the next (>= rows)
     auto k1 = tc_gemm_kernel<EPI_SPLIT>;
     auto k2 = tc_gemm_kernel<EPI_GAMMA>;
     e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
-    e = cudaMemcpyAsync(tiles_dev, tiles.data(), sizeof(int2) * std::max<size_t>(tiles.size(), 1),
-                        cudaMemcpyHostToDevice, st);
+    // tile records carry the mode's place in its batch: (tm | b << 16, tn)
+    std::vector<int2> enc(std::max<size_t>(tiles.size(), 1), make_int2(0, 0));
+    for (int mu = 0; mu < nb; ++mu)
+        for (int t = tile_start[mu]; t < tile_start[mu + 1]; ++t)
+            enc[t] = make_int2(tiles[t].x | ((mu % mb) << 16), tiles[t].y);
+    // (a copy from pageable memory returns once the host buffer is staged)
+    e = cudaMemcpyAsync(tiles_dev, enc.data(), sizeof(int2) * enc.size(), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
     const int nt = rows / kBM;
     const double sig2inv = 0.5 / (p.sigma_w * p.sigma_w);
-    for (int mu = 0; mu < nb; ++mu) {
-        const int t0 = tile_start[mu], t1 = tile_start[mu + 1];
-        if (!(gp.omega_h[mu] > 0.0) || t1 == t0) continue;
-        // Y_mu^T planes: the previous mode's entries live on the same (sparse)
-        // pattern and are all overwritten
-        ybuild_bf16_kernel<<<counted((gp.n_groups * 9 + 255) / 256), 256, 0, st>>>(
-            gp.n_groups, d.group_jk, d.group_start, d.blk_i, d.fc3, d.eig + (size_t)mu * nb, ld, Yh, Yl);
-        EpiSplit es{Th, Tl, ld};
+    for (int mu0 = 0; mu0 < nb; mu0 += mb) {
+        const int nm = std::min(mb, nb - mu0);
+        const int t0 = tile_start[mu0], t1 = tile_start[mu0 + nm];
+        if (t1 == t0) continue;                     // no delta-band tile (masked modes)
+        // Y_mu^T planes: every batch writes the same (sparse) pattern of
+        // entries, so the previous batch's values are all overwritten
+        ybuild_bf16_kernel<<<counted(dim3((gp.n_groups * 9 + 255) / 256, nm)), 256, 0, st>>>(
+            gp.n_groups, d.group_jk, d.group_start, d.blk_i, d.fc3, d.eig, nb, mu0, ld, plane_elems, Yh, Yl);
+        EpiSplit es{Th, Tl, ld, prow};
         EpiGamma eg{};
-        k1<<<counted(dim3(nt, nt)), 128, kSmemBytes, st>>>(mEh, mEl, mYh, mYl, nb, nb, ld, es, eg, err);
-        EpiGamma eg2{d.omega, d.occ, gp.omega_h[mu], sig2inv, p.cut_w, partial_tc + t0, d.allowed,
+        k1<<<counted(dim3(nt, nt, nm)), 128, kSmemBytes, st>>>(mEh, mEl, mYh, mYl, nb, nb, ld, es, eg, err);
+        EpiGamma eg2{d.omega, d.occ, mu0, prow, sig2inv, p.cut_w, partial_tc + t0, d.allowed,
                      tiles_dev + t0, symmetric};
-        EpiSplit es0{nullptr, nullptr, 0};
+        EpiSplit es0{nullptr, nullptr, 0, 0};
         k2<<<counted(t1 - t0), 128, kSmemBytes, st>>>(mTh, mTl, mEh, mEl, nb, nb, ld, es0, eg2, err);
     }
     return cudaGetLastError();
