@@ -389,6 +389,29 @@ def test_large_gamma_bf16split_tensor_cores(k, big324, kind):
     assert err < 1e-5
 
 
+@pytest.mark.parametrize("precision", ["fp64", "bf16split"])
+def test_batched_gamma_only_systems_match_single_calls(k, big324, precision):
+    """n_sys > 1, the batched Gamma-only mode of the 24-supercell workload: two
+    108-atom cells (different seeds and heavy fractions) in one call give,
+    bit for bit, the gamma and triplet counts of one call per system; the
+    first system is the oracle-checked cell of the tests above."""
+    kk, ctx = k
+    s1, nu1, eig1, g_o = big324
+    s2 = ki.fcc_supercell_system(3, seed=1001, heavy_fraction=0.45)
+    nu2, eig2 = ph.phonons(s2, (1, 1, 1))
+    w = ki.Workload("g324x2", [s1, s2], (1, 1, 1), 300.0, 0.05, 3.0)
+    opt = _opts(kk, w, precision)
+    nu = np.ascontiguousarray(np.concatenate([nu1.ravel(), nu2.ravel()]))
+    eig = np.ascontiguousarray(np.concatenate([eig1.ravel(), eig2.ravel()]))
+    g, (tot, allowed) = kk.kald_linewidths(ctx, [s1, s2], (1, 1, 1), nu, eig, opt)
+    ga, (ta, aa) = kk.kald_linewidths(ctx, s1, (1, 1, 1), nu1, eig1, opt)
+    gb, (tb, ab) = kk.kald_linewidths(ctx, s2, (1, 1, 1), nu2, eig2, opt)
+    np.testing.assert_array_equal(g[:324], np.ravel(ga))
+    np.testing.assert_array_equal(g[324:], np.ravel(gb))
+    assert tot == ta + tb == 2 * 324 ** 3 and allowed == aa + ab
+    assert _rel(np.ravel(ga), np.ravel(g_o), 1e-6 * g_o.max()) < (1e-10 if precision == "fp64" else 1e-5)
+
+
 def test_c3_bf16split_sampled_modes(k):
     """The 864-atom Gamma-only workload (2592 modes) on tensor cores, at full
     size in the benchmark's launch configuration, checked at sampled modes that
