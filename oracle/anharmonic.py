@@ -17,6 +17,9 @@ Definitions followed (paper, section "Boltzman Transport Equation"):
                    g^- = (1 + n' + n'') delta(omega - omega' - omega'')  Eq. phase_space
   linewidth        gamma_mu = Gamma^0_mu = (1/N_k) sum_{mu' mu''}
                                 (Gamma^+ + 1/2 Gamma^-)
+  full scattering  Gamma~_{mu mu'} = delta Gamma^0_mu + Gamma^1_{mu mu'}, Gamma^1 from
+  operator         the four rate terms of section "Boltzman Transport Equation"
+                   (see scattering_matrix)
 Readings where the paper is silent or inconsistent:
   * the 1/2 on Gamma^- (present in the linearised BTE, absent from the
     printed Gamma^0) and the 1/N_k (present in the BTE, absent from Gamma^0)
@@ -170,6 +173,68 @@ def linewidths(sys, mesh, nu, eig, T, sigma_thz, n_sigma=3.0, omega_min_thz=0.01
     if return_parts:
         return gamma, g_plus, g_minus
     return gamma
+
+
+def scattering_matrix(sys, mesh, nu, eig, T, sigma_thz, n_sigma=3.0, omega_min_thz=0.01,
+                      classical=False):
+    """The full linearised-BTE scattering operator of section "Boltzman
+    Transport Equation": Gamma~_{mu mu'} = delta_{mu mu'} Gamma^0_mu + Gamma^1_{mu mu'}
+    with (flat mode index mu = q nb + s)
+      Gamma^0_mu      = sum_{mu' mu''} (Gamma^+_{mu mu' mu''} + Gamma^-_{mu mu' mu''})
+      Gamma^1_{mu mu'} = (omega_mu' / omega_mu) sum_{mu''} (Gamma^+_{mu mu' mu''}
+                         - Gamma^+_{mu mu'' mu'} - Gamma^-_{mu mu' mu''} - Gamma^-_{mu mu'' mu'}).
+    Gamma^+- are the rates of Eq. gamma_operators with the same readings as
+    `linewidths` (1/N_k, the 1/2 on Gamma^-, Gaussian delta, masked modes);
+    no degenerate averaging, so Gamma^0 is the unaveraged linewidth.  For each
+    rate Gamma^+-_{mu a b} of a triplet (mu; a = (q', s'); b = (q'', s'')), the
+    sum over mu'' places (omega_a / omega_mu) Gamma^+-_{mu a b} at column a with
+    the sign of the first (+) or third (-) term, and (omega_b / omega_mu)
+    Gamma^+-_{mu a b} at column b with the sign of the second or fourth.
+    Returns (gamma0 [N], G1 [N, N]), N = N_k nb, in ps^-1."""
+    nq, nb = nu.shape
+    N = nq * nb
+    omega = TWO_PI * nu
+    valid = nu > omega_min_thz
+    n = bose(np.where(valid, omega, 0.0), T, classical)
+    eps = mass_scaled_eigvecs(sys, eig)
+    S = fc3_scatter_matrix(sys)
+    kf = mesh_fractions(mesh)
+    sig_w = TWO_PI * sigma_thz
+    inv_w = np.where(valid, 1.0 / np.where(valid, omega, 1.0), 0.0)
+    pref = HBAR_EVPS * np.pi / 8.0 * EV_A2_AMU ** 3 / nq
+    gamma0 = np.zeros(N)
+    G1 = np.zeros((N, N))
+    qps = np.arange(nq)
+    for q in range(nq):
+        rows = slice(q * nb, (q + 1) * nb)
+        for proc, sign in (("+", 1), ("-", -1)):
+            qpp = mesh_index(mesh, kf[q][None, :] + sign * kf[qps])
+            phi = projections(sys, mesh, eps, q, qps, proc, S)            # [q', s, s', s'']
+            w = omega[q][None, :, None, None]
+            wp = omega[qps][:, None, :, None]
+            wpp = omega[qpp][:, None, None, :]
+            npr = n[qps][:, None, :, None]
+            npp = n[qpp][:, None, None, :]
+            if proc == "+":
+                g = (npr - npp) * gaussian_delta(w + wp - wpp, sig_w, n_sigma)
+            else:
+                g = 0.5 * (1.0 + npr + npp) * gaussian_delta(w - wp - wpp, sig_w, n_sigma)
+            mask = (valid[q][None, :, None, None] & valid[qps][:, None, :, None]
+                    & valid[qpp][:, None, None, :])
+            rate = pref * np.where(mask, g * inv_w[q][None, :, None, None] * inv_w[qps][:, None, :, None]
+                                   * inv_w[qpp][:, None, None, :] * np.abs(phi) ** 2, 0.0)
+            gamma0[rows] += rate.sum(axis=(0, 2, 3))
+            # column a = (q', s'): + first term, - third term
+            to_a = rate.sum(axis=3)                                       # [q', s, s']
+            # column b = (q'', s''): - second term (+ process), - fourth term (- process)
+            to_b = rate.sum(axis=2)                                       # [q', s, s'']
+            sa = 1.0 if proc == "+" else -1.0
+            for x in range(nq):
+                ca = slice(qps[x] * nb, (qps[x] + 1) * nb)
+                cb = slice(qpp[x] * nb, (qpp[x] + 1) * nb)
+                G1[rows, ca] += sa * to_a[x] * omega[qps[x]][None, :] * inv_w[q][:, None]
+                G1[rows, cb] -= to_b[x] * omega[qpp[x]][None, :] * inv_w[q][:, None]
+    return gamma0, G1
 
 
 def degenerate_average(nu_q, gamma_q, tol):
