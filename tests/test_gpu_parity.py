@@ -389,6 +389,33 @@ def test_large_gamma_bf16split_tensor_cores(k, big324, kind):
     assert err < 1e-5
 
 
+def test_gamma_only_144_modes_partial_tiles_and_batch(k):
+    """A 2x2x3 conventional supercell (48 atoms, 144 modes): two 128-row tiles
+    per side with 112 padded columns, and a last batch of 16 modes after four
+    full batches of the tensor-core path.  Eigenpairs, gamma (FP64, BF16 split)
+    and the QHGK kappa against the oracle."""
+    kk, ctx = k
+    s = ki.fcc_supercell_system((2, 2, 3), seed=17, heavy_fraction=0.3)
+    assert s.n_branches == 144
+    nu_o, eig_o = ph.phonons(s, (1, 1, 1))
+    g_o = an.linewidths_gamma_only(s, nu_o, eig_o, 300.0, 0.05)
+    w = ki.Workload("g144", [s], (1, 1, 1), 300.0, 0.05, 3.0)
+    nu, eig, _ = kk.kald_phonons(ctx, s, (1, 1, 1), want_vel=False)
+    sq = lambda x: np.sign(x) * x * x
+    np.testing.assert_allclose(sq(nu), sq(nu_o), atol=1e-11 * np.max(nu_o) ** 2)
+    g64, (tot, allowed) = kk.kald_linewidths(ctx, s, (1, 1, 1), nu_o, eig_o, _opts(kk, w, "fp64"))
+    assert tot == 144 ** 3 and 0 < allowed < tot
+    assert _rel(np.ravel(g64), np.ravel(g_o), 1e-6 * g_o.max()) < 1e-10
+    gbf, (_, allowed_bf) = kk.kald_linewidths(ctx, s, (1, 1, 1), nu_o, eig_o, _opts(kk, w, "bf16split"))
+    assert allowed_bf == allowed
+    err = _rel(np.ravel(gbf), np.ravel(g_o), 1e-6 * g_o.max())
+    print(f"144 modes: bf16 split gamma max rel err {err:.3e}")
+    assert err < 1e-5
+    kap, _ = kk.kald_kappa_qhgk(ctx, [s], nu_o, eig_o, np.ravel(g64), _opts(kk, w))
+    kap_o = co.kappa_qhgk(s, nu_o, eig_o, g_o, 300.0)
+    np.testing.assert_allclose(kap[0], kap_o, rtol=1e-8, atol=1e-10 * np.abs(kap_o).max())
+
+
 @pytest.mark.parametrize("precision", ["fp64", "bf16split"])
 def test_batched_gamma_only_systems_match_single_calls(k, big324, precision):
     """n_sys > 1, the batched Gamma-only mode of the 24-supercell workload: two
