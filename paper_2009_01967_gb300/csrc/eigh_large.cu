@@ -1,6 +1,6 @@
 // FP64 eigensolver for one real symmetric matrix too large for the per-q
 // Jacobi kernel (the dynamical matrix of a Gamma-only supercell, nb > 96;
-// the eigenproblem of Section 2: D eta = omega^2 eta).
+// paper section "Lattice Dynamics", Eq. eigenvectors: D eta = omega^2 eta).
 //
 //   1. Householder tridiagonalisation.  Reflector k (k = 0 .. n-3) is
 //      H_k = I - 2 v v^T (|v| = 1) mapping row k right of the diagonal onto
