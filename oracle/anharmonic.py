@@ -175,6 +175,43 @@ def linewidths(sys, mesh, nu, eig, T, sigma_thz, n_sigma=3.0, omega_min_thz=0.01
     return gamma
 
 
+def phase_space(mesh, nu, T, sigma_thz, n_sigma=3.0, omega_min_thz=0.01, classical=False,
+                return_parts=False):
+    """Normalised phase space per mode g_mu = (1/N_k) sum_{mu' mu''} g_{mu mu' mu''}
+    (Eq. phase_space and the definition after Eq. delta_deconstructed), [N_k, nb]
+    in ps: the weights of Eq. phase_space over the momentum-conserving
+    triplets (q'' = q +- q'), with the same readings as `linewidths` (1/2 on
+    the - process, Gaussian delta, masked modes).  No matrix elements enter."""
+    nq, nb = nu.shape
+    omega = TWO_PI * nu
+    valid = nu > omega_min_thz
+    n = bose(np.where(valid, omega, 0.0), T, classical)
+    kf = mesh_fractions(mesh)
+    sig_w = TWO_PI * sigma_thz
+    g_plus = np.zeros((nq, nb))
+    g_minus = np.zeros((nq, nb))
+    qps = np.arange(nq)
+    for q in range(nq):
+        for sign in (1, -1):
+            qpp = mesh_index(mesh, kf[q][None, :] + sign * kf[qps])
+            w = omega[q][None, :, None, None]
+            wp = omega[qps][:, None, :, None]
+            wpp = omega[qpp][:, None, None, :]
+            npr = n[qps][:, None, :, None]
+            npp = n[qpp][:, None, None, :]
+            mask = (valid[q][None, :, None, None] & valid[qps][:, None, :, None]
+                    & valid[qpp][:, None, None, :])
+            if sign == 1:
+                g = (npr - npp) * gaussian_delta(w + wp - wpp, sig_w, n_sigma)
+                g_plus[q] += np.sum(np.where(mask, g, 0.0), axis=(0, 2, 3)) / nq
+            else:
+                g = 0.5 * (1.0 + npr + npp) * gaussian_delta(w - wp - wpp, sig_w, n_sigma)
+                g_minus[q] += np.sum(np.where(mask, g, 0.0), axis=(0, 2, 3)) / nq
+    if return_parts:
+        return g_plus + g_minus, g_plus, g_minus
+    return g_plus + g_minus
+
+
 def scattering_matrix(sys, mesh, nu, eig, T, sigma_thz, n_sigma=3.0, omega_min_thz=0.01,
                       classical=False):
     """The full linearised-BTE scattering operator of section "Boltzman

@@ -156,6 +156,23 @@ def kappa_qhgk(sys, nu, eig, gamma, T, omega_min_thz=0.01, degen_tol_thz=1e-5,
     return kappa * KAPPA_SI / sys.volume
 
 
+def diffusivity(sys, nu, eig, gamma, omega_min_thz=0.01, W=None):
+    """Mode diffusivity D_mu [nb] (A^2/ps) of a Gamma-only system, Eq.
+    diffusivity_per_mode read as D_mu = (1/3) sum_a sum_mu' |v^a_{mu mu'}|^2 tau_{mu mu'}
+    (the Allen-Feldman diffusivity averaged over the three directions; the
+    printed 1/(N_k V) prefactor would not give a diffusivity and is dropped).
+    With classical populations c_{mu mu'} = kB, so that tr(kappa_QHGK) / 3 =
+    kB / V sum_mu D_mu."""
+    omega = TWO_PI * nu[0]
+    valid = (nu[0] > omega_min_thz) & (gamma > 0)
+    if W is None:
+        W = generalized_velocity(sys, nu, eig, omega_min_thz)
+    tau = lorentzian_tau(omega, np.where(valid, gamma, 0.0))
+    pair = valid[:, None] & valid[None, :]
+    D = np.einsum("amn,mn->m", W * W, np.where(pair, tau, 0.0)) / 3.0
+    return np.where(valid, D, 0.0)
+
+
 def kappa_qhgk_mesh(sys, mesh, nu, eig, gamma, T, omega_min_thz=0.01, degen_tol_thz=1e-5,
                     classical=False, degenerate_pairs_only=False):
     """q-resolved QHGK on a mesh (same-q interband pairs), with velocities in
