@@ -200,13 +200,20 @@ kald_status kald_kappa_qhgk(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
  *           used when `stream` is NULL, and failures are described by
  *           kald_last_error(ctx)
  *   stream  cudaStream_t to run on, or NULL (then ctx's stream, or the
- *           default stream without ctx); the call synchronises it
+ *           default stream without ctx); the call waits for `stream` to
+ *           finish (cudaStreamSynchronize) before it returns
  *   nu_thz, eigvec, gamma, kappa   DEVICE pointers (as for kald_kappa_rta)
  * The first call on a device looks up the array's device address and caches
- * it; make that first call before any stream capture.  Calls share the one
- * array, so calls that overlap on the GPU race.  A system and mesh whose
- * scratch exceeds 4 MiB (roughly 48 KB per 1000 q-points plus 96 bytes per
- * fc2 block) is rejected with KALD_E_INVALID. */
+ * it; make that first call before any stream capture.  The cached address
+ * belongs to the device's current CUDA context: after cudaDeviceReset (or
+ * anything else that re-creates the primary context) it is stale, so do not
+ * call this entry point again in that process.  Calls share the one array,
+ * so calls that overlap on the GPU race.  Scratch needed: 96 bytes per
+ * q-point (24 B of coordinates and 72 B of partial sums, i.e. about 96 KB per
+ * 1000 q-points) plus, for the fc2 table, 96 bytes per fc2 block and 12 bytes
+ * per (i, j) atom pair, each table rounded up to 256 bytes.  A system and
+ * mesh that need more than 4 MiB (a 2-atom cell fits up to about 40,000
+ * q-points) are rejected with KALD_E_INVALID. */
 kald_status kald_kappa_rta_noalloc(kald_ctx *ctx, void *stream, const kald_system *sys,
                                    const int32_t mesh[3], const double *nu_thz,
                                    const double *eigvec, const double *gamma,

@@ -14,10 +14,15 @@
 // kernel (on the host it is only a stand-in, not a device address); the
 // device address is taken once per device with cudaGetSymbolAddress, on the
 // first call made with that device current, and cached.  That first call
-// should therefore come before any stream capture.  All calls share the one
-// array: calls that overlap on the GPU (two streams, or two host threads)
-// race on it.  Nothing in it needs to start at zero: every q-point writes its
-// own partial sums before they are added.
+// should therefore come before any stream capture.  The cached address is
+// only valid in the CUDA context it was taken in: after cudaDeviceReset the
+// module is loaded again and the address is stale, so the entry point must
+// not be called again in that process.  Each call waits for its stream
+// before it returns.  All calls share the one array: calls that overlap on
+// the GPU (two streams, or two host threads) race on it.  Nothing in it needs
+// to start at zero: every q-point writes its own partial sums before they are
+// added.  Sizes: 96 B per q-point (coordinates and partial sums) plus 96 B per
+// fc2 block and 12 B per atom pair of the fc2 table.
 
 #include <algorithm>
 #include <cmath>
