@@ -210,8 +210,9 @@ kald_status kald_kappa_qhgk(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
  * call this entry point again in that process.  Calls share the one array,
  * so calls that overlap on the GPU race.  Scratch needed: 96 bytes per
  * q-point (24 B of coordinates and 72 B of partial sums, i.e. about 96 KB per
- * 1000 q-points) plus, for the fc2 table, 96 bytes per fc2 block and 12 bytes
- * per (i, j) atom pair, each table rounded up to 256 bytes.  A system and
+ * 1000 q-points) plus, for the fc2 table, 104 bytes per fc2 block, 12 bytes
+ * per (i, j) atom pair and 8 bytes per atom, each table rounded up to 256
+ * bytes.  A system and
  * mesh that need more than 4 MiB (a 2-atom cell fits up to about 40,000
  * q-points) are rejected with KALD_E_INVALID. */
 kald_status kald_kappa_rta_noalloc(kald_ctx *ctx, void *stream, const kald_system *sys,

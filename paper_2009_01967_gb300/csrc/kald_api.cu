@@ -140,15 +140,38 @@ T *upload(kald_ctx *ctx, const std::vector<T> &v) {
 template <typename T>
 size_t bytes_of(const std::vector<T> &v) { return ws_round(sizeof(T) * std::max<size_t>(v.size(), 1)); }
 
+// Mass-scaled force constants on the device: the raw blocks, their atoms and
+// the masses are uploaded and a kernel divides each block by the square root
+// of its masses' product (launch_mass_scale); out_stride >= nval, f32 selects
+// an FP32 copy.  scaled_bytes() is the workspace this takes.
+size_t scaled_bytes(const std::vector<double> &raw, const std::vector<int> &atoms, const HostSystem &h,
+                    int nval, int out_stride, int f32) {
+    const size_t nblk = raw.size() / nval;
+    return bytes_of(raw) + bytes_of(atoms) + bytes_of(h.masses) +
+           ws_round((f32 ? sizeof(float) : sizeof(double)) * std::max<size_t>(nblk, 1) * out_stride);
+}
+void *upload_scaled(kald_ctx *ctx, const std::vector<double> &raw, const std::vector<int> &atoms,
+                    const HostSystem &h, int nval, int out_stride, int f32) {
+    const size_t nblk = raw.size() / nval;
+    const double *r = upload(ctx, raw);
+    const int *a = upload(ctx, atoms);
+    const double *m = upload(ctx, h.masses);
+    void *out = ws_take(ctx, (f32 ? sizeof(float) : sizeof(double)) * std::max<size_t>(nblk, 1) * out_stride);
+    // (a launch error surfaces at the call's final status check)
+    launch_mass_scale((int)nblk, nval, (int)(atoms.size() / std::max<size_t>(nblk, 1)), r, a, m, out_stride, f32,
+                      out, ctx->stream);
+    return out;
+}
+
 size_t fc2_bytes(const HostSystem &h) {
-    return bytes_of(h.pair2_i) + bytes_of(h.pair2_j) + bytes_of(h.pair2_start) + bytes_of(h.fc2_scaled) +
-           bytes_of(h.fc2_rcart) + bytes_of(h.fc2_dist);
+    return bytes_of(h.pair2_i) + bytes_of(h.pair2_j) + bytes_of(h.pair2_start) +
+           scaled_bytes(h.fc2_blk, h.fc2_atoms, h, 9, 9, 0) + bytes_of(h.fc2_rcart) + bytes_of(h.fc2_dist);
 }
 void upload_fc2(kald_ctx *ctx, const HostSystem &h, DevSystem &d) {
     d.pair2_i = upload(ctx, h.pair2_i);
     d.pair2_j = upload(ctx, h.pair2_j);
     d.pair2_start = upload(ctx, h.pair2_start);
-    d.fc2 = upload(ctx, h.fc2_scaled);
+    d.fc2 = static_cast<double *>(upload_scaled(ctx, h.fc2_blk, h.fc2_atoms, h, 9, 9, 0));
     d.fc2_r = upload(ctx, h.fc2_rcart);
     d.fc2_d = upload(ctx, h.fc2_dist);
 }
@@ -241,7 +264,8 @@ kald_status plan_system(kald_ctx *ctx, const kald_system *s, HostSystem &h) {
         const int32_t *x = s->fc2_idx + 5 * (size_t)b;
         return (long long)x[0] * n + x[1];
     });
-    h.fc2_scaled.resize(9 * (size_t)n2);
+    h.fc2_blk.resize(9 * (size_t)n2);
+    h.fc2_atoms.resize(2 * (size_t)n2);
     h.fc2_rcart.resize(3 * (size_t)n2);
     h.fc2_dist.resize(3 * (size_t)n2);
     h.pair2_i.clear(); h.pair2_j.clear(); h.pair2_start.clear();
@@ -252,8 +276,9 @@ kald_status plan_system(kald_ctx *ctx, const kald_system *s, HostSystem &h) {
         if (h.pair2_i.empty() || h.pair2_i.back() != i || h.pair2_j.back() != j) {
             h.pair2_i.push_back(i); h.pair2_j.push_back(j); h.pair2_start.push_back(t);
         }
-        const double sc = 1.0 / std::sqrt(s->masses[i] * s->masses[j]);
-        for (int e = 0; e < 9; ++e) h.fc2_scaled[9 * (size_t)t + e] = s->fc2[9 * (size_t)b + e] * sc;
+        for (int e = 0; e < 9; ++e) h.fc2_blk[9 * (size_t)t + e] = s->fc2[9 * (size_t)b + e];
+        h.fc2_atoms[2 * (size_t)t] = i;
+        h.fc2_atoms[2 * (size_t)t + 1] = j;
         double R[3];
         cart(x + 2, R);
         for (int c = 0; c < 3; ++c) {
@@ -309,7 +334,8 @@ kald_status plan_system(kald_ctx *ctx, const kald_system *s, HostSystem &h) {
         const int32_t *x = s->fc3_idx + 9 * (size_t)b;
         return (long long)x[1] * n + x[5];
     });
-    h.fc3_scaled.resize(27 * (size_t)n3);
+    h.fc3_blk.resize(27 * (size_t)n3);
+    h.fc3_atoms.resize(3 * (size_t)n3);
     h.fc3_i.resize(n3); h.fc3_rj.resize(n3); h.fc3_rk.resize(n3);
     h.pair3_j.clear(); h.pair3_k.clear(); h.pair3_start.clear();
     for (int t = 0; t < n3; ++t) {
@@ -319,8 +345,10 @@ kald_status plan_system(kald_ctx *ctx, const kald_system *s, HostSystem &h) {
         if (h.pair3_j.empty() || h.pair3_j.back() != j || h.pair3_k.back() != k) {
             h.pair3_j.push_back(j); h.pair3_k.push_back(k); h.pair3_start.push_back(t);
         }
-        const double sc = 1.0 / std::sqrt(s->masses[i] * s->masses[j] * s->masses[k]);
-        for (int e = 0; e < 27; ++e) h.fc3_scaled[27 * (size_t)t + e] = s->fc3[27 * (size_t)b + e] * sc;
+        for (int e = 0; e < 27; ++e) h.fc3_blk[27 * (size_t)t + e] = s->fc3[27 * (size_t)b + e];
+        h.fc3_atoms[3 * (size_t)t] = i;
+        h.fc3_atoms[3 * (size_t)t + 1] = j;
+        h.fc3_atoms[3 * (size_t)t + 2] = k;
         h.fc3_i[t] = i;
         h.fc3_rj[t] = rep_of(x + 2);
         h.fc3_rk[t] = rep_of(x + 6);
@@ -397,8 +425,8 @@ kald_status plan_system_cached(kald_ctx *ctx, const kald_system *s, std::shared_
     auto h = std::make_shared<HostSystem>();
     kald_status st = plan_system(ctx, s, *h);
     if (st) return st;
-    const size_t bytes = sizeof(double) * (h->fc3_scaled.size() + h->fc2_scaled.size() + 6 * h->fc2_rcart.size()) +
-                         sizeof(int) * 4 * h->fc3_i.size();
+    const size_t bytes = sizeof(double) * (h->fc3_blk.size() + h->fc2_blk.size() + 6 * h->fc2_rcart.size()) +
+                         sizeof(int) * (7 * h->fc3_i.size() + h->fc2_atoms.size());
     // keep at most 32 plans and 1 GB of them, dropping the oldest
     size_t total = bytes;
     for (const auto &p : ctx->plans) total += p.bytes;
@@ -657,7 +685,8 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
                            gp.tiles, gp.tile_start);
             }
             const size_t n_tiles = std::max<size_t>(gp.tiles.size(), 1);
-            size_t need = bytes_of(gjk) + bytes_of(h.pair3_start) + bytes_of(h.fc3_i) + bytes_of(h.fc3_scaled) +
+            size_t need = bytes_of(gjk) + bytes_of(h.pair3_start) + bytes_of(h.fc3_i) +
+                          scaled_bytes(h.fc3_blk, h.fc3_atoms, h, 27, 27, 0) +
                           2 * ws_round(sizeof(double) * nb) + ws_round(sizeof(int) * nb) + ws_round(16) +
                           ws_round(16);
             if (mode == KALD_BF16_SPLIT)
@@ -673,7 +702,7 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
             gd.group_jk = upload(ctx, gjk);
             gd.group_start = upload(ctx, h.pair3_start);
             gd.blk_i = upload(ctx, h.fc3_i);
-            gd.fc3 = upload(ctx, h.fc3_scaled);
+            gd.fc3 = static_cast<const double *>(upload_scaled(ctx, h.fc3_blk, h.fc3_atoms, h, 27, 27, 0));
             gd.nu = stage_in(ctx, nu_thz + off_nb, (size_t)nb, d_nu);
             gd.eig = stage_in(ctx, reinterpret_cast<const double2 *>(eigvec) + off_eig, nn, d_eig);
             gd.omega = static_cast<double *>(ws_take(ctx, sizeof(double) * nb));
@@ -799,18 +828,9 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
         p.n_rounds = ys.n_rounds;
         std::vector<int4> binfo(std::max<size_t>(n3, 1), make_int4(0, 0, 0, 0));
         for (size_t b = 0; b < n3; ++b) binfo[b] = make_int4(h.fc3_i[b], h.fc3_rj[b], h.fc3_rk[b], 0);
-        std::vector<float> fc3f;
-        std::vector<double> fc3d;
-        if (f32w) fc3f.assign(28 * std::max<size_t>(n3, 1), 0.0f);
-        else fc3d.assign(28 * std::max<size_t>(n3, 1), 0.0);
-        for (size_t b = 0; b < n3; ++b)
-            for (int e = 0; e < 27; ++e) {
-                if (f32w) fc3f[28 * b + e] = (float)h.fc3_scaled[27 * b + e];
-                else fc3d[28 * b + e] = h.fc3_scaled[27 * b + e];
-            }
         const size_t c2 = f32w ? sizeof(float2) : sizeof(double2);
         size_t need = bytes_of(ys.group_jk) + bytes_of(ys.segs) + bytes_of(ys.sched) + bytes_of(binfo) +
-                      (f32w ? bytes_of(fc3f) : bytes_of(fc3d)) +
+                      scaled_bytes(h.fc3_blk, h.fc3_atoms, h, 27, 28, f32w) +
                       bytes_of(h.rep_cart) + bytes_of(qc) + bytes_of(qf) +
                       2 * ws_round(sizeof(double) * nq * nb) + ws_round(c2 * nn) +
                       ws_round(c2 * (size_t)nq * h.n_rep) +
@@ -818,6 +838,7 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
         if (!d_nu) need += ws_round(sizeof(double) * nq * nb);
         if (!d_eig) need += ws_round(sizeof(double2) * nn);
         if (!d_g) need += ws_round(sizeof(double) * nq * nb);
+        if (f32w) need += ws_round(sizeof(float4) * (size_t)nq * nb);
         if (tcx)
             need += ws_round(tcx_scratch_bytes(nb, nq, tcx_b)) + ws_round(16) + bytes_of(tc_gjk) +
                     bytes_of(tc_part_start) + bytes_of(tc_glist) + bytes_of(h.pair3_start);
@@ -830,7 +851,8 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
         d.segs = upload(ctx, ys.segs);
         d.sched = upload(ctx, ys.sched);
         d.blkinfo = upload(ctx, binfo);
-        d.fc3 = f32w ? (const void *)upload(ctx, fc3f) : (const void *)upload(ctx, fc3d);
+        // Phi3 / sqrt(mi mj mk), 28 values per block (16-byte loads), in the working precision
+        d.fc3 = upload_scaled(ctx, h.fc3_blk, h.fc3_atoms, h, 27, 28, f32w);
         d.rep_cart = upload(ctx, h.rep_cart);
         d.qcart = upload(ctx, qc);
         d.qfrac = upload(ctx, qf);
@@ -838,6 +860,7 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
         d.eig = stage_in(ctx, reinterpret_cast<const double2 *>(eigvec) + off_eig, nn, d_eig);
         d.omega = static_cast<double *>(ws_take(ctx, sizeof(double) * nq * nb));
         d.occ = static_cast<double *>(ws_take(ctx, sizeof(double) * nq * nb));
+        d.wn32 = f32w ? static_cast<float4 *>(ws_take(ctx, sizeof(float4) * (size_t)nq * nb)) : nullptr;
         d.eps_work = ws_take(ctx, c2 * nn);
         d.chi = ws_take(ctx, c2 * (size_t)nq * h.n_rep);
         d.partial = static_cast<double *>(ws_take(ctx, sizeof(double) * (size_t)nq * p.n_chunks * nb));
@@ -960,7 +983,7 @@ kald_status kald_kappa_qhgk(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
         const int nb = h.nb;
         const size_t nn = (size_t)nb * nb;
         // CSR by row atom i: the (i, j) sorted fc2 order is contiguous in i
-        std::vector<int> row_start(h.n_atoms + 1, 0), col_j(h.fc2_scaled.size() / 9);
+        std::vector<int> row_start(h.n_atoms + 1, 0), col_j(h.fc2_blk.size() / 9);
         for (size_t p = 0; p < h.pair2_i.size(); ++p)
             for (int b = h.pair2_start[p]; b < h.pair2_start[p + 1]; ++b) {
                 col_j[b] = h.pair2_j[p];
@@ -968,7 +991,8 @@ kald_status kald_kappa_qhgk(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
             }
         for (int i = 0; i < h.n_atoms; ++i) row_start[i + 1] += row_start[i];
         const int n_partial = std::min(nb, 4 * std::max(1, ctx->sm_count));
-        size_t need = bytes_of(row_start) + bytes_of(col_j) + bytes_of(h.fc2_scaled) + bytes_of(h.fc2_dist) +
+        size_t need = bytes_of(row_start) + bytes_of(col_j) + scaled_bytes(h.fc2_blk, h.fc2_atoms, h, 9, 9, 0) +
+                      bytes_of(h.fc2_dist) +
                       ws_round(sizeof(double) * nn) + 2 * ws_round(sizeof(double) * 3 * nn) +
                       ws_round(sizeof(double) * (9 * (size_t)n_partial + nb)) + ws_round(72);
         if (!d_nu) need += ws_round(sizeof(double) * nb);
@@ -979,7 +1003,7 @@ kald_status kald_kappa_qhgk(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
         f.n_rows = h.n_atoms;
         f.row_start = upload(ctx, row_start);
         f.col_j = upload(ctx, col_j);
-        f.blk = upload(ctx, h.fc2_scaled);
+        f.blk = static_cast<const double *>(upload_scaled(ctx, h.fc2_blk, h.fc2_atoms, h, 9, 9, 0));
         f.dist = upload(ctx, h.fc2_dist);
         const double *nu_d = stage_in(ctx, nu_thz + off_nb, (size_t)nb, d_nu);
         const double2 *eig_d = stage_in(ctx, reinterpret_cast<const double2 *>(eigvec) + off_eig, nn, d_eig);

@@ -90,13 +90,15 @@ struct HostSystem {
     // fc2 grouped by (i, j) atom pair (CSR over pairs)
     std::vector<int> pair2_i, pair2_j, pair2_start;   // pairs, start offsets (n_pairs+1)
     std::vector<int> fc2_rep;                          // replica index per block (sorted order)
-    std::vector<double> fc2_scaled;                    // [n_fc2][9] Phi2/sqrt(mi mj)
+    std::vector<double> fc2_blk;                       // [n_fc2][9] Phi2 (eV/A^2), grouped, not mass-scaled
+    std::vector<int> fc2_atoms;                        // [n_fc2][2] (i, j) of each block
     std::vector<double> fc2_rcart;                     // [n_fc2][3] Cartesian R
     std::vector<double> fc2_dist;                      // [n_fc2][3] x_i - x_j - R
     // fc3 grouped by (j, k) atom pair (CSR over output pairs)
     std::vector<int> pair3_j, pair3_k, pair3_start;
     std::vector<int> fc3_i, fc3_rj, fc3_rk;            // per block (sorted order)
-    std::vector<double> fc3_scaled;                    // [n_fc3][27] Phi3/sqrt(mi mj mk)
+    std::vector<double> fc3_blk;                       // [n_fc3][27] Phi3 (eV/A^3), grouped, not mass-scaled
+    std::vector<int> fc3_atoms;                        // [n_fc3][3] (i, j, k) of each block
     // distinct replica vectors (Cartesian) referenced by fc3 / fc2
     std::vector<double> rep_cart;                      // [n_rep][3]
     std::vector<int> rep_int;                          // [n_rep][3] integer cell vectors
@@ -120,6 +122,11 @@ struct DevFc2 {
     const double *blk;        // [n][9]
     const double *rcart;      // [n][3]
 };
+// Mass-scaled copy of force-constant blocks on the device (Phi / sqrt of the
+// product of the n_at masses of each block): raw [n_blk][nval] FP64, atoms
+// [n_blk][n_at], out [n_blk][out_stride] (zero padding past nval), FP64 or FP32.
+cudaError_t launch_mass_scale(int n_blk, int nval, int n_at, const double *raw, const int *atoms,
+                              const double *masses, int out_stride, int f32, void *out, cudaStream_t st);
 cudaError_t launch_dynmat(const DevFc2 &f, int nb, int nq, const double *qcart,
                           double2 *D, cudaStream_t st);
 cudaError_t launch_jacobi(int nb, int nq, double2 *A, double2 *V, double *nu_thz,
@@ -169,6 +176,8 @@ struct LwDev {
     // derived (filled by prep kernels)
     double *omega;            // [nq*nb] rad/ps (0 if masked)
     double *occ;              // [nq*nb] Bose n (0 if masked)
+    float4 *wn32;             // [nq*nb] (w hi, w lo, n hi, n lo) FP32 pairs of omega and occ
+                              // (FP32 and BF16-split paths; see wdiff.cuh)
     void *eps_work;           // [nq][nb][nb] eps^T in the working precision
     void *chi;                // [nq][n_rep] exp(-i q.R) in the working precision
     double *partial;          // [nq][n_chunks][nb] FP64 partial sums

@@ -23,8 +23,10 @@
 // depend on the schedule.
 
 #include <algorithm>
+#include <type_traits>
 
 #include "kald_internal.h"
+#include "wdiff.cuh"
 
 namespace kald {
 namespace {
@@ -60,6 +62,15 @@ __global__ void mode_prep_kernel(int n, const double *__restrict__ nu, double om
     }
     omega[x] = ok ? w : 0.0;
     occ[x] = n_b;
+}
+
+// FP32 pairs (hi, lo) of omega and n for the compensated epilogue differences.
+__global__ void wn_pair_kernel(int n, const double *__restrict__ omega, const double *__restrict__ occ,
+                               float4 *__restrict__ out) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    const F2 w = f2_of(omega[x]), o = f2_of(occ[x]);
+    out[x] = make_float4(w.h, w.l, o.h, o.l);
 }
 
 template <typename R2>
@@ -131,7 +142,8 @@ __device__ __forceinline__ void load_blk(const double *f, double v[28]) {
 //   EppT [P][P]     conj(eps(q''))^T     (only when operands live in smem)
 //   es   [P]        eps(q, s) column
 //   chip, chipp [n_rep]    chi(q'), chi(q'')
-//   wp, np_, wpp, npp [P]  omega and n of q' / q'' (R)
+//   wp, np_, wpp, npp [P]  omega and n of q' / q'' (R; the hi parts for FP32)
+//   wpl, npl, wppl, nppl [P]  lo parts of the FP32 pairs (FP32 only; wdiff.cuh)
 //   red  [nb] double       per-mode sums over the item's q' (fixed order)
 //   wsum [nwarps] double   per-warp sums of the current mode
 //   tiles [kThreads] short active (s', s'') tiles of the delta band
@@ -158,8 +170,13 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
     R *np_ = wp + P;
     R *wpp = np_ + P;
     R *npp = wpp + P;
+    R *wpl = npp + P;
+    R *npl = wpl + P;
+    R *wppl = npl + P;
+    R *nppl = wppl + P;
+    constexpr bool kPair = std::is_same<R, float>::value;
     double *red = reinterpret_cast<double *>(
-        (reinterpret_cast<uintptr_t>(npp + P) + 15) & ~uintptr_t(15));
+        (reinterpret_cast<uintptr_t>(nppl + P) + 15) & ~uintptr_t(15));
     double *wsum = red + nb;
     short *tiles = reinterpret_cast<short *>(wsum + nwarps);
     __shared__ int item_sm, n_act_sm, warp_cnt[nwarps];
@@ -197,10 +214,17 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
             }
             for (int x = tid; x < P; x += kThreads) {
                 const bool in = x < nb;
-                wp[x] = in ? (R)d.omega[(size_t)qp * nb + x] : (R)0;
-                np_[x] = in ? (R)d.occ[(size_t)qp * nb + x] : (R)0;
-                wpp[x] = in ? (R)d.omega[(size_t)qpp * nb + x] : (R)0;
-                npp[x] = in ? (R)d.occ[(size_t)qpp * nb + x] : (R)0;
+                if constexpr (kPair) {
+                    const float4 a = in ? d.wn32[(size_t)qp * nb + x] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 b = in ? d.wn32[(size_t)qpp * nb + x] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    wp[x] = a.x; wpl[x] = a.y; np_[x] = a.z; npl[x] = a.w;
+                    wpp[x] = b.x; wppl[x] = b.y; npp[x] = b.z; nppl[x] = b.w;
+                } else {
+                    wp[x] = in ? (R)d.omega[(size_t)qp * nb + x] : (R)0;
+                    np_[x] = in ? (R)d.occ[(size_t)qp * nb + x] : (R)0;
+                    wpp[x] = in ? (R)d.omega[(size_t)qpp * nb + x] : (R)0;
+                    npp[x] = in ? (R)d.occ[(size_t)qpp * nb + x] : (R)0;
+                }
             }
             if (OPER_SMEM) {
                 const R2 *src1 = epsT_all + (size_t)qp * nb * nb;
@@ -221,6 +245,7 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
                 const double w_s = d.omega[(size_t)q * nb + s];
                 if (w_s <= 0.0) continue;              // masked mode (uniform branch)
                 const R w = (R)w_s;
+                const F2 wsp = f2_of(w_s);             // FP32 pair of w (FP32 epilogue)
                 // ---- Y_s: zero, then the scheduled gather over fc3 blocks
                 for (int x = tid; x < P; x += kThreads)
                     es[x] = x < nb ? epsT_all[((size_t)q * nb + x) * nb + s] : mk<R2>(0.0, 0.0);
@@ -306,8 +331,11 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
                     for (int c = 0; c < kTC; ++c) { xlo = fmin(xlo, wpp[c0 + c]); xhi = fmax(xhi, wpp[c0 + c]); }
                     // d+ = w + w' - w'' in [w + wlo - xhi, w + whi - xlo]
                     // d- = w - w' - w'' in [w - whi - xhi, w - wlo - xlo]
-                    band = ((w + wlo - xhi < cut) && (w + whi - xlo > -cut)) ||
-                           ((w - whi - xhi < cut) && (w - wlo - xlo > -cut));
+                    // (widened by 1e-4 of the cut so that rounding here never drops a
+                    // tile that the exact per-element test below would reach)
+                    const R cb = cut * (R)1.0001;
+                    band = ((w + wlo - xhi < cb) && (w + whi - xlo > -cb)) ||
+                           ((w - whi - xhi < cb) && (w - wlo - xlo > -cb));
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, band);
                 if (lane == 0) warp_cnt[warp] = __popc(bal);
@@ -391,16 +419,32 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
                             const R w1 = wp[r0 + r], n1 = np_[r0 + r];
                             if (w1 <= (R)0) continue;
                             const R iw1 = (R)1 / w1;
+                            F2 w1p, n1p, sp, sm;
+                            if constexpr (kPair) {
+                                w1p = F2{wp[r0 + r], wpl[r0 + r]};
+                                n1p = F2{np_[r0 + r], npl[r0 + r]};
+                                sp = f2_add(wsp, w1p);
+                                sm = f2_add(wsp, f2_neg(w1p));
+                            }
 #pragma unroll
                             for (int c = 0; c < kTC; ++c) {
                                 const R w2 = wpp[c0 + c];
                                 if (w2 <= (R)0) continue;
                                 const R n2 = npp[c0 + c];
-                                const R dp = w + w1 - w2;
-                                const R dm = w - w1 - w2;
+                                R dp, dm, dn;
+                                if constexpr (kPair) {
+                                    const F2 w2p{wpp[c0 + c], wppl[c0 + c]};
+                                    dp = f2_diff(sp, w2p);
+                                    dm = f2_diff(sm, w2p);
+                                    dn = f2_diff(n1p, F2{npp[c0 + c], nppl[c0 + c]});
+                                } else {
+                                    dp = w + w1 - w2;
+                                    dm = w - w1 - w2;
+                                    dn = n1 - n2;
+                                }
                                 R g = (R)0;
                                 bool hit = false;
-                                if (fabs(dp) < cut) { g += (n1 - n2) * exp(-dp * dp * sig2inv); hit = true; }
+                                if (fabs(dp) < cut) { g += dn * exp(-dp * dp * sig2inv); hit = true; }
                                 if (fabs(dm) < cut) {
                                     g += (R)0.5 * ((R)1 + n1 + n2) * exp(-dm * dm * sig2inv);
                                     hit = true;
@@ -480,7 +524,7 @@ size_t lw_smem_bytes(const LwParams &p, bool oper_smem) {
     size_t b = sizeof(R2) * (size_t)P * (P + 1);
     if (oper_smem) b += 2 * sizeof(R2) * (size_t)P * P;
     b += sizeof(R2) * (P + 2 * p.n_rep);
-    b += sizeof(R) * 4 * P;
+    b += sizeof(R) * 8 * P;
     b = (b + 15) & ~size_t(15);
     b += sizeof(double) * (p.nb + kThreads / 32);
     b += sizeof(short) * kThreads;
@@ -503,6 +547,7 @@ cudaError_t launch_lw_prep(const LwParams &p, const LwDev &d, int fp32, cudaStre
     const size_t ne = (size_t)p.nq * p.nb * p.nb;
     const int grid = (int)std::min<size_t>((ne + 255) / 256, 4096);
     if (fp32) {
+        wn_pair_kernel<<<counted((n + 255) / 256), 256, 0, st>>>(n, d.omega, d.occ, d.wn32);
         chi_kernel<float2><<<counted((nc + 255) / 256), 256, 0, st>>>(p.nq, p.n_rep, d.qcart, d.rep_cart,
                                                              (float2 *)d.chi);
         eps_transpose_kernel<float2><<<counted(grid), 256, 0, st>>>(p.nq, p.nb, d.eig, (float2 *)d.eps_work);

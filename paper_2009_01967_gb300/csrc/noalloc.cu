@@ -21,8 +21,8 @@
 // before it returns.  All calls share the one array: calls that overlap on
 // the GPU (two streams, or two host threads) race on it.  Nothing in it needs
 // to start at zero: every q-point writes its own partial sums before they are
-// added.  Sizes: 96 B per q-point (coordinates and partial sums) plus 96 B per
-// fc2 block and 12 B per atom pair of the fc2 table.
+// added.  Sizes: 96 B per q-point (coordinates and partial sums) plus 104 B
+// per fc2 block, 12 B per atom pair of the fc2 table and 8 B per atom.
 
 #include <algorithm>
 #include <cmath>
@@ -112,7 +112,7 @@ extern "C" kald_status kald_kappa_rta_noalloc(kald_ctx *ctx, void *stream, const
     inv[2][2] = (L[0][0] * L[1][1] - L[0][1] * L[1][0]) / det;
 
     // carve the static scratch: fc2 tables, q-points, per-q partial sums
-    const size_t n_pairs = h.pair2_i.size(), n_blk = h.fc2_scaled.size() / 9;
+    const size_t n_pairs = h.pair2_i.size(), n_blk = h.fc2_blk.size() / 9;
     size_t off = 0;
     auto carve = [&](size_t bytes) { const size_t o = off; off += ws_round(bytes); return o; };
     const size_t o_pi = carve(sizeof(int) * std::max<size_t>(n_pairs, 1));
@@ -120,6 +120,8 @@ extern "C" kald_status kald_kappa_rta_noalloc(kald_ctx *ctx, void *stream, const
     const size_t o_ps = carve(sizeof(int) * (n_pairs + 1));
     const size_t o_blk = carve(sizeof(double) * 9 * std::max<size_t>(n_blk, 1));
     const size_t o_rc = carve(sizeof(double) * 3 * std::max<size_t>(n_blk, 1));
+    const size_t o_at = carve(sizeof(int) * 2 * std::max<size_t>(n_blk, 1));
+    const size_t o_m = carve(sizeof(double) * (size_t)h.n_atoms);
     const size_t o_q = carve(sizeof(double) * 3 * (size_t)nq);
     const size_t o_part = carve(sizeof(double) * 9 * (size_t)nq);
     if (off > kStaticScratchBytes)
@@ -153,8 +155,15 @@ extern "C" kald_status kald_kappa_rta_noalloc(kald_ctx *ctx, void *stream, const
     put(o_pi, h.pair2_i.data(), sizeof(int) * n_pairs);
     put(o_pj, h.pair2_j.data(), sizeof(int) * n_pairs);
     put(o_ps, h.pair2_start.data(), sizeof(int) * (n_pairs + 1));
-    put(o_blk, h.fc2_scaled.data(), sizeof(double) * 9 * n_blk);
+    put(o_blk, h.fc2_blk.data(), sizeof(double) * 9 * n_blk);
     put(o_rc, h.fc2_rcart.data(), sizeof(double) * 3 * n_blk);
+    put(o_at, h.fc2_atoms.data(), sizeof(int) * 2 * n_blk);
+    put(o_m, h.masses.data(), sizeof(double) * (size_t)h.n_atoms);
+    // Phi2 / sqrt(mi mj), in place
+    if (e == cudaSuccess)
+        e = launch_mass_scale((int)n_blk, 9, 2, reinterpret_cast<const double *>(b + o_blk),
+                              reinterpret_cast<const int *>(b + o_at), reinterpret_cast<const double *>(b + o_m), 9, 0,
+                              b + o_blk, st);
     put(o_q, qc.data(), sizeof(double) * 3 * (size_t)nq);
     if (e != cudaSuccess) {
         cudaGetLastError();

@@ -246,7 +246,41 @@ __global__ void velocity_kernel(DevFc2 f, int nb, const double *__restrict__ qca
     }
 }
 
+// Mass scaling of force-constant blocks (the 1/sqrt(m m') of the dynamical
+// matrix, section "Lattice Dynamics", and the 1/sqrt(m m' m'') of Eq.
+// projection_plus): out[b][e] = raw[b][e] / sqrt(prod of the masses of the
+// block's atoms), e < nval, and zero padding up to out_stride; FP64, or
+// rounded to FP32 when f32.  One thread per output value; out may alias raw
+// when the strides agree.
+__global__ void mass_scale_kernel(int n_blk, int nval, int n_at, const double *__restrict__ raw,
+                                  const int *__restrict__ atoms, const double *__restrict__ masses,
+                                  int out_stride, int f32, void *out) {
+    const size_t n = (size_t)n_blk * out_stride;
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < n;
+         x += (size_t)gridDim.x * blockDim.x) {
+        const size_t b = x / out_stride;
+        const int e = (int)(x - b * out_stride);
+        double v = 0.0;
+        if (e < nval) {
+            double m = masses[atoms[b * n_at]];
+            for (int a = 1; a < n_at; ++a) m *= masses[atoms[b * n_at + a]];
+            v = raw[b * nval + e] * (1.0 / sqrt(m));
+        }
+        if (f32) static_cast<float *>(out)[x] = (float)v;
+        else static_cast<double *>(out)[x] = v;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_mass_scale(int n_blk, int nval, int n_at, const double *raw, const int *atoms,
+                              const double *masses, int out_stride, int f32, void *out, cudaStream_t st) {
+    if (n_blk <= 0) return cudaSuccess;
+    const size_t n = (size_t)n_blk * out_stride;
+    const int grid = (int)std::min<size_t>((n + 255) / 256, 4096);
+    mass_scale_kernel<<<counted(grid), 256, 0, st>>>(n_blk, nval, n_at, raw, atoms, masses, out_stride, f32, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_dynmat(const DevFc2 &f, int nb, int nq, const double *qcart, double2 *D,
                           cudaStream_t st) {

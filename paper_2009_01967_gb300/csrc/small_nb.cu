@@ -13,7 +13,10 @@
 // q' of the chunk in order, the CTA adds the lanes of each mode in order and
 // writes one FP64 partial per (q, chunk, s) for lw_finish.
 
+#include <type_traits>
+
 #include "kald_internal.h"
+#include "wdiff.cuh"
 
 namespace kald {
 namespace {
@@ -113,6 +116,10 @@ sn_kernel(LwParams p, LwDev d, SnTables t, const R *__restrict__ fc3, const type
     const int jl = tid / NB, s = tid - (tid / NB) * NB;
     const bool act = jl < JPC;
     const R w = act ? (R)d.omega[(size_t)q * NB + s] : (R)0;
+    // FP32: omega and n as hi + lo pairs, so that w +- w' - w'' and n' - n''
+    // keep their accuracy when the terms nearly cancel (wdiff.cuh)
+    constexpr bool kPair = std::is_same<R, float>::value;
+    const F2 wsp = act ? f2_of(d.omega[(size_t)q * NB + s]) : F2{0.f, 0.f};
     const R sig2inv = (R)(0.5 / (p.sigma_w * p.sigma_w));
     const R cut = (R)p.cut_w;
     const int *kq = d.qfrac + 3 * q;
@@ -175,6 +182,13 @@ sn_kernel(LwParams p, LwDev d, SnTables t, const R *__restrict__ fc3, const type
             const R w1 = (R)d.omega[(size_t)qp * NB + sp];
             if (!(w1 > (R)0)) continue;
             const R n1 = (R)d.occ[(size_t)qp * NB + sp];
+            F2 n1p, sump, difp;
+            if constexpr (kPair) {
+                const float4 a = __ldg(d.wn32 + (size_t)qp * NB + sp);
+                n1p = F2{a.z, a.w};
+                sump = f2_add(wsp, F2{a.x, a.y});
+                difp = f2_add(wsp, F2{-a.x, -a.y});
+            }
             R2 T[NB];
 #pragma unroll
             for (int c = 0; c < NB; ++c) T[c].x = T[c].y = (R)0;
@@ -186,18 +200,31 @@ sn_kernel(LwParams p, LwDev d, SnTables t, const R *__restrict__ fc3, const type
             }
 #pragma unroll
             for (int spp = 0; spp < NB; ++spp) {
-                const R w2 = (R)d.omega[(size_t)qpp * NB + spp];
-                if (!(w2 > (R)0)) continue;
-                const R dp = w + w1 - w2, dm = w - w1 - w2;
+                R w2, dp, dm, n2, dn;
+                if constexpr (kPair) {
+                    const float4 b = __ldg(d.wn32 + (size_t)qpp * NB + spp);
+                    w2 = b.x;
+                    if (!(w2 > 0.0f)) continue;
+                    dp = f2_diff(sump, F2{b.x, b.y});
+                    dm = f2_diff(difp, F2{b.x, b.y});
+                    n2 = b.z;
+                    dn = f2_diff(n1p, F2{b.z, b.w});
+                } else {
+                    w2 = d.omega[(size_t)qpp * NB + spp];
+                    if (!(w2 > (R)0)) continue;
+                    dp = w + w1 - w2;
+                    dm = w - w1 - w2;
+                    n2 = d.occ[(size_t)qpp * NB + spp];
+                    dn = n1 - n2;
+                }
                 const bool hp = fabs(dp) < cut, hm = fabs(dm) < cut;
                 if (!(hp || hm)) continue;
-                const R n2 = (R)d.occ[(size_t)qpp * NB + spp];
                 R2 f;
                 f.x = f.y = (R)0;
 #pragma unroll
                 for (int c = 0; c < NB; ++c) cfma_conj(f, T[c], __ldg(e2 + c * NB + spp));
                 R g = (R)0;
-                if (hp) g += (n1 - n2) * exp(-dp * dp * sig2inv);
+                if (hp) g += dn * exp(-dp * dp * sig2inv);
                 if (hm) g += (R)0.5 * ((R)1 + n1 + n2) * exp(-dm * dm * sig2inv);
                 part += (f.x * f.x + f.y * f.y) * g / (w1 * w2);
                 ++allowed;

@@ -18,7 +18,8 @@
 //   B2[q''][n''][k''] n'' = s'': (Re eps'' | Im eps''),  n'' = H + s'': (-Im eps'' | Re eps'')
 //   GEMM2 row m2 = (s, s'), column n'' = Re / Im phi(s, s', s''); the epilogue adds
 //     |phi|^2 / (w' w'') [ (n' - n'') G(w + w' - w'') + 1/2 (1 + n' + n'') G(w - w' - w'') ]
-//   with the same FP32 window test and Gaussian as the CUDA-core kernel.
+//   with the same FP32 window test and Gaussian as the CUDA-core kernel, the
+//   energy and occupation differences formed from FP32 pairs (wdiff.cuh).
 // A1 and T1 are stored MN-major (rows contiguous), so the gather (one thread
 // per mode s) and the GEMM1 epilogue (32 consecutive s' per thread) write
 // whole runs; the B operands are K-major.  GEMM2's epilogue sums each mode's
@@ -36,6 +37,7 @@
 
 #include "kald_internal.h"
 #include "tc_common.cuh"
+#include "wdiff.cuh"
 
 namespace kald {
 namespace {
@@ -65,8 +67,7 @@ struct XParams {
     int n_pairs;
     const int *qfrac;         // [nq][3] integer mesh coordinates
     __nv_bfloat16 *t1h, *t1l; // GEMM1 output [pairs][Kp][Mp]
-    const float *omega;       // [nq][nb] rad/ps (0 = masked)
-    const float *occ;         // [nq][nb]
+    const float4 *wn;         // [nq][nb] FP32 pairs (w hi, w lo, n hi, n lo); w = 0 when masked
     float sig2inv, cut;
     int n_slices;             // q-slices of slots (a batch spans fewer q values)
     float *slots;             // GEMM2 output [n_slices][nq (q')][nb][2]: per-mode sums over the
@@ -124,7 +125,7 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
     __shared__ __align__(8) uint64_t bfull, afull[kStages], aempty[kStages], tfull[2], tempty[2], drain;
     __shared__ uint32_t tmem_base_sm;
     __shared__ int fail_sm;
-    __shared__ float w2_sm[128], n2_sm[128], iw2_sm[128];
+    __shared__ float w2_sm[128], w2l_sm[128], n2_sm[128], n2l_sm[128], iw2_sm[128];
     __shared__ float rowsum[2][2][kBM];          // [tile parity][column half][row]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -150,11 +151,13 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
     if (EPI == EPI_PHI) {
         // columns of q'': masked modes and padding get a frequency no window reaches
         for (int t = threadIdx.x; t < 128; t += blockDim.x) {
-            const float w2 = t < nb ? x.omega[(size_t)qpp * nb + t] : 0.0f;
-            const bool v = w2 > 0.0f;
-            w2_sm[t] = v ? w2 : 1e30f;
-            n2_sm[t] = v ? x.occ[(size_t)qpp * nb + t] : 0.0f;
-            iw2_sm[t] = v ? 1.0f / w2 : 0.0f;
+            const float4 c = t < nb ? x.wn[(size_t)qpp * nb + t] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const bool v = c.x > 0.0f;
+            w2_sm[t] = v ? c.x : 1e30f;
+            w2l_sm[t] = v ? c.y : 0.0f;
+            n2_sm[t] = v ? c.z : 0.0f;
+            n2l_sm[t] = v ? c.w : 0.0f;
+            iw2_sm[t] = v ? 1.0f / c.x : 0.0f;
         }
     }
     if (warp == 1) {
@@ -290,11 +293,15 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
                 }
             } else {
                 const int s = r_hi, sp = r_lo;
-                const float w = rv ? x.omega[(size_t)q * nb + s] : 0.0f;
-                const float w1 = rv ? x.omega[(size_t)qp * nb + sp] : 0.0f;
-                const float n1 = rv ? x.occ[(size_t)qp * nb + sp] : 0.0f;
-                const bool live = rv && w > 0.0f && w1 > 0.0f;
-                const float wp = w + w1, wm = w - w1;
+                const float4 a0 = rv ? x.wn[(size_t)q * nb + s] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 a1 = rv ? x.wn[(size_t)qp * nb + sp] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const bool live = rv && a0.x > 0.0f && a1.x > 0.0f;
+                const float w1 = a1.x;
+                // w + w' and w - w' as FP32 pairs; n' as a pair (wdiff.cuh)
+                const F2 wp = f2_add(F2{a0.x, a0.y}, F2{a1.x, a1.y});
+                const F2 wm = f2_add(F2{a0.x, a0.y}, F2{-a1.x, -a1.y});
+                const F2 n1 = F2{a1.z, a1.w};
+                const float hn1 = 0.5f * (1.0f + a1.z);
                 float acc = 0.0f;
                 for (int ci = hf; ok && ci < H / 16; ci += 2) {
                     const int c0 = ci * 16;
@@ -304,11 +311,12 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
                     if (!live) continue;
 #pragma unroll
                     for (int k = 0; k < 16; ++k) {
-                        const float w2 = w2_sm[c0 + k], n2 = n2_sm[c0 + k];
-                        const float dp = wp - w2, dm = wm - w2;
+                        const F2 w2{w2_sm[c0 + k], w2l_sm[c0 + k]};
+                        const F2 n2{n2_sm[c0 + k], n2l_sm[c0 + k]};
+                        const float dp = f2_diff(wp, w2), dm = f2_diff(wm, w2);
                         const bool hp = fabsf(dp) < cut, hm = fabsf(dm) < cut;
-                        const float gp = hp ? (n1 - n2) * __expf(-dp * dp * s2i) : 0.0f;
-                        const float gm = hm ? 0.5f * (1.0f + n1 + n2) * __expf(-dm * dm * s2i) : 0.0f;
+                        const float gp = hp ? f2_diff(n1, n2) * __expf(-dp * dp * s2i) : 0.0f;
+                        const float gm = hm ? fmaf(0.5f, n2.h, hn1) * __expf(-dm * dm * s2i) : 0.0f;
                         const float p2 = fmaf(re[k], re[k], im[k] * im[k]);
                         acc = fmaf(p2 * (gp + gm), iw2_sm[c0 + k], acc);
                         cnt += (hp || hm) ? 1ull : 0ull;
@@ -508,12 +516,6 @@ __global__ void embed_kernel(int nq, int nb, int H, const double2 *__restrict__ 
     }
 }
 
-__global__ void f32_tables_kernel(int n, const double *__restrict__ omega, const double *__restrict__ occ,
-                                  float *__restrict__ wf, float *__restrict__ nf) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) { wf[t] = (float)omega[t]; nf[t] = (float)occ[t]; }
-}
-
 // gacc[q][s] = sum over q' in order of both slots of (q, q', s), FP64, for
 // the completed q in [q0, q1).
 __global__ void slots_reduce_kernel(XParams x, int q0, int q1, double *__restrict__ gacc) {
@@ -710,13 +712,12 @@ size_t tcx_scratch_bytes(int nb, int nq, int batch) {
     const size_t Mp = (size_t)(nb * nb + kBM - 1) / kBM * kBM;
     const size_t eb = ws_round(sizeof(__nv_bfloat16) * (size_t)nq * BN * Kp);
     const size_t ab = ws_round(sizeof(__nv_bfloat16) * (size_t)batch * Kp * Mp);
-    return 6 * eb + 8 * ab + 2 * ws_round(sizeof(float) * (size_t)nq * nb) +
-           ws_round(sizeof(float) * 2 * (size_t)tcx_slices(nq, batch) * nq * nb) +
+    return 6 * eb + 8 * ab + ws_round(sizeof(float) * 2 * (size_t)tcx_slices(nq, batch) * nq * nb) +
            ws_round(sizeof(double) * (size_t)nq * nb);
 }
 
 // Crystal linewidth sums on tensor cores (nb <= 96).  Needs the FP32 prep
-// of launch_lw_prep (eps^T, chi, omega, occ) in d and the group tables g;
+// of launch_lw_prep (eps^T, chi, omega, occ and their FP32 pairs) in d and the group tables g;
 // writes the per-(q, s) sums into d.partial ([nq][1][nb], n_chunks = 1) for
 // launch_lw_finish, the delta-allowed count into d.allowed and bounded-wait
 // failures into err.
@@ -741,8 +742,6 @@ cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups 
     __nv_bfloat16 *pl[2][4];                       // per lane: A1 hi, A1 lo, T1 hi, T1 lo
     for (int l = 0; l < 2; ++l)
         for (int k = 0; k < 4; ++k) pl[l][k] = reinterpret_cast<__nv_bfloat16 *>(take(ab));
-    auto *wf = reinterpret_cast<float *>(take(sizeof(float) * (size_t)nq * nb));
-    auto *nf = reinterpret_cast<float *>(take(sizeof(float) * (size_t)nq * nb));
     const int n_slices = tcx_slices(nq, batch);
     auto *slots = reinterpret_cast<float *>(take(sizeof(float) * 2 * (size_t)n_slices * nq * nb));
     auto *gacc = reinterpret_cast<double *>(take(sizeof(double) * (size_t)nq * nb));
@@ -756,7 +755,6 @@ cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups 
     const int eg = (int)std::min<size_t>(((size_t)nq * BN * Kp + 255) / 256, 4096);
     embed_kernel<<<counted(eg), 256, 0, st>>>(nq, nb, H, d.eig, 0, b1h, three ? b1m : nullptr, b1l);
     embed_kernel<<<counted(eg), 256, 0, st>>>(nq, nb, H, d.eig, 1, b2h, three ? b2m : nullptr, b2l);
-    f32_tables_kernel<<<counted((nq * nb + 255) / 256), 256, 0, st>>>(nq * nb, d.omega, d.occ, wf, nf);
 
     XParams x;
     x.nb = nb; x.H = H; x.Kp = Kp; x.Mp = Mp;
@@ -764,7 +762,7 @@ cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups 
     x.pair0 = 0; x.n_pairs = 0;
     x.qfrac = d.qfrac;
     x.t1h = nullptr; x.t1l = nullptr;
-    x.omega = wf; x.occ = nf;
+    x.wn = d.wn32;
     x.sig2inv = (float)(0.5 / (p.sigma_w * p.sigma_w));
     x.cut = (float)p.cut_w;
     x.n_slices = n_slices;

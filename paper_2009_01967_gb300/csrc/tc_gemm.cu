@@ -32,6 +32,7 @@
 
 #include "kald_internal.h"
 #include "tc_common.cuh"
+#include "wdiff.cuh"
 
 namespace kald {
 namespace {
@@ -94,7 +95,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ 
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
     __shared__ uint32_t tmem_base_sm;
     __shared__ int fail_sm;
-    __shared__ float wn_sm[kBN], nn_sm[kBN];
+    __shared__ float wn_sm[kBN], wl_sm[kBN], nn_sm[kBN], nl_sm[kBN];
     __shared__ double red[4];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -202,15 +203,22 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ 
             }
         }
     } else {
-        // delta weights in FP32 (window test first; the FP64 unit is slow)
+        // delta weights in FP32 (window test first; the FP64 unit is slow),
+        // the energy and occupation differences from FP32 pairs (wdiff.cuh)
         for (int x = threadIdx.x; x < kBN; x += blockDim.x) {
             const int n = tn * kBN + x;
-            wn_sm[x] = n < N ? (float)eg.omega[n] : 0.0f;
-            nn_sm[x] = n < N ? (float)eg.occ[n] : 0.0f;
+            const F2 wv = n < N ? f2_of(eg.omega[n]) : F2{0.f, 0.f};
+            const F2 nv = n < N ? f2_of(eg.occ[n]) : F2{0.f, 0.f};
+            wn_sm[x] = wv.h; wl_sm[x] = wv.l;
+            nn_sm[x] = nv.h; nl_sm[x] = nv.l;
         }
         __syncthreads();
-        const float w = (float)eg.omega[eg.mu0 + bz], cut = (float)eg.cut, s2i = (float)eg.sig2inv;
-        const float w1 = m < M ? (float)eg.omega[m] : 0.0f, n1 = m < M ? (float)eg.occ[m] : 0.0f;
+        const float cut = (float)eg.cut, s2i = (float)eg.sig2inv;
+        const F2 wmu = f2_of(eg.omega[eg.mu0 + bz]);
+        const F2 w1p = m < M ? f2_of(eg.omega[m]) : F2{0.f, 0.f};
+        const F2 n1p = m < M ? f2_of(eg.occ[m]) : F2{0.f, 0.f};
+        const float w1 = w1p.h, n1 = n1p.h;
+        const F2 wsum = f2_add(wmu, w1p), wdif = f2_add(wmu, f2_neg(w1p));
         const bool upper = eg.symmetric && (tn > tm);
         float acc = 0.0f;
         unsigned long long cnt = 0;
@@ -221,16 +229,20 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ 
             if (!(w1 > 0.0f)) continue;
 #pragma unroll 4
             for (int x = 0; x < 32; ++x) {
-                const float w2 = wn_sm[c0 + x];
-                const float dp = w + w1 - w2, dm = w - w1 - w2, dp2 = w + w2 - w1;
+                const F2 w2p{wn_sm[c0 + x], wl_sm[c0 + x]};
+                const float w2 = w2p.h;
+                // w + w' - w'', w - w' - w'' and (symmetric half) w + w'' - w'
+                const float dp = f2_diff(wsum, w2p), dm = f2_diff(wdif, w2p), dp2 = f2_diff(wdif, f2_neg(w2p));
                 const bool hp = fabsf(dp) < cut, hm = fabsf(dm) < cut;
                 const bool hp2 = upper && fabsf(dp2) < cut;
                 if (!(w2 > 0.0f) || !(hp || hm || hp2)) continue;
-                const float n2 = nn_sm[c0 + x];
+                const F2 n2p{nn_sm[c0 + x], nl_sm[c0 + x]};
+                const float n2 = n2p.h;
+                const float dn = f2_diff(n1p, n2p);
                 float g = 0.0f;
-                if (hp) g += (n1 - n2) * expf(-dp * dp * s2i);
+                if (hp) g += dn * expf(-dp * dp * s2i);
                 if (hm) g += (upper ? 1.0f : 0.5f) * (1.0f + n1 + n2) * expf(-dm * dm * s2i);
-                if (hp2) g += (n2 - n1) * expf(-dp2 * dp2 * s2i);
+                if (hp2) g -= dn * expf(-dp2 * dp2 * s2i);
                 const float f = v[x];
                 acc += f * f * g / (w1 * w2);
                 cnt += (unsigned long long)(hp || hm) + (unsigned long long)(upper && (hp2 || hm));

@@ -1,0 +1,50 @@
+// Compensated FP32 arithmetic for the energy and occupation differences of
+// the delta epilogues (paper Eq. phase_space: w +- w' - w'' and n' - n'').
+//
+// A frequency or an occupation number is carried as an unevaluated pair
+// hi + lo of FP32 values (hi = fl(x), lo = fl(x - hi), x the FP64 value), so
+// that a difference of nearly equal quantities -- the energy mismatch inside
+// the delta window, or n' - n'' when w is small -- is formed from the pair
+// parts and keeps a relative error of a few FP32 ulps of the difference
+// itself, instead of an absolute error of an ulp of the largest frequency.
+// The sum w + w' of two pairs uses Knuth's two-sum (exact for the hi parts).
+#pragma once
+
+namespace kald {
+
+struct F2 {
+    float h, l;
+};
+
+__host__ __device__ __forceinline__ F2 f2_of(double x) {
+    F2 r;
+    r.h = (float)x;
+    r.l = (float)(x - (double)r.h);
+    return r;
+}
+
+// a + b as a pair: two-sum of the hi parts (exact), lo parts added to the error.
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+    const float s = __fadd_rn(a.h, b.h);
+    const float v = __fsub_rn(s, a.h);
+    const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, v)), __fsub_rn(b.h, v));
+    F2 r;
+    r.h = s;
+    r.l = e + (a.l + b.l);
+    return r;
+}
+
+__device__ __forceinline__ F2 f2_neg(F2 a) {
+    F2 r;
+    r.h = -a.h;
+    r.l = -a.l;
+    return r;
+}
+
+// (a - b) rounded to FP32: hi parts first (exact when a and b are within a
+// factor of two of each other), then the lo parts.
+__device__ __forceinline__ float f2_diff(F2 a, F2 b) {
+    return __fadd_rn(__fsub_rn(a.h, b.h), __fsub_rn(a.l, b.l));
+}
+
+}  // namespace kald
