@@ -112,6 +112,22 @@ const char *kald_last_error(const kald_ctx *ctx);
  * context's own stream) for every later call.  The caller keeps ownership. */
 kald_status kald_set_stream(kald_ctx *ctx, void *stream);
 
+/* Failure handling (no counterpart in the paper).  Every wait inside the
+ * tensor-core pipelines is bounded: a wait that runs out of polls makes the
+ * kernel stop its pipeline, let the copies and MMAs it already issued finish,
+ * free its tensor memory and return, and the call returns KALD_E_TIMEOUT with
+ * the context still usable.  kald_set_wait_limit sets the number of polls of
+ * those pipeline waits for later calls (0 restores the default, 2^22, which
+ * no healthy pipeline comes near); a small value lets a test make a wait run
+ * out without faulting or hanging the GPU. */
+kald_status kald_set_wait_limit(kald_ctx *ctx, uint32_t polls);
+
+/* Cap the context's device workspace at `bytes` (0: no cap).  A later call
+ * that would need more returns KALD_E_NOMEM without allocating; the cap also
+ * lets a caller bound the library's device memory.  No counterpart in the
+ * paper. */
+kald_status kald_set_workspace_limit(kald_ctx *ctx, uint64_t bytes);
+
 /* Number of CUDA kernels this library has launched in the process so far,
  * over all contexts (a diagnostic counter, read without synchronising; it
  * has no counterpart in the paper).  Never fails. */

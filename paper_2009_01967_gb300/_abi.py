@@ -25,7 +25,8 @@ PRECISION = {"fp64": 0, "fp32": 1, "bf16split": 2}
 
 EXPORTS = ["kald_ctx_create", "kald_ctx_destroy", "kald_last_error", "kald_set_stream",
            "kald_phonons", "kald_linewidths", "kald_kappa_rta", "kald_kappa_qhgk",
-           "kald_kappa_rta_noalloc", "kald_kernel_launches"]
+           "kald_kappa_rta_noalloc", "kald_kernel_launches", "kald_set_wait_limit",
+           "kald_set_workspace_limit"]
 
 
 class KaldError(RuntimeError):
@@ -81,6 +82,10 @@ def load_library(path: str = LIB_PATH):
     lib.kald_kappa_rta_noalloc.argtypes = [vp, vp, C.POINTER(kald_system), C.POINTER(i32), vp, vp, vp,
                                            C.POINTER(kald_options), vp]
     lib.kald_kappa_rta_noalloc.restype = st
+    lib.kald_set_wait_limit.argtypes = [vp, C.c_uint32]
+    lib.kald_set_wait_limit.restype = st
+    lib.kald_set_workspace_limit.argtypes = [vp, C.c_uint64]
+    lib.kald_set_workspace_limit.restype = st
     lib.kald_kernel_launches.argtypes = []
     lib.kald_kernel_launches.restype = C.c_uint64
     _lib = lib
@@ -124,6 +129,14 @@ class Context:
 
     def set_stream(self, stream_ptr: int | None):
         self.check(self.lib.kald_set_stream(self.handle, C.c_void_p(stream_ptr or 0)))
+
+    def set_wait_limit(self, polls: int):
+        """Polls of the tensor-core pipeline waits (0: the default)."""
+        self.check(self.lib.kald_set_wait_limit(self.handle, int(polls)))
+
+    def set_workspace_limit(self, n_bytes: int):
+        """Cap the device workspace (0: no cap); larger requests give KALD_E_NOMEM."""
+        self.check(self.lib.kald_set_workspace_limit(self.handle, int(n_bytes)))
 
     def close(self):
         if self.handle:

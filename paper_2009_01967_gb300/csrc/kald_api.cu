@@ -33,6 +33,10 @@ kald_status cuda_check(kald_ctx *ctx, cudaError_t e, const char *what) {
 
 kald_status ws_reserve(kald_ctx *ctx, size_t bytes) {
     ctx->ws_used = 0;
+    if (ctx->ws_limit && bytes > ctx->ws_limit)
+        return fail(ctx, KALD_E_NOMEM, "this call needs " + std::to_string(bytes) +
+                                           " bytes of workspace, more than the context's limit of " +
+                                           std::to_string(ctx->ws_limit));
     if (bytes <= ctx->ws_cap) return KALD_OK;
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_check(ctx, e, "workspace sync");
@@ -493,6 +497,18 @@ kald_status kald_set_stream(kald_ctx *ctx, void *stream) {
     return KALD_OK;
 }
 
+kald_status kald_set_wait_limit(kald_ctx *ctx, uint32_t polls) {
+    if (!ctx) return KALD_E_INVALID;
+    ctx->wait_limit = polls ? polls : kDefaultWaitPolls;
+    return KALD_OK;
+}
+
+kald_status kald_set_workspace_limit(kald_ctx *ctx, uint64_t bytes) {
+    if (!ctx) return KALD_E_INVALID;
+    ctx->ws_limit = (size_t)bytes;
+    return KALD_OK;
+}
+
 kald_status kald_phonons(kald_ctx *ctx, const kald_system *sys, const int32_t mesh[3],
                          double *nu_thz, double *eigvec, double *vel) {
     if (!ctx) return KALD_E_INVALID;
@@ -734,6 +750,7 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
             p.T = opt->temperature_K;
             p.classical = opt->classical ? 1 : 0;
             p.omega_min_w = kTwoPi * opt->omega_min_thz;
+            p.wait_limit = ctx->wait_limit;
             cudaMemsetAsync(gd.err, 0, sizeof(int), ctx->stream);
             cudaError_t e = launch_gamma_only(gp, gd, p, mode, opt->degen_tol_thz, g_d, ctx->stream);
             if (e != cudaSuccess) return cuda_check(ctx, e, "kald_linewidths (Gamma-only) launch");
@@ -781,6 +798,7 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
         p.T = opt->temperature_K;
         p.classical = opt->classical ? 1 : 0;
         p.omega_min_w = kTwoPi * opt->omega_min_thz;
+        p.wait_limit = ctx->wait_limit;
         // about 64 items per SM for balance, q' chunks as long as that allows
         {
             const long long want = 64LL * std::max(1, ctx->sm_count);

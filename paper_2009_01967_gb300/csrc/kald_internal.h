@@ -28,6 +28,7 @@ constexpr double kTwoPi = 2.0 * kPi;
 constexpr double kKappaSI = 1e4 * 1e-12 / 1e-30;
 
 constexpr int kMaxNbSmall = 96;    // largest nb of the per-q dense kernels
+constexpr uint32_t kDefaultWaitPolls = 1u << 22;   // polls of a bounded device wait
 constexpr int kMaxDegen = 96;      // largest degenerate set handled
 }  // namespace kald
 
@@ -45,6 +46,8 @@ struct kald_ctx {
     std::string err;
     int sm_count = 0;
     size_t smem_optin = 0;
+    uint32_t wait_limit = kald::kDefaultWaitPolls;   // polls of the pipeline waits
+    size_t ws_limit = 0;                           // workspace cap in bytes (0: none)
     // host plans of recently seen systems, keyed by a 128-bit hash of their
     // whole content (oldest first)
     struct Plan {
@@ -154,6 +157,7 @@ struct LwParams {
     double omega_min_w;       // 2 pi omega_min (rad/ps)
     int qp_chunk;             // q' per work item
     int n_chunks;             // ceil(nq / qp_chunk)
+    uint32_t wait_limit;      // polls of the tensor-core pipeline waits
 };
 // Y-build lane schedule (built on the host by plan_ybuild): in round r lane t
 // runs segments sched[r*kLwThreads+t] .. sched[r*kLwThreads+t+1]-1.  A segment is

@@ -1,15 +1,20 @@
 // tcgen05 / TMA / mbarrier building blocks shared by the tensor-core kernels
-// (inline PTX).  Every wait is bounded by kWaitLimit polls.
+// (inline PTX).  Every wait is bounded: the pipeline waits by a limit the
+// host passes in (kald_set_wait_limit, default kWaitLimit polls), the
+// wind-down waits (copies already issued, MMAs already committed) by
+// kWaitLimit, so nothing is in flight when a CTA exits after a failed wait.
 #pragma once
 
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include "kald_internal.h"
+
 namespace kald {
 namespace tc {
 
-constexpr uint32_t kWaitLimit = 1u << 22;          // polls of a bounded wait
+constexpr uint32_t kWaitLimit = kDefaultWaitPolls;   // polls of a bounded wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -30,9 +35,9 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: true when the phase completed, false when the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (uint32_t it = 0; it < kWaitLimit; ++it)
+// Bounded wait: true when the phase completed, false when `limit` polls ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit = kWaitLimit) {
+    for (uint32_t it = 0; it < limit; ++it)
         if (mbar_try(bar, parity)) return true;
     return false;
 }

@@ -73,6 +73,7 @@ struct XParams {
     float *slots;             // GEMM2 output [n_slices][nq (q')][nb][2]: per-mode sums over the
                               // mode's rows in its first tile (0) and in the next tile (1)
     unsigned long long *allowed;
+    uint32_t wait_limit;      // polls of the pipeline waits
 };
 
 __device__ __forceinline__ void pair_of(const XParams &x, int a, int &q, int &qp, int &qpp) {
@@ -183,7 +184,7 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
             for (int tile = t0; tile < t1; ++tile) {
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const int s = it % kStages;
-                    if (it >= kStages && !mbar_wait(&aempty[s], ((it / kStages) - 1) & 1)) fail_sm = 1;
+                    if (it >= kStages && !mbar_wait(&aempty[s], ((it / kStages) - 1) & 1, x.wait_limit)) fail_sm = 1;
                     if (*(volatile int *)&fail_sm) break;
                     unsigned char *st = sA + (size_t)s * C::kStageBytes;
                     mbar_expect_tx(&afull[s], C::kStageBytes);
@@ -198,17 +199,17 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            if (!mbar_wait(&bfull, 0)) fail_sm = 1;
+            if (!mbar_wait(&bfull, 0, x.wait_limit)) fail_sm = 1;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             int it = 0;
             for (int i = 0; i < n_tiles && !*(volatile int *)&fail_sm; ++i) {
                 const int buf = i & 1;
-                if (i >= 2 && !mbar_wait(&tempty[buf], ((i >> 1) - 1) & 1)) { fail_sm = 1; break; }
+                if (i >= 2 && !mbar_wait(&tempty[buf], ((i >> 1) - 1) & 1, x.wait_limit)) { fail_sm = 1; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t d = tmem + (uint32_t)(buf * (C::kTmemCols / 2));
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const int s = it % kStages;
-                    if (!mbar_wait(&afull[s], (it / kStages) & 1) || *(volatile int *)&fail_sm) {
+                    if (!mbar_wait(&afull[s], (it / kStages) & 1, x.wait_limit) || *(volatile int *)&fail_sm) {
                         fail_sm = 1;
                         break;
                     }
@@ -244,7 +245,7 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
         unsigned long long cnt = 0;
         for (int i = 0; i < n_tiles; ++i) {
             const int tile = t0 + i, buf = i & 1;
-            bool ok = !*(volatile int *)&fail_sm && mbar_wait(&tfull[buf], (i >> 1) & 1);
+            bool ok = !*(volatile int *)&fail_sm && mbar_wait(&tfull[buf], (i >> 1) & 1, x.wait_limit);
             ok = __all_sync(0xffffffffu, ok);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             if (!ok) fail_sm = 1;
@@ -768,6 +769,7 @@ cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups 
     x.n_slices = n_slices;
     x.slots = slots;
     x.allowed = d.allowed;
+    x.wait_limit = p.wait_limit;
     Lane lanes[2];
     for (int l = 0; l < 2; ++l) {
         Lane &L = lanes[l];

@@ -87,7 +87,7 @@ template <int EPI>
 __global__ void __launch_bounds__(128, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
                const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
-               int M, int N, int K, EpiSplit es, EpiGamma eg, int *err) {
+               int M, int N, int K, EpiSplit es, EpiGamma eg, int *err, uint32_t wait_limit) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte alignment for the swizzled tiles
     unsigned char *base = reinterpret_cast<unsigned char *>(
@@ -134,7 +134,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ 
         // ---- producer
         for (int kb = 0; kb < nkb; ++kb) {
             const int s = kb % kStages;
-            if (kb >= kStages && !mbar_wait(&empty[s], ((kb / kStages) - 1) & 1)) { fail_sm = 1; break; }
+            if (kb >= kStages && !mbar_wait(&empty[s], ((kb / kStages) - 1) & 1, wait_limit)) { fail_sm = 1; break; }
             unsigned char *st = base + (size_t)s * kStageBytes;
             mbar_expect_tx(&full[s], kStageBytes);
             tma_load_2d(st, &mAh, &full[s], kb * kBK, a_row);
@@ -147,7 +147,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ 
         // ---- MMA issuer
         for (int kb = 0; kb < nkb; ++kb) {
             const int s = kb % kStages;
-            if (!mbar_wait(&full[s], (kb / kStages) & 1) || *(volatile int *)&fail_sm) { fail_sm = 1; break; }
+            if (!mbar_wait(&full[s], (kb / kStages) & 1, wait_limit) || *(volatile int *)&fail_sm) { fail_sm = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             unsigned char *st = base + (size_t)s * kStageBytes;
             const uint64_t ah = smem_desc(st), al = smem_desc(st + kTileBytes);
@@ -166,7 +166,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ 
     }
     __syncwarp();
     // ---- epilogue: wait for the accumulator (bounded)
-    bool ok = mbar_wait(&done, 0);
+    bool ok = mbar_wait(&done, 0, wait_limit);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!ok || *(volatile int *)&fail_sm) {
         ok = false;
@@ -261,13 +261,15 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ 
     // ---- teardown: let in-flight TMA/MMA work finish before freeing TMEM
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (*(volatile int *)&fail_sm && threadIdx.x == 0) {
-        // drain: the latest load of each stage completes its transaction (bounded)
+    if ((*(volatile int *)&fail_sm || !ok) && threadIdx.x == 0) {
+        // drain: the latest load of each stage completes its transaction, and
+        // every MMA the issuer committed has finished (bounded, full limit)
         for (int s = 0; s < kStages; ++s) {
             int last = -1;
             for (int kb = s; kb < issued; kb += kStages) last = kb;
             if (last >= 0) mbar_wait(&full[s], (last / kStages) & 1);
         }
+        mbar_wait(&done, 0);
     }
     __syncthreads();
     if (warp == 1) {
@@ -430,11 +432,12 @@ cudaError_t launch_gamma_only_tc(const GammaPlan &gp, const GammaDev &d, const L
             gp.n_groups, d.group_jk, d.group_start, d.blk_i, d.fc3, d.eig, nb, mu0, ld, plane_elems, Yh, Yl);
         EpiSplit es{Th, Tl, ld, prow};
         EpiGamma eg{};
-        k1<<<counted(dim3(nt, nt, nm)), 128, kSmemBytes, st>>>(mEh, mEl, mYh, mYl, nb, nb, ld, es, eg, err);
+        k1<<<counted(dim3(nt, nt, nm)), 128, kSmemBytes, st>>>(mEh, mEl, mYh, mYl, nb, nb, ld, es, eg, err,
+                                                               p.wait_limit);
         EpiGamma eg2{d.omega, d.occ, mu0, prow, sig2inv, p.cut_w, partial_tc + t0, d.allowed,
                      tiles_dev + t0, symmetric};
         EpiSplit es0{nullptr, nullptr, 0, 0};
-        k2<<<counted(t1 - t0), 128, kSmemBytes, st>>>(mTh, mTl, mEh, mEl, nb, nb, ld, es0, eg2, err);
+        k2<<<counted(t1 - t0), 128, kSmemBytes, st>>>(mTh, mTl, mEh, mEl, nb, nb, ld, es0, eg2, err, p.wait_limit);
     }
     return cudaGetLastError();
 }
