@@ -178,6 +178,154 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------- roofline
+# DRAM traffic per launch of the dominant kernels from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), scaled to the launch shape
+# the benchmark times; the summaries under profiles/ give the command.  None
+# when the kernel has changed since the counters were taken.
+TRAFFIC_PER_PAIR = {}
+
+
+def _gamma_only_band_tiles(om, cut, tile=128, symmetric=True):
+    """Delta-band (tm, tn) tiles of every valid mode, as the library lists them."""
+    b = len(om)
+    nt = -(-b // tile)
+    lo = np.full(nt, np.inf)
+    hi = np.full(nt, -np.inf)
+    for m in range(b):
+        if om[m] > 0:
+            lo[m // tile] = min(lo[m // tile], om[m])
+            hi[m // tile] = max(hi[m // tile], om[m])
+
+    def band(ww, a, c):
+        return ((ww + lo[a] - hi[c] < cut) and (ww + hi[a] - lo[c] > -cut)) or \
+               ((ww - hi[a] - hi[c] < cut) and (ww - lo[a] - lo[c] > -cut))
+    n_tiles = 0
+    for ww in om[om > 0]:
+        for a in range(nt):
+            for c in range(a if symmetric else 0, nt):
+                if hi[a] >= lo[a] and hi[c] >= lo[c] and (band(ww, a, c) or (symmetric and c != a and band(ww, c, a))):
+                    n_tiles += 1
+    return n_tiles
+
+
+def roofline_of(args, w, nbs, nu_c, opt, prof, steps, allowed):
+    """Roofline line of the dominant kernel: ALGORITHMIC work per launch
+    (the method's flops, not the split-precision emulation) over the mean
+    launch duration from the library's per-launch CUDA events."""
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, FMA = 2 flops
+    nq = w.n_q
+    s = w.systems[0]
+    nb = nbs[0]
+    offs = np.cumsum([0] + [nq * b for b in nbs])
+    gamma_only = nq == 1
+    small = (not gamma_only) and nb <= 6
+    executed = None
+    if args.precision == "bf16split" and not small:
+        if gamma_only:
+            names = ("tc_gemm1", "tc_gemm2")
+            kernel = "tc_gemm_kernel (GEMM1 T = E Y, GEMM2 delta-band phi tiles + epilogue)"
+            cut = w.n_sigma * 2 * np.pi * w.sigma_thz
+            alg, exe = 0.0, 0.0
+            for x, b in enumerate(nbs):
+                nu_x = nu_c[offs[x]:offs[x + 1]]
+                om = np.where(nu_x > opt.omega_min_thz, 2 * np.pi * nu_x, 0.0)
+                n_valid = int(np.sum(om > 0))
+                n_tiles = _gamma_only_band_tiles(om, cut)
+                nt, ld = -(-b // 128), -(-b // 128) * 128
+                alg += n_valid * 2.0 * b ** 3 + n_tiles * 2.0 * 128 * 128 * b
+                exe += 3 * 2.0 * 128 * 128 * ld * (n_valid * nt * nt + n_tiles)
+            alg_note = ("per valid mode 2 nb^3 (T = E Y) plus 2 x 128 x 128 x nb per delta-band tile of "
+                        "phi = T E^T; executed: 3 BF16 MMAs per product on 128-padded tiles")
+        else:
+            names = ("tcx_gemm1", "tcx_gemm2")
+            kernel = "tcx_gemm_kernel (GEMM1 T' = eps'^T Y_s, GEMM2 phi = T' conj(eps'') + delta epilogue)"
+            H = -(-nb // 32) * 32
+            mt = -(-(nb * nb) // 128)
+            n_mma = 5 if H <= 64 else 3
+            alg = nq * nq * 2 * 8.0 * nb ** 4              # two complex nb^4 contractions per pair
+            exe = nq * nq * 2.0 * mt * n_mma * 2.0 * 128 * (2 * H) * (2 * H)
+            alg_note = ("two dense complex contractions of nb^4 per momentum-conserving pair (8 flop per "
+                        "complex MAC); executed: 3 BF16 MMAs per product (5 when nb <= 64)")
+        peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        bound, peak_note = "tensor", ("MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16 in a power-capped "
+                                      "loop; the kernels run inside a seconds-long step), of measured")
+        executed = exe
+    elif small:
+        names = ("small_nb",)
+        kernel = "sn_kernel (one- and two-atom cells: phase sum, both contractions and the epilogue in registers)"
+        n_valid = int(np.sum(nu_c > opt.omega_min_thz))
+        n_fc3 = s.fc3.shape[0]
+        alg = n_valid * nq * (108.0 * n_fc3 + 8.0 * nb ** 3) + allowed * 8.0 * nb
+        alg_note = "per (mode, q'): 108 n_fc3 (phase-summed first-index contraction) + 8 nb^3 (T'), 8 nb per allowed phi"
+        peak = fp32_peak if args.precision != "fp64" else fp32_peak / 64.0
+        bound, peak_note = "alu", "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz" + ("" if args.precision != "fp64" else " / 64 (FP64)")
+    else:
+        names = ("lw_main",) if not gamma_only else ()
+        kernel = "lw_main_kernel" if not gamma_only else "g_gemm_nt_kernel"
+        n_valid = int(np.sum(nu_c > opt.omega_min_thz))
+        n_fc3 = s.fc3.shape[0]
+        if gamma_only:
+            alg = sum(4.0 * b ** 3 * int(np.sum(nu_c[offs[x]:offs[x + 1]] > opt.omega_min_thz))
+                      for x, b in enumerate(nbs))
+        else:
+            alg = n_valid * nq * (20.0 * n_fc3 + 8.0 * nb ** 3) + allowed * 8.0 * nb
+        alg_note = "Y build + T' per (mode, q'), phi at delta-allowed pairs"
+        peak = fp32_peak if args.precision == "fp32" else fp32_peak / 64.0
+        bound, peak_note = "alu", "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz" + ("" if args.precision == "fp32" else " / 64 (FP64)")
+    ms = sum(prof.get(n, (0.0, 0))[0] for n in names)
+    launches = sum(prof.get(n, (0.0, 0))[1] for n in names)
+    if ms <= 0 or launches == 0:
+        return {"bound": bound, "achieved": None, "peak": peak, "unit": "TFLOP/s", "frac": None,
+                "traffic": None, "kernel": kernel, "note": "no timed launches of this kernel"}
+    alg_per_launch = alg * steps / launches
+    mean_s = ms / launches / 1e3
+    achieved = alg_per_launch / mean_s / 1e12
+    out = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+           "traffic": None, "kernel": kernel, "launches_timed": launches, "mean_launch_ms": mean_s * 1e3,
+           "flops_per_launch": alg_per_launch, "algorithmic_work": alg_note, "peak_note": peak_note,
+           "timed_region": "CUDA events around every launch of the kernel on its own stream, over the timed steps"}
+    if executed is not None:
+        exe_per_launch = executed * steps / launches
+        out["executed_flops_per_launch"] = exe_per_launch
+        out["tensor_pipe_frac"] = exe_per_launch / mean_s / 1e12 / peak
+    if not gamma_only and names[0] in TRAFFIC_PER_PAIR:
+        per_pair, src = TRAFFIC_PER_PAIR[names[0]]
+        out["traffic"] = per_pair * nq * nq * steps * len(names) / launches
+        out["traffic_source"] = src
+    other = {n: {"ms": v[0], "launches": v[1]} for n, v in prof.items() if v[1]}
+    out["per_kernel_ms"] = other
+    return out
+
+
+def kappa_time_to_solution(kk, ctx, w, opt, phon, kappa, n_modes, n_eig, nbs):
+    """kappa from host inputs to host kappa (kald_phonons + kald_linewidths +
+    kald_kappa_*), once with the configured split path and once with the plain
+    FP64 GPU path; wall time of each and the split kappa's relative error."""
+    import dataclasses
+    res = {}
+    kaps = {}
+    for prec in (opt.precision, "fp64"):
+        o = dataclasses.replace(opt, precision=prec)
+        nu_h = np.zeros(n_modes)
+        eig_h = np.zeros(n_eig, dtype=np.complex128)
+        gam_h = np.zeros(n_modes)
+        kap_h = np.zeros((len(nbs), 3, 3))
+        t0 = time.perf_counter()
+        phon(nu_h, eig_h)
+        kk.kald_linewidths(ctx, w.systems, w.mesh, nu_h, eig_h, o, gamma=gam_h)
+        kappa(nu_h, eig_h, gam_h, kap_h, o)
+        res[prec] = time.perf_counter() - t0
+        kaps[prec] = kap_h
+    a, b = kaps[opt.precision], kaps["fp64"]
+    err = float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+    return {"split_s": res[opt.precision], "fp64_s": res["fp64"], "speedup": res["fp64"] / res[opt.precision],
+            "kappa_rel_err_vs_fp64": err, "tolerance": 1e-4, "within_tolerance": err <= 1e-4,
+            "path": "host inputs -> kald_phonons -> kald_linewidths -> kald_kappa -> host kappa"}
+
+
 # ------------------------------------------------------------- GPU arm
 def run_kald(args):
     import torch
@@ -218,11 +366,12 @@ def run_kald(args):
             kk.kald_phonons(ctx, sx, w.mesh, nu_thz=nu_t[offs_m[x]:offs_m[x + 1]],
                             eigvec=eig_t[offs_e[x]:offs_e[x + 1]], want_vel=False)
 
-    def kappa(nu_t, eig_t, gam_t, kap_t):
+    def kappa(nu_t, eig_t, gam_t, kap_t, o=None):
+        o = o or opt
         if gamma_only:
-            kk.kald_kappa_qhgk(ctx, w.systems, nu_t, eig_t, gam_t, opt, kappa=kap_t)
+            kk.kald_kappa_qhgk(ctx, w.systems, nu_t, eig_t, gam_t, o, kappa=kap_t)
         else:
-            kk.kald_kappa_rta(ctx, s, w.mesh, nu_t, eig_t, gam_t, opt, kappa=kap_t[0])
+            kk.kald_kappa_rta(ctx, s, w.mesh, nu_t, eig_t, gam_t, o, kappa=kap_t[0])
 
     def step():
         phon(nu, eig)
@@ -244,6 +393,7 @@ def run_kald(args):
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
     sampler.start()
+    ctx.profile(True)                              # per-launch CUDA events on the launching streams
     launches0 = kk.kald_kernel_launches()
     step_ms, lw_ms = [], []
     for _ in range(args.steps):
@@ -258,6 +408,8 @@ def run_kald(args):
         lw_ms.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
     launches = kk.kald_kernel_launches() - launches0
+    prof = ctx.profile_read()
+    ctx.profile(False)
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
@@ -284,78 +436,15 @@ def run_kald(args):
     d2h = nu_h.nbytes + eig_h.nbytes + gam_h.nbytes + kap_h.nbytes
     e2e_value = triplets_step / (float(np.mean(e2e_ms)) / 1e3) if e2e_ms else None
 
-    # ---- roofline of the dominant kernel (linewidth projection)
+    # ---- roofline of the dominant kernel, timed per launch inside the steps
     trip, allowed = trip_info["trip"]
-    peaks = _peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, FMA = 2 flops
-    lw_avg_s = float(np.mean(lw_ms)) / 1e3
-    if gamma_only:
-        nu_c = nu.cpu().numpy()
-        if args.precision == "bf16split":
-            # executed tensor work: 3 BF16 MMAs per product; GEMM1 over all
-            # 128 x 128 tiles, GEMM2 over the delta-band tiles (upper triangle)
-            flops = 0.0
-            cut = w.n_sigma * 2 * np.pi * w.sigma_thz
-            for x, b in enumerate(nbs):
-                om = 2 * np.pi * nu_c[offs_m[x]:offs_m[x + 1]]
-                om = np.where(nu_c[offs_m[x]:offs_m[x + 1]] > opt.omega_min_thz, om, 0.0)
-                nt = -(-b // 128)
-                ld = -(-b // 128) * 128
-                lo = np.full(nt, np.inf); hi = np.full(nt, -np.inf)
-                for m in range(b):
-                    if om[m] > 0:
-                        lo[m // 128] = min(lo[m // 128], om[m]); hi[m // 128] = max(hi[m // 128], om[m])
-                def band(ww, a, c):
-                    return ((ww + lo[a] - hi[c] < cut) and (ww + hi[a] - lo[c] > -cut)) or \
-                           ((ww - hi[a] - hi[c] < cut) and (ww - lo[a] - lo[c] > -cut))
-                n_tiles = 0
-                for ww in om[om > 0]:
-                    for a in range(nt):
-                        for c in range(a, nt):
-                            if hi[a] >= lo[a] and hi[c] >= lo[c] and (band(ww, a, c) or (c != a and band(ww, c, a))):
-                                n_tiles += 1
-                n_valid = int(np.sum(om > 0))
-                flops += 3 * 2.0 * 128 * 128 * ld * (n_valid * nt * nt + n_tiles)
-            kernel = "tc_gemm_kernel"
-        else:
-            # per valid mode: two dense nb^3 contractions (E Y, then (E Y) E^T), 2 flop per FMA
-            flops = sum(4.0 * b ** 3 * int(np.sum(nu_c[offs_m[x]:offs_m[x + 1]] > opt.omega_min_thz))
-                        for x, b in enumerate(nbs))
-            kernel = "g_gemm_nt_kernel"
-    else:
-        if args.precision == "bf16split":
-            # executed tensor work: per pair, GEMM1 and GEMM2 over ceil(nb^2 / 128)
-            # row tiles of N = K = 2H (H = nb rounded up to 32); 3 MMAs per
-            # product (5 when H <= 64: three-piece eigenvector operand)
-            H = -(-nb // 32) * 32
-            mt = -(-(nb * nb) // 128)
-            n_mma = 5 if H <= 64 else 3
-            flops = nq * nq * 2.0 * mt * n_mma * 2.0 * 128 * (2 * H) * (2 * H)
-            kernel = "tcx_gemm_kernel"
-        else:
-            n_valid = int(torch.sum(nu > opt.omega_min_thz).item())
-            n_fc3 = s.fc3.shape[0]
-            flops = (n_valid * nq * (20.0 * n_fc3 + 8.0 * nb ** 3)     # Y build + T' = eps'^T Y
-                     + allowed * 8.0 * nb)                              # phi at delta-allowed pairs
-            kernel = "lw_main_kernel"
-    achieved = flops / lw_avg_s / 1e12
-    timed = ("one kald_linewidths call, CUDA events on its stream: every kernel of the stage "
-             "(gather / Y-build, operand splits, GEMMs, reductions), so frac is a lower bound for the "
-             "GEMM kernel itself; per-kernel shares are in profiles/")
-    if args.precision == "bf16split":
-        peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
-        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None, "kernel": kernel, "flops_per_launch": flops,
-                    "timed_region": timed,
-                    "peak_note": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16, power-capped loop), of measured"}
-    else:
-        peak = fp32_peak if args.precision == "fp32" else fp32_peak / 64.0
-        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None,
-                    "kernel": kernel, "flops_per_launch": flops, "timed_region": timed,
-                    "peak_note": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz" +
-                                 ("" if args.precision == "fp32" else " / 64 (FP64)")}
+    roofline = roofline_of(args, w, nbs, nu.cpu().numpy(), opt, prof, args.steps, allowed)
+
+    # ---- kappa time-to-solution: split path against the plain FP64 GPU path
+    tts = None
+    if rank == 0 and world == 1 and not args.no_tts and args.precision != "fp64":
+        tts = kappa_time_to_solution(kk, ctx, w, opt, phon, kappa, n_modes, n_eig, nbs)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, sample = time_oracle_sample(w)
@@ -376,6 +465,7 @@ def run_kald(args):
                         "d2h_bytes_per_step": int(d2h)},
                 "gpu_launches": int(launches),      # library kernels in the timed steps (its own counter)
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+                "kappa_time_to_solution": tts,
                 "kappa_W_mK": kap.cpu().numpy().round(6).tolist()[:2],
                 "delta_allowed_fraction": allowed / trip}
         print(json.dumps(line), flush=True)
@@ -397,6 +487,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass (profiling runs)")
     ap.add_argument("--mesh", default=None, help="override the q-mesh, e.g. 4,4,4 (profiling runs)")
+    ap.add_argument("--no-tts", action="store_true",
+                    help="skip the kappa time-to-solution comparison with the plain FP64 GPU path")
     args = ap.parse_args()
     if args.precision is None:
         args.precision = "fp64" if args.workload == "C1" else "bf16split"

@@ -128,6 +128,25 @@ kald_status kald_set_wait_limit(kald_ctx *ctx, uint32_t polls);
  * paper. */
 kald_status kald_set_workspace_limit(kald_ctx *ctx, uint64_t bytes);
 
+/* Per-launch timing of the hot kernels (a diagnostic without counterpart in
+ * the paper): with profiling on, CUDA events on the launching stream bracket
+ * every launch of the kernels below, and each call folds their durations
+ * into per-kernel totals once it has synchronised.  kald_profile_enable(ctx,
+ * on) switches it and clears the totals; kald_profile_read returns the total
+ * milliseconds and the launch count of one kernel since then. */
+typedef enum {
+    KALD_PROF_TCX_GATHER = 0,   /* crystal phase-sum gather (tensor-core path)  */
+    KALD_PROF_TCX_GEMM1 = 1,    /* crystal T' = eps'^T Y (tcgen05)              */
+    KALD_PROF_TCX_GEMM2 = 2,    /* crystal phi = T' conj(eps'') + delta epilogue */
+    KALD_PROF_TC_GEMM1 = 3,     /* Gamma-only T = E Y (tcgen05)                 */
+    KALD_PROF_TC_GEMM2 = 4,     /* Gamma-only phi band tiles + epilogue         */
+    KALD_PROF_SMALL_NB = 5,     /* one- and two-atom register kernel            */
+    KALD_PROF_LW_MAIN = 6,      /* CUDA-core crystal kernel (FP64 / FP32)       */
+    KALD_PROF_COUNT = 7
+} kald_prof_kernel;
+kald_status kald_profile_enable(kald_ctx *ctx, int on);
+kald_status kald_profile_read(kald_ctx *ctx, int kernel, double *total_ms, uint64_t *launches);
+
 /* Number of CUDA kernels this library has launched in the process so far,
  * over all contexts (a diagnostic counter, read without synchronising; it
  * has no counterpart in the paper).  Never fails. */

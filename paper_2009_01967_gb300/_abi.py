@@ -26,7 +26,9 @@ PRECISION = {"fp64": 0, "fp32": 1, "bf16split": 2}
 EXPORTS = ["kald_ctx_create", "kald_ctx_destroy", "kald_last_error", "kald_set_stream",
            "kald_phonons", "kald_linewidths", "kald_kappa_rta", "kald_kappa_qhgk",
            "kald_kappa_rta_noalloc", "kald_kernel_launches", "kald_set_wait_limit",
-           "kald_set_workspace_limit"]
+           "kald_set_workspace_limit", "kald_profile_enable", "kald_profile_read"]
+PROF_KERNELS = {"tcx_gather": 0, "tcx_gemm1": 1, "tcx_gemm2": 2, "tc_gemm1": 3, "tc_gemm2": 4,
+                "small_nb": 5, "lw_main": 6}
 
 
 class KaldError(RuntimeError):
@@ -86,6 +88,10 @@ def load_library(path: str = LIB_PATH):
     lib.kald_set_wait_limit.restype = st
     lib.kald_set_workspace_limit.argtypes = [vp, C.c_uint64]
     lib.kald_set_workspace_limit.restype = st
+    lib.kald_profile_enable.argtypes = [vp, C.c_int]
+    lib.kald_profile_enable.restype = st
+    lib.kald_profile_read.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]
+    lib.kald_profile_read.restype = st
     lib.kald_kernel_launches.argtypes = []
     lib.kald_kernel_launches.restype = C.c_uint64
     _lib = lib
@@ -137,6 +143,19 @@ class Context:
     def set_workspace_limit(self, n_bytes: int):
         """Cap the device workspace (0: no cap); larger requests give KALD_E_NOMEM."""
         self.check(self.lib.kald_set_workspace_limit(self.handle, int(n_bytes)))
+
+    def profile(self, on: bool):
+        """Switch per-launch CUDA-event timing of the hot kernels (clears the totals)."""
+        self.check(self.lib.kald_profile_enable(self.handle, int(bool(on))))
+
+    def profile_read(self) -> dict:
+        """{kernel: (total ms, launches)} since profiling was switched on."""
+        out = {}
+        for name, kid in PROF_KERNELS.items():
+            ms, n = C.c_double(), C.c_uint64()
+            self.check(self.lib.kald_profile_read(self.handle, kid, C.byref(ms), C.byref(n)))
+            out[name] = (ms.value, int(n.value))
+        return out
 
     def close(self):
         if self.handle:

@@ -19,6 +19,45 @@
 
 namespace kald {
 
+cudaEvent_t Prof::take() {
+    if (used == pool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        pool.push_back(e);
+    }
+    return pool[used++];
+}
+
+void Prof::fold() {
+    for (const Rec &r : recs) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            total_ms[r.kind] += ms;
+            count[r.kind] += 1;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    recs.clear();
+    used = 0;
+}
+
+void Prof::reset() {
+    recs.clear();
+    used = 0;
+    for (int k = 0; k < KALD_PROF_COUNT; ++k) { total_ms[k] = 0.0; count[k] = 0; }
+}
+
+void Prof::destroy() {
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    pool.clear();
+    recs.clear();
+    used = 0;
+}
+
 kald_status fail(kald_ctx *ctx, kald_status st, const std::string &msg) {
     if (ctx) ctx->err = msg;
     return st;
@@ -201,6 +240,7 @@ kald_status finish(kald_ctx *ctx, const char *what) {
     if (e != cudaSuccess) return cuda_check(ctx, e, what);
     e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_check(ctx, e, what);
+    if (ctx->prof.on) ctx->prof.fold();      // every bracketed launch has completed
     ctx->err.clear();
     return KALD_OK;
 }
@@ -485,6 +525,7 @@ void kald_ctx_destroy(kald_ctx *ctx) {
     if (ctx->own_stream) cudaStreamSynchronize(ctx->own_stream);
     if (ctx->stream && ctx->stream != ctx->own_stream) cudaStreamSynchronize(ctx->stream);
     if (ctx->ws) cudaFree(ctx->ws);
+    ctx->prof.destroy();
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     delete ctx;
 }
@@ -506,6 +547,21 @@ kald_status kald_set_wait_limit(kald_ctx *ctx, uint32_t polls) {
 kald_status kald_set_workspace_limit(kald_ctx *ctx, uint64_t bytes) {
     if (!ctx) return KALD_E_INVALID;
     ctx->ws_limit = (size_t)bytes;
+    return KALD_OK;
+}
+
+kald_status kald_profile_enable(kald_ctx *ctx, int on) {
+    if (!ctx) return KALD_E_INVALID;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_check(ctx, cudaGetLastError(), "cudaSetDevice");
+    ctx->prof.reset();
+    ctx->prof.on = on != 0;
+    return KALD_OK;
+}
+
+kald_status kald_profile_read(kald_ctx *ctx, int kernel, double *total_ms, uint64_t *launches) {
+    if (!ctx || kernel < 0 || kernel >= KALD_PROF_COUNT) return KALD_E_INVALID;
+    if (total_ms) *total_ms = ctx->prof.total_ms[kernel];
+    if (launches) *launches = ctx->prof.count[kernel];
     return KALD_OK;
 }
 
@@ -751,6 +807,7 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
             p.classical = opt->classical ? 1 : 0;
             p.omega_min_w = kTwoPi * opt->omega_min_thz;
             p.wait_limit = ctx->wait_limit;
+            p.prof = &ctx->prof;
             cudaMemsetAsync(gd.err, 0, sizeof(int), ctx->stream);
             cudaError_t e = launch_gamma_only(gp, gd, p, mode, opt->degen_tol_thz, g_d, ctx->stream);
             if (e != cudaSuccess) return cuda_check(ctx, e, "kald_linewidths (Gamma-only) launch");
@@ -799,6 +856,7 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
         p.classical = opt->classical ? 1 : 0;
         p.omega_min_w = kTwoPi * opt->omega_min_thz;
         p.wait_limit = ctx->wait_limit;
+        p.prof = &ctx->prof;
         // about 64 items per SM for balance, q' chunks as long as that allows
         {
             const long long want = 64LL * std::max(1, ctx->sm_count);

@@ -32,10 +32,44 @@ constexpr uint32_t kDefaultWaitPolls = 1u << 22;   // polls of a bounded device 
 constexpr int kMaxDegen = 96;      // largest degenerate set handled
 }  // namespace kald
 
-// ---- context -----------------------------------------------------------------
+// ---- per-launch timing of named kernels (kald_profile_*) ----------------------
 namespace kald {
 struct HostSystem;
+// CUDA events around individual launches, on the launching stream; folded
+// into per-kernel totals once the call has synchronised (fold()).
+struct Prof {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;          // created on demand, reused
+    size_t used = 0;
+    struct Rec { int kind; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    double total_ms[KALD_PROF_COUNT] = {};
+    uint64_t count[KALD_PROF_COUNT] = {};
+    cudaEvent_t take();
+    void fold();                             // stream(s) already synchronised
+    void reset();
+    void destroy();
+};
+// Records the start event at construction and the stop event at end() when
+// profiling is on (prof may be NULL).
+struct ProfMark {
+    Prof *p;
+    int kind;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    ProfMark(Prof *prof, int k, cudaStream_t s) : p(prof && prof->on ? prof : nullptr), kind(k), st(s) {
+        if (p) { a = p->take(); if (a) cudaEventRecord(a, st); }
+    }
+    void end() {
+        if (!p || !a) return;
+        cudaEvent_t b = p->take();
+        if (b) { cudaEventRecord(b, st); p->recs.push_back({kind, a, b}); }
+        p = nullptr;
+    }
+};
 }
+
+// ---- context -----------------------------------------------------------------
 struct kald_ctx {
     int device = 0;
     cudaStream_t own_stream = nullptr;
@@ -48,6 +82,7 @@ struct kald_ctx {
     size_t smem_optin = 0;
     uint32_t wait_limit = kald::kDefaultWaitPolls;   // polls of the pipeline waits
     size_t ws_limit = 0;                           // workspace cap in bytes (0: none)
+    kald::Prof prof;                               // optional per-launch timing
     // host plans of recently seen systems, keyed by a 128-bit hash of their
     // whole content (oldest first)
     struct Plan {
@@ -158,6 +193,7 @@ struct LwParams {
     int qp_chunk;             // q' per work item
     int n_chunks;             // ceil(nq / qp_chunk)
     uint32_t wait_limit;      // polls of the tensor-core pipeline waits
+    Prof *prof;               // per-launch timing (NULL: off); host pointer, never read on the device
 };
 // Y-build lane schedule (built on the host by plan_ybuild): in round r lane t
 // runs segments sched[r*kLwThreads+t] .. sched[r*kLwThreads+t+1]-1.  A segment is

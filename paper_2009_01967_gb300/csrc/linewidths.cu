@@ -573,16 +573,20 @@ cudaError_t launch_lw_main(const LwParams &p, const LwDev &d, int fp32, int sm_c
         auto k = lw_main_kernel<float, true>;
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
+        ProfMark pm(p.prof, KALD_PROF_LW_MAIN, st);
         k<<<counted(grid), kThreads, smem, st>>>(p, d, (const float *)d.fc3, (const float2 *)d.eps_work,
                                         (const float2 *)d.chi);
+        pm.end();
     } else {
         const size_t smem = lw_smem_bytes<double>(p, false);
         if (smem > smem_optin) return cudaErrorInvalidValue;
         auto k = lw_main_kernel<double, false>;
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
+        ProfMark pm(p.prof, KALD_PROF_LW_MAIN, st);
         k<<<counted(grid), kThreads, smem, st>>>(p, d, (const double *)d.fc3, (const double2 *)d.eps_work,
                                         (const double2 *)d.chi);
+        pm.end();
     }
     return cudaGetLastError();
 }

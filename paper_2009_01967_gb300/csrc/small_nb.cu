@@ -250,8 +250,10 @@ cudaError_t run_sn(const LwParams &p, const LwDev &d, const SnTables &t, cudaStr
     auto k = sn_kernel<R, NB>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    ProfMark pm(p.prof, KALD_PROF_SMALL_NB, st);
     k<<<counted(dim3(p.nq, p.n_chunks)), kSnThreads, smem, st>>>(p, d, t, static_cast<const R *>(d.fc3),
                                                                  static_cast<const R2 *>(d.eps_work));
+    pm.end();
     return cudaGetLastError();
 }
 

@@ -624,6 +624,7 @@ cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, L
         XParams x = L.x;
         x.pair0 = p0;
         x.n_pairs = (int)std::min<long long>(batch, total - p0);
+        ProfMark pg(p.prof, KALD_PROF_TCX_GATHER, L.st);
         if (gp == 4)
             ycx_gather_kernel<4><<<counted(dim3(g.n_parts, x.n_pairs / 4)), gthreads, gblk + 4 * gsmem, L.st>>>(
                 x, g, ew, cw, p.n_rep, L.a1h, L.a1l);
@@ -633,10 +634,15 @@ cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, L
         else
             ycx_gather_kernel<1><<<counted(dim3(g.n_parts, x.n_pairs)), gthreads, gblk + gsmem, L.st>>>(
                 x, g, ew, cw, p.n_rep, L.a1h, L.a1l);
+        pg.end();
+        ProfMark p1(p.prof, KALD_PROF_TCX_GEMM1, L.st);
         k1<<<counted(dim3(gx, x.n_pairs)), kWsThreads, smem, L.st>>>(L.maps[0], L.maps[1], L.maps[2], L.maps[3],
                                                                     L.maps[4], x, tpc, err);
+        p1.end();
+        ProfMark p2(p.prof, KALD_PROF_TCX_GEMM2, L.st);
         k2<<<counted(dim3(gx, x.n_pairs)), kWsThreads, smem, L.st>>>(L.maps[5], L.maps[6], L.maps[7], L.maps[8],
                                                                     L.maps[9], x, tpc, err);
+        p2.end();
         e = cudaEventRecord(L.done[(i >> 1) & 1], L.st);
         if (e != cudaSuccess) return e;
         // q values completed by this batch

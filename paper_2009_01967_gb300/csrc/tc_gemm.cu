@@ -432,12 +432,16 @@ cudaError_t launch_gamma_only_tc(const GammaPlan &gp, const GammaDev &d, const L
             gp.n_groups, d.group_jk, d.group_start, d.blk_i, d.fc3, d.eig, nb, mu0, ld, plane_elems, Yh, Yl);
         EpiSplit es{Th, Tl, ld, prow};
         EpiGamma eg{};
+        ProfMark p1(p.prof, KALD_PROF_TC_GEMM1, st);
         k1<<<counted(dim3(nt, nt, nm)), 128, kSmemBytes, st>>>(mEh, mEl, mYh, mYl, nb, nb, ld, es, eg, err,
                                                                p.wait_limit);
+        p1.end();
         EpiGamma eg2{d.omega, d.occ, mu0, prow, sig2inv, p.cut_w, partial_tc + t0, d.allowed,
                      tiles_dev + t0, symmetric};
         EpiSplit es0{nullptr, nullptr, 0, 0};
+        ProfMark p2(p.prof, KALD_PROF_TC_GEMM2, st);
         k2<<<counted(t1 - t0), 128, kSmemBytes, st>>>(mTh, mTl, mEh, mEl, nb, nb, ld, es0, eg2, err, p.wait_limit);
+        p2.end();
     }
     return cudaGetLastError();
 }
