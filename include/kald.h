@@ -196,6 +196,21 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
                             const int32_t mesh[3], const double *nu_thz, const double *eigvec,
                             const kald_options *opt, double *gamma, uint64_t *n_triplets);
 
+/* kald_linewidths restricted to the q-points [q_begin, q_end) of one crystal
+ * (flat mesh index as in kald_phonons).  Every q' (and so every q'' = q + q')
+ * still runs over the whole mesh, so nu_thz and eigvec are the full-mesh
+ * arrays, while
+ *   gamma       [(q_end - q_begin)][nb] out: the linewidths of those q only
+ *   n_triplets  [2] out or NULL: the triplets (q_end - q_begin) Nq nb^3 and
+ *               the delta-allowed ones among them.
+ * The sums of a q-point do not depend on the range it is computed in, so the
+ * ranges of any partition of [0, Nq) concatenate to kald_linewidths' gamma bit
+ * for bit: the unit of a multi-GPU split (contiguous q ranges, one all-gather
+ * of gamma).  KALD_E_INVALID unless 0 <= q_begin < q_end <= Nq. */
+kald_status kald_linewidths_qrange(kald_ctx *ctx, const kald_system *sys, const int32_t mesh[3],
+                                   const double *nu_thz, const double *eigvec, const kald_options *opt,
+                                   int32_t q_begin, int32_t q_end, double *gamma, uint64_t *n_triplets);
+
 /* BTE-RTA conductivity (Eq. RTA, Eq. heat_capacity):
  *   kappa_ab = 1/(N_k V) sum_mu c_mu tau_mu v_a v_b,  tau = 1/(2 gamma),
  * with, inside each degenerate set D at one q, v_a v_b replaced by the

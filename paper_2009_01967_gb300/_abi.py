@@ -26,7 +26,8 @@ PRECISION = {"fp64": 0, "fp32": 1, "bf16split": 2}
 EXPORTS = ["kald_ctx_create", "kald_ctx_destroy", "kald_last_error", "kald_set_stream",
            "kald_phonons", "kald_linewidths", "kald_kappa_rta", "kald_kappa_qhgk",
            "kald_kappa_rta_noalloc", "kald_kernel_launches", "kald_set_wait_limit",
-           "kald_set_workspace_limit", "kald_profile_enable", "kald_profile_read"]
+           "kald_set_workspace_limit", "kald_profile_enable", "kald_profile_read",
+           "kald_linewidths_qrange"]
 PROF_KERNELS = {"tcx_gather": 0, "tcx_gemm1": 1, "tcx_gemm2": 2, "tc_gemm1": 3, "tc_gemm2": 4,
                 "small_nb": 5, "lw_main": 6}
 
@@ -75,6 +76,9 @@ def load_library(path: str = LIB_PATH):
     lib.kald_linewidths.argtypes = [vp, i32, C.POINTER(kald_system), C.POINTER(i32), vp, vp,
                                     C.POINTER(kald_options), vp, C.POINTER(C.c_uint64)]
     lib.kald_linewidths.restype = st
+    lib.kald_linewidths_qrange.argtypes = [vp, C.POINTER(kald_system), C.POINTER(i32), vp, vp,
+                                           C.POINTER(kald_options), i32, i32, vp, C.POINTER(C.c_uint64)]
+    lib.kald_linewidths_qrange.restype = st
     lib.kald_kappa_rta.argtypes = [vp, C.POINTER(kald_system), C.POINTER(i32), vp, vp, vp,
                                    C.POINTER(kald_options), vp]
     lib.kald_kappa_rta.restype = st
@@ -270,6 +274,31 @@ def kald_linewidths(ctx: Context, systems, mesh, nu_thz, eigvec, options: Option
                                       _ptr(nu_thz, np.float64, n_modes, "nu_thz"),
                                       _ptr(eigvec, np.complex128, n_eig, "eigvec"),
                                       C.byref(opt), _ptr(gamma, np.float64, n_modes, "gamma"), trip))
+    del keep
+    return gamma, (int(trip[0]), int(trip[1]))
+
+
+def kald_linewidths_qrange(ctx: Context, system, mesh, nu_thz, eigvec, options: Options, q_begin: int,
+                           q_end: int, gamma=None):
+    """Linewidths of the q-points [q_begin, q_end) of one crystal (full-mesh nu
+    and eigvec in); returns (gamma [(q_end - q_begin) * nb], (n_triplets, n_allowed))."""
+    cs, keep = c_system(system)
+    m, nq = _mesh(mesh)
+    nb = 3 * cs.n_atoms
+    n_out = (int(q_end) - int(q_begin)) * nb
+    if gamma is None:
+        if isinstance(nu_thz, np.ndarray):
+            gamma = np.zeros(max(n_out, 0))
+        else:
+            import torch
+            gamma = torch.zeros(max(n_out, 0), dtype=torch.float64, device=nu_thz.device)
+    trip = (C.c_uint64 * 2)()
+    opt = options.c()
+    ctx.check(ctx.lib.kald_linewidths_qrange(ctx.handle, C.byref(cs), m,
+                                             _ptr(nu_thz, np.float64, nq * nb, "nu_thz"),
+                                             _ptr(eigvec, np.complex128, nq * nb * nb, "eigvec"),
+                                             C.byref(opt), int(q_begin), int(q_end),
+                                             _ptr(gamma, np.float64, max(n_out, 0), "gamma"), trip))
     del keep
     return gamma, (int(trip[0]), int(trip[1]))
 

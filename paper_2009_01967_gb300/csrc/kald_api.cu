@@ -707,9 +707,12 @@ static kald_status check_options(kald_ctx *ctx, const kald_options *o) {
     return KALD_OK;
 }
 
-kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys,
-                            const int32_t mesh[3], const double *nu_thz, const double *eigvec,
-                            const kald_options *opt, double *gamma, uint64_t *n_triplets) {
+// Linewidths of every system (q_end < 0), or of the q-points [q_begin, q_end)
+// of one crystal.
+static kald_status linewidths_impl(kald_ctx *ctx, int32_t n_sys, const kald_system *sys,
+                                   const int32_t mesh[3], const double *nu_thz, const double *eigvec,
+                                   const kald_options *opt, int32_t q_begin, int32_t q_end, double *gamma,
+                                   uint64_t *n_triplets) {
     if (!ctx) return KALD_E_INVALID;
     kald_status st = set_device(ctx);
     if (st) return st;
@@ -720,6 +723,9 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
     if (n_sys > 1 && nq_mesh != 1)
         return fail(ctx, KALD_E_INVALID, "several systems need mesh {1,1,1} (Gamma-only batch)");
     if (!nu_thz || !eigvec || !gamma) return fail(ctx, KALD_E_INVALID, "nu/eigvec/gamma NULL");
+    const bool ranged = q_end >= 0;
+    if (ranged && (n_sys != 1 || q_begin < 0 || q_end > nq_mesh || q_begin >= q_end))
+        return fail(ctx, KALD_E_INVALID, "q range must satisfy 0 <= q_begin < q_end <= N_k (one system)");
     const bool d_nu = is_device_ptr(nu_thz), d_eig = is_device_ptr(eigvec), d_g = is_device_ptr(gamma);
     const int fp32 = opt->precision == KALD_FP32;
     uint64_t tot = 0, allowed_tot = 0;
@@ -732,6 +738,7 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
         if (nb > kMaxNbSmall && nq_mesh != 1)
             return fail(ctx, KALD_E_UNSUPPORTED, "kald_linewidths: nb > 96 needs mesh {1,1,1}");
         if (nb > kMaxNbSmall) {
+            // (a q range of a Gamma-only system is the whole system: [0, 1))
             // ---- Gamma-only path, mode by mode
             const size_t nn = (size_t)nb * nb;
             GammaPlan gp;
@@ -828,6 +835,8 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
         std::vector<int> qf;
         mesh_points(h.lattice, mesh, qc, qf);
         const int nq = nq_mesh;
+        const int q0 = ranged ? q_begin : 0, q1 = ranged ? q_end : nq;
+        const int nqr = q1 - q0;                 // q-points whose linewidths this call computes
         // One- and two-atom cells: the register kernel of small_nb.cu in every
         // precision (FP32 arithmetic unless FP64 is asked for), with the Bloch
         // phases from a table of L-th roots of unity (L = lcm of the mesh).
@@ -857,10 +866,12 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
         p.omega_min_w = kTwoPi * opt->omega_min_thz;
         p.wait_limit = ctx->wait_limit;
         p.prof = &ctx->prof;
+        p.q0 = q0;
+        p.q1 = q1;
         // about 64 items per SM for balance, q' chunks as long as that allows
         {
             const long long want = 64LL * std::max(1, ctx->sm_count);
-            int nch = (int)std::max(1LL, std::min<long long>(nq, (want + nq - 1) / nq));
+            int nch = (int)std::max(1LL, std::min<long long>(nq, (want + nqr - 1) / nqr));
             p.qp_chunk = (nq + nch - 1) / nch;
             p.n_chunks = (nq + p.qp_chunk - 1) / p.qp_chunk;
             if (tcx) { p.qp_chunk = nq; p.n_chunks = 1; }
@@ -910,10 +921,10 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
                       bytes_of(h.rep_cart) + bytes_of(qc) + bytes_of(qf) +
                       2 * ws_round(sizeof(double) * nq * nb) + ws_round(c2 * nn) +
                       ws_round(c2 * (size_t)nq * h.n_rep) +
-                      ws_round(sizeof(double) * (size_t)nq * p.n_chunks * nb) + 2 * ws_round(16);
+                      ws_round(sizeof(double) * (size_t)nqr * p.n_chunks * nb) + 2 * ws_round(16);
         if (!d_nu) need += ws_round(sizeof(double) * nq * nb);
         if (!d_eig) need += ws_round(sizeof(double2) * nn);
-        if (!d_g) need += ws_round(sizeof(double) * nq * nb);
+        if (!d_g) need += ws_round(sizeof(double) * nqr * nb);
         if (f32w) need += ws_round(sizeof(float4) * (size_t)nq * nb);
         if (tcx)
             need += ws_round(tcx_scratch_bytes(nb, nq, tcx_b)) + ws_round(16) + bytes_of(tc_gjk) +
@@ -939,10 +950,10 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
         d.wn32 = f32w ? static_cast<float4 *>(ws_take(ctx, sizeof(float4) * (size_t)nq * nb)) : nullptr;
         d.eps_work = ws_take(ctx, c2 * nn);
         d.chi = ws_take(ctx, c2 * (size_t)nq * h.n_rep);
-        d.partial = static_cast<double *>(ws_take(ctx, sizeof(double) * (size_t)nq * p.n_chunks * nb));
+        d.partial = static_cast<double *>(ws_take(ctx, sizeof(double) * (size_t)nqr * p.n_chunks * nb));
         d.allowed = static_cast<unsigned long long *>(ws_take(ctx, 16));
         d.queue = static_cast<int *>(ws_take(ctx, 16));
-        double *g_d = d_g ? gamma + off_nb : static_cast<double *>(ws_take(ctx, sizeof(double) * nq * nb));
+        double *g_d = d_g ? gamma + off_nb : static_cast<double *>(ws_take(ctx, sizeof(double) * nqr * nb));
         void *tc_scr = tcx ? ws_take(ctx, tcx_scratch_bytes(nb, nq, tcx_b)) : nullptr;
         int *tc_err = tcx ? static_cast<int *>(ws_take(ctx, 16)) : nullptr;
         TcxGroups tg;
@@ -985,16 +996,28 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
         int errf = 0;
         cudaMemcpyAsync(&al, d.allowed, sizeof(al), cudaMemcpyDeviceToHost, s);
         if (tcx) cudaMemcpyAsync(&errf, tc_err, sizeof(int), cudaMemcpyDeviceToHost, s);
-        if (!d_g) cudaMemcpyAsync(gamma + off_nb, g_d, sizeof(double) * nq * nb, cudaMemcpyDeviceToHost, s);
+        if (!d_g) cudaMemcpyAsync(gamma + off_nb, g_d, sizeof(double) * nqr * nb, cudaMemcpyDeviceToHost, s);
         if ((st = finish(ctx, "kald_linewidths"))) return st;
         if (errf) return fail(ctx, KALD_E_TIMEOUT, "kald_linewidths: a tensor-core pipeline wait expired");
-        tot += (uint64_t)nq * nq * (uint64_t)nb * nb * nb;
+        tot += (uint64_t)nqr * nq * (uint64_t)nb * nb * nb;
         allowed_tot += al;
         off_nb += (size_t)nq * nb;
         off_eig += nn;
     }
     if (n_triplets) { n_triplets[0] = tot; n_triplets[1] = allowed_tot; }
     return KALD_OK;
+}
+
+kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys,
+                            const int32_t mesh[3], const double *nu_thz, const double *eigvec,
+                            const kald_options *opt, double *gamma, uint64_t *n_triplets) {
+    return linewidths_impl(ctx, n_sys, sys, mesh, nu_thz, eigvec, opt, 0, -1, gamma, n_triplets);
+}
+
+kald_status kald_linewidths_qrange(kald_ctx *ctx, const kald_system *sys, const int32_t mesh[3],
+                                   const double *nu_thz, const double *eigvec, const kald_options *opt,
+                                   int32_t q_begin, int32_t q_end, double *gamma, uint64_t *n_triplets) {
+    return linewidths_impl(ctx, 1, sys, mesh, nu_thz, eigvec, opt, q_begin, q_end, gamma, n_triplets);
 }
 
 kald_status kald_kappa_rta(kald_ctx *ctx, const kald_system *sys, const int32_t mesh[3],

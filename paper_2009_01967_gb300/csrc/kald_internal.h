@@ -192,6 +192,7 @@ struct LwParams {
     double omega_min_w;       // 2 pi omega_min (rad/ps)
     int qp_chunk;             // q' per work item
     int n_chunks;             // ceil(nq / qp_chunk)
+    int q0, q1;               // q-points whose linewidths are computed: [q0, q1)
     uint32_t wait_limit;      // polls of the tensor-core pipeline waits
     Prof *prof;               // per-launch timing (NULL: off); host pointer, never read on the device
 };
@@ -220,7 +221,7 @@ struct LwDev {
                               // (FP32 and BF16-split paths; see wdiff.cuh)
     void *eps_work;           // [nq][nb][nb] eps^T in the working precision
     void *chi;                // [nq][n_rep] exp(-i q.R) in the working precision
-    double *partial;          // [nq][n_chunks][nb] FP64 partial sums
+    double *partial;          // [q1 - q0][n_chunks][nb] FP64 partial sums
     unsigned long long *allowed;   // [1] delta-allowed triplet count
     int *queue;               // [1] work counter
 };

@@ -184,7 +184,7 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const R sig2inv = (R)(0.5 / (p.sigma_w * p.sigma_w));
     const R cut = (R)p.cut_w;
-    const int n_items = p.nq * p.n_chunks;
+    const int n_items = (p.q1 - p.q0) * p.n_chunks;
     unsigned long long allowed = 0;
 
     for (;;) {
@@ -193,7 +193,7 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
         const int item = item_sm;
         __syncthreads();
         if (item >= n_items) break;
-        const int q = item / p.n_chunks;
+        const int q = p.q0 + item / p.n_chunks;
         const int chunk = item % p.n_chunks;
         for (int x = tid; x < nb; x += kThreads) red[x] = 0.0;
 
@@ -472,7 +472,7 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
         }
         __syncthreads();
         for (int s = tid; s < nb; s += kThreads)
-            d.partial[((size_t)q * p.n_chunks + chunk) * nb + s] = red[s];
+            d.partial[((size_t)(q - p.q0) * p.n_chunks + chunk) * nb + s] = red[s];
         __syncthreads();
     }
     // delta-allowed triplet count
@@ -481,15 +481,16 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
 }
 
 // gamma = pref / w * sum over chunks; then average over degenerate sets.
-__global__ void lw_finish_kernel(int nq, int nb, int n_chunks, const double *__restrict__ partial,
+// q-points q0 .. q1-1; partial and gamma are indexed from q0.
+__global__ void lw_finish_kernel(int q0, int q1, int nb, int n_chunks, const double *__restrict__ partial,
                                  const double *__restrict__ omega, const double *__restrict__ nu,
                                  double pref, double degen_tol, double *__restrict__ gamma) {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nq) return;
-    double *g = gamma + (size_t)q * nb;
+    const int q = q0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= q1) return;
+    double *g = gamma + (size_t)(q - q0) * nb;
     for (int s = 0; s < nb; ++s) {
         double t = 0.0;
-        for (int c = 0; c < n_chunks; ++c) t += partial[((size_t)q * n_chunks + c) * nb + s];
+        for (int c = 0; c < n_chunks; ++c) t += partial[((size_t)(q - q0) * n_chunks + c) * nb + s];
         const double w = omega[(size_t)q * nb + s];
         g[s] = (w > 0.0) ? pref * t / w : 0.0;
     }
@@ -565,7 +566,7 @@ cudaError_t launch_lw_main(const LwParams &p, const LwDev &d, int fp32, int sm_c
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(d.allowed, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    const int n_items = p.nq * p.n_chunks;
+    const int n_items = (p.q1 - p.q0) * p.n_chunks;
     const int grid = std::max(1, std::min(n_items, sm_count));
     if (fp32) {
         const size_t smem = lw_smem_bytes<float>(p, true);
@@ -595,8 +596,8 @@ cudaError_t launch_lw_finish(const LwParams &p, const LwDev &d, double degen_tol
                              double *gamma_out, cudaStream_t st) {
     const double pref = kHbarEvPs * kPi / 8.0 * kEvA2AmuPs2 * kEvA2AmuPs2 * kEvA2AmuPs2 /
                         (double)p.nq / (sqrt(kTwoPi) * p.sigma_w);
-    lw_finish_kernel<<<counted((p.nq + 63) / 64), 64, 0, st>>>(p.nq, p.nb, p.n_chunks, d.partial, d.omega,
-                                                     d.nu, pref, degen_tol_thz, gamma_out);
+    lw_finish_kernel<<<counted((p.q1 - p.q0 + 63) / 64), 64, 0, st>>>(p.q0, p.q1, p.nb, p.n_chunks, d.partial,
+                                                                   d.omega, d.nu, pref, degen_tol_thz, gamma_out);
     return cudaGetLastError();
 }
 

@@ -601,7 +601,7 @@ cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, L
     if (e != cudaSuccess) return e;
     const int mt = lanes[0].x.Mp / kBM;
     const int gx = (mt + tpc - 1) / tpc;
-    const long long total = (long long)p.nq * p.nq;
+    const long long pbeg = (long long)p.q0 * p.nq, pend = (long long)p.q1 * p.nq;   // pairs of q in [q0, q1)
     // pairs per gather CTA: 2 when that divides nq and the batch, so that the
     // CTA's pairs share q (every batch starts at a multiple of the batch);
     // 2 keeps the registers at ~80 per thread (4 needs ~130)
@@ -614,7 +614,7 @@ cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, L
     }
     const float2 *ew = static_cast<const float2 *>(d.eps_work), *cw = static_cast<const float2 *>(d.chi);
     long long i = 0;
-    for (long long p0 = 0; p0 < total; p0 += batch, ++i) {
+    for (long long p0 = pbeg; p0 < pend; p0 += batch, ++i) {
         Lane &L = lanes[i & 1];
         const Lane &O = lanes[(i & 1) ^ 1];
         if (i >= 3) {
@@ -623,7 +623,7 @@ cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, L
         }
         XParams x = L.x;
         x.pair0 = p0;
-        x.n_pairs = (int)std::min<long long>(batch, total - p0);
+        x.n_pairs = (int)std::min<long long>(batch, pend - p0);
         ProfMark pg(p.prof, KALD_PROF_TCX_GATHER, L.st);
         if (gp == 4)
             ycx_gather_kernel<4><<<counted(dim3(g.n_parts, x.n_pairs / 4)), gthreads, gblk + 4 * gsmem, L.st>>>(
@@ -824,7 +824,8 @@ cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups 
     for (int k = 0; k < 5; ++k)
         if (ev[k]) cudaEventDestroy(ev[k]);
     if (e != cudaSuccess) return e;
-    return cudaMemcpyAsync(d.partial, gacc, sizeof(double) * (size_t)nq * nb, cudaMemcpyDeviceToDevice, st);
+    return cudaMemcpyAsync(d.partial, gacc + (size_t)p.q0 * nb, sizeof(double) * (size_t)(p.q1 - p.q0) * nb,
+                           cudaMemcpyDeviceToDevice, st);
 }
 
 }  // namespace kald

@@ -686,3 +686,38 @@ def test_c2_kappa_split_vs_fp64_gpu_full_mesh(k):
     print(f"C2 8^3: linewidths + kappa fp64 {secs['fp64']:.2f} s, split {secs['bf16split']:.2f} s, "
           f"kappa rel err {err:.3e}, kappa_xx {b[0][0]:.6e}")
     assert err < 1e-4
+
+
+# ---------------------------------------------------------------- q ranges (the multi-GPU unit of work)
+@pytest.mark.parametrize("case,precision", [("binary3", "fp32"), ("binary3", "fp64"),
+                                            ("fcc4_mesh3", "fp64"), ("fcc4_mesh3", "bf16split"),
+                                            ("fcc32_mesh2", "bf16split")])
+def test_qrange_calls_concatenate_to_the_full_call(k, case, precision):
+    """kald_linewidths_qrange over a partition of the mesh into uneven
+    contiguous ranges, run back to back on the one GPU, gives the full call's
+    gamma and triplet counts bit for bit (register, CUDA-core and tensor-core
+    crystal paths)."""
+    kk, ctx = k
+    if case == "fcc4_mesh3":
+        w = ki.Workload("fcc4", [ki.fcc_supercell_system(1, seed=7)], (3, 3, 3), 300.0, 0.1, 3.0)
+    elif case == "fcc32_mesh2":
+        w = ki.Workload("fcc32", [ki.fcc_supercell_system(2, seed=2)], (2, 2, 2), 300.0, 0.1, 3.0)
+    else:
+        w = _lw_case(case)
+    s = w.systems[0]
+    nu_o, eig_o = ph.phonons(s, w.mesh)
+    opt = _opts(kk, w, precision)
+    g, (tot, allowed) = kk.kald_linewidths(ctx, s, w.mesh, nu_o, eig_o, opt)
+    nq = w.n_q
+    cuts = sorted({0, nq, max(1, nq // 5), max(1, (2 * nq) // 3)})
+    parts, t_sum, a_sum = [], 0, 0
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        gp, (t, al) = kk.kald_linewidths_qrange(ctx, s, w.mesh, nu_o, eig_o, opt, a, b)
+        parts.append(gp)
+        t_sum += t
+        a_sum += al
+    np.testing.assert_array_equal(np.concatenate(parts), np.ravel(g))
+    assert t_sum == tot and a_sum == allowed
+    with pytest.raises(kk.KaldError) as e:
+        kk.kald_linewidths_qrange(ctx, s, w.mesh, nu_o, eig_o, opt, 2, 2)
+    assert e.value.status == 1
