@@ -110,10 +110,10 @@ def dist_env():
 
 
 def job_throughput(local_ms: float, world: int, units_per_step: float, steps: int, device=None):
-    """Whole-job rate of N replicas (weak scaling, no data-path collective):
-    the slowest rank's time (max over ranks) for `steps` steps, and
-    world * units_per_step * steps / that time.  The max is one all-reduce on
-    `device` (a CUDA device under NCCL, the CPU under gloo)."""
+    """Whole-job rate: the slowest rank's time (max over ranks, one all-reduce
+    on `device`: a CUDA device under NCCL, the CPU under gloo) for `steps`
+    steps, and units_per_step * steps / that time, where units_per_step counts
+    the units ALL ranks process in one step."""
     total_ms = float(local_ms)
     if world > 1:
         import torch
@@ -121,7 +121,37 @@ def job_throughput(local_ms: float, world: int, units_per_step: float, steps: in
         t = torch.tensor([total_ms], dtype=torch.float64, device=device)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    return total_ms, world * units_per_step * steps / (total_ms / 1e3)
+    return total_ms, units_per_step * steps / (total_ms / 1e3)
+
+
+def shard_plan(nq: int, n_sys: int, world: int, rank: int) -> dict:
+    """How rank `rank` of `world` takes its share of one workload (strong
+    scaling: the workload is fixed).  A crystal: a contiguous range of q-points
+    (ceil(nq / world) each, the last ones shorter), every q' over the whole
+    mesh, then one all-gather of gamma (gather_q_sharded).  Several Gamma-only
+    systems: every world-th system, no collective (independent problems).  One
+    Gamma-only system: a replica (its modes are not split)."""
+    if world == 1:
+        return {"kind": "whole"}
+    if nq > 1:
+        per = -(-nq // world)
+        q0 = min(nq, rank * per)
+        return {"kind": "qrange", "q0": q0, "q1": min(nq, q0 + per), "per": per}
+    if n_sys >= world:
+        return {"kind": "systems", "idx": list(range(rank, n_sys, world))}
+    return {"kind": "replica"}
+
+
+def gather_q_sharded(local, per: int, nb: int, nq: int, world: int):
+    """All-gather of the q-sharded gamma: `local` holds this rank's
+    (q1 - q0) * nb values; every rank gets the full [nq * nb] vector."""
+    import torch
+    import torch.distributed as dist
+    buf = torch.zeros(per * nb, dtype=local.dtype, device=local.device)
+    buf[:local.numel()] = local
+    out = torch.empty(world * per * nb, dtype=local.dtype, device=local.device)
+    dist.all_gather_into_tensor(out, buf)
+    return out[:nq * nb]
 
 
 # ------------------------------------------------------------- oracle timing
@@ -209,10 +239,11 @@ def _gamma_only_band_tiles(om, cut, tile=128, symmetric=True):
     return n_tiles
 
 
-def roofline_of(args, w, nbs, nu_c, opt, prof, steps, allowed):
+def roofline_of(args, w, nbs, nu_c, opt, prof, steps, allowed, share=1.0):
     """Roofline line of the dominant kernel: ALGORITHMIC work per launch
     (the method's flops, not the split-precision emulation) over the mean
-    launch duration from the library's per-launch CUDA events."""
+    launch duration from the library's per-launch CUDA events.  `share` is
+    the fraction of the workload's q-points this rank computes."""
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, FMA = 2 flops
@@ -280,6 +311,9 @@ def roofline_of(args, w, nbs, nu_c, opt, prof, steps, allowed):
     if ms <= 0 or launches == 0:
         return {"bound": bound, "achieved": None, "peak": peak, "unit": "TFLOP/s", "frac": None,
                 "traffic": None, "kernel": kernel, "note": "no timed launches of this kernel"}
+    alg *= share
+    if executed is not None:
+        executed *= share
     alg_per_launch = alg * steps / launches
     mean_s = ms / launches / 1e3
     achieved = alg_per_launch / mean_s / 1e12
@@ -293,7 +327,7 @@ def roofline_of(args, w, nbs, nu_c, opt, prof, steps, allowed):
         out["tensor_pipe_frac"] = exe_per_launch / mean_s / 1e12 / peak
     if not gamma_only and names[0] in TRAFFIC_PER_PAIR:
         per_pair, src = TRAFFIC_PER_PAIR[names[0]]
-        out["traffic"] = per_pair * nq * nq * steps * len(names) / launches
+        out["traffic"] = per_pair * share * nq * nq * steps * len(names) / launches
         out["traffic_source"] = src
     other = {n: {"ms": v[0], "launches": v[1]} for n, v in prof.items() if v[1]}
     out["per_kernel_ms"] = other
@@ -340,6 +374,12 @@ def run_kald(args):
     w = WORKLOADS[args.workload]()
     if args.mesh:
         w.mesh = tuple(int(x) for x in args.mesh.split(","))
+    units_step = float(sum(w.n_q * w.n_q * x.n_branches ** 3 for x in w.systems))   # whole job
+    shard = shard_plan(w.n_q, len(w.systems), world, rank)
+    if shard["kind"] == "systems":
+        w.systems = [w.systems[x] for x in shard["idx"]]
+    elif shard["kind"] == "replica":
+        units_step *= world
     gamma_only = w.n_q == 1
     s = w.systems[0]
     nq = w.n_q
@@ -378,7 +418,15 @@ def run_kald(args):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        _, trip = kk.kald_linewidths(ctx, w.systems, w.mesh, nu, eig, opt, gamma=gam)
+        if shard["kind"] == "qrange":
+            q0, q1 = shard["q0"], shard["q1"]
+            loc = gam[:(q1 - q0) * nb]
+            trip = (0, 0)
+            if q1 > q0:
+                _, trip = kk.kald_linewidths_qrange(ctx, s, w.mesh, nu, eig, opt, q0, q1, gamma=loc)
+            gam.copy_(gather_q_sharded(loc.clone(), shard["per"], nb, nq, world))
+        else:
+            _, trip = kk.kald_linewidths(ctx, w.systems, w.mesh, nu, eig, opt, gamma=gam)
         ev1.record(stream)
         kappa(nu, eig, gam, kap)
         trip_info["trip"] = trip
@@ -414,7 +462,7 @@ def run_kald(args):
         dist.barrier()
     clocks = sampler.stop()
     triplets_step = sum(nq * nq * b ** 3 for b in nbs)
-    total_ms, value = job_throughput(float(sum(step_ms)), world, triplets_step, args.steps, device=dev)
+    total_ms, value = job_throughput(float(sum(step_ms)), world, units_step, args.steps, device=dev)
 
     # ---- end to end through host buffers (pinned), same calls
     nu_h = torch.zeros(n_modes, dtype=torch.float64).pin_memory().numpy()
@@ -429,16 +477,29 @@ def run_kald(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         phon(nu_h, eig_h)
-        kk.kald_linewidths(ctx, w.systems, w.mesh, nu_h, eig_h, opt, gamma=gam_h)
+        if shard["kind"] == "qrange":
+            q0, q1 = shard["q0"], shard["q1"]
+            loc = np.zeros((q1 - q0) * nb)
+            if q1 > q0:
+                kk.kald_linewidths_qrange(ctx, s, w.mesh, nu_h, eig_h, opt, q0, q1, gamma=loc)
+            full = gather_q_sharded(torch.from_numpy(loc).to(dev), shard["per"], nb, nq, world)
+            gam_h[:] = full.cpu().numpy()
+        else:
+            kk.kald_linewidths(ctx, w.systems, w.mesh, nu_h, eig_h, opt, gamma=gam_h)
         kappa(nu_h, eig_h, gam_h, kap_h)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    if world > 1 and e2e_ms:
+        _, e2e_rate = job_throughput(float(sum(e2e_ms)), world, units_step, len(e2e_ms), device=dev)
+    else:
+        e2e_rate = units_step / (float(np.mean(e2e_ms)) / 1e3) if e2e_ms else None
     h2d = 3 * sys_bytes + 2 * (nu_h.nbytes + eig_h.nbytes) + gam_h.nbytes
     d2h = nu_h.nbytes + eig_h.nbytes + gam_h.nbytes + kap_h.nbytes
-    e2e_value = triplets_step / (float(np.mean(e2e_ms)) / 1e3) if e2e_ms else None
+    e2e_value = e2e_rate
 
     # ---- roofline of the dominant kernel, timed per launch inside the steps
     trip, allowed = trip_info["trip"]
-    roofline = roofline_of(args, w, nbs, nu.cpu().numpy(), opt, prof, args.steps, allowed)
+    share = (shard["q1"] - shard["q0"]) / nq if shard["kind"] == "qrange" else 1.0
+    roofline = roofline_of(args, w, nbs, nu.cpu().numpy(), opt, prof, args.steps, allowed, share)
 
     # ---- kappa time-to-solution: split path against the plain FP64 GPU path
     tts = None
@@ -450,14 +511,21 @@ def run_kald(args):
         v, dt, sample = time_oracle_sample(w)
         cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": sample, "seconds": dt}
+    # strong scaling (one fixed workload shared by the ranks) unless a single
+    # Gamma-only system runs as replicas
+    one_system_gamma = (w.n_q == 1 and shard["kind"] in ("whole", "replica") and len(w.systems) == 1)
+    scaling = "weak" if one_system_gamma else "strong"
+    parallelism = {"whole": "single GPU", "qrange": f"q-sharded over {world} GPUs, all-gather of gamma (NCCL)",
+                   "systems": f"systems dealt over {world} GPUs", "replica": f"replicas{world}"}[shard["kind"]]
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "higher_is_better": True, "scaling": scaling, "vs_baseline": None,
                 "dtype": {"fp32": "f32", "fp64": "f64", "bf16split": "bf16x3"}[args.precision],
                 "data": "synthetic",
-                "config": {"workload": f"{w.name}: {w.description}", "global_batch": world,
-                           "seq_len": None, "parallelism": f"replicas{world}",
+                "config": {"workload": f"{w.name}: {w.description}",
+                           "global_batch": 1 if scaling == "strong" else world,
+                           "seq_len": None, "parallelism": parallelism,
                            "l2": "flushed (256 MB write) between timed steps",
                            "precision": args.precision,
                            "linewidth_ms": float(np.mean(lw_ms))},
@@ -467,7 +535,7 @@ def run_kald(args):
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
                 "kappa_time_to_solution": tts,
                 "kappa_W_mK": kap.cpu().numpy().round(6).tolist()[:2],
-                "delta_allowed_fraction": allowed / trip}
+                "delta_allowed_fraction": allowed / trip if trip else None}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

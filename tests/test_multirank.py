@@ -1,6 +1,8 @@
-"""The N > 1 host logic of bench.py on CPU: two gloo ranks run the replica
-aggregation (max over ranks of the timed region, whole-job rate) the way the
-GPU ranks do under NCCL.  No GPU is involved."""
+"""The N > 1 host logic of bench.py on CPU: two gloo ranks run the timing
+aggregation (max over ranks of the timed region, whole-job rate) and the
+q-sharded split (bench.shard_plan ranges, bench.gather_q_sharded all-gather)
+the way the GPU ranks do under NCCL, with the oracle standing in for
+kald_linewidths_qrange on each rank's range.  No GPU is involved."""
 
 import os
 import socket
@@ -24,7 +26,7 @@ def _rank(rank, world, port, q):
     dist.init_process_group("gloo", rank=r, world_size=w)
     dist.barrier()
     local_ms = 1000.0 * (rank + 1)                # rank 1 is the slow one
-    total_ms, value = bench.job_throughput(local_ms, w, units_per_step=5.0e9, steps=3, device="cpu")
+    total_ms, value = bench.job_throughput(local_ms, w, units_per_step=2 * 5.0e9, steps=3, device="cpu")
     q.put((r, w, local, total_ms, value))
     dist.barrier()
     dist.destroy_process_group()
@@ -67,15 +69,14 @@ def _shard_rank(rank, world, port, q):
     w = ki.small_binary(mesh=(3, 3, 3), sigma=0.1)
     s = w.systems[0]
     nu, eig = ph.phonons(s, w.mesh)
-    nq = nu.shape[0]
-    per = -(-nq // world)                          # contiguous q ranges
-    mine = list(range(rank * per, min(nq, (rank + 1) * per)))
+    import bench
+    nq, nb = nu.shape
+    plan = bench.shard_plan(nq, 1, world, rank)
+    assert plan["kind"] == "qrange"
+    mine = list(range(plan["q0"], plan["q1"]))
     g = an.linewidths(s, w.mesh, nu, eig, w.T, w.sigma_thz, w.n_sigma, q_list=mine)
-    buf = torch.zeros(per, nu.shape[1], dtype=torch.float64)
-    buf[:len(mine)] = torch.from_numpy(g)
-    parts = [torch.zeros_like(buf) for _ in range(world)]
-    dist.all_gather(parts, buf)
-    full = torch.cat(parts)[:nq].numpy()
+    full = bench.gather_q_sharded(torch.from_numpy(np.ravel(g)), plan["per"], nb, nq, world)
+    full = full.numpy().reshape(nq, nb)
     if rank == 0:
         ref = an.linewidths(s, w.mesh, nu, eig, w.T, w.sigma_thz, w.n_sigma)
         q.put(float(np.max(np.abs(full - ref))))
@@ -85,9 +86,10 @@ def _shard_rank(rank, world, port, q):
 
 def test_q_sharded_linewidths_gather_to_the_single_rank_result():
     """The multi-GPU split of the hot path (independent q items, contiguous q
-    ranges per rank, one all-gather of gamma), emulated by two gloo ranks that
-    each run the oracle on their shard: the gathered gamma equals the
-    single-rank result exactly."""
+    ranges per rank from bench.shard_plan, one all-gather of gamma by
+    bench.gather_q_sharded), emulated by two gloo ranks that each run the
+    oracle on their range: the gathered gamma equals the single-rank result
+    exactly."""
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
@@ -99,3 +101,20 @@ def test_q_sharded_linewidths_gather_to_the_single_rank_result():
         p.join(timeout=60)
         assert p.exitcode == 0
     assert diff == 0.0
+
+
+def test_shard_plan_covers_every_unit_once():
+    import bench
+    for nq in (1, 2, 7, 27, 512):
+        for world in (1, 2, 3, 4, 8):
+            plans = [bench.shard_plan(nq, 1, world, r) for r in range(world)]
+            if world == 1:
+                assert plans[0]["kind"] == "whole"
+                continue
+            if nq == 1:
+                assert all(p["kind"] == "replica" for p in plans)
+                continue
+            qs = [q for p in plans for q in range(p["q0"], p["q1"])]
+            assert qs == list(range(nq))
+    plans = [bench.shard_plan(1, 24, 8, r) for r in range(8)]
+    assert sorted(x for p in plans for x in p["idx"]) == list(range(24))
