@@ -173,6 +173,20 @@ uint64_t kald_kernel_launches(void);
 kald_status kald_phonons(kald_ctx *ctx, const kald_system *sys, const int32_t mesh[3],
                          double *nu_thz, double *eigvec, double *vel);
 
+/* Harmonic phonons of several Gamma-only supercells (mesh {1,1,1}) in one
+ * launch sequence (the batched disordered-supercell workload): the same
+ * eigenpairs as one kald_phonons call per system, bit for bit.  The FP64
+ * eigensolves of the cells with nb > 96 run together -- each Householder
+ * step of every cell in one launch, its CTAs dealt over the cells in
+ * proportion to their remaining rows, then one launch per later stage for all
+ * cells -- and the call synchronises once (per 64 cells).  Cells with
+ * nb <= 96 use the per-q solver of kald_phonons.
+ *   nu_thz  [sum of nb] out, per system concatenated (ascending per system)
+ *   eigvec  [sum of nb^2][2] out, complex128, per system row = mode
+ * No velocities (at Gamma they vanish by symmetry for these cells' use). */
+kald_status kald_phonons_batch(kald_ctx *ctx, int32_t n_sys, const kald_system *sys, double *nu_thz,
+                               double *eigvec);
+
 /* Three-phonon linewidths gamma_mu = Gamma^0_mu in ps^-1 (Eq. gamma_operators,
  * projection_plus, phase_space, delta_deconstructed):
  *   gamma_mu = (hbar pi / 8 N_k) sum_{q' s' s''} |phi|^2 / (w w' w'')

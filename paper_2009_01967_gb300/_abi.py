@@ -27,7 +27,7 @@ EXPORTS = ["kald_ctx_create", "kald_ctx_destroy", "kald_last_error", "kald_set_s
            "kald_phonons", "kald_linewidths", "kald_kappa_rta", "kald_kappa_qhgk",
            "kald_kappa_rta_noalloc", "kald_kernel_launches", "kald_set_wait_limit",
            "kald_set_workspace_limit", "kald_profile_enable", "kald_profile_read",
-           "kald_linewidths_qrange"]
+           "kald_linewidths_qrange", "kald_phonons_batch"]
 PROF_KERNELS = {"tcx_gather": 0, "tcx_gemm1": 1, "tcx_gemm2": 2, "tc_gemm1": 3, "tc_gemm2": 4,
                 "small_nb": 5, "lw_main": 6}
 
@@ -73,6 +73,8 @@ def load_library(path: str = LIB_PATH):
     lib.kald_set_stream.restype = st
     lib.kald_phonons.argtypes = [vp, C.POINTER(kald_system), C.POINTER(i32), vp, vp, vp]
     lib.kald_phonons.restype = st
+    lib.kald_phonons_batch.argtypes = [vp, i32, C.POINTER(kald_system), vp, vp]
+    lib.kald_phonons_batch.restype = st
     lib.kald_linewidths.argtypes = [vp, i32, C.POINTER(kald_system), C.POINTER(i32), vp, vp,
                                     C.POINTER(kald_options), vp, C.POINTER(C.c_uint64)]
     lib.kald_linewidths.restype = st
@@ -255,6 +257,24 @@ def _systems(systems):
         arr[x] = cs
         keep.append(k)
     return arr, keep, [3 * int(np.asarray(s.masses).shape[0]) for s in systems]
+
+
+def kald_phonons_batch(ctx: Context, systems, nu_thz=None, eigvec=None):
+    """Gamma-only phonons of several supercells in one launch sequence; returns
+    (nu_thz [sum nb], eigvec [sum nb^2]) concatenated per system (host numpy
+    arrays by default)."""
+    arr, keep, nbs = _systems(systems)
+    n_modes = sum(nbs)
+    n_eig = sum(nb * nb for nb in nbs)
+    if nu_thz is None:
+        nu_thz = np.zeros(n_modes)
+    if eigvec is None:
+        eigvec = np.zeros(n_eig, dtype=np.complex128)
+    ctx.check(ctx.lib.kald_phonons_batch(ctx.handle, len(nbs), arr,
+                                         _ptr(nu_thz, np.float64, n_modes, "nu_thz"),
+                                         _ptr(eigvec, np.complex128, n_eig, "eigvec")))
+    del keep
+    return nu_thz, eigvec
 
 
 def kald_linewidths(ctx: Context, systems, mesh, nu_thz, eigvec, options: Options, gamma=None):

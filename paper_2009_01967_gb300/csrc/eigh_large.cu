@@ -27,9 +27,20 @@
 //      writes eigenvalues (as frequencies) and row-major eigenvectors [s][d].
 // No host synchronisation inside: every stage reads its scalars from device
 // memory.
+//
+// Batched form: the eigensolves of several systems (different sizes) run as
+// one launch sequence.  Each system's matrices and vectors are described by
+// an EighSys record in device memory; the stage kernels take the system from
+// blockIdx.y, and the Householder step k of every system that still has
+// reflector k goes into one launch whose CTAs are dealt over the systems in
+// proportion to their remaining rows (cta_start).  Every value is computed by
+// the same threads in the same order as in a solve of the system alone (row
+// dot products by one warp, block sums over a fixed 512 threads, one warp per
+// eigenvalue or vector), so the batch does not change any result.
 
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "kald_internal.h"
 
@@ -38,6 +49,25 @@ namespace {
 
 constexpr double kEps = 2.220446049250313e-16;
 constexpr int kTriThreads = 512;
+constexpr int kMaxEighBatch = 64;
+
+// One system of a batched solve (device-resident record).
+struct EighSys {
+    int n;
+    const double2 *D;                     // dynamical matrix [n][n]
+    double *A, *X, *rdg, *u1, *u2, *ml;   // [n][n] each
+    unsigned char *piv;                   // [n][n]
+    double *vb[2], *pb[2];                // reflector and product ping-pong [n]
+    double *dd, *ee, *lam, *e2, *g;       // [n], g [4]
+    double *nu;                           // out [n] THz
+    double2 *eig;                         // out [n][n] row = eigenvector
+};
+// CTAs of one Householder launch dealt over the systems: system s owns CTAs
+// cta_start[s] .. cta_start[s+1]-1 (an empty range once its reflectors are done).
+struct TriMap {
+    int nsys;
+    int cta_start[kMaxEighBatch + 1];
+};
 
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -56,8 +86,12 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
     return warp_sum(lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0);
 }
 
-// A = Re(D) (row-major), symmetrised.
-__global__ void he_real_kernel(int n, const double2 *__restrict__ D, double *__restrict__ A) {
+// A = Re(D) (row-major), symmetrised.  System blockIdx.y.
+__global__ void he_real_kernel(const EighSys *__restrict__ sysv) {
+    const EighSys &S = sysv[blockIdx.y];
+    const int n = S.n;
+    const double2 *__restrict__ D = S.D;
+    double *__restrict__ A = S.A;
     const size_t nn = (size_t)n * n;
     for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < nn;
          x += (size_t)gridDim.x * blockDim.x) {
@@ -72,10 +106,26 @@ __global__ void he_real_kernel(int n, const double2 *__restrict__ D, double *__r
 // and the rebuilt row r (overwritten by v_r), n doubles each.  CTA 0 writes
 // d[r], e[r], v_r and stores v_k into row k of A.  For r = n-2 (the last
 // launch) only the 2 x 2 tail of T is left: d[n-2], e[n-2], d[n-1].
+// Batched: CTA blockIdx.x belongs to the system whose cta_start range holds
+// it; within the system it is CTA (blockIdx.x - cta_start[s]) of
+// (cta_start[s+1] - cta_start[s]).
 __global__ void __launch_bounds__(kTriThreads)
-tri_step_kernel(int n, int k, double *__restrict__ A, const double *__restrict__ vin,
-                const double *__restrict__ pin, double *__restrict__ vout, double *__restrict__ pout,
-                double *__restrict__ dd, double *__restrict__ ee) {
+tri_step_kernel(const EighSys *__restrict__ sysv, const __grid_constant__ TriMap map, int k) {
+    int sidx = 0;
+    while (sidx + 1 < map.nsys && (int)blockIdx.x >= map.cta_start[sidx + 1]) ++sidx;
+    const EighSys &S = sysv[sidx];
+    const int n = S.n;
+    const int cta = (int)blockIdx.x - map.cta_start[sidx];
+    const int n_cta = map.cta_start[sidx + 1] - map.cta_start[sidx];
+    if (k > n - 3) return;                             // (not reached: such systems own no CTA)
+    const int cur = (k + 2) & 1, nxt = (k + 1) & 1;   // v_k in vb[k & 1]
+    double *__restrict__ A = S.A;
+    const double *__restrict__ vin = S.vb[cur];
+    const double *__restrict__ pin = S.pb[cur];
+    double *__restrict__ vout = S.vb[nxt];
+    double *__restrict__ pout = S.pb[nxt];
+    double *__restrict__ dd = S.dd;
+    double *__restrict__ ee = S.ee;
     extern __shared__ double sm[];
     double *sv = sm, *sw = sm + n, *sa = sm + 2 * n;
     __shared__ double red[32];
@@ -103,14 +153,14 @@ tri_step_kernel(int n, int k, double *__restrict__ A, const double *__restrict__
     }
     __syncthreads();
     if (r >= n - 2) {                                  // tail: no reflector r
-        if (blockIdx.x == 0 && tid == 0) {
+        if (cta == 0 && tid == 0) {
             dd[n - 2] = sa[n - 2];
             ee[n - 2] = sa[n - 1];
             double a = A[(size_t)(n - 1) * n + n - 1];
             if (prev) a -= 2.0 * sv[n - 1] * sw[n - 1];
             dd[n - 1] = a;
         }
-        if (blockIdx.x == 0 && prev)
+        if (cta == 0 && prev)
             for (int j = k + 1 + tid; j < n; j += nt) A[(size_t)k * n + j] = sv[j];
         return;
     }
@@ -125,7 +175,7 @@ tri_step_kernel(int n, int k, double *__restrict__ A, const double *__restrict__
     const double sc = (vv > 0.0) ? 1.0 / sqrt(vv) : 0.0;
     for (int j = r + 1 + tid; j < n; j += nt) sa[j] = ((j == r + 1) ? sa[j] - alpha : sa[j]) * sc;
     __syncthreads();
-    if (blockIdx.x == 0) {
+    if (cta == 0) {
         if (tid == 0) {
             dd[r] = sa[r];
             ee[r] = (vv > 0.0) ? alpha : x0;
@@ -140,7 +190,7 @@ tri_step_kernel(int n, int k, double *__restrict__ A, const double *__restrict__
     const int lane = tid & 31;
     const int warps = nt >> 5;
     const int rows = n - r - 1;
-    for (int t = (int)blockIdx.x + (int)gridDim.x * (tid >> 5); t < rows; t += (int)gridDim.x * warps) {
+    for (int t = cta + n_cta * (tid >> 5); t < rows; t += n_cta * warps) {
         const int i = r + 1 + t;
         double *row = A + (size_t)i * n;
         double acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -180,8 +230,13 @@ tri_step_kernel(int n, int k, double *__restrict__ A, const double *__restrict__
 // (|d_i| + |e_{i-1}| + |e_i|) and the pivot floor of the Sturm counts:
 // g = {lo, hi, |T|, pivmin}; also e2_i = e_i^2.  One CTA.
 __global__ void __launch_bounds__(1024)
-gersh_kernel(int n, const double *__restrict__ d, const double *__restrict__ e, double *__restrict__ g,
-             double *__restrict__ e2) {
+gersh_kernel(const EighSys *__restrict__ sysv) {
+    const EighSys &S = sysv[blockIdx.y];
+    const int n = S.n;
+    const double *__restrict__ d = S.dd;
+    const double *__restrict__ e = S.ee;
+    double *__restrict__ g = S.g;
+    double *__restrict__ e2 = S.e2;
     __shared__ double s_lo[32], s_hi[32], s_tn[32];
     double lo = 1e300, hi = -1e300, tn = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -254,8 +309,13 @@ __device__ int sturm_count(int n, const double *__restrict__ d, const double *__
 // exceeds i (lambda_i < x there).  About 11 rounds reach an interval of
 // max(eps |T|, 2 eps |lambda|).
 __global__ void __launch_bounds__(128)
-bisect_kernel(int n, const double *__restrict__ d, const double *__restrict__ e2,
-              const double *__restrict__ g, double *__restrict__ lam) {
+bisect_kernel(const EighSys *__restrict__ sysv) {
+    const EighSys &S = sysv[blockIdx.y];
+    const int n = S.n;
+    const double *__restrict__ d = S.dd;
+    const double *__restrict__ e2 = S.e2;
+    const double *__restrict__ g = S.g;
+    double *__restrict__ lam = S.lam;
     const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (i >= n) return;                                // whole warps
@@ -282,11 +342,19 @@ bisect_kernel(int n, const double *__restrict__ d, const double *__restrict__ e2
 // superdiagonals u1, u2 of U, multipliers ml and row-exchange flags piv.
 // The running row of the elimination and the running components of the
 // solves stay in registers; x is stored component-major X[j][t].
-__global__ void invit_kernel(int n, const double *__restrict__ d, const double *__restrict__ e,
-                             const double *__restrict__ lam, const double *__restrict__ g,
-                             double *__restrict__ rdg, double *__restrict__ u1, double *__restrict__ u2,
-                             double *__restrict__ ml, unsigned char *__restrict__ piv,
-                             double *__restrict__ X) {
+__global__ void invit_kernel(const EighSys *__restrict__ sysv) {
+    const EighSys &S0 = sysv[blockIdx.y];
+    const int n = S0.n;
+    const double *__restrict__ d = S0.dd;
+    const double *__restrict__ e = S0.ee;
+    const double *__restrict__ lam = S0.lam;
+    const double *__restrict__ g = S0.g;
+    double *__restrict__ rdg = S0.rdg;
+    double *__restrict__ u1 = S0.u1;
+    double *__restrict__ u2 = S0.u2;
+    double *__restrict__ ml = S0.ml;
+    unsigned char *__restrict__ piv = S0.piv;
+    double *__restrict__ X = S0.X;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     const size_t S = (size_t)n;
@@ -358,10 +426,16 @@ __global__ void invit_kernel(int n, const double *__restrict__ d, const double *
 // Step 4: modified Gram-Schmidt inside the near-degenerate set that starts at
 // eigenvalue blockIdx.x (the CTA returns when no set of two or more starts there).
 __global__ void __launch_bounds__(256)
-mgs_kernel(int n, const double *__restrict__ lam, const double *__restrict__ g, double *__restrict__ X) {
+mgs_kernel(const EighSys *__restrict__ sysv) {
+    const EighSys &SY = sysv[blockIdx.y];
+    const int n = SY.n;
+    const double *__restrict__ lam = SY.lam;
+    const double *__restrict__ g = SY.g;
+    double *__restrict__ X = SY.X;
     __shared__ double red[8];
     __shared__ double s_dot;
     const int s0 = blockIdx.x;
+    if (s0 >= n) return;
     const double thr = 1e-9 * g[2];
     const bool starts = (s0 == 0 || lam[s0] - lam[s0 - 1] > thr) && (s0 + 1 < n && lam[s0 + 1] - lam[s0] <= thr);
     if (!starts) return;
@@ -397,11 +471,17 @@ mgs_kernel(int n, const double *__restrict__ lam, const double *__restrict__ g, 
 // Step 5: z_s <- H_0 ... H_{n-3} z_s for the vpb vectors s0 .. s0+vpb-1 of this
 // CTA (one warp per vector, vectors in shared memory), then the outputs:
 // eigenvector s as row s of eig (imaginary part 0) and its frequency.
-__global__ void backtransform_kernel(int n, int vpb, const double *__restrict__ A,
-                                     const double *__restrict__ X, const double *__restrict__ lam,
-                                     double *__restrict__ nu, double2 *__restrict__ eig) {
+__global__ void backtransform_kernel(const EighSys *__restrict__ sysv, int vpb) {
+    const EighSys &S = sysv[blockIdx.y];
+    const int n = S.n;
+    const double *__restrict__ A = S.A;
+    const double *__restrict__ X = S.X;
+    const double *__restrict__ lam = S.lam;
+    double *__restrict__ nu = S.nu;
+    double2 *__restrict__ eig = S.eig;
     extern __shared__ double zs[];
     const int s0 = blockIdx.x * vpb;
+    if (s0 >= n) return;
     const int nv = min(vpb, n - s0);
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int x = tid; x < nv * n; x += nt) {
@@ -452,50 +532,83 @@ bool eigh_large_supported(int n, size_t smem_optin) {
            sizeof(double) * (size_t)n <= smem_optin;
 }
 
-cudaError_t launch_eigh_large(int n, const double2 *D, double *scratch, double *nu_out,
-                              double2 *eig_out, int sms, size_t smem_optin, cudaStream_t st) {
-    if (!eigh_large_supported(n, smem_optin)) return cudaErrorInvalidValue;
-    const size_t nn = (size_t)n * n;
-    char *base = reinterpret_cast<char *>(scratch);
-    const size_t mat = ws_round(sizeof(double) * nn);
-    double *A = reinterpret_cast<double *>(base);
-    double *X = reinterpret_cast<double *>(base + mat);
-    double *rdg = reinterpret_cast<double *>(base + 2 * mat);
-    double *u1 = reinterpret_cast<double *>(base + 3 * mat);
-    double *u2 = reinterpret_cast<double *>(base + 4 * mat);
-    double *ml = reinterpret_cast<double *>(base + 5 * mat);
-    unsigned char *piv = reinterpret_cast<unsigned char *>(base + 6 * mat);
-    double *vec = reinterpret_cast<double *>(base + 6 * mat + ws_round(nn));
-    double *vb[2] = {vec, vec + n}, *pb[2] = {vec + 2 * n, vec + 3 * n};
-    double *dd = vec + 4 * n, *ee = vec + 5 * n, *lam = vec + 6 * n, *e2 = vec + 7 * n, *g = vec + 8 * n;
+size_t eigh_batch_records_bytes(int n_sys) { return ws_round(sizeof(EighSys) * (size_t)std::max(n_sys, 1)); }
 
-    const unsigned gr = (unsigned)std::min<size_t>((nn + 255) / 256, 16384);
-    he_real_kernel<<<counted(gr), 256, 0, st>>>(n, D, A);
-    const size_t tri_smem = sizeof(double) * 3 * (size_t)n;
-    cudaError_t e = cudaFuncSetAttribute(tri_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tri_smem);
-    if (e != cudaSuccess) return e;
-    for (int k = -1; k <= n - 3; ++k) {
-        const int rows = n - k - 2;                   // rows below the new reflector's row
-        const int grid = std::max(1, std::min(rows, std::max(sms, 1)));   // one CTA per SM
-        const int cur = (k + 2) & 1, nxt = (k + 1) & 1;   // v_k in vb[k & 1]
-        tri_step_kernel<<<counted(grid), kTriThreads, tri_smem, st>>>(n, k, A, vb[cur], pb[cur], vb[nxt],
-                                                                      pb[nxt], dd, ee);
+cudaError_t launch_eigh_large_batch(int n_sys, const EighJob *jobs, void *records, int sms, size_t smem_optin,
+                                    cudaStream_t st) {
+    if (n_sys < 1 || n_sys > kMaxEighBatch) return cudaErrorInvalidValue;
+    int n_max = 0;
+    for (int x = 0; x < n_sys; ++x) {
+        if (!eigh_large_supported(jobs[x].n, smem_optin)) return cudaErrorInvalidValue;
+        n_max = std::max(n_max, jobs[x].n);
     }
-    gersh_kernel<<<counted(1), 1024, 0, st>>>(n, dd, ee, g, e2);
-    const unsigned g32 = (unsigned)((n + 31) / 32);
-    bisect_kernel<<<counted((unsigned)((n + 3) / 4)), 128, 0, st>>>(n, dd, e2, g, lam);
-    invit_kernel<<<counted(g32), 32, 0, st>>>(n, dd, ee, lam, g, rdg, u1, u2, ml, piv, X);
-    mgs_kernel<<<counted(n), 256, 0, st>>>(n, lam, g, X);
-    // vectors per CTA: about one CTA per SM, within the shared memory limit
-    int vpb = std::max(1, (n + std::max(sms, 1) - 1) / std::max(sms, 1));
+    std::vector<EighSys> rec(n_sys);
+    for (int x = 0; x < n_sys; ++x) {
+        const int n = jobs[x].n;
+        const size_t nn = (size_t)n * n;
+        char *base = reinterpret_cast<char *>(jobs[x].scratch);
+        const size_t mat = ws_round(sizeof(double) * nn);
+        EighSys &R = rec[x];
+        R.n = n;
+        R.D = jobs[x].D;
+        R.A = reinterpret_cast<double *>(base);
+        R.X = reinterpret_cast<double *>(base + mat);
+        R.rdg = reinterpret_cast<double *>(base + 2 * mat);
+        R.u1 = reinterpret_cast<double *>(base + 3 * mat);
+        R.u2 = reinterpret_cast<double *>(base + 4 * mat);
+        R.ml = reinterpret_cast<double *>(base + 5 * mat);
+        R.piv = reinterpret_cast<unsigned char *>(base + 6 * mat);
+        double *vec = reinterpret_cast<double *>(base + 6 * mat + ws_round(nn));
+        R.vb[0] = vec; R.vb[1] = vec + n; R.pb[0] = vec + 2 * n; R.pb[1] = vec + 3 * n;
+        R.dd = vec + 4 * n; R.ee = vec + 5 * n; R.lam = vec + 6 * n; R.e2 = vec + 7 * n; R.g = vec + 8 * n;
+        R.nu = jobs[x].nu_out;
+        R.eig = jobs[x].eig_out;
+    }
+    EighSys *dev = static_cast<EighSys *>(records);
+    // (a copy from pageable memory returns once the host buffer is staged)
+    cudaError_t e = cudaMemcpyAsync(dev, rec.data(), sizeof(EighSys) * n_sys, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    const size_t nn_max = (size_t)n_max * n_max;
+    const unsigned gr = (unsigned)std::min<size_t>((nn_max + 255) / 256, 16384);
+    he_real_kernel<<<counted(dim3(gr, n_sys)), 256, 0, st>>>(dev);
+    const size_t tri_smem = sizeof(double) * 3 * (size_t)n_max;
+    e = cudaFuncSetAttribute(tri_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tri_smem);
+    if (e != cudaSuccess) return e;
+    const int budget = std::max(1, sms);
+    for (int k = -1; k <= n_max - 3; ++k) {
+        // CTAs of this step: every system that still has step k gets a share of
+        // about one CTA per SM in proportion to its remaining rows (at least one,
+        // at most one per row)
+        TriMap map;
+        map.nsys = n_sys;
+        long long rows_sum = 0;
+        for (int x = 0; x < n_sys; ++x)
+            if (k <= jobs[x].n - 3) rows_sum += jobs[x].n - k - 2;
+        int c = 0;
+        for (int x = 0; x < n_sys; ++x) {
+            map.cta_start[x] = c;
+            if (k > jobs[x].n - 3) continue;
+            const long long rows = jobs[x].n - k - 2;
+            const long long share = (budget * rows + rows_sum - 1) / rows_sum;
+            c += (int)std::max(1LL, std::min(rows, share));
+        }
+        map.cta_start[n_sys] = c;
+        tri_step_kernel<<<counted(c), kTriThreads, tri_smem, st>>>(dev, map, k);
+    }
+    gersh_kernel<<<counted(dim3(1, n_sys)), 1024, 0, st>>>(dev);
+    bisect_kernel<<<counted(dim3((unsigned)((n_max + 3) / 4), n_sys)), 128, 0, st>>>(dev);
+    invit_kernel<<<counted(dim3((unsigned)((n_max + 31) / 32), n_sys)), 32, 0, st>>>(dev);
+    mgs_kernel<<<counted(dim3((unsigned)n_max, n_sys)), 256, 0, st>>>(dev);
+    // vectors per CTA: about one CTA per SM for the largest system, within the
+    // shared memory limit; one warp per vector
+    int vpb = std::max(1, (n_max + std::max(sms, 1) - 1) / std::max(sms, 1));
     vpb = std::min(vpb, 32);
-    vpb = std::min<int>(vpb, (int)(smem_optin / (sizeof(double) * (size_t)n)));
-    const size_t bt_smem = sizeof(double) * (size_t)vpb * n;
+    vpb = std::min<int>(vpb, (int)(smem_optin / (sizeof(double) * (size_t)n_max)));
+    const size_t bt_smem = sizeof(double) * (size_t)vpb * n_max;
     e = cudaFuncSetAttribute(backtransform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt_smem);
     if (e != cudaSuccess) return e;
-    backtransform_kernel<<<counted((unsigned)((n + vpb - 1) / vpb)), 32 * vpb, bt_smem, st>>>(n, vpb, A, X, lam,
-                                                                                            nu_out, eig_out);
+    backtransform_kernel<<<counted(dim3((unsigned)((n_max + vpb - 1) / vpb), n_sys)), 32 * vpb, bt_smem, st>>>(dev,
+                                                                                                          vpb);
     return cudaGetLastError();
 }
 

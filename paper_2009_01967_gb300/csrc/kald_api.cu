@@ -526,6 +526,7 @@ void kald_ctx_destroy(kald_ctx *ctx) {
     if (ctx->stream && ctx->stream != ctx->own_stream) cudaStreamSynchronize(ctx->stream);
     if (ctx->ws) cudaFree(ctx->ws);
     ctx->prof.destroy();
+    for (cudaStream_t l : ctx->lanes) cudaStreamDestroy(l);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     delete ctx;
 }
@@ -589,7 +590,7 @@ kald_status kald_phonons(kald_ctx *ctx, const kald_system *sys, const int32_t me
     const bool d_nu = is_device_ptr(nu_thz), d_eig = is_device_ptr(eigvec);
     const bool d_vel = vel && is_device_ptr(vel);
     size_t need = fc2_bytes(h) + bytes_of(qc) + 2 * ws_round(sizeof(double2) * nn) + ws_round(sizeof(int));
-    if (large) need += eigh_large_scratch_bytes(nb);
+    if (large) need += eigh_large_scratch_bytes(nb) + eigh_batch_records_bytes(1);
     if (!d_nu) need += ws_round(sizeof(double) * nq * nb);
     if (!d_eig) need += ws_round(sizeof(double2) * nn);
     if (vel && !d_vel) need += ws_round(sizeof(double) * 3 * nq * nb);
@@ -607,10 +608,14 @@ kald_status kald_phonons(kald_ctx *ctx, const kald_system *sys, const int32_t me
     if (vel) vel_d = d_vel ? vel : static_cast<double *>(ws_take(ctx, sizeof(double) * 3 * nq * nb));
     cudaStream_t s = ctx->stream;
     double *big = large ? static_cast<double *>(ws_take(ctx, eigh_large_scratch_bytes(nb))) : nullptr;
+    void *rec = large ? ws_take(ctx, eigh_batch_records_bytes(1)) : nullptr;
     cudaMemsetAsync(nonconv, 0, sizeof(int), s);
     cudaError_t e = launch_dynmat(dev_fc2(h, d), nb, nq, qcart, D, s);
     if (e == cudaSuccess) {
-        if (large) e = launch_eigh_large(nb, D, big, nu_d, eig_d, ctx->sm_count, ctx->smem_optin, s);
+        if (large) {
+            const EighJob job{nb, D, big, nu_d, eig_d};
+            e = launch_eigh_large_batch(1, &job, rec, ctx->sm_count, ctx->smem_optin, s);
+        }
         else e = launch_jacobi(nb, nq, D, V, nu_d, eig_d, nonconv, ctx->smem_optin, s);
     }
     if (e == cudaSuccess && vel) e = launch_velocity_diag(dev_fc2(h, d), nb, nq, qcart, nu_d, eig_d, vel_d, s);
@@ -624,6 +629,95 @@ kald_status kald_phonons(kald_ctx *ctx, const kald_system *sys, const int32_t me
     if (nc)
         return fail(ctx, KALD_E_NOCONV,
                     "Jacobi eigensolver did not converge at " + std::to_string(nc) + " q-points");
+    return KALD_OK;
+}
+
+kald_status kald_phonons_batch(kald_ctx *ctx, int32_t n_sys, const kald_system *sys, double *nu_thz,
+                               double *eigvec) {
+    if (!ctx) return KALD_E_INVALID;
+    kald_status st = set_device(ctx);
+    if (st) return st;
+    if (n_sys <= 0 || !sys) return fail(ctx, KALD_E_INVALID, "n_sys must be > 0");
+    if (!nu_thz || !eigvec) return fail(ctx, KALD_E_INVALID, "nu_thz/eigvec NULL");
+    const int32_t gamma_mesh[3] = {1, 1, 1};
+    std::vector<std::shared_ptr<const HostSystem>> hp(n_sys);
+    std::vector<size_t> off_nb(n_sys), off_eig(n_sys);
+    size_t on = 0, oe = 0;
+    std::vector<int> large;
+    for (int x = 0; x < n_sys; ++x) {
+        if ((st = plan_system_cached(ctx, &sys[x], hp[x]))) return st;
+        const int nb = hp[x]->nb;
+        off_nb[x] = on;
+        off_eig[x] = oe;
+        on += nb;
+        oe += (size_t)nb * nb;
+        if (nb > kMaxNbSmall) {
+            if (!eigh_large_supported(nb, ctx->smem_optin))
+                return fail(ctx, KALD_E_UNSUPPORTED, "kald_phonons_batch: cell too large for the Gamma-only eigensolver");
+            large.push_back(x);
+        }
+    }
+    const bool d_nu = is_device_ptr(nu_thz), d_eig = is_device_ptr(eigvec);
+    // cells of nb <= 96: the per-q path, one call each
+    for (int x = 0; x < n_sys; ++x)
+        if (hp[x]->nb <= kMaxNbSmall &&
+            (st = kald_phonons(ctx, &sys[x], gamma_mesh, nu_thz + off_nb[x], eigvec + 2 * off_eig[x], nullptr)))
+            return st;
+    if (large.empty()) return KALD_OK;
+    for (size_t c = 0; c < large.size(); c += 64) {
+        const size_t c1 = std::min(large.size(), c + 64);
+        const std::vector<double> q0(3, 0.0);
+        size_t need = eigh_batch_records_bytes((int)(c1 - c));
+        for (size_t t = c; t < c1; ++t) {
+            const HostSystem &h = *hp[large[t]];
+            const size_t nn = (size_t)h.nb * h.nb;
+            need += fc2_bytes(h) + bytes_of(q0) + ws_round(sizeof(double2) * nn) + eigh_large_scratch_bytes(h.nb);
+            if (!d_nu) need += ws_round(sizeof(double) * h.nb);
+            if (!d_eig) need += ws_round(sizeof(double2) * nn);
+        }
+        if ((st = ws_reserve(ctx, need))) return st;
+        void *rec = ws_take(ctx, eigh_batch_records_bytes((int)(c1 - c)));
+        std::vector<EighJob> jobs;
+        std::vector<double *> nu_stage;
+        std::vector<double2 *> eig_stage;
+        cudaError_t e = cudaSuccess;
+        for (size_t t = c; t < c1 && e == cudaSuccess; ++t) {
+            const int x = large[t];
+            const HostSystem &h = *hp[x];
+            const int nb = h.nb;
+            const size_t nn = (size_t)nb * nb;
+            DevSystem d;
+            upload_fc2(ctx, h, d);
+            const double *qcart = upload(ctx, q0);
+            double2 *D = static_cast<double2 *>(ws_take(ctx, sizeof(double2) * nn));
+            double *big = static_cast<double *>(ws_take(ctx, eigh_large_scratch_bytes(nb)));
+            double *nu_d = d_nu ? nu_thz + off_nb[x] : static_cast<double *>(ws_take(ctx, sizeof(double) * nb));
+            double2 *eig_d = d_eig ? reinterpret_cast<double2 *>(eigvec) + off_eig[x]
+                                   : static_cast<double2 *>(ws_take(ctx, sizeof(double2) * nn));
+            e = launch_dynmat(dev_fc2(h, d), nb, 1, qcart, D, ctx->stream);
+            jobs.push_back({nb, D, big, nu_d, eig_d});
+            nu_stage.push_back(nu_d);
+            eig_stage.push_back(eig_d);
+        }
+        if (e == cudaSuccess)
+            e = launch_eigh_large_batch((int)jobs.size(), jobs.data(), rec, ctx->sm_count, ctx->smem_optin,
+                                        ctx->stream);
+        if (e != cudaSuccess) {
+            cudaStreamSynchronize(ctx->stream);
+            return cuda_check(ctx, e, "kald_phonons_batch launch");
+        }
+        for (size_t t = c; t < c1; ++t) {
+            const int x = large[t];
+            const int nb = hp[x]->nb;
+            if (!d_nu)
+                cudaMemcpyAsync(nu_thz + off_nb[x], nu_stage[t - c], sizeof(double) * nb, cudaMemcpyDeviceToHost,
+                                ctx->stream);
+            if (!d_eig)
+                cudaMemcpyAsync(eigvec + 2 * off_eig[x], eig_stage[t - c], sizeof(double2) * (size_t)nb * nb,
+                                cudaMemcpyDeviceToHost, ctx->stream);
+        }
+        if ((st = finish(ctx, "kald_phonons_batch"))) return st;
+    }
     return KALD_OK;
 }
 
@@ -707,6 +801,204 @@ static kald_status check_options(kald_ctx *ctx, const kald_options *o) {
     return KALD_OK;
 }
 
+// Lane streams of a context (forked from and joined back into ctx->stream).
+static kald_status get_lanes(kald_ctx *ctx, int n, std::vector<cudaStream_t> &out) {
+    while ((int)ctx->lanes.size() < n) {
+        cudaStream_t s = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "lane stream");
+        ctx->lanes.push_back(s);
+    }
+    out.assign(ctx->lanes.begin(), ctx->lanes.begin() + n);
+    return KALD_OK;
+}
+// Every lane waits for the work already queued on ctx->stream (fork), or
+// ctx->stream waits for every lane (join).
+static cudaError_t fork_lanes(kald_ctx *ctx, const std::vector<cudaStream_t> &lanes) {
+    cudaEvent_t ev = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, ctx->stream);
+    for (cudaStream_t l : lanes)
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(l, ev, 0);
+    if (ev) cudaEventDestroy(ev);
+    return e;
+}
+static cudaError_t join_lanes(kald_ctx *ctx, const std::vector<cudaStream_t> &lanes) {
+    cudaError_t first = cudaSuccess;
+    for (cudaStream_t l : lanes) {
+        cudaEvent_t ev = nullptr;
+        cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev, l);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ev, 0);
+        if (ev) cudaEventDestroy(ev);
+        if (first == cudaSuccess) first = e;
+    }
+    return first;
+}
+
+// The Gamma-only linewidths of every supercell with nb > 96 among `sys`, as
+// one launch sequence: all systems are planned first (one copy of the
+// frequencies to the host for the delta-band tile lists), one workspace
+// reservation holds every system's buffers, the systems' pipelines are dealt
+// over concurrent lane streams (so that small supercells share the GPU), and
+// the call synchronises once at the end.  Each system's arithmetic is the same
+// as when it is computed alone, so the results do not depend on the batch.
+static kald_status gamma_only_batch(kald_ctx *ctx, int n_sys, const kald_system *sys, const double *nu_thz,
+                                    const double *eigvec, const kald_options *opt, double *gamma, bool d_nu,
+                                    bool d_eig, bool d_g, uint64_t &tot, uint64_t &allowed_tot) {
+    kald_status st;
+    const int mode = opt->precision;     // 0 FP64, 1 FP32, 2 BF16 split (tensor cores)
+    const size_t rs = mode == KALD_FP32 ? sizeof(float) : sizeof(double);
+    struct Item {
+        int x;
+        std::shared_ptr<const HostSystem> hp;
+        GammaPlan gp;
+        std::vector<int> gjk;
+        size_t off_nb, off_eig, need;
+    };
+    std::vector<Item> items;
+    size_t off_nb = 0, off_eig = 0, total_modes = 0;
+    for (int x = 0; x < n_sys; ++x) {
+        std::shared_ptr<const HostSystem> hp;
+        if ((st = plan_system_cached(ctx, &sys[x], hp))) return st;
+        const int nb = hp->nb;
+        if (nb > kMaxNbSmall) items.push_back({x, hp, GammaPlan(), {}, off_nb, off_eig, 0});
+        off_nb += nb;
+        off_eig += (size_t)nb * nb;
+    }
+    total_modes = off_nb;
+    if (items.empty()) return KALD_OK;
+    std::vector<double> nu_all(total_modes);
+    if (d_nu) {
+        cudaError_t e = cudaMemcpy(nu_all.data(), nu_thz, sizeof(double) * total_modes, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "kald_linewidths: frequencies to the host");
+    } else {
+        std::copy(nu_thz, nu_thz + total_modes, nu_all.begin());
+    }
+    size_t need = ws_round(32 * items.size());
+    for (Item &it : items) {
+        const HostSystem &h = *it.hp;
+        const int nb = h.nb;
+        const size_t nn = (size_t)nb * nb;
+        GammaPlan &gp = it.gp;
+        gp.n_groups = (int)h.pair3_j.size();
+        gp.n_part = std::max(1, 2 * ctx->sm_count);
+        gp.sms = std::max(1, ctx->sm_count);
+        gp.omega_h.resize(nb);
+        for (int m = 0; m < nb; ++m) {
+            const double w = kTwoPi * nu_all[it.off_nb + m];
+            gp.omega_h[m] = (std::isfinite(w) && w > kTwoPi * opt->omega_min_thz) ? w : 0.0;
+        }
+        it.gjk.resize(2 * (size_t)gp.n_groups);
+        for (int g = 0; g < gp.n_groups; ++g) { it.gjk[2 * g] = h.pair3_j[g]; it.gjk[2 * g + 1] = h.pair3_k[g]; }
+        if (mode == KALD_BF16_SPLIT) {
+            if (h.fc3_symmetric < 0) h.fc3_symmetric = fc3_symmetric_last_two(&sys[it.x]) ? 1 : 0;
+            gp.symmetric = h.fc3_symmetric;
+            band_tiles(gp.omega_h, tc_tile(), opt->n_sigma * kTwoPi * opt->sigma_thz, gp.symmetric, gp.tiles,
+                       gp.tile_start);
+        }
+        const size_t n_tiles = std::max<size_t>(gp.tiles.size(), 1);
+        size_t b = bytes_of(it.gjk) + bytes_of(h.pair3_start) + bytes_of(h.fc3_i) +
+                   scaled_bytes(h.fc3_blk, h.fc3_atoms, h, 27, 27, 0) + 2 * ws_round(sizeof(double) * nb) +
+                   ws_round(sizeof(int) * nb);
+        if (mode == KALD_BF16_SPLIT)
+            b += tc_gamma_scratch_bytes(nb, ctx->sm_count) + ws_round(sizeof(int2) * n_tiles + sizeof(int) * (nb + 1)) +
+                 ws_round(sizeof(double) * n_tiles);
+        else
+            b += 4 * ws_round(rs * nn) + ws_round(sizeof(double) * nb * (size_t)gp.n_part);
+        if (!d_nu) b += ws_round(sizeof(double) * nb);
+        if (!d_eig) b += ws_round(sizeof(double2) * nn);
+        if (!d_g) b += ws_round(sizeof(double) * nb);
+        it.need = b;
+        need += b;
+    }
+    if ((st = ws_reserve(ctx, need))) return st;
+    // per-system counters: allowed triplets (8 B) and the wait-failure flag (4 B)
+    char *counters = static_cast<char *>(ws_take(ctx, 32 * items.size()));
+    cudaMemsetAsync(counters, 0, 32 * items.size(), ctx->stream);
+    struct Dev { GammaDev gd; double *g_d; };
+    std::vector<Dev> devs(items.size());
+    for (size_t t = 0; t < items.size(); ++t) {
+        Item &it = items[t];
+        const HostSystem &h = *it.hp;
+        const int nb = h.nb;
+        const size_t nn = (size_t)nb * nb;
+        const size_t n_tiles = std::max<size_t>(it.gp.tiles.size(), 1);
+        GammaDev &gd = devs[t].gd;
+        gd.group_jk = upload(ctx, it.gjk);
+        gd.group_start = upload(ctx, h.pair3_start);
+        gd.blk_i = upload(ctx, h.fc3_i);
+        gd.fc3 = static_cast<const double *>(upload_scaled(ctx, h.fc3_blk, h.fc3_atoms, h, 27, 27, 0));
+        gd.nu = stage_in(ctx, nu_thz + it.off_nb, (size_t)nb, d_nu);
+        gd.eig = stage_in(ctx, reinterpret_cast<const double2 *>(eigvec) + it.off_eig, nn, d_eig);
+        gd.omega = static_cast<double *>(ws_take(ctx, sizeof(double) * nb));
+        gd.occ = static_cast<double *>(ws_take(ctx, sizeof(double) * nb));
+        gd.E = gd.Y = gd.T = gd.PHI = nullptr;
+        gd.partial = nullptr;
+        gd.tc_scratch = nullptr; gd.tiles_dev = nullptr; gd.partial_tc = nullptr;
+        if (mode == KALD_BF16_SPLIT) {
+            gd.tc_scratch = ws_take(ctx, tc_gamma_scratch_bytes(nb, ctx->sm_count));
+            gd.tiles_dev = static_cast<int2 *>(ws_take(ctx, sizeof(int2) * n_tiles + sizeof(int) * (nb + 1)));
+            gd.partial_tc = static_cast<double *>(ws_take(ctx, sizeof(double) * n_tiles));
+        } else {
+            gd.E = ws_take(ctx, rs * nn);
+            gd.Y = ws_take(ctx, rs * nn);
+            gd.T = ws_take(ctx, rs * nn);
+            gd.PHI = ws_take(ctx, rs * nn);
+            gd.partial = static_cast<double *>(ws_take(ctx, sizeof(double) * nb * (size_t)it.gp.n_part));
+        }
+        gd.order = static_cast<int *>(ws_take(ctx, sizeof(int) * nb));
+        gd.allowed = reinterpret_cast<unsigned long long *>(counters + 32 * t);
+        gd.err = reinterpret_cast<int *>(counters + 32 * t + 16);
+        devs[t].g_d = d_g ? gamma + it.off_nb : static_cast<double *>(ws_take(ctx, sizeof(double) * nb));
+    }
+    std::vector<cudaStream_t> lanes;
+    const int n_lanes = (int)std::min<size_t>(items.size(), 4);
+    if ((st = get_lanes(ctx, n_lanes, lanes))) return st;
+    cudaError_t e = fork_lanes(ctx, lanes);
+    for (size_t t = 0; t < items.size() && e == cudaSuccess; ++t) {
+        const HostSystem &h = *items[t].hp;
+        LwParams p;
+        p.nb = h.nb; p.nq = 1;
+        p.mesh[0] = p.mesh[1] = p.mesh[2] = 1;
+        p.n_rep = 0; p.n_rounds = 0; p.qp_chunk = 1; p.n_chunks = 1;
+        p.q0 = 0; p.q1 = 1;
+        p.sigma_w = kTwoPi * opt->sigma_thz;
+        p.cut_w = opt->n_sigma * p.sigma_w;
+        p.T = opt->temperature_K;
+        p.classical = opt->classical ? 1 : 0;
+        p.omega_min_w = kTwoPi * opt->omega_min_thz;
+        p.wait_limit = ctx->wait_limit;
+        p.prof = &ctx->prof;
+        e = launch_gamma_only(items[t].gp, devs[t].gd, p, mode, opt->degen_tol_thz, devs[t].g_d,
+                              lanes[t % lanes.size()]);
+    }
+    const cudaError_t ej = join_lanes(ctx, lanes);       // always, so nothing runs on past the call
+    if (e == cudaSuccess) e = ej;
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(ctx->stream);
+        return cuda_check(ctx, e, "kald_linewidths (Gamma-only) launch");
+    }
+    std::vector<char> cnt_h(32 * items.size());
+    cudaMemcpyAsync(cnt_h.data(), counters, cnt_h.size(), cudaMemcpyDeviceToHost, ctx->stream);
+    for (size_t t = 0; t < items.size(); ++t)
+        if (!d_g)
+            cudaMemcpyAsync(gamma + items[t].off_nb, devs[t].g_d, sizeof(double) * items[t].hp->nb,
+                            cudaMemcpyDeviceToHost, ctx->stream);
+    if ((st = finish(ctx, "kald_linewidths"))) return st;
+    for (size_t t = 0; t < items.size(); ++t) {
+        unsigned long long al;
+        int errf;
+        std::memcpy(&al, cnt_h.data() + 32 * t, sizeof(al));
+        std::memcpy(&errf, cnt_h.data() + 32 * t + 16, sizeof(errf));
+        if (errf) return fail(ctx, KALD_E_TIMEOUT, "kald_linewidths: a tensor-core pipeline wait expired");
+        const uint64_t nb = (uint64_t)items[t].hp->nb;
+        tot += nb * nb * nb;
+        allowed_tot += al;
+    }
+    return KALD_OK;
+}
+
 // Linewidths of every system (q_end < 0), or of the q-points [q_begin, q_end)
 // of one crystal.
 static kald_status linewidths_impl(kald_ctx *ctx, int32_t n_sys, const kald_system *sys,
@@ -729,6 +1021,12 @@ static kald_status linewidths_impl(kald_ctx *ctx, int32_t n_sys, const kald_syst
     const bool d_nu = is_device_ptr(nu_thz), d_eig = is_device_ptr(eigvec), d_g = is_device_ptr(gamma);
     const int fp32 = opt->precision == KALD_FP32;
     uint64_t tot = 0, allowed_tot = 0;
+    if (nq_mesh == 1) {
+        // every Gamma-only supercell (nb > 96) of the call in one launch sequence
+        if ((st = gamma_only_batch(ctx, n_sys, sys, nu_thz, eigvec, opt, gamma, d_nu, d_eig, d_g, tot,
+                                   allowed_tot)))
+            return st;
+    }
     size_t off_nb = 0, off_eig = 0;
     for (int x = 0; x < n_sys; ++x) {
         std::shared_ptr<const HostSystem> hp;
@@ -738,97 +1036,9 @@ static kald_status linewidths_impl(kald_ctx *ctx, int32_t n_sys, const kald_syst
         if (nb > kMaxNbSmall && nq_mesh != 1)
             return fail(ctx, KALD_E_UNSUPPORTED, "kald_linewidths: nb > 96 needs mesh {1,1,1}");
         if (nb > kMaxNbSmall) {
-            // (a q range of a Gamma-only system is the whole system: [0, 1))
-            // ---- Gamma-only path, mode by mode
-            const size_t nn = (size_t)nb * nb;
-            GammaPlan gp;
-            gp.n_groups = (int)h.pair3_j.size();
-            gp.n_part = std::max(1, 2 * ctx->sm_count);
-            gp.sms = std::max(1, ctx->sm_count);
-            std::vector<double> nu_h(nb);
-            if (d_nu) cudaMemcpy(nu_h.data(), nu_thz + off_nb, sizeof(double) * nb, cudaMemcpyDeviceToHost);
-            else std::copy(nu_thz + off_nb, nu_thz + off_nb + nb, nu_h.begin());
-            gp.omega_h.resize(nb);
-            for (int m = 0; m < nb; ++m) {
-                const double w = kTwoPi * nu_h[m];
-                gp.omega_h[m] = (std::isfinite(w) && w > kTwoPi * opt->omega_min_thz) ? w : 0.0;
-            }
-            std::vector<int> gjk(2 * (size_t)gp.n_groups);
-            for (int g = 0; g < gp.n_groups; ++g) { gjk[2 * g] = h.pair3_j[g]; gjk[2 * g + 1] = h.pair3_k[g]; }
-            const int mode = opt->precision;     // 0 FP64, 1 FP32, 2 BF16 split (tensor cores)
-            const size_t rs = fp32 ? sizeof(float) : sizeof(double);
-            if (mode == KALD_BF16_SPLIT) {
-                if (h.fc3_symmetric < 0) h.fc3_symmetric = fc3_symmetric_last_two(&sys[x]) ? 1 : 0;
-                gp.symmetric = h.fc3_symmetric;
-                band_tiles(gp.omega_h, tc_tile(), opt->n_sigma * kTwoPi * opt->sigma_thz, gp.symmetric,
-                           gp.tiles, gp.tile_start);
-            }
-            const size_t n_tiles = std::max<size_t>(gp.tiles.size(), 1);
-            size_t need = bytes_of(gjk) + bytes_of(h.pair3_start) + bytes_of(h.fc3_i) +
-                          scaled_bytes(h.fc3_blk, h.fc3_atoms, h, 27, 27, 0) +
-                          2 * ws_round(sizeof(double) * nb) + ws_round(sizeof(int) * nb) + ws_round(16) +
-                          ws_round(16);
-            if (mode == KALD_BF16_SPLIT)
-                need += tc_gamma_scratch_bytes(nb, ctx->sm_count) + ws_round(sizeof(int2) * n_tiles + sizeof(int) * (nb + 1)) +
-                        ws_round(sizeof(double) * n_tiles);
-            else
-                need += 4 * ws_round(rs * nn) + ws_round(sizeof(double) * nb * (size_t)gp.n_part);
-            if (!d_nu) need += ws_round(sizeof(double) * nb);
-            if (!d_eig) need += ws_round(sizeof(double2) * nn);
-            if (!d_g) need += ws_round(sizeof(double) * nb);
-            if ((st = ws_reserve(ctx, need))) return st;
-            GammaDev gd;
-            gd.group_jk = upload(ctx, gjk);
-            gd.group_start = upload(ctx, h.pair3_start);
-            gd.blk_i = upload(ctx, h.fc3_i);
-            gd.fc3 = static_cast<const double *>(upload_scaled(ctx, h.fc3_blk, h.fc3_atoms, h, 27, 27, 0));
-            gd.nu = stage_in(ctx, nu_thz + off_nb, (size_t)nb, d_nu);
-            gd.eig = stage_in(ctx, reinterpret_cast<const double2 *>(eigvec) + off_eig, nn, d_eig);
-            gd.omega = static_cast<double *>(ws_take(ctx, sizeof(double) * nb));
-            gd.occ = static_cast<double *>(ws_take(ctx, sizeof(double) * nb));
-            gd.E = gd.Y = gd.T = gd.PHI = nullptr;
-            gd.partial = nullptr;
-            gd.tc_scratch = nullptr; gd.tiles_dev = nullptr; gd.partial_tc = nullptr;
-            if (mode == KALD_BF16_SPLIT) {
-                gd.tc_scratch = ws_take(ctx, tc_gamma_scratch_bytes(nb, ctx->sm_count));
-                gd.tiles_dev = static_cast<int2 *>(ws_take(ctx, sizeof(int2) * n_tiles + sizeof(int) * (nb + 1)));
-                gd.partial_tc = static_cast<double *>(ws_take(ctx, sizeof(double) * n_tiles));
-            } else {
-                gd.E = ws_take(ctx, rs * nn);
-                gd.Y = ws_take(ctx, rs * nn);
-                gd.T = ws_take(ctx, rs * nn);
-                gd.PHI = ws_take(ctx, rs * nn);
-                gd.partial = static_cast<double *>(ws_take(ctx, sizeof(double) * nb * (size_t)gp.n_part));
-            }
-            gd.order = static_cast<int *>(ws_take(ctx, sizeof(int) * nb));
-            gd.allowed = static_cast<unsigned long long *>(ws_take(ctx, 16));
-            gd.err = static_cast<int *>(ws_take(ctx, 16));
-            double *g_d = d_g ? gamma + off_nb : static_cast<double *>(ws_take(ctx, sizeof(double) * nb));
-            LwParams p;
-            p.nb = nb; p.nq = 1;
-            p.mesh[0] = p.mesh[1] = p.mesh[2] = 1;
-            p.n_rep = 0; p.n_rounds = 0; p.qp_chunk = 1; p.n_chunks = 1;
-            p.sigma_w = kTwoPi * opt->sigma_thz;
-            p.cut_w = opt->n_sigma * p.sigma_w;
-            p.T = opt->temperature_K;
-            p.classical = opt->classical ? 1 : 0;
-            p.omega_min_w = kTwoPi * opt->omega_min_thz;
-            p.wait_limit = ctx->wait_limit;
-            p.prof = &ctx->prof;
-            cudaMemsetAsync(gd.err, 0, sizeof(int), ctx->stream);
-            cudaError_t e = launch_gamma_only(gp, gd, p, mode, opt->degen_tol_thz, g_d, ctx->stream);
-            if (e != cudaSuccess) return cuda_check(ctx, e, "kald_linewidths (Gamma-only) launch");
-            unsigned long long al = 0;
-            int errf = 0;
-            cudaMemcpyAsync(&al, gd.allowed, sizeof(al), cudaMemcpyDeviceToHost, ctx->stream);
-            cudaMemcpyAsync(&errf, gd.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
-            if (!d_g) cudaMemcpyAsync(gamma + off_nb, g_d, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->stream);
-            if ((st = finish(ctx, "kald_linewidths"))) return st;
-            if (errf) return fail(ctx, KALD_E_TIMEOUT, "kald_linewidths: a tensor-core pipeline wait expired");
-            tot += (uint64_t)nb * nb * nb;
-            allowed_tot += al;
+            // Gamma-only systems were all computed by gamma_only_batch above
             off_nb += nb;
-            off_eig += nn;
+            off_eig += (size_t)nb * nb;
             continue;
         }
         std::vector<double> qc;
@@ -1074,57 +1284,95 @@ kald_status kald_kappa_qhgk(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
     if (!nu_thz || !eigvec || !gamma || !kappa) return fail(ctx, KALD_E_INVALID, "NULL array");
     const bool d_nu = is_device_ptr(nu_thz), d_eig = is_device_ptr(eigvec), d_g = is_device_ptr(gamma);
     const bool d_k = is_device_ptr(kappa), d_v = vgen && is_device_ptr(vgen);
-    size_t off_nb = 0, off_eig = 0;
-    for (int x = 0; x < n_sys; ++x) {
+    // all systems planned first, one workspace reservation, the systems dealt
+    // over concurrent lane streams, one synchronisation at the end
+    struct Item {
         std::shared_ptr<const HostSystem> hp;
-        if ((st = plan_system_cached(ctx, &sys[x], hp))) return st;
-        const HostSystem &h = *hp;
+        std::vector<int> row_start, col_j;
+        size_t off_nb, off_eig;
+        int n_partial;
+    };
+    std::vector<Item> items(n_sys);
+    size_t need = 0, off_nb = 0, off_eig = 0;
+    for (int x = 0; x < n_sys; ++x) {
+        Item &it = items[x];
+        if ((st = plan_system_cached(ctx, &sys[x], it.hp))) return st;
+        const HostSystem &h = *it.hp;
         const int nb = h.nb;
         const size_t nn = (size_t)nb * nb;
         // CSR by row atom i: the (i, j) sorted fc2 order is contiguous in i
-        std::vector<int> row_start(h.n_atoms + 1, 0), col_j(h.fc2_blk.size() / 9);
+        it.row_start.assign(h.n_atoms + 1, 0);
+        it.col_j.assign(h.fc2_blk.size() / 9, 0);
         for (size_t p = 0; p < h.pair2_i.size(); ++p)
             for (int b = h.pair2_start[p]; b < h.pair2_start[p + 1]; ++b) {
-                col_j[b] = h.pair2_j[p];
-                row_start[h.pair2_i[p] + 1]++;
+                it.col_j[b] = h.pair2_j[p];
+                it.row_start[h.pair2_i[p] + 1]++;
             }
-        for (int i = 0; i < h.n_atoms; ++i) row_start[i + 1] += row_start[i];
-        const int n_partial = std::min(nb, 4 * std::max(1, ctx->sm_count));
-        size_t need = bytes_of(row_start) + bytes_of(col_j) + scaled_bytes(h.fc2_blk, h.fc2_atoms, h, 9, 9, 0) +
-                      bytes_of(h.fc2_dist) +
-                      ws_round(sizeof(double) * nn) + 2 * ws_round(sizeof(double) * 3 * nn) +
-                      ws_round(sizeof(double) * (9 * (size_t)n_partial + nb)) + ws_round(72);
+        for (int i = 0; i < h.n_atoms; ++i) it.row_start[i + 1] += it.row_start[i];
+        it.n_partial = std::min(nb, 4 * std::max(1, ctx->sm_count));
+        it.off_nb = off_nb;
+        it.off_eig = off_eig;
+        need += bytes_of(it.row_start) + bytes_of(it.col_j) + scaled_bytes(h.fc2_blk, h.fc2_atoms, h, 9, 9, 0) +
+                bytes_of(h.fc2_dist) + ws_round(sizeof(double) * nn) + 2 * ws_round(sizeof(double) * 3 * nn) +
+                ws_round(sizeof(double) * (9 * (size_t)it.n_partial + nb)) + ws_round(72);
         if (!d_nu) need += ws_round(sizeof(double) * nb);
         if (!d_eig) need += ws_round(sizeof(double2) * nn);
         if (!d_g) need += ws_round(sizeof(double) * nb);
-        if ((st = ws_reserve(ctx, need))) return st;
-        DevFc2Dist f;
-        f.n_rows = h.n_atoms;
-        f.row_start = upload(ctx, row_start);
-        f.col_j = upload(ctx, col_j);
-        f.blk = static_cast<const double *>(upload_scaled(ctx, h.fc2_blk, h.fc2_atoms, h, 9, 9, 0));
-        f.dist = upload(ctx, h.fc2_dist);
-        const double *nu_d = stage_in(ctx, nu_thz + off_nb, (size_t)nb, d_nu);
-        const double2 *eig_d = stage_in(ctx, reinterpret_cast<const double2 *>(eigvec) + off_eig, nn, d_eig);
-        const double *g_d = stage_in(ctx, gamma + off_nb, (size_t)nb, d_g);
-        double *E = static_cast<double *>(ws_take(ctx, sizeof(double) * nn));
-        double *B = static_cast<double *>(ws_take(ctx, sizeof(double) * 3 * nn));
-        double *W = static_cast<double *>(ws_take(ctx, sizeof(double) * 3 * nn));
-        double *partial = static_cast<double *>(ws_take(ctx, sizeof(double) * (9 * (size_t)n_partial + nb)));
-        double *k_d = d_k ? kappa + 9 * (size_t)x : static_cast<double *>(ws_take(ctx, 72));
-        const double scale = kKappaSI / h.volume;
-        cudaError_t e = launch_qhgk(f, nb, nu_d, eig_d, g_d, opt->temperature_K, opt->classical,
-                                    opt->omega_min_thz, opt->degen_tol_thz, E, B, W, partial, n_partial,
-                                    k_d, scale, ctx->stream);
-        if (e != cudaSuccess) return cuda_check(ctx, e, "kald_kappa_qhgk launch");
-        if (!d_k) cudaMemcpyAsync(kappa + 9 * (size_t)x, k_d, 72, cudaMemcpyDeviceToHost, ctx->stream);
-        if (vgen && x == 0)
-            cudaMemcpyAsync(vgen, W, sizeof(double) * 3 * nn,
-                            d_v ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream);
-        if ((st = finish(ctx, "kald_kappa_qhgk"))) return st;
         off_nb += nb;
         off_eig += nn;
     }
+    if ((st = ws_reserve(ctx, need))) return st;
+    struct Dev {
+        DevFc2Dist f;
+        const double *nu, *g;
+        const double2 *eig;
+        double *E, *B, *W, *partial, *k;
+    };
+    std::vector<Dev> devs(n_sys);
+    for (int x = 0; x < n_sys; ++x) {
+        Item &it = items[x];
+        const HostSystem &h = *it.hp;
+        const int nb = h.nb;
+        const size_t nn = (size_t)nb * nb;
+        Dev &dv = devs[x];
+        dv.f.n_rows = h.n_atoms;
+        dv.f.row_start = upload(ctx, it.row_start);
+        dv.f.col_j = upload(ctx, it.col_j);
+        dv.f.blk = static_cast<const double *>(upload_scaled(ctx, h.fc2_blk, h.fc2_atoms, h, 9, 9, 0));
+        dv.f.dist = upload(ctx, h.fc2_dist);
+        dv.nu = stage_in(ctx, nu_thz + it.off_nb, (size_t)nb, d_nu);
+        dv.eig = stage_in(ctx, reinterpret_cast<const double2 *>(eigvec) + it.off_eig, nn, d_eig);
+        dv.g = stage_in(ctx, gamma + it.off_nb, (size_t)nb, d_g);
+        dv.E = static_cast<double *>(ws_take(ctx, sizeof(double) * nn));
+        dv.B = static_cast<double *>(ws_take(ctx, sizeof(double) * 3 * nn));
+        dv.W = static_cast<double *>(ws_take(ctx, sizeof(double) * 3 * nn));
+        dv.partial = static_cast<double *>(ws_take(ctx, sizeof(double) * (9 * (size_t)it.n_partial + nb)));
+        dv.k = d_k ? kappa + 9 * (size_t)x : static_cast<double *>(ws_take(ctx, 72));
+    }
+    std::vector<cudaStream_t> lanes;
+    if ((st = get_lanes(ctx, std::min(n_sys, 4), lanes))) return st;
+    cudaError_t e = fork_lanes(ctx, lanes);
+    for (int x = 0; x < n_sys && e == cudaSuccess; ++x) {
+        const Dev &dv = devs[x];
+        const HostSystem &h = *items[x].hp;
+        e = launch_qhgk(dv.f, h.nb, dv.nu, dv.eig, dv.g, opt->temperature_K, opt->classical, opt->omega_min_thz,
+                        opt->degen_tol_thz, dv.E, dv.B, dv.W, dv.partial, items[x].n_partial, dv.k,
+                        kKappaSI / h.volume, lanes[x % lanes.size()]);
+    }
+    const cudaError_t ej = join_lanes(ctx, lanes);
+    if (e == cudaSuccess) e = ej;
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(ctx->stream);
+        return cuda_check(ctx, e, "kald_kappa_qhgk launch");
+    }
+    for (int x = 0; x < n_sys; ++x)
+        if (!d_k) cudaMemcpyAsync(kappa + 9 * (size_t)x, devs[x].k, 72, cudaMemcpyDeviceToHost, ctx->stream);
+    if (vgen) {
+        const size_t nn0 = (size_t)items[0].hp->nb * items[0].hp->nb;
+        cudaMemcpyAsync(vgen, devs[0].W, sizeof(double) * 3 * nn0,
+                        d_v ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream);
+    }
+    if ((st = finish(ctx, "kald_kappa_qhgk"))) return st;
     return KALD_OK;
 }
 

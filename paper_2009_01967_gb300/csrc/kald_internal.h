@@ -83,6 +83,7 @@ struct kald_ctx {
     uint32_t wait_limit = kald::kDefaultWaitPolls;   // polls of the pipeline waits
     size_t ws_limit = 0;                           // workspace cap in bytes (0: none)
     kald::Prof prof;                               // optional per-launch timing
+    std::vector<cudaStream_t> lanes;               // extra streams for concurrent systems (lazy)
     // host plans of recently seen systems, keyed by a 128-bit hash of their
     // whole content (oldest first)
     struct Plan {
@@ -174,8 +175,21 @@ cudaError_t launch_jacobi(int nb, int nq, double2 *A, double2 *V, double *nu_thz
 size_t eigh_large_scratch_bytes(int n);
 // n >= 3 and three length-n FP64 vectors fit in one CTA's shared memory
 bool eigh_large_supported(int n, size_t smem_optin);
-cudaError_t launch_eigh_large(int n, const double2 *D, double *scratch, double *nu_out,
-                              double2 *eig_out, int sms, size_t smem_optin, cudaStream_t st);
+// One system of a batched large eigensolve: D [n][n] in, scratch of
+// eigh_large_scratch_bytes(n), frequencies (THz) and row-major eigenvectors out.
+struct EighJob {
+    int n;
+    const double2 *D;
+    double *scratch;
+    double *nu_out;
+    double2 *eig_out;
+};
+// Device records of a batch (eigh_batch_records_bytes(n_sys) of workspace).
+size_t eigh_batch_records_bytes(int n_sys);
+// The eigensolves of n_sys (<= 64) systems as one launch sequence; each
+// system's results equal those of a solve of it alone.
+cudaError_t launch_eigh_large_batch(int n_sys, const EighJob *jobs, void *records, int sms, size_t smem_optin,
+                                    cudaStream_t st);
 cudaError_t launch_velocity_diag(const DevFc2 &f, int nb, int nq, const double *qcart,
                                  const double *nu_thz, const double2 *eig, double *vel,
                                  cudaStream_t st);

@@ -721,3 +721,49 @@ def test_qrange_calls_concatenate_to_the_full_call(k, case, precision):
     with pytest.raises(kk.KaldError) as e:
         kk.kald_linewidths_qrange(ctx, s, w.mesh, nu_o, eig_o, opt, 2, 2)
     assert e.value.status == 1
+
+
+# ---------------------------------------------------------------- batched Gamma-only calls
+def test_phonons_batch_equals_one_call_per_system(k, c4w):
+    """kald_phonons_batch over supercells of 108, 256 and 500 atoms (and a
+    32-atom cell that takes the per-q solver) gives, bit for bit, the
+    eigenpairs of one kald_phonons call per system."""
+    kk, ctx = k
+    w, _ = c4w
+    systems = [w.systems[0], w.systems[9], ki.fcc_supercell_system(2, seed=5), w.systems[17], w.systems[1]]
+    nu_b, eig_b = kk.kald_phonons_batch(ctx, systems)
+    o_m, o_e = 0, 0
+    for s in systems:
+        nb = s.n_branches
+        nu1, eig1, _ = kk.kald_phonons(ctx, s, (1, 1, 1), want_vel=False)
+        np.testing.assert_array_equal(nu_b[o_m:o_m + nb], np.ravel(nu1))
+        np.testing.assert_array_equal(eig_b[o_e:o_e + nb * nb], np.ravel(eig1))
+        o_m += nb
+        o_e += nb * nb
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16split"])
+def test_batched_mixed_sizes_match_single_calls(k, c4w, precision):
+    """One kald_linewidths and one kald_kappa_qhgk call over supercells of 324,
+    768 and 1500 modes (the sizes of the batched workload, dealt over
+    concurrent streams) equal one call per system bit for bit."""
+    kk, ctx = k
+    w, ph_all = c4w
+    pick = [2, 10, 18] if precision == "bf16split" else [2, 10]
+    systems = [w.systems[x] for x in pick]
+    opt = _opts(kk, w, precision)
+    nu = np.ascontiguousarray(np.concatenate([ph_all[x][0].ravel() for x in pick]))
+    eig = np.ascontiguousarray(np.concatenate([ph_all[x][1].ravel() for x in pick]))
+    g, (tot, allowed) = kk.kald_linewidths(ctx, systems, (1, 1, 1), nu, eig, opt)
+    kap, _ = kk.kald_kappa_qhgk(ctx, systems, nu, eig, g, opt)
+    o, t_sum, a_sum = 0, 0, 0
+    for j, x in enumerate(pick):
+        nb = w.systems[x].n_branches
+        g1, (t1, a1) = kk.kald_linewidths(ctx, w.systems[x], (1, 1, 1), ph_all[x][0], ph_all[x][1], opt)
+        np.testing.assert_array_equal(g[o:o + nb], np.ravel(g1))
+        k1, _ = kk.kald_kappa_qhgk(ctx, [w.systems[x]], ph_all[x][0], ph_all[x][1], np.ravel(g1), opt)
+        np.testing.assert_array_equal(kap[j], k1[0])
+        t_sum += t1
+        a_sum += a1
+        o += nb
+    assert tot == t_sum and allowed == a_sum
