@@ -402,6 +402,9 @@ def run_kald(args):
     offs_e = np.cumsum([0] + [nq * b * b for b in nbs])
 
     def phon(nu_t, eig_t):
+        if gamma_only and len(w.systems) > 1:      # every supercell in one launch sequence
+            kk.kald_phonons_batch(ctx, w.systems, nu_thz=nu_t, eigvec=eig_t)
+            return
         for x, sx in enumerate(w.systems):
             kk.kald_phonons(ctx, sx, w.mesh, nu_thz=nu_t[offs_m[x]:offs_m[x + 1]],
                             eigvec=eig_t[offs_e[x]:offs_e[x + 1]], want_vel=False)
