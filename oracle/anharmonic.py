@@ -26,7 +26,9 @@ Readings where the paper is silent or inconsistent:
     are both included; the 1/N_k is pinned by the supercell folding test;
   * delta is a Gaussian in angular frequency with standard deviation
     2 pi sigma (sigma in THz), truncated at |d nu| < n_sigma sigma (strict),
-    not renormalised;
+    not renormalised; the Lorentzian (half width at half maximum 2 pi sigma)
+    and the triangle (half base 2 pi sigma) of the code's options are
+    truncated the same way (`delta` argument);
   * modes with nu < omega_min are excluded as mu, mu' and mu'' (their gamma is 0);
   * gamma is averaged over degenerate sets |d nu| < degen_tol at each q.
 Units: gamma in ps^-1 (an angular-frequency rate), tau = 1 / (2 gamma) in ps.
@@ -60,6 +62,38 @@ def gaussian_delta(d_omega, sigma_omega, n_sigma):
     d_omega = np.asarray(d_omega)
     g = np.exp(-0.5 * (d_omega / sigma_omega) ** 2) / (np.sqrt(2 * np.pi) * sigma_omega)
     return np.where(np.abs(d_omega) < n_sigma * sigma_omega, g, 0.0)
+
+
+def lorentzian_delta(d_omega, sigma_omega, n_sigma):
+    """Lorentzian delta (ps), half width at half maximum sigma:
+    (sigma / pi) / (d^2 + sigma^2), zero for |d| >= n_sigma sigma."""
+    d_omega = np.asarray(d_omega)
+    g = (sigma_omega / np.pi) / (d_omega ** 2 + sigma_omega ** 2)
+    return np.where(np.abs(d_omega) < n_sigma * sigma_omega, g, 0.0)
+
+
+def triangular_delta(d_omega, sigma_omega, n_sigma):
+    """Triangular delta (ps) of half base sigma: (1 - |d| / sigma) / sigma for
+    |d| < sigma, and zero for |d| >= n_sigma sigma as for the other shapes."""
+    d_omega = np.asarray(d_omega)
+    g = np.maximum(0.0, 1.0 - np.abs(d_omega) / sigma_omega) / sigma_omega
+    return np.where(np.abs(d_omega) < n_sigma * sigma_omega, g, 0.0)
+
+
+DELTA_SHAPES = ("gaussian", "lorentzian", "triangular")
+
+
+def energy_delta(d_omega, sigma_omega, n_sigma, shape="gaussian"):
+    """The energy-conservation delta of Eq. phase_space in one of the three
+    shapes the code-details options list (reading: sigma = 2 pi sigma_THz is
+    the standard deviation, the half width at half maximum, or the half base)."""
+    if shape == "gaussian":
+        return gaussian_delta(d_omega, sigma_omega, n_sigma)
+    if shape == "lorentzian":
+        return lorentzian_delta(d_omega, sigma_omega, n_sigma)
+    if shape == "triangular":
+        return triangular_delta(d_omega, sigma_omega, n_sigma)
+    raise ValueError(f"unknown delta shape {shape!r}")
 
 
 def mesh_index(mesh, k):
@@ -120,7 +154,7 @@ def projections(sys, mesh, eps, q, qp_list, process, S=None):
 
 def linewidths(sys, mesh, nu, eig, T, sigma_thz, n_sigma=3.0, omega_min_thz=0.01,
                degen_tol_thz=1e-5, classical=False, q_list=None, average=True,
-               return_parts=False):
+               return_parts=False, delta="gaussian"):
     """gamma [len(q_list), nb] in ps^-1 for the crystal on the mesh.
 
     Both processes are computed literally: for each q' the + triplet uses
@@ -154,9 +188,9 @@ def linewidths(sys, mesh, nu, eig, T, sigma_thz, n_sigma=3.0, omega_min_thz=0.01
                 npr = n[qps][:, None, :, None]
                 npp = n[qpp][:, None, None, :]
                 if proc == "+":
-                    g = (npr - npp) * gaussian_delta(w + wp - wpp, sig_w, n_sigma)
+                    g = (npr - npp) * energy_delta(w + wp - wpp, sig_w, n_sigma, delta)
                 else:
-                    g = 0.5 * (1.0 + npr + npp) * gaussian_delta(w - wp - wpp, sig_w, n_sigma)
+                    g = 0.5 * (1.0 + npr + npp) * energy_delta(w - wp - wpp, sig_w, n_sigma, delta)
                 mask = (valid[q][None, :, None, None] & valid[qps][:, None, :, None]
                         & valid[qpp][:, None, None, :])
                 wt = (g * inv_w[q][None, :, None, None] * inv_w[qps][:, None, :, None]
@@ -176,7 +210,7 @@ def linewidths(sys, mesh, nu, eig, T, sigma_thz, n_sigma=3.0, omega_min_thz=0.01
 
 
 def phase_space(mesh, nu, T, sigma_thz, n_sigma=3.0, omega_min_thz=0.01, classical=False,
-                return_parts=False):
+                return_parts=False, delta="gaussian"):
     """Normalised phase space per mode g_mu = (1/N_k) sum_{mu' mu''} g_{mu mu' mu''}
     (Eq. phase_space and the definition after Eq. delta_deconstructed), [N_k, nb]
     in ps: the weights of Eq. phase_space over the momentum-conserving
@@ -202,10 +236,10 @@ def phase_space(mesh, nu, T, sigma_thz, n_sigma=3.0, omega_min_thz=0.01, classic
             mask = (valid[q][None, :, None, None] & valid[qps][:, None, :, None]
                     & valid[qpp][:, None, None, :])
             if sign == 1:
-                g = (npr - npp) * gaussian_delta(w + wp - wpp, sig_w, n_sigma)
+                g = (npr - npp) * energy_delta(w + wp - wpp, sig_w, n_sigma, delta)
                 g_plus[q] += np.sum(np.where(mask, g, 0.0), axis=(0, 2, 3)) / nq
             else:
-                g = 0.5 * (1.0 + npr + npp) * gaussian_delta(w - wp - wpp, sig_w, n_sigma)
+                g = 0.5 * (1.0 + npr + npp) * energy_delta(w - wp - wpp, sig_w, n_sigma, delta)
                 g_minus[q] += np.sum(np.where(mask, g, 0.0), axis=(0, 2, 3)) / nq
     if return_parts:
         return g_plus + g_minus, g_plus, g_minus
@@ -213,7 +247,7 @@ def phase_space(mesh, nu, T, sigma_thz, n_sigma=3.0, omega_min_thz=0.01, classic
 
 
 def scattering_matrix(sys, mesh, nu, eig, T, sigma_thz, n_sigma=3.0, omega_min_thz=0.01,
-                      classical=False):
+                      classical=False, delta="gaussian"):
     """The full linearised-BTE scattering operator of section "Boltzman
     Transport Equation": Gamma~_{mu mu'} = delta_{mu mu'} Gamma^0_mu + Gamma^1_{mu mu'}
     with (flat mode index mu = q nb + s)
@@ -253,9 +287,9 @@ def scattering_matrix(sys, mesh, nu, eig, T, sigma_thz, n_sigma=3.0, omega_min_t
             npr = n[qps][:, None, :, None]
             npp = n[qpp][:, None, None, :]
             if proc == "+":
-                g = (npr - npp) * gaussian_delta(w + wp - wpp, sig_w, n_sigma)
+                g = (npr - npp) * energy_delta(w + wp - wpp, sig_w, n_sigma, delta)
             else:
-                g = 0.5 * (1.0 + npr + npp) * gaussian_delta(w - wp - wpp, sig_w, n_sigma)
+                g = 0.5 * (1.0 + npr + npp) * energy_delta(w - wp - wpp, sig_w, n_sigma, delta)
             mask = (valid[q][None, :, None, None] & valid[qps][:, None, :, None]
                     & valid[qpp][:, None, None, :])
             rate = pref * np.where(mask, g * inv_w[q][None, :, None, None] * inv_w[qps][:, None, :, None]
@@ -300,7 +334,8 @@ def fc3_mode_matrix(sys, eps_mode):
 
 
 def linewidths_gamma_only(sys, nu, eig, T, sigma_thz, n_sigma=3.0, omega_min_thz=0.01,
-                          degen_tol_thz=1e-5, classical=False, modes=None, average=True):
+                          degen_tol_thz=1e-5, classical=False, modes=None, average=True,
+                          delta="gaussian"):
     """gamma [len(modes)] (ps^-1) of a Gamma-only supercell with real
     eigenvectors eig [1, nb, nb].  At q = q' = q'' = 0 all phases are 1 and
     phi^+ = phi^- (eta real), so phi(mu, mu', mu'') = eps_mu'^T Y_mu eps_mu''
@@ -328,8 +363,8 @@ def linewidths_gamma_only(sys, nu, eig, T, sigma_thz, n_sigma=3.0, omega_min_thz
         Y = fc3_mode_matrix(sys, eps[mu])
         phi = eps @ Y @ eps.T
         w = omega[mu]
-        g = ((npr - npp) * gaussian_delta(w + wp - wpp, sig_w, n_sigma)
-             + 0.5 * (1.0 + npr + npp) * gaussian_delta(w - wp - wpp, sig_w, n_sigma))
+        g = ((npr - npp) * energy_delta(w + wp - wpp, sig_w, n_sigma, delta)
+             + 0.5 * (1.0 + npr + npp) * energy_delta(w - wp - wpp, sig_w, n_sigma, delta))
         wt = g * inv_w[mu] * inv_w[:, None] * inv_w[None, :]
         gamma[x] = pref * np.sum(np.where(pair_ok, wt * phi ** 2, 0.0))
     if average and len(modes) == nb:

@@ -291,3 +291,73 @@ def test_kappa_qhgk_recomputed_in_si():
     kap /= abs(np.linalg.det(s.lattice)) * ANG ** 3
     assert np.abs(kap).max() > 0
     np.testing.assert_allclose(kap_or, kap, rtol=1e-7, atol=1e-7 * np.abs(kap).max())
+
+
+# ---------------------------------------------------------------- the other delta shapes
+@pytest.mark.parametrize("sigma_w,n_sigma", [(0.1 * TWO_PI, 3.0), (0.7, 2.0)])
+def test_lorentzian_delta_is_the_truncated_cauchy_density(sigma_w, n_sigma):
+    from scipy.stats import cauchy
+    cut = n_sigma * sigma_w
+    d = np.linspace(-1.2 * cut, 1.2 * cut, 100001)
+    g = an.lorentzian_delta(d, sigma_w, n_sigma)
+    inside = np.abs(d) < cut
+    np.testing.assert_allclose(g[inside], cauchy.pdf(d[inside], scale=sigma_w), rtol=1e-13)
+    assert np.all(g[~inside] == 0.0)
+    h = 2.0 * cut / 200000
+    mid = -cut + (np.arange(200000) + 0.5) * h
+    integral = np.sum(an.lorentzian_delta(mid, sigma_w, n_sigma)) * h
+    assert abs(integral - 2.0 / np.pi * np.arctan(n_sigma)) < 1e-9
+    # half maximum at one half width
+    assert abs(an.lorentzian_delta(np.array([sigma_w]), sigma_w, n_sigma)[0] * 2.0
+               - an.lorentzian_delta(np.array([0.0]), sigma_w, n_sigma)[0]) < 1e-14 / sigma_w
+
+
+@pytest.mark.parametrize("sigma_w", [0.1 * TWO_PI, 0.7])
+def test_triangular_delta_is_the_symmetric_triangle_density(sigma_w):
+    from scipy.stats import triang
+    d = np.linspace(-2.0 * sigma_w, 2.0 * sigma_w, 100001)
+    g = an.triangular_delta(d, sigma_w, 3.0)
+    np.testing.assert_allclose(g, triang.pdf(d, 0.5, loc=-sigma_w, scale=2.0 * sigma_w), rtol=1e-12,
+                               atol=1e-14 / sigma_w)
+    h = 2.0 * sigma_w / 200000
+    mid = -sigma_w + (np.arange(200000) + 0.5) * h
+    assert abs(np.sum(an.triangular_delta(mid, sigma_w, 3.0)) * h - 1.0) < 1e-9
+
+
+@pytest.mark.parametrize("shape", ["lorentzian", "triangular"])
+@pytest.mark.parametrize("d_frac", [0.0, 0.4, 0.9])
+def test_phase_space_uses_the_chosen_shape_in_thz(shape, d_frac):
+    """Single-triplet spectrum: the phase space of mode 0 equals (n1 - n2)
+    times the library density of the chosen shape at 2 pi d, width 2 pi sigma."""
+    from scipy.stats import cauchy, triang
+    sigma = 0.1
+    d = d_frac * sigma
+    nu = _one_triplet_nu(d, 3)[None, :]
+    _check_single_triplet(nu[0], 3.0 * sigma)
+    g = an.phase_space((1, 1, 1), nu, 300.0, sigma, 3.0, delta=shape)[0, 0]
+    n = _bose_si(nu[0], 300.0)
+    sw = TWO_PI * sigma
+    dens = cauchy.pdf(TWO_PI * d, scale=sw) if shape == "lorentzian" else \
+        triang.pdf(TWO_PI * d, 0.5, loc=-sw, scale=2 * sw)
+    assert abs(g - (n[1] - n[2]) * dens) <= 1e-9 * abs((n[1] - n[2]) * dens)
+
+
+@pytest.mark.parametrize("shape", ["lorentzian", "triangular"])
+def test_linewidth_shape_ratio_matches_the_densities(shape):
+    """With one triplet in the window, gamma with a given shape over gamma with
+    the Gaussian is the ratio of the two densities at the mismatch."""
+    from scipy.stats import cauchy, triang
+    s = _gamma_only_cell()
+    _, eig = ph.phonons(s, (1, 1, 1))
+    sigma, d = 0.1, 0.03
+    nu = _one_triplet_nu(d, 12)[None, :]
+    _check_single_triplet(nu[0], 3.0 * sigma)
+    g_s = an.linewidths_gamma_only(s, nu, eig, 300.0, sigma, modes=[0], average=False, delta=shape)[0]
+    g_g = an.linewidths_gamma_only(s, nu, eig, 300.0, sigma, modes=[0], average=False)[0]
+    sw = TWO_PI * sigma
+    dens = cauchy.pdf(TWO_PI * d, scale=sw) if shape == "lorentzian" else \
+        triang.pdf(TWO_PI * d, 0.5, loc=-sw, scale=2 * sw)
+    want = dens / norm.pdf(TWO_PI * d, scale=sw)
+    assert abs(g_s / g_g - want) < 1e-12 * want
+    c = an.linewidths(s, (1, 1, 1), nu, eig, 300.0, sigma, average=False, delta=shape)[0, 0]
+    assert abs(c - g_s) < 1e-12 * g_s
