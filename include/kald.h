@@ -95,6 +95,10 @@ typedef struct {
     double degen_tol_thz;      /* degenerate sets: |d nu| < degen_tol        */
     int32_t classical;         /* 1: n = kB T / (hbar omega) (Eq. classic_n) */
     int32_t precision;         /* kald_precision                             */
+    int32_t delta_shape;       /* energy delta: 0 Gaussian (standard deviation
+                                  sigma), 1 Lorentzian (half width at half
+                                  maximum sigma), 2 triangle (half base sigma);
+                                  all truncated at |d nu| < n_sigma sigma     */
 } kald_options;
 
 /* Create a context on CUDA device `device` (own stream, empty workspace).

@@ -22,6 +22,7 @@ KALD_OK = 0
 STATUS = {0: "KALD_OK", 1: "KALD_E_INVALID", 2: "KALD_E_NOMEM", 3: "KALD_E_CUDA",
           4: "KALD_E_NOCONV", 5: "KALD_E_TIMEOUT", 6: "KALD_E_UNSUPPORTED"}
 PRECISION = {"fp64": 0, "fp32": 1, "bf16split": 2}
+DELTA_SHAPE = {"gaussian": 0, "lorentzian": 1, "triangular": 2}
 
 EXPORTS = ["kald_ctx_create", "kald_ctx_destroy", "kald_last_error", "kald_set_stream",
            "kald_phonons", "kald_linewidths", "kald_kappa_rta", "kald_kappa_qhgk",
@@ -48,7 +49,7 @@ class kald_system(C.Structure):
 class kald_options(C.Structure):
     _fields_ = [("temperature_K", C.c_double), ("sigma_thz", C.c_double), ("n_sigma", C.c_double),
                 ("omega_min_thz", C.c_double), ("degen_tol_thz", C.c_double),
-                ("classical", C.c_int32), ("precision", C.c_int32)]
+                ("classical", C.c_int32), ("precision", C.c_int32), ("delta_shape", C.c_int32)]
 
 
 _lib = None
@@ -118,10 +119,12 @@ class Options:
     degen_tol_thz: float = 1e-5
     classical: bool = False
     precision: str = "fp64"
+    delta: str = "gaussian"
 
     def c(self) -> kald_options:
         return kald_options(self.temperature_K, self.sigma_thz, self.n_sigma, self.omega_min_thz,
-                            self.degen_tol_thz, int(bool(self.classical)), PRECISION[self.precision])
+                            self.degen_tol_thz, int(bool(self.classical)), PRECISION[self.precision],
+                            DELTA_SHAPE[self.delta])
 
 
 class Context:

@@ -16,6 +16,7 @@
 #include <algorithm>
 
 #include "kald_internal.h"
+#include "wdiff.cuh"
 
 namespace kald {
 namespace {
@@ -99,7 +100,7 @@ g_gemm_nt_kernel(int M, int N, int K, const R *__restrict__ A, const R *__restri
 template <typename R>
 __global__ void __launch_bounds__(256)
 g_epilogue_kernel(int nb, const R *__restrict__ phi, double w, const double *__restrict__ omega,
-                  const double *__restrict__ occ, double sig2inv, double cut,
+                  const double *__restrict__ occ, double sig2inv, double cut, int shape,
                   double *__restrict__ partial, unsigned long long *allowed) {
     __shared__ double red[8];
     double acc = 0.0;
@@ -113,8 +114,8 @@ g_epilogue_kernel(int nb, const R *__restrict__ phi, double w, const double *__r
         const double dp = w + w1 - w2, dm = w - w1 - w2;
         double g = 0.0;
         bool hit = false;
-        if (fabs(dp) < cut) { g += (occ[a] - occ[b]) * exp(-dp * dp * sig2inv); hit = true; }
-        if (fabs(dm) < cut) { g += 0.5 * (1.0 + occ[a] + occ[b]) * exp(-dm * dm * sig2inv); hit = true; }
+        if (fabs(dp) < cut) { g += (occ[a] - occ[b]) * delta_shape(dp, shape, sig2inv); hit = true; }
+        if (fabs(dm) < cut) { g += 0.5 * (1.0 + occ[a] + occ[b]) * delta_shape(dm, shape, sig2inv); hit = true; }
         if (hit) {
             ++cnt;
             const double f = (double)phi[x];
@@ -182,7 +183,7 @@ cudaError_t run_plain(const GammaPlan &gp, const GammaDev &d, const LwParams &p,
     R *T = static_cast<R *>(d.T);
     R *PHI = static_cast<R *>(d.PHI);
     g_real_kernel<R><<<counted((unsigned)std::min<size_t>((nn + 255) / 256, 8192)), 256, 0, st>>>(nn, d.eig, E);
-    const double sig2inv = 0.5 / (p.sigma_w * p.sigma_w);
+    const double sig2inv = delta_param(p.shape, p.sigma_w);
     const dim3 ggrid((nb + 63) / 64, (nb + 63) / 64);
     for (int mu = 0; mu < nb; ++mu) {
         if (!(gp.omega_h[mu] > 0.0)) continue;
@@ -192,7 +193,8 @@ cudaError_t run_plain(const GammaPlan &gp, const GammaDev &d, const LwParams &p,
         g_gemm_nt_kernel<R><<<counted(ggrid), 256, 0, st>>>(nb, nb, nb, E, YT, T);
         g_gemm_nt_kernel<R><<<counted(ggrid), 256, 0, st>>>(nb, nb, nb, T, E, PHI);
         g_epilogue_kernel<R><<<counted(gp.n_part), 256, 0, st>>>(nb, PHI, gp.omega_h[mu], d.omega, d.occ, sig2inv,
-                                                        p.cut_w, d.partial + (size_t)mu * gp.n_part, d.allowed);
+                                                        p.cut_w, p.shape, d.partial + (size_t)mu * gp.n_part,
+                                                        d.allowed);
     }
     return cudaGetLastError();
 }
@@ -218,7 +220,7 @@ cudaError_t launch_gamma_only(const GammaPlan &gp, const GammaDev &d, const LwPa
     e = cudaMemsetAsync(d.allowed, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     const double pref = kHbarEvPs * kPi / 8.0 * kEvA2AmuPs2 * kEvA2AmuPs2 * kEvA2AmuPs2 /
-                        (sqrt(kTwoPi) * p.sigma_w);
+                        (1.0 / delta_norm(p.shape, p.sigma_w));
     if (mode == 2) {
         const size_t nt = gp.tiles.size();
         e = cudaMemsetAsync(d.partial_tc, 0, sizeof(double) * std::max<size_t>(nt, 1), st);

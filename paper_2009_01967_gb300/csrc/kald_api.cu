@@ -798,6 +798,8 @@ static kald_status check_options(kald_ctx *ctx, const kald_options *o) {
         return fail(ctx, KALD_E_INVALID, "omega_min and degen_tol must be >= 0");
     if (o->precision != KALD_FP64 && o->precision != KALD_FP32 && o->precision != KALD_BF16_SPLIT)
         return fail(ctx, KALD_E_INVALID, "unknown precision");
+    if (o->delta_shape < 0 || o->delta_shape > 2)
+        return fail(ctx, KALD_E_INVALID, "delta_shape must be 0 (Gaussian), 1 (Lorentzian) or 2 (triangle)");
     return KALD_OK;
 }
 
@@ -965,6 +967,7 @@ static kald_status gamma_only_batch(kald_ctx *ctx, int n_sys, const kald_system 
         p.q0 = 0; p.q1 = 1;
         p.sigma_w = kTwoPi * opt->sigma_thz;
         p.cut_w = opt->n_sigma * p.sigma_w;
+        p.shape = opt->delta_shape;
         p.T = opt->temperature_K;
         p.classical = opt->classical ? 1 : 0;
         p.omega_min_w = kTwoPi * opt->omega_min_thz;
@@ -1071,6 +1074,7 @@ static kald_status linewidths_impl(kald_ctx *ctx, int32_t n_sys, const kald_syst
         p.n_rep = h.n_rep;
         p.sigma_w = kTwoPi * opt->sigma_thz;
         p.cut_w = opt->n_sigma * p.sigma_w;
+        p.shape = opt->delta_shape;
         p.T = opt->temperature_K;
         p.classical = opt->classical ? 1 : 0;
         p.omega_min_w = kTwoPi * opt->omega_min_thz;

@@ -201,6 +201,7 @@ struct LwParams {
     int n_rounds;             // rounds of the Y-build lane schedule
     double sigma_w;           // 2 pi sigma (rad/ps)
     double cut_w;             // n_sigma * sigma_w
+    int shape;                // energy-delta shape (kald_options.delta_shape)
     double T;
     int classical;
     double omega_min_w;       // 2 pi omega_min (rad/ps)

@@ -182,7 +182,7 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
     __shared__ int item_sm, n_act_sm, warp_cnt[nwarps];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const R sig2inv = (R)(0.5 / (p.sigma_w * p.sigma_w));
+    const R sig2inv = (R)delta_param(p.shape, p.sigma_w);   // the delta shape's parameter
     const R cut = (R)p.cut_w;
     const int n_items = (p.q1 - p.q0) * p.n_chunks;
     unsigned long long allowed = 0;
@@ -444,9 +444,9 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
                                 }
                                 R g = (R)0;
                                 bool hit = false;
-                                if (fabs(dp) < cut) { g += dn * exp(-dp * dp * sig2inv); hit = true; }
+                                if (fabs(dp) < cut) { g += dn * delta_shape(dp, p.shape, sig2inv); hit = true; }
                                 if (fabs(dm) < cut) {
-                                    g += (R)0.5 * ((R)1 + n1 + n2) * exp(-dm * dm * sig2inv);
+                                    g += (R)0.5 * ((R)1 + n1 + n2) * delta_shape(dm, p.shape, sig2inv);
                                     hit = true;
                                 }
                                 if (hit) {
@@ -595,7 +595,7 @@ cudaError_t launch_lw_main(const LwParams &p, const LwDev &d, int fp32, int sm_c
 cudaError_t launch_lw_finish(const LwParams &p, const LwDev &d, double degen_tol_thz,
                              double *gamma_out, cudaStream_t st) {
     const double pref = kHbarEvPs * kPi / 8.0 * kEvA2AmuPs2 * kEvA2AmuPs2 * kEvA2AmuPs2 /
-                        (double)p.nq / (sqrt(kTwoPi) * p.sigma_w);
+                        (double)p.nq / (1.0 / delta_norm(p.shape, p.sigma_w));
     lw_finish_kernel<<<counted((p.q1 - p.q0 + 63) / 64), 64, 0, st>>>(p.q0, p.q1, p.nb, p.n_chunks, d.partial,
                                                                    d.omega, d.nu, pref, degen_tol_thz, gamma_out);
     return cudaGetLastError();

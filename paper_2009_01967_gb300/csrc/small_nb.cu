@@ -120,7 +120,7 @@ sn_kernel(LwParams p, LwDev d, SnTables t, const R *__restrict__ fc3, const type
     // keep their accuracy when the terms nearly cancel (wdiff.cuh)
     constexpr bool kPair = std::is_same<R, float>::value;
     const F2 wsp = act ? f2_of(d.omega[(size_t)q * NB + s]) : F2{0.f, 0.f};
-    const R sig2inv = (R)(0.5 / (p.sigma_w * p.sigma_w));
+    const R sig2inv = (R)delta_param(p.shape, p.sigma_w);   // the delta shape's parameter
     const R cut = (R)p.cut_w;
     const int *kq = d.qfrac + 3 * q;
     double sum = 0.0;
@@ -224,8 +224,8 @@ sn_kernel(LwParams p, LwDev d, SnTables t, const R *__restrict__ fc3, const type
 #pragma unroll
                 for (int c = 0; c < NB; ++c) cfma_conj(f, T[c], __ldg(e2 + c * NB + spp));
                 R g = (R)0;
-                if (hp) g += dn * exp(-dp * dp * sig2inv);
-                if (hm) g += (R)0.5 * ((R)1 + n1 + n2) * exp(-dm * dm * sig2inv);
+                if (hp) g += dn * delta_shape(dp, p.shape, sig2inv);
+                if (hm) g += (R)0.5 * ((R)1 + n1 + n2) * delta_shape(dm, p.shape, sig2inv);
                 part += (f.x * f.x + f.y * f.y) * g / (w1 * w2);
                 ++allowed;
             }

@@ -68,7 +68,8 @@ struct XParams {
     const int *qfrac;         // [nq][3] integer mesh coordinates
     __nv_bfloat16 *t1h, *t1l; // GEMM1 output [pairs][Kp][Mp]
     const float4 *wn;         // [nq][nb] FP32 pairs (w hi, w lo, n hi, n lo); w = 0 when masked
-    float sig2inv, cut;
+    float sig2inv, cut;       // delta-shape parameter (delta_param), window half width
+    int shape;                // energy-delta shape
     int n_slices;             // q-slices of slots (a batch spans fewer q values)
     float *slots;             // GEMM2 output [n_slices][nq (q')][nb][2]: per-mode sums over the
                               // mode's rows in its first tile (0) and in the next tile (1)
@@ -316,8 +317,8 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
                         const F2 n2{n2_sm[c0 + k], n2l_sm[c0 + k]};
                         const float dp = f2_diff(wp, w2), dm = f2_diff(wm, w2);
                         const bool hp = fabsf(dp) < cut, hm = fabsf(dm) < cut;
-                        const float gp = hp ? f2_diff(n1, n2) * __expf(-dp * dp * s2i) : 0.0f;
-                        const float gm = hm ? fmaf(0.5f, n2.h, hn1) * __expf(-dm * dm * s2i) : 0.0f;
+                        const float gp = hp ? f2_diff(n1, n2) * delta_shape(dp, x.shape, s2i) : 0.0f;
+                        const float gm = hm ? fmaf(0.5f, n2.h, hn1) * delta_shape(dm, x.shape, s2i) : 0.0f;
                         const float p2 = fmaf(re[k], re[k], im[k] * im[k]);
                         acc = fmaf(p2 * (gp + gm), iw2_sm[c0 + k], acc);
                         cnt += (hp || hm) ? 1ull : 0ull;
@@ -770,7 +771,8 @@ cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups 
     x.qfrac = d.qfrac;
     x.t1h = nullptr; x.t1l = nullptr;
     x.wn = d.wn32;
-    x.sig2inv = (float)(0.5 / (p.sigma_w * p.sigma_w));
+    x.sig2inv = (float)delta_param(p.shape, p.sigma_w);
+    x.shape = p.shape;
     x.cut = (float)p.cut_w;
     x.n_slices = n_slices;
     x.slots = slots;

@@ -58,7 +58,8 @@ struct EpiGamma {
     const double *occ;        // [nb]
     int mu0;                  // first mode of the batch
     int a_rows;               // rows of one T plane (stacked per mode of the batch)
-    double sig2inv, cut;
+    double sig2inv, cut;      // delta-shape parameter (delta_param), window half width
+    int shape;                // energy-delta shape
     double *partial;          // [n_tiles] per-tile sums of this batch
     unsigned long long *allowed;
     const int2 *tiles;        // (tm | b << 16, tn): band tile (tm, tn) of mode mu0 + b
@@ -240,9 +241,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ 
                 const float n2 = n2p.h;
                 const float dn = f2_diff(n1p, n2p);
                 float g = 0.0f;
-                if (hp) g += dn * expf(-dp * dp * s2i);
-                if (hm) g += (upper ? 1.0f : 0.5f) * (1.0f + n1 + n2) * expf(-dm * dm * s2i);
-                if (hp2) g -= dn * expf(-dp2 * dp2 * s2i);
+                if (hp) g += dn * delta_shape(dp, eg.shape, s2i);
+                if (hm) g += (upper ? 1.0f : 0.5f) * (1.0f + n1 + n2) * delta_shape(dm, eg.shape, s2i);
+                if (hp2) g -= dn * delta_shape(dp2, eg.shape, s2i);
                 const float f = v[x];
                 acc += f * f * g / (w1 * w2);
                 cnt += (unsigned long long)(hp || hm) + (unsigned long long)(upper && (hp2 || hm));
@@ -421,7 +422,7 @@ cudaError_t launch_gamma_only_tc(const GammaPlan &gp, const GammaDev &d, const L
     e = cudaMemcpyAsync(tiles_dev, enc.data(), sizeof(int2) * enc.size(), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
     const int nt = rows / kBM;
-    const double sig2inv = 0.5 / (p.sigma_w * p.sigma_w);
+    const double sig2inv = delta_param(p.shape, p.sigma_w);
     for (int mu0 = 0; mu0 < nb; mu0 += mb) {
         const int nm = std::min(mb, nb - mu0);
         const int t0 = tile_start[mu0], t1 = tile_start[mu0 + nm];
@@ -436,7 +437,7 @@ cudaError_t launch_gamma_only_tc(const GammaPlan &gp, const GammaDev &d, const L
         k1<<<counted(dim3(nt, nt, nm)), 128, kSmemBytes, st>>>(mEh, mEl, mYh, mYl, nb, nb, ld, es, eg, err,
                                                                p.wait_limit);
         p1.end();
-        EpiGamma eg2{d.omega, d.occ, mu0, prow, sig2inv, p.cut_w, partial_tc + t0, d.allowed,
+        EpiGamma eg2{d.omega, d.occ, mu0, prow, sig2inv, p.cut_w, p.shape, partial_tc + t0, d.allowed,
                      tiles_dev + t0, symmetric};
         EpiSplit es0{nullptr, nullptr, 0, 0};
         ProfMark p2(p.prof, KALD_PROF_TC_GEMM2, st);

@@ -10,6 +10,10 @@
 // The sum w + w' of two pairs uses Knuth's two-sum (exact for the hi parts).
 #pragma once
 
+#include <cmath>
+
+#include "kald_internal.h"
+
 namespace kald {
 
 struct F2 {
@@ -45,6 +49,32 @@ __device__ __forceinline__ F2 f2_neg(F2 a) {
 // factor of two of each other), then the lo parts.
 __device__ __forceinline__ float f2_diff(F2 a, F2 b) {
     return __fadd_rn(__fsub_rn(a.h, b.h), __fsub_rn(a.l, b.l));
+}
+
+// Energy-delta shapes of the epilogues, without their normalisation (applied
+// per mode at the end, delta_norm): 0 Gaussian exp(-a d^2), a = 1/(2 sigma^2);
+// 1 Lorentzian 1/(1 + a d^2), a = 1/sigma^2; 2 triangle max(0, 1 - a |d|),
+// a = 1/sigma.  The shape is uniform over a launch (no divergence).
+enum : int { kDeltaGauss = 0, kDeltaLorentz = 1, kDeltaTriangle = 2 };
+__device__ __forceinline__ float delta_shape(float d, int shape, float a) {
+    if (shape == kDeltaGauss) return __expf(-d * d * a);
+    if (shape == kDeltaLorentz) return 1.0f / fmaf(d * d, a, 1.0f);
+    return fmaxf(0.0f, 1.0f - fabsf(d) * a);
+}
+__device__ __forceinline__ double delta_shape(double d, int shape, double a) {
+    if (shape == kDeltaGauss) return exp(-d * d * a);
+    if (shape == kDeltaLorentz) return 1.0 / fma(d * d, a, 1.0);
+    return fmax(0.0, 1.0 - fabs(d) * a);
+}
+// Host side: the parameter a of a shape and width sigma (rad/ps), and the
+// normalisation that makes the shape a density in angular frequency.
+__host__ __device__ inline double delta_param(int shape, double sigma) {
+    return shape == kDeltaGauss ? 0.5 / (sigma * sigma) : shape == kDeltaLorentz ? 1.0 / (sigma * sigma) : 1.0 / sigma;
+}
+inline double delta_norm(int shape, double sigma) {
+    return shape == kDeltaGauss ? 1.0 / (std::sqrt(kTwoPi) * sigma)       // 1 / (sqrt(2 pi) sigma)
+           : shape == kDeltaLorentz ? 1.0 / (kPi * sigma)
+                                    : 1.0 / sigma;
 }
 
 }  // namespace kald

@@ -767,3 +767,31 @@ def test_batched_mixed_sizes_match_single_calls(k, c4w, precision):
         a_sum += a1
         o += nb
     assert tot == t_sum and allowed == a_sum
+
+
+# ---------------------------------------------------------------- delta shapes
+@pytest.mark.parametrize("shape", ["lorentzian", "triangular"])
+@pytest.mark.parametrize("case,precision", [("binary3", "fp64"), ("binary3", "fp32"), ("fcc4_mesh3", "fp64"),
+                                            ("fcc4_mesh3", "bf16split"), ("g144", "fp64"), ("g144", "bf16split")])
+def test_delta_shapes_match_oracle(k, case, precision, shape):
+    """The Lorentzian and triangular energy deltas (delta_shape option) in
+    every epilogue -- register, CUDA-core, crystal and Gamma-only tensor-core
+    -- against the oracle with the same shape."""
+    kk, ctx = k
+    if case == "fcc4_mesh3":
+        w = ki.Workload("fcc4", [ki.fcc_supercell_system(1, seed=7)], (3, 3, 3), 300.0, 0.1, 3.0)
+    elif case == "g144":
+        s = ki.fcc_supercell_system((2, 2, 3), seed=17, heavy_fraction=0.3)
+        w = ki.Workload("g144", [s], (1, 1, 1), 300.0, 0.05, 3.0)
+    else:
+        w = _lw_case(case)
+    s = w.systems[0]
+    nu_o, eig_o = ph.phonons(s, w.mesh)
+    if w.n_q == 1:
+        g_o = an.linewidths_gamma_only(s, nu_o, eig_o, w.T, w.sigma_thz, w.n_sigma, delta=shape)
+    else:
+        g_o = an.linewidths(s, w.mesh, nu_o, eig_o, w.T, w.sigma_thz, w.n_sigma, delta=shape)
+    g, _ = kk.kald_linewidths(ctx, s, w.mesh, nu_o, eig_o, _opts(kk, w, precision, delta=shape))
+    err = _rel(np.ravel(g), np.ravel(g_o), 1e-6 * np.max(g_o))
+    print(f"{case} {precision} {shape}: gamma rel err {err:.2e}")
+    assert err < (1e-10 if precision == "fp64" else 1e-5)
