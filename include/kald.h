@@ -229,6 +229,18 @@ kald_status kald_linewidths_qrange(kald_ctx *ctx, const kald_system *sys, const 
                                    const double *nu_thz, const double *eigvec, const kald_options *opt,
                                    int32_t q_begin, int32_t q_end, double *gamma, uint64_t *n_triplets);
 
+/* Phase space per mode (the definition after Eq. delta_deconstructed, with
+ * the weights of Eq. phase_space): the linewidth sum without the matrix
+ * elements,
+ *   g_mu = (1/N_k) sum_{q' s' s''} [(n' - n'') delta(w + w' - w'')
+ *                                  + 1/2 (1 + n' + n'') delta(w - w' - w'')],
+ * q'' = q + q', with the delta, masking and statistics of kald_linewidths
+ * (opt->delta_shape, classical; FP64 when opt->precision is KALD_FP64, else
+ * FP32 weights with FP64 sums over q').
+ *   g  [Nq][nb] out (ps); 0 for masked modes. */
+kald_status kald_phase_space(kald_ctx *ctx, const kald_system *sys, const int32_t mesh[3],
+                             const double *nu_thz, const kald_options *opt, double *g);
+
 /* BTE-RTA conductivity (Eq. RTA, Eq. heat_capacity):
  *   kappa_ab = 1/(N_k V) sum_mu c_mu tau_mu v_a v_b,  tau = 1/(2 gamma),
  * with, inside each degenerate set D at one q, v_a v_b replaced by the
@@ -254,6 +266,16 @@ kald_status kald_kappa_rta(kald_ctx *ctx, const kald_system *sys, const int32_t 
 kald_status kald_kappa_qhgk(kald_ctx *ctx, int32_t n_sys, const kald_system *sys,
                             const double *nu_thz, const double *eigvec, const double *gamma,
                             const kald_options *opt, double *kappa, double *vgen);
+
+/* Mode diffusivity of Gamma-only systems (Eq. diffusivity_per_mode, read as
+ * the Allen-Feldman diffusivity averaged over the three directions):
+ *   D_mu = 1/3 sum_a sum_mu' W_a(mu, mu')^2 tau_{mu mu'}   (A^2/ps),
+ * W_a and tau_{mu mu'} as in kald_kappa_qhgk; with classical populations
+ * tr(kappa_QHGK)/3 = kB/V sum_mu D_mu.  Modes with nu < omega_min or
+ * gamma <= 0 get 0.  FP64.
+ *   D  [sum over systems of nb] out */
+kald_status kald_diffusivity(kald_ctx *ctx, int32_t n_sys, const kald_system *sys, const double *nu_thz,
+                             const double *eigvec, const double *gamma, const kald_options *opt, double *D);
 
 /* kald_kappa_rta for callers that cannot allocate device memory.  The paper
  * has no counterpart: this is an interface addition, not part of the method.

@@ -28,7 +28,7 @@ EXPORTS = ["kald_ctx_create", "kald_ctx_destroy", "kald_last_error", "kald_set_s
            "kald_phonons", "kald_linewidths", "kald_kappa_rta", "kald_kappa_qhgk",
            "kald_kappa_rta_noalloc", "kald_kernel_launches", "kald_set_wait_limit",
            "kald_set_workspace_limit", "kald_profile_enable", "kald_profile_read",
-           "kald_linewidths_qrange", "kald_phonons_batch"]
+           "kald_linewidths_qrange", "kald_phonons_batch", "kald_phase_space", "kald_diffusivity"]
 PROF_KERNELS = {"tcx_gather": 0, "tcx_gemm1": 1, "tcx_gemm2": 2, "tc_gemm1": 3, "tc_gemm2": 4,
                 "small_nb": 5, "lw_main": 6}
 
@@ -74,6 +74,10 @@ def load_library(path: str = LIB_PATH):
     lib.kald_set_stream.restype = st
     lib.kald_phonons.argtypes = [vp, C.POINTER(kald_system), C.POINTER(i32), vp, vp, vp]
     lib.kald_phonons.restype = st
+    lib.kald_phase_space.argtypes = [vp, C.POINTER(kald_system), C.POINTER(i32), vp, C.POINTER(kald_options), vp]
+    lib.kald_phase_space.restype = st
+    lib.kald_diffusivity.argtypes = [vp, i32, C.POINTER(kald_system), vp, vp, vp, C.POINTER(kald_options), vp]
+    lib.kald_diffusivity.restype = st
     lib.kald_phonons_batch.argtypes = [vp, i32, C.POINTER(kald_system), vp, vp]
     lib.kald_phonons_batch.restype = st
     lib.kald_linewidths.argtypes = [vp, i32, C.POINTER(kald_system), C.POINTER(i32), vp, vp,
@@ -324,6 +328,36 @@ def kald_linewidths_qrange(ctx: Context, system, mesh, nu_thz, eigvec, options: 
                                              _ptr(gamma, np.float64, max(n_out, 0), "gamma"), trip))
     del keep
     return gamma, (int(trip[0]), int(trip[1]))
+
+
+def kald_phase_space(ctx: Context, system, mesh, nu_thz, options: Options, g=None):
+    """Phase space per mode g [Nq * nb] (ps)."""
+    cs, keep = c_system(system)
+    m, nq = _mesh(mesh)
+    nb = 3 * cs.n_atoms
+    if g is None:
+        g = np.zeros(nq * nb)
+    opt = options.c()
+    ctx.check(ctx.lib.kald_phase_space(ctx.handle, C.byref(cs), m, _ptr(nu_thz, np.float64, nq * nb, "nu_thz"),
+                                       C.byref(opt), _ptr(g, np.float64, nq * nb, "g")))
+    del keep
+    return g
+
+
+def kald_diffusivity(ctx: Context, systems, nu_thz, eigvec, gamma, options: Options, D=None):
+    """Mode diffusivity D [sum nb] (A^2/ps) of Gamma-only systems."""
+    arr, keep, nbs = _systems(systems)
+    n_modes = sum(nbs)
+    n_eig = sum(nb * nb for nb in nbs)
+    if D is None:
+        D = np.zeros(n_modes)
+    opt = options.c()
+    ctx.check(ctx.lib.kald_diffusivity(ctx.handle, len(nbs), arr, _ptr(nu_thz, np.float64, n_modes, "nu_thz"),
+                                       _ptr(eigvec, np.complex128, n_eig, "eigvec"),
+                                       _ptr(gamma, np.float64, n_modes, "gamma"), C.byref(opt),
+                                       _ptr(D, np.float64, n_modes, "D")))
+    del keep
+    return D
 
 
 def kald_kappa_rta(ctx: Context, system, mesh, nu_thz, eigvec, gamma, options: Options, kappa=None):

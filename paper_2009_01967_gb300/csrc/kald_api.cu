@@ -1234,6 +1234,111 @@ kald_status kald_linewidths_qrange(kald_ctx *ctx, const kald_system *sys, const 
     return linewidths_impl(ctx, 1, sys, mesh, nu_thz, eigvec, opt, q_begin, q_end, gamma, n_triplets);
 }
 
+kald_status kald_phase_space(kald_ctx *ctx, const kald_system *sys, const int32_t mesh[3],
+                             const double *nu_thz, const kald_options *opt, double *g) {
+    if (!ctx) return KALD_E_INVALID;
+    kald_status st = set_device(ctx);
+    if (st) return st;
+    if ((st = check_mesh(ctx, mesh))) return st;
+    if ((st = check_options(ctx, opt))) return st;
+    if (!nu_thz || !g) return fail(ctx, KALD_E_INVALID, "nu/g NULL");
+    std::shared_ptr<const HostSystem> hp;
+    if ((st = plan_system_cached(ctx, sys, hp))) return st;
+    const int nb = hp->nb;
+    std::vector<double> qc;
+    std::vector<int> qf;
+    mesh_points(hp->lattice, mesh, qc, qf);
+    const int nq = mesh[0] * mesh[1] * mesh[2];
+    const bool d_nu = is_device_ptr(nu_thz), d_g = is_device_ptr(g);
+    const int f32 = opt->precision != KALD_FP64;
+    const size_t nm = (size_t)nq * nb;
+    size_t need = bytes_of(qf) + 2 * ws_round(sizeof(double) * nm) + ws_round(sizeof(float4) * nm);
+    if (!d_nu) need += ws_round(sizeof(double) * nm);
+    if (!d_g) need += ws_round(sizeof(double) * nm);
+    if ((st = ws_reserve(ctx, need))) return st;
+    LwDev d{};
+    d.qfrac = upload(ctx, qf);
+    d.nu = stage_in(ctx, nu_thz, nm, d_nu);
+    d.omega = static_cast<double *>(ws_take(ctx, sizeof(double) * nm));
+    d.occ = static_cast<double *>(ws_take(ctx, sizeof(double) * nm));
+    d.wn32 = static_cast<float4 *>(ws_take(ctx, sizeof(float4) * nm));
+    double *g_d = d_g ? g : static_cast<double *>(ws_take(ctx, sizeof(double) * nm));
+    LwParams p{};
+    p.nb = nb; p.nq = nq;
+    for (int a = 0; a < 3; ++a) p.mesh[a] = mesh[a];
+    p.sigma_w = kTwoPi * opt->sigma_thz;
+    p.cut_w = opt->n_sigma * p.sigma_w;
+    p.shape = opt->delta_shape;
+    p.T = opt->temperature_K;
+    p.classical = opt->classical ? 1 : 0;
+    p.omega_min_w = kTwoPi * opt->omega_min_thz;
+    p.q0 = 0; p.q1 = nq;
+    p.wait_limit = ctx->wait_limit;
+    p.prof = &ctx->prof;
+    cudaError_t e = launch_mode_prep((int)nm, d.nu, p.omega_min_w, p.T, p.classical, d.omega, d.occ, ctx->stream);
+    if (e == cudaSuccess && f32) e = launch_wn_pairs((int)nm, d.omega, d.occ, d.wn32, ctx->stream);
+    if (e == cudaSuccess) e = launch_phase_space(p, d, f32, g_d, ctx->stream);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "kald_phase_space launch");
+    if (!d_g) cudaMemcpyAsync(g, g_d, sizeof(double) * nm, cudaMemcpyDeviceToHost, ctx->stream);
+    return finish(ctx, "kald_phase_space");
+}
+
+kald_status kald_diffusivity(kald_ctx *ctx, int32_t n_sys, const kald_system *sys, const double *nu_thz,
+                             const double *eigvec, const double *gamma, const kald_options *opt, double *D) {
+    if (!ctx) return KALD_E_INVALID;
+    kald_status st = set_device(ctx);
+    if (st) return st;
+    if ((st = check_options(ctx, opt))) return st;
+    if (n_sys <= 0 || !sys) return fail(ctx, KALD_E_INVALID, "n_sys must be > 0");
+    if (!nu_thz || !eigvec || !gamma || !D) return fail(ctx, KALD_E_INVALID, "NULL array");
+    const bool d_nu = is_device_ptr(nu_thz), d_eig = is_device_ptr(eigvec), d_g = is_device_ptr(gamma);
+    const bool d_D = is_device_ptr(D);
+    size_t off_nb = 0, off_eig = 0;
+    for (int x = 0; x < n_sys; ++x) {
+        std::shared_ptr<const HostSystem> hp;
+        if ((st = plan_system_cached(ctx, &sys[x], hp))) return st;
+        const HostSystem &h = *hp;
+        const int nb = h.nb;
+        const size_t nn = (size_t)nb * nb;
+        std::vector<int> row_start(h.n_atoms + 1, 0), col_j(h.fc2_blk.size() / 9);
+        for (size_t pp = 0; pp < h.pair2_i.size(); ++pp)
+            for (int b = h.pair2_start[pp]; b < h.pair2_start[pp + 1]; ++b) {
+                col_j[b] = h.pair2_j[pp];
+                row_start[h.pair2_i[pp] + 1]++;
+            }
+        for (int i = 0; i < h.n_atoms; ++i) row_start[i + 1] += row_start[i];
+        size_t need = bytes_of(row_start) + bytes_of(col_j) + scaled_bytes(h.fc2_blk, h.fc2_atoms, h, 9, 9, 0) +
+                      bytes_of(h.fc2_dist) + ws_round(sizeof(double) * nn) + 2 * ws_round(sizeof(double) * 3 * nn) +
+                      ws_round(sizeof(double) * nb) * 2;
+        if (!d_nu) need += ws_round(sizeof(double) * nb);
+        if (!d_eig) need += ws_round(sizeof(double2) * nn);
+        if (!d_g) need += ws_round(sizeof(double) * nb);
+        if ((st = ws_reserve(ctx, need))) return st;
+        DevFc2Dist f;
+        f.n_rows = h.n_atoms;
+        f.row_start = upload(ctx, row_start);
+        f.col_j = upload(ctx, col_j);
+        f.blk = static_cast<const double *>(upload_scaled(ctx, h.fc2_blk, h.fc2_atoms, h, 9, 9, 0));
+        f.dist = upload(ctx, h.fc2_dist);
+        const double *nu_d = stage_in(ctx, nu_thz + off_nb, (size_t)nb, d_nu);
+        const double2 *eig_d = stage_in(ctx, reinterpret_cast<const double2 *>(eigvec) + off_eig, nn, d_eig);
+        const double *g_d = stage_in(ctx, gamma + off_nb, (size_t)nb, d_g);
+        double *E = static_cast<double *>(ws_take(ctx, sizeof(double) * nn));
+        double *B = static_cast<double *>(ws_take(ctx, sizeof(double) * 3 * nn));
+        double *W = static_cast<double *>(ws_take(ctx, sizeof(double) * 3 * nn));
+        double *omega = static_cast<double *>(ws_take(ctx, sizeof(double) * nb));
+        double *D_d = d_D ? D + off_nb : static_cast<double *>(ws_take(ctx, sizeof(double) * nb));
+        cudaError_t e = launch_diffusivity(f, nb, nu_d, eig_d, g_d, opt->omega_min_thz, E, B, W, omega, D_d,
+                                           ctx->stream);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "kald_diffusivity launch");
+        if (!d_D) cudaMemcpyAsync(D + off_nb, D_d, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->stream);
+        if ((st = finish(ctx, "kald_diffusivity"))) return st;
+        off_nb += nb;
+        off_eig += nn;
+    }
+    return KALD_OK;
+}
+
 kald_status kald_kappa_rta(kald_ctx *ctx, const kald_system *sys, const int32_t mesh[3],
                            const double *nu_thz, const double *eigvec, const double *gamma,
                            const kald_options *opt, double *kappa) {

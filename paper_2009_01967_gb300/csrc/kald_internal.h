@@ -349,6 +349,15 @@ struct DevFc2Dist {
     const double *blk;        // [n][9] Phi2/sqrt(mi mj)
     const double *dist;       // [n][3] x_i - x_j - L
 };
+// Mode diffusivity D [nb] (A^2/ps) of a Gamma-only system (generalised
+// velocity as for QHGK, then the per-mode sum); omega [nb] scratch.
+cudaError_t launch_diffusivity(const DevFc2Dist &f, int nb, const double *nu_thz, const double2 *eig,
+                               const double *gamma, double omega_min_thz, double *Ework, double *Bwork,
+                               double *W, double *omega, double *D, cudaStream_t st);
+// FP32 pairs (hi, lo) of omega and occ (linewidths.cu).
+cudaError_t launch_wn_pairs(int n, const double *omega, const double *occ, float4 *wn32, cudaStream_t st);
+// Phase space per mode (linewidths.cu): g [(q1 - q0) * nb] in ps.
+cudaError_t launch_phase_space(const LwParams &p, const LwDev &d, int fp32, double *g_out, cudaStream_t st);
 cudaError_t launch_qhgk(const DevFc2Dist &f, int nb, const double *nu_thz, const double2 *eig,
                         const double *gamma, double T, int classical, double omega_min_thz,
                         double degen_tol_thz, double *Ework /*[nb*nb]*/, double *Bwork /*[3][nb][nb]*/,

@@ -348,6 +348,42 @@ qhgk_pairsum_kernel(int nb, const double *__restrict__ W, const double *__restri
         for (int a = 0; a < 9; ++a) partial[(size_t)blockIdx.x * 9 + a] = acc[a];
 }
 
+// Mode diffusivity (Eq. diffusivity_per_mode, read as the Allen-Feldman
+// diffusivity averaged over the three directions):
+//   D_mu = 1/3 sum_a sum_mu' W_a(mu, mu')^2 tau_{mu mu'},
+// tau as in the QHGK pair sum; modes with w <= 0 or gamma <= 0 get 0 and take
+// no part as mu'.  One CTA per mu, threads over mu', fixed-order reduction.
+__global__ void __launch_bounds__(256)
+diffusivity_kernel(int nb, const double *__restrict__ W, const double *__restrict__ omega,
+                   const double *__restrict__ gamma, double *__restrict__ D) {
+    __shared__ double red[8];
+    const int m = blockIdx.x;
+    const double w1 = omega[m], g1 = gamma[m];
+    const bool ok = w1 > 0.0 && g1 > 0.0;
+    double acc = 0.0;
+    if (ok) {
+        const double *W0 = W + (size_t)m * nb;
+        const double *W1 = W + ((size_t)nb + m) * nb;
+        const double *W2 = W + ((size_t)2 * nb + m) * nb;
+        for (int n = threadIdx.x; n < nb; n += blockDim.x) {
+            const double w2 = omega[n], g2 = gamma[n];
+            if (!(w2 > 0.0) || !(g2 > 0.0)) continue;
+            const double dw = w1 - w2, gs = g1 + g2;
+            const double tau = gs / (dw * dw + gs * gs);
+            const double x0 = W0[n], x1 = W1[n], x2 = W2[n];
+            acc += (x0 * x0 + x1 * x1 + x2 * x2) * tau;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+        D[m] = ok ? t / 3.0 : 0.0;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_kappa_rta(const DevFc2 &f, int nb, int nq, const double *qcart,
@@ -357,6 +393,20 @@ cudaError_t launch_kappa_rta(const DevFc2 &f, int nb, int nq, const double *qcar
     kappa_rta_kernel<<<counted(nq), kRtaThreads, 0, st>>>(f, nb, qcart, nu_thz, eig, gamma, T, classical,
                                                 omega_min_thz, degen_tol_thz, partial);
     sum_partials_kernel<<<counted(1), 32, 0, st>>>(nq, partial, scale, kappa_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diffusivity(const DevFc2Dist &f, int nb, const double *nu_thz, const double2 *eig,
+                               const double *gamma, double omega_min_thz, double *Ework, double *Bwork,
+                               double *W, double *omega, double *D, cudaStream_t st) {
+    const size_t nn = (size_t)nb * nb;
+    real_part_kernel<<<counted((unsigned)std::min<size_t>((nn + 255) / 256, 8192)), 256, 0, st>>>(nn, eig, Ework);
+    const size_t ns = (size_t)f.n_rows * 3 * nb;
+    sparse_ae_kernel<<<counted((unsigned)std::min<size_t>((ns + 255) / 256, 16384)), 256, 0, st>>>(f, nb, Ework, Bwork);
+    qhgk_modes_kernel<<<counted((nb + 255) / 256), 256, 0, st>>>(nb, nu_thz, omega_min_thz, omega);
+    dim3 grid((nb + 63) / 64, (nb + 63) / 64, 3);
+    dgemm_w_kernel<<<counted(grid), 256, 0, st>>>(nb, Ework, Bwork, omega, W);
+    diffusivity_kernel<<<counted(nb), 256, 0, st>>>(nb, W, omega, gamma, D);
     return cudaGetLastError();
 }
 

@@ -518,6 +518,91 @@ __global__ void lw_finish_kernel(int q0, int q1, int nb, int n_chunks, const dou
     }
 }
 
+// Phase space per mode (the definition after Eq. delta_deconstructed, with
+// the weights of Eq. phase_space and the readings of the linewidths: the 1/2
+// on the - process, 1/N_k, masked modes):
+//   g_mu = (1/N_k) sum_{q' s' s''} [(n' - n'') G(w + w' - w'') + 1/2 (1 + n' + n'') G(w - w' - w'')],
+// q'' = q + q' for both processes (the - process of (q, -q') has the same
+// frequencies, since w(-q) = w(q)).  One thread per (q, s), q' in order;
+// the modes of q' and q'' are staged in shared memory per q' (all threads of
+// a CTA share q).  FP64, or FP32 weights with the compensated differences and
+// FP64 sums over q'.  The delta normalisation and 1/N_k are applied at the end.
+template <typename R>
+__global__ void __launch_bounds__(128)
+phase_space_kernel(LwParams p, LwDev d, double scale, double *__restrict__ g_out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr bool kPair = std::is_same<R, float>::value;
+    const int nb = p.nb;
+    const int per_q = (nb + blockDim.x - 1) / blockDim.x;          // CTAs per q
+    const int q = p.q0 + (int)blockIdx.x / per_q;
+    const int s = ((int)blockIdx.x % per_q) * blockDim.x + threadIdx.x;
+    // modes of q' and q'': FP32 pairs (w hi, w lo, n hi, n lo), or FP64 (w, n)
+    float4 *f1 = reinterpret_cast<float4 *>(smem_raw);
+    float4 *f2 = f1 + nb;
+    double2 *e1 = reinterpret_cast<double2 *>(smem_raw);
+    double2 *e2 = e1 + nb;
+    const R a = (R)delta_param(p.shape, p.sigma_w);
+    const R cut = (R)p.cut_w;
+    const bool act = s < nb && q < p.q1;
+    const double w_s = act ? d.omega[(size_t)q * nb + s] : 0.0;
+    const F2 wsp = f2_of(w_s);
+    double sum = 0.0;
+    for (int qp = 0; qp < p.nq; ++qp) {
+        const int *kq = d.qfrac + 3 * q, *kp = d.qfrac + 3 * qp;
+        const int qpp = (((kq[0] + kp[0]) % p.mesh[0]) * p.mesh[1] + (kq[1] + kp[1]) % p.mesh[1]) * p.mesh[2] +
+                        (kq[2] + kp[2]) % p.mesh[2];
+        __syncthreads();
+        for (int x = threadIdx.x; x < nb; x += blockDim.x) {
+            if constexpr (kPair) {
+                f1[x] = d.wn32[(size_t)qp * nb + x];
+                f2[x] = d.wn32[(size_t)qpp * nb + x];
+            } else {
+                e1[x] = make_double2(d.omega[(size_t)qp * nb + x], d.occ[(size_t)qp * nb + x]);
+                e2[x] = make_double2(d.omega[(size_t)qpp * nb + x], d.occ[(size_t)qpp * nb + x]);
+            }
+        }
+        __syncthreads();
+        if (!act || !(w_s > 0.0)) continue;
+        R part = (R)0;
+        for (int sp = 0; sp < nb; ++sp) {
+            R w1, n1;
+            F2 n1p, sum_p, dif_p;
+            if constexpr (kPair) {
+                const float4 u = f1[sp];
+                w1 = u.x; n1 = u.z;
+                n1p = F2{u.z, u.w};
+                sum_p = f2_add(wsp, F2{u.x, u.y});
+                dif_p = f2_add(wsp, F2{-u.x, -u.y});
+            } else {
+                w1 = e1[sp].x; n1 = e1[sp].y;
+            }
+            if (!(w1 > (R)0)) continue;
+            R inner = (R)0;
+            for (int spp = 0; spp < nb; ++spp) {
+                R w2, n2, dp, dm, dn;
+                if constexpr (kPair) {
+                    const float4 v = f2[spp];
+                    w2 = v.x; n2 = v.z;
+                    dp = f2_diff(sum_p, F2{v.x, v.y});
+                    dm = f2_diff(dif_p, F2{v.x, v.y});
+                    dn = f2_diff(n1p, F2{v.z, v.w});
+                } else {
+                    w2 = e2[spp].x; n2 = e2[spp].y;
+                    dp = w_s + w1 - w2;
+                    dm = w_s - w1 - w2;
+                    dn = n1 - n2;
+                }
+                if (!(w2 > (R)0)) continue;
+                if (fabs(dp) < cut) inner += dn * delta_shape(dp, p.shape, a);
+                if (fabs(dm) < cut) inner += (R)0.5 * ((R)1 + n1 + n2) * delta_shape(dm, p.shape, a);
+            }
+            part += inner;
+        }
+        sum += (double)part;
+    }
+    if (act) g_out[(size_t)(q - p.q0) * nb + s] = (w_s > 0.0) ? scale * sum : 0.0;
+}
+
 template <typename R>
 size_t lw_smem_bytes(const LwParams &p, bool oper_smem) {
     using R2 = typename C2<R>::T;
@@ -589,6 +674,26 @@ cudaError_t launch_lw_main(const LwParams &p, const LwDev &d, int fp32, int sm_c
                                         (const double2 *)d.chi);
         pm.end();
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wn_pairs(int n, const double *omega, const double *occ, float4 *wn32, cudaStream_t st) {
+    wn_pair_kernel<<<counted((n + 255) / 256), 256, 0, st>>>(n, omega, occ, wn32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_phase_space(const LwParams &p, const LwDev &d, int fp32, double *g_out, cudaStream_t st) {
+    const int threads = 128;
+    const int per_q = (p.nb + threads - 1) / threads;
+    const size_t smem = 2 * sizeof(float4) * (size_t)p.nb;     // >= two double2 rows
+    const double scale = delta_norm(p.shape, p.sigma_w) / (double)p.nq;
+    auto k32 = phase_space_kernel<float>;
+    auto k64 = phase_space_kernel<double>;
+    cudaError_t e = cudaFuncSetAttribute(fp32 ? k32 : k64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((unsigned)((p.q1 - p.q0) * per_q));
+    if (fp32) k32<<<counted(grid), threads, smem, st>>>(p, d, scale, g_out);
+    else k64<<<counted(grid), threads, smem, st>>>(p, d, scale, g_out);
     return cudaGetLastError();
 }
 

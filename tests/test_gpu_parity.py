@@ -795,3 +795,46 @@ def test_delta_shapes_match_oracle(k, case, precision, shape):
     err = _rel(np.ravel(g), np.ravel(g_o), 1e-6 * np.max(g_o))
     print(f"{case} {precision} {shape}: gamma rel err {err:.2e}")
     assert err < (1e-10 if precision == "fp64" else 1e-5)
+
+
+# ---------------------------------------------------------------- phase space and diffusivity
+@pytest.mark.parametrize("case,precision,shape", [("binary3", "fp64", "gaussian"), ("binary3", "fp32", "gaussian"),
+                                                  ("fcc4_mesh4", "fp64", "gaussian"),
+                                                  ("fcc4_mesh4", "fp32", "lorentzian"),
+                                                  ("binary3", "fp64", "triangular")])
+def test_phase_space_matches_oracle(k, case, precision, shape):
+    """kald_phase_space (the weights of the linewidths without matrix elements)
+    against the oracle's phase space; the oracle forms the - process with
+    q'' = q - q', the GPU with q'' = q + q' and w(-q') = w(q'), equal up to the
+    rounding of the two frequencies."""
+    kk, ctx = k
+    if case == "fcc4_mesh4":
+        w = ki.Workload("fcc4", [ki.fcc_supercell_system(1, seed=7)], (4, 4, 4), 300.0, 0.1, 3.0)
+    else:
+        w = _lw_case(case)
+    s = w.systems[0]
+    nu_o, _ = ph.phonons(s, w.mesh)
+    g_o = an.phase_space(w.mesh, nu_o, w.T, w.sigma_thz, w.n_sigma, delta=shape)
+    g = kk.kald_phase_space(ctx, s, w.mesh, nu_o, _opts(kk, w, precision, delta=shape))
+    err = _rel(g.reshape(g_o.shape), g_o, 1e-6 * g_o.max())
+    print(f"{case} {precision} {shape}: phase space rel err {err:.2e}")
+    assert err < (1e-9 if precision == "fp64" else 1e-5)
+    assert np.all(g.reshape(g_o.shape)[nu_o <= 0.01] == 0.0)
+
+
+def test_diffusivity_matches_oracle_and_the_classical_trace_identity(k, big324):
+    """kald_diffusivity against the oracle (108-atom supercell), and the
+    identity tr(kappa_QHGK)/3 = kB/V sum_mu D_mu of the GPU's own classical
+    kappa_QHGK and diffusivities."""
+    kk, ctx = k
+    s, nu_o, eig_o, g_o = big324
+    w = ki.Workload("g324", [s], (1, 1, 1), 300.0, 0.05, 3.0)
+    g = np.ravel(g_o)
+    D = kk.kald_diffusivity(ctx, [s], nu_o, eig_o, g, _opts(kk, w))
+    D_o = co.diffusivity(s, nu_o, eig_o, g)
+    np.testing.assert_allclose(D, D_o, rtol=1e-10, atol=1e-12 * np.abs(D_o).max())
+    kap, _ = kk.kald_kappa_qhgk(ctx, [s], nu_o, eig_o, g, _opts(kk, w, classical=True))
+    kb = 1.380649e-23
+    lhs = np.trace(kap[0]) / 3.0
+    rhs = kb / s.volume * np.sum(D) * co.KAPPA_SI
+    assert abs(lhs - rhs) <= 1e-10 * abs(lhs)
