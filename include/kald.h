@@ -229,6 +229,43 @@ kald_status kald_linewidths_qrange(kald_ctx *ctx, const kald_system *sys, const 
                                    const double *nu_thz, const double *eigvec, const kald_options *opt,
                                    int32_t q_begin, int32_t q_end, double *gamma, uint64_t *n_triplets);
 
+/* The full linearised BTE scattering operator of one crystal (section
+ * "Boltzman Transport Equation": Gamma~ = diag(Gamma^0) + Gamma^1 with
+ *   Gamma^1_{mu mu'} = (w_mu' / w_mu) sum_mu'' (Gamma^+_{mu mu' mu''}
+ *     - Gamma^+_{mu mu'' mu'} - Gamma^-_{mu mu' mu''} - Gamma^-_{mu mu'' mu'})
+ * and the rates of Eq. gamma_operators; flat mode index mu = q nb + s).
+ * The FP64 projection kernels scatter every rate into three planes (the +
+ * rates at column (q', s'), the - rates at column (-q', s'), both at column
+ * (q + q', s'')), combined in a fixed order.  nb <= 96, N = Nq nb <= 200000
+ * (the operator is dense: 3 x 8 N^2 bytes while it is assembled, allocated for
+ * the call).
+ *   gamma0  [N] out: the unaveraged linewidths Gamma^0 (ps^-1)
+ *   G1      [N][N] out: Gamma^1 (ps^-1)
+ * opt->precision is ignored (FP64), opt->degen_tol_thz too (no averaging). */
+kald_status kald_scattering_matrix(kald_ctx *ctx, const kald_system *sys, const int32_t mesh[3],
+                                   const double *nu_thz, const double *eigvec, const kald_options *opt,
+                                   double *gamma0, double *G1);
+
+/* Conductivity from the full linearised BTE (Eq. inversemeanfreepath,
+ * full_conductivity, conductivity_from_lambda; mean free displacements from
+ * 2 (Gamma^0 + Gamma^1) lambda = v, the printed v = Gamma~ lambda read with the
+ * factor 2 of tau = 1/(2 Gamma^0) so that Gamma^1 = 0 gives Eq. RTA):
+ *   kappa_ab = 1/(N_k V) sum_mu c_mu v_mu,a lambda_mu,b   (W/(m K)),
+ * v the diagonal group velocities in the basis of `eigvec`; modes with
+ * nu < omega_min or Gamma^0 <= 0 are left out.
+ *   method    0: Jacobi-preconditioned BiCGSTAB (the operator is only nearly
+ *             symmetric with a finite-width delta), stopping at residual
+ *             <= tol |v| per direction; 1: the self-consistent series of Eq.
+ *             mfp_from_scattering_inv / self-consistent, stopping when the
+ *             newest term is <= tol of the sum
+ *   n_iter    out or NULL: iterations used
+ * KALD_E_NOCONV (kappa still written) when max_iter is reached or the
+ * iteration breaks down; the series needs the spectral radius of
+ * Gamma^1 / Gamma^0 below 1. */
+kald_status kald_kappa_bte(kald_ctx *ctx, const kald_system *sys, const int32_t mesh[3], const double *nu_thz,
+                           const double *eigvec, const kald_options *opt, int32_t method, double tol,
+                           int32_t max_iter, double *kappa, int32_t *n_iter);
+
 /* Phase space per mode (the definition after Eq. delta_deconstructed, with
  * the weights of Eq. phase_space): the linewidth sum without the matrix
  * elements,

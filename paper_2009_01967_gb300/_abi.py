@@ -28,7 +28,8 @@ EXPORTS = ["kald_ctx_create", "kald_ctx_destroy", "kald_last_error", "kald_set_s
            "kald_phonons", "kald_linewidths", "kald_kappa_rta", "kald_kappa_qhgk",
            "kald_kappa_rta_noalloc", "kald_kernel_launches", "kald_set_wait_limit",
            "kald_set_workspace_limit", "kald_profile_enable", "kald_profile_read",
-           "kald_linewidths_qrange", "kald_phonons_batch", "kald_phase_space", "kald_diffusivity"]
+           "kald_linewidths_qrange", "kald_phonons_batch", "kald_phase_space", "kald_diffusivity",
+           "kald_scattering_matrix", "kald_kappa_bte"]
 PROF_KERNELS = {"tcx_gather": 0, "tcx_gemm1": 1, "tcx_gemm2": 2, "tc_gemm1": 3, "tc_gemm2": 4,
                 "small_nb": 5, "lw_main": 6}
 
@@ -74,6 +75,12 @@ def load_library(path: str = LIB_PATH):
     lib.kald_set_stream.restype = st
     lib.kald_phonons.argtypes = [vp, C.POINTER(kald_system), C.POINTER(i32), vp, vp, vp]
     lib.kald_phonons.restype = st
+    lib.kald_scattering_matrix.argtypes = [vp, C.POINTER(kald_system), C.POINTER(i32), vp, vp,
+                                           C.POINTER(kald_options), vp, vp]
+    lib.kald_scattering_matrix.restype = st
+    lib.kald_kappa_bte.argtypes = [vp, C.POINTER(kald_system), C.POINTER(i32), vp, vp, C.POINTER(kald_options),
+                                   i32, C.c_double, i32, vp, C.POINTER(i32)]
+    lib.kald_kappa_bte.restype = st
     lib.kald_phase_space.argtypes = [vp, C.POINTER(kald_system), C.POINTER(i32), vp, C.POINTER(kald_options), vp]
     lib.kald_phase_space.restype = st
     lib.kald_diffusivity.argtypes = [vp, i32, C.POINTER(kald_system), vp, vp, vp, C.POINTER(kald_options), vp]
@@ -328,6 +335,46 @@ def kald_linewidths_qrange(ctx: Context, system, mesh, nu_thz, eigvec, options: 
                                              _ptr(gamma, np.float64, max(n_out, 0), "gamma"), trip))
     del keep
     return gamma, (int(trip[0]), int(trip[1]))
+
+
+def kald_scattering_matrix(ctx: Context, system, mesh, nu_thz, eigvec, options: Options):
+    """(Gamma^0 [N], Gamma^1 [N, N]) of the linearised BTE, N = Nq nb (host arrays)."""
+    cs, keep = c_system(system)
+    m, nq = _mesh(mesh)
+    nb = 3 * cs.n_atoms
+    N = nq * nb
+    g0 = np.zeros(N)
+    G1 = np.zeros((N, N))
+    opt = options.c()
+    ctx.check(ctx.lib.kald_scattering_matrix(ctx.handle, C.byref(cs), m, _ptr(nu_thz, np.float64, N, "nu_thz"),
+                                             _ptr(eigvec, np.complex128, N * nb, "eigvec"), C.byref(opt),
+                                             _ptr(g0, np.float64, N, "gamma0"), _ptr(G1, np.float64, N * N, "G1")))
+    del keep
+    return g0, G1
+
+
+BTE_METHOD = {"krylov": 0, "self_consistent": 1}
+
+
+def kald_kappa_bte(ctx: Context, system, mesh, nu_thz, eigvec, options: Options, method: str = "krylov",
+                   tol: float = 1e-10, max_iter: int = 500, kappa=None):
+    """kappa [3, 3] (W/(m K)) from the full linearised BTE; returns (kappa, iterations).
+    Raises KaldError (KALD_E_NOCONV) when the iteration does not converge."""
+    cs, keep = c_system(system)
+    m, nq = _mesh(mesh)
+    nb = 3 * cs.n_atoms
+    N = nq * nb
+    if kappa is None:
+        kappa = np.zeros((3, 3))
+    it = C.c_int32()
+    opt = options.c()
+    status = ctx.lib.kald_kappa_bte(ctx.handle, C.byref(cs), m, _ptr(nu_thz, np.float64, N, "nu_thz"),
+                                    _ptr(eigvec, np.complex128, N * nb, "eigvec"), C.byref(opt),
+                                    BTE_METHOD[method], float(tol), int(max_iter), _ptr(kappa, np.float64, 9, "kappa"),
+                                    C.byref(it))
+    del keep
+    ctx.check(status)
+    return kappa, int(it.value)
 
 
 def kald_phase_space(ctx: Context, system, mesh, nu_thz, options: Options, g=None):

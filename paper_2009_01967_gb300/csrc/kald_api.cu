@@ -16,6 +16,7 @@
 #include <unordered_map>
 
 #include "kald_internal.h"
+#include "wdiff.cuh"
 
 namespace kald {
 
@@ -1002,12 +1003,19 @@ static kald_status gamma_only_batch(kald_ctx *ctx, int n_sys, const kald_system 
     return KALD_OK;
 }
 
+// Full-BTE assembly requested from the linewidth pass: the three operator
+// planes (device, [N][N] each, zeroed by the caller) and the flat index of -q.
+struct BteHook {
+    double *g1_a, *g1_am, *g1_b;
+    const int *qneg;
+};
+
 // Linewidths of every system (q_end < 0), or of the q-points [q_begin, q_end)
-// of one crystal.
+// of one crystal; with `bte`, also the scattering-operator planes (FP64 paths).
 static kald_status linewidths_impl(kald_ctx *ctx, int32_t n_sys, const kald_system *sys,
                                    const int32_t mesh[3], const double *nu_thz, const double *eigvec,
                                    const kald_options *opt, int32_t q_begin, int32_t q_end, double *gamma,
-                                   uint64_t *n_triplets) {
+                                   uint64_t *n_triplets, const BteHook *bte = nullptr) {
     if (!ctx) return KALD_E_INVALID;
     kald_status st = set_device(ctx);
     if (st) return st;
@@ -1082,6 +1090,9 @@ static kald_status linewidths_impl(kald_ctx *ctx, int32_t n_sys, const kald_syst
         p.prof = &ctx->prof;
         p.q0 = q0;
         p.q1 = q1;
+        p.bte = bte ? 1 : 0;
+        p.bte_pref = kHbarEvPs * kPi / 8.0 * kEvA2AmuPs2 * kEvA2AmuPs2 * kEvA2AmuPs2 / (double)nq /
+                     (1.0 / delta_norm(opt->delta_shape, p.sigma_w));
         // about 64 items per SM for balance, q' chunks as long as that allows
         {
             const long long want = 64LL * std::max(1, ctx->sm_count);
@@ -1167,6 +1178,10 @@ static kald_status linewidths_impl(kald_ctx *ctx, int32_t n_sys, const kald_syst
         d.partial = static_cast<double *>(ws_take(ctx, sizeof(double) * (size_t)nqr * p.n_chunks * nb));
         d.allowed = static_cast<unsigned long long *>(ws_take(ctx, 16));
         d.queue = static_cast<int *>(ws_take(ctx, 16));
+        d.g1_a = bte ? bte->g1_a : nullptr;
+        d.g1_am = bte ? bte->g1_am : nullptr;
+        d.g1_b = bte ? bte->g1_b : nullptr;
+        d.qneg = bte ? bte->qneg : nullptr;
         double *g_d = d_g ? gamma + off_nb : static_cast<double *>(ws_take(ctx, sizeof(double) * nqr * nb));
         void *tc_scr = tcx ? ws_take(ctx, tcx_scratch_bytes(nb, nq, tcx_b)) : nullptr;
         int *tc_err = tcx ? static_cast<int *>(ws_take(ctx, 16)) : nullptr;
@@ -1220,6 +1235,155 @@ static kald_status linewidths_impl(kald_ctx *ctx, int32_t n_sys, const kald_syst
     }
     if (n_triplets) { n_triplets[0] = tot; n_triplets[1] = allowed_tot; }
     return KALD_OK;
+}
+
+// The scattering operator of one crystal (nb <= 96): the unaveraged
+// linewidths Gamma^0 [N] and Gamma^1 [N][N] (N = Nq nb) on the device, in one
+// separately allocated block (planes, -q table, Gamma^0) that the caller frees
+// with cudaFree(*block).  FP64 projection kernels.
+static kald_status bte_assemble(kald_ctx *ctx, const kald_system *sys, const int32_t mesh[3], const double *nu_thz,
+                                const double *eigvec, const kald_options *opt, void **block, double **g1,
+                                double **g0, int &N_out) {
+    *block = nullptr;
+    kald_status st;
+    std::shared_ptr<const HostSystem> hp;
+    if ((st = plan_system_cached(ctx, sys, hp))) return st;
+    const int nb = hp->nb;
+    if (nb > kMaxNbSmall)
+        return fail(ctx, KALD_E_UNSUPPORTED, "full BTE: cells of up to 32 atoms (nb <= 96)");
+    std::vector<double> qc;
+    std::vector<int> qf;
+    mesh_points(hp->lattice, mesh, qc, qf);
+    const int nq = mesh[0] * mesh[1] * mesh[2];
+    const size_t N = (size_t)nq * nb, NN = N * N;
+    if (N > 200000) return fail(ctx, KALD_E_UNSUPPORTED, "full BTE: N_k nb above 200000 (dense operator)");
+    std::vector<int> qneg(nq);
+    for (int x = 0; x < nq; ++x) {
+        const int k0 = (mesh[0] - qf[3 * x]) % mesh[0], k1 = (mesh[1] - qf[3 * x + 1]) % mesh[1],
+                  k2 = (mesh[2] - qf[3 * x + 2]) % mesh[2];
+        qneg[x] = (k0 * mesh[1] + k1) * mesh[2] + k2;
+    }
+    const size_t bytes = 3 * ws_round(sizeof(double) * NN) + ws_round(sizeof(int) * nq) + ws_round(sizeof(double) * N);
+    if (ctx->ws_limit && bytes > ctx->ws_limit)
+        return fail(ctx, KALD_E_NOMEM, "the scattering operator needs " + std::to_string(bytes) +
+                                           " bytes, more than the context's limit");
+    char *b = nullptr;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&b), bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, KALD_E_NOMEM, "cannot allocate " + std::to_string(bytes) + " bytes for the scattering operator");
+    }
+    *block = b;
+    double *pa = reinterpret_cast<double *>(b);
+    double *pam = reinterpret_cast<double *>(b + ws_round(sizeof(double) * NN));
+    double *pb = reinterpret_cast<double *>(b + 2 * ws_round(sizeof(double) * NN));
+    int *qn = reinterpret_cast<int *>(b + 3 * ws_round(sizeof(double) * NN));
+    double *g0d = reinterpret_cast<double *>(b + 3 * ws_round(sizeof(double) * NN) + ws_round(sizeof(int) * nq));
+    e = cudaMemsetAsync(pa, 0, 3 * ws_round(sizeof(double) * NN), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(qn, qneg.data(), sizeof(int) * nq, cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "scattering operator set-up");
+    kald_options o = *opt;
+    o.precision = KALD_FP64;
+    o.degen_tol_thz = 0.0;                       // Gamma^0 unaveraged, as in the operator
+    BteHook hook{pa, pam, pb, qn};
+    if ((st = linewidths_impl(ctx, 1, sys, mesh, nu_thz, eigvec, &o, 0, -1, g0d, nullptr, &hook))) return st;
+    e = bte_combine(NN, pa, pam, pb, ctx->stream);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "scattering operator combine");
+    *g1 = pa;
+    *g0 = g0d;
+    N_out = (int)N;
+    return KALD_OK;
+}
+
+kald_status kald_scattering_matrix(kald_ctx *ctx, const kald_system *sys, const int32_t mesh[3],
+                                   const double *nu_thz, const double *eigvec, const kald_options *opt,
+                                   double *gamma0, double *G1) {
+    if (!ctx) return KALD_E_INVALID;
+    kald_status st = set_device(ctx);
+    if (st) return st;
+    if ((st = check_mesh(ctx, mesh))) return st;
+    if ((st = check_options(ctx, opt))) return st;
+    if (!nu_thz || !eigvec || !gamma0 || !G1) return fail(ctx, KALD_E_INVALID, "NULL array");
+    void *block = nullptr;
+    double *g1 = nullptr, *g0 = nullptr;
+    int N = 0;
+    st = bte_assemble(ctx, sys, mesh, nu_thz, eigvec, opt, &block, &g1, &g0, N);
+    if (st == KALD_OK) {
+        cudaError_t e = cudaMemcpyAsync(gamma0, g0, sizeof(double) * N, cudaMemcpyDefault, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(G1, g1, sizeof(double) * (size_t)N * N, cudaMemcpyDefault, ctx->stream);
+        if (e != cudaSuccess) st = cuda_check(ctx, e, "kald_scattering_matrix copy");
+        else st = finish(ctx, "kald_scattering_matrix");
+    }
+    if (block) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(block);
+    }
+    return st;
+}
+
+kald_status kald_kappa_bte(kald_ctx *ctx, const kald_system *sys, const int32_t mesh[3], const double *nu_thz,
+                           const double *eigvec, const kald_options *opt, int32_t method, double tol,
+                           int32_t max_iter, double *kappa, int32_t *n_iter) {
+    if (!ctx) return KALD_E_INVALID;
+    kald_status st = set_device(ctx);
+    if (st) return st;
+    if ((st = check_mesh(ctx, mesh))) return st;
+    if ((st = check_options(ctx, opt))) return st;
+    if (!nu_thz || !eigvec || !kappa) return fail(ctx, KALD_E_INVALID, "NULL array");
+    if (method != 0 && method != 1) return fail(ctx, KALD_E_INVALID, "method must be 0 (Krylov) or 1 (self-consistent)");
+    if (!(tol > 0.0) || max_iter < 1) return fail(ctx, KALD_E_INVALID, "tol must be > 0 and max_iter >= 1");
+    void *block = nullptr;
+    double *g1 = nullptr, *g0 = nullptr;
+    int N = 0;
+    st = bte_assemble(ctx, sys, mesh, nu_thz, eigvec, opt, &block, &g1, &g0, N);
+    int iters = 0;
+    bool conv = false;
+    if (st == KALD_OK) {
+        std::shared_ptr<const HostSystem> hp;
+        st = plan_system_cached(ctx, sys, hp);
+        if (st == KALD_OK) {
+            const HostSystem &h = *hp;
+            const int nb = h.nb, nq = N / nb;
+            std::vector<double> qc;
+            std::vector<int> qf;
+            mesh_points(h.lattice, mesh, qc, qf);
+            const bool d_nu = is_device_ptr(nu_thz), d_eig = is_device_ptr(eigvec), d_k = is_device_ptr(kappa);
+            size_t need = fc2_bytes(h) + bytes_of(qc) + ws_round(sizeof(double) * 3 * (size_t)N) +
+                          bte_work_bytes(N) + ws_round(72);
+            if (!d_nu) need += ws_round(sizeof(double) * N);
+            if (!d_eig) need += ws_round(sizeof(double2) * (size_t)N * nb);
+            st = ws_reserve(ctx, need);
+            if (st == KALD_OK) {
+                DevSystem d;
+                upload_fc2(ctx, h, d);
+                const double *qcart = upload(ctx, qc);
+                const double *nu_d = stage_in(ctx, nu_thz, (size_t)N, d_nu);
+                const double2 *eig_d = stage_in(ctx, reinterpret_cast<const double2 *>(eigvec), (size_t)N * nb, d_eig);
+                double *vel = static_cast<double *>(ws_take(ctx, sizeof(double) * 3 * (size_t)N));
+                void *work = ws_take(ctx, bte_work_bytes(N));
+                double *k_d = d_k ? kappa : static_cast<double *>(ws_take(ctx, 72));
+                cudaError_t e = launch_velocity_diag(dev_fc2(h, d), nb, nq, qcart, nu_d, eig_d, vel, ctx->stream);
+                if (e == cudaSuccess)
+                    e = bte_solve(N, g1, g0, nu_d, vel, opt->omega_min_thz, opt->temperature_K, opt->classical,
+                                  method, tol, max_iter, work, kKappaSI / ((double)nq * h.volume), k_d, iters, conv,
+                                  ctx->stream);
+                if (e == cudaSuccess && !d_k) e = cudaMemcpyAsync(kappa, k_d, 72, cudaMemcpyDeviceToHost, ctx->stream);
+                if (e != cudaSuccess) st = cuda_check(ctx, e, "kald_kappa_bte");
+                else st = finish(ctx, "kald_kappa_bte");
+            }
+        }
+    }
+    if (block) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(block);
+    }
+    if (n_iter) *n_iter = iters;
+    if (st == KALD_OK && !conv)
+        return fail(ctx, KALD_E_NOCONV, "kald_kappa_bte: no convergence in " + std::to_string(iters) +
+                                            " iterations (the self-consistent series converges only when the "
+                                            "spectral radius of Gamma^1 / Gamma^0 is below 1)");
+    return st;
 }
 
 kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys,

@@ -208,6 +208,8 @@ struct LwParams {
     int qp_chunk;             // q' per work item
     int n_chunks;             // ceil(nq / qp_chunk)
     int q0, q1;               // q-points whose linewidths are computed: [q0, q1)
+    int bte;                  // 1: also scatter the rates into the BTE operator planes (FP64 paths)
+    double bte_pref;          // hbar pi / (8 N_k) (eV/A^2 amu -> ps^-2)^3 x delta normalisation
     uint32_t wait_limit;      // polls of the tensor-core pipeline waits
     Prof *prof;               // per-launch timing (NULL: off); host pointer, never read on the device
 };
@@ -237,6 +239,12 @@ struct LwDev {
     void *eps_work;           // [nq][nb][nb] eps^T in the working precision
     void *chi;                // [nq][n_rep] exp(-i q.R) in the working precision
     double *partial;          // [q1 - q0][n_chunks][nb] FP64 partial sums
+    // full-BTE assembly (p.bte): three [N][N] planes, N = nq nb, row mu = q nb + s:
+    //   g1_a  (w'/w) Gamma^+ summed over s'' at column (q', s')
+    //   g1_am (w'/w) Gamma^- summed over s'' at column (-q', s')
+    //   g1_b  (w''/w) (Gamma^+ + Gamma^-) summed over s' at column (q + q', s'')
+    double *g1_a, *g1_am, *g1_b;
+    const int *qneg;          // [nq] flat index of -q
     unsigned long long *allowed;   // [1] delta-allowed triplet count
     int *queue;               // [1] work counter
 };
@@ -335,6 +343,15 @@ void plan_tcx_parts(const HostSystem &h, int n_parts, std::vector<int> &part_sta
 size_t tcx_scratch_bytes(int nb, int nq, int batch);
 cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups &g, void *scratch, int batch,
                              int sms, int *err, cudaStream_t st);
+
+// bte.cu: the full linearised BTE on the assembled operator
+size_t bte_work_bytes(int N);
+cudaError_t bte_combine(size_t NN, double *a, const double *am, const double *b, cudaStream_t st);
+// method 0: Jacobi-preconditioned BiCGSTAB, 1: the self-consistent series;
+// writes kappa (9 values, scale = KAPPA_SI / (N_k V)) on the device.
+cudaError_t bte_solve(int N, const double *G1, const double *g0, const double *nu, const double *vel,
+                      double omega_min_thz, double T, int classical, int method, double tol, int max_iter,
+                      void *work, double scale, double *kappa_out, int &iters, bool &converged, cudaStream_t st);
 
 // kappa.cu
 cudaError_t launch_kappa_rta(const DevFc2 &f, int nb, int nq, const double *qcart,

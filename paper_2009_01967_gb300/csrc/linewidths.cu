@@ -442,17 +442,32 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
                                     dm = w - w1 - w2;
                                     dn = n1 - n2;
                                 }
-                                R g = (R)0;
+                                R gpv = (R)0, gmv = (R)0;
                                 bool hit = false;
-                                if (fabs(dp) < cut) { g += dn * delta_shape(dp, p.shape, sig2inv); hit = true; }
+                                if (fabs(dp) < cut) { gpv = dn * delta_shape(dp, p.shape, sig2inv); hit = true; }
                                 if (fabs(dm) < cut) {
-                                    g += (R)0.5 * ((R)1 + n1 + n2) * delta_shape(dm, p.shape, sig2inv);
+                                    gmv = (R)0.5 * ((R)1 + n1 + n2) * delta_shape(dm, p.shape, sig2inv);
                                     hit = true;
                                 }
+                                const R g = gpv + gmv;
                                 if (hit) {
                                     ++allowed;
                                     const R2 f = acc[r][c];
-                                    part += (f.x * f.x + f.y * f.y) * g * iw1 / w2;
+                                    const R f2 = f.x * f.x + f.y * f.y;
+                                    part += f2 * g * iw1 / w2;
+                                    if constexpr (!kPair) {
+                                        if (p.bte) {
+                                            // rates into the BTE operator planes (FP64 atomics;
+                                            // every (q, s) row is owned by this item)
+                                            const double sc = p.bte_pref / (w_s * w_s);
+                                            const size_t N = (size_t)p.nq * nb;
+                                            const size_t row = ((size_t)q * nb + s) * N;
+                                            atomicAdd(d.g1_a + row + (size_t)qp * nb + r0 + r, sc * f2 * gpv / w2);
+                                            atomicAdd(d.g1_am + row + (size_t)d.qneg[qp] * nb + r0 + r,
+                                                      sc * f2 * gmv / w2);
+                                            atomicAdd(d.g1_b + row + (size_t)qpp * nb + c0 + c, sc * f2 * g / w1);
+                                        }
+                                    }
                                 }
                             }
                         }

@@ -94,7 +94,9 @@ __global__ void roots_kernel(int L, int m0, int fp32, void *out) {
     else static_cast<double2 *>(out)[t] = make_double2(cs, -sn);
 }
 
-template <typename R, int NB>
+// BTE: each thread also scatters its (q', s) rates into the three operator
+// planes (FP64 only; every plane entry has exactly one writer).
+template <typename R, int NB, bool BTE>
 __global__ void __launch_bounds__(kSnThreads)
 sn_kernel(LwParams p, LwDev d, SnTables t, const R *__restrict__ fc3, const typename Cx<R>::T *__restrict__ epsT) {
     using R2 = typename Cx<R>::T;
@@ -177,6 +179,11 @@ sn_kernel(LwParams p, LwDev d, SnTables t, const R *__restrict__ fc3, const type
         const R2 *e1 = epsT + (size_t)qp * NB * NB;    // e1[b * NB + s']
         const R2 *e2 = epsT + (size_t)qpp * NB * NB;   // e2[c * NB + s'']
         R part = (R)0;
+        R ap[BTE ? NB : 1], am[BTE ? NB : 1], bb[BTE ? NB : 1];
+        if constexpr (BTE) {
+#pragma unroll
+            for (int x = 0; x < NB; ++x) ap[x] = am[x] = bb[x] = (R)0;
+        }
 #pragma unroll
         for (int sp = 0; sp < NB; ++sp) {
             const R w1 = (R)d.omega[(size_t)qp * NB + sp];
@@ -223,14 +230,33 @@ sn_kernel(LwParams p, LwDev d, SnTables t, const R *__restrict__ fc3, const type
                 f.x = f.y = (R)0;
 #pragma unroll
                 for (int c = 0; c < NB; ++c) cfma_conj(f, T[c], __ldg(e2 + c * NB + spp));
-                R g = (R)0;
-                if (hp) g += dn * delta_shape(dp, p.shape, sig2inv);
-                if (hm) g += (R)0.5 * ((R)1 + n1 + n2) * delta_shape(dm, p.shape, sig2inv);
-                part += (f.x * f.x + f.y * f.y) * g / (w1 * w2);
+                const R gpv = hp ? dn * delta_shape(dp, p.shape, sig2inv) : (R)0;
+                const R gmv = hm ? (R)0.5 * ((R)1 + n1 + n2) * delta_shape(dm, p.shape, sig2inv) : (R)0;
+                const R g = gpv + gmv;
+                const R f2 = f.x * f.x + f.y * f.y;
+                part += f2 * g / (w1 * w2);
                 ++allowed;
+                if constexpr (BTE) {
+                    ap[sp] += f2 * gpv / w2;
+                    am[sp] += f2 * gmv / w2;
+                    bb[spp] += f2 * g / w1;
+                }
             }
         }
         sum += (double)part;
+        if constexpr (BTE) {
+            // (w'/w) Gamma = pref |phi|^2 g / (w^2 w''), (w''/w) Gamma = pref |phi|^2 g / (w^2 w')
+            const double sc = p.bte_pref / ((double)w * (double)w);
+            const size_t N = (size_t)p.nq * NB;
+            const size_t row = ((size_t)q * NB + s) * N;
+            const int qm = d.qneg[qp];
+#pragma unroll
+            for (int x = 0; x < NB; ++x) {
+                d.g1_a[row + (size_t)qp * NB + x] = sc * (double)ap[x];
+                d.g1_am[row + (size_t)qm * NB + x] = sc * (double)am[x];
+                d.g1_b[row + (size_t)qpp * NB + x] = sc * (double)bb[x];
+            }
+        }
     }
     red[tid] = sum;
     for (int o = 16; o > 0; o >>= 1) allowed += __shfl_xor_sync(0xffffffffu, allowed, o);
@@ -243,11 +269,11 @@ sn_kernel(LwParams p, LwDev d, SnTables t, const R *__restrict__ fc3, const type
     }
 }
 
-template <typename R, int NB>
+template <typename R, int NB, bool BTE = false>
 cudaError_t run_sn(const LwParams &p, const LwDev &d, const SnTables &t, cudaStream_t st) {
     using R2 = typename Cx<R>::T;
     const size_t smem = sizeof(R2) * ((size_t)(2 * t.m0 + 1) + NB * NB) + 16 + sizeof(double) * kSnThreads;
-    auto k = sn_kernel<R, NB>;
+    auto k = sn_kernel<R, NB, BTE>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     ProfMark pm(p.prof, KALD_PROF_SMALL_NB, st);
@@ -270,6 +296,7 @@ cudaError_t launch_lw_small(const LwParams &p, const LwDev &d, const SnTables &t
     if (e != cudaSuccess) return e;
     roots_kernel<<<counted((2 * t.m0 + 1 + 255) / 256), 256, 0, st>>>(t.L, t.m0, fp32, t.roots);
     if (fp32) return p.nb == 3 ? run_sn<float, 3>(p, d, t, st) : run_sn<float, 6>(p, d, t, st);
+    if (p.bte) return p.nb == 3 ? run_sn<double, 3, true>(p, d, t, st) : run_sn<double, 6, true>(p, d, t, st);
     return p.nb == 3 ? run_sn<double, 3>(p, d, t, st) : run_sn<double, 6>(p, d, t, st);
 }
 
