@@ -1123,7 +1123,7 @@ static kald_status linewidths_impl(kald_ctx *ctx, int32_t n_sys, const kald_syst
             sn_gjk.resize(std::max(1, ng));
             for (int g = 0; g < ng; ++g) sn_gjk[g] = make_int2(h.pair3_j[g], h.pair3_k[g]);
         }
-        const int tcx_b = tcx ? tcx_batch(nb, nq, ctx->sm_count) : 0;
+        const int tcx_b = tcx ? tcx_batch_max(nb, nq, ctx->sm_count) : 0;   // scratch for the tuner's largest batch
         // tensor-core path: the fc3 blocks in (j, k) group order, the groups
         // split over the gather CTAs
         std::vector<int2> tc_gjk;

@@ -338,6 +338,7 @@ struct TcxGroups {
 };
 int tcx_half(int nb);
 int tcx_batch(int nb, int nq, int sm_count);
+int tcx_batch_max(int nb, int nq, int sm_count);
 int tcx_parts(int n_groups);
 void plan_tcx_parts(const HostSystem &h, int n_parts, std::vector<int> &part_start, std::vector<int> &glist);
 size_t tcx_scratch_bytes(int nb, int nq, int batch);

@@ -31,9 +31,13 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdlib>
+#include <map>
+#include <mutex>
 #include <queue>
+#include <vector>
 
 #include "kald_internal.h"
 #include "tc_common.cuh"
@@ -579,9 +583,18 @@ struct Lane {
 // the lane whose batch completes it, after the other lane's latest batch.
 // Batch i starts only after batch i - 3 (the other lane) has finished, which
 // bounds the q values in flight (see tcx_slices).
+// Schedule of the batched pipeline: pairs per launch, row tiles per GEMM CTA,
+// pairs per gather CTA.  The arithmetic of every (pair, mode) is the same for
+// any schedule (fixed-order sums per tile row), so the schedule changes only
+// the time.
+struct TcxSched {
+    int batch, tpc, gp;
+};
+
 template <int BN, int PB>
-cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, Lane *lanes, int batch, int tpc,
-                        double *gacc, int *err) {
+cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, Lane *lanes, TcxSched sc,
+                        long long pbeg, long long pend, bool reduce, double *gacc, int *err) {
+    const int batch = sc.batch, tpc = sc.tpc;
     auto k1 = tcx_gemm_kernel<EPI_T, BN, PB>;
     auto k2 = tcx_gemm_kernel<EPI_PHI, BN, PB>;
     constexpr int smem = Cfg<BN, PB>::kSmem;
@@ -602,17 +615,9 @@ cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, L
     if (e != cudaSuccess) return e;
     const int mt = lanes[0].x.Mp / kBM;
     const int gx = (mt + tpc - 1) / tpc;
-    const long long pbeg = (long long)p.q0 * p.nq, pend = (long long)p.q1 * p.nq;   // pairs of q in [q0, q1)
-    // pairs per gather CTA: 2 when that divides nq and the batch, so that the
-    // CTA's pairs share q (every batch starts at a multiple of the batch);
-    // 2 keeps the registers at ~80 per thread (4 needs ~130)
-    int gp = 1;
-    for (int c = 2; c > 1; c /= 2)
-        if (p.nq % c == 0 && batch % c == 0) { gp = c; break; }
-    if (const char *env = std::getenv("KALD_TCX_GP")) {
-        const int v = std::atoi(env);
-        if (v == 1 || ((v == 2 || v == 4) && p.nq % v == 0 && batch % v == 0)) gp = v;
-    }
+    // pairs per gather CTA (1, 2 or 4): the CTA's pairs must share q, so gp
+    // divides nq and the batch (and the first pair is a multiple of nq)
+    const int gp = (sc.gp > 1 && p.nq % sc.gp == 0 && batch % sc.gp == 0) ? sc.gp : 1;
     const float2 *ew = static_cast<const float2 *>(d.eps_work), *cw = static_cast<const float2 *>(d.chi);
     long long i = 0;
     for (long long p0 = pbeg; p0 < pend; p0 += batch, ++i) {
@@ -648,7 +653,7 @@ cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, L
         if (e != cudaSuccess) return e;
         // q values completed by this batch
         const int qa = (int)(p0 / p.nq), qb = (int)((p0 + x.n_pairs) / p.nq);
-        if (qb > qa) {
+        if (reduce && qb > qa) {
             if (i > 0) {
                 e = cudaStreamWaitEvent(L.st, O.done[((i - 1) >> 1) & 1], 0);
                 if (e != cudaSuccess) return e;
@@ -684,6 +689,12 @@ int tcx_batch(int nb, int nq, int sm_count) {
         if (v > 0) b = v;
     }
     return (int)std::max(1LL, std::min(b, total));
+}
+
+// Largest pairs per launch the autotuner may choose (the scratch is sized for it).
+int tcx_batch_max(int nb, int nq, int sm_count) {
+    const long long total = (long long)nq * nq;
+    return (int)std::max(1LL, std::min<long long>(2LL * tcx_batch(nb, nq, sm_count), total));
 }
 
 int tcx_parts(int n_groups) { return std::max(1, std::min(n_groups, 128)); }
@@ -722,6 +733,83 @@ size_t tcx_scratch_bytes(int nb, int nq, int batch) {
     const size_t ab = ws_round(sizeof(__nv_bfloat16) * (size_t)batch * Kp * Mp);
     return 6 * eb + 8 * ab + ws_round(sizeof(float) * 2 * (size_t)tcx_slices(nq, batch) * nq * nb) +
            ws_round(sizeof(double) * (size_t)nq * nb);
+}
+
+// Autotuner of the crystal pipeline's schedule.  Candidates: pairs per launch
+// b/2, b and 2b (b = tcx_batch, the hand-set default), row tiles per GEMM
+// CTA for one and for two waves of CTAs, one or two pairs per gather CTA.  The
+// first call for a (nb, nq, fc3 groups, SM count) times every candidate on the
+// same first pairs of the workload (both lanes, no reduction: the slots these
+// runs write are written again by the real run, and the counters are reset),
+// keeps the fastest for the rest of the process, and the real run uses it.
+// Any of KALD_TCX_BATCH, KALD_TCX_TPC, KALD_TCX_GP fixes the schedule instead.
+// Problems too small to time (fewer than two samples of pairs) take the default.
+static std::mutex g_tune_mu;
+static std::map<std::array<int, 4>, TcxSched> g_tuned;
+
+template <typename Run>
+TcxSched tcx_schedule(int nb, int nq, int n_groups, int sms, int mt, int batch_max, long long pbeg, long long pend,
+                      Run &run, cudaStream_t st, cudaStream_t aux, cudaEvent_t fork_ev, unsigned long long *allowed,
+                      int *err, cudaError_t &e) {
+    const int b0 = std::max(1, std::min(tcx_batch(nb, nq, sms), batch_max));
+    auto tpc_for = [&](int batch, int waves) {
+        const long long t = ((long long)mt * batch + (long long)sms * waves - 1) / ((long long)sms * waves);
+        return (int)std::max<long long>(1, std::min<long long>(t, mt));
+    };
+    TcxSched def{b0, tpc_for(b0, 1), 2};
+    const char *eb = std::getenv("KALD_TCX_BATCH"), *et = std::getenv("KALD_TCX_TPC"), *eg = std::getenv("KALD_TCX_GP");
+    if (eb || et || eg) {
+        if (eb && std::atoi(eb) > 0) def.batch = std::min(std::atoi(eb), batch_max);
+        def.tpc = tpc_for(def.batch, 1);
+        if (et && std::atoi(et) > 0) def.tpc = std::min(std::atoi(et), mt);
+        if (eg) def.gp = std::atoi(eg);
+        return def;
+    }
+    const std::array<int, 4> key{nb, nq, n_groups, sms};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) return it->second;
+    }
+    std::vector<TcxSched> cand;
+    for (int batch : {std::max(1, b0 / 2), b0, std::min(2 * b0, batch_max)})
+        for (int waves : {1, 2})
+            for (int gp : {1, 2}) {
+                const TcxSched c{batch, tpc_for(batch, waves), gp};
+                bool dup = false;
+                for (const TcxSched &x : cand) dup |= x.batch == c.batch && x.tpc == c.tpc && x.gp == c.gp;
+                if (!dup) cand.push_back(c);
+            }
+    const long long sample = 4LL * std::min(2 * b0, batch_max);
+    if (pend - pbeg < 2 * sample) return def;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if ((e = cudaEventCreate(&t0)) != cudaSuccess || (e = cudaEventCreate(&t1)) != cudaSuccess) return def;
+    TcxSched best = def;
+    float best_ms = 1e30f;
+    for (const TcxSched &c : cand) {
+        if ((e = cudaEventRecord(t0, st)) != cudaSuccess) break;
+        if ((e = cudaEventRecord(fork_ev, st)) != cudaSuccess || (e = cudaStreamWaitEvent(aux, fork_ev, 0)) != cudaSuccess)
+            break;
+        if ((e = run(c, pbeg, pbeg + sample, false)) != cudaSuccess) break;
+        if ((e = cudaEventRecord(fork_ev, aux)) != cudaSuccess || (e = cudaStreamWaitEvent(st, fork_ev, 0)) != cudaSuccess)
+            break;
+        if ((e = cudaEventRecord(t1, st)) != cudaSuccess || (e = cudaEventSynchronize(t1)) != cudaSuccess) break;
+        float ms = 0.0f;
+        if ((e = cudaEventElapsedTime(&ms, t0, t1)) != cudaSuccess) break;
+        if (ms < best_ms) { best_ms = ms; best = c; }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (e != cudaSuccess) return def;
+    // the timing runs counted delta-allowed triplets and may have set the wait flag
+    if ((e = cudaMemsetAsync(allowed, 0, sizeof(unsigned long long), st)) != cudaSuccess) return def;
+    if ((e = cudaMemsetAsync(err, 0, sizeof(int), st)) != cudaSuccess) return def;
+    // the real run's lane 1 starts after the timing runs
+    if ((e = cudaEventRecord(fork_ev, st)) != cudaSuccess || (e = cudaStreamWaitEvent(aux, fork_ev, 0)) != cudaSuccess)
+        return def;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned[key] = best;
+    return best;
 }
 
 // Crystal linewidth sums on tensor cores (nb <= 96).  Needs the FP32 prep
@@ -792,15 +880,6 @@ cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups 
             !make_map3(&L.maps[8], b2m, Kp, BN, nq, BN) || !make_map3(&L.maps[9], b2l, Kp, BN, nq, BN))
             return cudaErrorInvalidValue;
     }
-    // tiles per GEMM CTA: at most one wave of CTAs per batch (each CTA loads
-    // its B operand once); KALD_TCX_TPC overrides (tuning)
-    const int mt = Mp / kBM;
-    int tpc = (int)std::max<long long>(1, ((long long)mt * batch + sms - 1) / sms);
-    if (const char *env = std::getenv("KALD_TCX_TPC")) {
-        const int v = std::atoi(env);
-        if (v > 0) tpc = v;
-    }
-    tpc = std::min(tpc, mt);
     // second lane: its own stream, forked from and joined back into st
     cudaStream_t aux = nullptr;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -811,11 +890,17 @@ cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups 
     if (e == cudaSuccess) {
         lanes[0].st = st; lanes[0].done[0] = ev[0]; lanes[0].done[1] = ev[1];
         lanes[1].st = aux; lanes[1].done[0] = ev[2]; lanes[1].done[1] = ev[3];
-        switch (BN) {
-            case 64: e = run_batches<64, 3>(p, d, g, lanes, batch, tpc, gacc, err); break;
-            case 128: e = run_batches<128, 3>(p, d, g, lanes, batch, tpc, gacc, err); break;
-            default: e = run_batches<192, 2>(p, d, g, lanes, batch, tpc, gacc, err); break;
-        }
+        auto run = [&](TcxSched sc, long long b0, long long b1, bool reduce) -> cudaError_t {
+            switch (BN) {
+                case 64: return run_batches<64, 3>(p, d, g, lanes, sc, b0, b1, reduce, gacc, err);
+                case 128: return run_batches<128, 3>(p, d, g, lanes, sc, b0, b1, reduce, gacc, err);
+                default: return run_batches<192, 2>(p, d, g, lanes, sc, b0, b1, reduce, gacc, err);
+            }
+        };
+        const long long pbeg = (long long)p.q0 * nq, pend = (long long)p.q1 * nq;   // pairs of q in [q0, q1)
+        const TcxSched sc = tcx_schedule(nb, nq, g.n_groups, sms, Mp / kBM, batch, pbeg, pend, run, st, aux, ev[4],
+                                         d.allowed, err, e);
+        if (e == cudaSuccess) e = run(sc, pbeg, pend, true);
     }
     // join (also after an error, so that nothing is left running on aux)
     if (aux && ev[4]) {
