@@ -133,30 +133,88 @@ def generalized_heat_capacity(omega, T, degen_tol_omega, classical=False):
     return np.where(close, cmid, cc)
 
 
-def lorentzian_tau(omega, gamma):
-    """tau_{mu mu'} [nb, nb] in ps (Eq. lorentzian_amorphous)."""
+def lorentzian_tau(omega, gamma, bandwidth_w=None, threshold_w=None):
+    """tau_{mu mu'} [nb, nb] in ps (Eq. lorentzian_amorphous).
+
+    Options of the QHGK engine (code-details appendix), readings:
+      bandwidth_w  a fixed width (rad/ps) in place of gamma + gamma' for every
+                   pair -- the Allen-Feldman model the appendix names;
+      threshold_w  tau = 0 for pairs with |omega - omega'| > threshold (the
+                   printed '<' would discard the near-degenerate pairs that
+                   carry the diffusive transport, so it is read reversed)."""
     gs = gamma[:, None] + gamma[None, :]
+    if bandwidth_w is not None:
+        gs = np.full_like(gs, float(bandwidth_w))
     dw = omega[:, None] - omega[None, :]
     den = dw * dw + gs * gs
-    return np.where(den > 0, gs / np.where(den > 0, den, 1.0), 0.0)
+    tau = np.where(den > 0, gs / np.where(den > 0, den, 1.0), 0.0)
+    if threshold_w is not None:
+        tau = np.where(np.abs(dw) > threshold_w, 0.0, tau)
+    return tau
 
 
 def kappa_qhgk(sys, nu, eig, gamma, T, omega_min_thz=0.01, degen_tol_thz=1e-5,
-               classical=False, W=None):
-    """3x3 kappa (W/(m K)) of a Gamma-only system (Eq. conductivity_amorphous)."""
+               classical=False, W=None, bandwidth_thz=None, threshold_thz=None):
+    """3x3 kappa (W/(m K)) of a Gamma-only system (Eq. conductivity_amorphous).
+    With bandwidth_thz the linewidths are not used (every mode with
+    nu > omega_min takes part) and gamma + gamma' becomes 2 pi bandwidth;
+    threshold_thz drops the pairs with |d nu| > threshold (lorentzian_tau)."""
     omega = TWO_PI * nu[0]
-    valid = (nu[0] > omega_min_thz) & (gamma > 0)
+    if bandwidth_thz is None:
+        valid = (nu[0] > omega_min_thz) & (gamma > 0)
+    else:
+        valid = nu[0] > omega_min_thz
     if W is None:
         W = generalized_velocity(sys, nu, eig, omega_min_thz)
     cc = generalized_heat_capacity(np.where(valid, omega, 1.0), T, TWO_PI * degen_tol_thz, classical)
-    tau = lorentzian_tau(omega, np.where(valid, gamma, 0.0))
+    tau = lorentzian_tau(omega, np.where(valid, gamma, 0.0),
+                         None if bandwidth_thz is None else TWO_PI * bandwidth_thz,
+                         None if threshold_thz is None else TWO_PI * threshold_thz)
     pair = valid[:, None] & valid[None, :]
     wgt = np.where(pair, cc * tau, 0.0)
     kappa = np.einsum("mn,amn,bmn->ab", wgt, W, W)
     return kappa * KAPPA_SI / sys.volume
 
 
-def diffusivity(sys, nu, eig, gamma, omega_min_thz=0.01, W=None):
+def interpolate_gamma(nu_src, gamma_src, nu_dst, omega_min_thz=0.01, degen_tol_thz=1e-5):
+    """Linewidths of a large system from those of a smaller one, as a function
+    of frequency (the QHGK section's interpolation of lifetimes with
+    third-order splines, read as a cubic spline of gamma(nu)):
+      * source modes with nu <= omega_min or gamma <= 0 are left out, and
+        frequencies closer than degen_tol are merged (their gamma averaged) so
+        that the abscissae increase strictly;
+      * the spline is scipy's CubicSpline with not-a-knot ends;
+      * destination modes with nu <= omega_min get 0; outside the source
+        range gamma is held at the nearest end value (no extrapolation, so it
+        cannot turn negative).
+    Returns gamma_dst (same shape as nu_dst)."""
+    from scipy.interpolate import CubicSpline
+    nu_src = np.asarray(nu_src, float).reshape(-1)
+    g_src = np.asarray(gamma_src, float).reshape(-1)
+    keep = (nu_src > omega_min_thz) & (g_src > 0)
+    x = nu_src[keep]
+    y = g_src[keep]
+    o = np.argsort(x, kind="stable")
+    x, y = x[o], y[o]
+    xs, ys = [], []
+    i = 0
+    while i < len(x):
+        j = i + 1
+        while j < len(x) and x[j] - x[j - 1] < degen_tol_thz:
+            j += 1
+        xs.append(np.mean(x[i:j]))
+        ys.append(np.mean(y[i:j]))
+        i = j
+    xs, ys = np.array(xs), np.array(ys)
+    nu_dst = np.asarray(nu_dst, float)
+    out = np.zeros_like(nu_dst)
+    live = nu_dst > omega_min_thz
+    xq = np.clip(nu_dst[live], xs[0], xs[-1])
+    out[live] = CubicSpline(xs, ys, bc_type="not-a-knot")(xq)
+    return out
+
+
+def diffusivity(sys, nu, eig, gamma, omega_min_thz=0.01, W=None, bandwidth_thz=None, threshold_thz=None):
     """Mode diffusivity D_mu [nb] (A^2/ps) of a Gamma-only system, Eq.
     diffusivity_per_mode read as D_mu = (1/3) sum_a sum_mu' |v^a_{mu mu'}|^2 tau_{mu mu'}
     (the Allen-Feldman diffusivity averaged over the three directions; the
@@ -164,10 +222,15 @@ def diffusivity(sys, nu, eig, gamma, omega_min_thz=0.01, W=None):
     With classical populations c_{mu mu'} = kB, so that tr(kappa_QHGK) / 3 =
     kB / V sum_mu D_mu."""
     omega = TWO_PI * nu[0]
-    valid = (nu[0] > omega_min_thz) & (gamma > 0)
+    if bandwidth_thz is None:
+        valid = (nu[0] > omega_min_thz) & (gamma > 0)
+    else:
+        valid = nu[0] > omega_min_thz
     if W is None:
         W = generalized_velocity(sys, nu, eig, omega_min_thz)
-    tau = lorentzian_tau(omega, np.where(valid, gamma, 0.0))
+    tau = lorentzian_tau(omega, np.where(valid, gamma, 0.0),
+                         None if bandwidth_thz is None else TWO_PI * bandwidth_thz,
+                         None if threshold_thz is None else TWO_PI * threshold_thz)
     pair = valid[:, None] & valid[None, :]
     D = np.einsum("amn,mn->m", W * W, np.where(pair, tau, 0.0)) / 3.0
     return np.where(valid, D, 0.0)
