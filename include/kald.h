@@ -99,6 +99,11 @@ typedef struct {
                                   sigma), 1 Lorentzian (half width at half
                                   maximum sigma), 2 triangle (half base sigma);
                                   all truncated at |d nu| < n_sigma sigma     */
+    double qhgk_bandwidth_thz; /* > 0: QHGK with a fixed width 2 pi bandwidth
+                                  in place of gamma + gamma' (the Allen-Feldman
+                                  model; linewidths unused); 0: off          */
+    double qhgk_threshold_thz; /* > 0: tau_{mu mu'} = 0 for |d nu| > threshold
+                                  (QHGK and diffusivity); 0: off             */
 } kald_options;
 
 /* Create a context on CUDA device `device` (own stream, empty workspace).
@@ -289,7 +294,10 @@ kald_status kald_kappa_rta(kald_ctx *ctx, const kald_system *sys, const int32_t 
                            const double *nu_thz, const double *eigvec, const double *gamma,
                            const kald_options *opt, double *kappa);
 
-/* Quasi-harmonic Green-Kubo conductivity of Gamma-only systems (Eq.
+/* (opt->qhgk_bandwidth_thz > 0: the Allen-Feldman model, gamma + gamma'
+ *  replaced by 2 pi bandwidth and the linewidths unused; opt->qhgk_threshold_thz
+ *  > 0: pairs with |d nu| > threshold left out -- the code-details options.)
+ * Quasi-harmonic Green-Kubo conductivity of Gamma-only systems (Eq.
  * conductivity_amorphous, twod_heat_capacity, generalized_velocity,
  * lorentzian_amorphous):
  *   kappa_ab = 1/V sum_{mu mu'} c_{mu mu'} tau_{mu mu'} W_a W_b,
@@ -313,6 +321,18 @@ kald_status kald_kappa_qhgk(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
  *   D  [sum over systems of nb] out */
 kald_status kald_diffusivity(kald_ctx *ctx, int32_t n_sys, const kald_system *sys, const double *nu_thz,
                              const double *eigvec, const double *gamma, const kald_options *opt, double *D);
+
+/* Linewidths of a large Gamma-only system from those of a smaller one, as a
+ * function of frequency (the QHGK section's interpolation of lifetimes with
+ * third-order splines, read as a cubic spline gamma(nu) with not-a-knot
+ * ends): source modes with nu <= omega_min or gamma <= 0 are left out,
+ * frequencies closer than degen_tol are merged (gamma averaged), and the
+ * destination modes get the spline's value -- held at the end values outside
+ * the source range, 0 for nu <= omega_min.  Two knots give a line, three a
+ * parabola.  FP64; all arrays host or device.
+ *   nu_src, gamma_src  [n_src]     nu_dst, gamma_dst  [n_dst] */
+kald_status kald_interpolate_gamma(kald_ctx *ctx, int32_t n_src, const double *nu_src, const double *gamma_src,
+                                   int32_t n_dst, const double *nu_dst, const kald_options *opt, double *gamma_dst);
 
 /* kald_kappa_rta for callers that cannot allocate device memory.  The paper
  * has no counterpart: this is an interface addition, not part of the method.

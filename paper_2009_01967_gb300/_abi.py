@@ -29,7 +29,7 @@ EXPORTS = ["kald_ctx_create", "kald_ctx_destroy", "kald_last_error", "kald_set_s
            "kald_kappa_rta_noalloc", "kald_kernel_launches", "kald_set_wait_limit",
            "kald_set_workspace_limit", "kald_profile_enable", "kald_profile_read",
            "kald_linewidths_qrange", "kald_phonons_batch", "kald_phase_space", "kald_diffusivity",
-           "kald_scattering_matrix", "kald_kappa_bte"]
+           "kald_scattering_matrix", "kald_kappa_bte", "kald_interpolate_gamma"]
 PROF_KERNELS = {"tcx_gather": 0, "tcx_gemm1": 1, "tcx_gemm2": 2, "tc_gemm1": 3, "tc_gemm2": 4,
                 "small_nb": 5, "lw_main": 6}
 
@@ -50,7 +50,8 @@ class kald_system(C.Structure):
 class kald_options(C.Structure):
     _fields_ = [("temperature_K", C.c_double), ("sigma_thz", C.c_double), ("n_sigma", C.c_double),
                 ("omega_min_thz", C.c_double), ("degen_tol_thz", C.c_double),
-                ("classical", C.c_int32), ("precision", C.c_int32), ("delta_shape", C.c_int32)]
+                ("classical", C.c_int32), ("precision", C.c_int32), ("delta_shape", C.c_int32),
+                ("qhgk_bandwidth_thz", C.c_double), ("qhgk_threshold_thz", C.c_double)]
 
 
 _lib = None
@@ -81,6 +82,8 @@ def load_library(path: str = LIB_PATH):
     lib.kald_kappa_bte.argtypes = [vp, C.POINTER(kald_system), C.POINTER(i32), vp, vp, C.POINTER(kald_options),
                                    i32, C.c_double, i32, vp, C.POINTER(i32)]
     lib.kald_kappa_bte.restype = st
+    lib.kald_interpolate_gamma.argtypes = [vp, i32, vp, vp, i32, vp, C.POINTER(kald_options), vp]
+    lib.kald_interpolate_gamma.restype = st
     lib.kald_phase_space.argtypes = [vp, C.POINTER(kald_system), C.POINTER(i32), vp, C.POINTER(kald_options), vp]
     lib.kald_phase_space.restype = st
     lib.kald_diffusivity.argtypes = [vp, i32, C.POINTER(kald_system), vp, vp, vp, C.POINTER(kald_options), vp]
@@ -131,11 +134,14 @@ class Options:
     classical: bool = False
     precision: str = "fp64"
     delta: str = "gaussian"
+    qhgk_bandwidth_thz: float = 0.0
+    qhgk_threshold_thz: float = 0.0
 
     def c(self) -> kald_options:
         return kald_options(self.temperature_K, self.sigma_thz, self.n_sigma, self.omega_min_thz,
                             self.degen_tol_thz, int(bool(self.classical)), PRECISION[self.precision],
-                            DELTA_SHAPE[self.delta])
+                            DELTA_SHAPE[self.delta], float(self.qhgk_bandwidth_thz),
+                            float(self.qhgk_threshold_thz))
 
 
 class Context:
@@ -375,6 +381,20 @@ def kald_kappa_bte(ctx: Context, system, mesh, nu_thz, eigvec, options: Options,
     del keep
     ctx.check(status)
     return kappa, int(it.value)
+
+
+def kald_interpolate_gamma(ctx: Context, nu_src, gamma_src, nu_dst, options: Options, gamma_dst=None):
+    """gamma at nu_dst from (nu_src, gamma_src) by a not-a-knot cubic spline of gamma(nu)."""
+    n_src = int(np.asarray(nu_src).size) if isinstance(nu_src, np.ndarray) else int(nu_src.numel())
+    n_dst = int(np.asarray(nu_dst).size) if isinstance(nu_dst, np.ndarray) else int(nu_dst.numel())
+    if gamma_dst is None:
+        gamma_dst = np.zeros(n_dst)
+    opt = options.c()
+    ctx.check(ctx.lib.kald_interpolate_gamma(ctx.handle, n_src, _ptr(nu_src, np.float64, n_src, "nu_src"),
+                                             _ptr(gamma_src, np.float64, n_src, "gamma_src"), n_dst,
+                                             _ptr(nu_dst, np.float64, n_dst, "nu_dst"), C.byref(opt),
+                                             _ptr(gamma_dst, np.float64, n_dst, "gamma_dst")))
+    return gamma_dst
 
 
 def kald_phase_space(ctx: Context, system, mesh, nu_thz, options: Options, g=None):

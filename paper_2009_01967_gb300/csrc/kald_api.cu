@@ -801,6 +801,9 @@ static kald_status check_options(kald_ctx *ctx, const kald_options *o) {
         return fail(ctx, KALD_E_INVALID, "unknown precision");
     if (o->delta_shape < 0 || o->delta_shape > 2)
         return fail(ctx, KALD_E_INVALID, "delta_shape must be 0 (Gaussian), 1 (Lorentzian) or 2 (triangle)");
+    if (!(o->qhgk_bandwidth_thz >= 0.0) || !(o->qhgk_threshold_thz >= 0.0) || !std::isfinite(o->qhgk_bandwidth_thz) ||
+        !std::isfinite(o->qhgk_threshold_thz))
+        return fail(ctx, KALD_E_INVALID, "qhgk bandwidth and threshold must be finite and >= 0");
     return KALD_OK;
 }
 
@@ -1492,8 +1495,9 @@ kald_status kald_diffusivity(kald_ctx *ctx, int32_t n_sys, const kald_system *sy
         double *W = static_cast<double *>(ws_take(ctx, sizeof(double) * 3 * nn));
         double *omega = static_cast<double *>(ws_take(ctx, sizeof(double) * nb));
         double *D_d = d_D ? D + off_nb : static_cast<double *>(ws_take(ctx, sizeof(double) * nb));
-        cudaError_t e = launch_diffusivity(f, nb, nu_d, eig_d, g_d, opt->omega_min_thz, E, B, W, omega, D_d,
-                                           ctx->stream);
+        cudaError_t e = launch_diffusivity(f, nb, nu_d, eig_d, g_d, opt->omega_min_thz,
+                                           kTwoPi * opt->qhgk_bandwidth_thz, kTwoPi * opt->qhgk_threshold_thz, E, B,
+                                           W, omega, D_d, ctx->stream);
         if (e != cudaSuccess) return cuda_check(ctx, e, "kald_diffusivity launch");
         if (!d_D) cudaMemcpyAsync(D + off_nb, D_d, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->stream);
         if ((st = finish(ctx, "kald_diffusivity"))) return st;
@@ -1501,6 +1505,34 @@ kald_status kald_diffusivity(kald_ctx *ctx, int32_t n_sys, const kald_system *sy
         off_eig += nn;
     }
     return KALD_OK;
+}
+
+kald_status kald_interpolate_gamma(kald_ctx *ctx, int32_t n_src, const double *nu_src, const double *gamma_src,
+                                   int32_t n_dst, const double *nu_dst, const kald_options *opt, double *gamma_dst) {
+    if (!ctx) return KALD_E_INVALID;
+    kald_status st = set_device(ctx);
+    if (st) return st;
+    if ((st = check_options(ctx, opt))) return st;
+    if (n_src <= 0 || n_dst <= 0 || !nu_src || !gamma_src || !nu_dst || !gamma_dst)
+        return fail(ctx, KALD_E_INVALID, "kald_interpolate_gamma: empty or NULL arrays");
+    const bool d1 = is_device_ptr(nu_src), d2 = is_device_ptr(gamma_src), d3 = is_device_ptr(nu_dst),
+               d4 = is_device_ptr(gamma_dst);
+    size_t need = interp_work_bytes(n_src);
+    if (!d1) need += ws_round(sizeof(double) * n_src);
+    if (!d2) need += ws_round(sizeof(double) * n_src);
+    if (!d3) need += ws_round(sizeof(double) * n_dst);
+    if (!d4) need += ws_round(sizeof(double) * n_dst);
+    if ((st = ws_reserve(ctx, need))) return st;
+    const double *a = stage_in(ctx, nu_src, (size_t)n_src, d1);
+    const double *b = stage_in(ctx, gamma_src, (size_t)n_src, d2);
+    const double *c = stage_in(ctx, nu_dst, (size_t)n_dst, d3);
+    double *out = d4 ? gamma_dst : static_cast<double *>(ws_take(ctx, sizeof(double) * n_dst));
+    void *work = ws_take(ctx, interp_work_bytes(n_src));
+    cudaError_t e = launch_interpolate_gamma(n_src, a, b, n_dst, c, out, opt->omega_min_thz, opt->degen_tol_thz, work,
+                                             ctx->stream);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "kald_interpolate_gamma launch");
+    if (!d4) cudaMemcpyAsync(gamma_dst, out, sizeof(double) * n_dst, cudaMemcpyDeviceToHost, ctx->stream);
+    return finish(ctx, "kald_interpolate_gamma");
 }
 
 kald_status kald_kappa_rta(kald_ctx *ctx, const kald_system *sys, const int32_t mesh[3],
@@ -1629,8 +1661,9 @@ kald_status kald_kappa_qhgk(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
         const Dev &dv = devs[x];
         const HostSystem &h = *items[x].hp;
         e = launch_qhgk(dv.f, h.nb, dv.nu, dv.eig, dv.g, opt->temperature_K, opt->classical, opt->omega_min_thz,
-                        opt->degen_tol_thz, dv.E, dv.B, dv.W, dv.partial, items[x].n_partial, dv.k,
-                        kKappaSI / h.volume, lanes[x % lanes.size()]);
+                        opt->degen_tol_thz, kTwoPi * opt->qhgk_bandwidth_thz, kTwoPi * opt->qhgk_threshold_thz,
+                        dv.E, dv.B, dv.W, dv.partial, items[x].n_partial, dv.k, kKappaSI / h.volume,
+                        lanes[x % lanes.size()]);
     }
     const cudaError_t ej = join_lanes(ctx, lanes);
     if (e == cudaSuccess) e = ej;

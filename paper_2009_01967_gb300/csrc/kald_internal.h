@@ -369,17 +369,26 @@ struct DevFc2Dist {
 };
 // Mode diffusivity D [nb] (A^2/ps) of a Gamma-only system (generalised
 // velocity as for QHGK, then the per-mode sum); omega [nb] scratch.
+// bandwidth_w > 0: fixed width in place of gamma + gamma'; threshold_w > 0:
+// pairs with |d omega| > threshold left out (rad/ps, as for launch_qhgk).
 cudaError_t launch_diffusivity(const DevFc2Dist &f, int nb, const double *nu_thz, const double2 *eig,
-                               const double *gamma, double omega_min_thz, double *Ework, double *Bwork,
-                               double *W, double *omega, double *D, cudaStream_t st);
+                               const double *gamma, double omega_min_thz, double bandwidth_w, double threshold_w,
+                               double *Ework, double *Bwork, double *W, double *omega, double *D, cudaStream_t st);
 // FP32 pairs (hi, lo) of omega and occ (linewidths.cu).
 cudaError_t launch_wn_pairs(int n, const double *omega, const double *occ, float4 *wn32, cudaStream_t st);
 // Phase space per mode (linewidths.cu): g [(q1 - q0) * nb] in ps.
 cudaError_t launch_phase_space(const LwParams &p, const LwDev &d, int fp32, double *g_out, cudaStream_t st);
 cudaError_t launch_qhgk(const DevFc2Dist &f, int nb, const double *nu_thz, const double2 *eig,
                         const double *gamma, double T, int classical, double omega_min_thz,
-                        double degen_tol_thz, double *Ework /*[nb*nb]*/, double *Bwork /*[3][nb][nb]*/,
+                        double degen_tol_thz, double bandwidth_w, double threshold_w,
+                        double *Ework /*[nb*nb]*/, double *Bwork /*[3][nb][nb]*/,
                         double *W /*[3][nb][nb]*/, double *partial, int n_partial,
                         double *kappa_out /*[9]*/, double scale, cudaStream_t st);
+// gamma(nu) by a not-a-knot cubic spline through the valid source modes
+// (interp.cu); work of interp_work_bytes(n_src).
+size_t interp_work_bytes(int n_src);
+cudaError_t launch_interpolate_gamma(int n_src, const double *nu_src, const double *g_src, int n_dst,
+                                     const double *nu_dst, double *g_dst, double omega_min_thz, double degen_tol_thz,
+                                     void *work, cudaStream_t st);
 
 }  // namespace kald

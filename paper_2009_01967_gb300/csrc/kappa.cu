@@ -308,7 +308,7 @@ __global__ void qhgk_modes_kernel(int nb, const double *__restrict__ nu, double 
 __global__ void __launch_bounds__(256)
 qhgk_pairsum_kernel(int nb, const double *__restrict__ W, const double *__restrict__ omega,
                     const double *__restrict__ gamma, double T, int classical, double degen_tol_w,
-                    int rows_per_cta, double *__restrict__ partial) {
+                    double bandwidth_w, double threshold_w, int rows_per_cta, double *__restrict__ partial) {
     __shared__ double red[8 * 9];
     const int r0 = blockIdx.x * rows_per_cta;
     const int r1 = min(nb, r0 + rows_per_cta);
@@ -317,7 +317,8 @@ qhgk_pairsum_kernel(int nb, const double *__restrict__ W, const double *__restri
     for (int m = r0; m < r1; ++m) {
         const double w1 = omega[m];
         const double g1 = gamma[m];
-        if (!(w1 > 0.0) || !(g1 > 0.0)) continue;
+        // with a bandwidth the linewidths are not used (Allen-Feldman)
+        if (!(w1 > 0.0) || (!(bandwidth_w > 0.0) && !(g1 > 0.0))) continue;
         const double n1 = bose(w1, T, classical);
         const double c1 = heat_cap(w1, T, classical);
         const double *W0 = W + (size_t)m * nb;
@@ -325,8 +326,9 @@ qhgk_pairsum_kernel(int nb, const double *__restrict__ W, const double *__restri
         const double *W2 = W + ((size_t)2 * nb + m) * nb;
         for (int n = threadIdx.x; n < nb; n += blockDim.x) {
             const double w2 = omega[n];
-            if (!(w2 > 0.0) || !(gamma[n] > 0.0)) continue;
+            if (!(w2 > 0.0) || (!(bandwidth_w > 0.0) && !(gamma[n] > 0.0))) continue;
             const double dw = w1 - w2;
+            if (threshold_w > 0.0 && fabs(dw) > threshold_w) continue;
             double cc;
             if (fabs(dw) < degen_tol_w) {
                 cc = 0.5 * (c1 + heat_cap(w2, T, classical));
@@ -334,7 +336,7 @@ qhgk_pairsum_kernel(int nb, const double *__restrict__ W, const double *__restri
                 const double n2 = bose(w2, T, classical);
                 cc = hbar_J * (w1 * 1e12) * (w2 * 1e12) / T * (n2 - n1) / (dw * 1e12);
             }
-            const double gs = g1 + gamma[n];
+            const double gs = bandwidth_w > 0.0 ? bandwidth_w : g1 + gamma[n];
             const double tau = gs / (dw * dw + gs * gs);
             const double wgt = cc * tau;
             const double x0 = W0[n], x1 = W1[n], x2 = W2[n];
@@ -355,11 +357,12 @@ qhgk_pairsum_kernel(int nb, const double *__restrict__ W, const double *__restri
 // no part as mu'.  One CTA per mu, threads over mu', fixed-order reduction.
 __global__ void __launch_bounds__(256)
 diffusivity_kernel(int nb, const double *__restrict__ W, const double *__restrict__ omega,
-                   const double *__restrict__ gamma, double *__restrict__ D) {
+                   const double *__restrict__ gamma, double bandwidth_w, double threshold_w, double *__restrict__ D) {
     __shared__ double red[8];
     const int m = blockIdx.x;
     const double w1 = omega[m], g1 = gamma[m];
-    const bool ok = w1 > 0.0 && g1 > 0.0;
+    const bool bw = bandwidth_w > 0.0;
+    const bool ok = w1 > 0.0 && (bw || g1 > 0.0);
     double acc = 0.0;
     if (ok) {
         const double *W0 = W + (size_t)m * nb;
@@ -367,8 +370,9 @@ diffusivity_kernel(int nb, const double *__restrict__ W, const double *__restric
         const double *W2 = W + ((size_t)2 * nb + m) * nb;
         for (int n = threadIdx.x; n < nb; n += blockDim.x) {
             const double w2 = omega[n], g2 = gamma[n];
-            if (!(w2 > 0.0) || !(g2 > 0.0)) continue;
-            const double dw = w1 - w2, gs = g1 + g2;
+            if (!(w2 > 0.0) || (!bw && !(g2 > 0.0))) continue;
+            const double dw = w1 - w2, gs = bw ? bandwidth_w : g1 + g2;
+            if (threshold_w > 0.0 && fabs(dw) > threshold_w) continue;
             const double tau = gs / (dw * dw + gs * gs);
             const double x0 = W0[n], x1 = W1[n], x2 = W2[n];
             acc += (x0 * x0 + x1 * x1 + x2 * x2) * tau;
@@ -397,8 +401,8 @@ cudaError_t launch_kappa_rta(const DevFc2 &f, int nb, int nq, const double *qcar
 }
 
 cudaError_t launch_diffusivity(const DevFc2Dist &f, int nb, const double *nu_thz, const double2 *eig,
-                               const double *gamma, double omega_min_thz, double *Ework, double *Bwork,
-                               double *W, double *omega, double *D, cudaStream_t st) {
+                               const double *gamma, double omega_min_thz, double bandwidth_w, double threshold_w,
+                               double *Ework, double *Bwork, double *W, double *omega, double *D, cudaStream_t st) {
     const size_t nn = (size_t)nb * nb;
     real_part_kernel<<<counted((unsigned)std::min<size_t>((nn + 255) / 256, 8192)), 256, 0, st>>>(nn, eig, Ework);
     const size_t ns = (size_t)f.n_rows * 3 * nb;
@@ -406,14 +410,14 @@ cudaError_t launch_diffusivity(const DevFc2Dist &f, int nb, const double *nu_thz
     qhgk_modes_kernel<<<counted((nb + 255) / 256), 256, 0, st>>>(nb, nu_thz, omega_min_thz, omega);
     dim3 grid((nb + 63) / 64, (nb + 63) / 64, 3);
     dgemm_w_kernel<<<counted(grid), 256, 0, st>>>(nb, Ework, Bwork, omega, W);
-    diffusivity_kernel<<<counted(nb), 256, 0, st>>>(nb, W, omega, gamma, D);
+    diffusivity_kernel<<<counted(nb), 256, 0, st>>>(nb, W, omega, gamma, bandwidth_w, threshold_w, D);
     return cudaGetLastError();
 }
 
 cudaError_t launch_qhgk(const DevFc2Dist &f, int nb, const double *nu_thz, const double2 *eig,
                         const double *gamma, double T, int classical, double omega_min_thz,
-                        double degen_tol_thz, double *Ework, double *Bwork, double *W,
-                        double *partial, int n_partial, double *kappa_out, double scale,
+                        double degen_tol_thz, double bandwidth_w, double threshold_w, double *Ework,
+                        double *Bwork, double *W, double *partial, int n_partial, double *kappa_out, double scale,
                         cudaStream_t st) {
     const size_t nn = (size_t)nb * nb;
     real_part_kernel<<<counted((unsigned)std::min<size_t>((nn + 255) / 256, 8192)), 256, 0, st>>>(nn, eig, Ework);
@@ -426,7 +430,7 @@ cudaError_t launch_qhgk(const DevFc2Dist &f, int nb, const double *nu_thz, const
     const int rows = (nb + n_partial - 1) / n_partial;
     const int nblk = (nb + rows - 1) / rows;
     qhgk_pairsum_kernel<<<counted(nblk), 256, 0, st>>>(nb, W, omega, gamma, T, classical,
-                                              kTwoPi * degen_tol_thz, rows, partial);
+                                              kTwoPi * degen_tol_thz, bandwidth_w, threshold_w, rows, partial);
     sum_partials_kernel<<<counted(1), 32, 0, st>>>(nblk, partial, scale, kappa_out);
     return cudaGetLastError();
 }

@@ -838,3 +838,41 @@ def test_diffusivity_matches_oracle_and_the_classical_trace_identity(k, big324):
     lhs = np.trace(kap[0]) / 3.0
     rhs = kb / s.volume * np.sum(D) * co.KAPPA_SI
     assert abs(lhs - rhs) <= 1e-10 * abs(lhs)
+
+
+# ---------------------------------------------------------------- large-system QHGK options
+@pytest.mark.parametrize("bandwidth,threshold", [(0.2, 0.0), (0.0, 0.5), (0.3, 1.0)])
+def test_qhgk_bandwidth_and_threshold_match_oracle(k, big324, bandwidth, threshold):
+    """The Allen-Feldman bandwidth and the threshold on tau (QHGK options) in
+    kald_kappa_qhgk and kald_diffusivity against the oracle."""
+    kk, ctx = k
+    s, nu_o, eig_o, g_o = big324
+    w = ki.Workload("g324", [s], (1, 1, 1), 300.0, 0.05, 3.0)
+    g = np.ravel(g_o)
+    opt = _opts(kk, w, qhgk_bandwidth_thz=bandwidth, qhgk_threshold_thz=threshold)
+    kw = dict(bandwidth_thz=bandwidth or None, threshold_thz=threshold or None)
+    kap, _ = kk.kald_kappa_qhgk(ctx, [s], nu_o, eig_o, g, opt)
+    kap_o = co.kappa_qhgk(s, nu_o, eig_o, g, 300.0, **kw)
+    np.testing.assert_allclose(kap[0], kap_o, rtol=1e-10, atol=1e-12 * np.abs(kap_o).max())
+    D = kk.kald_diffusivity(ctx, [s], nu_o, eig_o, g, opt)
+    D_o = co.diffusivity(s, nu_o, eig_o, g, **kw)
+    np.testing.assert_allclose(D, D_o, rtol=1e-10, atol=1e-12 * np.abs(D_o).max())
+
+
+def test_interpolate_gamma_matches_oracle(k, big324, c4w):
+    """gamma(nu) of the 108-atom cell spline-interpolated onto the frequencies
+    of a 500-atom cell, against the oracle's scipy spline; and a cubic gamma(nu)
+    reproduced exactly."""
+    kk, ctx = k
+    s, nu_o, eig_o, g_o = big324
+    w, ph_all = c4w
+    nu_dst = np.ascontiguousarray(ph_all[16][0].ravel())
+    opt = _opts(kk, ki.Workload("g", [s], (1, 1, 1), 300.0, 0.05, 3.0))
+    g_dst = kk.kald_interpolate_gamma(ctx, np.ascontiguousarray(nu_o.ravel()), np.ascontiguousarray(np.ravel(g_o)),
+                                      nu_dst, opt)
+    ref = co.interpolate_gamma(nu_o.ravel(), np.ravel(g_o), nu_dst)
+    np.testing.assert_allclose(g_dst, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
+    x = np.linspace(0.3, 9.0, 57)
+    cubic = lambda v: 0.05 + 0.01 * v - 0.002 * v ** 2 + 0.0003 * v ** 3
+    xq = np.linspace(0.3, 9.0, 201)
+    np.testing.assert_allclose(kk.kald_interpolate_gamma(ctx, x, cubic(x), xq, opt), cubic(xq), rtol=1e-11)
