@@ -16,4 +16,4 @@ taken as printed (it agrees with the golden-rule self-energy); no number in
 the paper fixes it for these inputs.
 """
 
-from . import units, phonons, anharmonic, conductivity  # noqa: F401
+from . import units, phonons, anharmonic, conductivity, ifc  # noqa: F401
