@@ -322,6 +322,29 @@ kald_status kald_kappa_qhgk(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
 kald_status kald_diffusivity(kald_ctx *ctx, int32_t n_sys, const kald_system *sys, const double *nu_thz,
                              const double *eigvec, const double *gamma, const kald_options *opt, double *D);
 
+/* A pair potential for kald_fd_force_constants.  kind 0: truncated
+ * Lennard-Jones V(r) = 4 epsilon [(sigma/r)^12 - (sigma/r)^6] for r < cutoff
+ * (eV, Angstrom). */
+typedef struct {
+    int32_t kind;
+    double epsilon, sigma, cutoff;
+} kald_pair_potential;
+
+/* Second and third order force constants by finite differences of forces
+ * (Eq. second_and_third_ifc and the finite-displacement recipe after it),
+ * for the blocks listed in sys->fc2_idx / sys->fc3_idx (the sparsity
+ * pattern; the values in sys are not read), in the same order:
+ *   Phi2_{i a, jR b}         = -[F_{jR b}(+h e_{i a}) - F_{jR b}(-h e_{i a})] / (2 h)
+ *   Phi3_{i a, jRj b, kRk c} = -sum_{s,t=+-1} s t F_{kRk c}(s h e_{i a}, t h e_{jRj b}) / (4 h^2)
+ * with the home-cell-first storage (only home atoms, and one more atom for
+ * the third order, are displaced) and the forces of the infinite crystal
+ * (pairs within the cutoff of the undisplaced structure).  FP64 on the GPU;
+ * the outputs feed a kald_system directly.
+ *   h        displacement (Angstrom), > 0
+ *   fc2_out  [n_fc2][3][3] (eV/A^2), fc3_out [n_fc3][3][3][3] (eV/A^3); host or device */
+kald_status kald_fd_force_constants(kald_ctx *ctx, const kald_system *sys, const kald_pair_potential *pot,
+                                    double h, double *fc2_out, double *fc3_out);
+
 /* Linewidths of a large Gamma-only system from those of a smaller one, as a
  * function of frequency (the QHGK section's interpolation of lifetimes with
  * third-order splines, read as a cubic spline gamma(nu) with not-a-knot

@@ -9,10 +9,12 @@ from ._abi import (Context, KaldError, Options, EXPORTS, LIB_PATH, load_library,
                    kald_phonons, kald_linewidths, kald_kappa_rta, kald_kappa_qhgk,
                    kald_kappa_rta_noalloc, kald_kernel_launches, kald_linewidths_qrange,
                    kald_phonons_batch, kald_phase_space, kald_diffusivity,
-                   kald_scattering_matrix, kald_kappa_bte, kald_interpolate_gamma)
+                   kald_scattering_matrix, kald_kappa_bte, kald_interpolate_gamma,
+                   kald_fd_force_constants)
 
 __all__ = ["Context", "KaldError", "Options", "EXPORTS", "LIB_PATH", "load_library",
            "kald_phonons", "kald_linewidths", "kald_kappa_rta", "kald_kappa_qhgk",
            "kald_kappa_rta_noalloc", "kald_kernel_launches", "kald_linewidths_qrange",
            "kald_phonons_batch", "kald_phase_space", "kald_diffusivity",
-           "kald_scattering_matrix", "kald_kappa_bte", "kald_interpolate_gamma"]
+           "kald_scattering_matrix", "kald_kappa_bte", "kald_interpolate_gamma",
+           "kald_fd_force_constants"]

@@ -29,7 +29,7 @@ EXPORTS = ["kald_ctx_create", "kald_ctx_destroy", "kald_last_error", "kald_set_s
            "kald_kappa_rta_noalloc", "kald_kernel_launches", "kald_set_wait_limit",
            "kald_set_workspace_limit", "kald_profile_enable", "kald_profile_read",
            "kald_linewidths_qrange", "kald_phonons_batch", "kald_phase_space", "kald_diffusivity",
-           "kald_scattering_matrix", "kald_kappa_bte", "kald_interpolate_gamma"]
+           "kald_scattering_matrix", "kald_kappa_bte", "kald_interpolate_gamma", "kald_fd_force_constants"]
 PROF_KERNELS = {"tcx_gather": 0, "tcx_gemm1": 1, "tcx_gemm2": 2, "tc_gemm1": 3, "tc_gemm2": 4,
                 "small_nb": 5, "lw_main": 6}
 
@@ -45,6 +45,10 @@ class kald_system(C.Structure):
                 ("lattice", C.c_double * 9), ("n_fc2", C.c_int32), ("fc2_idx", C.c_void_p),
                 ("fc2", C.c_void_p), ("n_fc3", C.c_int32), ("fc3_idx", C.c_void_p),
                 ("fc3", C.c_void_p)]
+
+
+class kald_pair_potential(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("epsilon", C.c_double), ("sigma", C.c_double), ("cutoff", C.c_double)]
 
 
 class kald_options(C.Structure):
@@ -82,6 +86,9 @@ def load_library(path: str = LIB_PATH):
     lib.kald_kappa_bte.argtypes = [vp, C.POINTER(kald_system), C.POINTER(i32), vp, vp, C.POINTER(kald_options),
                                    i32, C.c_double, i32, vp, C.POINTER(i32)]
     lib.kald_kappa_bte.restype = st
+    lib.kald_fd_force_constants.argtypes = [vp, C.POINTER(kald_system), C.POINTER(kald_pair_potential), C.c_double,
+                                            vp, vp]
+    lib.kald_fd_force_constants.restype = st
     lib.kald_interpolate_gamma.argtypes = [vp, i32, vp, vp, i32, vp, C.POINTER(kald_options), vp]
     lib.kald_interpolate_gamma.restype = st
     lib.kald_phase_space.argtypes = [vp, C.POINTER(kald_system), C.POINTER(i32), vp, C.POINTER(kald_options), vp]
@@ -381,6 +388,20 @@ def kald_kappa_bte(ctx: Context, system, mesh, nu_thz, eigvec, options: Options,
     del keep
     ctx.check(status)
     return kappa, int(it.value)
+
+
+def kald_fd_force_constants(ctx: Context, system, epsilon: float, sigma: float, cutoff: float, h: float = 1e-3):
+    """(fc2 [n_fc2, 3, 3], fc3 [n_fc3, 3, 3, 3]) of a Lennard-Jones pair potential by
+    finite differences on the GPU, for the blocks of `system` (its values unused)."""
+    cs, keep = c_system(system)
+    pot = kald_pair_potential(0, float(epsilon), float(sigma), float(cutoff))
+    fc2 = np.zeros((cs.n_fc2, 3, 3))
+    fc3 = np.zeros((cs.n_fc3, 3, 3, 3))
+    ctx.check(ctx.lib.kald_fd_force_constants(ctx.handle, C.byref(cs), C.byref(pot), float(h),
+                                              fc2.ctypes.data if cs.n_fc2 else None,
+                                              fc3.ctypes.data if cs.n_fc3 else None))
+    del keep
+    return fc2, fc3
 
 
 def kald_interpolate_gamma(ctx: Context, nu_src, gamma_src, nu_dst, options: Options, gamma_dst=None):

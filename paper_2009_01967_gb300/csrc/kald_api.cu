@@ -1535,6 +1535,90 @@ kald_status kald_interpolate_gamma(kald_ctx *ctx, int32_t n_src, const double *n
     return finish(ctx, "kald_interpolate_gamma");
 }
 
+kald_status kald_fd_force_constants(kald_ctx *ctx, const kald_system *sys, const kald_pair_potential *pot,
+                                    double h, double *fc2_out, double *fc3_out) {
+    if (!ctx) return KALD_E_INVALID;
+    kald_status st = set_device(ctx);
+    if (st) return st;
+    if (!pot || pot->kind != 0) return fail(ctx, KALD_E_UNSUPPORTED, "pair potential kind must be 0 (Lennard-Jones)");
+    if (!(pot->epsilon > 0.0) || !(pot->sigma > 0.0) || !(pot->cutoff > 0.0) || !std::isfinite(pot->cutoff))
+        return fail(ctx, KALD_E_INVALID, "Lennard-Jones epsilon, sigma and cutoff must be finite and > 0");
+    if (!(h > 0.0) || !std::isfinite(h)) return fail(ctx, KALD_E_INVALID, "displacement h must be > 0");
+    std::shared_ptr<const HostSystem> hp;
+    if ((st = plan_system_cached(ctx, sys, hp))) return st;      // validates indices and geometry
+    if ((sys->n_fc2 && !fc2_out) || (sys->n_fc3 && !fc3_out)) return fail(ctx, KALD_E_INVALID, "output NULL");
+    const HostSystem &hs = *hp;
+    const int n = hs.n_atoms;
+    // neighbour table: every cell within reach of the cutoff (perpendicular widths)
+    const double (*L)[3] = hs.lattice;
+    auto cross = [](const double *a, const double *b, double *c) {
+        c[0] = a[1] * b[2] - a[2] * b[1]; c[1] = a[2] * b[0] - a[0] * b[2]; c[2] = a[0] * b[1] - a[1] * b[0];
+    };
+    double ext = 0.0;
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b) {
+            double d2 = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                const double d = hs.positions[3 * a + c] - hs.positions[3 * b + c];
+                d2 += d * d;
+            }
+            ext = std::max(ext, std::sqrt(d2));
+        }
+    int reach[3];
+    for (int d = 0; d < 3; ++d) {
+        double cr[3];
+        cross(L[(d + 1) % 3], L[(d + 2) % 3], cr);
+        const double width = hs.volume / std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+        reach[d] = (int)std::ceil((pot->cutoff + ext) / width) + 1;
+    }
+    std::vector<int> start(1, 0), basis;
+    std::vector<int3> cell;
+    std::vector<double3> vec;
+    const double rc2 = pot->cutoff * pot->cutoff;
+    for (int k = 0; k < n; ++k) {
+        for (int n0 = -reach[0]; n0 <= reach[0]; ++n0)
+            for (int n1 = -reach[1]; n1 <= reach[1]; ++n1)
+                for (int n2 = -reach[2]; n2 <= reach[2]; ++n2)
+                    for (int b = 0; b < n; ++b) {
+                        double d[3], d2 = 0.0;
+                        for (int c = 0; c < 3; ++c) {
+                            d[c] = hs.positions[3 * b + c] + n0 * L[0][c] + n1 * L[1][c] + n2 * L[2][c] -
+                                   hs.positions[3 * k + c];
+                            d2 += d[c] * d[c];
+                        }
+                        if (d2 < rc2 && d2 > 1e-16) {
+                            basis.push_back(b);
+                            cell.push_back(make_int3(n0, n1, n2));
+                            vec.push_back(make_double3(d[0], d[1], d[2]));
+                        }
+                    }
+        start.push_back((int)basis.size());
+    }
+    const std::vector<int> i2(sys->fc2_idx, sys->fc2_idx + 5 * (size_t)sys->n_fc2);
+    const std::vector<int> i3(sys->fc3_idx, sys->fc3_idx + 9 * (size_t)sys->n_fc3);
+    const bool d2o = fc2_out && is_device_ptr(fc2_out), d3o = fc3_out && is_device_ptr(fc3_out);
+    size_t need = bytes_of(start) + bytes_of(basis) + bytes_of(cell) + bytes_of(vec) + bytes_of(i2) + bytes_of(i3);
+    if (!d2o) need += ws_round(sizeof(double) * 9 * std::max(1, sys->n_fc2));
+    if (!d3o) need += ws_round(sizeof(double) * 27 * std::max(1, sys->n_fc3));
+    if ((st = ws_reserve(ctx, need))) return st;
+    IfcNeighbours nb;
+    nb.start = upload(ctx, start);
+    nb.basis = upload(ctx, basis);
+    nb.cell = upload(ctx, cell);
+    nb.vec = upload(ctx, vec);
+    const int *i2d = upload(ctx, i2), *i3d = upload(ctx, i3);
+    double *o2 = d2o ? fc2_out : static_cast<double *>(ws_take(ctx, sizeof(double) * 9 * std::max(1, sys->n_fc2)));
+    double *o3 = d3o ? fc3_out : static_cast<double *>(ws_take(ctx, sizeof(double) * 27 * std::max(1, sys->n_fc3)));
+    cudaError_t e = launch_fd_force_constants(sys->n_fc2, i2d, sys->n_fc3, i3d, nb, h, pot->epsilon, pot->sigma, o2,
+                                              o3, ctx->stream);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "kald_fd_force_constants launch");
+    if (!d2o && sys->n_fc2)
+        cudaMemcpyAsync(fc2_out, o2, sizeof(double) * 9 * sys->n_fc2, cudaMemcpyDeviceToHost, ctx->stream);
+    if (!d3o && sys->n_fc3)
+        cudaMemcpyAsync(fc3_out, o3, sizeof(double) * 27 * sys->n_fc3, cudaMemcpyDeviceToHost, ctx->stream);
+    return finish(ctx, "kald_fd_force_constants");
+}
+
 kald_status kald_kappa_rta(kald_ctx *ctx, const kald_system *sys, const int32_t mesh[3],
                            const double *nu_thz, const double *eigvec, const double *gamma,
                            const kald_options *opt, double *kappa) {

@@ -345,6 +345,19 @@ size_t tcx_scratch_bytes(int nb, int nq, int batch);
 cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups &g, void *scratch, int batch,
                              int sms, int *err, cudaStream_t st);
 
+// ifc.cu: finite-difference force constants of a pair potential.  Neighbours
+// of each basis atom k within the cutoff (infinite lattice), CSR over k:
+// basis atom, cell offset n and the vector x_b + n A - x_k.
+struct IfcNeighbours {
+    const int *start;        // [n_atoms + 1]
+    const int *basis;        // [n]
+    const int3 *cell;        // [n]
+    const double3 *vec;      // [n]
+};
+cudaError_t launch_fd_force_constants(int n_fc2, const int *fc2_idx, int n_fc3, const int *fc3_idx,
+                                      const IfcNeighbours &nb, double h, double eps, double sig, double *fc2_out,
+                                      double *fc3_out, cudaStream_t st);
+
 // bte.cu: the full linearised BTE on the assembled operator
 size_t bte_work_bytes(int N);
 cudaError_t bte_combine(size_t NN, double *a, const double *am, const double *b, cudaStream_t st);

@@ -876,3 +876,33 @@ def test_interpolate_gamma_matches_oracle(k, big324, c4w):
     cubic = lambda v: 0.05 + 0.01 * v - 0.002 * v ** 2 + 0.0003 * v ** 3
     xq = np.linspace(0.3, 9.0, 201)
     np.testing.assert_allclose(kk.kald_interpolate_gamma(ctx, x, cubic(x), xq, opt), cubic(xq), rtol=1e-11)
+
+
+# ---------------------------------------------------------------- finite-difference force constants
+def test_fd_force_constants_match_oracle_and_feed_the_path(k):
+    """kald_fd_force_constants (Lennard-Jones, h = 1e-3 A) against the oracle's
+    finite differences, and the linewidths of the finite-difference system
+    against those of the analytic one (O(h^2) apart)."""
+    from oracle import ifc
+    kk, ctx = k
+    w = ki.small_binary(mesh=(3, 3, 3), sigma=0.1)
+    s = w.systems[0]
+    h = 1e-3
+    f2, f3 = kk.kald_fd_force_constants(ctx, s, ki.LJ_EPSILON, ki.LJ_SIGMA, ki.LJ_CUTOFF, h)
+    o2, o3 = ifc.fd_force_constants(s, h=h)
+    e2 = np.abs(f2 - o2).max() / np.abs(o2).max()
+    e3 = np.abs(f3 - o3).max() / np.abs(o3).max()
+    a2 = np.abs(f2 - s.fc2).max() / np.abs(s.fc2).max()
+    a3 = np.abs(f3 - s.fc3).max() / np.abs(s.fc3).max()
+    print(f"FD vs oracle FD: fc2 {e2:.1e}, fc3 {e3:.1e}; FD vs analytic: fc2 {a2:.1e}, fc3 {a3:.1e}")
+    assert e2 < 1e-9 and e3 < 1e-8
+    assert a2 < 1e-5 and a3 < 1e-4
+    fd = ki.System(s.masses.copy(), s.positions.copy(), s.lattice.copy(), s.fc2_idx.copy(), f2,
+                   s.fc3_idx.copy(), f3, name="binary_fd")
+    nu, eig, _ = kk.kald_phonons(ctx, fd, w.mesh)
+    g, _ = kk.kald_linewidths(ctx, fd, w.mesh, nu, eig, _opts(kk, w))
+    nu_a, eig_a, _ = kk.kald_phonons(ctx, s, w.mesh)
+    g_a, _ = kk.kald_linewidths(ctx, s, w.mesh, nu_a, eig_a, _opts(kk, w))
+    err = _rel(np.ravel(g), np.ravel(g_a), 1e-6 * np.max(g_a))
+    print(f"linewidths from FD force constants vs analytic: {err:.1e}")
+    assert err < 1e-3
