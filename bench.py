@@ -213,7 +213,14 @@ def run_reference(args):
 # (dram__bytes_read.sum + dram__bytes_write.sum), scaled to the launch shape
 # the benchmark times; the summaries under profiles/ give the command.  None
 # when the kernel has changed since the counters were taken.
-TRAFFIC_PER_PAIR = {}
+TRAFFIC_PER_PAIR = {
+    # tcx_gemm_kernel on the 32-atom cell, 4x4x4 mesh, 76-pair launches:
+    # GEMM1 562.2 + 490.1 MB, GEMM2 547.6 + 0.2 MB (profiles/tcx_crystal_c2_mesh4_ncu.md)
+    "tcx_gemm1": 1052.27e6 / 76,
+    "tcx_gemm2": 547.72e6 / 76,
+}
+TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of tcx_gemm_kernel on the same cell with a "
+                  "4x4x4 mesh (76-pair launches), per pair, scaled to the pairs of the timed launches")
 
 
 def _gamma_only_band_tiles(om, cut, tile=128, symmetric=True):
@@ -325,10 +332,14 @@ def roofline_of(args, w, nbs, nu_c, opt, prof, steps, allowed, share=1.0):
         exe_per_launch = executed * steps / launches
         out["executed_flops_per_launch"] = exe_per_launch
         out["tensor_pipe_frac"] = exe_per_launch / mean_s / 1e12 / peak
-    if not gamma_only and names[0] in TRAFFIC_PER_PAIR:
-        per_pair, src = TRAFFIC_PER_PAIR[names[0]]
-        out["traffic"] = per_pair * share * nq * nq * steps * len(names) / launches
-        out["traffic_source"] = src
+    if not gamma_only and nb == 96 and all(n in TRAFFIC_PER_PAIR for n in names):
+        # bytes per launch: per-pair DRAM traffic of each kernel x the pairs all its launches covered
+        pairs = share * nq * nq * steps
+        out["traffic"] = sum(TRAFFIC_PER_PAIR[n] * pairs for n in names) / launches
+        out["traffic_source"] = TRAFFIC_SOURCE
+        out["algorithmic_bytes_per_launch"] = None
+        out["traffic_note"] = ("A1 (Y) and T1 (T') as BF16 hi/lo in HBM: 7.1 MB per pair each way; the "
+                               "method's own data (eps, Phi3, gamma) is ~0.1 GB per step")
     other = {n: {"ms": v[0], "launches": v[1]} for n, v in prof.items() if v[1]}
     out["per_kernel_ms"] = other
     return out
