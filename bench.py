@@ -337,7 +337,6 @@ def roofline_of(args, w, nbs, nu_c, opt, prof, steps, allowed, share=1.0):
         pairs = share * nq * nq * steps
         out["traffic"] = sum(TRAFFIC_PER_PAIR[n] * pairs for n in names) / launches
         out["traffic_source"] = TRAFFIC_SOURCE
-        out["algorithmic_bytes_per_launch"] = None
         out["traffic_note"] = ("A1 (Y) and T1 (T') as BF16 hi/lo in HBM: 7.1 MB per pair each way; the "
                                "method's own data (eps, Phi3, gamma) is ~0.1 GB per step")
     other = {n: {"ms": v[0], "launches": v[1]} for n, v in prof.items() if v[1]}
