@@ -736,7 +736,7 @@ size_t tcx_scratch_bytes(int nb, int nq, int batch) {
 }
 
 // Autotuner of the crystal pipeline's schedule.  Candidates: pairs per launch
-// b/2, b and 2b (b = tcx_batch, the hand-set default), row tiles per GEMM
+// b/8, b/4, b/2, b and 2b (b = tcx_batch, the hand-set default), row tiles per GEMM
 // CTA for one and for two waves of CTAs, one or two pairs per gather CTA.  The
 // first call for a (nb, nq, fc3 groups, SM count) times every candidate on the
 // same first pairs of the workload (both lanes, no reduction: the slots these
@@ -772,7 +772,11 @@ TcxSched tcx_schedule(int nb, int nq, int n_groups, int sms, int mt, int batch_m
         if (it != g_tuned.end()) return it->second;
     }
     std::vector<TcxSched> cand;
-    for (int batch : {std::max(1, b0 / 2), b0, std::min(2 * b0, batch_max)})
+    // small batches keep a batch's A1 and T1 (7 MB per pair each) in L2 between
+    // the gather, GEMM1 and GEMM2 at the price of more launches; large ones
+    // amortise the prologues
+    const auto even = [](int b) { return std::max(2, b / 2 * 2); };
+    for (int batch : {even(b0 / 8), even(b0 / 4), std::max(1, b0 / 2), b0, std::min(2 * b0, batch_max)})
         for (int waves : {1, 2})
             for (int gp : {1, 2}) {
                 const TcxSched c{batch, tpc_for(batch, waves), gp};
