@@ -14,6 +14,10 @@
 // CUDA-core) kernels of that pipeline.
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
+#include <vector>
 
 #include "kald_internal.h"
 #include "wdiff.cuh"
@@ -226,7 +230,7 @@ cudaError_t launch_gamma_only(const GammaPlan &gp, const GammaDev &d, const LwPa
         e = cudaMemsetAsync(d.partial_tc, 0, sizeof(double) * std::max<size_t>(nt, 1), st);
         if (e != cudaSuccess) return e;
         e = launch_gamma_only_tc(gp, d, p, d.tc_scratch, gp.tiles, gp.tile_start, d.tiles_dev, gp.symmetric,
-                                 d.partial_tc, d.err, gp.sms, st);
+                                 d.partial_tc, d.err, gp.sms, st, nb);
         if (e != cudaSuccess) return e;
         // tile_start is uploaded right after the tiles (same allocation)
         const int *ts = reinterpret_cast<const int *>(d.tiles_dev + std::max<size_t>(nt, 1));
@@ -244,6 +248,59 @@ cudaError_t launch_gamma_only(const GammaPlan &gp, const GammaDev &d, const LwPa
     g_rank_kernel<<<counted((nb + 127) / 128), 128, 0, st>>>(nb, d.nu, d.order);
     g_degen_kernel<<<counted(1), 32, 0, st>>>(nb, d.nu, d.order, degen_tol_thz, gamma_out);
     return cudaGetLastError();
+}
+
+// Autotuner of the modes per launch: candidates half, once and twice the
+// default (at most 32), timed on the same first modes of the system (about
+// four batches of the largest candidate; the tiles they write are written
+// again by the real run), fastest kept per (nb, SMs) for the process.  The
+// per-mode arithmetic does not depend on the batch.
+static std::mutex g_mb_mu;
+static std::map<std::pair<int, int>, int> g_mb_tuned;
+
+int tune_gamma_batch(const GammaPlan &gp, const GammaDev &d, const LwParams &p, cudaStream_t st) {
+    const int nb = p.nb, sms = gp.sms;
+    const int def = tc_gamma_batch(nb, sms), mbx = tc_gamma_batch_max(nb, sms);
+    const std::pair<int, int> key(nb, sms);
+    {
+        std::lock_guard<std::mutex> lock(g_mb_mu);
+        auto it = g_mb_tuned.find(key);
+        if (it != g_mb_tuned.end()) return it->second;
+    }
+    const int sample = std::min(nb, 4 * mbx);
+    if (sample < 2 * mbx) return def;                // too small to time
+    std::vector<int> cand;
+    for (int c : {std::max(1, def / 2), def, mbx})
+        if (std::find(cand.begin(), cand.end(), c) == cand.end()) cand.push_back(c);
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess) {
+        cudaGetLastError();
+        return def;
+    }
+    int best = def;
+    float best_ms = 1e30f;
+    bool ok = launch_mode_prep(nb, d.nu, p.omega_min_w, p.T, p.classical, d.omega, d.occ, st) == cudaSuccess;
+    for (int c : cand) {
+        if (!ok) break;
+        GammaPlan g2 = gp;
+        g2.mb = c;
+        ok = cudaEventRecord(t0, st) == cudaSuccess &&
+             launch_gamma_only_tc(g2, d, p, d.tc_scratch, g2.tiles, g2.tile_start, d.tiles_dev, g2.symmetric,
+                                  d.partial_tc, d.err, sms, st, sample) == cudaSuccess &&
+             cudaEventRecord(t1, st) == cudaSuccess && cudaEventSynchronize(t1) == cudaSuccess;
+        float ms = 0.0f;
+        if (ok) ok = cudaEventElapsedTime(&ms, t0, t1) == cudaSuccess;
+        if (ok && ms < best_ms) { best_ms = ms; best = c; }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (!ok) {
+        cudaGetLastError();
+        return def;
+    }
+    std::lock_guard<std::mutex> lock(g_mb_mu);
+    g_mb_tuned[key] = best;
+    return best;
 }
 
 }  // namespace kald

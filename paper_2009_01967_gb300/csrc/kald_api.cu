@@ -958,6 +958,34 @@ static kald_status gamma_only_batch(kald_ctx *ctx, int n_sys, const kald_system 
         gd.err = reinterpret_cast<int *>(counters + 32 * t + 16);
         devs[t].g_d = d_g ? gamma + it.off_nb : static_cast<double *>(ws_take(ctx, sizeof(double) * nb));
     }
+    auto params_of = [&](const HostSystem &h) {
+        LwParams p{};
+        p.nb = h.nb; p.nq = 1;
+        p.mesh[0] = p.mesh[1] = p.mesh[2] = 1;
+        p.n_rep = 0; p.n_rounds = 0; p.qp_chunk = 1; p.n_chunks = 1;
+        p.q0 = 0; p.q1 = 1;
+        p.sigma_w = kTwoPi * opt->sigma_thz;
+        p.cut_w = opt->n_sigma * p.sigma_w;
+        p.shape = opt->delta_shape;
+        p.T = opt->temperature_K;
+        p.classical = opt->classical ? 1 : 0;
+        p.omega_min_w = kTwoPi * opt->omega_min_thz;
+        p.wait_limit = ctx->wait_limit;
+        p.prof = nullptr;
+        return p;
+    };
+    if (mode == KALD_BF16_SPLIT) {
+        // modes per launch: the autotuner's choice per distinct nb (timed on the
+        // first system of that size, before the concurrent launches)
+        std::map<int, int> mb_of;
+        for (size_t t = 0; t < items.size(); ++t) {
+            const int nb = items[t].hp->nb;
+            if (!mb_of.count(nb)) mb_of[nb] = tune_gamma_batch(items[t].gp, devs[t].gd, params_of(*items[t].hp),
+                                                               ctx->stream);
+            items[t].gp.mb = mb_of[nb];
+        }
+        cudaMemsetAsync(counters, 0, 32 * items.size(), ctx->stream);   // the timing runs counted too
+    }
     std::vector<cudaStream_t> lanes;
     const int n_lanes = (int)std::min<size_t>(items.size(), 4);
     if ((st = get_lanes(ctx, n_lanes, lanes))) return st;

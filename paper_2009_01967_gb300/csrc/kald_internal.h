@@ -276,6 +276,7 @@ struct GammaPlan {
     std::vector<int> tile_start;     // [nb + 1]
     int symmetric = 0;               // Phi3 symmetric in its last two indices
     int sms = 1;                     // SMs of the device (modes per tensor-core launch)
+    int mb = 0;                      // modes per tensor-core launch (0: tc_gamma_batch; autotuned)
 };
 struct GammaDev {
     const int *group_jk, *group_start, *blk_i;   // (j, k) groups of fc3 blocks
@@ -296,14 +297,19 @@ struct GammaDev {
 // mode: 0 FP64 CUDA cores, 1 FP32 CUDA cores, 2 BF16-split tensor cores
 cudaError_t launch_gamma_only(const GammaPlan &gp, const GammaDev &d, const LwParams &p, int mode,
                               double degen_tol_thz, double *gamma_out, cudaStream_t st);
+// Modes per launch of the Gamma-only tensor-core path for this system (the
+// autotuner's choice for (nb, SMs), timed on first use; tc_gamma_batch
+// before that).  The timing runs use the system's own buffers.
+int tune_gamma_batch(const GammaPlan &gp, const GammaDev &d, const LwParams &p, cudaStream_t st);
 // modes per launch of the tensor-core Gamma-only path and its scratch bytes
 int tc_gamma_batch(int nb, int sms);
+int tc_gamma_batch_max(int nb, int sms);
 size_t tc_gamma_scratch_bytes(int nb, int sms);
 int tc_tile(void);
 cudaError_t launch_gamma_only_tc(const GammaPlan &gp, const GammaDev &d, const LwParams &p, void *scratch,
                                  const std::vector<int2> &tiles, const std::vector<int> &tile_start,
                                  int2 *tiles_dev, int symmetric, double *partial_tc, int *err, int sms,
-                                 cudaStream_t st);
+                                 cudaStream_t st, int mode_limit);
 
 // small_nb.cu: crystal linewidths of one- and two-atom cells (nb = 3 or 6),
 // one thread per (pair, mode), the projection in registers.  The Bloch phase

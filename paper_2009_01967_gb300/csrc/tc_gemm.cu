@@ -368,24 +368,28 @@ int tc_gamma_batch(int nb, int sms) {
     return std::max(1, std::min({want, 32, nb}));
 }
 
+// Largest modes per launch the autotuner may choose (twice the default, at most 32).
+int tc_gamma_batch_max(int nb, int sms) { return std::max(1, std::min({2 * tc_gamma_batch(nb, sms), 32, nb})); }
+
 size_t tc_gamma_scratch_bytes(int nb, int sms) {
     const int ld = (nb + kBN - 1) / kBN * kBN;     // whole 128-column tiles per row
     const int rows = (nb + kBM - 1) / kBM * kBM;
     const size_t plane = ws_round(sizeof(__nv_bfloat16) * (size_t)rows * ld);
-    // E hi/lo, then Y hi, Y lo, T hi, T lo of every mode of a batch
-    return (2 + 4 * (size_t)tc_gamma_batch(nb, sms)) * plane + ws_round(sizeof(int) * 4);
+    // E hi/lo, then Y hi, Y lo, T hi, T lo of every mode of a batch (the largest batch)
+    return (2 + 4 * (size_t)tc_gamma_batch_max(nb, sms)) * plane + ws_round(sizeof(int) * 4);
 }
 
 // The tensor-core pipeline for one Gamma-only system (Y build, T = E Y^T-form,
-// phi tiles of the delta band with the weight epilogue), MB modes per launch.
+// phi tiles of the delta band with the weight epilogue), gp.mb modes per
+// launch (0: tc_gamma_batch), modes below mode_limit only (tuning runs).
 cudaError_t launch_gamma_only_tc(const GammaPlan &gp, const GammaDev &d, const LwParams &p, void *scratch,
                                  const std::vector<int2> &tiles, const std::vector<int> &tile_start,
                                  int2 *tiles_dev, int symmetric, double *partial_tc, int *err, int sms,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, int mode_limit) {
     const int nb = p.nb;
     const int ld = (nb + kBN - 1) / kBN * kBN;     // whole 128-column tiles per row
     const int rows = (nb + kBM - 1) / kBM * kBM;
-    const int mb = tc_gamma_batch(nb, sms);
+    const int mb = (gp.mb > 0) ? std::min(gp.mb, tc_gamma_batch_max(nb, sms)) : tc_gamma_batch(nb, sms);
     const size_t plane = ws_round(sizeof(__nv_bfloat16) * (size_t)rows * ld);
     const size_t stack = (size_t)mb * plane;        // one operand plane for every mode of a batch
     char *b = static_cast<char *>(scratch);
@@ -423,7 +427,8 @@ cudaError_t launch_gamma_only_tc(const GammaPlan &gp, const GammaDev &d, const L
     if (e != cudaSuccess) return e;
     const int nt = rows / kBM;
     const double sig2inv = delta_param(p.shape, p.sigma_w);
-    for (int mu0 = 0; mu0 < nb; mu0 += mb) {
+    const int mu_end = std::min(nb, mode_limit);
+    for (int mu0 = 0; mu0 < mu_end; mu0 += mb) {
         const int nm = std::min(mb, nb - mu0);
         const int t0 = tile_start[mu0], t1 = tile_start[mu0 + nm];
         if (t1 == t0) continue;                     // no delta-band tile (masked modes)
