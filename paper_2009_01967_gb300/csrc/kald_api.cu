@@ -1102,9 +1102,10 @@ static kald_status linewidths_impl(kald_ctx *ctx, int32_t n_sys, const kald_syst
             sn_m0 = std::max(sn_m0, (sn_L - 1) * l1);
         }
         const int small = sn_supported(nb) && sn_m0 < 8192;
-        // BF16 split: the two dense contractions on tensor cores, with the
-        // FP32 tables of the CUDA-core path for the phase sum
-        const int tcx = opt->precision == KALD_BF16_SPLIT && !small;
+        // BF16 split: the three contractions on tensor cores for 65..96
+        // branches; smaller cells (tiles mostly padding) take the FP32
+        // CUDA-core kernel, whose error is below the split's
+        const int tcx = opt->precision == KALD_BF16_SPLIT && !small && tcx_supported(nb);
         const int f32w = opt->precision != KALD_FP64;
         const size_t nn = (size_t)nq * nb * nb;
         LwParams p;
@@ -1166,6 +1167,33 @@ static kald_status linewidths_impl(kald_ctx *ctx, int32_t n_sys, const kald_syst
             plan_tcx_parts(h, tcx_parts(n_groups), tc_part_start, tc_glist);
             if (tc_glist.empty()) tc_glist.push_back(0);
         }
+        // tensor-core phase sum: the blocks of each group ordered by the home atom i
+        std::vector<double> y_blk;
+        std::vector<int> y_atoms, y_gi;
+        std::vector<int2> y_rep;
+        const int y_n_at = nb / 3;
+        if (tcx && nb % 3 == 0) {
+            const int n_groups = (int)h.pair3_j.size();
+            y_blk.resize(27 * std::max<size_t>(n3, 1), 0.0);
+            y_atoms.resize(3 * std::max<size_t>(n3, 1), 0);
+            y_rep.resize(std::max<size_t>(n3, 1), make_int2(0, 0));
+            y_gi.assign((size_t)std::max(1, n_groups) * (y_n_at + 1), 0);
+            for (int g = 0; g < n_groups; ++g) {
+                const int b0 = h.pair3_start[g], b1 = h.pair3_start[g + 1];
+                std::vector<int> ord(b1 - b0);
+                for (int t = b0; t < b1; ++t) ord[t - b0] = t;
+                std::stable_sort(ord.begin(), ord.end(), [&](int u, int v) { return h.fc3_i[u] < h.fc3_i[v]; });
+                int at = 0;
+                for (int x = 0; x < b1 - b0; ++x) {
+                    const int t = ord[x], y = b0 + x;
+                    while (at <= h.fc3_i[t]) y_gi[(size_t)g * (y_n_at + 1) + at++] = y;
+                    for (int v = 0; v < 27; ++v) y_blk[27 * (size_t)y + v] = h.fc3_blk[27 * (size_t)t + v];
+                    for (int v = 0; v < 3; ++v) y_atoms[3 * (size_t)y + v] = h.fc3_atoms[3 * (size_t)t + v];
+                    y_rep[y] = make_int2(h.fc3_rj[t], h.fc3_rk[t]);
+                }
+                while (at <= y_n_at) y_gi[(size_t)g * (y_n_at + 1) + at++] = b1;
+            }
+        }
         YSchedule ys;
         plan_ybuild(h, ys);
         p.n_rounds = ys.n_rounds;
@@ -1185,6 +1213,8 @@ static kald_status linewidths_impl(kald_ctx *ctx, int32_t n_sys, const kald_syst
         if (tcx)
             need += ws_round(tcx_scratch_bytes(nb, nq, tcx_b)) + ws_round(16) + bytes_of(tc_gjk) +
                     bytes_of(tc_part_start) + bytes_of(tc_glist) + bytes_of(h.pair3_start);
+        if (!y_blk.empty())
+            need += scaled_bytes(y_blk, y_atoms, h, 27, 28, 1) + bytes_of(y_gi) + bytes_of(y_rep);
         if (small)
             need += bytes_of(sn_kk) + bytes_of(sn_bj) + bytes_of(sn_bk) + bytes_of(sn_gjk) +
                     bytes_of(h.pair3_start) + ws_round(c2 * (2 * (size_t)sn_m0 + 1));
@@ -1232,6 +1262,14 @@ static kald_status linewidths_impl(kald_ctx *ctx, int32_t n_sys, const kald_syst
             tg.gjk = upload(ctx, tc_gjk);
             tg.blkinfo = d.blkinfo;               // group order (HostSystem order)
             tg.fc3 = static_cast<const float *>(d.fc3);
+            if (!y_blk.empty()) {
+                tg.y.n_at = y_n_at;
+                tg.y.n_groups = tg.n_groups;
+                tg.y.gi_start = upload(ctx, y_gi);
+                tg.y.fc3 = static_cast<const float4 *>(upload_scaled(ctx, y_blk, y_atoms, h, 27, 28, 1));
+                tg.y.rep = upload(ctx, y_rep);
+                tg.y.gjk = tg.gjk;
+            }
         }
         SnTables sn;
         if (small) {
@@ -1249,7 +1287,7 @@ static kald_status linewidths_impl(kald_ctx *ctx, int32_t n_sys, const kald_syst
         if (e == cudaSuccess)
             e = small ? launch_lw_small(p, d, sn, f32w, s)
                 : tcx ? launch_lw_tensor(p, d, tg, tc_scr, tcx_b, ctx->sm_count, tc_err, s)
-                      : launch_lw_main(p, d, fp32, ctx->sm_count, ctx->smem_optin, s);
+                      : launch_lw_main(p, d, f32w, ctx->sm_count, ctx->smem_optin, s);
         if (e == cudaSuccess) e = launch_lw_finish(p, d, opt->degen_tol_thz, g_d, s);
         if (e != cudaSuccess) return cuda_check(ctx, e, "kald_linewidths launch");
         unsigned long long al = 0;

@@ -332,7 +332,18 @@ cudaError_t launch_lw_small(const LwParams &p, const LwDev &d, const SnTables &t
 // tc_crystal.cu: crystal linewidth sums on tensor cores (BF16 split, nb <= 96).
 // The gather runs over the fc3 blocks grouped by (j, k) atom pair (the order
 // of HostSystem), the groups split over CTAs by plan_tcx_parts.
+// Tables of the tensor-core phase sum (tcx_y_kernel): the fc3 blocks of each
+// (j, k) group ordered by the home atom i.
+struct TcxYTables {
+    int n_at = 0;                     // atoms of the cell (nb / 3)
+    int n_groups = 0;                 // (j, k) groups with blocks, HostSystem order
+    const int *gi_start = nullptr;    // [n_groups][n_at + 1] first block of (group, i) in fc3 / rep
+    const float4 *fc3 = nullptr;      // [n_fc3][7] Phi3 / sqrt(mi mj mk), FP32, 27 values + 1 pad
+    const int2 *rep = nullptr;        // [n_fc3] (rep(Rj), rep(Rk))
+    const int2 *gjk = nullptr;        // [n_groups] atoms (j, k)
+};
 struct TcxGroups {
+    TcxYTables y;                     // the same blocks for the tensor-core phase sum
     int n_groups = 0, n_parts = 0;
     int max_part_blocks = 0;          // most fc3 blocks in one part (shared-memory staging)
     const int *part_start = nullptr;  // [n_parts + 1] into glist
@@ -342,6 +353,7 @@ struct TcxGroups {
     const int4 *blkinfo = nullptr;    // [n_fc3] (i, rep(Rj), rep(Rk), 0), group order
     const float *fc3 = nullptr;       // [n_fc3][28] Phi3 / sqrt(mi mj mk), FP32, padded
 };
+bool tcx_supported(int nb);           // 65 <= nb <= 96 (one tile width, N = K = 192)
 int tcx_half(int nb);
 int tcx_batch(int nb, int nq, int sm_count);
 int tcx_batch_max(int nb, int nq, int sm_count);

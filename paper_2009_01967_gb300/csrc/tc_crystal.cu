@@ -29,6 +29,7 @@
 
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <array>
@@ -47,15 +48,19 @@ namespace kald {
 namespace {
 using namespace tc;
 
-constexpr int kBM = 128, kBK = 64, kStages = 2;
+// kBK: K of one resident B block (one 128-byte swizzle row); kAK: K of one
+// streamed A stage.  Four stages of 32 K keep three stages (48 KB) in flight
+// while the MMAs read the fourth, in the shared memory left by the resident B.
+constexpr int kBM = 128, kBK = 64, kAK = 32, kStages = 4;
 enum : int { EPI_T = 0, EPI_PHI = 1 };
 
 // BN = N = K' = 2H (64, 128 or 192; crystals have nb <= 96); PB = BF16
 // pieces of the eigenvector operand B (3 where the resident copy fits in
 // shared memory, else 2).
 template <int BN, int PB> struct Cfg {
-    static constexpr int kNkb = BN / kBK;                  // K blocks
-    static constexpr int kABytes = kBM * kBK * 2;          // one A plane per stage (two 64-row atoms)
+    static constexpr int kNkb = BN / kBK;                  // K blocks of B
+    static constexpr int kNks = BN / kAK;                  // A stages per tile
+    static constexpr int kABytes = kBM * kAK * 2;          // one A plane per stage (two 64-row halves)
     static constexpr int kBBlk = BN * kBK * 2;             // one B plane of one K block
     static constexpr int kBBytes = kNkb * PB * kBBlk;      // resident B, all pieces
     static constexpr int kStageBytes = 2 * kABytes;
@@ -93,16 +98,47 @@ __device__ __forceinline__ void pair_of(const XParams &x, int a, int &q, int &qp
 }
 
 // MN-major operand tile, 128-byte swizzle: atoms of 64 rows (128 B) x 8 K
-// values; LBO = 8 KB between the two 64-row halves of the 128-row tile,
-// SBO = 1 KB between groups of 8 K values.
+// values; LBO = kAK x 128 B between the two 64-row halves of the 128-row
+// stage, SBO = 1 KB between groups of 8 K values.
 __device__ __forceinline__ uint64_t smem_desc_mn(const void *p) {
     const uint64_t a = smem_u32(p);
-    return ((a >> 4) & 0x3FFFull) | ((uint64_t)(8192 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+    return ((a >> 4) & 0x3FFFull) | ((uint64_t)((kAK * 128) >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
            (1ull << 46) | (2ull << 61);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo_half, __nv_bfloat16 hi_half) {
     return (uint32_t)__bfloat16_as_ushort(lo_half) | ((uint32_t)__bfloat16_as_ushort(hi_half) << 16);
+}
+__device__ __forceinline__ uint32_t pack_f16x2(__half lo_half, __half hi_half) {
+    return (uint32_t)__half_as_ushort(lo_half) | ((uint32_t)__half_as_ushort(hi_half) << 16);
+}
+
+__device__ __forceinline__ void st_global_v8(void *p, const uint32_t w[8]) {
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(w[0]), "r"(w[1]),
+                 "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                 : "memory");
+}
+// Row segments of 64 bytes (32 BF16, words w[0..7] the first half, w[8..15]
+// the second) held one per lane, the two lanes of each pair holding
+// consecutive rows (partner row at own -+ rs bytes): one exchange gives each
+// lane its half of both rows, and two 32-byte stores per lane then write two
+// whole segments per lane pair, so a warp store touches 16 segments instead
+// of 32 scattered 16-byte pieces.  All 32 lanes take part; own is 32-byte aligned.
+__device__ __forceinline__ void st_rowpair_v8(char *own, size_t rs, const uint32_t w[16], int qb) {
+    uint32_t mine[8], got[8], a[8], b[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        mine[i] = qb ? w[8 + i] : w[i];
+        got[i] = __shfl_xor_sync(0xffffffffu, qb ? w[i] : w[8 + i], 1);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        a[i] = qb ? got[i] : mine[i];          // first row of the pair, half qb
+        b[i] = qb ? mine[i] : got[i];          // second row, half qb
+    }
+    char *r0 = own - (qb ? rs : 0) + 32 * qb;
+    st_global_v8(r0, a);
+    st_global_v8(r0 + rs, b);
 }
 
 // D[m][n] = sum_k A[pair][k][m] B[z][n][k] over the 128-row tiles
@@ -131,7 +167,10 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
     __shared__ __align__(8) uint64_t bfull, afull[kStages], aempty[kStages], tfull[2], tempty[2], drain;
     __shared__ uint32_t tmem_base_sm;
     __shared__ int fail_sm;
-    __shared__ float w2_sm[128], w2l_sm[128], n2_sm[128], n2l_sm[128], iw2_sm[128];
+    // columns of q'' in pairs (2u, 2u + 1) for the packed FP32x2 epilogue:
+    // (-w hi, -w hi', -w lo, -w lo'), the same for n, and 1 / w
+    __shared__ float4 wpk_sm[64], npk_sm[64];
+    __shared__ float2 iwk_sm[64];
     __shared__ float rowsum[2][2][kBM];          // [tile parity][column half][row]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -140,7 +179,7 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
     const int t0 = blockIdx.x * tpc, t1 = min(mt, t0 + tpc);
     const int n_tiles = max(0, t1 - t0);
     const int nb = x.nb, H = x.H;
-    constexpr int nkb = C::kNkb;
+    constexpr int nkb = C::kNkb, nks = C::kNks;
     constexpr uint32_t idesc = idesc_bf16(BN) | (1u << 15);     // A MN-major
     int q, qp, qpp;
     pair_of(x, a, q, qp, qpp);
@@ -156,14 +195,22 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
     }
     if (EPI == EPI_PHI) {
         // columns of q'': masked modes and padding get a frequency no window reaches
-        for (int t = threadIdx.x; t < 128; t += blockDim.x) {
-            const float4 c = t < nb ? x.wn[(size_t)qpp * nb + t] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const bool v = c.x > 0.0f;
-            w2_sm[t] = v ? c.x : 1e30f;
-            w2l_sm[t] = v ? c.y : 0.0f;
-            n2_sm[t] = v ? c.z : 0.0f;
-            n2l_sm[t] = v ? c.w : 0.0f;
-            iw2_sm[t] = v ? 1.0f / c.x : 0.0f;
+        for (int t = threadIdx.x; t < 64; t += blockDim.x) {
+            float mw[2][2], mn[2][2], iw[2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int col = 2 * t + j;
+                const float4 c = col < nb ? x.wn[(size_t)qpp * nb + col] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const bool v = c.x > 0.0f;
+                mw[0][j] = v ? -c.x : -1e30f;
+                mw[1][j] = v ? -c.y : 0.0f;
+                mn[0][j] = v ? -c.z : 0.0f;
+                mn[1][j] = v ? -c.w : 0.0f;
+                iw[j] = v ? 1.0f / c.x : 0.0f;
+            }
+            wpk_sm[t] = make_float4(mw[0][0], mw[0][1], mw[1][0], mw[1][1]);
+            npk_sm[t] = make_float4(mn[0][0], mn[0][1], mn[1][0], mn[1][1]);
+            iwk_sm[t] = make_float2(iw[0], iw[1]);
         }
     }
     if (warp == 1) {
@@ -187,16 +234,16 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
             }
             int it = 0;
             for (int tile = t0; tile < t1; ++tile) {
-                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                for (int ks = 0; ks < nks; ++ks, ++it) {
                     const int s = it % kStages;
                     if (it >= kStages && !mbar_wait(&aempty[s], ((it / kStages) - 1) & 1, x.wait_limit)) fail_sm = 1;
                     if (*(volatile int *)&fail_sm) break;
                     unsigned char *st = sA + (size_t)s * C::kStageBytes;
                     mbar_expect_tx(&afull[s], C::kStageBytes);
-                    tma_load_3d(st, &mAh, &afull[s], tile * kBM, kb * kBK, a);
-                    tma_load_3d(st + C::kABytes / 2, &mAh, &afull[s], tile * kBM + 64, kb * kBK, a);
-                    tma_load_3d(st + C::kABytes, &mAl, &afull[s], tile * kBM, kb * kBK, a);
-                    tma_load_3d(st + C::kABytes + C::kABytes / 2, &mAl, &afull[s], tile * kBM + 64, kb * kBK, a);
+                    tma_load_3d(st, &mAh, &afull[s], tile * kBM, ks * kAK, a);
+                    tma_load_3d(st + C::kABytes / 2, &mAh, &afull[s], tile * kBM + 64, ks * kAK, a);
+                    tma_load_3d(st + C::kABytes, &mAl, &afull[s], tile * kBM, ks * kAK, a);
+                    tma_load_3d(st + C::kABytes + C::kABytes / 2, &mAl, &afull[s], tile * kBM + 64, ks * kAK, a);
                     ++issued;
                 }
                 if (*(volatile int *)&fail_sm) break;
@@ -212,7 +259,7 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
                 if (i >= 2 && !mbar_wait(&tempty[buf], ((i >> 1) - 1) & 1, x.wait_limit)) { fail_sm = 1; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t d = tmem + (uint32_t)(buf * (C::kTmemCols / 2));
-                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                for (int ks = 0; ks < nks; ++ks, ++it) {
                     const int s = it % kStages;
                     if (!mbar_wait(&afull[s], (it / kStages) & 1, x.wait_limit) || *(volatile int *)&fail_sm) {
                         fail_sm = 1;
@@ -220,15 +267,16 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     unsigned char *st = sA + (size_t)s * C::kStageBytes;
+                    const int kb = ks * kAK / kBK, k0 = (ks * kAK % kBK) / 16;   // B block, K16 step in it
                     const uint64_t ah = smem_desc_mn(st), al = smem_desc_mn(st + C::kABytes);
                     const uint64_t bh = smem_desc(sB + (PB * kb) * C::kBBlk);
                     const uint64_t bm = smem_desc(sB + (PB * kb + 1) * C::kBBlk);
                     const uint64_t bl = smem_desc(sB + (PB * kb + PB - 1) * C::kBBlk);
 #pragma unroll
-                    for (int k = 0; k < kBK / 16; ++k) {
-                        const uint64_t da = (uint64_t)((k * 2048) >> 4), db = (uint64_t)((k * 32) >> 4);
+                    for (int k = 0; k < kAK / 16; ++k) {
+                        const uint64_t da = (uint64_t)((k * 2048) >> 4), db = (uint64_t)(((k0 + k) * 32) >> 4);
                         // a b = (ah + al)(bh [+ bm] + bl) without the smallest terms
-                        mma_bf16(d, ah + da, bh + db, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                        mma_bf16(d, ah + da, bh + db, idesc, (ks > 0 || k > 0) ? 1u : 0u);
                         mma_bf16(d, ah + da, bl + db, idesc, 1u);
                         mma_bf16(d, al + da, bh + db, idesc, 1u);
                         if (PB == 3) {
@@ -247,7 +295,7 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
         const int ew = warp - 4, qd = warp & 3, hf = ew >> 2;
         const int row = qd * 32 + lane;
         float cut = x.cut, s2i = x.sig2inv;
-        unsigned long long cnt = 0;
+        unsigned int cnt = 0;                      // window hits of this thread (at most H / 2 per tile)
         for (int i = 0; i < n_tiles; ++i) {
             const int tile = t0 + i, buf = i & 1;
             bool ok = !*(volatile int *)&fail_sm && mbar_wait(&tfull[buf], (i >> 1) & 1, x.wait_limit);
@@ -261,6 +309,9 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
             if (EPI == EPI_T) {
                 const int c = r_hi, s = r_lo;
                 const bool vec = (nb % 8) == 0;
+                // nb a multiple of 32 (so H = nb and nb^2 = Mp): every warp's 32 rows
+                // are valid and share c, with consecutive s
+                const bool pairs = (nb % 32) == 0 && H == nb && x.Mp == nb * nb;
                 for (int ci = hf; ok && ci < BN / 32; ci += 2) {
                     const int c0 = ci * 32;
                     float v[32];
@@ -270,7 +321,20 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
                     const int sp0 = c0 - part * H;
                     if (sp0 >= nb) continue;
                     const size_t off = ((size_t)a * x.Kp + part * H + c) * x.Mp + (size_t)s * nb + sp0;
-                    if (vec && sp0 + 32 <= nb) {
+                    if (pairs) {
+                        uint32_t hw[16], lw[16];
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            const float f0 = v[2 * e], f1 = v[2 * e + 1];
+                            const __nv_bfloat16 h0 = __float2bfloat16_rn(f0), h1 = __float2bfloat16_rn(f1);
+                            hw[e] = pack_bf16x2(h0, h1);
+                            lw[e] = pack_bf16x2(__float2bfloat16_rn(f0 - __bfloat162float(h0)),
+                                                __float2bfloat16_rn(f1 - __bfloat162float(h1)));
+                        }
+                        const size_t rs = sizeof(__nv_bfloat16) * (size_t)nb;
+                        st_rowpair_v8(reinterpret_cast<char *>(x.t1h + off), rs, hw, lane & 1);
+                        st_rowpair_v8(reinterpret_cast<char *>(x.t1l + off), rs, lw, lane & 1);
+                    } else if (vec && sp0 + 32 <= nb) {
                         uint4 *ph = reinterpret_cast<uint4 *>(x.t1h + off);
                         uint4 *pl = reinterpret_cast<uint4 *>(x.t1l + off);
 #pragma unroll
@@ -306,9 +370,13 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
                 // w + w' and w - w' as FP32 pairs; n' as a pair (wdiff.cuh)
                 const F2 wp = f2_add(F2{a0.x, a0.y}, F2{a1.x, a1.y});
                 const F2 wm = f2_add(F2{a0.x, a0.y}, F2{-a1.x, -a1.y});
-                const F2 n1 = F2{a1.z, a1.w};
                 const float hn1 = 0.5f * (1.0f + a1.z);
-                float acc = 0.0f;
+                // the same differences as f2_diff, two columns per packed FP32x2 operation
+                const float2 WPH = make_float2(wp.h, wp.h), WPL = make_float2(wp.l, wp.l);
+                const float2 WMH = make_float2(wm.h, wm.h), WML = make_float2(wm.l, wm.l);
+                const float2 N1H = make_float2(a1.z, a1.z), N1L = make_float2(a1.w, a1.w);
+                const float2 HN1 = make_float2(hn1, hn1);
+                float2 acc = make_float2(0.0f, 0.0f);
                 for (int ci = hf; ok && ci < H / 16; ci += 2) {
                     const int c0 = ci * 16;
                     float re[16], im[16];
@@ -316,19 +384,30 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
                     tmem_ld16(taddr + H + c0, im);
                     if (!live) continue;
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) {
-                        const F2 w2{w2_sm[c0 + k], w2l_sm[c0 + k]};
-                        const F2 n2{n2_sm[c0 + k], n2l_sm[c0 + k]};
-                        const float dp = f2_diff(wp, w2), dm = f2_diff(wm, w2);
-                        const bool hp = fabsf(dp) < cut, hm = fabsf(dm) < cut;
-                        const float gp = hp ? f2_diff(n1, n2) * delta_shape(dp, x.shape, s2i) : 0.0f;
-                        const float gm = hm ? fmaf(0.5f, n2.h, hn1) * delta_shape(dm, x.shape, s2i) : 0.0f;
-                        const float p2 = fmaf(re[k], re[k], im[k] * im[k]);
-                        acc = fmaf(p2 * (gp + gm), iw2_sm[c0 + k], acc);
-                        cnt += (hp || hm) ? 1ull : 0ull;
+                    for (int k = 0; k < 16; k += 2) {
+                        const int u = (c0 + k) >> 1;
+                        const float4 cw = wpk_sm[u], cn = npk_sm[u];
+                        const float2 mwh = make_float2(cw.x, cw.y), mwl = make_float2(cw.z, cw.w);
+                        const float2 mnh = make_float2(cn.x, cn.y), mnl = make_float2(cn.z, cn.w);
+                        const float2 dp = __fadd2_rn(__fadd2_rn(WPH, mwh), __fadd2_rn(WPL, mwl));
+                        const float2 dm = __fadd2_rn(__fadd2_rn(WMH, mwh), __fadd2_rn(WML, mwl));
+                        const float2 nd = __fadd2_rn(__fadd2_rn(N1H, mnh), __fadd2_rn(N1L, mnl));   // n' - n''
+                        const float2 gc = __ffma2_rn(make_float2(-0.5f, -0.5f), mnh, HN1);          // (1 + n' + n'') / 2
+                        const float2 ep = delta_shape2(dp, x.shape, s2i), em = delta_shape2(dm, x.shape, s2i);
+                        const bool hp0 = fabsf(dp.x) < cut, hp1 = fabsf(dp.y) < cut;
+                        const bool hm0 = fabsf(dm.x) < cut, hm1 = fabsf(dm.y) < cut;
+                        float2 gp = __fmul2_rn(nd, ep), gm = __fmul2_rn(gc, em);
+                        gp.x = hp0 ? gp.x : 0.0f;
+                        gp.y = hp1 ? gp.y : 0.0f;
+                        gm.x = hm0 ? gm.x : 0.0f;
+                        gm.y = hm1 ? gm.y : 0.0f;
+                        const float2 r2 = make_float2(re[k], re[k + 1]), i2 = make_float2(im[k], im[k + 1]);
+                        const float2 p2 = __ffma2_rn(r2, r2, __fmul2_rn(i2, i2));
+                        acc = __ffma2_rn(__fmul2_rn(p2, __fadd2_rn(gp, gm)), iwk_sm[u], acc);
+                        cnt += ((hp0 || hm0) ? 1u : 0u) + ((hp1 || hm1) ? 1u : 0u);
                     }
                 }
-                rowsum[buf][hf][row] = live ? acc / w1 : 0.0f;
+                rowsum[buf][hf][row] = live ? (acc.x + acc.y) / w1 : 0.0f;
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
@@ -361,8 +440,9 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
             }
         }
         if (EPI == EPI_PHI) {
-            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-            if (lane == 0 && cnt) atomicAdd(x.allowed, cnt);
+            unsigned long long c64 = cnt;
+            for (int o = 16; o > 0; o >>= 1) c64 += __shfl_xor_sync(0xffffffffu, c64, o);
+            if (lane == 0 && c64) atomicAdd(x.allowed, c64);
         }
     }
     __syncthreads();
@@ -489,6 +569,297 @@ ycx_gather_kernel(XParams x, TcxGroups g, const float2 *__restrict__ epsT_all,
     }
 }
 
+// Phase sum on tensor cores: per pair, the home-index contraction
+//   Y_s(b, c) = sum_a eps_a(q s) W(a, b, c),
+//   W(3i + alpha, 3j + beta, 3k + gamma) = sum over the blocks (i; j Rj; k Rk)
+//       of Phi3~[alpha beta gamma] chi(q', Rj) conj(chi(q'', Rk)),
+// as a GEMM D0[row][n] = sum_k W[row][k] B0[q][n][k] with rows (group, beta,
+// gamma) -- kYGroups (j, k) groups of 9 rows per 128-row tile -- columns
+// n = (Re | Im, s) as for GEMM1, and K index k = 2a + (0: Re W, 1: Im W).
+// CUDA-core builder warps form W tile by tile in shared memory (FP32 sums
+// over each (group, i)'s blocks, written in the K-major 128-byte-swizzle
+// layout the MMA reads), one 64-wide K block per stage; the eigenvector
+// operand B0 of q stays resident; the epilogue writes Y into A1 (BF16 hi/lo)
+// exactly as the CUDA-core gather does.  Both operands of this contraction
+// are FP16 hi + lo pieces (11-bit significands: a pair carries a value to
+// about 2^-22 of itself, where BF16 pieces carry 2^-18) scaled by powers of
+// two that keep them in FP16 range: B0 = 2^14 eps (|eps| <= 1) and W times
+// wscale[0] = 2^(14 - e), e = exponent of a bound on |W| (max over entries
+// of the sum of |Phi3~| over their blocks, the phases having modulus one);
+// the epilogue multiplies by wscale[1] = 2^-14 / wscale[0] (exact).  Roles: warp 0 loads B0
+// (TMA), warp 1 issues the MMAs, warps 4..11 run the epilogue, warps 2, 3 and
+// 12..15 build.  Every wait is bounded; the builders pass the same named
+// barriers whether or not a wait failed.
+constexpr int kYGroups = 14, kYThreads = 512, kYBuilders = 192, kYStages = 2;
+
+template <int BN, int PB> struct CfgY {
+    static constexpr int kNkb = BN / kBK;                  // K blocks (K = BN = 2H)
+    static constexpr int kAPlane = kBM * kBK * 2;          // one piece of one stage (16 KB)
+    static constexpr int kStageBytes = 2 * kAPlane;        // hi + lo
+    static constexpr int kBBytes = Cfg<BN, PB>::kBBytes;
+    static constexpr int kBBlk = Cfg<BN, PB>::kBBlk;
+    static constexpr int kFixed = kBBytes + kYStages * kStageBytes + 1024;
+    static constexpr int kTmemCols = Cfg<BN, PB>::kTmemCols;
+};
+// dynamic shared memory of tcx_y_kernel: fixed part + chi of q', q'' + the
+// tile's (group, i) block table
+__host__ __device__ inline size_t tcx_y_smem(int fixed, int n_rep, int n_at) {
+    return (size_t)fixed + sizeof(float2) * 2 * (size_t)n_rep + sizeof(int) * (size_t)kYGroups * (n_at + 1);
+}
+
+template <int BN, int PB>
+__global__ void __launch_bounds__(kYThreads, 1)
+tcx_y_kernel(const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBm,
+             const __grid_constant__ CUtensorMap mBl, XParams x, TcxYTables yt, const float2 *__restrict__ chi_all,
+             int n_rep, const float *__restrict__ wscale, __nv_bfloat16 *__restrict__ a1h,
+             __nv_bfloat16 *__restrict__ a1l, int tpc, int *err) {
+    using C = CfgY<BN, PB>;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char *sB = base;                              // [kb][piece][BN rows x 128 B]
+    unsigned char *sA = base + C::kBBytes;                 // [stage][hi, lo][128 rows x 128 B]
+    float2 *chi_sm = reinterpret_cast<float2 *>(sA + kYStages * C::kStageBytes);   // chi(q', .), chi(q'', .)
+    int *gi_sm = reinterpret_cast<int *>(chi_sm + 2 * n_rep);                     // [kYGroups][n_at + 1]
+    __shared__ __align__(8) uint64_t bfull, afull[kYStages], aempty[kYStages], tfull[2], tempty[2], drain;
+    __shared__ uint32_t tmem_base_sm;
+    __shared__ int fail_sm;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int a = blockIdx.y;
+    const int mt = (yt.n_groups + kYGroups - 1) / kYGroups;
+    const int t0 = blockIdx.x * tpc, t1 = min(mt, t0 + tpc);
+    const int n_tiles = max(0, t1 - t0);
+    const int nb = x.nb, H = x.H, n_at = yt.n_at, ld = n_at + 1;
+    constexpr int nkb = C::kNkb;
+    constexpr uint32_t idesc = idesc_f16(BN);              // FP16 operands, both K-major
+    int q, qp, qpp;
+    pair_of(x, a, q, qp, qpp);
+    const bool builder = warp == 2 || warp == 3 || warp >= 12;
+    const int bt = (warp >= 12 ? warp - 10 : warp - 2) * 32 + lane;    // builder thread 0..191
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bfull, 1);
+        for (int s = 0; s < kYStages; ++s) { mbar_init(&afull[s], kYBuilders); mbar_init(&aempty[s], 1); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], kEpiWarps); }
+        mbar_init(&drain, 1);
+        fail_sm = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int t = threadIdx.x; t < n_rep; t += blockDim.x) {
+        chi_sm[t] = chi_all[(size_t)qp * n_rep + t];
+        chi_sm[n_rep + t] = chi_all[(size_t)qpp * n_rep + t];
+    }
+    if (builder) {
+        // stage rows and K columns no group writes (padding) must read as zeros
+        uint4 *z = reinterpret_cast<uint4 *>(sA);
+        for (int t = bt; t < kYStages * C::kStageBytes / 16; t += kYBuilders) z[t] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(&tmem_base_sm)), "r"(C::kTmemCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_sm;
+
+    bool b_issued = false;
+    if (warp == 0) {
+        if (lane == 0 && n_tiles > 0) {
+            mbar_expect_tx(&bfull, C::kBBytes);
+            for (int kb = 0; kb < nkb; ++kb) {
+                tma_load_3d(sB + (PB * kb) * C::kBBlk, &mBh, &bfull, kb * kBK, 0, q);
+                if (PB == 3) tma_load_3d(sB + (PB * kb + 1) * C::kBBlk, &mBm, &bfull, kb * kBK, 0, q);
+                tma_load_3d(sB + (PB * kb + PB - 1) * C::kBBlk, &mBl, &bfull, kb * kBK, 0, q);
+            }
+            b_issued = true;
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            if (n_tiles > 0 && !mbar_wait(&bfull, 0, x.wait_limit)) fail_sm = 1;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            int it = 0;
+            for (int i = 0; i < n_tiles && !*(volatile int *)&fail_sm; ++i) {
+                const int buf = i & 1;
+                if (i >= 2 && !mbar_wait(&tempty[buf], ((i >> 1) - 1) & 1, x.wait_limit)) { fail_sm = 1; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + (uint32_t)(buf * (C::kTmemCols / 2));
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = it % kYStages;
+                    if (!mbar_wait(&afull[s], (it / kYStages) & 1, x.wait_limit) || *(volatile int *)&fail_sm) {
+                        fail_sm = 1;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    unsigned char *st = sA + (size_t)s * C::kStageBytes;
+                    const uint64_t ah = smem_desc(st), al = smem_desc(st + C::kAPlane);
+                    const uint64_t bh = smem_desc(sB + (PB * kb) * C::kBBlk);
+                    const uint64_t bm = smem_desc(sB + (PB * kb + 1) * C::kBBlk);
+                    const uint64_t bl = smem_desc(sB + (PB * kb + PB - 1) * C::kBBlk);
+#pragma unroll
+                    for (int k = 0; k < kBK / 16; ++k) {
+                        const uint64_t dk = (uint64_t)((k * 32) >> 4);
+                        mma_bf16(d, ah + dk, bh + dk, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                        mma_bf16(d, ah + dk, bl + dk, idesc, 1u);
+                        mma_bf16(d, al + dk, bh + dk, idesc, 1u);
+                        if (PB == 3) {
+                            mma_bf16(d, ah + dk, bm + dk, idesc, 1u);
+                            mma_bf16(d, al + dk, bm + dk, idesc, 1u);
+                        }
+                    }
+                    mma_commit(&aempty[s]);
+                }
+                if (*(volatile int *)&fail_sm) break;
+                mma_commit(&tfull[buf]);
+            }
+            mma_commit(&drain);
+        }
+    } else if (builder) {
+        const float sw = __ldg(wscale);
+        int it = 0;
+        for (int i = 0; i < n_tiles; ++i) {
+            const int g0 = (t0 + i) * kYGroups, ng = min(kYGroups, yt.n_groups - g0);
+            named_sync(2, kYBuilders);                     // the previous tile's table is no longer read
+            for (int t = bt; t < ng * ld; t += kYBuilders) gi_sm[t] = yt.gi_start[(size_t)g0 * ld + t];
+            named_sync(2, kYBuilders);
+            for (int kb = 0; kb < nkb; ++kb, ++it) {
+                const int s = it % kYStages;
+                if (*(volatile int *)&fail_sm) continue;
+                if (it >= kYStages && !mbar_wait(&aempty[s], ((it / kYStages) - 1) & 1, x.wait_limit)) {
+                    fail_sm = 1;
+                    continue;
+                }
+                unsigned char *sh = sA + (size_t)s * C::kStageBytes, *sl = sh + C::kAPlane;
+                const int a_lo = kb * (kBK / 2), a_hi = min(nb, a_lo + kBK / 2);   // a of this K block
+                const int i_lo = a_lo / 3, n_i = a_hi > a_lo ? (a_hi - 1) / 3 - i_lo + 1 : 0;
+                for (int item = bt; item < ng * n_i; item += kYBuilders) {
+                    const int g = item / n_i, ia = i_lo + item % n_i;
+                    float2 acc[3][9];
+#pragma unroll
+                    for (int al = 0; al < 3; ++al)
+#pragma unroll
+                        for (int t = 0; t < 9; ++t) acc[al][t] = make_float2(0.f, 0.f);
+                    const int x0 = gi_sm[g * ld + ia], x1 = gi_sm[g * ld + ia + 1];
+                    for (int xb = x0; xb < x1; ++xb) {
+                        const int2 rr = __ldg(yt.rep + xb);
+                        const float4 *f4 = yt.fc3 + 7 * (size_t)xb;
+                        float v[28];
+#pragma unroll
+                        for (int t = 0; t < 7; ++t) {
+                            const float4 u = __ldg(f4 + t);
+                            v[4 * t] = u.x; v[4 * t + 1] = u.y; v[4 * t + 2] = u.z; v[4 * t + 3] = u.w;
+                        }
+                        const float2 c1 = chi_sm[rr.x], c2 = chi_sm[n_rep + rr.y];
+                        const float2 ph = make_float2(c1.x * c2.x + c1.y * c2.y, c1.y * c2.x - c1.x * c2.y);
+#pragma unroll
+                        for (int al = 0; al < 3; ++al)
+#pragma unroll
+                            for (int t = 0; t < 9; ++t)
+                                acc[al][t] = __ffma2_rn(make_float2(v[9 * al + t], v[9 * al + t]), ph, acc[al][t]);
+                    }
+#pragma unroll
+                    for (int al = 0; al < 3; ++al) {
+                        const int aa = 3 * ia + al;
+                        if (aa < a_lo || aa >= a_hi) continue;
+                        const int col = 4 * (aa - a_lo);          // byte of (Re, Im) in the 128-byte row
+#pragma unroll
+                        for (int t = 0; t < 9; ++t) {
+                            const int r = 9 * g + t;
+                            const int off = (r >> 3) * 1024 + (r & 7) * 128 + ((((col >> 4) ^ (r & 7)) << 4) | (col & 15));
+                            const float re = acc[al][t].x * sw, im = acc[al][t].y * sw;
+                            const __half hr = __float2half_rn(re), hi = __float2half_rn(im);
+                            *reinterpret_cast<uint32_t *>(sh + off) = pack_f16x2(hr, hi);
+                            *reinterpret_cast<uint32_t *>(sl + off) =
+                                pack_f16x2(__float2half_rn(re - __half2float(hr)), __float2half_rn(im - __half2float(hi)));
+                        }
+                    }
+                }
+                // the writes above (and the zero fill) become visible to the MMAs
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(&afull[s]);
+            }
+        }
+    } else if (warp >= 4) {
+        const int ew = warp - 4, qd = warp & 3, hf = ew >> 2;
+        const int row = qd * 32 + lane;
+        const bool vec = (nb % 8) == 0;
+        const float unscale = __ldg(wscale + 1);
+        for (int i = 0; i < n_tiles; ++i) {
+            const int buf = i & 1;
+            bool ok = !*(volatile int *)&fail_sm && mbar_wait(&tfull[buf], (i >> 1) & 1, x.wait_limit);
+            ok = __all_sync(0xffffffffu, ok);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (!ok) fail_sm = 1;
+            const uint32_t taddr = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(buf * (C::kTmemCols / 2));
+            const int g0 = (t0 + i) * kYGroups, ng = min(kYGroups, yt.n_groups - g0);
+            const bool rv = row < 9 * ng;
+            int b = 0, c = 0;
+            if (rv) {
+                const int2 jk = __ldg(yt.gjk + g0 + row / 9);
+                const int t = row % 9;
+                b = 3 * jk.x + t / 3;
+                c = 3 * jk.y + t % 3;
+            }
+            for (int ci = hf; ok && ci < BN / 32; ci += 2) {
+                const int c0 = ci * 32;
+                float v[32];
+                tmem_ld32(taddr + c0, v);
+                if (!rv) continue;
+                const int part = c0 >= H ? 1 : 0;
+                const int s0 = c0 - part * H;
+                if (s0 >= nb) continue;
+#pragma unroll
+                for (int e = 0; e < 32; ++e) v[e] *= unscale;
+                const size_t off = ((size_t)a * x.Kp + part * H + b) * x.Mp + (size_t)c * nb + s0;
+                if (vec && s0 + 32 <= nb) {
+                    uint4 *ph = reinterpret_cast<uint4 *>(a1h + off);
+                    uint4 *pl = reinterpret_cast<uint4 *>(a1l + off);
+#pragma unroll
+                    for (int gq = 0; gq < 4; ++gq) {
+                        uint32_t hw[4], lw[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float f0 = v[8 * gq + 2 * e], f1 = v[8 * gq + 2 * e + 1];
+                            const __nv_bfloat16 h0 = __float2bfloat16_rn(f0), h1 = __float2bfloat16_rn(f1);
+                            hw[e] = pack_bf16x2(h0, h1);
+                            lw[e] = pack_bf16x2(__float2bfloat16_rn(f0 - __bfloat162float(h0)),
+                                                __float2bfloat16_rn(f1 - __bfloat162float(h1)));
+                        }
+                        ph[gq] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        pl[gq] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) {
+                        if (s0 + e >= nb) continue;
+                        const __nv_bfloat16 h = __float2bfloat16_rn(v[e]);
+                        a1h[off + e] = h;
+                        a1l[off + e] = __float2bfloat16_rn(v[e] - __bfloat162float(h));
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[buf]);
+        }
+    }
+    __syncthreads();
+    if (*(volatile int *)&fail_sm) {
+        if (threadIdx.x == 0) atomicOr(err, 1);
+        // the resident copy of B0 lands before the CTA exits (bounded)
+        if (b_issued) mbar_wait(&bfull, 0);
+    }
+    if (warp == 1) {
+        if (lane == 0) mbar_wait(&drain, 0);
+        __syncwarp();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::kTmemCols)
+                     : "memory");
+    }
+}
+
 // B1 (which = 0) and B2 (which = 1) of every q, [nq][2H][2H] K-major, as
 // BF16 pieces: hi + lo, or hi + mid + lo when mid is given.
 __global__ void embed_kernel(int nq, int nb, int H, const double2 *__restrict__ eig, int which,
@@ -519,6 +890,62 @@ __global__ void embed_kernel(int nq, int nb, int H, const double2 *__restrict__ 
         } else {
             lo[t] = __float2bfloat16_rn(r);
         }
+    }
+}
+
+// B0 of every q for the tensor-core phase sum, [nq][2H][2H] K-major, FP16 hi
+// and lo of 2^14 eps: row (Re | Im, s), column k = 2a + (0: Re W, 1: Im W).
+__global__ void embed_b0_kernel(int nq, int nb, int H, const double2 *__restrict__ eig, __half *__restrict__ hi,
+                                __half *__restrict__ lo) {
+    const int Kp = 2 * H, BN = 2 * H;
+    const size_t n = (size_t)nq * BN * Kp;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const int q = (int)(t / ((size_t)BN * Kp));
+        const int rem = (int)(t % ((size_t)BN * Kp));
+        const int rw = rem / Kp, k = rem % Kp;
+        const bool im_row = rw >= H;
+        const int sm = rw - (im_row ? H : 0), aa = k >> 1, odd = k & 1;
+        float v = 0.0f;
+        if (sm < nb && aa < nb) {
+            const double2 e = eig[((size_t)q * nb + sm) * nb + aa];      // eps(q)(a, sm)
+            v = 16384.0f * (float)(im_row ? (odd ? e.x : e.y) : (odd ? -e.y : e.x));
+        }
+        const __half h = __float2half_rn(v);
+        hi[t] = h;
+        lo[t] = __float2half_rn(v - __half2float(h));
+    }
+}
+
+// wscale[0] = 2^(14 - e), e the exponent of max over (group, i, alpha beta
+// gamma) of the sum of |Phi3~[alpha beta gamma]| over the blocks of (group,
+// i) (a bound on |W|); wscale[1] = 2^-14 / wscale[0].  One block.
+__global__ void y_scale_kernel(TcxYTables yt, float *__restrict__ wscale) {
+    __shared__ float red[32];
+    const int ld = yt.n_at + 1;
+    float m = 0.0f;
+    for (int item = threadIdx.x; item < yt.n_groups * yt.n_at; item += blockDim.x) {
+        const int g = item / yt.n_at, i = item % yt.n_at;
+        float sum[27];
+#pragma unroll
+        for (int t = 0; t < 27; ++t) sum[t] = 0.0f;
+        for (int xb = yt.gi_start[(size_t)g * ld + i]; xb < yt.gi_start[(size_t)g * ld + i + 1]; ++xb) {
+            const float *v = reinterpret_cast<const float *>(yt.fc3 + 7 * (size_t)xb);
+#pragma unroll
+            for (int t = 0; t < 27; ++t) sum[t] += fabsf(v[t]);
+        }
+#pragma unroll
+        for (int t = 0; t < 27; ++t) m = fmaxf(m, sum[t]);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+        // bound * 1.0001 absorbs the rounding of the FP32 sums
+        const int e = m > 0.0f ? ilogbf(m * 1.0001f) : 0;
+        wscale[0] = ldexpf(1.0f, 14 - e);
+        wscale[1] = ldexpf(1.0f, e - 28);
     }
 }
 
@@ -554,16 +981,17 @@ EncodeTiledFn encode_fn() {
     }
     return fn;
 }
-// 3-D map of BF16 planes [items][rows][inner]: box 64 x box_rows x 1,
+// 3-D map of 16-bit planes [items][rows][inner]: box 64 x box_rows x 1,
 // 128-byte swizzle (64 BF16 = one swizzle row).
-bool make_map3(CUtensorMap *map, const __nv_bfloat16 *ptr, int inner, int rows, int items, int box_rows) {
+bool make_map3(CUtensorMap *map, const void *ptr, int inner, int rows, int items, int box_rows,
+               CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)rows, (cuuint64_t)items};
     const cuuint64_t strides[2] = {(cuuint64_t)inner * 2, (cuuint64_t)inner * 2 * rows};
     const cuuint32_t box[3] = {64u, (cuuint32_t)box_rows, 1u};
     const cuuint32_t estr[3] = {1, 1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(ptr), dims, strides, box,
+    return fn(map, dt, 3, const_cast<void *>(ptr), dims, strides, box,
               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -574,8 +1002,9 @@ struct Lane {
     cudaStream_t st;
     cudaEvent_t done[2];           // after GEMM2 of the lane's batches, alternately
     XParams x;
-    CUtensorMap maps[10];          // A1 hi/lo, B1 h/m/l, T1 hi/lo, B2 h/m/l
+    CUtensorMap maps[13];          // A1 hi/lo, B1 h/m/l, T1 hi/lo, B2 h/m/l, B0 h/l/l (FP16)
     __nv_bfloat16 *a1h, *a1l;
+    const float *wscale;           // scales of the tensor-core phase sum (y_scale_kernel)
 };
 
 // Batches alternate between two lanes, so that one batch's gather (CUDA
@@ -589,7 +1018,17 @@ struct Lane {
 // the time.
 struct TcxSched {
     int batch, tpc, gp;
+    int yk;                        // phase sum: 1 tensor cores (tcx_y_kernel), 0 CUDA cores
+    int tpy;                       // row tiles per tcx_y_kernel CTA
 };
+
+// The tensor-core phase sum fits when its shared memory (resident B0, two
+// stages, the phase tables and one tile's block table) is within the opt-in limit.
+constexpr size_t kSmemOptin = 232448 - 2048;   // less the kernel's static shared memory
+size_t tcx_y_bytes(int nb, int n_rep) {
+    return tcx_y_smem(CfgY<192, 2>::kFixed, std::max(1, n_rep), nb / 3);
+}
+bool tcx_y_fits(int nb, int n_rep) { return nb % 3 == 0 && tcx_y_bytes(nb, n_rep) <= kSmemOptin; }
 
 template <int BN, int PB>
 cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, Lane *lanes, TcxSched sc,
@@ -619,6 +1058,14 @@ cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, L
     // divides nq and the batch (and the first pair is a multiple of nq)
     const int gp = (sc.gp > 1 && p.nq % sc.gp == 0 && batch % sc.gp == 0) ? sc.gp : 1;
     const float2 *ew = static_cast<const float2 *>(d.eps_work), *cw = static_cast<const float2 *>(d.chi);
+    // tensor-core phase sum: row tiles of kYGroups groups, about one wave of CTAs per launch
+    const bool yk = sc.yk && tcx_y_fits(nb, p.n_rep) && g.y.n_groups > 0;
+    const int mty = (g.y.n_groups + kYGroups - 1) / kYGroups;
+    const size_t ysmem = tcx_y_smem(CfgY<BN, PB>::kFixed, std::max(1, p.n_rep), nb / 3);
+    if (yk) {
+        e = cudaFuncSetAttribute(tcx_y_kernel<BN, PB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ysmem);
+        if (e != cudaSuccess) return e;
+    }
     long long i = 0;
     for (long long p0 = pbeg; p0 < pend; p0 += batch, ++i) {
         Lane &L = lanes[i & 1];
@@ -631,7 +1078,11 @@ cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, L
         x.pair0 = p0;
         x.n_pairs = (int)std::min<long long>(batch, pend - p0);
         ProfMark pg(p.prof, KALD_PROF_TCX_GATHER, L.st);
-        if (gp == 4)
+        if (yk) {
+            const int tpy = std::max(1, std::min(sc.tpy, mty));
+            tcx_y_kernel<BN, PB><<<counted(dim3((mty + tpy - 1) / tpy, x.n_pairs)), kYThreads, ysmem, L.st>>>(
+                L.maps[10], L.maps[11], L.maps[12], x, g.y, cw, p.n_rep, L.wscale, L.a1h, L.a1l, tpy, err);
+        } else if (gp == 4)
             ycx_gather_kernel<4><<<counted(dim3(g.n_parts, x.n_pairs / 4)), gthreads, gblk + 4 * gsmem, L.st>>>(
                 x, g, ew, cw, p.n_rep, L.a1h, L.a1l);
         else if (gp == 2)
@@ -668,6 +1119,7 @@ cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, L
 }  // namespace
 
 int tcx_half(int nb) { return (nb + 31) / 32 * 32; }
+bool tcx_supported(int nb) { return nb > 64 && nb <= 96; }
 
 // q-slices of the slot buffer: the batches that may run at once (k+1..k+3
 // while the q completed by batch k waits for its reduction) touch at most
@@ -731,41 +1183,50 @@ size_t tcx_scratch_bytes(int nb, int nq, int batch) {
     const size_t Mp = (size_t)(nb * nb + kBM - 1) / kBM * kBM;
     const size_t eb = ws_round(sizeof(__nv_bfloat16) * (size_t)nq * BN * Kp);
     const size_t ab = ws_round(sizeof(__nv_bfloat16) * (size_t)batch * Kp * Mp);
-    return 6 * eb + 8 * ab + ws_round(sizeof(float) * 2 * (size_t)tcx_slices(nq, batch) * nq * nb) +
+    return 8 * eb + 8 * ab + ws_round(16) + ws_round(sizeof(float) * 2 * (size_t)tcx_slices(nq, batch) * nq * nb) +
            ws_round(sizeof(double) * (size_t)nq * nb);
 }
 
 // Autotuner of the crystal pipeline's schedule.  Candidates: pairs per launch
 // b/8, b/4, b/2, b and 2b (b = tcx_batch, the hand-set default), row tiles per GEMM
-// CTA for one and for two waves of CTAs, one or two pairs per gather CTA.  The
-// first call for a (nb, nq, fc3 groups, SM count) times every candidate on the
-// same first pairs of the workload (both lanes, no reduction: the slots these
-// runs write are written again by the real run, and the counters are reset),
-// keeps the fastest for the rest of the process, and the real run uses it.
-// Any of KALD_TCX_BATCH, KALD_TCX_TPC, KALD_TCX_GP fixes the schedule instead.
+// CTA for one and for two waves of CTAs, the phase sum on tensor cores or on
+// CUDA cores (one, two or four pairs per gather CTA).  The first call for a (nb, nq,
+// fc3 groups, SM count) times every candidate twice on the same first pairs of
+// the workload (both lanes, no reduction: the slots these runs write are
+// written again by the real run, and the counters are reset), keeps the
+// fastest for the rest of the process, and the real run uses it.
+// Any of KALD_TCX_BATCH, KALD_TCX_TPC, KALD_TCX_GP, KALD_TCX_Y (0: CUDA-core phase sum)
+// fixes the schedule instead.
 // Problems too small to time (fewer than two samples of pairs) take the default.
 static std::mutex g_tune_mu;
-static std::map<std::array<int, 4>, TcxSched> g_tuned;
+static std::map<std::array<int, 5>, TcxSched> g_tuned;
 
 template <typename Run>
-TcxSched tcx_schedule(int nb, int nq, int n_groups, int sms, int mt, int batch_max, long long pbeg, long long pend,
+TcxSched tcx_schedule(int nb, int nq, int n_groups, bool y_ok, int sms, int mt, int batch_max, long long pbeg,
+                      long long pend,
                       Run &run, cudaStream_t st, cudaStream_t aux, cudaEvent_t fork_ev, unsigned long long *allowed,
                       int *err, cudaError_t &e) {
     const int b0 = std::max(1, std::min(tcx_batch(nb, nq, sms), batch_max));
-    auto tpc_for = [&](int batch, int waves) {
-        const long long t = ((long long)mt * batch + (long long)sms * waves - 1) / ((long long)sms * waves);
-        return (int)std::max<long long>(1, std::min<long long>(t, mt));
+    auto tiles_for = [&](int m, int batch, int waves) {
+        const long long t = ((long long)m * batch + (long long)sms * waves - 1) / ((long long)sms * waves);
+        return (int)std::max<long long>(1, std::min<long long>(t, m));
     };
-    TcxSched def{b0, tpc_for(b0, 1), 2};
+    auto tpc_for = [&](int batch, int waves) { return tiles_for(mt, batch, waves); };
+    const int mty = std::max(1, (n_groups + kYGroups - 1) / kYGroups);
+    const int yk0 = y_ok ? 1 : 0;
+    TcxSched def{b0, tpc_for(b0, 1), 2, yk0, tiles_for(mty, b0, 1)};
     const char *eb = std::getenv("KALD_TCX_BATCH"), *et = std::getenv("KALD_TCX_TPC"), *eg = std::getenv("KALD_TCX_GP");
-    if (eb || et || eg) {
+    const char *ey = std::getenv("KALD_TCX_Y");
+    if (eb || et || eg || ey) {
         if (eb && std::atoi(eb) > 0) def.batch = std::min(std::atoi(eb), batch_max);
         def.tpc = tpc_for(def.batch, 1);
+        def.tpy = tiles_for(mty, def.batch, 1);
         if (et && std::atoi(et) > 0) def.tpc = std::min(std::atoi(et), mt);
         if (eg) def.gp = std::atoi(eg);
+        if (ey) def.yk = std::atoi(ey) != 0 ? yk0 : 0;
         return def;
     }
-    const std::array<int, 4> key{nb, nq, n_groups, sms};
+    const std::array<int, 5> key{nb, nq, n_groups, sms, yk0};
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tuned.find(key);
@@ -778,30 +1239,42 @@ TcxSched tcx_schedule(int nb, int nq, int n_groups, int sms, int mt, int batch_m
     const auto even = [](int b) { return std::max(2, b / 2 * 2); };
     for (int batch : {even(b0 / 8), even(b0 / 4), std::max(1, b0 / 2), b0, std::min(2 * b0, batch_max)})
         for (int waves : {1, 2})
-            for (int gp : {1, 2}) {
-                const TcxSched c{batch, tpc_for(batch, waves), gp};
-                bool dup = false;
-                for (const TcxSched &x : cand) dup |= x.batch == c.batch && x.tpc == c.tpc && x.gp == c.gp;
-                if (!dup) cand.push_back(c);
-            }
+            for (int yk = yk0; yk >= 0; --yk)
+                for (int gp : {1, 2, 4}) {
+                    // (pairs per gather CTA only matters for the CUDA-core phase sum)
+                    const TcxSched c{batch, tpc_for(batch, waves), yk ? 1 : gp, yk, tiles_for(mty, batch, waves)};
+                    bool dup = false;
+                    for (const TcxSched &x : cand)
+                        dup |= x.batch == c.batch && x.tpc == c.tpc && x.gp == c.gp && x.yk == c.yk && x.tpy == c.tpy;
+                    if (!dup) cand.push_back(c);
+                }
     const long long sample = 4LL * std::min(2 * b0, batch_max);
     if (pend - pbeg < 2 * sample) return def;
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     if ((e = cudaEventCreate(&t0)) != cudaSuccess || (e = cudaEventCreate(&t1)) != cudaSuccess) return def;
+    auto time_one = [&](const TcxSched &c, float &ms) -> cudaError_t {
+        cudaError_t r;
+        if ((r = cudaEventRecord(t0, st)) != cudaSuccess) return r;
+        if ((r = cudaEventRecord(fork_ev, st)) != cudaSuccess || (r = cudaStreamWaitEvent(aux, fork_ev, 0)) != cudaSuccess)
+            return r;
+        if ((r = run(c, pbeg, pbeg + sample, false)) != cudaSuccess) return r;
+        if ((r = cudaEventRecord(fork_ev, aux)) != cudaSuccess || (r = cudaStreamWaitEvent(st, fork_ev, 0)) != cudaSuccess)
+            return r;
+        if ((r = cudaEventRecord(t1, st)) != cudaSuccess || (r = cudaEventSynchronize(t1)) != cudaSuccess) return r;
+        return cudaEventElapsedTime(&ms, t0, t1);
+    };
+    // one untimed run of the default first (module loading, clocks), then two
+    // rounds over all candidates; each keeps its faster time
+    std::vector<float> best_of(cand.size(), 1e30f);
+    float ms = 0.0f;
+    e = time_one(def, ms);
+    for (int round = 0; round < 2 && e == cudaSuccess; ++round)
+        for (size_t c = 0; c < cand.size() && e == cudaSuccess; ++c)
+            if ((e = time_one(cand[c], ms)) == cudaSuccess) best_of[c] = std::min(best_of[c], ms);
     TcxSched best = def;
     float best_ms = 1e30f;
-    for (const TcxSched &c : cand) {
-        if ((e = cudaEventRecord(t0, st)) != cudaSuccess) break;
-        if ((e = cudaEventRecord(fork_ev, st)) != cudaSuccess || (e = cudaStreamWaitEvent(aux, fork_ev, 0)) != cudaSuccess)
-            break;
-        if ((e = run(c, pbeg, pbeg + sample, false)) != cudaSuccess) break;
-        if ((e = cudaEventRecord(fork_ev, aux)) != cudaSuccess || (e = cudaStreamWaitEvent(st, fork_ev, 0)) != cudaSuccess)
-            break;
-        if ((e = cudaEventRecord(t1, st)) != cudaSuccess || (e = cudaEventSynchronize(t1)) != cudaSuccess) break;
-        float ms = 0.0f;
-        if ((e = cudaEventElapsedTime(&ms, t0, t1)) != cudaSuccess) break;
-        if (ms < best_ms) { best_ms = ms; best = c; }
-    }
+    for (size_t c = 0; c < cand.size(); ++c)
+        if (best_of[c] < best_ms) { best_ms = best_of[c]; best = cand[c]; }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     if (e != cudaSuccess) return def;
@@ -824,7 +1297,7 @@ TcxSched tcx_schedule(int nb, int nq, int n_groups, int sms, int mt, int batch_m
 cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups &g, void *scratch, int batch,
                              int sms, int *err, cudaStream_t st) {
     const int nb = p.nb, nq = p.nq;
-    if (nb < 1 || nb > 96 || batch < 1 || g.n_parts < 1 || sms < 1) return cudaErrorInvalidValue;
+    if (!tcx_supported(nb) || batch < 1 || g.n_parts < 1 || sms < 1) return cudaErrorInvalidValue;
     const int H = tcx_half(nb), Kp = 2 * H, BN = 2 * H;
     const int Mp = (nb * nb + kBM - 1) / kBM * kBM;
     char *b = static_cast<char *>(scratch);
@@ -837,6 +1310,9 @@ cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups 
     auto *b2h = reinterpret_cast<__nv_bfloat16 *>(take(eb));
     auto *b2m = reinterpret_cast<__nv_bfloat16 *>(take(eb));
     auto *b2l = reinterpret_cast<__nv_bfloat16 *>(take(eb));
+    auto *b0h = reinterpret_cast<__half *>(take(eb));
+    auto *b0l = reinterpret_cast<__half *>(take(eb));
+    auto *wscale = reinterpret_cast<float *>(take(16));
     const bool three = BN <= 128;          // three pieces of B fit in shared memory
     const size_t ab = sizeof(__nv_bfloat16) * (size_t)batch * Kp * Mp;
     __nv_bfloat16 *pl[2][4];                       // per lane: A1 hi, A1 lo, T1 hi, T1 lo
@@ -855,6 +1331,10 @@ cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups 
     const int eg = (int)std::min<size_t>(((size_t)nq * BN * Kp + 255) / 256, 4096);
     embed_kernel<<<counted(eg), 256, 0, st>>>(nq, nb, H, d.eig, 0, b1h, three ? b1m : nullptr, b1l);
     embed_kernel<<<counted(eg), 256, 0, st>>>(nq, nb, H, d.eig, 1, b2h, three ? b2m : nullptr, b2l);
+    if (g.y.fc3) {
+        embed_b0_kernel<<<counted(eg), 256, 0, st>>>(nq, nb, H, d.eig, b0h, b0l);
+        y_scale_kernel<<<counted(1), 1024, 0, st>>>(g.y, wscale);
+    }
 
     XParams x;
     x.nb = nb; x.H = H; x.Kp = Kp; x.Mp = Mp;
@@ -875,13 +1355,17 @@ cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups 
         Lane &L = lanes[l];
         L.x = x;
         L.a1h = pl[l][0]; L.a1l = pl[l][1];
+        L.wscale = wscale;
         L.x.t1h = pl[l][2]; L.x.t1l = pl[l][3];
-        if (!make_map3(&L.maps[0], pl[l][0], Mp, Kp, batch, kBK) ||
-            !make_map3(&L.maps[1], pl[l][1], Mp, Kp, batch, kBK) || !make_map3(&L.maps[2], b1h, Kp, BN, nq, BN) ||
+        if (!make_map3(&L.maps[0], pl[l][0], Mp, Kp, batch, kAK) ||
+            !make_map3(&L.maps[1], pl[l][1], Mp, Kp, batch, kAK) || !make_map3(&L.maps[2], b1h, Kp, BN, nq, BN) ||
             !make_map3(&L.maps[3], b1m, Kp, BN, nq, BN) || !make_map3(&L.maps[4], b1l, Kp, BN, nq, BN) ||
-            !make_map3(&L.maps[5], pl[l][2], Mp, Kp, batch, kBK) ||
-            !make_map3(&L.maps[6], pl[l][3], Mp, Kp, batch, kBK) || !make_map3(&L.maps[7], b2h, Kp, BN, nq, BN) ||
-            !make_map3(&L.maps[8], b2m, Kp, BN, nq, BN) || !make_map3(&L.maps[9], b2l, Kp, BN, nq, BN))
+            !make_map3(&L.maps[5], pl[l][2], Mp, Kp, batch, kAK) ||
+            !make_map3(&L.maps[6], pl[l][3], Mp, Kp, batch, kAK) || !make_map3(&L.maps[7], b2h, Kp, BN, nq, BN) ||
+            !make_map3(&L.maps[8], b2m, Kp, BN, nq, BN) || !make_map3(&L.maps[9], b2l, Kp, BN, nq, BN) ||
+            !make_map3(&L.maps[10], b0h, Kp, BN, nq, BN, CU_TENSOR_MAP_DATA_TYPE_FLOAT16) ||
+            !make_map3(&L.maps[11], b0l, Kp, BN, nq, BN, CU_TENSOR_MAP_DATA_TYPE_FLOAT16) ||
+            !make_map3(&L.maps[12], b0l, Kp, BN, nq, BN, CU_TENSOR_MAP_DATA_TYPE_FLOAT16))
             return cudaErrorInvalidValue;
     }
     // second lane: its own stream, forked from and joined back into st
@@ -895,15 +1379,12 @@ cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups 
         lanes[0].st = st; lanes[0].done[0] = ev[0]; lanes[0].done[1] = ev[1];
         lanes[1].st = aux; lanes[1].done[0] = ev[2]; lanes[1].done[1] = ev[3];
         auto run = [&](TcxSched sc, long long b0, long long b1, bool reduce) -> cudaError_t {
-            switch (BN) {
-                case 64: return run_batches<64, 3>(p, d, g, lanes, sc, b0, b1, reduce, gacc, err);
-                case 128: return run_batches<128, 3>(p, d, g, lanes, sc, b0, b1, reduce, gacc, err);
-                default: return run_batches<192, 2>(p, d, g, lanes, sc, b0, b1, reduce, gacc, err);
-            }
+            return run_batches<192, 2>(p, d, g, lanes, sc, b0, b1, reduce, gacc, err);
         };
         const long long pbeg = (long long)p.q0 * nq, pend = (long long)p.q1 * nq;   // pairs of q in [q0, q1)
-        const TcxSched sc = tcx_schedule(nb, nq, g.n_groups, sms, Mp / kBM, batch, pbeg, pend, run, st, aux, ev[4],
-                                         d.allowed, err, e);
+        const bool y_ok = tcx_y_fits(nb, p.n_rep) && g.y.n_groups > 0 && g.y.fc3 != nullptr;
+        const TcxSched sc = tcx_schedule(nb, nq, g.n_groups, y_ok, sms, Mp / kBM, batch, pbeg, pend, run, st, aux,
+                                         ev[4], d.allowed, err, e);
         if (e == cudaSuccess) e = run(sc, pbeg, pend, true);
     }
     // join (also after an error, so that nothing is left running on aux)

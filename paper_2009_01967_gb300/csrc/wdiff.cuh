@@ -61,6 +61,20 @@ __device__ __forceinline__ float delta_shape(float d, int shape, float a) {
     if (shape == kDeltaLorentz) return 1.0f / fmaf(d * d, a, 1.0f);
     return fmaxf(0.0f, 1.0f - fabsf(d) * a);
 }
+// The same on a pair of values (packed FP32x2 arithmetic; per component the
+// operations and their rounding are those of delta_shape).
+__device__ __forceinline__ float2 delta_shape2(float2 d, int shape, float a) {
+    const float2 d2 = __fmul2_rn(d, d);
+    if (shape == kDeltaGauss) {
+        const float2 x = __fmul2_rn(d2, make_float2(-a, -a));
+        return make_float2(__expf(x.x), __expf(x.y));
+    }
+    if (shape == kDeltaLorentz) {
+        const float2 x = __ffma2_rn(d2, make_float2(a, a), make_float2(1.0f, 1.0f));
+        return make_float2(1.0f / x.x, 1.0f / x.y);
+    }
+    return make_float2(fmaxf(0.0f, 1.0f - fabsf(d.x) * a), fmaxf(0.0f, 1.0f - fabsf(d.y) * a));
+}
 __device__ __forceinline__ double delta_shape(double d, int shape, double a) {
     if (shape == kDeltaGauss) return exp(-d * d * a);
     if (shape == kDeltaLorentz) return 1.0 / fma(d * d, a, 1.0);

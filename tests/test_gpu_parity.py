@@ -96,6 +96,26 @@ def _lw_case(case):
     raise KeyError(case)
 
 
+def _cell_case(case):
+    """Crystal cells of 4 and 32 atoms: fcc4_mesh3 (12 branches, the FP32
+    CUDA-core kernel in the split mode), fcc32_mesh2 / fcc32_mesh211 (96
+    branches, the tensor-core path), fcc32_random (96 branches with random
+    third-order blocks whose two lattice vectors are both non-zero)."""
+    if case == "fcc4_mesh3":
+        return ki.Workload("fcc4", [ki.fcc_supercell_system(1, seed=7)], (3, 3, 3), 300.0, 0.1, 3.0)
+    if case == "fcc32_mesh2":
+        return ki.Workload("fcc32", [ki.fcc_supercell_system(2, seed=2)], (2, 2, 2), 300.0, 0.1, 3.0)
+    if case == "fcc32_mesh211":
+        return ki.Workload("fcc32", [ki.fcc_supercell_system(2, seed=2)], (2, 1, 1), 300.0, 0.1, 3.0)
+    if case == "fcc32_mesh311":
+        # (1/3, 0, 0) carries group velocities (on a 2 x 1 x 1 mesh they vanish by symmetry)
+        return ki.Workload("fcc32", [ki.fcc_supercell_system(2, seed=2)], (3, 1, 1), 300.0, 0.1, 3.0)
+    if case == "fcc32_random":
+        base = ki.fcc_supercell_system(2, seed=2)
+        return ki.Workload("fcc32r", [ki.random_fc3_system(base, 400, seed=13)], (2, 1, 1), 300.0, 0.1, 3.0)
+    raise KeyError(case)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("case", ["C1", "binary3", "binary_random", "gamma_only_32", "C5_mesh6",
                                   "binary_mesh234"])
@@ -148,20 +168,18 @@ def test_linewidths_c2_sampled_q(k):
     assert tot == 512 ** 2 * 96 ** 3 and 0 < allowed < tot
 
 
-@pytest.mark.parametrize("case", ["binary3", "binary_random", "C5_mesh6", "fcc4_mesh3", "fcc32_mesh2"])
+@pytest.mark.parametrize("case", ["binary3", "binary_random", "C5_mesh6", "fcc4_mesh3", "fcc32_mesh2",
+                                  "fcc32_random"])
 def test_crystal_bf16split_tensor_cores(k, case):
-    """Crystal linewidths in the BF16-split mode: the two dense contractions on
-    tcgen05 (BF16 pieces, FP32 accumulation) for cells of three or more atoms,
-    the FP32 register kernel for one- and two-atom cells.  The delta windows
-    are decided in FP32 as in the FP32 CUDA-core path, so the allowed counts
-    agree exactly; gamma within 1e-5 of the FP64 oracle."""
+    """Crystal linewidths in the BF16-split mode: the contractions on tcgen05
+    (BF16 pieces, FP32 accumulation) for cells of 65 to 96 branches, the FP32
+    CUDA-core kernel for 3 to 64 branches, the FP32 register kernel for one-
+    and two-atom cells.  The delta windows are decided in FP32 as in the FP32
+    CUDA-core path, so the allowed counts agree exactly; gamma within 1e-5 of
+    the FP64 oracle."""
     kk, ctx = k
-    if case == "fcc32_mesh2":
-        w = ki.Workload("fcc32", [ki.fcc_supercell_system(2, seed=2)], (2, 2, 2), 300.0, 0.1, 3.0)
-    elif case == "fcc4_mesh3":
-        # 4-atom cell (12 branches): tensor tiles with N = K = 64 and the
-        # three-piece eigenvector operand
-        w = ki.Workload("fcc4", [ki.fcc_supercell_system(1, seed=7)], (3, 3, 3), 300.0, 0.1, 3.0)
+    if case.startswith("fcc"):
+        w = _cell_case(case)
     else:
         w = _lw_case(case)
     s = w.systems[0]
@@ -176,6 +194,30 @@ def test_crystal_bf16split_tensor_cores(k, case):
     err = _rel(g, g_o, 1e-6 * g_o.max())
     print(f"{case}: bf16 split gamma max rel err {err:.3e}")
     assert err < 1e-5
+
+
+@pytest.mark.parametrize("case", ["fcc32_random", "fcc32_mesh2"])
+def test_crystal_bf16split_phase_sum_kernels(k, case, monkeypatch):
+    """The phase sum Y_s(b, c) of the tensor-core crystal path computed either
+    way -- as a tcgen05 GEMM over the phase-folded fc3 blocks (the default)
+    or on CUDA cores (KALD_TCX_Y=0) -- gives gamma within 1e-5 of the FP64
+    oracle and the same delta-allowed count."""
+    kk, ctx = k
+    w = _cell_case(case)
+    s = w.systems[0]
+    nu_o, eig_o = ph.phonons(s, w.mesh)
+    g_o = an.linewidths(s, w.mesh, nu_o, eig_o, w.T, w.sigma_thz, w.n_sigma)
+    out = {}
+    for yk in ("1", "0"):
+        monkeypatch.setenv("KALD_TCX_Y", yk)
+        g, (tot, allowed) = kk.kald_linewidths(ctx, s, w.mesh, nu_o, eig_o, _opts(kk, w, "bf16split"))
+        out[yk] = (g.reshape(g_o.shape), allowed)
+    monkeypatch.delenv("KALD_TCX_Y")
+    assert out["1"][1] == out["0"][1]
+    for yk, (g, _) in out.items():
+        err = _rel(g, g_o, 1e-6 * g_o.max())
+        print(f"{case} phase sum on {'tensor' if yk == '1' else 'CUDA'} cores: gamma max rel err {err:.3e}")
+        assert err < 1e-5
 
 
 def test_crystal_bf16split_c2_sampled_q(k):
@@ -502,20 +544,21 @@ def test_c5_full_mesh_sampled_q(k):
     assert tot == 13824 ** 2 * 6 ** 3 and 0 < allowed < tot
 
 
-@pytest.mark.parametrize("cell", ["binary", "fcc4"])
+@pytest.mark.parametrize("cell", ["binary", "fcc4", "fcc32"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16split"])
 def test_no_third_order_blocks_gives_zero_gamma(k, cell, precision):
     """Degenerate input: without Phi3 blocks every projection vanishes, so
     gamma is exactly zero in every path (register kernel for the 2-atom cell,
-    tensor cores or CUDA cores for the 4-atom cell), while the delta-allowed
-    count, which depends on the frequencies only, is unchanged."""
+    CUDA cores for the 4-atom cell, tensor cores or CUDA cores for the 32-atom
+    cell), while the delta-allowed count, which depends on the frequencies
+    only, is unchanged."""
     kk, ctx = k
     if cell == "binary":
         w = ki.small_binary(mesh=(3, 3, 3), sigma=0.1)
         base = w.systems[0]
     else:
-        base = ki.fcc_supercell_system(1, seed=7)
-        w = ki.Workload("fcc4", [base], (3, 3, 3), 300.0, 0.1, 3.0)
+        w = _cell_case("fcc4_mesh3" if cell == "fcc4" else "fcc32_mesh211")
+        base = w.systems[0]
     empty = ki.System(base.masses.copy(), base.positions.copy(), base.lattice.copy(),
                       base.fc2_idx.copy(), base.fc2.copy(), np.zeros((0, 9), dtype=np.int32),
                       np.zeros((0, 3, 3, 3)), name=base.name + "_no_fc3")
@@ -555,16 +598,13 @@ def test_kappa_split_path_against_fp64_gpu_path(k, case):
 
 # ---------------------------------------------------------------- classical statistics
 @pytest.mark.parametrize("case,precision", [("binary3", "fp64"), ("fcc4_mesh3", "bf16split"),
-                                            ("gamma_only_32", "fp64")])
+                                            ("fcc32_mesh311", "bf16split"), ("gamma_only_32", "fp64")])
 def test_classical_statistics_match_oracle(k, case, precision):
     """classical = 1 (Eq. classic_n: n = kB T / hbar omega, c = kB) through the
     linewidths and kappa_RTA / kappa_QHGK, against the oracle run with the same
     statistics."""
     kk, ctx = k
-    if case == "fcc4_mesh3":
-        w = ki.Workload("fcc4", [ki.fcc_supercell_system(1, seed=7)], (3, 3, 3), 300.0, 0.1, 3.0)
-    else:
-        w = _lw_case(case)
+    w = _cell_case(case) if case.startswith("fcc") else _lw_case(case)
     s = w.systems[0]
     nu_o, eig_o = ph.phonons(s, w.mesh)
     opt = _opts(kk, w, precision, classical=True)
@@ -772,14 +812,15 @@ def test_batched_mixed_sizes_match_single_calls(k, c4w, precision):
 # ---------------------------------------------------------------- delta shapes
 @pytest.mark.parametrize("shape", ["lorentzian", "triangular"])
 @pytest.mark.parametrize("case,precision", [("binary3", "fp64"), ("binary3", "fp32"), ("fcc4_mesh3", "fp64"),
-                                            ("fcc4_mesh3", "bf16split"), ("g144", "fp64"), ("g144", "bf16split")])
+                                            ("fcc4_mesh3", "bf16split"), ("fcc32_mesh211", "bf16split"),
+                                            ("g144", "fp64"), ("g144", "bf16split")])
 def test_delta_shapes_match_oracle(k, case, precision, shape):
     """The Lorentzian and triangular energy deltas (delta_shape option) in
     every epilogue -- register, CUDA-core, crystal and Gamma-only tensor-core
     -- against the oracle with the same shape."""
     kk, ctx = k
-    if case == "fcc4_mesh3":
-        w = ki.Workload("fcc4", [ki.fcc_supercell_system(1, seed=7)], (3, 3, 3), 300.0, 0.1, 3.0)
+    if case.startswith("fcc"):
+        w = _cell_case(case)
     elif case == "g144":
         s = ki.fcc_supercell_system((2, 2, 3), seed=17, heavy_fraction=0.3)
         w = ki.Workload("g144", [s], (1, 1, 1), 300.0, 0.05, 3.0)
