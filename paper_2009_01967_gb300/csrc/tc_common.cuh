@@ -109,6 +109,54 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
 #pragma unroll
     for (int x = 0; x < 16; ++x) v[x] = __uint_as_float(r[x]);
 }
+__device__ __forceinline__ void st_global_v8(void *p, const uint32_t w[8]) {
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(w[0]), "r"(w[1]),
+                 "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                 : "memory");
+}
+// Row segments of 64 bytes (32 BF16, words w[0..7] the first half, w[8..15]
+// the second) held one per lane, the two lanes of each pair holding
+// consecutive rows (partner row at own -+ rs bytes): one exchange gives each
+// lane its half of both rows, and two 32-byte stores per lane then write two
+// whole segments per lane pair, so a warp store touches 16 segments instead
+// of 32 scattered 16-byte pieces.  All 32 lanes take part; own is 32-byte aligned.
+__device__ __forceinline__ void st_rowpair_v8(char *own, size_t rs, const uint32_t w[16], int qb) {
+    uint32_t mine[8], got[8], a[8], b[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        mine[i] = qb ? w[8 + i] : w[i];
+        got[i] = __shfl_xor_sync(0xffffffffu, qb ? w[i] : w[8 + i], 1);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        a[i] = qb ? got[i] : mine[i];          // first row of the pair, half qb
+        b[i] = qb ? mine[i] : got[i];          // second row, half qb
+    }
+    char *r0 = own - (qb ? rs : 0) + 32 * qb;
+    st_global_v8(r0, a);
+    st_global_v8(r0 + rs, b);
+}
+
+// Two 16-column loads (e.g. the Re and Im halves of a tile row) and one wait.
+__device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float va[16], float vb[16]) {
+    uint32_t r[16], u[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(ta));
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+          "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+        : "r"(tb));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int x = 0; x < 16; ++x) {
+        va[x] = __uint_as_float(r[x]);
+        vb[x] = __uint_as_float(u[x]);
+    }
+}
 // Arrive (count 1) on an mbarrier from one thread.
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");

@@ -113,48 +113,28 @@ __device__ __forceinline__ uint32_t pack_f16x2(__half lo_half, __half hi_half) {
     return (uint32_t)__half_as_ushort(lo_half) | ((uint32_t)__half_as_ushort(hi_half) << 16);
 }
 
-__device__ __forceinline__ void st_global_v8(void *p, const uint32_t w[8]) {
-    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(w[0]), "r"(w[1]),
-                 "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
-                 : "memory");
-}
-// Row segments of 64 bytes (32 BF16, words w[0..7] the first half, w[8..15]
-// the second) held one per lane, the two lanes of each pair holding
-// consecutive rows (partner row at own -+ rs bytes): one exchange gives each
-// lane its half of both rows, and two 32-byte stores per lane then write two
-// whole segments per lane pair, so a warp store touches 16 segments instead
-// of 32 scattered 16-byte pieces.  All 32 lanes take part; own is 32-byte aligned.
-__device__ __forceinline__ void st_rowpair_v8(char *own, size_t rs, const uint32_t w[16], int qb) {
-    uint32_t mine[8], got[8], a[8], b[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        mine[i] = qb ? w[8 + i] : w[i];
-        got[i] = __shfl_xor_sync(0xffffffffu, qb ? w[i] : w[8 + i], 1);
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        a[i] = qb ? got[i] : mine[i];          // first row of the pair, half qb
-        b[i] = qb ? mine[i] : got[i];          // second row, half qb
-    }
-    char *r0 = own - (qb ? rs : 0) + 32 * qb;
-    st_global_v8(r0, a);
-    st_global_v8(r0 + rs, b);
-}
 
 // D[m][n] = sum_k A[pair][k][m] B[z][n][k] over the 128-row tiles
 // [blockIdx.x * tpc, ...) of one pair (blockIdx.y); A MN-major, B K-major;
 // z = q' for GEMM1, q'' for GEMM2.  Warp-specialised and persistent over the
-// CTA's tiles: warp 0 issues TMA (B once, resident; A through a two-stage
-// ring), warp 1 issues the MMAs into one of two TMEM accumulators (at
-// column 0 and at half the allocation), warps 4..11 run the epilogue of
-// the previous tile meanwhile (warp w reads TMEM lanes 32 (w % 4) ..; warps
-// 4..7 take one half of the columns, 8..11 the other).  Every wait is bounded; a failed wait sets *err and the CTA winds
-// down without touching memory it does not own.
-constexpr int kWsThreads = 384;
+// CTA's tiles: warp 0 issues TMA (B once, resident; A through a ring of
+// kStages stages), warp 1 issues the MMAs into one of two TMEM accumulators
+// (at column 0 and at half the allocation), and the epilogue warps (4 ..)
+// drain the previous tile meanwhile: warp w reads TMEM lanes 32 (w % 4) ..,
+// and the groups of four warps take the column chunks in turn -- two groups
+// for GEMM1 (its T1 stores are bound by HBM), three for GEMM2 (its delta
+// arithmetic is bound by latency, so more warps per SM sub-partition).
+// Every wait is bounded; a failed wait sets *err and the CTA winds down
+// without touching memory it does not own.
 constexpr int kEpiWarps = 8;
+template <int EPI> struct Warps {
+    static constexpr int kEpi = EPI == EPI_PHI ? 12 : 8;     // epilogue warps
+    static constexpr int kGroups = kEpi / 4;                  // column groups
+    static constexpr int kThreads = 32 * (4 + kEpi);
+};
 
 template <int EPI, int BN, int PB>
-__global__ void __launch_bounds__(kWsThreads, 1)
+__global__ void __launch_bounds__(Warps<EPI>::kThreads, 1)
 tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
                 const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBm,
                 const __grid_constant__ CUtensorMap mBl, XParams x, int tpc, int *err) {
@@ -171,7 +151,8 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
     // (-w hi, -w hi', -w lo, -w lo'), the same for n, and 1 / w
     __shared__ float4 wpk_sm[64], npk_sm[64];
     __shared__ float2 iwk_sm[64];
-    __shared__ float rowsum[2][2][kBM];          // [tile parity][column half][row]
+    __shared__ float rowsum[2][3][kBM];          // [tile parity][column group][row]
+    constexpr int NE = Warps<EPI>::kEpi, NG = Warps<EPI>::kGroups;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int a = blockIdx.y;
@@ -188,7 +169,7 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
     if (threadIdx.x == 0) {
         mbar_init(&bfull, 1);
         for (int s = 0; s < kStages; ++s) { mbar_init(&afull[s], 1); mbar_init(&aempty[s], 1); }
-        for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], kEpiWarps); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], NE); }
         mbar_init(&drain, 1);
         fail_sm = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -312,7 +293,7 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
                 // nb a multiple of 32 (so H = nb and nb^2 = Mp): every warp's 32 rows
                 // are valid and share c, with consecutive s
                 const bool pairs = (nb % 32) == 0 && H == nb && x.Mp == nb * nb;
-                for (int ci = hf; ok && ci < BN / 32; ci += 2) {
+                for (int ci = hf; ok && ci < BN / 32; ci += NG) {
                     const int c0 = ci * 32;
                     float v[32];
                     tmem_ld32(taddr + c0, v);
@@ -377,11 +358,10 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
                 const float2 N1H = make_float2(a1.z, a1.z), N1L = make_float2(a1.w, a1.w);
                 const float2 HN1 = make_float2(hn1, hn1);
                 float2 acc = make_float2(0.0f, 0.0f);
-                for (int ci = hf; ok && ci < H / 16; ci += 2) {
+                for (int ci = hf; ok && ci < H / 16; ci += NG) {
                     const int c0 = ci * 16;
                     float re[16], im[16];
-                    tmem_ld16(taddr + c0, re);
-                    tmem_ld16(taddr + H + c0, im);
+                    tmem_ld16x2(taddr + c0, taddr + H + c0, re, im);
                     if (!live) continue;
 #pragma unroll
                     for (int k = 0; k < 16; k += 2) {
@@ -417,7 +397,7 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
                 // 4 + (j % 4), lanes take rows 32 apart, then a fixed shuffle tree.
                 // (The buffer of this tile parity is rewritten two tiles later,
                 // after the next named barrier.)
-                named_sync(1, kEpiWarps * 32);
+                named_sync(1, NE * 32);
                 if (hf == 0 && ok) {
                     const int rt = tile * kBM, re = min(nb * nb, rt + kBM);
                     if (rt < re) {
@@ -427,7 +407,8 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
                             const int b0 = max(rt, sm * nb), b1 = min(re, (sm + 1) * nb);
                             float v = 0.0f;
                             for (int rr = b0 + lane; rr < b1; rr += 32)
-                                v += rowsum[buf][0][rr - rt] + rowsum[buf][1][rr - rt];
+#pragma unroll
+                                for (int gq = 0; gq < NG; ++gq) v += rowsum[buf][gq][rr - rt];
                             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                             if (lane == 0) {
                                 const bool first = b0 == sm * nb;
@@ -522,26 +503,42 @@ ycx_gather_kernel(XParams x, TcxGroups g, const float2 *__restrict__ epsT_all,
         for (int p = 0; p < P; ++p)
 #pragma unroll
             for (int t = 0; t < 9; ++t) acc[p][t] = make_float2(0.f, 0.f);
+        // the next block's indices and eps row are loaded one block ahead
+        int4 bi_n = make_int4(0, 0, 0, 0);
+        float2 u_n[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        if (lb < lb_end) {
+            bi_n = b_sm[lb];
+#pragma unroll
+            for (int t = 0; t < 3; ++t) u_n[t] = __ldg(eps + (size_t)(3 * bi_n.x + t) * nb + s);
+        }
         for (; lb < lb_end; ++lb) {
-            const int4 bi = b_sm[lb];
+            const int4 bi = bi_n;
+            float2 u[3];
+#pragma unroll
+            for (int t = 0; t < 3; ++t) u[t] = u_n[t];
+            if (lb + 1 < lb_end) {
+                bi_n = b_sm[lb + 1];
+#pragma unroll
+                for (int t = 0; t < 3; ++t) u_n[t] = __ldg(eps + (size_t)(3 * bi_n.x + t) * nb + s);
+            }
             const float4 *f4 = f_sm + 7 * (size_t)lb;
             float v[28];
 #pragma unroll
             for (int t = 0; t < 7; ++t) {
-                const float4 u = f4[t];
-                v[4 * t] = u.x; v[4 * t + 1] = u.y; v[4 * t + 2] = u.z; v[4 * t + 3] = u.w;
+                const float4 w4 = f4[t];
+                v[4 * t] = w4.x; v[4 * t + 1] = w4.y; v[4 * t + 2] = w4.z; v[4 * t + 3] = w4.w;
             }
-            float2 u[3];
-#pragma unroll
-            for (int t = 0; t < 3; ++t) u[t] = __ldg(eps + (size_t)(3 * bi.x + t) * nb + s);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 const float2 c1 = chi_sm[(2 * p) * n_rep + bi.y], c2 = chi_sm[(2 * p + 1) * n_rep + bi.z];
-                const float2 ph = make_float2(c1.x * c2.x + c1.y * c2.y, c1.y * c2.x - c1.x * c2.y);
+                // ph = c1 conj(c2), e = u ph: complex products as packed FP32x2 operations
+                const float2 ph = __ffma2_rn(make_float2(c1.y, -c1.x), make_float2(c2.y, c2.y),
+                                             __fmul2_rn(make_float2(c1.x, c1.y), make_float2(c2.x, c2.x)));
                 float2 e[3];
 #pragma unroll
                 for (int t = 0; t < 3; ++t)
-                    e[t] = make_float2(u[t].x * ph.x - u[t].y * ph.y, u[t].x * ph.y + u[t].y * ph.x);
+                    e[t] = __ffma2_rn(make_float2(-u[t].y, u[t].y), make_float2(ph.y, ph.x),
+                                      __fmul2_rn(make_float2(u[t].x, u[t].x), ph));
                 // complex += real * complex as packed FP32x2 FMAs
 #pragma unroll
                 for (int t = 0; t < 9; ++t) {
@@ -1093,11 +1090,11 @@ cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, L
                 x, g, ew, cw, p.n_rep, L.a1h, L.a1l);
         pg.end();
         ProfMark p1(p.prof, KALD_PROF_TCX_GEMM1, L.st);
-        k1<<<counted(dim3(gx, x.n_pairs)), kWsThreads, smem, L.st>>>(L.maps[0], L.maps[1], L.maps[2], L.maps[3],
+        k1<<<counted(dim3(gx, x.n_pairs)), Warps<EPI_T>::kThreads, smem, L.st>>>(L.maps[0], L.maps[1], L.maps[2], L.maps[3],
                                                                     L.maps[4], x, tpc, err);
         p1.end();
         ProfMark p2(p.prof, KALD_PROF_TCX_GEMM2, L.st);
-        k2<<<counted(dim3(gx, x.n_pairs)), kWsThreads, smem, L.st>>>(L.maps[5], L.maps[6], L.maps[7], L.maps[8],
+        k2<<<counted(dim3(gx, x.n_pairs)), Warps<EPI_PHI>::kThreads, smem, L.st>>>(L.maps[5], L.maps[6], L.maps[7], L.maps[8],
                                                                     L.maps[9], x, tpc, err);
         p2.end();
         e = cudaEventRecord(L.done[(i >> 1) & 1], L.st);

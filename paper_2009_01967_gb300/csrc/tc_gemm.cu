@@ -177,31 +177,32 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ 
     const int m = tm * kBM + row;
     const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
     if (EPI == EPI_SPLIT) {
-        // whole tile, 16-byte stores: rows and columns past M, N hold exact
-        // zeros (their A rows / B rows are zero padding) and the planes are
-        // allocated to the padded size
+        // whole tile: rows and columns past M, N hold exact zeros (their A rows
+        // / B rows are zero padding) and the planes are allocated to the padded
+        // size (ld a multiple of 128).  The lanes of a warp hold consecutive
+        // rows, so each lane pair writes two whole 64-byte row segments per
+        // chunk with 32-byte stores (st_rowpair_v8).
+        const bool okw = __all_sync(0xffffffffu, ok);
         const size_t orow = (size_t)bz * es.b_rows + m;
-        uint4 *ph = reinterpret_cast<uint4 *>(es.hi + orow * es.ld + tn * kBN);
-        uint4 *pl = reinterpret_cast<uint4 *>(es.lo + orow * es.ld + tn * kBN);
+        char *ph = reinterpret_cast<char *>(es.hi + orow * es.ld + tn * kBN);
+        char *pl = reinterpret_cast<char *>(es.lo + orow * es.ld + tn * kBN);
+        const size_t rs = sizeof(__nv_bfloat16) * (size_t)es.ld;
 #pragma unroll 1
         for (int c0 = 0; c0 < kBN; c0 += 32) {
             float v[32];
             tmem_ld_sum(taddr + c0, nacc, v);
-            if (!ok) continue;
+            if (!okw) continue;
+            uint32_t hw[16], lw[16];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                uint32_t hw[4], lw[4];
-#pragma unroll
-                for (int x = 0; x < 4; ++x) {
-                    const float a = v[8 * q + 2 * x], b = v[8 * q + 2 * x + 1];
-                    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-                    const __nv_bfloat162 l = __floats2bfloat162_rn(a - __low2float(h), b - __high2float(h));
-                    hw[x] = *reinterpret_cast<const uint32_t *>(&h);
-                    lw[x] = *reinterpret_cast<const uint32_t *>(&l);
-                }
-                ph[(c0 >> 3) + q] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                pl[(c0 >> 3) + q] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            for (int x = 0; x < 16; ++x) {
+                const float a = v[2 * x], b = v[2 * x + 1];
+                const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+                const __nv_bfloat162 l = __floats2bfloat162_rn(a - __low2float(h), b - __high2float(h));
+                hw[x] = *reinterpret_cast<const uint32_t *>(&h);
+                lw[x] = *reinterpret_cast<const uint32_t *>(&l);
             }
+            st_rowpair_v8(ph + 2 * c0, rs, hw, lane & 1);
+            st_rowpair_v8(pl + 2 * c0, rs, lw, lane & 1);
         }
     } else {
         // delta weights in FP32 (window test first; the FP64 unit is slow),
