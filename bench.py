@@ -124,34 +124,101 @@ def job_throughput(local_ms: float, world: int, units_per_step: float, steps: in
     return total_ms, units_per_step * steps / (total_ms / 1e3)
 
 
-def shard_plan(nq: int, n_sys: int, world: int, rank: int) -> dict:
+def inversion_classes(mesh) -> list:
+    """The q-points of a Gamma-centred mesh (flat index (k0 m1 + k1) m2 + k2)
+    grouped into the pairs {q, -q} (one member where -q = q), ordered by
+    their lower index."""
+    m0, m1, m2 = (int(x) for x in mesh)
+    out = []
+    for q in range(m0 * m1 * m2):
+        k0, k1, k2 = q // (m1 * m2), (q // m2) % m1, q % m2
+        qn = (((m0 - k0) % m0) * m1 + (m1 - k1) % m1) * m2 + (m2 - k2) % m2
+        if qn >= q:
+            out.append([q] if qn == q else [q, qn])
+    return out
+
+
+def shard_plan(mesh, n_sys: int, world: int, rank: int) -> dict:
     """How rank `rank` of `world` takes its share of one workload (strong
-    scaling: the workload is fixed).  A crystal: a contiguous range of q-points
-    (ceil(nq / world) each, the last ones shorter), every q' over the whole
-    mesh, then one all-gather of gamma (gather_q_sharded).  Several Gamma-only
-    systems: every world-th system, no collective (independent problems).  One
-    Gamma-only system: a replica (its modes are not split)."""
+    scaling: the workload is fixed).  A crystal: a contiguous run of the
+    inversion classes {q, -q} (ceil(classes / world) each), so that every
+    rank's q list is closed under q -> -q and kald_linewidths_qlist projects
+    each class once, every q' over the whole mesh; then one all-gather of gamma
+    (gather_q_sharded).  Several Gamma-only systems: every world-th system, no
+    collective (independent problems).  One Gamma-only system: a replica (its
+    modes are not split)."""
+    nq = int(np.prod(mesh))
     if world == 1:
         return {"kind": "whole"}
     if nq > 1:
-        per = -(-nq // world)
-        q0 = min(nq, rank * per)
-        return {"kind": "qrange", "q0": q0, "q1": min(nq, q0 + per), "per": per}
+        cls = inversion_classes(mesh)
+        per = -(-len(cls) // world)
+        lists = [[q for c in cls[r * per:(r + 1) * per] for q in c] for r in range(world)]
+        return {"kind": "qlist", "q": lists[rank], "lists": lists, "per": max(len(x) for x in lists)}
     if n_sys >= world:
         return {"kind": "systems", "idx": list(range(rank, n_sys, world))}
     return {"kind": "replica"}
 
 
-def gather_q_sharded(local, per: int, nb: int, nq: int, world: int):
+def orbit_pairs(mesh) -> int:
+    """Number of orbits of ordered momentum triples (q1, q2, -(q1 + q2)) under
+    the six permutations and inversion q -> -q: the projections the tensor
+    path makes when Phi3 is symmetric under permutations (host counting)."""
+    m = np.asarray(mesh, dtype=np.int64)
+    nq = int(np.prod(m))
+    k = np.stack(np.meshgrid(*[np.arange(x) for x in m], indexing="ij"), -1).reshape(-1, 3)
+
+    def flat(v):
+        v = np.mod(v, m)
+        return (v[..., 0] * m[1] + v[..., 1]) * m[2] + v[..., 2]
+    q1, q2 = np.meshgrid(np.arange(nq), np.arange(nq), indexing="ij")
+    q1, q2 = q1.ravel(), q2.ravel()
+    q3 = flat(-(k[q1] + k[q2]))
+    neg = flat(-k)
+    code = lambda a, b, c: (a * nq + b) * nq + c
+    t = code(q1, q2, q3)
+    lowest = np.ones(t.shape, dtype=bool)
+    for a, b, c in ((q1, q2, q3), (q1, q3, q2), (q2, q1, q3), (q2, q3, q1), (q3, q1, q2), (q3, q2, q1)):
+        lowest &= t <= code(a, b, c)
+        lowest &= t <= code(neg[a], neg[b], neg[c])
+    return int(np.sum(lowest))
+
+
+def projected_pairs(mesh, plan: dict, opt, nb: int) -> int:
+    """(q, q') projections per step on this rank: one per orbit of momentum
+    triples on the BF16-split tensor path over the whole mesh (Phi3 of a pair
+    potential is symmetric under permutations); else the inversion classes
+    {q, -q} of its q-points times the mesh (time reversal, when symmetry is not
+    "none" and degenerate averaging is on); else its q-points times the mesh."""
+    nq = int(np.prod(mesh))
+    qs = plan["q"] if plan["kind"] == "qlist" else list(range(nq))
+    if nq == 1 or opt.symmetry == "none" or not opt.degen_tol_thz > 0:
+        return len(qs) * nq
+    if (opt.symmetry == "all" and opt.precision == "bf16split" and 65 <= nb <= 96
+            and plan["kind"] != "qlist"):
+        return orbit_pairs(mesh)
+    mine = set(qs)
+    return sum(1 for c in inversion_classes(mesh) if mine.intersection(c)) * nq
+
+
+def gather_q_sharded(local, plan: dict, nb: int, nq: int, world: int):
     """All-gather of the q-sharded gamma: `local` holds this rank's
-    (q1 - q0) * nb values; every rank gets the full [nq * nb] vector."""
+    len(plan["q"]) * nb values (row j = q-point plan["q"][j]); every rank gets
+    the full [nq * nb] vector (each rank's rows placed at its q-points)."""
     import torch
     import torch.distributed as dist
+    per = plan["per"]
     buf = torch.zeros(per * nb, dtype=local.dtype, device=local.device)
     buf[:local.numel()] = local
     out = torch.empty(world * per * nb, dtype=local.dtype, device=local.device)
     dist.all_gather_into_tensor(out, buf)
-    return out[:nq * nb]
+    rows = out.view(world * per, nb)
+    src = torch.tensor([r * per + j for r in range(world) for j in range(len(plan["lists"][r]))],
+                       device=local.device)
+    dst = torch.tensor([q for lst in plan["lists"] for q in lst], device=local.device)
+    full = torch.empty(nq, nb, dtype=local.dtype, device=local.device)
+    full[dst] = rows[src]
+    return full.view(-1)
 
 
 # ------------------------------------------------------------- oracle timing
@@ -246,11 +313,11 @@ def _gamma_only_band_tiles(om, cut, tile=128, symmetric=True):
     return n_tiles
 
 
-def roofline_of(args, w, nbs, nu_c, opt, prof, steps, allowed, share=1.0):
+def roofline_of(args, w, nbs, nu_c, opt, prof, steps, allowed, pairs_step=None):
     """Roofline line of the dominant kernel: ALGORITHMIC work per launch
     (the method's flops, not the split-precision emulation) over the mean
-    launch duration from the library's per-launch CUDA events.  `share` is
-    the fraction of the workload's q-points this rank computes."""
+    launch duration from the library's per-launch CUDA events.  `pairs_step`
+    is the number of (q, q') projections this rank makes per step."""
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, FMA = 2 flops
@@ -318,6 +385,7 @@ def roofline_of(args, w, nbs, nu_c, opt, prof, steps, allowed, share=1.0):
     if ms <= 0 or launches == 0:
         return {"bound": bound, "achieved": None, "peak": peak, "unit": "TFLOP/s", "frac": None,
                 "traffic": None, "kernel": kernel, "note": "no timed launches of this kernel"}
+    share = (pairs_step / (nq * nq)) if pairs_step is not None else 1.0
     alg *= share
     if executed is not None:
         executed *= share
@@ -385,7 +453,7 @@ def run_kald(args):
     if args.mesh:
         w.mesh = tuple(int(x) for x in args.mesh.split(","))
     units_step = float(sum(w.n_q * w.n_q * x.n_branches ** 3 for x in w.systems))   # whole job
-    shard = shard_plan(w.n_q, len(w.systems), world, rank)
+    shard = shard_plan(w.mesh, len(w.systems), world, rank)
     if shard["kind"] == "systems":
         w.systems = [w.systems[x] for x in shard["idx"]]
     elif shard["kind"] == "replica":
@@ -431,13 +499,12 @@ def run_kald(args):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        if shard["kind"] == "qrange":
-            q0, q1 = shard["q0"], shard["q1"]
-            loc = gam[:(q1 - q0) * nb]
+        if shard["kind"] == "qlist":
+            loc = gam[:len(shard["q"]) * nb]
             trip = (0, 0)
-            if q1 > q0:
-                _, trip = kk.kald_linewidths_qrange(ctx, s, w.mesh, nu, eig, opt, q0, q1, gamma=loc)
-            gam.copy_(gather_q_sharded(loc.clone(), shard["per"], nb, nq, world))
+            if shard["q"]:
+                _, trip = kk.kald_linewidths_qlist(ctx, s, w.mesh, nu, eig, opt, shard["q"], gamma=loc)
+            gam.copy_(gather_q_sharded(loc.clone(), shard, nb, nq, world))
         else:
             _, trip = kk.kald_linewidths(ctx, w.systems, w.mesh, nu, eig, opt, gamma=gam)
         ev1.record(stream)
@@ -490,12 +557,11 @@ def run_kald(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         phon(nu_h, eig_h)
-        if shard["kind"] == "qrange":
-            q0, q1 = shard["q0"], shard["q1"]
-            loc = np.zeros((q1 - q0) * nb)
-            if q1 > q0:
-                kk.kald_linewidths_qrange(ctx, s, w.mesh, nu_h, eig_h, opt, q0, q1, gamma=loc)
-            full = gather_q_sharded(torch.from_numpy(loc).to(dev), shard["per"], nb, nq, world)
+        if shard["kind"] == "qlist":
+            loc = np.zeros(len(shard["q"]) * nb)
+            if shard["q"]:
+                kk.kald_linewidths_qlist(ctx, s, w.mesh, nu_h, eig_h, opt, shard["q"], gamma=loc)
+            full = gather_q_sharded(torch.from_numpy(loc).to(dev), shard, nb, nq, world)
             gam_h[:] = full.cpu().numpy()
         else:
             kk.kald_linewidths(ctx, w.systems, w.mesh, nu_h, eig_h, opt, gamma=gam_h)
@@ -511,8 +577,8 @@ def run_kald(args):
 
     # ---- roofline of the dominant kernel, timed per launch inside the steps
     trip, allowed = trip_info["trip"]
-    share = (shard["q1"] - shard["q0"]) / nq if shard["kind"] == "qrange" else 1.0
-    roofline = roofline_of(args, w, nbs, nu.cpu().numpy(), opt, prof, args.steps, allowed, share)
+    pairs_step = projected_pairs(w.mesh, shard, opt, nbs[0])
+    roofline = roofline_of(args, w, nbs, nu.cpu().numpy(), opt, prof, args.steps, allowed, pairs_step)
 
     # ---- kappa time-to-solution: split path against the plain FP64 GPU path
     tts = None
@@ -528,7 +594,7 @@ def run_kald(args):
     # Gamma-only system runs as replicas
     one_system_gamma = (w.n_q == 1 and shard["kind"] in ("whole", "replica") and len(w.systems) == 1)
     scaling = "weak" if one_system_gamma else "strong"
-    parallelism = {"whole": "single GPU", "qrange": f"q-sharded over {world} GPUs, all-gather of gamma (NCCL)",
+    parallelism = {"whole": "single GPU", "qlist": f"q-sharded over {world} GPUs (inversion classes), all-gather of gamma (NCCL)",
                    "systems": f"systems dealt over {world} GPUs", "replica": f"replicas{world}"}[shard["kind"]]
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -541,6 +607,11 @@ def run_kald(args):
                            "seq_len": None, "parallelism": parallelism,
                            "l2": "flushed (256 MB write) between timed steps",
                            "precision": args.precision,
+                           "symmetry": opt.symmetry,
+                           "projected_pairs_per_step": (
+                               sum(projected_pairs(w.mesh, dict(shard, q=lst), opt, nbs[0]) for lst in shard["lists"])
+                               if shard["kind"] == "qlist" else pairs_step),
+                           "momentum_pairs_per_step": nq * nq if not gamma_only else None,
                            "linewidth_ms": float(np.mean(lw_ms))},
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},

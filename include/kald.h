@@ -65,6 +65,27 @@ typedef enum {
                                 Gamma-only systems.                           */
 } kald_precision;
 
+/* Exact symmetries of the three-phonon projections that kald_linewidths may
+ * use to project fewer momentum triplets (crystals).  Both leave every
+ * linewidth unchanged up to rounding; each needs degenerate averaging
+ * (degen_tol_thz > 0), since a degenerate mode's own linewidth depends on the
+ * eigenvector basis while the averages do not.
+ *  - Time reversal: Phi3 is real, so the projection of (-q, -q', -q'') is the
+ *    conjugate of that of (q, q', q'') and w(-q) = w(q); one q-point of each
+ *    pair {q, -q} is projected and the other takes its averaged linewidths.
+ *  - Permutation (Eq. gamma_operators with Phi3 symmetric under permutations
+ *    of its three indices, checked on the host to 1e-12 of max |Phi3|): the
+ *    squared projection |phi|^2 of a momentum triple (q1, q2, q3),
+ *    q1 + q2 + q3 = 0 modulo G, is the same for every order of the triple, so
+ *    one projection per orbit of ordered triples under permutations and
+ *    inversion feeds the linewidths of all three members (BF16-split tensor
+ *    path, whole-mesh calls). */
+typedef enum {
+    KALD_SYM_ALL = 0,        /* every symmetry the path supports (default)    */
+    KALD_SYM_INVERSION = 1,  /* time reversal only                            */
+    KALD_SYM_NONE = 2        /* every q-point projected against every q'      */
+} kald_symmetry;
+
 /* One crystal unit cell, or one Gamma-only supercell (used with mesh 1x1x1).
  * Force constants are in home-cell-first sparse atom-block form (the storage
  * of the paper's appendix "Code details"):
@@ -104,6 +125,8 @@ typedef struct {
                                   model; linewidths unused); 0: off          */
     double qhgk_threshold_thz; /* > 0: tau_{mu mu'} = 0 for |d nu| > threshold
                                   (QHGK and diffusivity); 0: off             */
+    int32_t symmetry;          /* kald_symmetry: exact symmetries of the
+                                  projections that the linewidths may use    */
 } kald_options;
 
 /* Create a context on CUDA device `device` (own stream, empty workspace).
@@ -226,13 +249,29 @@ kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys
  *   gamma       [(q_end - q_begin)][nb] out: the linewidths of those q only
  *   n_triplets  [2] out or NULL: the triplets (q_end - q_begin) Nq nb^3 and
  *               the delta-allowed ones among them.
- * The sums of a q-point do not depend on the range it is computed in, so the
- * ranges of any partition of [0, Nq) concatenate to kald_linewidths' gamma bit
- * for bit: the unit of a multi-GPU split (contiguous q ranges, one all-gather
- * of gamma).  KALD_E_INVALID unless 0 <= q_begin < q_end <= Nq. */
+ * Time reversal is the only symmetry used here: a q-point is projected as
+ * the lower index of {q, -q} whichever of the two is asked for, so the sums
+ * of a q-point do not depend on the call and the ranges of any partition of
+ * [0, Nq) concatenate to the gamma of kald_linewidths with
+ * symmetry = KALD_SYM_INVERSION bit for bit.
+ * KALD_E_INVALID unless 0 <= q_begin < q_end <= Nq. */
 kald_status kald_linewidths_qrange(kald_ctx *ctx, const kald_system *sys, const int32_t mesh[3],
                                    const double *nu_thz, const double *eigvec, const kald_options *opt,
                                    int32_t q_begin, int32_t q_end, double *gamma, uint64_t *n_triplets);
+
+/* kald_linewidths for an explicit list of q-points of one crystal (flat mesh
+ * indices, any order, repeats allowed), the unit of a multi-GPU split:
+ *   q_list      [n_q] in: 0 <= q_list[j] < Nq
+ *   gamma       [n_q][nb] out: row j holds the linewidths of q_list[j]
+ *   n_triplets  [2] out or NULL: n_q Nq nb^3 and the delta-allowed ones.
+ * A list that holds both q and -q projects the pair once (time reversal is
+ * the only symmetry used here), so lists closed under q -> -q cost half of
+ * their length; rows are bit for bit those of kald_linewidths with
+ * symmetry = KALD_SYM_INVERSION.  KALD_E_INVALID for an empty list or an
+ * entry outside [0, Nq). */
+kald_status kald_linewidths_qlist(kald_ctx *ctx, const kald_system *sys, const int32_t mesh[3],
+                                  const double *nu_thz, const double *eigvec, const kald_options *opt,
+                                  int32_t n_q, const int32_t *q_list, double *gamma, uint64_t *n_triplets);
 
 /* The full linearised BTE scattering operator of one crystal (section
  * "Boltzman Transport Equation": Gamma~ = diag(Gamma^0) + Gamma^1 with

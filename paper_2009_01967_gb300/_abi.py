@@ -23,12 +23,13 @@ STATUS = {0: "KALD_OK", 1: "KALD_E_INVALID", 2: "KALD_E_NOMEM", 3: "KALD_E_CUDA"
           4: "KALD_E_NOCONV", 5: "KALD_E_TIMEOUT", 6: "KALD_E_UNSUPPORTED"}
 PRECISION = {"fp64": 0, "fp32": 1, "bf16split": 2}
 DELTA_SHAPE = {"gaussian": 0, "lorentzian": 1, "triangular": 2}
+SYMMETRY = {"all": 0, "inversion": 1, "none": 2}
 
 EXPORTS = ["kald_ctx_create", "kald_ctx_destroy", "kald_last_error", "kald_set_stream",
            "kald_phonons", "kald_linewidths", "kald_kappa_rta", "kald_kappa_qhgk",
            "kald_kappa_rta_noalloc", "kald_kernel_launches", "kald_set_wait_limit",
            "kald_set_workspace_limit", "kald_profile_enable", "kald_profile_read",
-           "kald_linewidths_qrange", "kald_phonons_batch", "kald_phase_space", "kald_diffusivity",
+           "kald_linewidths_qrange", "kald_linewidths_qlist", "kald_phonons_batch", "kald_phase_space", "kald_diffusivity",
            "kald_scattering_matrix", "kald_kappa_bte", "kald_interpolate_gamma", "kald_fd_force_constants"]
 PROF_KERNELS = {"tcx_gather": 0, "tcx_gemm1": 1, "tcx_gemm2": 2, "tc_gemm1": 3, "tc_gemm2": 4,
                 "small_nb": 5, "lw_main": 6}
@@ -55,7 +56,8 @@ class kald_options(C.Structure):
     _fields_ = [("temperature_K", C.c_double), ("sigma_thz", C.c_double), ("n_sigma", C.c_double),
                 ("omega_min_thz", C.c_double), ("degen_tol_thz", C.c_double),
                 ("classical", C.c_int32), ("precision", C.c_int32), ("delta_shape", C.c_int32),
-                ("qhgk_bandwidth_thz", C.c_double), ("qhgk_threshold_thz", C.c_double)]
+                ("qhgk_bandwidth_thz", C.c_double), ("qhgk_threshold_thz", C.c_double),
+                ("symmetry", C.c_int32)]
 
 
 _lib = None
@@ -103,6 +105,9 @@ def load_library(path: str = LIB_PATH):
     lib.kald_linewidths_qrange.argtypes = [vp, C.POINTER(kald_system), C.POINTER(i32), vp, vp,
                                            C.POINTER(kald_options), i32, i32, vp, C.POINTER(C.c_uint64)]
     lib.kald_linewidths_qrange.restype = st
+    lib.kald_linewidths_qlist.argtypes = [vp, C.POINTER(kald_system), C.POINTER(i32), vp, vp,
+                                          C.POINTER(kald_options), i32, vp, vp, C.POINTER(C.c_uint64)]
+    lib.kald_linewidths_qlist.restype = st
     lib.kald_kappa_rta.argtypes = [vp, C.POINTER(kald_system), C.POINTER(i32), vp, vp, vp,
                                    C.POINTER(kald_options), vp]
     lib.kald_kappa_rta.restype = st
@@ -143,12 +148,13 @@ class Options:
     delta: str = "gaussian"
     qhgk_bandwidth_thz: float = 0.0
     qhgk_threshold_thz: float = 0.0
+    symmetry: str = "all"          # "all", "inversion" (time reversal only) or "none"
 
     def c(self) -> kald_options:
         return kald_options(self.temperature_K, self.sigma_thz, self.n_sigma, self.omega_min_thz,
                             self.degen_tol_thz, int(bool(self.classical)), PRECISION[self.precision],
                             DELTA_SHAPE[self.delta], float(self.qhgk_bandwidth_thz),
-                            float(self.qhgk_threshold_thz))
+                            float(self.qhgk_threshold_thz), SYMMETRY[self.symmetry])
 
 
 class Context:
@@ -346,6 +352,32 @@ def kald_linewidths_qrange(ctx: Context, system, mesh, nu_thz, eigvec, options: 
                                              _ptr(eigvec, np.complex128, nq * nb * nb, "eigvec"),
                                              C.byref(opt), int(q_begin), int(q_end),
                                              _ptr(gamma, np.float64, max(n_out, 0), "gamma"), trip))
+    del keep
+    return gamma, (int(trip[0]), int(trip[1]))
+
+
+def kald_linewidths_qlist(ctx: Context, system, mesh, nu_thz, eigvec, options: Options, q_list, gamma=None):
+    """Linewidths of the listed q-points of one crystal (full-mesh nu and
+    eigvec in); returns (gamma [len(q_list) * nb], row j = q_list[j],
+    (n_triplets, n_allowed))."""
+    cs, keep = c_system(system)
+    m, nq = _mesh(mesh)
+    nb = 3 * cs.n_atoms
+    ql = np.ascontiguousarray(np.asarray(q_list, dtype=np.int32).ravel())
+    n_out = ql.size * nb
+    if gamma is None:
+        if isinstance(nu_thz, np.ndarray):
+            gamma = np.zeros(max(n_out, 0))
+        else:
+            import torch
+            gamma = torch.zeros(max(n_out, 0), dtype=torch.float64, device=nu_thz.device)
+    trip = (C.c_uint64 * 2)()
+    opt = options.c()
+    ctx.check(ctx.lib.kald_linewidths_qlist(ctx.handle, C.byref(cs), m,
+                                            _ptr(nu_thz, np.float64, nq * nb, "nu_thz"),
+                                            _ptr(eigvec, np.complex128, nq * nb * nb, "eigvec"),
+                                            C.byref(opt), int(ql.size), ql.ctypes.data,
+                                            _ptr(gamma, np.float64, max(n_out, 0), "gamma"), trip))
     del keep
     return gamma, (int(trip[0]), int(trip[1]))
 

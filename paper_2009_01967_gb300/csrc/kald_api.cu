@@ -725,8 +725,9 @@ kald_status kald_phonons_batch(kald_ctx *ctx, int32_t n_sys, const kald_system *
 namespace kald {
 namespace {
 // True when every fc3 block (i; j Rj; k Rk) has the partner (i; k Rk; j Rj)
-// with the last two Cartesian indices exchanged (then Y_mu and phi are
-// symmetric and the tensor-core path computes only the upper triangle).
+// with the last two Cartesian indices exchanged, to 1e-12 of the largest
+// |Phi3| (then Y_mu and phi are symmetric and the tensor-core path computes
+// only the upper triangle).
 bool fc3_symmetric_last_two(const kald_system *s) {
     struct H {
         size_t operator()(const std::array<int, 9> &a) const {
@@ -737,6 +738,11 @@ bool fc3_symmetric_last_two(const kald_system *s) {
     };
     std::unordered_map<std::array<int, 9>, int, H> idx;
     idx.reserve((size_t)s->n_fc3 * 2);
+    // entries agree to 1e-12 of the largest |Phi3| (the self blocks (i; i; i)
+    // are sums that cancel to rounding noise, so no per-entry relative test)
+    double tol = 0.0;
+    for (size_t v = 0; v < 27 * (size_t)s->n_fc3; ++v) tol = std::max(tol, std::fabs(s->fc3[v]));
+    tol *= 1e-12;
     for (int b = 0; b < s->n_fc3; ++b) {
         std::array<int, 9> k;
         for (int x = 0; x < 9; ++x) k[x] = s->fc3_idx[9 * (size_t)b + x];
@@ -752,7 +758,48 @@ bool fc3_symmetric_last_two(const kald_system *s) {
             for (int c = 0; c < 3; ++c)
                 for (int d = 0; d < 3; ++d) {
                     const double u = f[9 * a + 3 * c + d], v = g[9 * a + 3 * d + c];
-                    if (std::fabs(u - v) > 1e-12 * (std::fabs(u) + std::fabs(v)) + 1e-300) return false;
+                    if (std::fabs(u - v) > tol) return false;
+                }
+    }
+    return true;
+}
+// True when Phi3 is symmetric under every permutation of its three (atom,
+// cell, Cartesian) indices: with the exchange of the last two (above), every
+// block (i; j Rj; k Rk) has the partner (j; i -Rj; k Rk - Rj) (home atom j)
+// with the first two Cartesian indices exchanged, to 1e-12 of the largest
+// |Phi3|.  The two exchanges generate all six permutations.
+bool fc3_symmetric_all(const kald_system *s) {
+    if (!fc3_symmetric_last_two(s)) return false;
+    struct H {
+        size_t operator()(const std::array<int, 9> &a) const {
+            size_t h = 1469598103934665603ull;
+            for (int v : a) h = (h ^ (size_t)(uint32_t)v) * 1099511628211ull;
+            return h;
+        }
+    };
+    std::unordered_map<std::array<int, 9>, int, H> idx;
+    idx.reserve((size_t)s->n_fc3 * 2);
+    // entries agree to 1e-12 of the largest |Phi3| (the self blocks (i; i; i)
+    // are sums that cancel to rounding noise, so no per-entry relative test)
+    double tol = 0.0;
+    for (size_t v = 0; v < 27 * (size_t)s->n_fc3; ++v) tol = std::max(tol, std::fabs(s->fc3[v]));
+    tol *= 1e-12;
+    for (int b = 0; b < s->n_fc3; ++b) {
+        std::array<int, 9> k;
+        for (int x = 0; x < 9; ++x) k[x] = s->fc3_idx[9 * (size_t)b + x];
+        idx.emplace(k, b);
+    }
+    for (int b = 0; b < s->n_fc3; ++b) {
+        const int32_t *x = s->fc3_idx + 9 * (size_t)b;
+        const std::array<int, 9> k = {x[1], x[0], -x[2], -x[3], -x[4], x[5], x[6] - x[2], x[7] - x[3], x[8] - x[4]};
+        auto it = idx.find(k);
+        if (it == idx.end()) return false;
+        const double *f = s->fc3 + 27 * (size_t)b, *g = s->fc3 + 27 * (size_t)it->second;
+        for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < 3; ++c)
+                for (int d = 0; d < 3; ++d) {
+                    const double u = f[9 * a + 3 * c + d], v = g[9 * c + 3 * a + d];
+                    if (std::fabs(u - v) > tol) return false;
                 }
     }
     return true;
@@ -804,6 +851,8 @@ static kald_status check_options(kald_ctx *ctx, const kald_options *o) {
     if (!(o->qhgk_bandwidth_thz >= 0.0) || !(o->qhgk_threshold_thz >= 0.0) || !std::isfinite(o->qhgk_bandwidth_thz) ||
         !std::isfinite(o->qhgk_threshold_thz))
         return fail(ctx, KALD_E_INVALID, "qhgk bandwidth and threshold must be finite and >= 0");
+    if (o->symmetry < KALD_SYM_ALL || o->symmetry > KALD_SYM_NONE)
+        return fail(ctx, KALD_E_INVALID, "symmetry must be 0 (all), 1 (time reversal only) or 2 (none)");
     return KALD_OK;
 }
 
@@ -1045,7 +1094,7 @@ struct BteHook {
 // of one crystal; with `bte`, also the scattering-operator planes (FP64 paths).
 static kald_status linewidths_impl(kald_ctx *ctx, int32_t n_sys, const kald_system *sys,
                                    const int32_t mesh[3], const double *nu_thz, const double *eigvec,
-                                   const kald_options *opt, int32_t q_begin, int32_t q_end, double *gamma,
+                                   const kald_options *opt, int32_t n_list, const int32_t *q_list, double *gamma,
                                    uint64_t *n_triplets, const BteHook *bte = nullptr) {
     if (!ctx) return KALD_E_INVALID;
     kald_status st = set_device(ctx);
@@ -1057,9 +1106,14 @@ static kald_status linewidths_impl(kald_ctx *ctx, int32_t n_sys, const kald_syst
     if (n_sys > 1 && nq_mesh != 1)
         return fail(ctx, KALD_E_INVALID, "several systems need mesh {1,1,1} (Gamma-only batch)");
     if (!nu_thz || !eigvec || !gamma) return fail(ctx, KALD_E_INVALID, "nu/eigvec/gamma NULL");
-    const bool ranged = q_end >= 0;
-    if (ranged && (n_sys != 1 || q_begin < 0 || q_end > nq_mesh || q_begin >= q_end))
-        return fail(ctx, KALD_E_INVALID, "q range must satisfy 0 <= q_begin < q_end <= N_k (one system)");
+    const bool listed = n_list >= 0;
+    if (listed) {
+        if (n_sys != 1 || n_list < 1 || !q_list)
+            return fail(ctx, KALD_E_INVALID, "a q list needs one system and at least one q-point");
+        for (int i = 0; i < n_list; ++i)
+            if (q_list[i] < 0 || q_list[i] >= nq_mesh)
+                return fail(ctx, KALD_E_INVALID, "q list entries must satisfy 0 <= q < N_k");
+    }
     const bool d_nu = is_device_ptr(nu_thz), d_eig = is_device_ptr(eigvec), d_g = is_device_ptr(gamma);
     const int fp32 = opt->precision == KALD_FP32;
     uint64_t tot = 0, allowed_tot = 0;
@@ -1087,8 +1141,43 @@ static kald_status linewidths_impl(kald_ctx *ctx, int32_t n_sys, const kald_syst
         std::vector<int> qf;
         mesh_points(h.lattice, mesh, qc, qf);
         const int nq = nq_mesh;
-        const int q0 = ranged ? q_begin : 0, q1 = ranged ? q_end : nq;
-        const int nqr = q1 - q0;                 // q-points whose linewidths this call computes
+        // q-points whose linewidths this call returns (gamma row j: qout[j])
+        std::vector<int> qout(listed ? q_list : nullptr, listed ? q_list + n_list : nullptr);
+        if (!listed) {
+            qout.resize(nq);
+            for (int q = 0; q < nq; ++q) qout[q] = q;
+        }
+        const int nqr = (int)qout.size();
+        // Projected q-points: with degenerate averaging on, the lower index of
+        // each pair {q, -q} (Phi3 is real, so phi(-q, -q', -q'') =
+        // conj phi(q, q', q'') and w(-q) = w(q): the averaged linewidths of -q
+        // are those of q), whichever of the two is asked for; every q-point for
+        // the operator of the full BTE (its rows are per q) or without averaging
+        // (a degenerate mode's own linewidth depends on the basis).  The choice
+        // depends on q alone, so a q-point's sums are the same in any call.
+        const bool reuse = !bte && opt->symmetry != KALD_SYM_NONE && opt->degen_tol_thz > 0.0;
+        std::vector<int> rep_row(nq, -1);
+        std::vector<int2> qsel;
+        std::vector<int> qrow(nqr);
+        for (int j = 0; j < nqr; ++j) {
+            const int q = qout[j];
+            const int *k = &qf[3 * (size_t)q];
+            const int qn = (((mesh[0] - k[0]) % mesh[0]) * mesh[1] + (mesh[1] - k[1]) % mesh[1]) * mesh[2] +
+                           (mesh[2] - k[2]) % mesh[2];
+            const int rep = reuse ? std::min(q, qn) : q;
+            if (rep_row[rep] < 0) {
+                rep_row[rep] = (int)qsel.size();
+                qsel.push_back(make_int2(rep, 0));
+            }
+            qrow[j] = rep_row[rep];
+            qsel[qrow[j]].y += 1;              // returned q-points this projection stands for
+        }
+        const int nqc = (int)qsel.size();
+        int n_self_inverse = 0;                  // q-points with -q = q (on the mesh)
+        for (int q = 0; q < nq; ++q) {
+            const int *k = &qf[3 * (size_t)q];
+            n_self_inverse += (2 * k[0]) % mesh[0] == 0 && (2 * k[1]) % mesh[1] == 0 && (2 * k[2]) % mesh[2] == 0;
+        }
         // One- and two-atom cells: the register kernel of small_nb.cu in every
         // precision (FP32 arithmetic unless FP64 is asked for), with the Bloch
         // phases from a table of L-th roots of unity (L = lcm of the mesh).
@@ -1120,15 +1209,19 @@ static kald_status linewidths_impl(kald_ctx *ctx, int32_t n_sys, const kald_syst
         p.omega_min_w = kTwoPi * opt->omega_min_thz;
         p.wait_limit = ctx->wait_limit;
         p.prof = &ctx->prof;
-        p.q0 = q0;
-        p.q1 = q1;
+        p.q0 = 0;
+        p.q1 = nqr;
+        p.nqc = nqc;
         p.bte = bte ? 1 : 0;
         p.bte_pref = kHbarEvPs * kPi / 8.0 * kEvA2AmuPs2 * kEvA2AmuPs2 * kEvA2AmuPs2 / (double)nq /
                      (1.0 / delta_norm(opt->delta_shape, p.sigma_w));
-        // about 64 items per SM for balance, q' chunks as long as that allows
+        // about 64 items per SM for balance when the whole mesh is computed, q'
+        // chunks as long as that allows (sized from the mesh, not from this
+        // call's q-points, so that a q-point's sums are the same in any call)
         {
             const long long want = 64LL * std::max(1, ctx->sm_count);
-            int nch = (int)std::max(1LL, std::min<long long>(nq, (want + nqr - 1) / nqr));
+            const long long n_full = reuse ? (nq + n_self_inverse) / 2 : nq;
+            int nch = (int)std::max(1LL, std::min<long long>(nq, (want + n_full - 1) / n_full));
             p.qp_chunk = (nq + nch - 1) / nch;
             p.n_chunks = (nq + p.qp_chunk - 1) / p.qp_chunk;
             if (tcx) { p.qp_chunk = nq; p.n_chunks = 1; }
@@ -1156,6 +1249,19 @@ static kald_status linewidths_impl(kald_ctx *ctx, int32_t n_sys, const kald_syst
             for (int g = 0; g < ng; ++g) sn_gjk[g] = make_int2(h.pair3_j[g], h.pair3_k[g]);
         }
         const int tcx_b = tcx ? tcx_batch_max(nb, nq, ctx->sm_count) : 0;   // scratch for the tuner's largest batch
+        // tensor-core path over the whole mesh with Phi3 symmetric under
+        // permutations: one projection per orbit of momentum triples
+        TcxSymHost symh;
+        bool use_sym = false;
+        if (tcx && !listed && reuse && opt->symmetry == KALD_SYM_ALL && nq > 1) {
+            if (h.fc3_perm_symmetric < 0) h.fc3_perm_symmetric = fc3_symmetric_all(&sys[x]) ? 1 : 0;
+            if (h.fc3_perm_symmetric) {
+                std::vector<int> self_inv(nqc);
+                for (int i = 0; i < nqc; ++i) self_inv[i] = qsel[i].y == 1 ? 1 : 0;
+                plan_tcx_sym(mesh, qf, qrow, self_inv, symh);       // qrow[q]: class row (whole mesh)
+                use_sym = !symh.pairs.empty();
+            }
+        }
         // tensor-core path: the fc3 blocks in (j, k) group order, the groups
         // split over the gather CTAs
         std::vector<int2> tc_gjk;
@@ -1205,7 +1311,8 @@ static kald_status linewidths_impl(kald_ctx *ctx, int32_t n_sys, const kald_syst
                       bytes_of(h.rep_cart) + bytes_of(qc) + bytes_of(qf) +
                       2 * ws_round(sizeof(double) * nq * nb) + ws_round(c2 * nn) +
                       ws_round(c2 * (size_t)nq * h.n_rep) +
-                      ws_round(sizeof(double) * (size_t)nqr * p.n_chunks * nb) + 2 * ws_round(16);
+                      ws_round(sizeof(double) * (size_t)nqc * p.n_chunks * nb) + 2 * ws_round(16) +
+                      bytes_of(qsel) + bytes_of(qrow) + bytes_of(qout);
         if (!d_nu) need += ws_round(sizeof(double) * nq * nb);
         if (!d_eig) need += ws_round(sizeof(double2) * nn);
         if (!d_g) need += ws_round(sizeof(double) * nqr * nb);
@@ -1213,6 +1320,9 @@ static kald_status linewidths_impl(kald_ctx *ctx, int32_t n_sys, const kald_syst
         if (tcx)
             need += ws_round(tcx_scratch_bytes(nb, nq, tcx_b)) + ws_round(16) + bytes_of(tc_gjk) +
                     bytes_of(tc_part_start) + bytes_of(tc_glist) + bytes_of(h.pair3_start);
+        if (use_sym)
+            need += ws_round(tcx_sym_bytes(nb, tcx_b, (int)symh.pairs.size())) + bytes_of(symh.pairs) +
+                    bytes_of(symh.orbit) + bytes_of(symh.cls_start) + bytes_of(symh.ent) + bytes_of(symh.fac);
         if (!y_blk.empty())
             need += scaled_bytes(y_blk, y_atoms, h, 27, 28, 1) + bytes_of(y_gi) + bytes_of(y_rep);
         if (small)
@@ -1236,7 +1346,10 @@ static kald_status linewidths_impl(kald_ctx *ctx, int32_t n_sys, const kald_syst
         d.wn32 = f32w ? static_cast<float4 *>(ws_take(ctx, sizeof(float4) * (size_t)nq * nb)) : nullptr;
         d.eps_work = ws_take(ctx, c2 * nn);
         d.chi = ws_take(ctx, c2 * (size_t)nq * h.n_rep);
-        d.partial = static_cast<double *>(ws_take(ctx, sizeof(double) * (size_t)nqr * p.n_chunks * nb));
+        d.partial = static_cast<double *>(ws_take(ctx, sizeof(double) * (size_t)nqc * p.n_chunks * nb));
+        d.qsel = upload(ctx, qsel);
+        d.qrow = upload(ctx, qrow);
+        d.qout = upload(ctx, qout);
         d.allowed = static_cast<unsigned long long *>(ws_take(ctx, 16));
         d.queue = static_cast<int *>(ws_take(ctx, 16));
         d.g1_a = bte ? bte->g1_a : nullptr;
@@ -1246,6 +1359,18 @@ static kald_status linewidths_impl(kald_ctx *ctx, int32_t n_sys, const kald_syst
         double *g_d = d_g ? gamma + off_nb : static_cast<double *>(ws_take(ctx, sizeof(double) * nqr * nb));
         void *tc_scr = tcx ? ws_take(ctx, tcx_scratch_bytes(nb, nq, tcx_b)) : nullptr;
         int *tc_err = tcx ? static_cast<int *>(ws_take(ctx, 16)) : nullptr;
+        TcxSym tsym;
+        void *sym_scr = nullptr;
+        if (use_sym) {
+            tsym.n_pairs = (int)symh.pairs.size();
+            tsym.n_cls = nqc;
+            tsym.plist = upload(ctx, symh.pairs);
+            tsym.porb = upload(ctx, symh.orbit);
+            tsym.cls_start = upload(ctx, symh.cls_start);
+            tsym.ent = upload(ctx, symh.ent);
+            tsym.fac = upload(ctx, symh.fac);
+            sym_scr = ws_take(ctx, tcx_sym_bytes(nb, tcx_b, tsym.n_pairs));
+        }
         TcxGroups tg;
         if (tcx) {
             tg.n_groups = (int)h.pair3_j.size();
@@ -1286,7 +1411,8 @@ static kald_status linewidths_impl(kald_ctx *ctx, int32_t n_sys, const kald_syst
         cudaError_t e = launch_lw_prep(p, d, f32w, s);
         if (e == cudaSuccess)
             e = small ? launch_lw_small(p, d, sn, f32w, s)
-                : tcx ? launch_lw_tensor(p, d, tg, tc_scr, tcx_b, ctx->sm_count, tc_err, s)
+                : tcx ? launch_lw_tensor(p, d, tg, tc_scr, tcx_b, ctx->sm_count, tc_err, s,
+                                         use_sym ? &tsym : nullptr, sym_scr)
                       : launch_lw_main(p, d, f32w, ctx->sm_count, ctx->smem_optin, s);
         if (e == cudaSuccess) e = launch_lw_finish(p, d, opt->degen_tol_thz, g_d, s);
         if (e != cudaSuccess) return cuda_check(ctx, e, "kald_linewidths launch");
@@ -1298,7 +1424,8 @@ static kald_status linewidths_impl(kald_ctx *ctx, int32_t n_sys, const kald_syst
         if ((st = finish(ctx, "kald_linewidths"))) return st;
         if (errf) return fail(ctx, KALD_E_TIMEOUT, "kald_linewidths: a tensor-core pipeline wait expired");
         tot += (uint64_t)nqr * nq * (uint64_t)nb * nb * nb;
-        allowed_tot += al;
+        // one projection per orbit counts three times the orbit's ordered triples
+        allowed_tot += use_sym ? (al + 1) / 3 : al;
         off_nb += (size_t)nq * nb;
         off_eig += nn;
     }
@@ -1355,7 +1482,7 @@ static kald_status bte_assemble(kald_ctx *ctx, const kald_system *sys, const int
     o.precision = KALD_FP64;
     o.degen_tol_thz = 0.0;                       // Gamma^0 unaveraged, as in the operator
     BteHook hook{pa, pam, pb, qn};
-    if ((st = linewidths_impl(ctx, 1, sys, mesh, nu_thz, eigvec, &o, 0, -1, g0d, nullptr, &hook))) return st;
+    if ((st = linewidths_impl(ctx, 1, sys, mesh, nu_thz, eigvec, &o, -1, nullptr, g0d, nullptr, &hook))) return st;
     e = bte_combine(NN, pa, pam, pb, ctx->stream);
     if (e != cudaSuccess) return cuda_check(ctx, e, "scattering operator combine");
     *g1 = pa;
@@ -1458,13 +1585,27 @@ kald_status kald_kappa_bte(kald_ctx *ctx, const kald_system *sys, const int32_t 
 kald_status kald_linewidths(kald_ctx *ctx, int32_t n_sys, const kald_system *sys,
                             const int32_t mesh[3], const double *nu_thz, const double *eigvec,
                             const kald_options *opt, double *gamma, uint64_t *n_triplets) {
-    return linewidths_impl(ctx, n_sys, sys, mesh, nu_thz, eigvec, opt, 0, -1, gamma, n_triplets);
+    return linewidths_impl(ctx, n_sys, sys, mesh, nu_thz, eigvec, opt, -1, nullptr, gamma, n_triplets);
 }
 
 kald_status kald_linewidths_qrange(kald_ctx *ctx, const kald_system *sys, const int32_t mesh[3],
                                    const double *nu_thz, const double *eigvec, const kald_options *opt,
                                    int32_t q_begin, int32_t q_end, double *gamma, uint64_t *n_triplets) {
-    return linewidths_impl(ctx, 1, sys, mesh, nu_thz, eigvec, opt, q_begin, q_end, gamma, n_triplets);
+    if (!ctx) return KALD_E_INVALID;
+    if (!mesh || q_begin < 0 || q_begin >= q_end || (int64_t)q_end > (int64_t)mesh[0] * mesh[1] * mesh[2])
+        return fail(ctx, KALD_E_INVALID, "q range must satisfy 0 <= q_begin < q_end <= N_k (one system)");
+    std::vector<int32_t> ql(q_end - q_begin);
+    for (int32_t q = q_begin; q < q_end; ++q) ql[q - q_begin] = q;
+    return linewidths_impl(ctx, 1, sys, mesh, nu_thz, eigvec, opt, (int32_t)ql.size(), ql.data(), gamma,
+                           n_triplets);
+}
+
+kald_status kald_linewidths_qlist(kald_ctx *ctx, const kald_system *sys, const int32_t mesh[3],
+                                  const double *nu_thz, const double *eigvec, const kald_options *opt,
+                                  int32_t n_q, const int32_t *q_list, double *gamma, uint64_t *n_triplets) {
+    if (!ctx) return KALD_E_INVALID;
+    if (n_q < 1 || !q_list) return fail(ctx, KALD_E_INVALID, "q list must hold at least one q-point");
+    return linewidths_impl(ctx, 1, sys, mesh, nu_thz, eigvec, opt, n_q, q_list, gamma, n_triplets);
 }
 
 kald_status kald_phase_space(kald_ctx *ctx, const kald_system *sys, const int32_t mesh[3],

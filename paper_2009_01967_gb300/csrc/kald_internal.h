@@ -143,6 +143,7 @@ struct HostSystem {
     std::vector<int> rep_int;                          // [n_rep][3] integer cell vectors
     int n_rep = 0;
     mutable int fc3_symmetric = -1;                    // Phi3 symmetric in its last two indices (lazy)
+    mutable int fc3_perm_symmetric = -1;               // ... under every permutation of its indices (lazy)
 };
 
 // Validate and plan one kald_system (host).  Returns KALD_OK or an error.
@@ -207,7 +208,8 @@ struct LwParams {
     double omega_min_w;       // 2 pi omega_min (rad/ps)
     int qp_chunk;             // q' per work item
     int n_chunks;             // ceil(nq / qp_chunk)
-    int q0, q1;               // q-points whose linewidths are computed: [q0, q1)
+    int q0, q1;               // q-points whose linewidths are returned: [q0, q1)
+    int nqc;                  // q-points projected (rows of LwDev::partial), <= q1 - q0
     int bte;                  // 1: also scatter the rates into the BTE operator planes (FP64 paths)
     double bte_pref;          // hbar pi / (8 N_k) (eV/A^2 amu -> ps^-2)^3 x delta normalisation
     uint32_t wait_limit;      // polls of the tensor-core pipeline waits
@@ -238,7 +240,14 @@ struct LwDev {
                               // (FP32 and BF16-split paths; see wdiff.cuh)
     void *eps_work;           // [nq][nb][nb] eps^T in the working precision
     void *chi;                // [nq][n_rep] exp(-i q.R) in the working precision
-    double *partial;          // [q1 - q0][n_chunks][nb] FP64 partial sums
+    double *partial;          // [nqc][n_chunks][nb] FP64 partial sums
+    // returned q-points qout[j], j < q1 - q0 (gamma row j), and the projected
+    // ones qsel[i] = (q, number of returned q-points it stands for), i < nqc;
+    // qrow[j] = the row i of partial that holds the sums of qout[j] (those of
+    // qout[j] itself or of -qout[j])
+    const int *qout;
+    const int2 *qsel;
+    const int *qrow;
     // full-BTE assembly (p.bte): three [N][N] planes, N = nq nb, row mu = q nb + s:
     //   g1_a  (w'/w) Gamma^+ summed over s'' at column (q', s')
     //   g1_am (w'/w) Gamma^- summed over s'' at column (-q', s')
@@ -353,6 +362,29 @@ struct TcxGroups {
     const int4 *blkinfo = nullptr;    // [n_fc3] (i, rep(Rj), rep(Rk), 0), group order
     const float *fc3 = nullptr;       // [n_fc3][28] Phi3 / sqrt(mi mj mk), FP32, padded
 };
+// One projection per orbit of momentum triples (q1, q2, q3 = -(q1 + q2))
+// under permutations and inversion (Phi3 symmetric under permutations of its
+// indices, whole-mesh call): the pairs (q1, q2) of the canonical triples (the
+// lexicographically smallest ordered triple of each orbit), their orbit sizes,
+// and per inversion class {q, -q} the CSR of (3 pair + position, factor)
+// entries whose position holds a member of the class; factor = orbit size / 12
+// times 2 for a class with -q = q.
+struct TcxSymHost {
+    std::vector<int2> pairs;
+    std::vector<int> orbit;
+    std::vector<int> cls_start, ent;
+    std::vector<double> fac;
+};
+// qcls[q] = class row of q (rows 0 .. n_cls - 1), self_inv[row] = 1 where -q = q.
+void plan_tcx_sym(const int32_t mesh[3], const std::vector<int> &qf, const std::vector<int> &qcls,
+                  const std::vector<int> &self_inv, TcxSymHost &out);
+struct TcxSym {
+    int n_pairs = 0, n_cls = 0;
+    const int2 *plist = nullptr;
+    const int *porb = nullptr, *cls_start = nullptr, *ent = nullptr;
+    const double *fac = nullptr;
+};
+size_t tcx_sym_bytes(int nb, int batch, int n_pairs);
 bool tcx_supported(int nb);           // 65 <= nb <= 96 (one tile width, N = K = 192)
 int tcx_half(int nb);
 int tcx_batch(int nb, int nq, int sm_count);
@@ -361,7 +393,8 @@ int tcx_parts(int n_groups);
 void plan_tcx_parts(const HostSystem &h, int n_parts, std::vector<int> &part_start, std::vector<int> &glist);
 size_t tcx_scratch_bytes(int nb, int nq, int batch);
 cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups &g, void *scratch, int batch,
-                             int sms, int *err, cudaStream_t st);
+                             int sms, int *err, cudaStream_t st, const TcxSym *sym = nullptr,
+                             void *sym_scratch = nullptr);
 
 // ifc.cu: finite-difference force constants of a pair potential.  Neighbours
 // of each basis atom k within the cutoff (infinite lattice), CSR over k:

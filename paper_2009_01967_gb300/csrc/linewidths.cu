@@ -184,7 +184,7 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const R sig2inv = (R)delta_param(p.shape, p.sigma_w);   // the delta shape's parameter
     const R cut = (R)p.cut_w;
-    const int n_items = (p.q1 - p.q0) * p.n_chunks;
+    const int n_items = p.nqc * p.n_chunks;
     unsigned long long allowed = 0;
 
     for (;;) {
@@ -193,8 +193,11 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
         const int item = item_sm;
         __syncthreads();
         if (item >= n_items) break;
-        const int q = p.q0 + item / p.n_chunks;
+        const int qi = item / p.n_chunks;
+        const int2 qm = d.qsel[qi];
+        const int q = qm.x;
         const int chunk = item % p.n_chunks;
+        const unsigned long long allowed0 = allowed;
         for (int x = tid; x < nb; x += kThreads) red[x] = 0.0;
 
         const int qp0 = chunk * p.qp_chunk;
@@ -487,7 +490,9 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
         }
         __syncthreads();
         for (int s = tid; s < nb; s += kThreads)
-            d.partial[((size_t)(q - p.q0) * p.n_chunks + chunk) * nb + s] = red[s];
+            d.partial[((size_t)qi * p.n_chunks + chunk) * nb + s] = red[s];
+        // an item of q stands for -q as well when it takes q's linewidths
+        allowed += (unsigned long long)(qm.y - 1) * (allowed - allowed0);
         __syncthreads();
     }
     // delta-allowed triplet count
@@ -496,16 +501,20 @@ lw_main_kernel(LwParams p, LwDev d, const R *__restrict__ fc3,
 }
 
 // gamma = pref / w * sum over chunks; then average over degenerate sets.
-// q-points q0 .. q1-1; partial and gamma are indexed from q0.
-__global__ void lw_finish_kernel(int q0, int q1, int nb, int n_chunks, const double *__restrict__ partial,
-                                 const double *__restrict__ omega, const double *__restrict__ nu,
-                                 double pref, double degen_tol, double *__restrict__ gamma) {
-    const int q = q0 + blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= q1) return;
-    double *g = gamma + (size_t)(q - q0) * nb;
+// Row j of gamma is q-point qout[j], j < n_out; its sums are in row qrow[j]
+// of partial (those of q itself, or of -q).
+__global__ void lw_finish_kernel(int n_out, int nb, int n_chunks, const double *__restrict__ partial,
+                                 const int *__restrict__ qout, const int *__restrict__ qrow,
+                                 const double *__restrict__ omega, const double *__restrict__ nu, double pref,
+                                 double degen_tol, double *__restrict__ gamma) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_out) return;
+    const int q = qout[j];
+    double *g = gamma + (size_t)j * nb;
+    const size_t row = (size_t)qrow[j];
     for (int s = 0; s < nb; ++s) {
         double t = 0.0;
-        for (int c = 0; c < n_chunks; ++c) t += partial[((size_t)(q - q0) * n_chunks + c) * nb + s];
+        for (int c = 0; c < n_chunks; ++c) t += partial[(row * n_chunks + c) * nb + s];
         const double w = omega[(size_t)q * nb + s];
         g[s] = (w > 0.0) ? pref * t / w : 0.0;
     }
@@ -666,7 +675,7 @@ cudaError_t launch_lw_main(const LwParams &p, const LwDev &d, int fp32, int sm_c
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(d.allowed, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    const int n_items = (p.q1 - p.q0) * p.n_chunks;
+    const int n_items = p.nqc * p.n_chunks;
     const int grid = std::max(1, std::min(n_items, sm_count));
     if (fp32) {
         const size_t smem = lw_smem_bytes<float>(p, true);
@@ -716,8 +725,9 @@ cudaError_t launch_lw_finish(const LwParams &p, const LwDev &d, double degen_tol
                              double *gamma_out, cudaStream_t st) {
     const double pref = kHbarEvPs * kPi / 8.0 * kEvA2AmuPs2 * kEvA2AmuPs2 * kEvA2AmuPs2 /
                         (double)p.nq / (1.0 / delta_norm(p.shape, p.sigma_w));
-    lw_finish_kernel<<<counted((p.q1 - p.q0 + 63) / 64), 64, 0, st>>>(p.q0, p.q1, p.nb, p.n_chunks, d.partial,
-                                                                   d.omega, d.nu, pref, degen_tol_thz, gamma_out);
+    const int n_out = p.q1 - p.q0;
+    lw_finish_kernel<<<counted((n_out + 63) / 64), 64, 0, st>>>(n_out, p.nb, p.n_chunks, d.partial, d.qout, d.qrow,
+                                                             d.omega, d.nu, pref, degen_tol_thz, gamma_out);
     return cudaGetLastError();
 }
 

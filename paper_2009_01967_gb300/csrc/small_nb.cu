@@ -109,7 +109,9 @@ sn_kernel(LwParams p, LwDev d, SnTables t, const R *__restrict__ fc3, const type
     double *red = reinterpret_cast<double *>(
         (reinterpret_cast<uintptr_t>(eq + NB * NB) + 15) & ~uintptr_t(15));
 
-    const int q = p.q0 + blockIdx.x, chunk = blockIdx.y;
+    const int qi = blockIdx.x, chunk = blockIdx.y;
+    const int2 qm = d.qsel[qi];
+    const int q = qm.x;
     const int tid = threadIdx.x;
     for (int x = tid; x < nroot; x += kSnThreads) roots[x] = static_cast<const R2 *>(t.roots)[x];
     for (int x = tid; x < NB * NB; x += kSnThreads) eq[x] = epsT[(size_t)q * NB * NB + x];
@@ -259,13 +261,14 @@ sn_kernel(LwParams p, LwDev d, SnTables t, const R *__restrict__ fc3, const type
         }
     }
     red[tid] = sum;
+    allowed *= (unsigned long long)qm.y;           // the count of -q too, where -q takes q's linewidths
     for (int o = 16; o > 0; o >>= 1) allowed += __shfl_xor_sync(0xffffffffu, allowed, o);
     if ((tid & 31) == 0 && allowed) atomicAdd(d.allowed, allowed);
     __syncthreads();
     if (tid < NB) {
         double r = 0.0;
         for (int x = 0; x < JPC; ++x) r += red[x * NB + tid];
-        d.partial[((size_t)(q - p.q0) * p.n_chunks + chunk) * NB + tid] = r;
+        d.partial[((size_t)qi * p.n_chunks + chunk) * NB + tid] = r;
     }
 }
 
@@ -277,7 +280,7 @@ cudaError_t run_sn(const LwParams &p, const LwDev &d, const SnTables &t, cudaStr
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     ProfMark pm(p.prof, KALD_PROF_SMALL_NB, st);
-    k<<<counted(dim3(p.q1 - p.q0, p.n_chunks)), kSnThreads, smem, st>>>(p, d, t, static_cast<const R *>(d.fc3),
+    k<<<counted(dim3(p.nqc, p.n_chunks)), kSnThreads, smem, st>>>(p, d, t, static_cast<const R *>(d.fc3),
                                                                  static_cast<const R2 *>(d.eps_work));
     pm.end();
     return cudaGetLastError();

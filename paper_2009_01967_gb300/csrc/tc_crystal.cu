@@ -52,7 +52,7 @@ using namespace tc;
 // streamed A stage.  Four stages of 32 K keep three stages (48 KB) in flight
 // while the MMAs read the fourth, in the shared memory left by the resident B.
 constexpr int kBM = 128, kBK = 64, kAK = 32, kStages = 4;
-enum : int { EPI_T = 0, EPI_PHI = 1 };
+enum : int { EPI_T = 0, EPI_PHI = 1, EPI_SYM = 2 };
 
 // BN = N = K' = 2H (64, 128 or 192; crystals have nb <= 96); PB = BF16
 // pieces of the eigenvector operand B (3 where the resident copy fits in
@@ -72,9 +72,10 @@ struct XParams {
     int nb, H, Kp;            // branches, half width (nb rounded up to 32), K' = 2H
     int Mp;                   // rows nb^2 padded to a multiple of 128
     int nq, mesh0, mesh1, mesh2;
-    long long pair0;          // first pair of the batch: pair = q * nq + q'
+    long long pair0;          // first pair of the batch: pair = i * nq + q', q = qsel[i].x
     int n_pairs;
     const int *qfrac;         // [nq][3] integer mesh coordinates
+    const int2 *qsel;         // projected q-points (q, multiplicity); row i of the slots and sums
     __nv_bfloat16 *t1h, *t1l; // GEMM1 output [pairs][Kp][Mp]
     const float4 *wn;         // [nq][nb] FP32 pairs (w hi, w lo, n hi, n lo); w = 0 when masked
     float sig2inv, cut;       // delta-shape parameter (delta_param), window half width
@@ -84,12 +85,30 @@ struct XParams {
                               // mode's rows in its first tile (0) and in the next tile (1)
     unsigned long long *allowed;
     uint32_t wait_limit;      // polls of the pipeline waits
+    // one projection per orbit of momentum triples (EPI_SYM): pair = plist[i]
+    // (q1, q2), the triple (q1, q2, -(q1 + q2)); porb[i] = orbit size; per
+    // pair of the batch the epilogue writes the mode sums of position 1 into
+    // slots ([pair][nb][2], as above), the row sums of position 2 into rbuf
+    // ([pair][Mp]) and the tile column sums of position 3 into cbuf
+    // ([pair][row tiles][nb])
+    const int2 *plist;
+    const int *porb;
+    float *rbuf, *cbuf;
 };
 
+// row i (index into qsel) of pair a of the batch
+__device__ __forceinline__ int row_of(const XParams &x, int a) { return (int)((x.pair0 + a) / x.nq); }
 __device__ __forceinline__ void pair_of(const XParams &x, int a, int &q, int &qp, int &qpp) {
     const long long pi = x.pair0 + a;
-    q = (int)(pi / x.nq);
-    qp = (int)(pi - (long long)q * x.nq);
+    if (x.plist) {
+        const int2 t = x.plist[pi];
+        q = t.x;
+        qp = t.y;
+    } else {
+        const int qi = (int)(pi / x.nq);
+        q = x.qsel[qi].x;
+        qp = (int)(pi - (long long)qi * x.nq);
+    }
     const int *kq = x.qfrac + 3 * q, *kp = x.qfrac + 3 * qp;
     const int k0 = (kq[0] + kp[0]) % x.mesh0;
     const int k1 = (kq[1] + kp[1]) % x.mesh1;
@@ -128,7 +147,7 @@ __device__ __forceinline__ uint32_t pack_f16x2(__half lo_half, __half hi_half) {
 // without touching memory it does not own.
 constexpr int kEpiWarps = 8;
 template <int EPI> struct Warps {
-    static constexpr int kEpi = EPI == EPI_PHI ? 12 : 8;     // epilogue warps
+    static constexpr int kEpi = EPI != EPI_T ? 12 : 8;      // epilogue warps
     static constexpr int kGroups = kEpi / 4;                  // column groups
     static constexpr int kThreads = 32 * (4 + kEpi);
 };
@@ -152,6 +171,10 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
     __shared__ float4 wpk_sm[64], npk_sm[64];
     __shared__ float2 iwk_sm[64];
     __shared__ float rowsum[2][3][kBM];          // [tile parity][column group][row]
+    // EPI_SYM: row sums of position 2 and per-quadrant column sums of position 3
+    constexpr int kSymRows = EPI == EPI_SYM ? kBM : 1, kSymCols = EPI == EPI_SYM ? 96 : 1;
+    __shared__ float rowsum_b[2][3][kSymRows];
+    __shared__ float colsum[2][4][kSymCols];
     constexpr int NE = Warps<EPI>::kEpi, NG = Warps<EPI>::kGroups;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -174,7 +197,7 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
         fail_sm = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (EPI == EPI_PHI) {
+    if (EPI != EPI_T) {
         // columns of q'': masked modes and padding get a frequency no window reaches
         for (int t = threadIdx.x; t < 64; t += blockDim.x) {
             float mw[2][2], mn[2][2], iw[2];
@@ -342,6 +365,104 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
                         }
                     }
                 }
+            } else if (EPI == EPI_SYM) {
+                // positions 1 = (q, s), 2 = (q', s'), 3 = (-q'', s'') of the triple;
+                // w3 = w(q''), n3 = n(q'').  With D1 = G(w2 + w3 - w1),
+                // D2 = G(w1 + w3 - w2), D3 = G(w1 + w2 - w3) (Gaussian, or the
+                // chosen shape, inside the window), each position p takes
+                //   F1 = (n2 - n3)(D3 - D2) + (1 + n2 + n3) D1
+                //   F2 = (n1 - n3)(D3 - D1) + (1 + n1 + n3) D2
+                //   F3 = (n1 - n2)(D2 - D1) + (1 + n1 + n2) D3
+                // times |phi|^2 / (w of the other two positions).
+                const int s = r_hi, sp = r_lo;
+                const float4 a0 = rv ? x.wn[(size_t)q * nb + s] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 a1 = rv ? x.wn[(size_t)qp * nb + sp] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const bool live = rv && a0.x > 0.0f && a1.x > 0.0f;
+                const F2 wp = f2_add(F2{a0.x, a0.y}, F2{a1.x, a1.y});     // w1 + w2
+                const F2 wm = f2_add(F2{a0.x, a0.y}, F2{-a1.x, -a1.y});   // w1 - w2
+                const float2 WPH = make_float2(wp.h, wp.h), WPL = make_float2(wp.l, wp.l);
+                const float2 WMH = make_float2(wm.h, wm.h), WML = make_float2(wm.l, wm.l);
+                const float2 N2H = make_float2(a1.z, a1.z), N2L = make_float2(a1.w, a1.w);
+                const float2 N1H = make_float2(a0.z, a0.z), N1L = make_float2(a0.w, a0.w);
+                const float2 K2 = make_float2(1.0f + a1.z, 1.0f + a1.z), K1 = make_float2(1.0f + a0.z, 1.0f + a0.z);
+                const float n12 = __fadd_rn(__fsub_rn(a0.z, a1.z), __fsub_rn(a0.w, a1.w));   // n1 - n2
+                const float2 N12 = make_float2(n12, n12);
+                const float2 S12 = make_float2(1.0f + a0.z + a1.z, 1.0f + a0.z + a1.z);
+                const float rf = live ? 1.0f / (a0.x * a1.x) : 0.0f;                      // 1 / (w1 w2)
+                const float2 RF = make_float2(rf, rf), M1 = make_float2(-1.0f, -1.0f);
+                float2 acc1 = make_float2(0.0f, 0.0f), acc2 = make_float2(0.0f, 0.0f);
+                for (int ci = hf; ok && ci < H / 16; ci += NG) {
+                    const int c0 = ci * 16;
+                    float re[16], im[16];
+                    tmem_ld16x2(taddr + c0, taddr + H + c0, re, im);
+                    float cv[16];
+#pragma unroll
+                    for (int k = 0; k < 16; k += 2) {
+                        const int u = (c0 + k) >> 1;
+                        const float4 cw = wpk_sm[u], cn = npk_sm[u];
+                        const float2 mwh = make_float2(cw.x, cw.y), mwl = make_float2(cw.z, cw.w);
+                        const float2 mnh = make_float2(cn.x, cn.y), mnl = make_float2(cn.z, cn.w);
+                        const float2 d3 = __fadd2_rn(__fadd2_rn(WPH, mwh), __fadd2_rn(WPL, mwl));   // w1 + w2 - w3
+                        const float2 d1 = __fadd2_rn(__fadd2_rn(WMH, mwh), __fadd2_rn(WML, mwl));   // w1 - w2 - w3
+                        const float2 d2 = __fadd2_rn(__ffma2_rn(M1, mwh, WMH), __ffma2_rn(M1, mwl, WML));   // w1 - w2 + w3
+                        const float2 n23 = __fadd2_rn(__fadd2_rn(N2H, mnh), __fadd2_rn(N2L, mnl));  // n2 - n3
+                        const float2 n13 = __fadd2_rn(__fadd2_rn(N1H, mnh), __fadd2_rn(N1L, mnl));  // n1 - n3
+                        const float2 s23 = __ffma2_rn(M1, mnh, K2);                                 // 1 + n2 + n3
+                        const float2 s13 = __ffma2_rn(M1, mnh, K1);                                 // 1 + n1 + n3
+                        float2 e1 = delta_shape2(d1, x.shape, s2i), e2 = delta_shape2(d2, x.shape, s2i);
+                        float2 e3 = delta_shape2(d3, x.shape, s2i);
+                        const bool h1x = fabsf(d1.x) < cut, h1y = fabsf(d1.y) < cut;
+                        const bool h2x = fabsf(d2.x) < cut, h2y = fabsf(d2.y) < cut;
+                        const bool h3x = fabsf(d3.x) < cut, h3y = fabsf(d3.y) < cut;
+                        e1.x = h1x ? e1.x : 0.0f; e1.y = h1y ? e1.y : 0.0f;
+                        e2.x = h2x ? e2.x : 0.0f; e2.y = h2y ? e2.y : 0.0f;
+                        e3.x = h3x ? e3.x : 0.0f; e3.y = h3y ? e3.y : 0.0f;
+                        const float2 f1 = __ffma2_rn(n23, __fadd2_rn(e3, __fmul2_rn(M1, e2)), __fmul2_rn(s23, e1));
+                        const float2 f2 = __ffma2_rn(n13, __fadd2_rn(e3, __fmul2_rn(M1, e1)), __fmul2_rn(s13, e2));
+                        const float2 f3 = __ffma2_rn(N12, __fadd2_rn(e2, __fmul2_rn(M1, e1)), __fmul2_rn(S12, e3));
+                        const float2 r2 = make_float2(re[k], re[k + 1]), i2 = make_float2(im[k], im[k + 1]);
+                        const float2 p2 = live ? __ffma2_rn(r2, r2, __fmul2_rn(i2, i2)) : make_float2(0.0f, 0.0f);
+                        const float2 pw = __fmul2_rn(p2, iwk_sm[u]);                                // |phi|^2 / w3
+                        acc1 = __ffma2_rn(pw, f1, acc1);
+                        acc2 = __ffma2_rn(pw, f2, acc2);
+                        const float2 c3 = __fmul2_rn(__fmul2_rn(p2, f3), RF);
+                        cv[k] = c3.x;
+                        cv[k + 1] = c3.y;
+                        if (live)
+                            cnt += (unsigned)((h1x || h2x) + (h2x || h3x) + (h1x || h3x)) +
+                                   (unsigned)((h1y || h2y) + (h2y || h3y) + (h1y || h3y));
+                    }
+                    // column sums over the warp's 32 rows: halving exchanges, then
+                    // lanes 2c and 2c + 1 hold column c of the chunk
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const bool up = lane & 16;
+                        const float give = up ? cv[i] : cv[i + 8], keep = up ? cv[i + 8] : cv[i];
+                        cv[i] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const bool up = lane & 8;
+                        const float give = up ? cv[i] : cv[i + 4], keep = up ? cv[i + 4] : cv[i];
+                        cv[i] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        const bool up = lane & 4;
+                        const float give = up ? cv[i] : cv[i + 2], keep = up ? cv[i + 2] : cv[i];
+                        cv[i] = keep + __shfl_xor_sync(0xffffffffu, give, 4);
+                    }
+                    {
+                        const bool up = lane & 2;
+                        const float give = up ? cv[0] : cv[1], keep = up ? cv[1] : cv[0];
+                        cv[0] = keep + __shfl_xor_sync(0xffffffffu, give, 2);
+                    }
+                    cv[0] += __shfl_xor_sync(0xffffffffu, cv[0], 1);
+                    const int col = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+                    if ((lane & 1) == 0 && c0 + col < kSymCols) colsum[buf][qd][c0 + col] = cv[0];
+                }
+                rowsum[buf][hf][row] = live ? (acc1.x + acc1.y) / a1.x : 0.0f;      // / w2
+                rowsum_b[buf][hf][row] = live ? (acc2.x + acc2.y) / a0.x : 0.0f;    // / w1
             } else {
                 const int s = r_hi, sp = r_lo;
                 const float4 a0 = rv ? x.wn[(size_t)q * nb + s] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -392,17 +513,32 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[buf]);
-            if (EPI == EPI_PHI) {
+            if (EPI != EPI_T) {
                 // per-mode sums over the tile's rows: mode segment j goes to warp
                 // 4 + (j % 4), lanes take rows 32 apart, then a fixed shuffle tree.
                 // (The buffer of this tile parity is rewritten two tiles later,
                 // after the next named barrier.)
                 named_sync(1, NE * 32);
+                if (EPI == EPI_SYM && hf == 0 && ok) {
+                    // position 2: the tile's row sums; position 3: its column sums
+                    if (r < nb * nb) {
+                        float v = 0.0f;
+#pragma unroll
+                        for (int gq = 0; gq < NG; ++gq) v += rowsum_b[buf][gq][row];
+                        x.rbuf[(size_t)a * x.Mp + r] = v;
+                    }
+                    if (row < nb) {
+                        const float v = ((colsum[buf][0][row] + colsum[buf][1][row]) + colsum[buf][2][row]) +
+                                        colsum[buf][3][row];
+                        x.cbuf[((size_t)a * mt + tile) * nb + row] = v;
+                    }
+                }
                 if (hf == 0 && ok) {
                     const int rt = tile * kBM, re = min(nb * nb, rt + kBM);
                     if (rt < re) {
                         const int s_lo = rt / nb, s_hi = (re - 1) / nb;
-                        float *sl = x.slots + ((size_t)(q % x.n_slices) * x.nq + qp) * nb * 2;
+                        float *sl = EPI == EPI_SYM ? x.slots + (size_t)a * nb * 2
+                                                   : x.slots + ((size_t)(row_of(x, a) % x.n_slices) * x.nq + qp) * nb * 2;
                         for (int sm = s_lo + qd; sm <= s_hi; sm += 4) {
                             const int b0 = max(rt, sm * nb), b1 = min(re, (sm + 1) * nb);
                             float v = 0.0f;
@@ -420,8 +556,12 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__
                 }
             }
         }
-        if (EPI == EPI_PHI) {
-            unsigned long long c64 = cnt;
+        if (EPI != EPI_T) {
+            // EPI_PHI: the count of -q too, where -q takes q's linewidths;
+            // EPI_SYM: three times the count of the orbit's ordered triples
+            const unsigned long long mult = EPI == EPI_SYM ? (unsigned long long)x.porb[x.pair0 + a]
+                                                           : (unsigned long long)x.qsel[row_of(x, a)].y;
+            unsigned long long c64 = (unsigned long long)cnt * mult;
             for (int o = 16; o > 0; o >>= 1) c64 += __shfl_xor_sync(0xffffffffu, c64, o);
             if (lane == 0 && c64) atomicAdd(x.allowed, c64);
         }
@@ -946,13 +1086,13 @@ __global__ void y_scale_kernel(TcxYTables yt, float *__restrict__ wscale) {
     }
 }
 
-// gacc[q][s] = sum over q' in order of both slots of (q, q', s), FP64, for
-// the completed q in [q0, q1).
-__global__ void slots_reduce_kernel(XParams x, int q0, int q1, double *__restrict__ gacc) {
+// gacc[i][s] = sum over q' in order of both slots of (qsel[i], q', s), FP64,
+// for the completed rows i in [i0, i1).
+__global__ void slots_reduce_kernel(XParams x, int i0, int i1, double *__restrict__ gacc) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int nb = x.nb;
-    if (t >= (q1 - q0) * nb) return;
-    const int q = q0 + t / nb, s = t - (t / nb) * nb;
+    if (t >= (i1 - i0) * nb) return;
+    const int q = i0 + t / nb, s = t - (t / nb) * nb;
     const float2 *sl = reinterpret_cast<const float2 *>(x.slots) + (size_t)(q % x.n_slices) * x.nq * nb + s;
     double sum = 0.0;
 #pragma unroll 4
@@ -961,6 +1101,45 @@ __global__ void slots_reduce_kernel(XParams x, int q0, int q1, double *__restric
         sum += (double)v.x + (double)v.y;
     }
     gacc[(size_t)q * nb + s] = sum;
+}
+
+// One projection per orbit (EPI_SYM), after GEMM2 of a batch: the sums of
+// pair a of the batch per mode of each position, in a fixed order,
+//   out3[pair0 + a][0][s]   = both slots of mode s            (position 1)
+//   out3[pair0 + a][1][s']  = sum over s of rbuf[a][s nb + s'] (position 2)
+//   out3[pair0 + a][2][s''] = sum over tiles of cbuf[a][t][s''] (position 3)
+__global__ void sym_pair_sums_kernel(XParams x, float *__restrict__ out3) {
+    const int a = blockIdx.x, nb = x.nb, t = threadIdx.x;
+    if (a >= x.n_pairs || t >= 3 * nb) return;
+    const int pos = t / nb, m = t - pos * nb;
+    float v = 0.0f;
+    if (pos == 0) {
+        const float *sl = x.slots + (size_t)a * nb * 2;
+        v = sl[2 * m] + sl[2 * m + 1];
+    } else if (pos == 1) {
+        const float *rb = x.rbuf + (size_t)a * x.Mp + m;
+        for (int s = 0; s < nb; ++s) v += rb[(size_t)s * nb];
+    } else {
+        const int mt = x.Mp / kBM;
+        const float *cb = x.cbuf + (size_t)a * mt * nb + m;
+        for (int tl = 0; tl < mt; ++tl) v += cb[(size_t)tl * nb];
+    }
+    out3[((size_t)(x.pair0 + a) * 3 + pos) * nb + m] = v;
+}
+
+// gacc[i][s] = sum over the entries e of class i (CSR, a fixed order) of
+// fac[e] out3[ent[e]][s], FP64: the linewidth sums of the q-points of class
+// i ({q, -q}) from every orbit projection that holds one of them.
+__global__ void sym_class_sums_kernel(int n_cls, int nb, const int *__restrict__ cls_start,
+                                      const int *__restrict__ ent, const double *__restrict__ fac,
+                                      const float *__restrict__ out3, double *__restrict__ gacc) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_cls * nb) return;
+    const int i = t / nb, m = t - i * nb;
+    double sum = 0.0;
+    for (int e = cls_start[i]; e < cls_start[i + 1]; ++e)
+        sum += fac[e] * (double)out3[(size_t)ent[e] * nb + m];
+    gacc[t] = sum;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -1029,10 +1208,11 @@ bool tcx_y_fits(int nb, int n_rep) { return nb % 3 == 0 && tcx_y_bytes(nb, n_rep
 
 template <int BN, int PB>
 cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, Lane *lanes, TcxSched sc,
-                        long long pbeg, long long pend, bool reduce, double *gacc, int *err) {
+                        long long pbeg, long long pend, bool reduce, double *gacc, int *err, float *out3) {
     const int batch = sc.batch, tpc = sc.tpc;
+    const bool sym = lanes[0].x.plist != nullptr;
     auto k1 = tcx_gemm_kernel<EPI_T, BN, PB>;
-    auto k2 = tcx_gemm_kernel<EPI_PHI, BN, PB>;
+    auto k2 = sym ? tcx_gemm_kernel<EPI_SYM, BN, PB> : tcx_gemm_kernel<EPI_PHI, BN, PB>;
     constexpr int smem = Cfg<BN, PB>::kSmem;
     cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -1052,8 +1232,9 @@ cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, L
     const int mt = lanes[0].x.Mp / kBM;
     const int gx = (mt + tpc - 1) / tpc;
     // pairs per gather CTA (1, 2 or 4): the CTA's pairs must share q, so gp
-    // divides nq and the batch (and the first pair is a multiple of nq)
-    const int gp = (sc.gp > 1 && p.nq % sc.gp == 0 && batch % sc.gp == 0) ? sc.gp : 1;
+    // divides nq and the batch (and the first pair is a multiple of nq); the
+    // orbit pairs of EPI_SYM take one pair per CTA
+    const int gp = (!sym && sc.gp > 1 && p.nq % sc.gp == 0 && batch % sc.gp == 0) ? sc.gp : 1;
     const float2 *ew = static_cast<const float2 *>(d.eps_work), *cw = static_cast<const float2 *>(d.chi);
     // tensor-core phase sum: row tiles of kYGroups groups, about one wave of CTAs per launch
     const bool yk = sc.yk && tcx_y_fits(nb, p.n_rep) && g.y.n_groups > 0;
@@ -1097,11 +1278,15 @@ cudaError_t run_batches(const LwParams &p, const LwDev &d, const TcxGroups &g, L
         k2<<<counted(dim3(gx, x.n_pairs)), Warps<EPI_PHI>::kThreads, smem, L.st>>>(L.maps[5], L.maps[6], L.maps[7], L.maps[8],
                                                                     L.maps[9], x, tpc, err);
         p2.end();
+        if (sym) {
+            const int nt = (3 * p.nb + 31) / 32 * 32;
+            sym_pair_sums_kernel<<<counted(x.n_pairs), nt, 0, L.st>>>(x, out3);
+        }
         e = cudaEventRecord(L.done[(i >> 1) & 1], L.st);
         if (e != cudaSuccess) return e;
         // q values completed by this batch
         const int qa = (int)(p0 / p.nq), qb = (int)((p0 + x.n_pairs) / p.nq);
-        if (reduce && qb > qa) {
+        if (!sym && reduce && qb > qa) {
             if (i > 0) {
                 e = cudaStreamWaitEvent(L.st, O.done[((i - 1) >> 1) & 1], 0);
                 if (e != cudaSuccess) return e;
@@ -1175,6 +1360,72 @@ void plan_tcx_parts(const HostSystem &h, int n_parts, std::vector<int> &part_sta
     }
 }
 
+// Per lane: the row sums (position 2) and tile column sums (position 3) of a
+// batch; the per-pair sums out3 [n_pairs][3][nb] and the class sums.
+size_t tcx_sym_bytes(int nb, int batch, int n_pairs) {
+    const size_t Mp = (size_t)(nb * nb + kBM - 1) / kBM * kBM, mt = Mp / kBM;
+    return 2 * ws_round(sizeof(float) * (size_t)batch * Mp) + 2 * ws_round(sizeof(float) * (size_t)batch * mt * nb) +
+           ws_round(sizeof(float) * 3 * (size_t)n_pairs * nb);
+}
+
+// Canonical triples: for every ordered pair (q1, q2) the triple (q1, q2, q3),
+// q3 = -(q1 + q2) on the mesh, is kept when it is the smallest (lexicographic)
+// of the ordered triples its orbit under the six permutations and inversion
+// q -> -q reaches.  Each orbit is kept once, by its smallest member.
+void plan_tcx_sym(const int32_t mesh[3], const std::vector<int> &qf, const std::vector<int> &qcls,
+                  const std::vector<int> &self_inv, TcxSymHost &out) {
+    const int m0 = mesh[0], m1 = mesh[1], m2 = mesh[2], nq = m0 * m1 * m2;
+    auto flat = [&](int k0, int k1, int k2) {
+        return (((k0 % m0) + m0) % m0 * m1 + ((k1 % m1) + m1) % m1) * m2 + ((k2 % m2) + m2) % m2;
+    };
+    std::vector<int> neg(nq);
+    for (int q = 0; q < nq; ++q) neg[q] = flat(-qf[3 * q], -qf[3 * q + 1], -qf[3 * q + 2]);
+    out.pairs.clear();
+    out.orbit.clear();
+    for (int q1 = 0; q1 < nq; ++q1)
+        for (int q2 = 0; q2 < nq; ++q2) {
+            const int q3 = neg[flat(qf[3 * q1] + qf[3 * q2], qf[3 * q1 + 1] + qf[3 * q2 + 1],
+                                    qf[3 * q1 + 2] + qf[3 * q2 + 2])];
+            const std::array<int, 3> t{q1, q2, q3};
+            std::array<std::array<int, 3>, 12> img;
+            const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+            bool canonical = true;
+            for (int p = 0; p < 6 && canonical; ++p) {
+                img[2 * p] = {t[perm[p][0]], t[perm[p][1]], t[perm[p][2]]};
+                img[2 * p + 1] = {neg[img[2 * p][0]], neg[img[2 * p][1]], neg[img[2 * p][2]]};
+                canonical = !(img[2 * p] < t) && !(img[2 * p + 1] < t);
+            }
+            if (!canonical) continue;
+            std::sort(img.begin(), img.end());
+            const int n_orb = (int)(std::unique(img.begin(), img.end()) - img.begin());
+            out.pairs.push_back(make_int2(q1, q2));
+            out.orbit.push_back(n_orb);
+        }
+    // entries per class, in (class, pair, position) order
+    const int n_cls = (int)self_inv.size();
+    const size_t np = out.pairs.size();
+    out.cls_start.assign(n_cls + 1, 0);
+    std::vector<int> cls_of(3 * np);
+    for (size_t i = 0; i < np; ++i) {
+        const int q1 = out.pairs[i].x, q2 = out.pairs[i].y;
+        const int q3 = neg[flat(qf[3 * q1] + qf[3 * q2], qf[3 * q1 + 1] + qf[3 * q2 + 1], qf[3 * q1 + 2] + qf[3 * q2 + 2])];
+        const int qs[3] = {q1, q2, q3};
+        for (int pos = 0; pos < 3; ++pos) {
+            cls_of[3 * i + pos] = qcls[qs[pos]];
+            ++out.cls_start[qcls[qs[pos]] + 1];
+        }
+    }
+    for (int c = 0; c < n_cls; ++c) out.cls_start[c + 1] += out.cls_start[c];
+    out.ent.assign(3 * np, 0);
+    out.fac.assign(3 * np, 0.0);
+    std::vector<int> fill(out.cls_start.begin(), out.cls_start.end() - 1);
+    for (size_t e = 0; e < 3 * np; ++e) {
+        const int c = cls_of[e], at = fill[c]++;
+        out.ent[at] = (int)e;
+        out.fac[at] = out.orbit[e / 3] / 12.0 * (self_inv[c] ? 2.0 : 1.0);
+    }
+}
+
 size_t tcx_scratch_bytes(int nb, int nq, int batch) {
     const int H = tcx_half(nb), Kp = 2 * H, BN = 2 * H;
     const size_t Mp = (size_t)(nb * nb + kBM - 1) / kBM * kBM;
@@ -1196,10 +1447,10 @@ size_t tcx_scratch_bytes(int nb, int nq, int batch) {
 // fixes the schedule instead.
 // Problems too small to time (fewer than two samples of pairs) take the default.
 static std::mutex g_tune_mu;
-static std::map<std::array<int, 5>, TcxSched> g_tuned;
+static std::map<std::array<int, 6>, TcxSched> g_tuned;
 
 template <typename Run>
-TcxSched tcx_schedule(int nb, int nq, int n_groups, bool y_ok, int sms, int mt, int batch_max, long long pbeg,
+TcxSched tcx_schedule(int nb, int nq, int n_groups, bool y_ok, bool sym, int sms, int mt, int batch_max, long long pbeg,
                       long long pend,
                       Run &run, cudaStream_t st, cudaStream_t aux, cudaEvent_t fork_ev, unsigned long long *allowed,
                       int *err, cudaError_t &e) {
@@ -1223,7 +1474,7 @@ TcxSched tcx_schedule(int nb, int nq, int n_groups, bool y_ok, int sms, int mt, 
         if (ey) def.yk = std::atoi(ey) != 0 ? yk0 : 0;
         return def;
     }
-    const std::array<int, 5> key{nb, nq, n_groups, sms, yk0};
+    const std::array<int, 6> key{nb, nq, n_groups, sms, yk0, sym ? 1 : 0};
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tuned.find(key);
@@ -1238,6 +1489,7 @@ TcxSched tcx_schedule(int nb, int nq, int n_groups, bool y_ok, int sms, int mt, 
         for (int waves : {1, 2})
             for (int yk = yk0; yk >= 0; --yk)
                 for (int gp : {1, 2, 4}) {
+                    if (sym && gp > 1) continue;              // one orbit pair per gather CTA
                     // (pairs per gather CTA only matters for the CUDA-core phase sum)
                     const TcxSched c{batch, tpc_for(batch, waves), yk ? 1 : gp, yk, tiles_for(mty, batch, waves)};
                     bool dup = false;
@@ -1288,11 +1540,12 @@ TcxSched tcx_schedule(int nb, int nq, int n_groups, bool y_ok, int sms, int mt, 
 
 // Crystal linewidth sums on tensor cores (nb <= 96).  Needs the FP32 prep
 // of launch_lw_prep (eps^T, chi, omega, occ and their FP32 pairs) in d and the group tables g;
-// writes the per-(q, s) sums into d.partial ([nq][1][nb], n_chunks = 1) for
+// writes the per-(q, s) sums of the projected q-points d.qsel into d.partial
+// ([nqc][1][nb], n_chunks = 1) for
 // launch_lw_finish, the delta-allowed count into d.allowed and bounded-wait
 // failures into err.
 cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups &g, void *scratch, int batch,
-                             int sms, int *err, cudaStream_t st) {
+                             int sms, int *err, cudaStream_t st, const TcxSym *sym, void *sym_scratch) {
     const int nb = p.nb, nq = p.nq;
     if (!tcx_supported(nb) || batch < 1 || g.n_parts < 1 || sms < 1) return cudaErrorInvalidValue;
     const int H = tcx_half(nb), Kp = 2 * H, BN = 2 * H;
@@ -1338,6 +1591,7 @@ cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups 
     x.nq = nq; x.mesh0 = p.mesh[0]; x.mesh1 = p.mesh[1]; x.mesh2 = p.mesh[2];
     x.pair0 = 0; x.n_pairs = 0;
     x.qfrac = d.qfrac;
+    x.qsel = d.qsel;
     x.t1h = nullptr; x.t1l = nullptr;
     x.wn = d.wn32;
     x.sig2inv = (float)delta_param(p.shape, p.sigma_w);
@@ -1347,10 +1601,31 @@ cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups 
     x.slots = slots;
     x.allowed = d.allowed;
     x.wait_limit = p.wait_limit;
+    x.plist = nullptr;
+    x.porb = nullptr;
+    x.rbuf = x.cbuf = nullptr;
+    float *out3 = nullptr;
+    const size_t mtl = (size_t)Mp / kBM;
+    if (sym) {
+        x.plist = sym->plist;
+        x.porb = sym->porb;
+        char *sb = static_cast<char *>(sym_scratch);
+        out3 = reinterpret_cast<float *>(sb + 2 * ws_round(sizeof(float) * (size_t)batch * Mp) +
+                                         2 * ws_round(sizeof(float) * (size_t)batch * mtl * nb));
+    }
     Lane lanes[2];
     for (int l = 0; l < 2; ++l) {
         Lane &L = lanes[l];
         L.x = x;
+        if (sym) {
+            // per lane: its batch's slots (the slot array holds at least four
+            // batches of pairs), row sums and tile column sums
+            char *sb = static_cast<char *>(sym_scratch);
+            L.x.slots = slots + (size_t)l * batch * nb * 2;
+            L.x.rbuf = reinterpret_cast<float *>(sb + l * ws_round(sizeof(float) * (size_t)batch * Mp));
+            L.x.cbuf = reinterpret_cast<float *>(sb + 2 * ws_round(sizeof(float) * (size_t)batch * Mp) +
+                                                 l * ws_round(sizeof(float) * (size_t)batch * mtl * nb));
+        }
         L.a1h = pl[l][0]; L.a1l = pl[l][1];
         L.wscale = wscale;
         L.x.t1h = pl[l][2]; L.x.t1l = pl[l][3];
@@ -1376,12 +1651,13 @@ cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups 
         lanes[0].st = st; lanes[0].done[0] = ev[0]; lanes[0].done[1] = ev[1];
         lanes[1].st = aux; lanes[1].done[0] = ev[2]; lanes[1].done[1] = ev[3];
         auto run = [&](TcxSched sc, long long b0, long long b1, bool reduce) -> cudaError_t {
-            return run_batches<192, 2>(p, d, g, lanes, sc, b0, b1, reduce, gacc, err);
+            return run_batches<192, 2>(p, d, g, lanes, sc, b0, b1, reduce, gacc, err, out3);
         };
-        const long long pbeg = (long long)p.q0 * nq, pend = (long long)p.q1 * nq;   // pairs of q in [q0, q1)
+        // pairs of the projected q-points, or the orbit pairs
+        const long long pbeg = 0, pend = sym ? (long long)sym->n_pairs : (long long)p.nqc * nq;
         const bool y_ok = tcx_y_fits(nb, p.n_rep) && g.y.n_groups > 0 && g.y.fc3 != nullptr;
-        const TcxSched sc = tcx_schedule(nb, nq, g.n_groups, y_ok, sms, Mp / kBM, batch, pbeg, pend, run, st, aux,
-                                         ev[4], d.allowed, err, e);
+        const TcxSched sc = tcx_schedule(nb, nq, g.n_groups, y_ok, sym != nullptr, sms, Mp / kBM, batch, pbeg, pend,
+                                         run, st, aux, ev[4], d.allowed, err, e);
         if (e == cudaSuccess) e = run(sc, pbeg, pend, true);
     }
     // join (also after an error, so that nothing is left running on aux)
@@ -1393,7 +1669,15 @@ cudaError_t launch_lw_tensor(const LwParams &p, const LwDev &d, const TcxGroups 
     for (int k = 0; k < 5; ++k)
         if (ev[k]) cudaEventDestroy(ev[k]);
     if (e != cudaSuccess) return e;
-    return cudaMemcpyAsync(d.partial, gacc + (size_t)p.q0 * nb, sizeof(double) * (size_t)(p.q1 - p.q0) * nb,
+    if (sym) {
+        // class sums from the per-pair sums of every orbit (after both lanes)
+        const int n = sym->n_cls * nb;
+        sym_class_sums_kernel<<<counted((n + 127) / 128), 128, 0, st>>>(sym->n_cls, nb, sym->cls_start, sym->ent,
+                                                                        sym->fac, out3, gacc);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaMemcpyAsync(d.partial, gacc, sizeof(double) * (size_t)p.nqc * nb,
                            cudaMemcpyDeviceToDevice, st);
 }
 

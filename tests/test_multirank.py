@@ -1,8 +1,9 @@
 """The N > 1 host logic of bench.py on CPU: two gloo ranks run the timing
 aggregation (max over ranks of the timed region, whole-job rate) and the
-q-sharded split (bench.shard_plan ranges, bench.gather_q_sharded all-gather)
-the way the GPU ranks do under NCCL, with the oracle standing in for
-kald_linewidths_qrange on each rank's range.  No GPU is involved."""
+q-sharded split (bench.shard_plan lists of inversion classes {q, -q},
+bench.gather_q_sharded all-gather) the way the GPU ranks do under NCCL, with
+the oracle standing in for kald_linewidths_qlist on each rank's q-points.  No
+GPU is involved."""
 
 import os
 import socket
@@ -71,11 +72,11 @@ def _shard_rank(rank, world, port, q):
     nu, eig = ph.phonons(s, w.mesh)
     import bench
     nq, nb = nu.shape
-    plan = bench.shard_plan(nq, 1, world, rank)
-    assert plan["kind"] == "qrange"
-    mine = list(range(plan["q0"], plan["q1"]))
+    plan = bench.shard_plan(w.mesh, 1, world, rank)
+    assert plan["kind"] == "qlist"
+    mine = plan["q"]
     g = an.linewidths(s, w.mesh, nu, eig, w.T, w.sigma_thz, w.n_sigma, q_list=mine)
-    full = bench.gather_q_sharded(torch.from_numpy(np.ravel(g)), plan["per"], nb, nq, world)
+    full = bench.gather_q_sharded(torch.from_numpy(np.ravel(g)), plan, nb, nq, world)
     full = full.numpy().reshape(nq, nb)
     if rank == 0:
         ref = an.linewidths(s, w.mesh, nu, eig, w.T, w.sigma_thz, w.n_sigma)
@@ -85,11 +86,11 @@ def _shard_rank(rank, world, port, q):
 
 
 def test_q_sharded_linewidths_gather_to_the_single_rank_result():
-    """The multi-GPU split of the hot path (independent q items, contiguous q
-    ranges per rank from bench.shard_plan, one all-gather of gamma by
-    bench.gather_q_sharded), emulated by two gloo ranks that each run the
-    oracle on their range: the gathered gamma equals the single-rank result
-    exactly."""
+    """The multi-GPU split of the hot path (independent q items, runs of
+    inversion classes {q, -q} per rank from bench.shard_plan, one all-gather of
+    gamma by bench.gather_q_sharded), emulated by two gloo ranks that each run
+    the oracle on their q-points: the gathered gamma equals the single-rank
+    result exactly."""
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
@@ -104,17 +105,29 @@ def test_q_sharded_linewidths_gather_to_the_single_rank_result():
 
 
 def test_shard_plan_covers_every_unit_once():
+    """Every q-point is in exactly one rank's list, each list is closed under
+    q -> -q, and the ranks' inversion classes differ in number by at most one
+    (ceil split)."""
     import bench
-    for nq in (1, 2, 7, 27, 512):
+    for mesh in ((1, 1, 1), (2, 1, 1), (7, 1, 1), (3, 3, 3), (4, 4, 4), (8, 8, 8), (3, 4, 5)):
+        nq = mesh[0] * mesh[1] * mesh[2]
+        cls = bench.inversion_classes(mesh)
+        assert sorted(q for c in cls for q in c) == list(range(nq))
         for world in (1, 2, 3, 4, 8):
-            plans = [bench.shard_plan(nq, 1, world, r) for r in range(world)]
+            plans = [bench.shard_plan(mesh, 1, world, r) for r in range(world)]
             if world == 1:
                 assert plans[0]["kind"] == "whole"
                 continue
             if nq == 1:
                 assert all(p["kind"] == "replica" for p in plans)
                 continue
-            qs = [q for p in plans for q in range(p["q0"], p["q1"])]
+            qs = sorted(q for p in plans for q in p["q"])
             assert qs == list(range(nq))
-    plans = [bench.shard_plan(1, 24, 8, r) for r in range(8)]
+            for p in plans:
+                mine = set(p["q"])
+                for c in cls:
+                    assert mine.issuperset(c) or not mine.intersection(c)
+    # the inverse of a mesh point, by its coordinates
+    assert bench.inversion_classes((4, 1, 1)) == [[0], [1, 3], [2]]
+    plans = [bench.shard_plan((1, 1, 1), 24, 8, r) for r in range(8)]
     assert sorted(x for p in plans for x in p["idx"]) == list(range(24))
