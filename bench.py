@@ -281,13 +281,15 @@ def run_reference(args):
 # the benchmark times; the summaries under profiles/ give the command.  None
 # when the kernel has changed since the counters were taken.
 TRAFFIC_PER_PAIR = {
-    # tcx_gemm_kernel on the 32-atom cell, 4x4x4 mesh, 76-pair launches:
-    # GEMM1 562.2 + 490.1 MB, GEMM2 547.6 + 0.2 MB (profiles/tcx_crystal_c2_mesh4_ncu.md)
-    "tcx_gemm1": 1052.27e6 / 76,
-    "tcx_gemm2": 547.72e6 / 76,
+    # tcx_gemm_kernel on the 32-atom cell, 4x4x4 mesh, one projection per orbit,
+    # 38-pair launches: GEMM1 274.37 + 221.41 MB, GEMM2 (three-position
+    # epilogue) 274.43 + 4.98 MB (profiles/tcx_crystal_c2_sym_mesh4_ncu.md)
+    "tcx_gemm1": 495.78e6 / 38,
+    "tcx_gemm2": 279.41e6 / 38,
 }
 TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of tcx_gemm_kernel on the same cell with a "
-                  "4x4x4 mesh (76-pair launches), per pair, scaled to the pairs of the timed launches")
+                  "4x4x4 mesh (38-pair launches, one projection per orbit), per pair, scaled to the pairs of the "
+                  "timed launches")
 
 
 def _gamma_only_band_tiles(om, cut, tile=128, symmetric=True):
@@ -414,27 +416,37 @@ def roofline_of(args, w, nbs, nu_c, opt, prof, steps, allowed, pairs_step=None):
 
 def kappa_time_to_solution(kk, ctx, w, opt, phon, kappa, n_modes, n_eig, nbs):
     """kappa from host inputs to host kappa (kald_phonons + kald_linewidths +
-    kald_kappa_*), once with the configured split path and once with the plain
-    FP64 GPU path; wall time of each and the split kappa's relative error."""
+    kald_kappa_*): the configured split path, the same path with time reversal
+    as its only symmetry (the projections the FP64 path makes; timed after one
+    untimed call that tunes its schedule), and the plain FP64 GPU path (time
+    reversal); wall time of each and the split kappas' relative errors."""
     import dataclasses
     res = {}
     kaps = {}
-    for prec in (opt.precision, "fp64"):
-        o = dataclasses.replace(opt, precision=prec)
-        nu_h = np.zeros(n_modes)
-        eig_h = np.zeros(n_eig, dtype=np.complex128)
-        gam_h = np.zeros(n_modes)
-        kap_h = np.zeros((len(nbs), 3, 3))
-        t0 = time.perf_counter()
-        phon(nu_h, eig_h)
-        kk.kald_linewidths(ctx, w.systems, w.mesh, nu_h, eig_h, o, gamma=gam_h)
-        kappa(nu_h, eig_h, gam_h, kap_h, o)
-        res[prec] = time.perf_counter() - t0
-        kaps[prec] = kap_h
-    a, b = kaps[opt.precision], kaps["fp64"]
-    err = float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
-    return {"split_s": res[opt.precision], "fp64_s": res["fp64"], "speedup": res["fp64"] / res[opt.precision],
+    runs = (("split", dataclasses.replace(opt)),
+            ("split_inversion", dataclasses.replace(opt, symmetry="inversion")),
+            ("fp64", dataclasses.replace(opt, precision="fp64", symmetry="inversion")))
+    for name, o in runs:
+        for rep in range(2 if name == "split_inversion" else 1):
+            nu_h = np.zeros(n_modes)
+            eig_h = np.zeros(n_eig, dtype=np.complex128)
+            gam_h = np.zeros(n_modes)
+            kap_h = np.zeros((len(nbs), 3, 3))
+            t0 = time.perf_counter()
+            phon(nu_h, eig_h)
+            kk.kald_linewidths(ctx, w.systems, w.mesh, nu_h, eig_h, o, gamma=gam_h)
+            kappa(nu_h, eig_h, gam_h, kap_h, o)
+            res[name] = time.perf_counter() - t0
+            kaps[name] = kap_h
+    b = kaps["fp64"]
+    err = float(np.max(np.abs(kaps["split"] - b)) / np.max(np.abs(b)))
+    err_i = float(np.max(np.abs(kaps["split_inversion"] - b)) / np.max(np.abs(b)))
+    return {"split_s": res["split"], "fp64_s": res["fp64"], "speedup": res["fp64"] / res["split"],
             "kappa_rel_err_vs_fp64": err, "tolerance": 1e-4, "within_tolerance": err <= 1e-4,
+            "split_inversion_only_s": res["split_inversion"],
+            "speedup_same_projections": res["fp64"] / res["split_inversion"],
+            "kappa_rel_err_inversion_only": err_i,
+            "symmetry": {"split": opt.symmetry, "split_inversion_only": "inversion", "fp64": "inversion"},
             "path": "host inputs -> kald_phonons -> kald_linewidths -> kald_kappa -> host kappa"}
 
 
@@ -523,7 +535,7 @@ def run_kald(args):
     sampler.start()
     ctx.profile(True)                              # per-launch CUDA events on the launching streams
     launches0 = kk.kald_kernel_launches()
-    step_ms, lw_ms = [], []
+    step_ms, lw_ms, ph_ms, kp_ms = [], [], [], []
     for _ in range(args.steps):
         flush.fill_(float(_))                      # L2 flush, outside the step events
         a = torch.cuda.Event(enable_timing=True)
@@ -534,6 +546,8 @@ def run_kald(args):
         torch.cuda.synchronize()
         step_ms.append(a.elapsed_time(b))
         lw_ms.append(e0.elapsed_time(e1))
+        ph_ms.append(a.elapsed_time(e0))
+        kp_ms.append(e1.elapsed_time(b))
     torch.cuda.synchronize()
     launches = kk.kald_kernel_launches() - launches0
     prof = ctx.profile_read()
@@ -612,7 +626,8 @@ def run_kald(args):
                                sum(projected_pairs(w.mesh, dict(shard, q=lst), opt, nbs[0]) for lst in shard["lists"])
                                if shard["kind"] == "qlist" else pairs_step),
                            "momentum_pairs_per_step": nq * nq if not gamma_only else None,
-                           "linewidth_ms": float(np.mean(lw_ms))},
+                           "linewidth_ms": float(np.mean(lw_ms)),
+                           "phonons_ms": float(np.mean(ph_ms)), "kappa_ms": float(np.mean(kp_ms))},
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},
                 "gpu_launches": int(launches),      # library kernels in the timed steps (its own counter)

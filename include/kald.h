@@ -197,7 +197,9 @@ uint64_t kald_kernel_launches(void);
  *           unit norm (interleaved re, im)
  *   vel     [Nq][nb][3] out (A/ps), or NULL
  * nb <= 96: one parallel Jacobi eigensolver per q (KALD_E_NOCONV if the
- * sweeps do not converge).  nb > 96 is supported at Gamma only (mesh
+ * sweeps do not converge) for the lower index of each pair {q, -q}; the
+ * other takes the same frequencies and the conjugate eigenvectors (time
+ * reversal: D(-q) = conj D(q) for real Phi2).  nb > 96 is supported at Gamma only (mesh
  * {1,1,1}; KALD_E_UNSUPPORTED otherwise) and up to the size whose three
  * length-nb FP64 vectors fit one CTA's shared memory (nb of about 9600 on
  * GB300; KALD_E_UNSUPPORTED beyond): Householder tridiagonalisation, Sturm

@@ -590,7 +590,32 @@ kald_status kald_phonons(kald_ctx *ctx, const kald_system *sys, const int32_t me
     const size_t nn = (size_t)nq * nb * nb;
     const bool d_nu = is_device_ptr(nu_thz), d_eig = is_device_ptr(eigvec);
     const bool d_vel = vel && is_device_ptr(vel);
-    size_t need = fc2_bytes(h) + bytes_of(qc) + 2 * ws_round(sizeof(double2) * nn) + ws_round(sizeof(int));
+    // Time reversal: D(-q) = conj D(q) (real Phi2), so only the lower index
+    // of each pair {q, -q} is diagonalised; -q takes the same frequencies and
+    // the conjugate eigenvectors (an eigenbasis of D(-q)).
+    std::vector<int> rep_row(nq, -1), rep_conj(nq, 0);
+    std::vector<double> qc_rep;
+    int nrep = 0;
+    if (!large) {
+        for (int q = 0; q < nq; ++q) {
+            const int *k = &qf[3 * (size_t)q];
+            const int qn = (((mesh[0] - k[0]) % mesh[0]) * mesh[1] + (mesh[1] - k[1]) % mesh[1]) * mesh[2] +
+                           (mesh[2] - k[2]) % mesh[2];
+            if (qn < q) {
+                rep_row[q] = rep_row[qn];
+                rep_conj[q] = 1;
+            } else {
+                rep_row[q] = nrep++;
+                qc_rep.insert(qc_rep.end(), qc.begin() + 3 * (size_t)q, qc.begin() + 3 * (size_t)q + 3);
+            }
+        }
+    }
+    const bool mirror = !large && nrep < nq;
+    const size_t nnr = mirror ? (size_t)nrep * nb * nb : nn;
+    size_t need = fc2_bytes(h) + bytes_of(qc) + 2 * ws_round(sizeof(double2) * nnr) + ws_round(sizeof(int));
+    if (mirror)
+        need += bytes_of(qc_rep) + bytes_of(rep_row) + bytes_of(rep_conj) + ws_round(sizeof(double) * nrep * nb) +
+                ws_round(sizeof(double2) * nnr);
     if (large) need += eigh_large_scratch_bytes(nb) + eigh_batch_records_bytes(1);
     if (!d_nu) need += ws_round(sizeof(double) * nq * nb);
     if (!d_eig) need += ws_round(sizeof(double2) * nn);
@@ -599,9 +624,14 @@ kald_status kald_phonons(kald_ctx *ctx, const kald_system *sys, const int32_t me
     DevSystem d;
     upload_fc2(ctx, h, d);
     const double *qcart = upload(ctx, qc);
-    double2 *D = static_cast<double2 *>(ws_take(ctx, sizeof(double2) * nn));
-    double2 *V = static_cast<double2 *>(ws_take(ctx, sizeof(double2) * nn));
+    double2 *D = static_cast<double2 *>(ws_take(ctx, sizeof(double2) * nnr));
+    double2 *V = static_cast<double2 *>(ws_take(ctx, sizeof(double2) * nnr));
     int *nonconv = static_cast<int *>(ws_take(ctx, sizeof(int)));
+    const double *qcart_rep = mirror ? upload(ctx, qc_rep) : qcart;
+    const int *row_d = mirror ? upload(ctx, rep_row) : nullptr;
+    const int *conj_d = mirror ? upload(ctx, rep_conj) : nullptr;
+    double *nu_rep = mirror ? static_cast<double *>(ws_take(ctx, sizeof(double) * nrep * nb)) : nullptr;
+    double2 *eig_rep = mirror ? static_cast<double2 *>(ws_take(ctx, sizeof(double2) * nnr)) : nullptr;
     double *nu_d = d_nu ? nu_thz : static_cast<double *>(ws_take(ctx, sizeof(double) * nq * nb));
     double2 *eig_d = d_eig ? reinterpret_cast<double2 *>(eigvec)
                            : static_cast<double2 *>(ws_take(ctx, sizeof(double2) * nn));
@@ -611,11 +641,14 @@ kald_status kald_phonons(kald_ctx *ctx, const kald_system *sys, const int32_t me
     double *big = large ? static_cast<double *>(ws_take(ctx, eigh_large_scratch_bytes(nb))) : nullptr;
     void *rec = large ? ws_take(ctx, eigh_batch_records_bytes(1)) : nullptr;
     cudaMemsetAsync(nonconv, 0, sizeof(int), s);
-    cudaError_t e = launch_dynmat(dev_fc2(h, d), nb, nq, qcart, D, s);
+    cudaError_t e = launch_dynmat(dev_fc2(h, d), nb, mirror ? nrep : nq, qcart_rep, D, s);
     if (e == cudaSuccess) {
         if (large) {
             const EighJob job{nb, D, big, nu_d, eig_d};
             e = launch_eigh_large_batch(1, &job, rec, ctx->sm_count, ctx->smem_optin, s);
+        } else if (mirror) {
+            e = launch_jacobi(nb, nrep, D, V, nu_rep, eig_rep, nonconv, ctx->smem_optin, s);
+            if (e == cudaSuccess) e = launch_mirror_phonons(nq, nb, row_d, conj_d, nu_rep, eig_rep, nu_d, eig_d, s);
         }
         else e = launch_jacobi(nb, nq, D, V, nu_d, eig_d, nonconv, ctx->smem_optin, s);
     }

@@ -167,6 +167,8 @@ struct DevFc2 {
 // [n_blk][n_at], out [n_blk][out_stride] (zero padding past nval), FP64 or FP32.
 cudaError_t launch_mass_scale(int n_blk, int nval, int n_at, const double *raw, const int *atoms,
                               const double *masses, int out_stride, int f32, void *out, cudaStream_t st);
+cudaError_t launch_mirror_phonons(int nq, int nb, const int *row, const int *conj, const double *nu_c,
+                                  const double2 *eig_c, double *nu, double2 *eig, cudaStream_t st);
 cudaError_t launch_dynmat(const DevFc2 &f, int nb, int nq, const double *qcart,
                           double2 *D, cudaStream_t st);
 cudaError_t launch_jacobi(int nb, int nq, double2 *A, double2 *V, double *nu_thz,

@@ -315,6 +315,32 @@ cudaError_t launch_jacobi(int nb, int nq, double2 *A, double2 *V, double *nu_thz
     return cudaGetLastError();
 }
 
+// Time reversal on the mesh: the phonons of q-point q are those of rep[q]
+// (frequencies equal; eigenvectors conjugated where rep[q] != q, since
+// D(-q) = conj D(q) for real Phi2).  Sources are the compact arrays of the
+// representatives, row row[q].
+__global__ void mirror_phonons_kernel(int nq, int nb, const int *__restrict__ row, const int *__restrict__ conj,
+                                      const double *__restrict__ nu_c, const double2 *__restrict__ eig_c,
+                                      double *__restrict__ nu, double2 *__restrict__ eig) {
+    const size_t per = (size_t)nb * nb;
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < (size_t)nq * per;
+         x += (size_t)gridDim.x * blockDim.x) {
+        const int q = (int)(x / per);
+        const size_t e = x - (size_t)q * per;
+        const double2 v = eig_c[(size_t)row[q] * per + e];
+        eig[x] = conj[q] ? make_double2(v.x, -v.y) : v;
+        if (e < (size_t)nb) nu[(size_t)q * nb + e] = nu_c[(size_t)row[q] * nb + e];
+    }
+}
+
+cudaError_t launch_mirror_phonons(int nq, int nb, const int *row, const int *conj, const double *nu_c,
+                                  const double2 *eig_c, double *nu, double2 *eig, cudaStream_t st) {
+    const size_t n = (size_t)nq * nb * nb;
+    const int grid = (int)std::min<size_t>((n + 255) / 256, 4096);
+    mirror_phonons_kernel<<<counted(grid), 256, 0, st>>>(nq, nb, row, conj, nu_c, eig_c, nu, eig);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_velocity_diag(const DevFc2 &f, int nb, int nq, const double *qcart,
                                  const double *nu_thz, const double2 *eig, double *vel,
                                  cudaStream_t st) {

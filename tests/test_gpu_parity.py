@@ -738,7 +738,8 @@ def test_qrange_calls_concatenate_to_the_full_call(k, case, precision):
     """kald_linewidths_qrange over a partition of the mesh into uneven
     contiguous ranges, run back to back on the one GPU, gives the full call's
     gamma and triplet counts bit for bit (register, CUDA-core and tensor-core
-    crystal paths)."""
+    crystal paths; the full call with time reversal as its only symmetry, as
+    the range calls)."""
     kk, ctx = k
     if case == "fcc4_mesh3":
         w = ki.Workload("fcc4", [ki.fcc_supercell_system(1, seed=7)], (3, 3, 3), 300.0, 0.1, 3.0)
@@ -748,7 +749,7 @@ def test_qrange_calls_concatenate_to_the_full_call(k, case, precision):
         w = _lw_case(case)
     s = w.systems[0]
     nu_o, eig_o = ph.phonons(s, w.mesh)
-    opt = _opts(kk, w, precision)
+    opt = _opts(kk, w, precision, symmetry="inversion")   # the symmetry range calls use
     g, (tot, allowed) = kk.kald_linewidths(ctx, s, w.mesh, nu_o, eig_o, opt)
     nq = w.n_q
     cuts = sorted({0, nq, max(1, nq // 5), max(1, (2 * nq) // 3)})
@@ -858,14 +859,14 @@ def test_orbit_projections_need_a_symmetric_phi3(k):
                                             ("fcc32_mesh331", "bf16split")])
 def test_qlist_rows_equal_the_full_call(k, case, precision):
     """kald_linewidths_qlist on a shuffled list with repeats, lone members of
-    pairs {q, -q} and whole pairs returns, row by row, the full call's gamma
-    bit for bit; the triplet counts add up over a partition of the mesh into
+    pairs {q, -q} and whole pairs returns, row by row, the gamma of the full
+    call with time reversal as its only symmetry bit for bit; the triplet counts add up over a partition of the mesh into
     lists; an entry outside the mesh is refused."""
     kk, ctx = k
     w = _tr_case(case)
     s = w.systems[0]
     nu_o, eig_o = ph.phonons(s, w.mesh)
-    opt = _opts(kk, w, precision)
+    opt = _opts(kk, w, precision, symmetry="inversion")   # the symmetry list calls use
     g, (tot, allowed) = kk.kald_linewidths(ctx, s, w.mesh, nu_o, eig_o, opt)
     nq = w.n_q
     g = g.reshape(nq, -1)
