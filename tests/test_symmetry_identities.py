@@ -122,3 +122,29 @@ def test_a_plausible_slip_in_the_orbit_sums_is_caught(slip):
     w = ki.small_binary(mesh=(3, 3, 1), sigma=0.1)
     gam, ref, _ = _orbit_gamma(w, slip=slip)
     assert np.max(np.abs(gam - ref) / np.maximum(np.abs(ref), 1e-6 * ref.max())) > 1e-3
+
+
+@pytest.mark.parametrize("mesh", [(2, 2, 2), (3, 3, 1), (4, 2, 1), (3, 4, 5)])
+def test_orbit_count_of_the_bench_matches_a_brute_force_enumeration(mesh):
+    """bench.orbit_pairs (the projections the tensor path makes on a whole
+    mesh) equals the number of orbits of ordered momentum triples under the
+    six permutations and inversion, enumerated here one triple at a time."""
+    import bench
+    kf = an.mesh_fractions(mesh)
+    nq = len(kf)
+
+    def idx(k):
+        return int(an.mesh_index(mesh, np.asarray(k)))
+    neg = [idx(-kf[q]) for q in range(nq)]
+    seen, n = set(), 0
+    for q1 in range(nq):
+        for q2 in range(nq):
+            t = (q1, q2, neg[idx(kf[q1] + kf[q2])])
+            if t in seen:
+                continue
+            n += 1
+            for p in itertools.permutations(t):
+                seen.add(p)
+                seen.add(tuple(neg[x] for x in p))
+    assert bench.orbit_pairs(mesh) == n
+    assert len(seen) == nq * nq
