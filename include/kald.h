@@ -196,8 +196,9 @@ uint64_t kald_kernel_launches(void);
  *   eigvec  [Nq][nb][nb][2] out, complex128, row s = eigenvector of mode s,
  *           unit norm (interleaved re, im)
  *   vel     [Nq][nb][3] out (A/ps), or NULL
- * nb <= 96: one parallel Jacobi eigensolver per q (KALD_E_NOCONV if the
- * sweeps do not converge) for the lower index of each pair {q, -q}; the
+ * nb <= 96: one Householder tridiagonalisation + implicit QL eigensolver per q
+ * (KALD_E_NOCONV if an eigenvalue takes more than 60 QL sweeps) for the lower
+ * index of each pair {q, -q}; the
  * other takes the same frequencies and the conjugate eigenvectors (time
  * reversal: D(-q) = conj D(q) for real Phi2).  nb > 96 is supported at Gamma only (mesh
  * {1,1,1}; KALD_E_UNSUPPORTED otherwise) and up to the size whose three

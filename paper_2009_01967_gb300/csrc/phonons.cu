@@ -1,5 +1,6 @@
 // Harmonic phonons on the GPU (FP64): Bloch-summed dynamical matrix, a
-// parallel cyclic Jacobi Hermitian eigensolver with one CTA per q-point, and
+// Householder-QL Hermitian eigensolver with one CTA per q-point (a parallel
+// cyclic Jacobi solver where its shared memory does not fit), and
 // Hellmann-Feynman group velocities.
 //
 // Paper: section "Lattice Dynamics" -- D(q) = sum_R Phi2(i0, jR)/sqrt(mi mj)
@@ -206,6 +207,258 @@ jacobi_kernel(int nb, double2 *__restrict__ Ain, double2 *__restrict__ Vt_all,
     }
 }
 
+// Householder-QL Hermitian eigensolver, one matrix per CTA (FP64), about a
+// twentieth of the Jacobi sweeps' flops:
+//  1. tridiagonalisation by complex reflectors H_k = I - tau_k v_k v_k^H
+//     (v_k[k+1] = 1, the rest stored below the subdiagonal of column k of A in
+//     shared memory); the subdiagonal beta_k is real for k < n-2, and the last
+//     one is made real by a phase on the last index;
+//  2. implicit QL with Wilkinson shifts on the real tridiagonal: thread 0 forms
+//     the rotations of each sweep, every thread applies them to its row of the
+//     real eigenvector matrix Z (shared memory, column-major);
+//  3. eigenvectors Q P Z: the phase, then the reflectors in reverse order,
+//     each thread on one column of a global scratch G[dof][j] (coalesced);
+//  4. ascending order, as the Jacobi kernel writes it.
+// Shared memory: A n*n complex, Z n*n real, d, e, tau, work, order.
+constexpr int kHqlThreads = 256;
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+
+// (x, y) summed over the CTA in a fixed order; every thread gets the sum.
+__device__ double2 hql_block_sum(double2 v, double2 *red) {
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    __syncthreads();                               // red is free again
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double2 t = make_double2(0.0, 0.0);
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = cadd(t, red[w]);
+    return t;
+}
+
+struct HqlLayout {
+    size_t z, d, e, tau, w, red, ord, bytes;
+};
+__host__ __device__ inline HqlLayout hql_layout(int n) {
+    auto up16 = [](size_t b) { return (b + 15) & ~size_t(15); };
+    HqlLayout L;
+    L.z = up16(sizeof(double2) * (size_t)n * n);
+    L.d = up16(L.z + sizeof(double) * (size_t)n * n);
+    L.e = up16(L.d + sizeof(double) * n);
+    L.tau = up16(L.e + sizeof(double) * n);
+    L.w = up16(L.tau + sizeof(double2) * n);
+    L.red = up16(L.w + sizeof(double2) * n);
+    L.ord = up16(L.red + sizeof(double2) * (kHqlThreads / 32));
+    L.bytes = up16(L.ord + sizeof(int) * n);
+    return L;
+}
+
+__global__ void __launch_bounds__(kHqlThreads)
+hermitian_ql_kernel(int n, const double2 *__restrict__ Ain, double2 *__restrict__ G_all,
+                    double *__restrict__ nu_out, double2 *__restrict__ eig_out, int *nonconv) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const HqlLayout L = hql_layout(n);
+    double2 *A = reinterpret_cast<double2 *>(smem_raw);                 // [n][n] row-major
+    double *Zt = reinterpret_cast<double *>(smem_raw + L.z);            // Zt[col * n + row]
+    double *d = reinterpret_cast<double *>(smem_raw + L.d);
+    double *e = reinterpret_cast<double *>(smem_raw + L.e);
+    double2 *tau = reinterpret_cast<double2 *>(smem_raw + L.tau);
+    double2 *w = reinterpret_cast<double2 *>(smem_raw + L.w);           // tridiagonalisation
+    double *rc = reinterpret_cast<double *>(smem_raw + L.w);            // QL rotations (over w)
+    double *rs = rc + n;
+    double2 *red = reinterpret_cast<double2 *>(smem_raw + L.red);
+    int *ord = reinterpret_cast<int *>(smem_raw + L.ord);
+    __shared__ int ql_lo, ql_hi, ql_go, ql_fail;
+
+    const int q = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    const double2 *Aq = Ain + (size_t)q * n * n;
+    double2 *G = G_all + (size_t)q * n * n;
+    const double2 one = make_double2(1.0, 0.0);
+
+    // the Hermitian part (D + D^dagger)/2, Z = I
+    for (int x = tid; x < n * n; x += nt) {
+        const int r = x / n, c = x - (x / n) * n;
+        const double2 a = Aq[(size_t)r * n + c], b = Aq[(size_t)c * n + r];
+        A[x] = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+        Zt[x] = (r == c) ? 1.0 : 0.0;
+    }
+    if (tid == 0) ql_fail = 0;
+    __syncthreads();
+
+    // ---- 1. tridiagonalisation
+    for (int k = 0; k + 2 < n; ++k) {
+        const int m = n - k - 1;
+        double2 part = make_double2(0.0, 0.0);
+        for (int i = k + 2 + tid; i < n; i += nt) {
+            const double2 v = A[i * n + k];
+            part.x += v.x * v.x + v.y * v.y;
+        }
+        const double xn2 = hql_block_sum(part, red).x;
+        const double2 alpha = A[(k + 1) * n + k];
+        const bool refl = !(xn2 == 0.0 && alpha.y == 0.0);
+        double beta = alpha.x;
+        double2 t = make_double2(0.0, 0.0);
+        if (refl) {
+            beta = -copysign(sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2), alpha.x);
+            t = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
+            // v = x / (alpha - beta) below the leading 1
+            const double2 den = make_double2(alpha.x - beta, alpha.y);
+            const double dd = den.x * den.x + den.y * den.y;
+            const double2 sc = make_double2(den.x / dd, -den.y / dd);
+            for (int i = k + 2 + tid; i < n; i += nt) A[i * n + k] = cmul(A[i * n + k], sc);
+        }
+        if (tid == 0) { tau[k] = t; e[k] = beta; }
+        __syncthreads();
+        if (refl) {
+            // w = tau B v with B = A[k+1.., k+1..] Hermitian: w_i = tau sum_j conj(B_ji) v_j
+            double2 pd = make_double2(0.0, 0.0);
+            for (int i = k + 1 + tid; i < n; i += nt) {
+                double2 acc = make_double2(0.0, 0.0);
+                for (int j = k + 1; j < n; ++j) {
+                    const double2 vj = (j == k + 1) ? one : A[j * n + k];
+                    acc = cadd(acc, cmulc(A[j * n + i], vj));
+                }
+                w[i] = cmul(t, acc);
+                const double2 vi = (i == k + 1) ? one : A[i * n + k];
+                pd = cadd(pd, cmulc(w[i], vi));                  // w^H v
+            }
+            const double2 wv = hql_block_sum(pd, red);
+            const double2 a2 = cmul(make_double2(-0.5 * t.x, -0.5 * t.y), wv);
+            for (int i = k + 1 + tid; i < n; i += nt) {
+                const double2 vi = (i == k + 1) ? one : A[i * n + k];
+                w[i] = cadd(w[i], cmul(a2, vi));
+            }
+            __syncthreads();
+            // B -= v w^H + w v^H
+            for (int x = tid; x < m * m; x += nt) {
+                const int i = k + 1 + x / m, j = k + 1 + (x - (x / m) * m);
+                const double2 vi = (i == k + 1) ? one : A[i * n + k];
+                const double2 vj = (j == k + 1) ? one : A[j * n + k];
+                const double2 u = cadd(cmul(vi, make_double2(w[j].x, -w[j].y)),
+                                       cmul(w[i], make_double2(vj.x, -vj.y)));
+                A[i * n + j] = make_double2(A[i * n + j].x - u.x, A[i * n + j].y - u.y);
+            }
+            __syncthreads();
+        }
+    }
+    // the last subdiagonal element made real by the phase ph on index n-1
+    double2 ph = one;
+    if (n >= 2) {
+        const double2 sub = A[(n - 1) * n + (n - 2)];
+        const double r = hypot(sub.x, sub.y);
+        if (r > 0.0) ph = make_double2(sub.x / r, sub.y / r);
+        if (tid == 0) e[n - 2] = r;
+    }
+    for (int i = tid; i < n; i += nt) d[i] = A[i * n + i].x;
+    if (tid == 0) e[n - 1] = 0.0;
+    __syncthreads();
+
+    // ---- 2. implicit QL (thread 0 forms each sweep, all threads rotate Z)
+    int l = 0, iter = 0;                           // thread 0's state
+    for (;;) {
+        if (tid == 0) {
+            ql_go = 0;
+            while (l < n) {
+                int mm = l;
+                for (; mm < n - 1; ++mm) {
+                    const double dd = fabs(d[mm]) + fabs(d[mm + 1]);
+                    if (fabs(e[mm]) <= 1.0e-16 * dd) break;
+                }
+                if (mm == l) { ++l; iter = 0; continue; }
+                if (++iter > 60) { ql_fail = 1; ++l; iter = 0; continue; }
+                double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+                double r = hypot(g, 1.0);
+                g = d[mm] - d[l] + e[l] / (g + copysign(r, g));
+                double s = 1.0, c = 1.0, p = 0.0;
+                int i = mm - 1;
+                bool early = false;
+                for (; i >= l; --i) {
+                    const double f = s * e[i], b = c * e[i];
+                    r = hypot(f, g);
+                    e[i + 1] = r;
+                    if (r == 0.0) {                  // deflation inside the sweep
+                        d[i + 1] -= p;
+                        e[mm] = 0.0;
+                        early = true;
+                        break;
+                    }
+                    s = f / r;
+                    c = g / r;
+                    g = d[i + 1] - p;
+                    r = (d[i] - g) * s + 2.0 * c * b;
+                    p = s * r;
+                    d[i + 1] = g + p;
+                    g = c * r - b;
+                    rc[i] = c;
+                    rs[i] = s;
+                }
+                if (!early) {
+                    d[l] -= p;
+                    e[l] = g;
+                    e[mm] = 0.0;
+                }
+                ql_hi = mm - 1;
+                ql_lo = early ? i + 1 : l;
+                ql_go = 1;
+                break;
+            }
+        }
+        __syncthreads();
+        if (!ql_go) break;
+        const int hi = ql_hi, lo = ql_lo;
+        for (int r = tid; r < n; r += nt)
+            for (int i = hi; i >= lo; --i) {
+                const double zi1 = Zt[(i + 1) * n + r], zi = Zt[i * n + r];
+                Zt[(i + 1) * n + r] = rs[i] * zi + rc[i] * zi1;
+                Zt[i * n + r] = rc[i] * zi - rs[i] * zi1;
+            }
+        __syncthreads();
+    }
+    if (tid == 0 && ql_fail) atomicAdd(nonconv, 1);
+
+    // ---- 3. eigenvectors Q P Z in G[dof][j]
+    for (int x = tid; x < n * n; x += nt) {
+        const int r = x / n, j = x - (x / n) * n;
+        const double z = Zt[j * n + r];
+        G[x] = (r == n - 1) ? make_double2(z * ph.x, z * ph.y) : make_double2(z, 0.0);
+    }
+    __syncthreads();
+    for (int k = n - 3; k >= 0; --k) {
+        const double2 t = tau[k];
+        if (t.x == 0.0 && t.y == 0.0) continue;
+        for (int j = tid; j < n; j += nt) {
+            double2 dot = G[(size_t)(k + 1) * n + j];
+            for (int i = k + 2; i < n; ++i) dot = cadd(dot, cmulc(A[i * n + k], G[(size_t)i * n + j]));
+            const double2 td = cmul(t, dot);
+            G[(size_t)(k + 1) * n + j] = make_double2(G[(size_t)(k + 1) * n + j].x - td.x,
+                                                      G[(size_t)(k + 1) * n + j].y - td.y);
+            for (int i = k + 2; i < n; ++i) {
+                const double2 u = cmul(A[i * n + k], td);
+                G[(size_t)i * n + j] = make_double2(G[(size_t)i * n + j].x - u.x, G[(size_t)i * n + j].y - u.y);
+            }
+        }
+    }
+    // ---- 4. ascending order (ties by index), as rows of eig_out
+    for (int s = tid; s < n; s += nt) {
+        const double ls = d[s];
+        int rank = 0;
+        for (int t2 = 0; t2 < n; ++t2) {
+            const double lt = d[t2];
+            rank += (lt < ls) || (lt == ls && t2 < s);
+        }
+        ord[rank] = s;
+        const double w2 = ls * kEvA2AmuPs2;
+        nu_out[(size_t)q * n + rank] = (w2 >= 0.0 ? sqrt(w2) : -sqrt(-w2)) / kTwoPi;
+    }
+    __syncthreads();
+    for (int x = tid; x < n * n; x += nt) {
+        const int rk = x / n, dof = x - (x / n) * n;
+        eig_out[(size_t)q * n * n + x] = G[(size_t)dof * n + ord[rk]];
+    }
+}
+
 // Diagonal Hellmann-Feynman velocity of every mode at every q.
 __global__ void velocity_kernel(DevFc2 f, int nb, const double *__restrict__ qcart,
                                 const double *__restrict__ nu, const double2 *__restrict__ eig,
@@ -304,8 +557,19 @@ size_t jacobi_smem_bytes(int nb) {
     return b;
 }
 
+// Per-q Hermitian eigenpairs: the Householder-QL kernel where its shared
+// memory fits (nb <= 96 on GB300), the Jacobi kernel otherwise.  V is a
+// scratch of nq * nb * nb complex values.
 cudaError_t launch_jacobi(int nb, int nq, double2 *A, double2 *V, double *nu_thz,
                           double2 *eig_out, int *nonconv, size_t smem_optin, cudaStream_t st) {
+    const size_t hsm = hql_layout(nb).bytes;
+    if (nb >= 2 && hsm <= smem_optin) {
+        cudaError_t e = cudaFuncSetAttribute(hermitian_ql_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)hsm);
+        if (e != cudaSuccess) return e;
+        hermitian_ql_kernel<<<counted(nq), kHqlThreads, hsm, st>>>(nb, A, V, nu_thz, eig_out, nonconv);
+        return cudaGetLastError();
+    }
     const size_t smem = jacobi_smem_bytes(nb);
     if (smem > smem_optin) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
