@@ -283,7 +283,7 @@ def run_reference(args):
 TRAFFIC_PER_PAIR = {
     # tcx_gemm_kernel on the 32-atom cell, 4x4x4 mesh, one projection per orbit,
     # 38-pair launches: GEMM1 274.37 + 221.41 MB, GEMM2 (three-position
-    # epilogue) 274.43 + 4.98 MB (profiles/tcx_crystal_c2_sym_mesh4_ncu.md)
+    # epilogue) 274.43 + 4.98 MB (ncu --set full of the first batch's kernels)
     "tcx_gemm1": 495.78e6 / 38,
     "tcx_gemm2": 279.41e6 / 38,
 }
