@@ -65,3 +65,38 @@ def test_launch_counter_starts_at_zero_without_gpu(lib):
         pass
     lib.kald_kernel_launches.restype = ctypes.c_uint64
     assert lib.kald_kernel_launches() == 0
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """The ctypes structures of the binding have the size and field offsets
+    of the C structures in include/kald.h (compiled here with the host C
+    compiler), so an added or reordered field cannot silently shift the
+    arguments the library reads."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    from paper_2009_01967_gb300 import _abi
+    structs = {"kald_options": _abi.kald_options, "kald_system": _abi.kald_system,
+               "kald_pair_potential": _abi.kald_pair_potential}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "kald.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln.strip():
+            parts = ln.split()
+            got[tuple(parts[:-1])] = int(parts[-1])
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
