@@ -375,17 +375,22 @@ hermitian_ql_kernel(int n, const double2 *__restrict__ Ain, double2 *__restrict_
                 int i = mm - 1;
                 bool early = false;
                 for (; i >= l; --i) {
+                    // one reciprocal square root per rotation: the chain of
+                    // dependent FP64 operations on thread 0 bounds this stage
                     const double f = s * e[i], b = c * e[i];
-                    r = hypot(f, g);
-                    e[i + 1] = r;
-                    if (r == 0.0) {                  // deflation inside the sweep
+                    const double rr = f * f + g * g;
+                    if (rr == 0.0) {                 // deflation inside the sweep
+                        e[i + 1] = 0.0;
                         d[i + 1] -= p;
                         e[mm] = 0.0;
                         early = true;
                         break;
                     }
-                    s = f / r;
-                    c = g / r;
+                    const double ir = rsqrt(rr);
+                    r = rr * ir;
+                    e[i + 1] = r;
+                    s = f * ir;
+                    c = g * ir;
                     g = d[i + 1] - p;
                     r = (d[i] - g) * s + 2.0 * c * b;
                     p = s * r;
